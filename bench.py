@@ -1,0 +1,472 @@
+#!/usr/bin/env python3
+"""Benchmark: retarded phi, A grid-point updates per second per time step.
+
+Workload (default): two 48^3 sub-domains, h = 0.25 bohr, centres 2000 bohr
+apart on x (cross delays 290..294 steps), 320-step history ring, c = 137.036,
+dt = 0.05 -- synthetic Gaussian sources with continuity-consistent currents.
+One step = push (rho, Jx, Jy, Jz) of both domains + evaluate (phi, Ax, Ay, Az)
+on both grids.  One update = all four fields complete at one grid point,
+summed over every source domain including itself.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle
+on this machine's host cores on a bounded sample of the same workload instead.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2311_15429_gb300 import synth  # noqa: E402
+
+METRIC = "retarded phi,A grid updates/s per timestep vs plain path, at stated rel-L2 error"
+UNIT = "updates/s"
+L2_BYTES = 129 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=2000)
+    p.add_argument("--warmup", type=int, default=20)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--workload", default="cfg2", help="cfg1 | cfg2 | near48 (48^3 pair 200 bohr apart)")
+    p.add_argument("--no-plain", action="store_true", help="skip timing the plain direct path")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--oracle-nodes", type=int, default=1024, help="oracle sample per domain")
+    return p.parse_args()
+
+
+def get_workload(name):
+    if name == "near48":
+        w = synth.two_domain(48, 0.25, 200.0, "near48", steps=100, history=40)
+        w.description = "2 x 48^3, h=0.25 bohr, centres 200 bohr apart on x (small ring, for profiling)"
+        return w
+    return synth.workload(name)
+
+
+def lag_window(w):
+    """Largest lag any pair of the workload reads (for the pre-fill)."""
+    from paper_2311_15429_gb300 import rp
+    ctx = rp.rp_create(w.c, w.dt, flags=rp.RP_FLAG_PLAN_ONLY)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        return rp.rp_query(ctx)["max_lag"]
+    finally:
+        rp.rp_destroy(ctx)
+
+
+# ----------------------------------------------------------------------------- dist
+
+def dist_init(args):
+    if args.gpus <= 1 and "RANK" not in os.environ:
+        return 0, 1, 0
+    import torch
+    import torch.distributed as dist
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", args.gpus))
+    local = int(os.environ.get("LOCAL_RANK", rank))
+    backend = "nccl" if (args.impl == "ours" and torch.cuda.is_available()) else "gloo"
+    if backend == "nccl":
+        torch.cuda.set_device(local)
+    dist.init_process_group(backend, rank=rank, world_size=world)
+    return rank, world, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world, device=None):
+    if world <= 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------- clocks
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            os.makedirs(os.path.join(ROOT, "gpurun_out"), exist_ok=True)
+            self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ----------------------------------------------------------------------------- roofline
+
+def algorithmic_bytes(w, info):
+    """Bytes each kernel class must move per launch (one step, all domains),
+    from the plan: spectra complex64, self kernels real float32."""
+    nd = len(w.domains)
+    out = {"fwd_plane": 0, "fwd_column": 0, "mac_inv_column": 0, "inv_plane": 0}
+    for t in range(nd):
+        m = info[(t, t)]["fft_m"]
+        kx = m[0] // 2 + 1
+        cells = kx * m[1] * m[2]
+        Nt = w.domains[t].N
+        nz = w.domains[t].n[2]
+        t2 = 4 * kx * nz * m[1] * 8
+        mac = t2                                          # write T2
+        for s in range(nd):
+            p = info[(t, s)]
+            if p["kind"] != 0:
+                continue
+            nlag = p["lag_hi"] - p["lag_lo"] + 1
+            g = cells * (4 if s == t else 8)
+            mac += nlag * (g + 4 * cells * 8)
+        out["mac_inv_column"] += mac
+        out["inv_plane"] += t2 + 4 * Nt * 4
+    for s in range(nd):
+        m = info[(s, s)]["fft_m"]
+        kx = m[0] // 2 + 1
+        Ns = w.domains[s].N
+        t1 = 4 * kx * w.domains[s].n[2] * m[1] * 8
+        out["fwd_plane"] += 4 * Ns * 4 + t1
+        out["fwd_column"] += t1 + 4 * kx * m[1] * m[2] * 8
+    return out
+
+
+def measured_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def committed_traffic(kernel, workload):
+    """dram bytes per launch from the committed ncu summary, if it was taken
+    on the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
+    if not m1 or not m2:
+        return None
+    src = os.path.join(ROOT, "paper_2311_15429_gb300", "csrc", "rp_fft_kernels.cu")
+    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m2.group(1):
+        return None
+    return float(m1.group(1))
+
+
+# ----------------------------------------------------------------------------- oracle
+
+def oracle_sample(w, hists, j0, step, nodes_per_dom, seed=0):
+    """Oracle at seeded sample nodes of every domain.  Returns (values per
+    domain, nodes per domain, wall seconds, threads)."""
+    import oracle
+    rng = np.random.default_rng(seed)
+    vals, nodes, threads = [], [], 1
+    t0 = time.perf_counter()
+    for t, d in enumerate(w.domains):
+        sel = np.sort(rng.choice(d.N, size=min(nodes_per_dom, d.N), replace=False))
+        v, threads = oracle.eval_points_parallel([x.origin for x in w.domains], [x.n for x in w.domains],
+                                                 [x.h for x in w.domains], hists, j0, w.c, w.dt, t, step, sel)
+        vals.append(v)
+        nodes.append(sel)
+    return vals, nodes, time.perf_counter() - t0, threads
+
+
+# ----------------------------------------------------------------------------- reference arm
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    w = get_workload(args.workload)
+    lag = lag_window(w)
+    W, K = args.warmup, args.steps
+    hists = [s.history(-lag - 1, 1, w.dt) for s in w.sources]
+    import oracle
+    cores = os.cpu_count() or 1
+    # calibrate with one node per thread per domain, then size the per-step
+    # sample so that the whole run stays within ~90 s of wall time
+    _, _, t_cal, _ = oracle_sample(w, hists, -lag - 1, 0, cores, seed=99)
+    per_step_budget = 90.0 / max(1, K + W)
+    nodes_per_dom = max(1, int(cores * per_step_budget / max(t_cal, 1e-9)))
+    nodes_per_dom = min(nodes_per_dom, min(d.N for d in w.domains))
+    for i in range(W):
+        oracle_sample(w, hists, -lag - 1, 0, nodes_per_dom, seed=1000 + i)
+    t_total = 0.0
+    for i in range(K):
+        _, _, dt_, threads = oracle_sample(w, hists, -lag - 1, 0, nodes_per_dom, seed=i)
+        t_total += dt_
+    pts = nodes_per_dom * len(w.domains)
+    value = pts * K / t_total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": K, "warmup": W, "ms_per_step": 1e3 * t_total / K, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "points_per_step": w.points},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{nodes_per_dom} seeded target nodes per domain per step, "
+                                   f"all {w.points} source nodes, FP64 direct retarded sum"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ----------------------------------------------------------------------------- our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    from paper_2311_15429_gb300 import rp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = get_workload(args.workload)
+    lag = lag_window(w)
+    W, K = args.warmup, args.steps
+    ncycle = min(max(w.steps, 8), 100)
+    pre = lag + 1
+    depth = max(w.history, lag + 1)
+
+    # host history: pre-fill (pre slices, t < 0) then ncycle slices; inputs on
+    # the device for the timed region: ncycle slices per domain, cycled
+    hists = [s.history(-pre, ncycle, w.dt) for s in w.sources]
+    dev_in = [torch.from_numpy(h).to(dev) for h in hists]            # [T][4][N]
+    rho = [[dev_in[d][i, 0] for d in range(len(w.domains))] for i in range(pre + ncycle)]
+    J = [[dev_in[d][i, 1:].reshape(-1) for d in range(len(w.domains))] for i in range(pre + ncycle)]
+    in_bytes = sum(x.numel() * 4 for x in dev_in)
+
+    lib = rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=rp.RP_MODE_FFT,
+                                flags=rp.RP_FLAG_PROFILE, device=local, stream=stream)
+    info = {(t, s): lib.pair_info(t, s) for t in range(len(w.domains)) for s in range(len(w.domains))}
+    for i in range(pre):
+        lib.push_all(rho[i], J[i])
+    # warm-up on continuous time (t = 0, dt, ...), the accuracy check on the
+    # last continuous step, then the rest of the warm-up on cycled inputs
+    nwc = min(W, ncycle)
+    for i in range(nwc):
+        lib.push_all(rho[pre + i], J[pre + i])
+        lib.evaluate()
+    lib.sync()
+    check_step = nwc - 1
+    acc = None
+    cpu = None
+    if rank == 0 and not args.no_cpu and check_step >= 0:
+        gpu_vals = [torch.cat([lib.phi[d][None], lib.A[d].reshape(3, -1)]).cpu().numpy()
+                    for d in range(len(w.domains))]
+        ovals, onodes, t_or, threads = oracle_sample(w, hists, -pre, check_step, args.oracle_nodes)
+        errs = []
+        for d in range(len(w.domains)):
+            g = gpu_vals[d][:, onodes[d]]
+            for f in range(4):
+                errs.append(float(np.linalg.norm(g[f] - ovals[d][:, f]) / np.linalg.norm(ovals[d][:, f])))
+        npts = sum(len(n) for n in onodes)
+        acc = {"rel_l2_max": max(errs), "rel_l2_per_field_domain": errs,
+               "checked": f"{npts} sampled nodes at step t={check_step * w.dt:.2f} vs FP64 oracle"}
+        cpu = {"value": npts / t_or, "unit": UNIT, "cores": threads, "kind": "oracle",
+               "sample": f"{args.oracle_nodes} seeded target nodes per domain x all {w.points} "
+                         f"source nodes at one step ({t_or:.1f} s wall)"}
+    for i in range(W - nwc):
+        k = pre + (nwc + i) % ncycle
+        lib.push_all(rho[k], J[k])
+        lib.evaluate()
+    lib.sync()
+
+    # ---- timed region (device-resident inputs)
+    rp.rp_kernel_stats(lib.ctx, 0, reset=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.15)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        k = pre + (W + i) % ncycle
+        lib.push_all(rho[k], J[k])
+        lib.evaluate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = e0.elapsed_time(e1)
+    ms_max = max_over_ranks(ms, world, dev)
+    value = world * w.points * K / (ms_max / 1e3)
+    kstats = {}
+    launches = 0
+    for kind in range(rp.RP_K_COUNT):
+        n, t = rp.rp_kernel_stats(lib.ctx, kind)
+        if n:
+            kstats[rp.rp_kernel_name(kind)] = {"launches": n, "avg_us": 1e3 * t / n, "total_ms": t}
+            launches += n
+    alg = algorithmic_bytes(w, info)
+    dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
+    peak, peak_kind = measured_peak()
+    ach = alg[dom] / (kstats[dom]["avg_us"] * 1e-6) / 1e9
+    roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+            "frac": ach / peak, "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)",
+            "traffic": committed_traffic(dom, w.name),
+            "algorithmic_bytes_per_launch": alg[dom]}
+    for k in kstats:
+        if k in alg:
+            kstats[k]["algorithmic_GBps"] = alg[k] / (kstats[k]["avg_us"] * 1e-6) / 1e9
+
+    # ---- plain path: direct FP32 sum of every pair
+    plain = None
+    if not args.no_plain and rank == 0:
+        with rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=rp.RP_MODE_DIRECT,
+                                   device=local, stream=stream) as dl:
+            for i in range(pre):
+                dl.push_all(rho[i], J[i])
+            nplain = 3
+            for i in range(1):
+                dl.push_all(rho[pre], J[pre])
+                dl.evaluate()
+            torch.cuda.synchronize()
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for i in range(nplain):
+                k = pre + 1 + i
+                dl.push_all(rho[k], J[k])
+                dl.evaluate()
+            b.record(stream)
+            torch.cuda.synchronize()
+            pms = a.elapsed_time(b) / nplain
+            plain = {"path": "direct FP32 retarded sum, every pair (Kahan-compensated)",
+                     "value": w.points / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": nplain,
+                     "speedup_of_ours": (w.points / (ms / K / 1e3)) / (w.points / (pms / 1e3))}
+
+    # ---- end to end through the C-ABI with host buffers
+    e2e = None
+    if not args.no_e2e:
+        ctx = lib.ctx
+        nd = len(w.domains)
+        hin = [torch.from_numpy(h).pin_memory() for h in hists]
+        hout = [torch.empty(4 * d.N, dtype=torch.float32).pin_memory() for d in w.domains]
+        hphi = [hout[d][: w.domains[d].N] for d in range(nd)]
+        hA = [hout[d][w.domains[d].N:] for d in range(nd)]
+        for i in range(3):
+            k = pre + i % ncycle
+            for d in range(nd):
+                rp.rp_push_host(ctx, d, hin[d][k, 0], hin[d][k, 1:].reshape(-1))
+            rp.rp_evaluate_host(ctx, hphi, hA)
+        rp.rp_sync(ctx)
+        Ke = max(1, min(K, 500))
+        barrier(world)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        a.record(stream)
+        for i in range(Ke):
+            k = pre + i % ncycle
+            for d in range(nd):
+                rp.rp_push_host(ctx, d, hin[d][k, 0], hin[d][k, 1:].reshape(-1))
+            rp.rp_evaluate_host(ctx, hphi, hA)
+        b.record(stream)
+        rp.rp_sync(ctx)
+        wall = time.perf_counter() - t0
+        ems = max_over_ranks(a.elapsed_time(b), world, dev)
+        e2e = {"value": world * w.points * Ke / (ems / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": sum(4 * 4 * d.N for d in w.domains),
+               "d2h_bytes_per_step": sum(4 * 4 * d.N for d in w.domains),
+               "steps": Ke, "host_wall_s": wall,
+               "api": "rp_push_host per domain + rp_evaluate_host, pinned host buffers"}
+    lib.close()
+
+    if rank != 0:
+        return
+    q_points = w.points
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
+        "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "points_per_step": q_points,
+                   "path": "FFT: Hockney self term + delay-binned cross pairs, spectral history ring",
+                   "l2": f"inputs larger than L2: {ncycle} distinct input slices per domain cycled "
+                         f"({in_bytes / 2**20:.0f} MiB), spectral ring "
+                         f"{lib_bytes_str(w, info, depth)} read per step",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "accuracy": acc,
+        "plain_path": plain,
+        "roofline": roof,
+        "kernels": kstats,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+
+
+def lib_bytes_str(w, info, depth):
+    alg = algorithmic_bytes(w, info)
+    return f"{alg['mac_inv_column'] / 2**20:.0f} MiB"
+
+
+def main():
+    args = parse()
+    rank, world, local = dist_init(args)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

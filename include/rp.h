@@ -1,0 +1,246 @@
+/*
+ * rp.h -- C-ABI of the GB300 retarded-potential library (librp.so).
+ *
+ * The library evaluates, at every time step, the retarded scalar and vector
+ * potentials of a set of sub-domains on every sub-domain grid:
+ *
+ *   phi(r_k, l) = sum_n sum_{k' in d_n} h_n^3 rho_n(k', l dt - R/c) / R
+ *   A(r_k, l)   = (1/c) sum_n sum_{k'} h_n^3 J_n(k', l dt - R/c) / R,   R = |r_k - r_k'|
+ *
+ * i.e. the Lorenz-gauge integral of Eq. 2 summed over sub-domains (Eqs. 3-4),
+ * sampled on each domain's grid (Eq. 8), with the sources between time samples
+ * given by the hat-function interpolation of Eq. 7 -- equivalently the
+ * space-time sampled Green's function G_m = h^3 T(m dt - R/c)/R of Eq. 11
+ * applied as in Eq. 12.  At R = 0 (a node and itself) the 1/R singularity is
+ * replaced by its average over the node's cell, C h^2 with
+ * C = 3 ln(2 + sqrt 3) - pi/2, at lag 0 (the paper's "smoothed Green's
+ * function" for the self domain, Sec. III after Eq. 6).  The electron charge
+ * q_e of the paper's four-vector source (Sec. II, before Eq. 2) is NOT
+ * applied; multiply by q_e = -1 if wanted.  Atomic units throughout.
+ *
+ * Grids: a domain has origin o (position of node (0,0,0)), n = (nx, ny, nz)
+ * nodes and spacing h; node (i,j,k) is at o + h(i,j,k) and has id
+ * i + nx*(j + ny*k).  Every per-domain field array is float32, x fastest.
+ *
+ * Ownership: the caller owns every input and output buffer it passes; the
+ * library owns its history rings, kernel spectra, plan and workspace.  Device
+ * pointers must be device memory of the context's device.  All work is
+ * enqueued on the context's stream and is asynchronous unless stated: a
+ * buffer passed to a call may be reused once the stream has passed that call
+ * (e.g. after rp_sync or a stream-ordered event).
+ *
+ * Errors: bad arguments and calls out of order are detected synchronously and
+ * returned as a status; nothing aborts.  A CUDA failure from earlier
+ * asynchronous work is returned by the next call that checks the stream, or
+ * by rp_sync.  rp_last_error() gives a one-line description of the last
+ * failure of a context.
+ */
+#ifndef RP_H
+#define RP_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    RP_OK = 0,
+    RP_ERR_ARG = 1,         /* invalid argument (NULL, non-positive size, ...) */
+    RP_ERR_STATE = 2,       /* call out of order (see rp_push / rp_evaluate) */
+    RP_ERR_HISTORY = 3,     /* a needed past sample is older than the first push */
+    RP_ERR_CUDA = 4,        /* CUDA runtime error, or no usable device */
+    RP_ERR_OOM = 5,         /* device allocation failed */
+    RP_ERR_UNSUPPORTED = 6, /* sizes beyond what the kernels handle */
+    RP_ERR_TIMEOUT = 7      /* a bounded device-side wait ran out */
+} rp_status;
+
+/* How pairs of domains are evaluated. */
+typedef enum {
+    /* Self term by zero-padded (Hockney) FFT convolution with the cell-averaged
+     * kernel; cross pairs of equal spacing by FFT convolution split by lag
+     * ("delay bin") with a spectral history ring; other pairs by direct sum. */
+    RP_MODE_FFT = 0,
+    /* Every pair by the direct retarded sum in FP32 with compensated
+     * accumulation (the plain path). */
+    RP_MODE_DIRECT = 1
+} rp_mode;
+
+/* Samples before the first push equal the first push: S(t <= 0) = S(0), the
+ * reading of Eqs. 7 and 9.  Without it, evaluating a step that needs such a
+ * sample returns RP_ERR_HISTORY. */
+#define RP_FLAG_GROUND_STATE_CLAMP 0x1u
+/* Plan only: no CUDA call is made and nothing is allocated; rp_finalize
+ * computes the pair plan (see rp_pair_info / rp_query) and push/evaluate
+ * return RP_ERR_STATE.  Usable on a host without a GPU. */
+#define RP_FLAG_PLAN_ONLY 0x2u
+/* Time every kernel launch with CUDA events on the context stream; read the
+ * totals with rp_kernel_stats. */
+#define RP_FLAG_PROFILE 0x4u
+
+typedef struct {
+    double c;            /* speed of light, > 0 (137.036 in atomic units) */
+    double dt;           /* time step, > 0 */
+    int history_depth;   /* minimum history ring depth in steps (0: what the geometry needs) */
+    int mode;            /* rp_mode */
+    unsigned int flags;  /* RP_FLAG_* */
+    int reserved[9];     /* set to zero */
+} rp_config;
+
+typedef struct rp_ctx rp_ctx;
+
+/* Pair kinds reported by rp_pair_info. */
+typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1 } rp_pair_kind;
+
+typedef struct {
+    int kind;          /* rp_pair_kind */
+    int lag_lo;        /* smallest lag m with a nonzero hat weight T(m dt - R/c) */
+    int lag_hi;        /* largest such lag; the pair reads steps l-lag_hi .. l-lag_lo */
+    int fft_m[3];      /* padded FFT size per axis (0 for direct pairs) */
+    double r_min;      /* smallest node distance between the two grids (0 for self) */
+    double r_max;      /* largest node distance */
+} rp_pair_info_t;
+
+typedef struct {
+    int ndomains;
+    int npairs_fft;
+    int npairs_direct;
+    int max_lag;              /* largest lag_hi over all pairs */
+    int raw_depth;            /* raw (rho, J) ring depth in steps, 0 if no pair reads it */
+    int spectral_depth;       /* largest spectral ring depth in steps */
+    long long step;           /* index of the last completed push round, -1 before the first */
+    long long device_bytes;   /* device memory held by the context */
+    long long spectral_bytes; /* of which: spectral history rings */
+    long long kernel_bytes;   /* of which: kernel spectra */
+    long long points;         /* sum of grid points over all domains */
+} rp_stats;
+
+/* Kernel classes timed under RP_FLAG_PROFILE. */
+typedef enum {
+    RP_K_RING_PUSH = 0,     /* raw slice into the history ring */
+    RP_K_FWD_PLANE = 1,     /* forward FFT, x and y axes, one z-plane per block */
+    RP_K_FWD_COLUMN = 2,    /* forward FFT along z, into the spectral ring */
+    RP_K_MAC_INV_COLUMN = 3,/* spectral multiply-accumulate over (source, lag) + inverse FFT along z */
+    RP_K_INV_PLANE = 4,     /* inverse FFT along y and x, crop, scale, write phi/A */
+    RP_K_DIRECT = 5,        /* direct retarded sum */
+    RP_K_COUNT = 6
+} rp_kernel_kind;
+
+/*
+ * rp_create -- make a context on CUDA device `device` using `stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  With
+ * RP_FLAG_PLAN_ONLY, device and stream are ignored and no CUDA call is made.
+ * cfg is copied.  Returns RP_ERR_ARG for c <= 0, dt <= 0, an unknown mode or
+ * NULL pointers; RP_ERR_CUDA if the device cannot be used.
+ */
+rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out);
+
+/*
+ * rp_add_domain -- declare sub-domain d_n (Eqs. 3-4): origin[3] is the
+ * position of node (0,0,0), n[3] the node counts (>= 1), h > 0 the spacing.
+ * Writes the new domain's id (0, 1, ...) to *id.  Only before rp_finalize.
+ * Two domains may not have a node at the same position (RP_ERR_ARG at
+ * finalize).  At most 256 domains.
+ */
+rp_status rp_add_domain(rp_ctx *ctx, const double origin[3], const int n[3], double h, int *id);
+
+/*
+ * rp_finalize -- plan every ordered pair (target, source), self pairs
+ * included (Eq. 3): its lag window [lag_lo, lag_hi] from the smallest and
+ * largest node distance (Sec. IV: only Delta N_R = Delta D/(c dt) past steps
+ * contribute), its kind, the FFT sizes; build the kernel spectra of Eq. 11 in
+ * FP64 on the host and store them in FP32; allocate the history rings
+ * (Sec. IV: samples for [l - N_Rmax, l] are kept).  Synchronous.
+ * RP_ERR_UNSUPPORTED if a domain exceeds 96 nodes per axis in FFT mode.
+ */
+rp_status rp_finalize(rp_ctx *ctx);
+
+/*
+ * rp_push -- hand over the sample of step l of domain `id`: d_rho[N] and
+ * d_J[3][N] (Jx, Jy, Jz), device float32.  The library copies what it needs
+ * into its rings (and in FFT mode transforms it into the spectral ring)
+ * on the stream before returning control of the buffers.  The first push
+ * after a complete round (every domain pushed) starts step l + 1.  Pushing a
+ * domain twice in one round returns RP_ERR_STATE.
+ */
+rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J);
+
+/*
+ * rp_push_all -- rp_push for every domain in id order with batched launches:
+ * d_rho[n] and d_J[n] are the device buffers of domain n.  Only at the start
+ * of a round (no domain pushed yet in it).
+ */
+rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J);
+
+/*
+ * rp_push_host -- rp_push from HOST buffers h_rho[N], h_J[3][N] (pinned
+ * memory recommended): the library copies them to the device on the stream.
+ * The host buffers must stay valid and unchanged until the stream has
+ * passed the call (rp_sync).
+ */
+rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J);
+
+/*
+ * rp_evaluate -- the retarded phi and A of the last complete step l on every
+ * domain (Eq. 12: each target sums the contributions of every source, itself
+ * included; lag 0 is included since the step's own samples are visible,
+ * App. A uses j at the current time for A at the next step).  d_phi[n] has
+ * N_n floats, d_A[n] has 3*N_n floats (Ax, Ay, Az), device memory, written
+ * (not accumulated).  Returns RP_ERR_STATE if the last round is incomplete or
+ * no step was pushed, RP_ERR_HISTORY if a needed sample predates the first
+ * push and RP_FLAG_GROUND_STATE_CLAMP is not set.
+ */
+rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
+
+/*
+ * rp_evaluate_host -- rp_evaluate into HOST buffers h_phi[n] (N_n floats) and
+ * h_A[n] (3*N_n floats): the results are copied device-to-host on the
+ * stream; they are valid after rp_sync.
+ */
+rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
+
+/* rp_sync -- wait for the context's stream; reports asynchronous failures. */
+rp_status rp_sync(rp_ctx *ctx);
+
+/* rp_query -- plan and memory summary (see rp_stats).  After rp_finalize. */
+rp_status rp_query(rp_ctx *ctx, rp_stats *out);
+
+/* rp_pair_info -- plan of the ordered pair (target, source).  After rp_finalize. */
+rp_status rp_pair_info(rp_ctx *ctx, int target, int source, rp_pair_info_t *out);
+
+/*
+ * rp_kernel_stats -- under RP_FLAG_PROFILE: launches and summed device time
+ * (ms, CUDA events on the context stream) of kernel class `kind` since the
+ * last reset; waits for the stream.  reset != 0 clears all counters after
+ * reading.
+ */
+rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *total_ms,
+                          int reset);
+
+/* rp_kernel_name -- short name of a kernel class (NULL if out of range). */
+const char *rp_kernel_name(int kind);
+
+/*
+ * rp_save_state / rp_load_state -- write / read the history rings and the
+ * step counter to / from a file, so that a run resumes with bit-identical
+ * outputs.  Synchronous.  load requires a finalized context with the same
+ * domains and configuration (RP_ERR_STATE otherwise).
+ */
+rp_status rp_save_state(rp_ctx *ctx, const char *path);
+rp_status rp_load_state(rp_ctx *ctx, const char *path);
+
+/* rp_destroy -- free everything (waits for the stream).  NULL is a no-op. */
+void rp_destroy(rp_ctx *ctx);
+
+/* rp_status_str -- static name of a status code. */
+const char *rp_status_str(rp_status s);
+
+/* rp_last_error -- one-line description of the context's last failure ("" if none). */
+const char *rp_last_error(rp_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RP_H */

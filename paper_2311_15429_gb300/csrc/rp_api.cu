@@ -1,0 +1,1035 @@
+// C-ABI of the retarded-potential library: context, pair planning, memory,
+// kernel spectra and the push / evaluate launch sequence.  See include/rp.h.
+#include <algorithm>
+#include <array>
+#include <atomic>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/rp.h"
+#include "rp_internal.h"
+
+namespace rp {
+size_t smem_direct(int max_nlag);
+int direct_blocks(long long n);
+cudaError_t set_direct_smem_limit(size_t bytes);
+}  // namespace rp
+
+using namespace rp;
+
+namespace {
+
+struct DomainDesc {
+    double o[3];
+    int n[3];
+    double h;
+    long long N;
+};
+
+struct PairPlan {
+    int kind;       // rp_pair_kind
+    int lag_lo, lag_hi;
+    double rmin, rmax;
+    int m[3];       // FFT size of the target (FFT pairs)
+};
+
+struct ProfRec {
+    int kind;
+    cudaEvent_t a, b;
+};
+
+// Supported padded lengths: R * L with R in {1,2,3,4,6}, L a power of two <= 32.
+const int kSizes[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192};
+
+int good_size(int n, bool even)
+{
+    for (int m : kSizes)
+        if (m >= n && (!even || m % 2 == 0)) return m;
+    return -1;
+}
+
+Axis make_axis(int M)
+{
+    Axis a{};
+    a.M = M;
+    if (M % 3 == 0) {
+        const int rest = M / 3;
+        if (rest <= 32) { a.R = 3; a.L = rest; }
+        else { a.R = 6; a.L = rest / 2; }
+    } else if (M <= 32) {
+        a.R = 1; a.L = M;
+    } else {
+        a.R = M / 32; a.L = 32;
+    }
+    a.logL = 0;
+    while ((1 << a.logL) < a.L) ++a.logL;
+    return a;
+}
+
+}  // namespace
+
+struct rp_ctx {
+    rp_config cfg{};
+    int device = -1;
+    cudaStream_t stream = nullptr;
+    bool plan_only = false, clamp = false, profile = false;
+    bool finalized = false;
+    std::vector<DomainDesc> doms;
+    std::vector<PairPlan> pairs;   // [t * ndom + s]
+
+    // plan
+    std::vector<FwdRing> fwd;
+    std::vector<int> src_ring0, src_ring1;           // ring range per source
+    std::vector<int> src_plane_lo, src_plane_hi, src_col_lo, src_col_hi;
+    std::vector<InvTarget> inv;
+    std::vector<MacEntry> entries;
+    std::vector<DirectTarget> dtg;
+    std::vector<DirectPair> dpairs;
+    std::vector<RawRing> raw;
+    std::vector<int> raw_block0;                     // [ndom + 1], blocks of k_ring_push
+    int plane_blocks = 0, col_blocks = 0, mac_blocks = 0, invp_blocks = 0, dir_blocks = 0;
+    size_t smem_plane = 0, smem_col = 0, smem_mac = 0, smem_inv = 0, smem_dir = 0;
+    int max_lag = 0, raw_depth = 0, spec_depth = 0;
+    long long spectral_bytes = 0, kernel_bytes = 0, device_bytes = 0;
+
+    // device
+    FwdRing *d_fwd = nullptr;
+    InvTarget *d_inv = nullptr;
+    MacEntry *d_entries = nullptr;
+    DirectTarget *d_dtg = nullptr;
+    DirectPair *d_dpairs = nullptr;
+    RawRing *d_raw = nullptr;
+    std::vector<void *> allocs;
+    std::vector<float *> in_stage;    // per domain [4][N], for host pushes
+    std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
+
+    // step state
+    long long step = -1;
+    std::vector<char> pushed;
+    int npushed = 0;
+
+    // profiling
+    std::vector<ProfRec> pending;
+    std::vector<cudaEvent_t> spare_events;
+    long long launches[RP_K_COUNT] = {};
+    double ms[RP_K_COUNT] = {};
+
+    std::string last_error;
+};
+
+namespace {
+
+rp_status fail(rp_ctx *ctx, rp_status st, const std::string &msg)
+{
+    if (ctx) ctx->last_error = msg;
+    return st;
+}
+
+rp_status cuda_fail(rp_ctx *ctx, cudaError_t e, const char *what)
+{
+    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? RP_ERR_OOM : RP_ERR_CUDA, m);
+}
+
+#define RP_CUDA(ctx, expr)                                           \
+    do {                                                             \
+        cudaError_t e_ = (expr);                                     \
+        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr);   \
+    } while (0)
+
+rp_status use_device(rp_ctx *ctx)
+{
+    int cur = -1;
+    RP_CUDA(ctx, cudaGetDevice(&cur));
+    if (cur != ctx->device) RP_CUDA(ctx, cudaSetDevice(ctx->device));
+    return RP_OK;
+}
+
+template <class T>
+rp_status dev_alloc(rp_ctx *ctx, T **p, size_t count)
+{
+    void *q = nullptr;
+    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    cudaError_t e = cudaMalloc(&q, bytes);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
+    ctx->allocs.push_back(q);
+    ctx->device_bytes += (long long)bytes;
+    *p = static_cast<T *>(q);
+    return RP_OK;
+}
+
+template <class T>
+rp_status upload(rp_ctx *ctx, T **dst, const std::vector<T> &v)
+{
+    rp_status st = dev_alloc(ctx, dst, v.size());
+    if (st) return st;
+    if (!v.empty()) RP_CUDA(ctx, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
+    return RP_OK;
+}
+
+cudaEvent_t take_event(rp_ctx *ctx)
+{
+    if (!ctx->spare_events.empty()) {
+        cudaEvent_t e = ctx->spare_events.back();
+        ctx->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+// Runs `launch` (returns cudaError_t) bracketed by events when profiling.
+template <class F>
+rp_status timed_launch(rp_ctx *ctx, int kind, const char *what, F &&launch)
+{
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (ctx->profile) {
+        a = take_event(ctx);
+        b = take_event(ctx);
+        RP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
+    }
+    cudaError_t e = launch();
+    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
+    if (ctx->profile) {
+        RP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
+        ctx->pending.push_back({kind, a, b});
+    }
+    return RP_OK;
+}
+
+rp_status drain_profile(rp_ctx *ctx)
+{
+    for (const ProfRec &r : ctx->pending) {
+        RP_CUDA(ctx, cudaEventSynchronize(r.b));
+        float t = 0.0f;
+        RP_CUDA(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+        ctx->ms[r.kind] += t;
+        ctx->launches[r.kind] += 1;
+        ctx->spare_events.push_back(r.a);
+        ctx->spare_events.push_back(r.b);
+    }
+    ctx->pending.clear();
+    return RP_OK;
+}
+
+// Smallest and largest distance between the node lattices of two domains:
+// the gap between their boxes (a lower bound) and between the farthest
+// corners (exact).
+void pair_distances(const DomainDesc &t, const DomainDesc &s, bool self, double *rmin, double *rmax)
+{
+    double g2 = 0.0, f2 = 0.0;
+    for (int a = 0; a < 3; ++a) {
+        const double a0 = t.o[a], a1 = t.o[a] + t.h * (t.n[a] - 1);
+        const double b0 = s.o[a], b1 = s.o[a] + s.h * (s.n[a] - 1);
+        const double gap = std::max(0.0, std::max(a0 - b1, b0 - a1));
+        const double far = std::max(std::fabs(a1 - b0), std::fabs(b1 - a0));
+        g2 += gap * gap;
+        f2 += far * far;
+    }
+    *rmin = self ? 0.0 : std::sqrt(g2);
+    *rmax = std::sqrt(f2);
+}
+
+// True if some node of t sits on a node of s (only possible when the boxes touch).
+bool nodes_coincide(const DomainDesc &t, const DomainDesc &s)
+{
+    for (int a = 0; a < 3; ++a) {
+        const double a0 = t.o[a], a1 = t.o[a] + t.h * (t.n[a] - 1);
+        const double b0 = s.o[a], b1 = s.o[a] + s.h * (s.n[a] - 1);
+        if (a1 < b0 - 1e-12 || b1 < a0 - 1e-12) return false;
+    }
+    const double tol = 1e-9;
+    for (long long q = 0; q < t.N; ++q) {
+        const int i[3] = {(int)(q % t.n[0]), (int)((q / t.n[0]) % t.n[1]), (int)(q / ((long long)t.n[0] * t.n[1]))};
+        bool on = true;
+        for (int a = 0; a < 3 && on; ++a) {
+            const double u = (t.o[a] + t.h * i[a] - s.o[a]) / s.h;
+            const double r = std::round(u);
+            on = std::fabs(u - r) <= tol * std::max(1.0, std::fabs(u)) && r >= 0 && r <= s.n[a] - 1;
+        }
+        if (on) return true;
+    }
+    return false;
+}
+
+rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
+{
+    for (auto &kv : tw) {
+        const int M = kv.first;
+        std::vector<float2> h(M);
+        for (int j = 0; j < M; ++j) {
+            const double a = -2.0 * M_PI * (double)j / (double)M;
+            h[j] = make_float2((float)std::cos(a), (float)std::sin(a));
+        }
+        float2 *d = nullptr;
+        rp_status st = upload(ctx, &d, h);
+        if (st) return st;
+        kv.second = d;
+    }
+    return RP_OK;
+}
+
+}  // namespace
+
+// =========================================================================== C-ABI
+
+extern "C" {
+
+const char *rp_status_str(rp_status s)
+{
+    switch (s) {
+    case RP_OK: return "RP_OK";
+    case RP_ERR_ARG: return "RP_ERR_ARG";
+    case RP_ERR_STATE: return "RP_ERR_STATE";
+    case RP_ERR_HISTORY: return "RP_ERR_HISTORY";
+    case RP_ERR_CUDA: return "RP_ERR_CUDA";
+    case RP_ERR_OOM: return "RP_ERR_OOM";
+    case RP_ERR_UNSUPPORTED: return "RP_ERR_UNSUPPORTED";
+    case RP_ERR_TIMEOUT: return "RP_ERR_TIMEOUT";
+    }
+    return "RP_ERR_UNKNOWN";
+}
+
+const char *rp_last_error(rp_ctx *ctx) { return ctx ? ctx->last_error.c_str() : ""; }
+
+const char *rp_kernel_name(int kind)
+{
+    static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column",
+                                            "mac_inv_column", "inv_plane", "direct"};
+    return (kind >= 0 && kind < RP_K_COUNT) ? names[kind] : nullptr;
+}
+
+rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out)
+{
+    if (!cfg || !out) return RP_ERR_ARG;
+    *out = nullptr;
+    if (!(cfg->c > 0.0) || !(cfg->dt > 0.0) || cfg->history_depth < 0) return RP_ERR_ARG;
+    if (cfg->mode != RP_MODE_FFT && cfg->mode != RP_MODE_DIRECT) return RP_ERR_ARG;
+    rp_ctx *ctx = new rp_ctx();
+    ctx->cfg = *cfg;
+    ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
+    ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0;
+    ctx->profile = (cfg->flags & RP_FLAG_PROFILE) != 0 && !ctx->plan_only;
+    if (!ctx->plan_only) {
+        int count = 0;
+        if (cudaGetDeviceCount(&count) != cudaSuccess || device < 0 || device >= count) {
+            cudaGetLastError();
+            delete ctx;
+            return RP_ERR_CUDA;
+        }
+        ctx->device = device;
+        ctx->stream = static_cast<cudaStream_t>(stream);
+        if (cudaSetDevice(device) != cudaSuccess) {
+            cudaGetLastError();
+            delete ctx;
+            return RP_ERR_CUDA;
+        }
+    }
+    *out = ctx;
+    return RP_OK;
+}
+
+rp_status rp_add_domain(rp_ctx *ctx, const double origin[3], const int n[3], double h, int *id)
+{
+    if (!ctx || !origin || !n || !id) return RP_ERR_ARG;
+    if (ctx->finalized) return fail(ctx, RP_ERR_STATE, "rp_add_domain after rp_finalize");
+    if (!(h > 0.0) || n[0] < 1 || n[1] < 1 || n[2] < 1) return fail(ctx, RP_ERR_ARG, "bad domain size or spacing");
+    for (int a = 0; a < 3; ++a)
+        if (!std::isfinite(origin[a])) return fail(ctx, RP_ERR_ARG, "non-finite origin");
+    if ((int)ctx->doms.size() >= kMaxDomains) return fail(ctx, RP_ERR_ARG, "too many domains");
+    DomainDesc d{};
+    for (int a = 0; a < 3; ++a) { d.o[a] = origin[a]; d.n[a] = n[a]; }
+    d.h = h;
+    d.N = (long long)n[0] * n[1] * n[2];
+    ctx->doms.push_back(d);
+    *id = (int)ctx->doms.size() - 1;
+    return RP_OK;
+}
+
+rp_status rp_finalize(rp_ctx *ctx)
+{
+    if (!ctx) return RP_ERR_ARG;
+    if (ctx->finalized) return fail(ctx, RP_ERR_STATE, "already finalized");
+    const int nd = (int)ctx->doms.size();
+    if (nd == 0) return fail(ctx, RP_ERR_STATE, "no domains");
+    const double cdt = ctx->cfg.c * ctx->cfg.dt;
+    const bool fft_mode = ctx->cfg.mode == RP_MODE_FFT;
+
+    // ---- pairs: lag windows and kinds
+    ctx->pairs.assign((size_t)nd * nd, PairPlan{});
+    for (int t = 0; t < nd; ++t)
+        for (int s = 0; s < nd; ++s) {
+            const DomainDesc &T = ctx->doms[t], &S = ctx->doms[s];
+            if (t != s && nodes_coincide(T, S))
+                return fail(ctx, RP_ERR_ARG, "domains " + std::to_string(t) + " and " + std::to_string(s) +
+                                                 " have a node at the same position");
+            PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            pair_distances(T, S, t == s, &p.rmin, &p.rmax);
+            p.lag_lo = t == s ? 0 : std::max(0, (int)std::floor(p.rmin / cdt - 1e-9));
+            p.lag_hi = (int)std::floor(p.rmax / cdt + 1e-9) + 1;
+            p.kind = RP_PAIR_DIRECT;
+            if (fft_mode && std::fabs(T.h - S.h) <= 1e-12 * T.h) {
+                int m[3];
+                bool ok = true;
+                for (int a = 0; a < 3; ++a) {
+                    m[a] = good_size(T.n[a] + S.n[a] - 1, a == 0);
+                    ok = ok && m[a] > 0;
+                }
+                if (ok) {
+                    p.kind = RP_PAIR_FFT;
+                    for (int a = 0; a < 3; ++a) p.m[a] = m[a];
+                }
+            }
+            if (t == s && fft_mode && p.kind != RP_PAIR_FFT)
+                return fail(ctx, RP_ERR_UNSUPPORTED, "domain " + std::to_string(t) +
+                                                         " exceeds 96 nodes per axis (FFT self term)");
+            ctx->max_lag = std::max(ctx->max_lag, p.lag_hi);
+        }
+    // a target's FFT size: the largest over its FFT pairs
+    std::vector<std::array<int, 3>> tm(nd, {0, 0, 0});
+    std::vector<char> tgt_fft(nd, 0);
+    for (int t = 0; t < nd; ++t)
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_FFT) continue;
+            tgt_fft[t] = 1;
+            for (int a = 0; a < 3; ++a) tm[t][a] = std::max(tm[t][a], p.m[a]);
+        }
+    for (int t = 0; t < nd; ++t)
+        for (int s = 0; s < nd; ++s) {
+            PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind == RP_PAIR_FFT)
+                for (int a = 0; a < 3; ++a) p.m[a] = tm[t][a];
+        }
+
+    // ---- spectral rings: one per (source, target FFT size)
+    std::map<std::pair<int, std::array<int, 3>>, int> ring_of;
+    std::vector<std::pair<int, std::array<int, 3>>> ring_keys;
+    std::vector<int> ring_depth;
+    for (int s = 0; s < nd; ++s)
+        for (int t = 0; t < nd; ++t) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_FFT) continue;
+            auto key = std::make_pair(s, tm[t]);
+            auto it = ring_of.find(key);
+            if (it == ring_of.end()) {
+                ring_of[key] = (int)ring_keys.size();
+                ring_keys.push_back(key);
+                ring_depth.push_back(std::max(ctx->cfg.history_depth, 1));
+                it = ring_of.find(key);
+            }
+            ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1);
+        }
+    ctx->src_ring0.assign(nd, 0);
+    ctx->src_ring1.assign(nd, 0);
+    ctx->src_plane_lo.assign(nd, 0);
+    ctx->src_plane_hi.assign(nd, 0);
+    ctx->src_col_lo.assign(nd, 0);
+    ctx->src_col_hi.assign(nd, 0);
+    std::map<int, const float2 *> tw;
+    for (size_t r = 0; r < ring_keys.size(); ++r) {
+        const int s = ring_keys[r].first;
+        const auto &m = ring_keys[r].second;
+        const DomainDesc &S = ctx->doms[s];
+        FwdRing R{};
+        R.nx = S.n[0]; R.ny = S.n[1]; R.nz = S.n[2];
+        R.ax = make_axis(m[0]); R.ay = make_axis(m[1]); R.az = make_axis(m[2]);
+        R.kx = m[0] / 2 + 1;
+        R.src = s;
+        R.depth = ring_depth[r];
+        R.slot_elems = 4LL * R.kx * m[2] * m[1];
+        R.plane0 = ctx->plane_blocks;
+        R.tile0 = ctx->col_blocks;
+        ctx->plane_blocks += 4 * R.nz;
+        ctx->col_blocks += 4 * R.kx * ((m[1] + kTileY - 1) / kTileY);
+        tw[m[0]]; tw[m[1]]; tw[m[2]];
+        ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
+        ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
+        ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(R.ny, R.ax));
+        ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
+        ctx->fwd.push_back(R);
+    }
+    for (int s = 0; s < nd; ++s) {
+        int r0 = -1, r1 = -1;
+        for (size_t r = 0; r < ctx->fwd.size(); ++r)
+            if (ctx->fwd[r].src == s) {
+                if (r0 < 0) r0 = (int)r;
+                r1 = (int)r + 1;
+            }
+        if (r0 < 0) { r0 = r1 = 0; }
+        ctx->src_ring0[s] = r0;
+        ctx->src_ring1[s] = r1;
+        if (r1 > r0) {
+            ctx->src_plane_lo[s] = ctx->fwd[r0].plane0;
+            ctx->src_col_lo[s] = ctx->fwd[r0].tile0;
+            const FwdRing &L = ctx->fwd[r1 - 1];
+            ctx->src_plane_hi[s] = L.plane0 + 4 * L.nz;
+            ctx->src_col_hi[s] = L.tile0 + 4 * L.kx * ((L.ay.M + kTileY - 1) / kTileY);
+        }
+    }
+
+    // ---- FFT targets and their (source, lag) entries
+    struct EntryPlan { int t, s, lag, ring; bool real_g; };
+    std::vector<EntryPlan> eplan;
+    for (int t = 0; t < nd; ++t) {
+        if (!tgt_fft[t]) continue;
+        const DomainDesc &T = ctx->doms[t];
+        InvTarget I{};
+        I.nx = T.n[0]; I.ny = T.n[1]; I.nz = T.n[2];
+        I.ax = make_axis(tm[t][0]); I.ay = make_axis(tm[t][1]); I.az = make_axis(tm[t][2]);
+        I.kx = tm[t][0] / 2 + 1;
+        I.dom = t;
+        I.e0 = (int)eplan.size();
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_FFT) continue;
+            const int ring = ring_of[std::make_pair(s, tm[t])];
+            for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s});
+        }
+        I.e1 = (int)eplan.size();
+        I.tile0 = ctx->mac_blocks;
+        I.plane0 = ctx->invp_blocks;
+        ctx->mac_blocks += I.kx * ((tm[t][1] + kTileY - 1) / kTileY);
+        ctx->invp_blocks += 4 * I.nz;
+        ctx->smem_mac = std::max(ctx->smem_mac, smem_mac_inv_column(I.az));
+        ctx->smem_inv = std::max(ctx->smem_inv, smem_inv_plane(I.nx, I.ny, I.ax, I.ay));
+        ctx->inv.push_back(I);
+    }
+    for (const EntryPlan &e : eplan) {
+        const auto &m = tm[e.t];
+        const long long cells = (long long)(m[0] / 2 + 1) * m[1] * m[2];
+        ctx->kernel_bytes += cells * (long long)(e.real_g ? sizeof(float) : sizeof(float2));
+    }
+
+    // ---- direct pairs, raw rings
+    ctx->raw.assign(nd, RawRing{});
+    std::vector<int> rdepth(nd, 0);
+    int max_nlag = 2;
+    for (int t = 0; t < nd; ++t) {
+        DirectTarget D{};
+        const DomainDesc &T = ctx->doms[t];
+        D.dom = t;
+        D.nx = T.n[0]; D.ny = T.n[1]; D.nz = T.n[2];
+        D.n = T.N;
+        D.ht = T.h;
+        D.p0 = (int)ctx->dpairs.size();
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_DIRECT) continue;
+            const DomainDesc &S = ctx->doms[s];
+            DirectPair P{};
+            P.src = s;
+            P.nx_s = S.n[0]; P.ny_s = S.n[1]; P.nz_s = S.n[2];
+            P.n_s = S.N;
+            P.dx = T.o[0] - S.o[0]; P.dy = T.o[1] - S.o[1]; P.dz = T.o[2] - S.o[2];
+            P.hs = (float)S.h;
+            P.vol = (float)(S.h * S.h * S.h);
+            P.is_self = t == s;
+            P.self_w = t == s ? (float)(cube_average_constant() * S.h * S.h) : 0.0f;
+            P.lag_lo = p.lag_lo;
+            P.nlag = p.lag_hi - p.lag_lo + 1;
+            max_nlag = std::max(max_nlag, P.nlag);
+            rdepth[s] = std::max(rdepth[s], p.lag_hi + 1);
+            ctx->dpairs.push_back(P);
+        }
+        D.p1 = (int)ctx->dpairs.size();
+        if (D.p1 > D.p0) {
+            D.block0 = ctx->dir_blocks;
+            D.accumulate = tgt_fft[t];
+            ctx->dir_blocks += direct_blocks(T.N);
+            ctx->dtg.push_back(D);
+        }
+    }
+    if (max_nlag > 600) return fail(ctx, RP_ERR_UNSUPPORTED, "direct pair lag window above 600 steps");
+    ctx->smem_dir = smem_direct(max_nlag);
+    ctx->raw_block0.assign(nd + 1, 0);
+    for (int d = 0; d < nd; ++d) {
+        int nb = 0;
+        if (rdepth[d] > 0) {
+            ctx->raw[d].depth = std::max(rdepth[d], ctx->cfg.history_depth);
+            ctx->raw[d].n = ctx->doms[d].N;
+            ctx->raw_depth = std::max(ctx->raw_depth, ctx->raw[d].depth);
+            nb = (int)((4 * ctx->doms[d].N + kThreads * 8 - 1) / (kThreads * 8));
+        }
+        ctx->raw_block0[d + 1] = ctx->raw_block0[d] + nb;
+    }
+    ctx->pushed.assign(nd, 0);
+
+    if (ctx->plan_only) {
+        long long raw_bytes = 0;
+        for (int d = 0; d < nd; ++d) raw_bytes += 16LL * ctx->raw[d].depth * ctx->raw[d].n;
+        ctx->device_bytes = ctx->spectral_bytes + ctx->kernel_bytes + raw_bytes;
+        ctx->finalized = true;
+        return RP_OK;
+    }
+
+    // ---- device memory
+    rp_status st = use_device(ctx);
+    if (st) return st;
+    if ((st = build_twiddles(ctx, tw))) return st;
+    for (FwdRing &R : ctx->fwd) {
+        if ((st = dev_alloc(ctx, &R.ring, (size_t)R.depth * R.slot_elems))) return st;
+        RP_CUDA(ctx, cudaMemset(R.ring, 0, (size_t)R.depth * R.slot_elems * sizeof(float2)));
+        if ((st = dev_alloc(ctx, &R.t1, 4ULL * R.kx * R.nz * R.ay.M))) return st;
+        R.tw_x = tw[R.ax.M]; R.tw_y = tw[R.ay.M]; R.tw_z = tw[R.az.M];
+    }
+    for (InvTarget &I : ctx->inv) {
+        if ((st = dev_alloc(ctx, &I.t2, 4ULL * I.kx * I.nz * I.ay.M))) return st;
+        I.tw_x = tw[I.ax.M]; I.tw_y = tw[I.ay.M]; I.tw_z = tw[I.az.M];
+        I.has_direct = 0;
+        for (const DirectTarget &D : ctx->dtg)
+            if (D.dom == I.dom) I.has_direct = 1;
+    }
+    for (int d = 0; d < nd; ++d) {
+        RawRing &rr = ctx->raw[d];
+        if (rr.depth > 0) {
+            if ((st = dev_alloc(ctx, &rr.ring, (size_t)rr.depth * 4 * rr.n))) return st;
+            RP_CUDA(ctx, cudaMemset(rr.ring, 0, (size_t)rr.depth * 4 * rr.n * sizeof(float)));
+        }
+    }
+    for (DirectPair &P : ctx->dpairs) {
+        P.raw = ctx->raw[P.src].ring;
+        P.depth = ctx->raw[P.src].depth;
+    }
+
+    // ---- kernel spectra (FP64 on the host, stored FP32), built in parallel
+    std::vector<void *> gptr(eplan.size(), nullptr);
+    for (size_t i = 0; i < eplan.size(); ++i) {
+        const auto &m = tm[eplan[i].t];
+        const size_t cells = (size_t)(m[0] / 2 + 1) * m[1] * m[2];
+        if (eplan[i].real_g) {
+            float *p = nullptr;
+            if ((st = dev_alloc(ctx, &p, cells))) return st;
+            gptr[i] = p;
+        } else {
+            float2 *p = nullptr;
+            if ((st = dev_alloc(ctx, &p, cells))) return st;
+            gptr[i] = p;
+        }
+    }
+    {
+        std::atomic<size_t> next(0);
+        std::atomic<int> err(0);
+        const int dev = ctx->device;
+        auto worker = [&]() {
+            cudaSetDevice(dev);
+            std::vector<float> hr;
+            std::vector<float2> hc;
+            for (;;) {
+                const size_t i = next.fetch_add(1);
+                if (i >= eplan.size() || err.load()) break;
+                const EntryPlan &e = eplan[i];
+                const DomainDesc &T = ctx->doms[e.t], &S = ctx->doms[e.s];
+                const int *m = tm[e.t].data();
+                const size_t cells = (size_t)(m[0] / 2 + 1) * m[1] * m[2];
+                if (e.real_g) hr.resize(cells); else hc.resize(cells);
+                build_kernel_spectrum(T.o, T.n, S.o, S.n, S.h, e.t == e.s, e.lag, ctx->cfg.c, ctx->cfg.dt, m,
+                                      e.real_g, hr.data(), hc.data());
+                cudaError_t ce = e.real_g ? cudaMemcpy(gptr[i], hr.data(), cells * sizeof(float), cudaMemcpyHostToDevice)
+                                          : cudaMemcpy(gptr[i], hc.data(), cells * sizeof(float2), cudaMemcpyHostToDevice);
+                if (ce != cudaSuccess) err.store((int)ce);
+            }
+        };
+        unsigned nthr = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+        nthr = (unsigned)std::min<size_t>(nthr, std::max<size_t>(1, eplan.size()));
+        std::vector<std::thread> pool;
+        for (unsigned i = 0; i < nthr; ++i) pool.emplace_back(worker);
+        for (auto &th : pool) th.join();
+        if (err.load()) return cuda_fail(ctx, (cudaError_t)err.load(), "kernel spectrum upload");
+    }
+    for (size_t i = 0; i < eplan.size(); ++i) {
+        const EntryPlan &e = eplan[i];
+        const FwdRing &R = ctx->fwd[e.ring];
+        MacEntry E{};
+        E.g = gptr[i];
+        E.ring = R.ring;
+        E.slot_elems = R.slot_elems;
+        E.depth = R.depth;
+        E.lag = e.lag;
+        E.is_real = e.real_g ? 1 : 0;
+        ctx->entries.push_back(E);
+    }
+
+    // ---- device tables and kernel limits
+    if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
+    if ((st = upload(ctx, &ctx->d_inv, ctx->inv))) return st;
+    if ((st = upload(ctx, &ctx->d_entries, ctx->entries))) return st;
+    if ((st = upload(ctx, &ctx->d_dtg, ctx->dtg))) return st;
+    if ((st = upload(ctx, &ctx->d_dpairs, ctx->dpairs))) return st;
+    if ((st = upload(ctx, &ctx->d_raw, ctx->raw))) return st;
+    RP_CUDA(ctx, set_kernel_smem_limits(std::max<size_t>(ctx->smem_plane, 1024), std::max<size_t>(ctx->smem_col, 1024),
+                                        std::max<size_t>(ctx->smem_mac, 1024), std::max<size_t>(ctx->smem_inv, 1024)));
+    RP_CUDA(ctx, set_direct_smem_limit(ctx->smem_dir));
+    RP_CUDA(ctx, cudaDeviceSynchronize());
+    ctx->finalized = true;
+    return RP_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+rp_status check_ready(rp_ctx *ctx)
+{
+    if (!ctx) return RP_ERR_ARG;
+    if (!ctx->finalized || ctx->plan_only) return fail(ctx, RP_ERR_STATE, "context not finalized for execution");
+    return use_device(ctx);
+}
+
+// Marks domain id pushed in the current round, starting a new round if the
+// previous one is complete.
+rp_status begin_push(rp_ctx *ctx, int id)
+{
+    const int nd = (int)ctx->doms.size();
+    if (ctx->step < 0 || ctx->npushed == nd) {
+        ctx->step += 1;
+        std::fill(ctx->pushed.begin(), ctx->pushed.end(), 0);
+        ctx->npushed = 0;
+    }
+    if (ctx->pushed[id]) return fail(ctx, RP_ERR_STATE, "domain " + std::to_string(id) + " pushed twice in one step");
+    ctx->pushed[id] = 1;
+    ctx->npushed += 1;
+    return RP_OK;
+}
+
+rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
+{
+    rp_status st;
+    const long long step = ctx->step;
+    // raw ring
+    int blk = ctx->raw_block0[d1] - ctx->raw_block0[d0];
+    if (blk > 0) {
+        std::vector<int> b0(kMaxDomains + 1, 0);
+        for (int d = d0; d <= d1; ++d) b0[d] = ctx->raw_block0[d] - ctx->raw_block0[d0];
+        if ((st = timed_launch(ctx, RP_K_RING_PUSH, "ring push", [&] {
+                 return launch_ring_push(ctx->d_raw, in, d0, d1, b0.data(), blk, step, ctx->stream);
+             })))
+            return st;
+    }
+    // spectral rings of these sources (rings are ordered by source, so the
+    // rings of d0..d1-1 form one contiguous range)
+    int rr0 = -1, rr1 = -1, plo = 0, phi = 0, clo = 0, chi = 0;
+    for (int d = d0; d < d1; ++d) {
+        if (ctx->src_ring1[d] <= ctx->src_ring0[d]) continue;
+        if (rr0 < 0) { rr0 = ctx->src_ring0[d]; plo = ctx->src_plane_lo[d]; clo = ctx->src_col_lo[d]; }
+        rr1 = ctx->src_ring1[d];
+        phi = ctx->src_plane_hi[d];
+        chi = ctx->src_col_hi[d];
+    }
+    if (rr0 >= 0) {
+        if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "forward plane pass", [&] {
+                 return launch_fwd_plane(ctx->d_fwd, in, rr0, rr1, plo, phi - plo, ctx->smem_plane, ctx->stream);
+             })))
+            return st;
+        if ((st = timed_launch(ctx, RP_K_FWD_COLUMN, "forward column pass", [&] {
+                 return launch_fwd_column(ctx->d_fwd, rr0, rr1, clo, chi - clo, ctx->smem_col, step, ctx->stream);
+             })))
+            return st;
+    }
+    return RP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (id < 0 || id >= (int)ctx->doms.size() || !d_rho || !d_J) return fail(ctx, RP_ERR_ARG, "rp_push: bad id or pointer");
+    if ((st = begin_push(ctx, id))) return st;
+    IoPtrs in{};
+    in.rho[id] = d_rho;
+    in.J[id] = d_J;
+    return enqueue_push(ctx, id, id + 1, in);
+}
+
+rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!d_rho || !d_J) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!d_rho[d] || !d_J[d]) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL buffer");
+    if (ctx->step >= 0 && ctx->npushed != 0 && ctx->npushed != nd)
+        return fail(ctx, RP_ERR_STATE, "rp_push_all inside a partially pushed step");
+    ctx->step += 1;
+    std::fill(ctx->pushed.begin(), ctx->pushed.end(), 1);
+    ctx->npushed = nd;
+    IoPtrs in{};
+    for (int d = 0; d < nd; ++d) { in.rho[d] = d_rho[d]; in.J[d] = d_J[d]; }
+    return enqueue_push(ctx, 0, nd, in);
+}
+
+rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (id < 0 || id >= (int)ctx->doms.size() || !h_rho || !h_J) return fail(ctx, RP_ERR_ARG, "rp_push_host: bad id or pointer");
+    if (ctx->in_stage.empty()) ctx->in_stage.assign(ctx->doms.size(), nullptr);
+    const long long N = ctx->doms[id].N;
+    if (!ctx->in_stage[id] && (st = dev_alloc(ctx, &ctx->in_stage[id], 4 * (size_t)N))) return st;
+    RP_CUDA(ctx, cudaMemcpyAsync(ctx->in_stage[id], h_rho, N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    RP_CUDA(ctx, cudaMemcpyAsync(ctx->in_stage[id] + N, h_J, 3 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
+    return rp_push(ctx, id, ctx->in_stage[id], ctx->in_stage[id] + N);
+}
+
+rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!d_phi || !d_A) return fail(ctx, RP_ERR_ARG, "rp_evaluate: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_evaluate: NULL output buffer");
+    if (ctx->step < 0 || ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_evaluate before every domain pushed the step");
+    if (!ctx->clamp && ctx->step - ctx->max_lag < 0)
+        return fail(ctx, RP_ERR_HISTORY, "step " + std::to_string(ctx->step) + " needs samples " +
+                                             std::to_string(ctx->max_lag) + " steps back");
+    OutPtrs out{};
+    for (int d = 0; d < nd; ++d) { out.phi[d] = d_phi[d]; out.A[d] = d_A[d]; }
+    const long long step = ctx->step;
+    const int clamp = ctx->clamp ? 1 : 0;
+    const float inv_c = (float)(1.0 / ctx->cfg.c);
+    if (!ctx->inv.empty()) {
+        if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
+                 return launch_mac_inv_column(ctx->d_inv, (int)ctx->inv.size(), ctx->d_entries, ctx->mac_blocks,
+                                              ctx->smem_mac, step, clamp, ctx->stream);
+             })))
+            return st;
+        if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
+                 return launch_inv_plane(ctx->d_inv, (int)ctx->inv.size(), out, ctx->invp_blocks, ctx->smem_inv,
+                                         inv_c, ctx->stream);
+             })))
+            return st;
+    }
+    if (!ctx->dtg.empty()) {
+        const float inv_cdt = (float)(1.0 / (ctx->cfg.c * ctx->cfg.dt));
+        if ((st = timed_launch(ctx, RP_K_DIRECT, "direct sum", [&] {
+                 return launch_direct(ctx->d_dtg, (int)ctx->dtg.size(), ctx->d_dpairs, out, ctx->dir_blocks,
+                                      ctx->smem_dir, step, clamp, inv_cdt, inv_c, ctx->stream);
+             })))
+            return st;
+    }
+    return RP_OK;
+}
+
+rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!h_phi || !h_A) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!h_phi[d] || !h_A[d]) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host: NULL output buffer");
+    if (ctx->out_stage.empty()) ctx->out_stage.assign(nd, nullptr);
+    std::vector<float *> phi(nd), A(nd);
+    for (int d = 0; d < nd; ++d) {
+        if (!ctx->out_stage[d] && (st = dev_alloc(ctx, &ctx->out_stage[d], 4 * (size_t)ctx->doms[d].N))) return st;
+        phi[d] = ctx->out_stage[d];
+        A[d] = ctx->out_stage[d] + ctx->doms[d].N;
+    }
+    if ((st = rp_evaluate(ctx, phi.data(), A.data()))) return st;
+    for (int d = 0; d < nd; ++d) {
+        const long long N = ctx->doms[d].N;
+        RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        RP_CUDA(ctx, cudaMemcpyAsync(h_A[d], A[d], 3 * N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return RP_OK;
+}
+
+rp_status rp_sync(rp_ctx *ctx)
+{
+    if (!ctx) return RP_ERR_ARG;
+    if (ctx->plan_only) return RP_OK;
+    rp_status st = use_device(ctx);
+    if (st) return st;
+    RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    RP_CUDA(ctx, cudaGetLastError());
+    return RP_OK;
+}
+
+rp_status rp_query(rp_ctx *ctx, rp_stats *out)
+{
+    if (!ctx || !out) return RP_ERR_ARG;
+    if (!ctx->finalized) return fail(ctx, RP_ERR_STATE, "rp_query before rp_finalize");
+    std::memset(out, 0, sizeof(*out));
+    const int nd = (int)ctx->doms.size();
+    out->ndomains = nd;
+    for (const PairPlan &p : ctx->pairs) {
+        if (p.kind == RP_PAIR_FFT) out->npairs_fft++;
+        else out->npairs_direct++;
+    }
+    out->max_lag = ctx->max_lag;
+    out->raw_depth = ctx->raw_depth;
+    out->spectral_depth = ctx->spec_depth;
+    out->step = ctx->step;
+    out->device_bytes = ctx->device_bytes;
+    out->spectral_bytes = ctx->spectral_bytes;
+    out->kernel_bytes = ctx->kernel_bytes;
+    for (const DomainDesc &d : ctx->doms) out->points += d.N;
+    return RP_OK;
+}
+
+rp_status rp_pair_info(rp_ctx *ctx, int target, int source, rp_pair_info_t *out)
+{
+    if (!ctx || !out) return RP_ERR_ARG;
+    if (!ctx->finalized) return fail(ctx, RP_ERR_STATE, "rp_pair_info before rp_finalize");
+    const int nd = (int)ctx->doms.size();
+    if (target < 0 || target >= nd || source < 0 || source >= nd) return fail(ctx, RP_ERR_ARG, "rp_pair_info: bad domain");
+    const PairPlan &p = ctx->pairs[(size_t)target * nd + source];
+    std::memset(out, 0, sizeof(*out));
+    out->kind = p.kind;
+    out->lag_lo = p.lag_lo;
+    out->lag_hi = p.lag_hi;
+    for (int a = 0; a < 3; ++a) out->fft_m[a] = p.kind == RP_PAIR_FFT ? p.m[a] : 0;
+    out->r_min = p.rmin;
+    out->r_max = p.rmax;
+    return RP_OK;
+}
+
+rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *total_ms, int reset)
+{
+    if (!ctx || kind < 0 || kind >= RP_K_COUNT) return RP_ERR_ARG;
+    if (!ctx->profile) return fail(ctx, RP_ERR_STATE, "context created without RP_FLAG_PROFILE");
+    rp_status st = use_device(ctx);
+    if (st) return st;
+    if ((st = drain_profile(ctx))) return st;
+    if (launches) *launches = ctx->launches[kind];
+    if (total_ms) *total_ms = ctx->ms[kind];
+    if (reset) {
+        for (int k = 0; k < RP_K_COUNT; ++k) { ctx->launches[k] = 0; ctx->ms[k] = 0.0; }
+    }
+    return RP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- checkpoint
+
+namespace {
+
+const char kMagic[8] = {'R', 'P', 'S', 'T', 'A', 'T', 'E', '1'};
+
+// A hash of everything that must match between save and load.
+unsigned long long layout_hash(const rp_ctx *ctx)
+{
+    unsigned long long h = 1469598103934665603ULL;
+    auto mix = [&](const void *p, size_t n) {
+        const unsigned char *b = static_cast<const unsigned char *>(p);
+        for (size_t i = 0; i < n; ++i) { h ^= b[i]; h *= 1099511628211ULL; }
+    };
+    for (const DomainDesc &d : ctx->doms) { mix(d.o, sizeof d.o); mix(d.n, sizeof d.n); mix(&d.h, sizeof d.h); }
+    mix(&ctx->cfg.c, sizeof(double));
+    mix(&ctx->cfg.dt, sizeof(double));
+    mix(&ctx->cfg.mode, sizeof(int));
+    for (const FwdRing &R : ctx->fwd) { mix(&R.depth, sizeof(int)); mix(&R.slot_elems, sizeof(long long)); }
+    for (const RawRing &r : ctx->raw) { mix(&r.depth, sizeof(int)); mix(&r.n, sizeof(long long)); }
+    return h;
+}
+
+template <class Fn>
+rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
+{
+    rp_status st;
+    for (const RawRing &r : ctx->raw)
+        if (r.ring && (st = fn((void *)r.ring, (size_t)r.depth * 4 * r.n * sizeof(float)))) return st;
+    for (const FwdRing &R : ctx->fwd)
+        if ((st = fn((void *)R.ring, (size_t)R.depth * R.slot_elems * sizeof(float2)))) return st;
+    return RP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rp_status rp_save_state(rp_ctx *ctx, const char *path)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (!path) return fail(ctx, RP_ERR_ARG, "NULL path");
+    RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(ctx, RP_ERR_ARG, std::string("cannot open ") + path);
+    const unsigned long long h = layout_hash(ctx);
+    const int nd = (int)ctx->doms.size();
+    bool ok = std::fwrite(kMagic, 1, 8, f) == 8 && std::fwrite(&h, sizeof h, 1, f) == 1 &&
+              std::fwrite(&ctx->step, sizeof ctx->step, 1, f) == 1 &&
+              std::fwrite(&ctx->npushed, sizeof ctx->npushed, 1, f) == 1 &&
+              std::fwrite(ctx->pushed.data(), 1, nd, f) == (size_t)nd;
+    std::vector<char> buf;
+    if (ok)
+        st = for_each_ring(ctx, [&](void *dptr, size_t bytes) -> rp_status {
+            buf.resize(bytes);
+            RP_CUDA(ctx, cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost));
+            if (std::fwrite(buf.data(), 1, bytes, f) != bytes) return fail(ctx, RP_ERR_ARG, "write failed");
+            return RP_OK;
+        });
+    std::fclose(f);
+    if (!ok) return fail(ctx, RP_ERR_ARG, "write failed");
+    return st;
+}
+
+rp_status rp_load_state(rp_ctx *ctx, const char *path)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (!path) return fail(ctx, RP_ERR_ARG, "NULL path");
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(ctx, RP_ERR_ARG, std::string("cannot open ") + path);
+    char magic[8];
+    unsigned long long h = 0;
+    long long step = 0;
+    int npushed = 0;
+    const int nd = (int)ctx->doms.size();
+    std::vector<char> pushed(nd);
+    bool ok = std::fread(magic, 1, 8, f) == 8 && std::memcmp(magic, kMagic, 8) == 0 &&
+              std::fread(&h, sizeof h, 1, f) == 1 && std::fread(&step, sizeof step, 1, f) == 1 &&
+              std::fread(&npushed, sizeof npushed, 1, f) == 1 &&
+              std::fread(pushed.data(), 1, nd, f) == (size_t)nd;
+    if (!ok || h != layout_hash(ctx)) {
+        std::fclose(f);
+        return fail(ctx, RP_ERR_STATE, "state file does not match this context");
+    }
+    RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    std::vector<char> buf;
+    st = for_each_ring(ctx, [&](void *dptr, size_t bytes) -> rp_status {
+        buf.resize(bytes);
+        if (std::fread(buf.data(), 1, bytes, f) != bytes) return fail(ctx, RP_ERR_STATE, "state file truncated");
+        RP_CUDA(ctx, cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice));
+        return RP_OK;
+    });
+    std::fclose(f);
+    if (st) return st;
+    ctx->step = step;
+    ctx->npushed = npushed;
+    ctx->pushed = pushed;
+    return RP_OK;
+}
+
+void rp_destroy(rp_ctx *ctx)
+{
+    if (!ctx) return;
+    if (!ctx->plan_only && ctx->device >= 0) {
+        int cur = -1;
+        cudaGetDevice(&cur);
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        for (const ProfRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+        for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
+        for (void *p : ctx->allocs) cudaFree(p);
+        cudaGetLastError();
+        if (cur >= 0) cudaSetDevice(cur);
+    }
+    delete ctx;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Device building blocks of the FFT path: complex helpers and the line FFT.
+//
+// A line of length M = R * L is transformed by L lanes of one warp (several
+// lines share a warp when L < 32).  Lane g holds x[n*L + g] for n < R in
+// registers.  With n = n1*L + n2 and k = k1 + R*k2,
+//
+//   X[k1 + R k2] = sum_{n2} W_L^{n2 k2} [ W_M^{n2 k1} sum_{n1} x[n1 L + n2] W_R^{n1 k1} ],
+//
+// so each lane first does an R-point DFT over its registers, multiplies by
+// W_M^{g k1}, and the lanes then do an L-point decimation-in-frequency FFT
+// across the lane group with __shfl_xor_sync butterflies.  Lane g ends up
+// holding X[k1 + R * bitrev_L(g)] in register k1.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "rp_internal.h"
+
+namespace rp {
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+{
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+
+// W_M^j (forward) or its conjugate (inverse) from a table of exp(-2 pi i j/M).
+template <bool INV>
+__device__ __forceinline__ float2 twid(const float2 *tw, int j)
+{
+    float2 w = tw[j];
+    if (INV) w.y = -w.y;
+    return w;
+}
+
+__device__ __forceinline__ int bitrev_lanes(int g, int logL)
+{
+    return logL == 0 ? 0 : (int)(__brev((unsigned)g) >> (32 - logL));
+}
+
+// In-register R-point DFT (twiddles W_R^j = W_M^{j L} from the M table).
+template <int R, bool INV>
+__device__ __forceinline__ void small_dft(float2 (&v)[R], const float2 *tw, int L)
+{
+    if constexpr (R == 2) {
+        float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 4) {
+        // radix 4: W_4 = -i (forward) / +i (inverse)
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+        float2 jb1 = INV ? make_float2(-b1.y, b1.x) : make_float2(b1.y, -b1.x);  // W_4 * b1
+        v[0] = cadd(a0, b0);
+        v[2] = csub(a0, b0);
+        v[1] = cadd(a1, jb1);
+        v[3] = csub(a1, jb1);
+    } else if constexpr (R > 2) {
+        float2 o[R];
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 acc = v[0];
+#pragma unroll
+            for (int n = 1; n < R; ++n) acc = cadd(acc, cmul(v[n], twid<INV>(tw, ((n * k) % R) * L)));
+            o[k] = acc;
+        }
+#pragma unroll
+        for (int k = 0; k < R; ++k) v[k] = o[k];
+    }
+}
+
+// The line FFT described above.  All 32 lanes of the warp must call it
+// together (the shuffles use the full mask); g is the lane index within its
+// group of L lanes.
+template <int R, bool INV>
+__device__ __forceinline__ void line_fft(float2 (&v)[R], int g, const Axis &a, const float2 *tw)
+{
+    small_dft<R, INV>(v, tw, a.L);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], twid<INV>(tw, g * k));
+    for (int h = a.L >> 1; h >= 1; h >>= 1) {
+        const bool upper = (g & h) != 0;
+        const float2 w = twid<INV>(tw, (g & (h - 1)) * (a.M / (2 * h)));
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 p;
+            p.x = __shfl_xor_sync(0xffffffffu, v[k].x, h);
+            p.y = __shfl_xor_sync(0xffffffffu, v[k].y, h);
+            v[k] = upper ? cmul(csub(p, v[k]), w) : cadd(v[k], p);
+        }
+    }
+}
+
+// Runtime dispatch on R for a functor templated on R:  f.template run<R>().
+template <class F>
+__device__ __forceinline__ void dispatch_radix(int R, F &f)
+{
+    switch (R) {
+    case 1: f.template run<1>(); break;
+    case 2: f.template run<2>(); break;
+    case 3: f.template run<3>(); break;
+    case 4: f.template run<4>(); break;
+    case 6: f.template run<6>(); break;
+    default: break;
+    }
+}
+
+// Copy a twiddle table into shared memory.
+__device__ __forceinline__ void load_twiddles(float2 *dst, const float2 *src, int M)
+{
+    for (int i = threadIdx.x; i < M; i += blockDim.x) dst[i] = src[i];
+}
+
+}  // namespace rp

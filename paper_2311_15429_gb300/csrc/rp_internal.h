@@ -1,0 +1,151 @@
+// Internal structures shared by the host planner (rp_api.cu) and the kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace rp {
+
+constexpr int kMaxDomains = 256;
+constexpr int kMaxFFT = 192;   // largest padded FFT length per axis
+constexpr int kThreads = 256;  // threads per block of every FFT-path kernel
+constexpr int kTileY = 16;     // ky columns per block of the column passes
+constexpr int kTileYPad = 17;  // shared-memory row stride of a column tile (bank spread)
+
+// Radix split of one FFT axis: M = R * L with L a power of two (lanes) and
+// R in {1, 2, 3, 4, 6} (registers per lane).
+struct Axis {
+    int M, R, L, logL;
+};
+
+// One (source domain, padded size) spectral history ring and its forward
+// transform.  Spectra are stored [4 fields][kx][kz][ky] (ky fastest), kx in
+// [0, mx/2], as complex64.
+struct FwdRing {
+    int nx, ny, nz;          // source grid
+    Axis ax, ay, az;         // padded sizes
+    int kx;                  // mx/2 + 1
+    int src;                 // source domain id
+    int depth;               // ring depth in steps
+    float2 *ring;            // [depth][4][kx][mz][my]
+    float2 *t1;              // scratch after the plane pass: [4][kx][nz][my]
+    long long slot_elems;    // float2 per slot = 4*kx*mz*my
+    const float2 *tw_x, *tw_y, *tw_z;  // twiddles exp(-2 pi i j/M), j < M
+    int plane0;              // first block of this ring in the plane-pass grid
+    int tile0;               // first block of this ring in the column-pass grid
+};
+
+// One (source, lag) term of a target's spectral sum: G_m (kernel spectrum of
+// Eq. 11 for lag m, scaled by 1/(mx my mz)) times the source spectrum of
+// step l - m.
+struct MacEntry {
+    const void *g;           // [kx][mz][my] float (is_real) or float2
+    const float2 *ring;      // the source's spectral ring at this target's size
+    long long slot_elems;
+    int depth;
+    int lag;
+    int is_real;
+    int pad_;
+};
+
+// A target domain evaluated by the FFT path.
+struct InvTarget {
+    int nx, ny, nz;
+    Axis ax, ay, az;
+    int kx;
+    int dom;                 // domain id
+    int e0, e1;              // its MacEntry range
+    float2 *t2;              // scratch after the column pass: [4][kx][nz][my]
+    const float2 *tw_x, *tw_y, *tw_z;
+    int tile0;               // first block in the MAC/column grid
+    int plane0;              // first block in the plane grid
+    int has_direct;          // direct pairs add onto this target afterwards
+    int pad_;
+};
+
+// A (target, source) pair evaluated by the direct retarded sum.
+struct DirectPair {
+    int src;
+    int nx_s, ny_s, nz_s;
+    long long n_s;
+    double dx, dy, dz;       // o_t - o_s
+    float hs;
+    float vol;               // hs^3
+    float self_w;            // C hs^2 (self pair only)
+    int is_self;
+    int lag_lo, nlag;        // samples of lags lag_lo .. lag_lo + nlag - 1
+    const float *raw;        // source raw ring [depth][4][n_s]
+    int depth;
+    int pad_;
+};
+
+// A target of the direct kernel: its pair list and grid.
+struct DirectTarget {
+    int dom;
+    int nx, ny, nz;
+    long long n;
+    double ht;
+    int p0, p1;              // DirectPair range
+    int block0;              // first block in the direct grid
+    int accumulate;          // add onto the output (FFT pairs wrote it) instead of writing
+};
+
+// A raw history ring (rho, Jx, Jy, Jz per slot).
+struct RawRing {
+    float *ring;             // [depth][4][n]
+    long long n;
+    int depth;
+    int pad_;
+};
+
+struct IoPtrs {
+    const float *rho[kMaxDomains];
+    const float *J[kMaxDomains];
+};
+
+struct OutPtrs {
+    float *phi[kMaxDomains];
+    float *A[kMaxDomains];
+};
+
+// ---- launchers (rp_fft_kernels.cu, rp_direct.cu) ----
+
+cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, int d1,
+                             const int *h_block0, int nblocks, long long step,
+                             cudaStream_t s);
+cudaError_t launch_fwd_plane(const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
+                             int block_lo, int nblocks, size_t smem, cudaStream_t s);
+cudaError_t launch_fwd_column(const FwdRing *d_rings, int r0, int r1, int block_lo,
+                              int nblocks, size_t smem, long long step, cudaStream_t s);
+cudaError_t launch_mac_inv_column(const InvTarget *d_tgts, int ntgt, const MacEntry *d_entries,
+                                  int nblocks, size_t smem, long long step, int clamp,
+                                  cudaStream_t s);
+cudaError_t launch_inv_plane(const InvTarget *d_tgts, int ntgt, const OutPtrs &out,
+                             int nblocks, size_t smem, float inv_c, cudaStream_t s);
+cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair *d_pairs,
+                          const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
+                          float inv_cdt, float inv_c, cudaStream_t s);
+
+// shared-memory sizes the kernels need for the given shapes
+size_t smem_fwd_plane(int ny, const Axis &ax);
+size_t smem_fwd_column(const Axis &az);
+size_t smem_mac_inv_column(const Axis &az);
+size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay);
+cudaError_t set_kernel_smem_limits(size_t plane, size_t column, size_t mac, size_t inv);
+
+// ---- host FP64 kernel spectra (rp_spectra.cpp) ----
+
+// The kernel of Eq. 11 for one lag m of the pair (target t, source s),
+// placed for a linear (non-cyclic) convolution on an mx x my x mz grid and
+// transformed with an FP64 FFT; returns the half spectrum [kx][kz][ky],
+// kx <= mx/2, scaled by 1/(mx my mz).  If real_out, only real parts are
+// written to out_real (the self pair's kernel is even, so its spectrum is real).
+void build_kernel_spectrum(const double o_t[3], const int n_t[3], const double o_s[3],
+                           const int n_s[3], double h, bool self_pair, int lag, double c,
+                           double dt, const int m[3], bool real_out, float *out_real,
+                           float2 *out_cplx);
+
+// Cell-averaged 1/R over a cube of side 1 (the self weight is this times h^2).
+double cube_average_constant();
+
+}  // namespace rp

@@ -1,0 +1,299 @@
+"""Thin ctypes binding of the C-ABI in include/rp.h.
+
+Argument marshalling only: every function here has the name of the C entry
+point it calls, converts torch tensors / numpy arrays to raw pointers, and
+raises ``RPError`` on a non-OK status.  All computation happens in librp.so.
+``load()`` fails loudly if the library is missing or does not load; there is
+no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+from . import build as _build
+
+RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_HISTORY, RP_ERR_CUDA, RP_ERR_OOM, \
+    RP_ERR_UNSUPPORTED, RP_ERR_TIMEOUT = range(8)
+RP_MODE_FFT, RP_MODE_DIRECT = 0, 1
+RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE = 0x1, 0x2, 0x4
+RP_PAIR_FFT, RP_PAIR_DIRECT = 0, 1
+(RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
+ RP_K_DIRECT, RP_K_COUNT) = range(7)
+MAX_DOMAINS = 256
+
+
+class rp_config(ctypes.Structure):
+    _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("history_depth", ctypes.c_int),
+                ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("reserved", ctypes.c_int * 9)]
+
+
+class rp_pair_info_t(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("lag_lo", ctypes.c_int), ("lag_hi", ctypes.c_int),
+                ("fft_m", ctypes.c_int * 3), ("r_min", ctypes.c_double), ("r_max", ctypes.c_double)]
+
+
+class rp_stats(ctypes.Structure):
+    _fields_ = [("ndomains", ctypes.c_int), ("npairs_fft", ctypes.c_int),
+                ("npairs_direct", ctypes.c_int), ("max_lag", ctypes.c_int),
+                ("raw_depth", ctypes.c_int), ("spectral_depth", ctypes.c_int),
+                ("step", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
+                ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
+                ("points", ctypes.c_longlong)]
+
+
+class RPError(RuntimeError):
+    def __init__(self, status: int, message: str = ""):
+        self.status = status
+        super().__init__(f"{rp_status_str(status)}: {message}" if message else rp_status_str(status))
+
+
+_lib = None
+_V = ctypes.c_void_p
+_I = ctypes.c_int
+_PP = ctypes.POINTER(ctypes.c_void_p)
+
+# name -> (restype, argtypes); every entry point declared in include/rp.h
+SIGNATURES = {
+    "rp_create": (_I, [ctypes.POINTER(rp_config), _I, _V, ctypes.POINTER(_V)]),
+    "rp_add_domain": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I),
+                           ctypes.c_double, ctypes.POINTER(_I)]),
+    "rp_finalize": (_I, [_V]),
+    "rp_push": (_I, [_V, _I, _V, _V]),
+    "rp_push_all": (_I, [_V, _PP, _PP]),
+    "rp_push_host": (_I, [_V, _I, _V, _V]),
+    "rp_evaluate": (_I, [_V, _PP, _PP]),
+    "rp_evaluate_host": (_I, [_V, _PP, _PP]),
+    "rp_sync": (_I, [_V]),
+    "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
+    "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
+    "rp_kernel_stats": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong),
+                             ctypes.POINTER(ctypes.c_double), _I]),
+    "rp_kernel_name": (ctypes.c_char_p, [_I]),
+    "rp_save_state": (_I, [_V, ctypes.c_char_p]),
+    "rp_load_state": (_I, [_V, ctypes.c_char_p]),
+    "rp_destroy": (None, [_V]),
+    "rp_status_str": (ctypes.c_char_p, [_I]),
+    "rp_last_error": (ctypes.c_char_p, [_V]),
+}
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load(build: bool = True):
+    """Load librp.so (building it first if ``build`` and it is stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if build:
+        _build.build()
+    if not os.path.exists(_build.LIB):
+        raise RuntimeError(f"librp.so not found at {_build.LIB}; run paper_2311_15429_gb300/build.py")
+    lib = ctypes.CDLL(_build.LIB)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def _ptr(x) -> int:
+    """Raw address of a torch tensor, numpy array or int."""
+    if x is None:
+        return 0
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if str(x.dtype) != "torch.float32" or not x.is_contiguous():
+            raise ValueError("tensor must be contiguous float32")
+        return x.data_ptr()
+    if hasattr(x, "ctypes"):
+        import numpy as np
+        if x.dtype != np.float32 or not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous float32")
+        return x.ctypes.data
+    raise TypeError(f"cannot take the address of {type(x)}")
+
+
+def _ptr_array(xs: Sequence):
+    arr = (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
+    return ctypes.cast(arr, _PP), arr
+
+
+def _check(st: int, ctx=None):
+    if st != RP_OK:
+        msg = load().rp_last_error(ctx).decode() if ctx else ""
+        raise RPError(st, msg)
+
+
+def rp_status_str(status: int) -> str:
+    return load().rp_status_str(status).decode()
+
+
+def rp_kernel_name(kind: int) -> Optional[str]:
+    s = load().rp_kernel_name(kind)
+    return s.decode() if s is not None else None
+
+
+def rp_last_error(ctx) -> str:
+    return load().rp_last_error(ctx).decode()
+
+
+def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
+              flags: int = 0, device: int = 0, stream=None):
+    """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
+    cudaStream_t int, or None for torch's current stream (NULL without torch)."""
+    cfg = rp_config(c, dt, history_depth, mode, flags)
+    if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
+        try:
+            import torch
+            if torch.cuda.is_available():
+                stream = torch.cuda.current_stream(device).cuda_stream
+        except ImportError:
+            stream = None
+    if stream is not None and hasattr(stream, "cuda_stream"):
+        stream = stream.cuda_stream
+    out = ctypes.c_void_p()
+    _check(load().rp_create(ctypes.byref(cfg), device, stream or 0, ctypes.byref(out)))
+    return out
+
+
+def rp_add_domain(ctx, origin, n, h: float) -> int:
+    o = (ctypes.c_double * 3)(*[float(v) for v in origin])
+    nn = (ctypes.c_int * 3)(*[int(v) for v in n])
+    i = ctypes.c_int()
+    _check(load().rp_add_domain(ctx, o, nn, float(h), ctypes.byref(i)), ctx)
+    return i.value
+
+
+def rp_finalize(ctx):
+    _check(load().rp_finalize(ctx), ctx)
+
+
+def rp_push(ctx, dom: int, rho, J):
+    _check(load().rp_push(ctx, dom, _ptr(rho), _ptr(J)), ctx)
+
+
+def rp_push_all(ctx, rhos: Sequence, Js: Sequence):
+    pr, _a = _ptr_array(rhos)
+    pj, _b = _ptr_array(Js)
+    _check(load().rp_push_all(ctx, pr, pj), ctx)
+
+
+def rp_push_host(ctx, dom: int, rho, J):
+    _check(load().rp_push_host(ctx, dom, _ptr(rho), _ptr(J)), ctx)
+
+
+def rp_evaluate(ctx, phis: Sequence, As: Sequence):
+    pp, _a = _ptr_array(phis)
+    pa, _b = _ptr_array(As)
+    _check(load().rp_evaluate(ctx, pp, pa), ctx)
+
+
+def rp_evaluate_host(ctx, phis: Sequence, As: Sequence):
+    pp, _a = _ptr_array(phis)
+    pa, _b = _ptr_array(As)
+    _check(load().rp_evaluate_host(ctx, pp, pa), ctx)
+
+
+def rp_sync(ctx):
+    _check(load().rp_sync(ctx), ctx)
+
+
+def rp_query(ctx) -> dict:
+    s = rp_stats()
+    _check(load().rp_query(ctx, ctypes.byref(s)), ctx)
+    return {name: getattr(s, name) for name, _ in rp_stats._fields_}
+
+
+def rp_pair_info(ctx, target: int, source: int) -> dict:
+    p = rp_pair_info_t()
+    _check(load().rp_pair_info(ctx, target, source, ctypes.byref(p)), ctx)
+    return {"kind": p.kind, "lag_lo": p.lag_lo, "lag_hi": p.lag_hi, "fft_m": tuple(p.fft_m),
+            "r_min": p.r_min, "r_max": p.r_max}
+
+
+def rp_kernel_stats(ctx, kind: int, reset: bool = False):
+    n = ctypes.c_longlong()
+    ms = ctypes.c_double()
+    _check(load().rp_kernel_stats(ctx, kind, ctypes.byref(n), ctypes.byref(ms), int(reset)), ctx)
+    return n.value, ms.value
+
+
+def rp_save_state(ctx, path: str):
+    _check(load().rp_save_state(ctx, path.encode()), ctx)
+
+
+def rp_load_state(ctx, path: str):
+    _check(load().rp_load_state(ctx, path.encode()), ctx)
+
+
+def rp_destroy(ctx):
+    if ctx:
+        load().rp_destroy(ctx)
+
+
+class RetardedPotentials:
+    """Owns one context: domains from ``synth.Domain``-like objects (origin,
+    n, h), device output buffers as torch tensors, and the push / evaluate
+    calls of a time step."""
+
+    def __init__(self, domains, c: float, dt: float, history_depth: int = 0,
+                 mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None):
+        import torch
+        self.domains = list(domains)
+        self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream)
+        try:
+            for d in self.domains:
+                rp_add_domain(self.ctx, d.origin, d.n, d.h)
+            rp_finalize(self.ctx)
+        except Exception:
+            rp_destroy(self.ctx)
+            self.ctx = None
+            raise
+        if flags & RP_FLAG_PLAN_ONLY:
+            self.phi = self.A = None
+        else:
+            dev = torch.device("cuda", device)
+            self.phi = [torch.empty(d.N, dtype=torch.float32, device=dev) for d in self.domains]
+            self.A = [torch.empty(3 * d.N, dtype=torch.float32, device=dev) for d in self.domains]
+
+    def push(self, dom: int, rho, J):
+        rp_push(self.ctx, dom, rho, J)
+
+    def push_all(self, rhos, Js):
+        rp_push_all(self.ctx, rhos, Js)
+
+    def evaluate(self):
+        rp_evaluate(self.ctx, self.phi, self.A)
+        return self.phi, self.A
+
+    def sync(self):
+        rp_sync(self.ctx)
+
+    def query(self):
+        return rp_query(self.ctx)
+
+    def pair_info(self, t, s):
+        return rp_pair_info(self.ctx, t, s)
+
+    def close(self):
+        if self.ctx:
+            rp_destroy(self.ctx)
+            self.ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

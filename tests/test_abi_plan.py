@@ -1,0 +1,186 @@
+"""CPU checks of the C-ABI library: it builds for sm_103a, loads, exports
+every entry point of include/rp.h, and its host-side planner (lag windows,
+FFT sizes, pair kinds, ring depths, argument and state errors) is right.
+No compute call is made: contexts here are RP_FLAG_PLAN_ONLY."""
+import math
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2311_15429_gb300 import rp, synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+SIZES = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192}
+
+
+def header_entry_points():
+    src = open(os.path.join(ROOT, "include", "rp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(rp_[a-z_]+)\s*\(", src)))
+
+
+def test_library_builds_and_exports_every_declared_symbol():
+    lib = rp.load()
+    names = header_entry_points()
+    assert len(names) >= 18
+    for name in names:
+        assert hasattr(lib, name), name
+        assert name in rp.SIGNATURES, f"binding lacks {name}"
+    out = os.popen(f"nm -D --defined-only {rp.library_path()}").read()
+    for name in names:
+        assert re.search(rf"\bT {name}\b", out), f"{name} not exported"
+
+
+def test_status_strings_and_kernel_names():
+    assert rp.rp_status_str(rp.RP_OK) == "RP_OK"
+    assert rp.rp_status_str(rp.RP_ERR_HISTORY) == "RP_ERR_HISTORY"
+    assert rp.rp_kernel_name(rp.RP_K_MAC_INV_COLUMN) == "mac_inv_column"
+    assert rp.rp_kernel_name(rp.RP_K_COUNT) is None
+
+
+def test_create_rejects_bad_config():
+    for c, dt, mode in ((0.0, 0.05, 0), (137.0, -1.0, 0), (137.0, 0.05, 7)):
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_create(c, dt, mode=mode, flags=rp.RP_FLAG_PLAN_ONLY)
+        assert e.value.status == rp.RP_ERR_ARG
+
+
+def _plan(domains, c=synth.C_AU, dt=0.05, mode=rp.RP_MODE_FFT, depth=0):
+    ctx = rp.rp_create(c, dt, depth, mode, rp.RP_FLAG_PLAN_ONLY)
+    for d in domains:
+        rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+    rp.rp_finalize(ctx)
+    return ctx
+
+
+def _node_distances(a, b):
+    xa, ya, za = a.coords()
+    xb, yb, zb = b.coords()
+    d = np.sqrt((xa[:, None] - xb[None]) ** 2 + (ya[:, None] - yb[None]) ** 2 + (za[:, None] - zb[None]) ** 2)
+    return d
+
+
+@pytest.mark.parametrize("geom", ["cfg1", "ragged", "offset"])
+def test_lag_windows_cover_every_node_pair(geom):
+    """Every lag m with a nonzero hat weight T(m - R/(c dt)) for some node pair
+    lies in [lag_lo, lag_hi] (Eq. 11), and lag_hi is the tightest such bound."""
+    if geom == "cfg1":
+        doms = synth.workload("cfg1").domains
+    elif geom == "ragged":
+        doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3)]
+    else:
+        doms = [synth.Domain((0.0, 0.0, 0.0), (6, 6, 6), 0.25), synth.Domain((40.3, 17.1, -9.2), (5, 7, 4), 0.25)]
+    c, dt = synth.C_AU, 0.05
+    ctx = _plan(doms, c, dt)
+    try:
+        for t in range(len(doms)):
+            for s in range(len(doms)):
+                info = rp.rp_pair_info(ctx, t, s)
+                R = _node_distances(doms[t], doms[s])
+                tau = R / (c * dt)
+                lo_need = 0 if t == s else int(np.floor(tau.min()))
+                hi_need = int(np.floor(tau.max())) + 1
+                assert info["lag_lo"] <= lo_need
+                assert info["lag_hi"] == hi_need
+                assert info["r_max"] == pytest.approx(R.max(), rel=1e-12)
+                assert info["r_min"] <= R[R > 0].min() + 1e-12 or t == s
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_cfg2_plan():
+    w = synth.workload("cfg2")
+    ctx = _plan(w.domains, w.c, w.dt, depth=w.history)
+    try:
+        cross = rp.rp_pair_info(ctx, 0, 1)
+        assert (cross["lag_lo"], cross["lag_hi"]) == (290, 294)   # B = 5 delay bins
+        assert cross["kind"] == rp.RP_PAIR_FFT and cross["fft_m"] == (96, 96, 96)
+        self_ = rp.rp_pair_info(ctx, 0, 0)
+        assert (self_["lag_lo"], self_["lag_hi"]) == (0, 3)
+        q = rp.rp_query(ctx)
+        assert q["npairs_fft"] == 4 and q["npairs_direct"] == 0
+        assert q["spectral_depth"] == 320 and q["raw_depth"] == 0
+        # two sources x 320 slots x 4 fields x (49 x 96 x 96) complex64
+        assert q["spectral_bytes"] == 2 * 320 * 4 * 49 * 96 * 96 * 8
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_fft_sizes_are_supported_and_large_enough():
+    doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3),
+            synth.Domain((-9.0, 2.0, 1.0), (1, 1, 1), 0.3)]
+    ctx = _plan(doms)
+    try:
+        for t in range(3):
+            m_t = None
+            for s in range(3):
+                info = rp.rp_pair_info(ctx, t, s)
+                assert info["kind"] == rp.RP_PAIR_FFT
+                m = info["fft_m"]
+                assert all(v in SIZES for v in m) and m[0] % 2 == 0
+                assert all(m[a] >= doms[t].n[a] + doms[s].n[a] - 1 for a in range(3))
+                m_t = m_t or m
+                assert m == m_t          # one spectral size per target
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_unequal_spacing_goes_direct_and_direct_mode():
+    doms = [synth.Domain((0.0, 0.0, 0.0), (4, 4, 4), 0.3), synth.Domain((5.0, 0.0, 0.0), (4, 4, 4), 0.25)]
+    ctx = _plan(doms)
+    try:
+        assert rp.rp_pair_info(ctx, 0, 1)["kind"] == rp.RP_PAIR_DIRECT
+        assert rp.rp_pair_info(ctx, 0, 0)["kind"] == rp.RP_PAIR_FFT
+        q = rp.rp_query(ctx)
+        assert q["raw_depth"] >= rp.rp_pair_info(ctx, 1, 0)["lag_hi"] + 1
+    finally:
+        rp.rp_destroy(ctx)
+    ctx = _plan(doms, mode=rp.RP_MODE_DIRECT)
+    try:
+        q = rp.rp_query(ctx)
+        assert q["npairs_direct"] == 4 and q["npairs_fft"] == 0
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_plan_errors():
+    # a self term beyond 96 nodes per axis is not supported by the FFT path
+    with pytest.raises(rp.RPError) as e:
+        _plan([synth.Domain((0.0, 0.0, 0.0), (97, 4, 4), 0.3)])
+    assert e.value.status == rp.RP_ERR_UNSUPPORTED
+    # coincident nodes of two domains
+    with pytest.raises(rp.RPError) as e:
+        _plan([synth.Domain((0.0, 0.0, 0.0), (3, 3, 3), 0.5), synth.Domain((0.5, 0.5, 0.5), (3, 3, 3), 0.5)])
+    assert e.value.status == rp.RP_ERR_ARG
+    ctx = rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY)
+    try:
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_add_domain(ctx, (0, 0, 0), (0, 4, 4), 0.3)
+        assert e.value.status == rp.RP_ERR_ARG
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_finalize(ctx)                 # no domains
+        assert e.value.status == rp.RP_ERR_STATE
+        rp.rp_add_domain(ctx, (0, 0, 0), (4, 4, 4), 0.3)
+        rp.rp_finalize(ctx)
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_add_domain(ctx, (9, 0, 0), (4, 4, 4), 0.3)
+        assert e.value.status == rp.RP_ERR_STATE
+        # a plan-only context runs nothing
+        import numpy as np
+        x = np.zeros(64, np.float32)
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_push(ctx, 0, x, x)
+        assert e.value.status == rp.RP_ERR_STATE
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_no_gpu_create_fails_cleanly():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(rp.RPError) as e:
+        rp.rp_create(137.0, 0.05, stream=0)
+    assert e.value.status == rp.RP_ERR_CUDA

@@ -1,0 +1,193 @@
+"""GPU parity: the CUDA path through the C-ABI against the FP64 oracle.
+
+The bar is the FP32 path's: rel-L2 <= 1e-6 per (field, target domain),
+pooled over the checked steps, with inputs rounded to FP32 for both sides.
+"""
+import numpy as np
+import pytest
+
+from paper_2311_15429_gb300 import rp, synth
+
+from _harness import histories, oracle_values, rel_l2, run_library
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-6
+
+
+def _score(domains, hists, j0, c, dt, results, nodes=None, clamp=False):
+    worst = 0.0
+    for step, outs in results.items():
+        for t, d in enumerate(domains):
+            sel = np.arange(d.N) if nodes is None else nodes[t]
+            want = oracle_values(domains, hists, j0, c, dt, t, step, sel, clamp=clamp)
+            errs = rel_l2(outs[t][:, sel], want)
+            worst = max(worst, max(errs))
+            assert max(errs) <= TOL, (step, t, errs)
+    return worst
+
+
+@pytest.mark.parametrize("mode", [rp.RP_MODE_FFT, rp.RP_MODE_DIRECT])
+def test_cfg1_full_grids(mode):
+    """2 x 16^3, h = 0.3, 20 bohr apart, 64-step history, last 8 steps, every node."""
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 64, w.dt)
+    res = run_library(w.domains, w.c, w.dt, hists, 0, range(56, 64), mode=mode)
+    _score(w.domains, hists, 0, w.c, w.dt, res)
+
+
+def test_ragged_grids_fft():
+    """Non-cubic, unequal grids (FFT sizes 12/16/... with ragged tails)."""
+    doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3),
+            synth.Domain((-2.0, 4.0, 1.5), (11, 3, 13), 0.3)]
+    srcs = synth._sources(doms)
+    hists = histories(srcs, 0, 12, 0.05)
+    res = run_library(doms, synth.C_AU, 0.05, hists, 0, [10, 11])
+    _score(doms, hists, 0, synth.C_AU, 0.05, res)
+
+
+def test_mixed_spacing_direct_fallback():
+    """A pair of unequal spacing goes through the direct kernel and adds onto
+    the FFT result of the target's other pairs."""
+    doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.3), synth.cubic((9.0, 2.0, -1.0), 10, 0.25),
+            synth.cubic((-8.0, 0.0, 3.0), 9, 0.3)]
+    srcs = synth._sources(doms)
+    hists = histories(srcs, 0, 16, 0.05)
+    res = run_library(doms, synth.C_AU, 0.05, hists, 0, [15], push="each")
+    _score(doms, hists, 0, synth.C_AU, 0.05, res)
+
+
+def test_slow_light_many_lags():
+    """c = 5 a.u.: every pair spans tens of delay bins."""
+    doms = [synth.cubic((0.0, 0.0, 0.0), 10, 0.3), synth.cubic((6.0, 1.0, 0.0), 10, 0.3)]
+    srcs = synth._sources(doms)
+    c, dt = 5.0, 0.05
+    hists = histories(srcs, 0, 60, dt)
+    res = run_library(doms, c, dt, hists, 0, [58, 59])
+    _score(doms, hists, 0, c, dt, res)
+
+
+def test_cfg2_full_size_sampled():
+    """2 x 48^3, 2000 bohr apart, 320-step ring (cross delays 290..294 steps):
+    the bench's workload in its launch configuration, checked on sampled nodes
+    (corners, centre and 60 seeded random nodes per domain)."""
+    w = synth.workload("cfg2")
+    pre = 295
+    j0, j1 = -pre, 3
+    hists = histories(w.sources, j0, j1, w.dt)
+    res = run_library(w.domains, w.c, w.dt, hists, j0, [1, 2], depth=w.history)
+    rng = np.random.default_rng(4)
+    nodes = []
+    for d in w.domains:
+        n = d.n[0]
+        corners = [i + n * (j + n * k) for i in (0, n - 1) for j in (0, n - 1) for k in (0, n - 1)]
+        centre = [n // 2 + n * (n // 2 + n * (n // 2))]
+        nodes.append(np.array(corners + centre + list(rng.integers(0, d.N, 60))))
+    _score(w.domains, hists, j0, w.c, w.dt, res, nodes=nodes)
+
+
+def test_ground_state_clamp():
+    """Under RP_FLAG_GROUND_STATE_CLAMP, samples before the first push equal it."""
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 4, w.dt)
+    res = run_library(w.domains, w.c, w.dt, hists, 0, [0, 1, 3], flags=rp.RP_FLAG_GROUND_STATE_CLAMP)
+    _score(w.domains, hists, 0, w.c, w.dt, res, clamp=True)
+
+
+def test_single_node_domain_and_zero_source():
+    """A 1x1x1 domain (its self term is just C h^2 rho) beside a normal one; an
+    all-zero source gives exactly zero from that source."""
+    doms = [synth.Domain((5.0, 0.0, 0.0), (1, 1, 1), 0.4), synth.cubic((0.0, 0.0, 0.0), 6, 0.4)]
+    rng = np.random.default_rng(2)
+    T = 8
+    hists = [rng.standard_normal((T, 4, 1)).astype(np.float32), np.zeros((T, 4, 216), np.float32)]
+    res = run_library(doms, synth.C_AU, 0.05, hists, 0, [T - 1])
+    _score(doms, hists, 0, synth.C_AU, 0.05, res)
+    C = 3 * np.log(2 + np.sqrt(3)) - np.pi / 2
+    out0 = res[T - 1][0][:, 0]
+    want = C * 0.4 ** 2 * hists[0][T - 1, :, 0].astype(np.float64)
+    want[1:] /= synth.C_AU
+    np.testing.assert_allclose(out0, want, rtol=1e-6)
+
+
+def test_push_paths_agree_bitwise():
+    """rp_push per domain, rp_push_all and rp_push_host / rp_evaluate_host give
+    identical bits."""
+    import torch
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 10, w.dt)
+    a = run_library(w.domains, w.c, w.dt, hists, 0, [9], push="all")[9]
+    b = run_library(w.domains, w.c, w.dt, hists, 0, [9], push="each")[9]
+    for x, y in zip(a, b):
+        np.testing.assert_array_equal(x, y)
+    ctx = rp.rp_create(w.c, w.dt)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        outs = [np.zeros(4 * d.N, np.float32) for d in w.domains]
+        for i in range(10):
+            for dd in range(2):
+                rho = np.ascontiguousarray(hists[dd][i, 0])
+                J = np.ascontiguousarray(hists[dd][i, 1:]).reshape(-1)
+                rp.rp_push_host(ctx, dd, rho, J)
+                rp.rp_sync(ctx)
+        phis = [o[: d.N] for o, d in zip(outs, w.domains)]
+        As = [o[d.N:] for o, d in zip(outs, w.domains)]
+        rp.rp_evaluate_host(ctx, phis, As)
+        rp.rp_sync(ctx)
+    finally:
+        rp.rp_destroy(ctx)
+    for x, o in zip(a, outs):
+        np.testing.assert_array_equal(x.reshape(-1), o)
+
+
+def test_state_errors_and_history():
+    import torch
+    w = synth.workload("cfg1")
+    dev = torch.device("cuda", 0)
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        x = [torch.zeros(d.N, device=dev) for d in w.domains]
+        J = [torch.zeros(3 * d.N, device=dev) for d in w.domains]
+        with pytest.raises(rp.RPError) as e:
+            lib.evaluate()                                   # nothing pushed
+        assert e.value.status == rp.RP_ERR_STATE
+        lib.push(0, x[0], J[0])
+        with pytest.raises(rp.RPError) as e:
+            lib.push(0, x[0], J[0])                          # twice in one step
+        assert e.value.status == rp.RP_ERR_STATE
+        with pytest.raises(rp.RPError) as e:
+            lib.evaluate()                                   # domain 1 missing
+        assert e.value.status == rp.RP_ERR_STATE
+        lib.push(1, x[1], J[1])
+        with pytest.raises(rp.RPError) as e:
+            lib.evaluate()                                   # needs 4 steps of history
+        assert e.value.status == rp.RP_ERR_HISTORY
+        lib.sync()
+
+
+def test_checkpoint_resume_bitwise(tmp_path):
+    import torch
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 14, w.dt)
+    dev = torch.device("cuda", 0)
+
+    def push(lib, i):
+        lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
+                     [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists])
+
+    path = str(tmp_path / "state.bin")
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        for i in range(10):
+            push(lib, i)
+        rp.rp_save_state(lib.ctx, path)
+        for i in range(10, 14):
+            push(lib, i)
+        ref = [t.cpu().numpy().copy() for t in lib.evaluate()[0]]
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        rp.rp_load_state(lib.ctx, path)
+        assert lib.query()["step"] == 9
+        for i in range(10, 14):
+            push(lib, i)
+        got = [t.cpu().numpy() for t in lib.evaluate()[0]]
+    for a, b in zip(ref, got):
+        np.testing.assert_array_equal(a, b)
