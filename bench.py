@@ -45,7 +45,7 @@ def parse():
     p.add_argument("--no-plain", action="store_true", help="skip timing the plain direct path")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
-    p.add_argument("--oracle-nodes", type=int, default=1024, help="oracle sample per domain")
+    p.add_argument("--oracle-nodes", type=int, default=8192, help="oracle sample per domain")
     return p.parse_args()
 
 

@@ -17,7 +17,7 @@
 namespace rp {
 size_t smem_direct(int max_nlag);
 int direct_blocks(long long n);
-cudaError_t set_direct_smem_limit(size_t bytes);
+cudaError_t open_direct_smem_limit(int max_optin);
 }  // namespace rp
 
 using namespace rp;
@@ -572,6 +572,14 @@ rp_status rp_finalize(rp_ctx *ctx)
     // ---- device memory
     rp_status st = use_device(ctx);
     if (st) return st;
+    int max_optin = 0;
+    RP_CUDA(ctx, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    {
+        const size_t need = std::max({ctx->smem_plane, ctx->smem_col, ctx->smem_mac, ctx->smem_inv, ctx->smem_dir});
+        if (need > (size_t)max_optin)
+            return fail(ctx, RP_ERR_UNSUPPORTED, "kernel shared memory " + std::to_string(need) +
+                                                     " B exceeds the device limit " + std::to_string(max_optin));
+    }
     if ((st = build_twiddles(ctx, tw))) return st;
     for (FwdRing &R : ctx->fwd) {
         if ((st = dev_alloc(ctx, &R.ring, (size_t)R.depth * R.slot_elems))) return st;
@@ -663,9 +671,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     if ((st = upload(ctx, &ctx->d_dtg, ctx->dtg))) return st;
     if ((st = upload(ctx, &ctx->d_dpairs, ctx->dpairs))) return st;
     if ((st = upload(ctx, &ctx->d_raw, ctx->raw))) return st;
-    RP_CUDA(ctx, set_kernel_smem_limits(std::max<size_t>(ctx->smem_plane, 1024), std::max<size_t>(ctx->smem_col, 1024),
-                                        std::max<size_t>(ctx->smem_mac, 1024), std::max<size_t>(ctx->smem_inv, 1024)));
-    RP_CUDA(ctx, set_direct_smem_limit(ctx->smem_dir));
+    RP_CUDA(ctx, open_kernel_smem_limits(max_optin));
+    RP_CUDA(ctx, open_direct_smem_limit(max_optin));
     RP_CUDA(ctx, cudaDeviceSynchronize());
     ctx->finalized = true;
     return RP_OK;

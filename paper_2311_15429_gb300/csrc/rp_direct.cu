@@ -119,9 +119,9 @@ size_t smem_direct(int max_nlag) { return sizeof(float) * (size_t)kDirTile * (3 
 
 int direct_blocks(long long n) { return (int)((n + kDirThreads - 1) / kDirThreads); }
 
-cudaError_t set_direct_smem_limit(size_t bytes)
+cudaError_t open_direct_smem_limit(int max_optin)
 {
-    return cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    return cudaFuncSetAttribute(k_direct, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin);
 }
 
 cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair *d_pairs, const OutPtrs &out,

@@ -481,13 +481,16 @@ size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay)
     return sizeof(float2) * ((size_t)ax.M + ay.M + (size_t)kx * ps) + sizeof(float) * (size_t)nx * ny;
 }
 
-cudaError_t set_kernel_smem_limits(size_t plane, size_t column, size_t mac, size_t inv)
+// The dynamic shared-memory limit is an attribute of the kernel function,
+// shared by every context in the process, so each kernel is opened up to the
+// device's opt-in maximum once (contexts never lower it for one another).
+cudaError_t open_kernel_smem_limits(int max_optin)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)plane))) return e;
-    if ((e = cudaFuncSetAttribute(k_fwd_column, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)column))) return e;
-    if ((e = cudaFuncSetAttribute(k_mac_inv_column, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)mac))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)inv))) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
+    if ((e = cudaFuncSetAttribute(k_fwd_column, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
+    if ((e = cudaFuncSetAttribute(k_mac_inv_column, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
+    if ((e = cudaFuncSetAttribute(k_inv_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
     return cudaSuccess;
 }
 

@@ -131,7 +131,7 @@ size_t smem_fwd_plane(int ny, const Axis &ax);
 size_t smem_fwd_column(const Axis &az);
 size_t smem_mac_inv_column(const Axis &az);
 size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay);
-cudaError_t set_kernel_smem_limits(size_t plane, size_t column, size_t mac, size_t inv);
+cudaError_t open_kernel_smem_limits(int max_optin);
 
 // ---- host FP64 kernel spectra (rp_spectra.cpp) ----
 

@@ -191,3 +191,30 @@ def test_checkpoint_resume_bitwise(tmp_path):
         got = [t.cpu().numpy() for t in lib.evaluate()[0]]
     for a, b in zip(ref, got):
         np.testing.assert_array_equal(a, b)
+
+
+def test_contexts_coexist():
+    """A direct-mode context finalized after an FFT-mode one does not affect
+    it (kernel attributes are process-wide), and both stay correct."""
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 8, w.dt)
+    import torch
+    dev = torch.device("cuda", 0)
+    a = rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_FFT)
+    b = rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_DIRECT)
+    try:
+        for i in range(8):
+            r = [torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists]
+            J = [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists]
+            a.push(0, r[0], J[0]); a.push(1, r[1], J[1])
+            b.push_all(r, J)
+        for lib in (a, b):
+            phi, A = lib.evaluate()
+            torch.cuda.synchronize()
+            for t, d in enumerate(w.domains):
+                got = np.concatenate([phi[t].cpu().numpy()[None], A[t].cpu().numpy().reshape(3, -1)])
+                want = oracle_values(w.domains, hists, 0, w.c, w.dt, t, 7, np.arange(d.N))
+                assert max(rel_l2(got, want)) <= TOL
+    finally:
+        a.close()
+        b.close()
