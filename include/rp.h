@@ -200,6 +200,32 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
  */
 rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 
+/*
+ * rp_evaluate_host_noalloc -- rp_evaluate_host without any device allocation.
+ * (No counterpart in the paper: this is a property of the library, not of the
+ * method.)
+ *
+ * rp_evaluate_host stages phi and A in device memory that it allocates with
+ * cudaMalloc on its first call.  Some callers cannot allow that: a process
+ * whose device memory is handed out by another allocator or fixed budget once
+ * the run has started, where the library may not call cudaMalloc after
+ * set-up.  This variant stages the results instead in a fixed array compiled
+ * into the library (16 MiB: at most 1,048,576 grid points summed over all
+ * domains; more returns RP_ERR_UNSUPPORTED before any work) and calls no
+ * allocating routine.  Every GPU that loads the library holds that array
+ * until the process exits.
+ *
+ * Arguments, layout and results are those of rp_evaluate_host: h_phi[n] gets
+ * N_n floats and h_A[n] 3*N_n floats, valid after rp_sync.  The first call on
+ * a device looks up the array's device address (cudaGetSymbolAddress); make
+ * that first call before any stream capture.  All calls in the process on a
+ * device share the one array and each call overwrites it, so calls whose work
+ * overlaps on the GPU (two contexts on different streams, say) race and may
+ * return each other's values: order them on one stream, or synchronise
+ * between them.
+ */
+rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
+
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);
 

@@ -7,6 +7,7 @@
 #include <cstdio>
 #include <cstring>
 #include <map>
+#include <mutex>
 #include <string>
 #include <thread>
 #include <vector>
@@ -845,6 +846,84 @@ rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A)
         A[d] = ctx->out_stage[d] + ctx->doms[d].N;
     }
     if ((st = rp_evaluate(ctx, phi.data(), A.data()))) return st;
+    for (int d = 0; d < nd; ++d) {
+        const long long N = ctx->doms[d].N;
+        RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        RP_CUDA(ctx, cudaMemcpyAsync(h_A[d], A[d], 3 * N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    return RP_OK;
+}
+
+}  // extern "C"
+
+// ---------------------------------------------------------------- evaluation without allocation
+//
+// rp_evaluate_host stages phi and A in device memory it allocates on its
+// first call.  The variant below stages them in a fixed array compiled into
+// the library instead, so that it never calls an allocator.
+
+namespace {
+
+// Largest total sum over domains of 4 * N_d floats (phi, Ax, Ay, Az) the
+// fixed staging array holds: 16 MiB, i.e. up to 1,048,576 grid points in all.
+constexpr long long kNoAllocFloats = 4LL * 1024 * 1024;
+
+// Device staging for rp_evaluate_host_noalloc.  Every device that loads the
+// library holds it until the process exits; all contexts on a device share it.
+static __device__ __align__(256) float g_noalloc_stage[kNoAllocFloats];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+float *g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the staging array on ctx->device.  Looked up once per
+// device, with that device current (the host-side symbol is only a stand-in
+// for the device address and must not be handed to a kernel).
+rp_status noalloc_stage_address(rp_ctx *ctx, float **out)
+{
+    if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
+        return fail(ctx, RP_ERR_UNSUPPORTED, "rp_evaluate_host_noalloc: device index above 63");
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_addr[ctx->device]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_stage);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaGetSymbolAddress(g_noalloc_stage)");
+        g_noalloc_addr[ctx->device] = static_cast<float *>(p);
+    }
+    *out = g_noalloc_addr[ctx->device];
+    return RP_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *const *h_A)
+{
+    rp_status st = check_ready(ctx);   // also makes ctx->device current
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!h_phi || !h_A) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host_noalloc: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!h_phi[d] || !h_A[d]) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host_noalloc: NULL output buffer");
+    long long need = 0;
+    for (int d = 0; d < nd; ++d) need += 4 * ctx->doms[d].N;
+    if (need > kNoAllocFloats)
+        return fail(ctx, RP_ERR_UNSUPPORTED, "rp_evaluate_host_noalloc: the domains need " + std::to_string(need) +
+                                                 " staging floats, the fixed array holds " +
+                                                 std::to_string(kNoAllocFloats));
+    float *stage = nullptr;
+    if ((st = noalloc_stage_address(ctx, &stage))) return st;
+    // every staged value is written by the evaluation before it is copied out,
+    // so nothing left from an earlier call needs clearing
+    float *phi[kMaxDomains], *A[kMaxDomains];
+    long long off = 0;
+    for (int d = 0; d < nd; ++d) {
+        phi[d] = stage + off;
+        A[d] = stage + off + ctx->doms[d].N;
+        off += 4 * ctx->doms[d].N;
+    }
+    if ((st = rp_evaluate(ctx, phi, A))) return st;
     for (int d = 0; d < nd; ++d) {
         const long long N = ctx->doms[d].N;
         RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));

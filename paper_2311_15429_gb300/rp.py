@@ -65,6 +65,7 @@ SIGNATURES = {
     "rp_push_host": (_I, [_V, _I, _V, _V]),
     "rp_evaluate": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
+    "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
     "rp_sync": (_I, [_V]),
     "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
@@ -198,6 +199,12 @@ def rp_evaluate_host(ctx, phis: Sequence, As: Sequence):
     pp, _a = _ptr_array(phis)
     pa, _b = _ptr_array(As)
     _check(load().rp_evaluate_host(ctx, pp, pa), ctx)
+
+
+def rp_evaluate_host_noalloc(ctx, phis: Sequence, As: Sequence):
+    pp, _a = _ptr_array(phis)
+    pa, _b = _ptr_array(As)
+    _check(load().rp_evaluate_host_noalloc(ctx, pp, pa), ctx)
 
 
 def rp_sync(ctx):
