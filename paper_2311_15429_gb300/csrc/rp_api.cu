@@ -44,6 +44,16 @@ struct ProfRec {
     cudaEvent_t a, b;
 };
 
+// One launch of a kernel pair over a contiguous range [i0, i1) of rings (or
+// targets) of one size class: first kernel's blocks [blk0, blk1), second
+// kernel's blocks [blk2_0, blk2_1).
+struct LaunchGroup {
+    int cls;
+    int i0, i1;
+    int blk0, blk1;
+    int blk2_0, blk2_1;
+};
+
 // Supported padded lengths: R * L with R in {1,2,3,4,6}, L a power of two <= 32.
 const int kSizes[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192};
 
@@ -85,8 +95,8 @@ struct rp_ctx {
 
     // plan
     std::vector<FwdRing> fwd;
-    std::vector<int> src_ring0, src_ring1;           // ring range per source
-    std::vector<int> src_plane_lo, src_plane_hi, src_col_lo, src_col_hi;
+    std::vector<LaunchGroup> fwd_groups;             // (plane pass, column pass) per size class
+    std::vector<LaunchGroup> inv_groups;             // (MAC + column pass, plane pass) per size class
     std::vector<InvTarget> inv;
     std::vector<MacEntry> entries;
     std::vector<DirectTarget> dtg;
@@ -427,14 +437,22 @@ rp_status rp_finalize(rp_ctx *ctx)
             }
             ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1);
         }
-    ctx->src_ring0.assign(nd, 0);
-    ctx->src_ring1.assign(nd, 0);
-    ctx->src_plane_lo.assign(nd, 0);
-    ctx->src_plane_hi.assign(nd, 0);
-    ctx->src_col_lo.assign(nd, 0);
-    ctx->src_col_hi.assign(nd, 0);
+    // order rings by (kernel size class, source): each class is one launch
+    std::vector<int> ring_order(ring_keys.size());
+    for (size_t r = 0; r < ring_keys.size(); ++r) ring_order[r] = (int)r;
+    auto ring_class = [&](int r) {
+        const auto &m = ring_keys[r].second;
+        return size_class(make_axis(m[0]), make_axis(m[1]), make_axis(m[2]));
+    };
+    std::stable_sort(ring_order.begin(), ring_order.end(), [&](int x, int y) {
+        const int cx = ring_class(x), cy = ring_class(y);
+        return cx != cy ? cx < cy : ring_keys[x].first < ring_keys[y].first;
+    });
+    std::vector<int> ring_pos(ring_keys.size());
     std::map<int, const float2 *> tw;
-    for (size_t r = 0; r < ring_keys.size(); ++r) {
+    for (size_t i = 0; i < ring_order.size(); ++i) {
+        const int r = ring_order[i];
+        ring_pos[r] = (int)i;
         const int s = ring_keys[r].first;
         const auto &m = ring_keys[r].second;
         const DomainDesc &S = ctx->doms[s];
@@ -448,38 +466,36 @@ rp_status rp_finalize(rp_ctx *ctx)
         R.plane0 = ctx->plane_blocks;
         R.tile0 = ctx->col_blocks;
         ctx->plane_blocks += 4 * R.nz;
-        ctx->col_blocks += 4 * R.kx * ((m[1] + kTileY - 1) / kTileY);
+        ctx->col_blocks += R.kx * ((m[1] + kTileY - 1) / kTileY);
         tw[m[0]]; tw[m[1]]; tw[m[2]];
         ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
         ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
         ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(R.ny, R.ax));
         ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
+        const int cls = ring_class(r);
+        if (ctx->fwd_groups.empty() || ctx->fwd_groups.back().cls != cls)
+            ctx->fwd_groups.push_back({cls, (int)i, (int)i, R.plane0, R.plane0, R.tile0, R.tile0});
+        LaunchGroup &g = ctx->fwd_groups.back();
+        g.i1 = (int)i + 1;
+        g.blk1 = ctx->plane_blocks;
+        g.blk2_1 = ctx->col_blocks;
         ctx->fwd.push_back(R);
     }
-    for (int s = 0; s < nd; ++s) {
-        int r0 = -1, r1 = -1;
-        for (size_t r = 0; r < ctx->fwd.size(); ++r)
-            if (ctx->fwd[r].src == s) {
-                if (r0 < 0) r0 = (int)r;
-                r1 = (int)r + 1;
-            }
-        if (r0 < 0) { r0 = r1 = 0; }
-        ctx->src_ring0[s] = r0;
-        ctx->src_ring1[s] = r1;
-        if (r1 > r0) {
-            ctx->src_plane_lo[s] = ctx->fwd[r0].plane0;
-            ctx->src_col_lo[s] = ctx->fwd[r0].tile0;
-            const FwdRing &L = ctx->fwd[r1 - 1];
-            ctx->src_plane_hi[s] = L.plane0 + 4 * L.nz;
-            ctx->src_col_hi[s] = L.tile0 + 4 * L.kx * ((L.ay.M + kTileY - 1) / kTileY);
-        }
-    }
+    for (auto &kv : ring_of) kv.second = ring_pos[kv.second];
 
-    // ---- FFT targets and their (source, lag) entries
+    // ---- FFT targets, ordered by size class, and their (source, lag)
+    // entries: the self pair's real kernels first, then the complex ones
     struct EntryPlan { int t, s, lag, ring; bool real_g; };
     std::vector<EntryPlan> eplan;
-    for (int t = 0; t < nd; ++t) {
-        if (!tgt_fft[t]) continue;
+    std::vector<int> tgt_order;
+    for (int t = 0; t < nd; ++t)
+        if (tgt_fft[t]) tgt_order.push_back(t);
+    auto tgt_class = [&](int t) {
+        return size_class(make_axis(tm[t][0]), make_axis(tm[t][1]), make_axis(tm[t][2]));
+    };
+    std::stable_sort(tgt_order.begin(), tgt_order.end(),
+                     [&](int x, int y) { return tgt_class(x) < tgt_class(y); });
+    for (int t : tgt_order) {
         const DomainDesc &T = ctx->doms[t];
         InvTarget I{};
         I.nx = T.n[0]; I.ny = T.n[1]; I.nz = T.n[2];
@@ -487,11 +503,14 @@ rp_status rp_finalize(rp_ctx *ctx)
         I.kx = tm[t][0] / 2 + 1;
         I.dom = t;
         I.e0 = (int)eplan.size();
-        for (int s = 0; s < nd; ++s) {
-            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
-            if (p.kind != RP_PAIR_FFT) continue;
-            const int ring = ring_of[std::make_pair(s, tm[t])];
-            for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s});
+        for (int pass = 0; pass < 2; ++pass) {
+            for (int s = 0; s < nd; ++s) {
+                const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+                if (p.kind != RP_PAIR_FFT || (pass == 0) != (s == t)) continue;
+                const int ring = ring_of[std::make_pair(s, tm[t])];
+                for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s});
+            }
+            if (pass == 0) I.er = (int)eplan.size();
         }
         I.e1 = (int)eplan.size();
         I.tile0 = ctx->mac_blocks;
@@ -500,6 +519,14 @@ rp_status rp_finalize(rp_ctx *ctx)
         ctx->invp_blocks += 4 * I.nz;
         ctx->smem_mac = std::max(ctx->smem_mac, smem_mac_inv_column(I.az));
         ctx->smem_inv = std::max(ctx->smem_inv, smem_inv_plane(I.nx, I.ny, I.ax, I.ay));
+        const int cls = tgt_class(t);
+        const int i = (int)ctx->inv.size();
+        if (ctx->inv_groups.empty() || ctx->inv_groups.back().cls != cls)
+            ctx->inv_groups.push_back({cls, i, i, I.tile0, I.tile0, I.plane0, I.plane0});
+        LaunchGroup &g = ctx->inv_groups.back();
+        g.i1 = i + 1;
+        g.blk1 = ctx->mac_blocks;
+        g.blk2_1 = ctx->invp_blocks;
         ctx->inv.push_back(I);
     }
     for (const EntryPlan &e : eplan) {
@@ -720,23 +747,32 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
              })))
             return st;
     }
-    // spectral rings of these sources (rings are ordered by source, so the
-    // rings of d0..d1-1 form one contiguous range)
-    int rr0 = -1, rr1 = -1, plo = 0, phi = 0, clo = 0, chi = 0;
-    for (int d = d0; d < d1; ++d) {
-        if (ctx->src_ring1[d] <= ctx->src_ring0[d]) continue;
-        if (rr0 < 0) { rr0 = ctx->src_ring0[d]; plo = ctx->src_plane_lo[d]; clo = ctx->src_col_lo[d]; }
-        rr1 = ctx->src_ring1[d];
-        phi = ctx->src_plane_hi[d];
-        chi = ctx->src_col_hi[d];
+    // spectral rings of these sources: one launch pair per size class when
+    // every domain pushes, else one per ring of the pushing domain
+    const int nd = (int)ctx->doms.size();
+    std::vector<LaunchGroup> launches;
+    if (d0 == 0 && d1 == nd) {
+        launches = ctx->fwd_groups;
+    } else {
+        for (int r = 0; r < (int)ctx->fwd.size(); ++r) {
+            const FwdRing &R = ctx->fwd[r];
+            if (R.src < d0 || R.src >= d1) continue;
+            const int tiles = R.kx * ((R.ay.M + kTileY - 1) / kTileY);
+            launches.push_back({size_class(R.ax, R.ay, R.az), r, r + 1, R.plane0, R.plane0 + 4 * R.nz, R.tile0,
+                                R.tile0 + tiles});
+        }
     }
-    if (rr0 >= 0) {
+    for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "forward plane pass", [&] {
-                 return launch_fwd_plane(ctx->d_fwd, in, rr0, rr1, plo, phi - plo, ctx->smem_plane, ctx->stream);
+                 return launch_fwd_plane(g.cls, ctx->d_fwd, in, g.i0, g.i1, g.blk0, g.blk1 - g.blk0, ctx->smem_plane,
+                                         ctx->stream);
              })))
             return st;
+    }
+    for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_COLUMN, "forward column pass", [&] {
-                 return launch_fwd_column(ctx->d_fwd, rr0, rr1, clo, chi - clo, ctx->smem_col, step, ctx->stream);
+                 return launch_fwd_column(g.cls, ctx->d_fwd, g.i0, g.i1, g.blk2_0, g.blk2_1 - g.blk2_0,
+                                          ctx->smem_col, step, ctx->stream);
              })))
             return st;
     }
@@ -807,15 +843,17 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     const long long step = ctx->step;
     const int clamp = ctx->clamp ? 1 : 0;
     const float inv_c = (float)(1.0 / ctx->cfg.c);
-    if (!ctx->inv.empty()) {
+    for (const LaunchGroup &g : ctx->inv_groups) {
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
-                 return launch_mac_inv_column(ctx->d_inv, (int)ctx->inv.size(), ctx->d_entries, ctx->mac_blocks,
+                 return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, g.blk1 - g.blk0,
                                               ctx->smem_mac, step, clamp, ctx->stream);
              })))
             return st;
+    }
+    for (const LaunchGroup &g : ctx->inv_groups) {
         if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
-                 return launch_inv_plane(ctx->d_inv, (int)ctx->inv.size(), out, ctx->invp_blocks, ctx->smem_inv,
-                                         inv_c, ctx->stream);
+                 return launch_inv_plane(g.cls, ctx->d_inv, g.i0, g.i1, g.blk2_0, out, g.blk2_1 - g.blk2_0,
+                                         ctx->smem_inv, inv_c, ctx->stream);
              })))
             return st;
     }

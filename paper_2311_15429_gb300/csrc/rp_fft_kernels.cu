@@ -4,7 +4,7 @@
 //
 //   push   : k_ring_push   raw (rho, J) slice -> raw history ring (direct pairs only)
 //            k_fwd_plane   R2C along x + FFT along y of one z-plane of a source
-//            k_fwd_column  FFT along z of a (kx, ky-tile) column block -> spectral ring
+//            k_fwd_column  FFT along z of a (kx, 16 ky) column block, 4 fields -> spectral ring
 //   eval   : k_mac_inv_col sum over (source, lag) of G_m * S(l - m) for a column
 //                          block, then inverse FFT along z (kept z < nz of the target)
 //            k_inv_plane   inverse FFT along y then C2R along x of one z-plane,
@@ -13,6 +13,11 @@
 // Layouts: a spectrum is [field][kx][kz][ky] with ky fastest and kx <= mx/2;
 // the scratch after a plane pass is [field][kx][z][ky]; every field array of
 // a domain is [z][y][x].
+//
+// Every kernel is instantiated for the cubic padded sizes M in
+// {32, 48, 64, 96, 128, 192} (shapes known at compile time, 16-byte loads
+// and stores of column pairs) and for M = 0 (any supported shape, read at run
+// time).
 #include <cuda_runtime.h>
 
 #include "rp_fft.cuh"
@@ -21,6 +26,27 @@
 namespace rp {
 
 namespace {
+
+__host__ __device__ constexpr int radix_R(int M)
+{
+    return M % 3 == 0 ? (M / 3 <= 32 ? 3 : 6) : (M <= 32 ? 1 : M / 32);
+}
+__host__ __device__ constexpr int radix_L(int M) { return M / radix_R(M); }
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
+
+template <int M>
+__device__ __forceinline__ Axis axis_of(const Axis &rt)
+{
+    if constexpr (M == 0) return rt;
+    else return Axis{M, radix_R(M), radix_L(M), ilog2c(radix_L(M))};
+}
+
+template <int M, class F>
+__device__ __forceinline__ void run_radix(int R_rt, F &f)
+{
+    if constexpr (M == 0) dispatch_radix(R_rt, f);
+    else f.template run<radix_R(M)>();
+}
 
 // index r in [lo, hi) of the last record whose first block (field) is <= b
 template <class T>
@@ -32,6 +58,8 @@ __device__ __forceinline__ int owner_of(const T *arr, int lo, int hi, int b, int
     }
     return lo;
 }
+
+__device__ __forceinline__ float4 ldg4(const float2 *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
 // ---------------------------------------------------------------- raw ring push
 
@@ -64,7 +92,8 @@ __global__ void __launch_bounds__(kThreads) k_ring_push(const RawRing *__restric
 // ---------------------------------------------------------------- forward plane pass
 
 struct FwdPlaneX {
-    const FwdRing &R;
+    Axis a;
+    int nx, ny, kx;
     const float *plane;
     float2 *Q;      // [ny][qs]
     int qs;
@@ -73,26 +102,25 @@ struct FwdPlaneX {
     int lane, warp, nwarps;
 
     template <int RX>
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
-        const Axis &a = R.ax;
         const int G = 32 >> a.logL;
         const int grp = lane >> a.logL, g = lane & (a.L - 1);
-        const int pairs = (R.ny + 1) >> 1;
+        const int pairs = (ny + 1) >> 1;
         const int per_iter = nwarps * G;
         float2 *Wg = W + (warp * G + grp) * a.M;
         for (int base = 0; base < pairs; base += per_iter) {
             const int p = base + warp * G + grp;
             const bool valid = p < pairs;
             const int ya = 2 * p, yb = 2 * p + 1;
-            const bool vb = valid && yb < R.ny;
+            const bool vb = valid && yb < ny;
             float2 v[RX];
 #pragma unroll
             for (int n = 0; n < RX; ++n) {
                 const int xi = n * a.L + g;
-                const bool in_x = xi < R.nx;
-                v[n].x = (valid && in_x) ? plane[ya * R.nx + xi] : 0.0f;
-                v[n].y = (vb && in_x) ? plane[yb * R.nx + xi] : 0.0f;
+                const bool in_x = xi < nx;
+                v[n].x = (valid && in_x) ? plane[ya * nx + xi] : 0.0f;
+                v[n].y = (vb && in_x) ? plane[yb * nx + xi] : 0.0f;
             }
             line_fft<RX, false>(v, g, a, tw);
             const int kb = bitrev_lanes(g, a.logL) * RX;
@@ -101,9 +129,9 @@ struct FwdPlaneX {
             __syncwarp();
             // two real rows from one complex transform:
             //   A[k] = (Z[k] + conj Z[M-k]) / 2,  B[k] = (Z[k] - conj Z[M-k]) / (2i)
-            for (int k = g; k < R.kx; k += a.L) {
+            for (int k = g; k < kx; k += a.L) {
                 const float2 zk = Wg[k];
-                const float2 zc = cconj(Wg[(a.M - k) % a.M]);
+                const float2 zc = cconj(Wg[k == 0 ? 0 : a.M - k]);
                 const float2 A = cscale(cadd(zk, zc), 0.5f);
                 const float2 D = csub(zk, zc);
                 const float2 B = make_float2(0.5f * D.y, -0.5f * D.x);
@@ -116,29 +144,29 @@ struct FwdPlaneX {
 };
 
 struct FwdPlaneY {
-    const FwdRing &R;
+    Axis a;
+    int ny, kx, nz;
     const float2 *Q;
     int qs;
-    float2 *out;    // t1 + ((f*kx + 0)*nz + z)*my ; row kx at out + kx*nz*my
+    float2 *out;    // row kx at out + kx*nz*my
     const float2 *tw;
     int lane, warp, nwarps;
 
     template <int RY>
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
-        const Axis &a = R.ay;
         const int G = 32 >> a.logL;
         const int grp = lane >> a.logL, g = lane & (a.L - 1);
         const int per_iter = nwarps * G;
-        const long long row_stride = (long long)R.nz * a.M;
-        for (int base = 0; base < R.kx; base += per_iter) {
+        const long long row_stride = (long long)nz * a.M;
+        for (int base = 0; base < kx; base += per_iter) {
             const int kxi = base + warp * G + grp;
-            const bool valid = kxi < R.kx;
+            const bool valid = kxi < kx;
             float2 v[RY];
 #pragma unroll
             for (int n = 0; n < RY; ++n) {
                 const int yi = n * a.L + g;
-                v[n] = (valid && yi < R.ny) ? Q[yi * qs + kxi] : make_float2(0.0f, 0.0f);
+                v[n] = (valid && yi < ny) ? Q[yi * qs + kxi] : make_float2(0.0f, 0.0f);
             }
             line_fft<RY, false>(v, g, a, tw);
             const int kb = bitrev_lanes(g, a.logL) * RY;
@@ -151,6 +179,7 @@ struct FwdPlaneY {
     }
 };
 
+template <int M>
 __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restrict__ rings, IoPtrs in,
                                                           int r0, int r1, int block_lo)
 {
@@ -159,46 +188,50 @@ __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restric
     const int b = blockIdx.x + block_lo;
     const int r = owner_of(rings, r0, r1, b, &FwdRing::plane0);
     const FwdRing &R = rings[r];
+    const Axis ax = axis_of<M>(R.ax), ay = axis_of<M>(R.ay);
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const int kx = ax.M / 2 + 1;
     const int local = b - R.plane0;
-    const int f = local / R.nz, z = local % R.nz;
-    const long long N = (long long)R.nx * R.ny * R.nz;
+    const int f = local / nz, z = local % nz;
+    const long long N = (long long)nx * ny * nz;
 
     float2 *twx = sm;
-    float2 *twy = twx + R.ax.M;
-    const int qs = R.kx | 1;
-    float2 *Q = twy + R.ay.M;
-    float2 *W = Q + R.ny * qs;
-    load_twiddles(twx, R.tw_x, R.ax.M);
-    load_twiddles(twy, R.tw_y, R.ay.M);
+    float2 *twy = twx + ax.M;
+    const int qs = kx | 1;
+    float2 *Q = twy + ay.M;
+    float2 *W = Q + ny * qs;
+    load_twiddles(twx, R.tw_x, ax.M);
+    load_twiddles(twy, R.tw_y, ay.M);
     __syncthreads();
 
     const float *src = f == 0 ? in.rho[R.src] : in.J[R.src] + (long long)(f - 1) * N;
-    const float *plane = src + (long long)z * R.nx * R.ny;
+    const float *plane = src + (long long)z * nx * ny;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    FwdPlaneX px{R, plane, Q, qs, W, twx, lane, warp, nwarps};
-    dispatch_radix(R.ax.R, px);
+    FwdPlaneX px{ax, nx, ny, kx, plane, Q, qs, W, twx, lane, warp, nwarps};
+    run_radix<M>(ax.R, px);
     __syncthreads();
-    float2 *out = R.t1 + ((long long)f * R.kx * R.nz + z) * R.ay.M;
-    FwdPlaneY py{R, Q, qs, out, twy, lane, warp, nwarps};
-    dispatch_radix(R.ay.R, py);
+    float2 *out = R.t1 + ((long long)f * kx * nz + z) * ay.M;
+    FwdPlaneY py{ay, ny, kx, nz, Q, qs, out, twy, lane, warp, nwarps};
+    run_radix<M>(ay.R, py);
 }
 
-// ---------------------------------------------------------------- forward column pass
+// ---------------------------------------------------------------- column passes
 
+// Line FFTs down the columns of a shared-memory tile [field][M][kTileYPad].
 struct ColumnFFT {
-    const Axis &a;
-    float2 *V;        // [M][kTileYPad] (per field block: base passed in)
-    long long field_stride;  // float2 between fields in V (0 if one field)
-    int ncols;        // columns per field
+    Axis a;
+    float2 *V;
+    int field_stride;  // float2 between fields in V
+    int ncols;         // columns per field
     int nfields;
-    int keep;         // outputs kept: index < keep
+    int keep;          // outputs kept: index < keep
     const float2 *tw;
     bool inverse;
     int lane, warp, nwarps;
 
     template <int RR>
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
         const int G = 32 >> a.logL;
         const int grp = lane >> a.logL, g = lane & (a.L - 1);
@@ -225,6 +258,8 @@ struct ColumnFFT {
     }
 };
 
+// Forward FFT along z of the four fields of one (kx, 16-ky) column block.
+template <int M>
 __global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restrict__ rings, int r0, int r1,
                                                            int block_lo, long long step)
 {
@@ -233,121 +268,247 @@ __global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restri
     const int b = blockIdx.x + block_lo;
     const int r = owner_of(rings, r0, r1, b, &FwdRing::tile0);
     const FwdRing &R = rings[r];
-    const int my = R.ay.M, mz = R.az.M;
+    const Axis az = axis_of<M>(R.az);
+    const int my = M ? M : R.ay.M, mz = az.M, nz = R.nz;
+    const int kx = M ? M / 2 + 1 : R.kx;
     const int ntile = (my + kTileY - 1) / kTileY;
     const int local = b - R.tile0;
-    const int per_field = R.kx * ntile;
-    const int f = local / per_field, rem = local % per_field;
-    const int kxi = rem / ntile, ky0 = (rem % ntile) * kTileY;
+    const int kxi = local / ntile, ky0 = (local % ntile) * kTileY;
+    const int ncols = min(kTileY, my - ky0);
+    const int fs = mz * kTileYPad;
 
     float2 *tw = sm;
     float2 *V = tw + mz;
     load_twiddles(tw, R.tw_z, mz);
-    const float2 *src = R.t1 + ((long long)f * R.kx + kxi) * R.nz * my;
-    for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
-        const int zi = i / kTileY, c = i % kTileY;
-        float2 v = make_float2(0.0f, 0.0f);
-        if (zi < R.nz && ky0 + c < my) v = src[(long long)zi * my + ky0 + c];
-        V[zi * kTileYPad + c] = v;
-    }
-    __syncthreads();
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const int ncols = min(kTileY, my - ky0);
-    ColumnFFT cf{R.az, V, 0, ncols, 1, mz, tw, false, lane, warp, nwarps};
-    dispatch_radix(R.az.R, cf);
-    __syncthreads();
-    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems +
-                  ((long long)f * R.kx + kxi) * mz * my;
-    for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
-        const int kz = i / kTileY, c = i % kTileY;
-        if (c < ncols) dst[(long long)kz * my + ky0 + c] = V[kz * kTileYPad + c];
-    }
-}
-
-// ---------------------------------------------------------------- MAC + inverse column pass
-
-__global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__restrict__ tgts, int ntgt,
-                                                               const MacEntry *__restrict__ entries,
-                                                               long long step, int clamp)
-{
-    extern __shared__ float4 smem_f4[];
-    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
-    const int b = blockIdx.x;
-    const int t = owner_of(tgts, 0, ntgt, b, &InvTarget::tile0);
-    const InvTarget &T = tgts[t];
-    const int my = T.ay.M, mz = T.az.M;
-    const int ntile = (my + kTileY - 1) / kTileY;
-    const int local = b - T.tile0;
-    const int kxi = local / ntile, ky0 = (local % ntile) * kTileY;
-    const int ncols = min(kTileY, my - ky0);
-    const long long fstride = (long long)T.kx * mz * my;
-    const long long col0 = (long long)kxi * mz * my + ky0;
-
-    float2 *tw = sm;
-    float2 *acc = tw + mz;                 // [4][mz][kTileYPad]
-    const int fs = mz * kTileYPad;
-    load_twiddles(tw, T.tw_z, mz);
-    for (int i = threadIdx.x; i < 4 * fs; i += blockDim.x) acc[i] = make_float2(0.0f, 0.0f);
-    __syncthreads();
-
-    // Each thread owns the (kz, c) cells i = threadIdx.x + k*blockDim.x; the
-    // same cells for every entry, so no barrier is needed between entries.
-    for (int e = T.e0; e < T.e1; ++e) {
-        const MacEntry E = entries[e];
-        long long j = step - E.lag;
-        if (clamp && j < 0) j = 0;
-        const float2 *S = E.ring + (j % E.depth) * E.slot_elems + col0;
-        const float *Gr = static_cast<const float *>(E.g) + col0;
-        const float2 *Gc = static_cast<const float2 *>(E.g) + col0;
-#pragma unroll 2
-        for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
-            const int kz = i / kTileY, c = i % kTileY;
-            if (c >= ncols) continue;
-            const long long off = (long long)kz * my + c;
-            const float2 g = E.is_real ? make_float2(__ldg(Gr + off), 0.0f) : __ldg(Gc + off);
-            const float2 s0 = __ldg(S + off);
-            const float2 s1 = __ldg(S + fstride + off);
-            const float2 s2 = __ldg(S + 2 * fstride + off);
-            const float2 s3 = __ldg(S + 3 * fstride + off);
-            const int a = kz * kTileYPad + c;
-            acc[a] = cadd(acc[a], cmul(g, s0));
-            acc[fs + a] = cadd(acc[fs + a], cmul(g, s1));
-            acc[2 * fs + a] = cadd(acc[2 * fs + a], cmul(g, s2));
-            acc[3 * fs + a] = cadd(acc[3 * fs + a], cmul(g, s3));
+    const long long t1_field = (long long)kx * nz * my;
+    const float2 *src = R.t1 + (long long)kxi * nz * my + ky0;
+    if constexpr (M > 0) {
+        // 16-byte loads of column pairs; rows z >= nz are the zero padding
+        for (int i = threadIdx.x; i < 4 * mz * (kTileY / 2); i += blockDim.x) {
+            const int f = i / (mz * (kTileY / 2)), rem = i % (mz * (kTileY / 2));
+            const int zi = rem / (kTileY / 2), p = rem % (kTileY / 2);
+            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (zi < nz) v = ldg4(src + f * t1_field + (long long)zi * my + 2 * p);
+            float2 *d = V + f * fs + zi * kTileYPad + 2 * p;
+            d[0] = make_float2(v.x, v.y);
+            d[1] = make_float2(v.z, v.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 4 * mz * kTileY; i += blockDim.x) {
+            const int f = i / (mz * kTileY), rem = i % (mz * kTileY);
+            const int zi = rem / kTileY, c = rem % kTileY;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (zi < nz && c < ncols) v = src[f * t1_field + (long long)zi * my + c];
+            V[f * fs + zi * kTileYPad + c] = v;
         }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    ColumnFFT cf{T.az, acc, fs, ncols, 4, T.nz, tw, true, lane, warp, nwarps};
-    dispatch_radix(T.az.R, cf);
+    ColumnFFT cf{az, V, fs, ncols, 4, mz, tw, false, lane, warp, nwarps};
+    run_radix<M>(az.R, cf);
     __syncthreads();
-    for (int i = threadIdx.x; i < 4 * T.nz * kTileY; i += blockDim.x) {
-        const int f = i / (T.nz * kTileY), rem = i % (T.nz * kTileY);
-        const int zi = rem / kTileY, c = rem % kTileY;
-        if (c < ncols)
-            T.t2[(((long long)f * T.kx + kxi) * T.nz + zi) * my + ky0 + c] = acc[f * fs + zi * kTileYPad + c];
+    const long long ring_field = (long long)kx * mz * my;
+    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems + (long long)kxi * mz * my + ky0;
+    if constexpr (M > 0) {
+        for (int i = threadIdx.x; i < 4 * mz * (kTileY / 2); i += blockDim.x) {
+            const int f = i / (mz * (kTileY / 2)), rem = i % (mz * (kTileY / 2));
+            const int kz = rem / (kTileY / 2), p = rem % (kTileY / 2);
+            const float2 *s = V + f * fs + kz * kTileYPad + 2 * p;
+            *reinterpret_cast<float4 *>(dst + f * ring_field + (long long)kz * my + 2 * p) =
+                make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 4 * mz * kTileY; i += blockDim.x) {
+            const int f = i / (mz * kTileY), rem = i % (mz * kTileY);
+            const int kz = rem / kTileY, c = rem % kTileY;
+            if (c < ncols) dst[f * ring_field + (long long)kz * my + c] = V[f * fs + kz * kTileYPad + c];
+        }
+    }
+}
+
+// Spectral multiply-accumulate over the target's (source, lag) entries for
+// one (kx, 16-ky) column block and all four fields, then the inverse FFT
+// along z of the 64 columns; rows z < nz of the target go to T2.
+template <int M>
+__global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__restrict__ tgts, int t0, int t1,
+                                                               int block_lo, const MacEntry *__restrict__ entries,
+                                                               long long step, int clamp)
+{
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const int b = blockIdx.x + block_lo;
+    const int t = owner_of(tgts, t0, t1, b, &InvTarget::tile0);
+    const InvTarget &T = tgts[t];
+    const Axis az = axis_of<M>(T.az);
+    const int my = M ? M : T.ay.M, mz = az.M;
+    const int kx = M ? M / 2 + 1 : T.kx;
+    const int ntile = (my + kTileY - 1) / kTileY;
+    const int local = b - T.tile0;
+    const int kxi = local / ntile, ky0 = (local % ntile) * kTileY;
+    const int ncols = min(kTileY, my - ky0);
+    const long long fstride = (long long)kx * mz * my;
+    const long long col0 = (long long)kxi * mz * my + ky0;
+    const int fs = mz * kTileYPad;
+
+    float2 *tw = sm;
+    float2 *acc = tw + mz;                 // [4][mz][kTileYPad]
+    load_twiddles(tw, T.tw_z, mz);
+
+    if constexpr (M > 0) {
+        // Thread (p, r0) owns ky columns 2p, 2p+1 and kz rows r0 + 32 i.  All
+        // operands of an entry (kernel + four fields, CH rows) are loaded
+        // before the multiply-adds, so 5*CH 16-byte loads are in flight.
+        constexpr int ROWS = (M + 31) / 32;
+        constexpr int CH = ROWS < 3 ? ROWS : 3;
+        constexpr int NCH = (ROWS + CH - 1) / CH;
+        const int p = threadIdx.x & 7, r0 = threadIdx.x >> 3;
+#pragma unroll 1
+        for (int ch = 0; ch < NCH; ++ch) {
+            float4 a[4][CH];
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+                for (int j = 0; j < CH; ++j) a[f][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+            long long off[CH];
+            bool ok[CH];
+#pragma unroll
+            for (int j = 0; j < CH; ++j) {
+                const int row = r0 + 32 * (ch * CH + j);
+                ok[j] = row < M;
+                off[j] = col0 + (long long)(ok[j] ? row : 0) * my + 2 * p;
+            }
+#pragma unroll 2
+            for (int e = T.e0; e < T.er; ++e) {   // self pair: real kernel
+                const MacEntry E = entries[e];
+                long long j = step - E.lag;
+                if (clamp && j < 0) j = 0;
+                const float2 *S = E.ring + (j % E.depth) * E.slot_elems;
+                const float *G = static_cast<const float *>(E.g);
+                float2 g[CH];
+                float4 s[4][CH];
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj) {
+                    g[jj] = __ldg(reinterpret_cast<const float2 *>(G + off[jj]));
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) s[f][jj] = ldg4(S + f * fstride + off[jj]);
+                }
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        a[f][jj].x = fmaf(g[jj].x, s[f][jj].x, a[f][jj].x);
+                        a[f][jj].y = fmaf(g[jj].x, s[f][jj].y, a[f][jj].y);
+                        a[f][jj].z = fmaf(g[jj].y, s[f][jj].z, a[f][jj].z);
+                        a[f][jj].w = fmaf(g[jj].y, s[f][jj].w, a[f][jj].w);
+                    }
+            }
+#pragma unroll 2
+            for (int e = T.er; e < T.e1; ++e) {   // other sources: complex kernel
+                const MacEntry E = entries[e];
+                long long j = step - E.lag;
+                if (clamp && j < 0) j = 0;
+                const float2 *S = E.ring + (j % E.depth) * E.slot_elems;
+                const float2 *G = static_cast<const float2 *>(E.g);
+                float4 g[CH];
+                float4 s[4][CH];
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj) {
+                    g[jj] = ldg4(G + off[jj]);
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) s[f][jj] = ldg4(S + f * fstride + off[jj]);
+                }
+#pragma unroll
+                for (int jj = 0; jj < CH; ++jj)
+#pragma unroll
+                    for (int f = 0; f < 4; ++f) {
+                        float4 &x = a[f][jj];
+                        const float4 gg = g[jj], ss = s[f][jj];
+                        x.x = fmaf(gg.x, ss.x, fmaf(-gg.y, ss.y, x.x));
+                        x.y = fmaf(gg.x, ss.y, fmaf(gg.y, ss.x, x.y));
+                        x.z = fmaf(gg.z, ss.z, fmaf(-gg.w, ss.w, x.z));
+                        x.w = fmaf(gg.z, ss.w, fmaf(gg.w, ss.z, x.w));
+                    }
+            }
+#pragma unroll
+            for (int jj = 0; jj < CH; ++jj) {
+                if (!ok[jj]) continue;
+                const int row = r0 + 32 * (ch * CH + jj);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    float2 *d = acc + f * fs + row * kTileYPad + 2 * p;
+                    d[0] = make_float2(a[f][jj].x, a[f][jj].y);
+                    d[1] = make_float2(a[f][jj].z, a[f][jj].w);
+                }
+            }
+        }
+    } else {
+        for (int i = threadIdx.x; i < 4 * fs; i += blockDim.x) acc[i] = make_float2(0.0f, 0.0f);
+        __syncthreads();
+        // Each thread owns the (kz, c) cells i = threadIdx.x + k*blockDim.x, the
+        // same for every entry, so no barrier is needed between entries.
+        for (int e = T.e0; e < T.e1; ++e) {
+            const MacEntry E = entries[e];
+            long long j = step - E.lag;
+            if (clamp && j < 0) j = 0;
+            const float2 *S = E.ring + (j % E.depth) * E.slot_elems + col0;
+            const float *Gr = static_cast<const float *>(E.g) + col0;
+            const float2 *Gc = static_cast<const float2 *>(E.g) + col0;
+            for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
+                const int kz = i / kTileY, c = i % kTileY;
+                if (c >= ncols) continue;
+                const long long off = (long long)kz * my + c;
+                const float2 g = E.is_real ? make_float2(__ldg(Gr + off), 0.0f) : __ldg(Gc + off);
+                const int a_ = kz * kTileYPad + c;
+#pragma unroll
+                for (int f = 0; f < 4; ++f)
+                    acc[f * fs + a_] = cadd(acc[f * fs + a_], cmul(g, __ldg(S + f * fstride + off)));
+            }
+        }
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    ColumnFFT cf{az, acc, fs, ncols, 4, T.nz, tw, true, lane, warp, nwarps};
+    run_radix<M>(az.R, cf);
+    __syncthreads();
+    const int nz = T.nz;
+    const long long t2_field = (long long)kx * nz * my;
+    float2 *dst = T.t2 + (long long)kxi * nz * my + ky0;
+    if constexpr (M > 0) {
+        for (int i = threadIdx.x; i < 4 * nz * (kTileY / 2); i += blockDim.x) {
+            const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
+            const int zi = rem / (kTileY / 2), p = rem % (kTileY / 2);
+            const float2 *s = acc + f * fs + zi * kTileYPad + 2 * p;
+            *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * my + 2 * p) =
+                make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
+        }
+    } else {
+        for (int i = threadIdx.x; i < 4 * nz * kTileY; i += blockDim.x) {
+            const int f = i / (nz * kTileY), rem = i % (nz * kTileY);
+            const int zi = rem / kTileY, c = rem % kTileY;
+            if (c < ncols) dst[f * t2_field + (long long)zi * my + c] = acc[f * fs + zi * kTileYPad + c];
+        }
     }
 }
 
 // ---------------------------------------------------------------- inverse plane pass
 
 struct InvPlaneY {
-    const InvTarget &T;
+    Axis a;
+    int kx, ny;
     float2 *P;
     int ps;
     const float2 *tw;
     int lane, warp, nwarps;
 
     template <int RY>
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
-        const Axis &a = T.ay;
         const int G = 32 >> a.logL;
         const int grp = lane >> a.logL, g = lane & (a.L - 1);
         const int per_iter = nwarps * G;
-        for (int base = 0; base < T.kx; base += per_iter) {
+        for (int base = 0; base < kx; base += per_iter) {
             const int kxi = base + warp * G + grp;
-            const bool valid = kxi < T.kx;
+            const bool valid = kxi < kx;
             float2 *row = P + (valid ? kxi : 0) * ps;
             float2 v[RY];
 #pragma unroll
@@ -358,7 +519,7 @@ struct InvPlaneY {
             if (valid) {
 #pragma unroll
                 for (int k1 = 0; k1 < RY; ++k1)
-                    if (k1 + kb < T.ny) row[k1 + kb] = v[k1];
+                    if (k1 + kb < ny) row[k1 + kb] = v[k1];
             }
             __syncwarp();
         }
@@ -366,7 +527,8 @@ struct InvPlaneY {
 };
 
 struct InvPlaneX {
-    const InvTarget &T;
+    Axis a;
+    int nx, ny;
     const float2 *P;
     int ps;
     float *O;       // [ny][nx]
@@ -375,19 +537,18 @@ struct InvPlaneX {
     int lane, warp, nwarps;
 
     template <int RX>
-    __device__ void run()
+    __device__ __forceinline__ void run()
     {
-        const Axis &a = T.ax;
         const int G = 32 >> a.logL;
         const int grp = lane >> a.logL, g = lane & (a.L - 1);
-        const int pairs = (T.ny + 1) >> 1;
+        const int pairs = (ny + 1) >> 1;
         const int half = a.M >> 1;
         const int per_iter = nwarps * G;
         for (int base = 0; base < pairs; base += per_iter) {
             const int p = base + warp * G + grp;
             const bool valid = p < pairs;
             const int ya = valid ? 2 * p : 0, yb = ya + 1;
-            const bool vb = valid && yb < T.ny;
+            const bool vb = valid && yb < ny;
             float2 v[RX];
 #pragma unroll
             for (int n = 0; n < RX; ++n) {
@@ -406,9 +567,9 @@ struct InvPlaneX {
 #pragma unroll
                 for (int k1 = 0; k1 < RX; ++k1) {
                     const int x = k1 + kb;
-                    if (x < T.nx) {
-                        O[ya * T.nx + x] = scale * v[k1].x;
-                        if (vb) O[yb * T.nx + x] = scale * v[k1].y;
+                    if (x < nx) {
+                        O[ya * nx + x] = scale * v[k1].x;
+                        if (vb) O[yb * nx + x] = scale * v[k1].y;
                     }
                 }
             }
@@ -416,48 +577,70 @@ struct InvPlaneX {
     }
 };
 
-__global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restrict__ tgts, int ntgt, OutPtrs out,
-                                                          float inv_c)
+template <int M>
+__global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restrict__ tgts, int t0, int t1,
+                                                          int block_lo, OutPtrs out, float inv_c)
 {
     extern __shared__ float4 smem_f4[];
     float2 *sm = reinterpret_cast<float2 *>(smem_f4);
-    const int b = blockIdx.x;
-    const int t = owner_of(tgts, 0, ntgt, b, &InvTarget::plane0);
+    const int b = blockIdx.x + block_lo;
+    const int t = owner_of(tgts, t0, t1, b, &InvTarget::plane0);
     const InvTarget &T = tgts[t];
+    const Axis ax = axis_of<M>(T.ax), ay = axis_of<M>(T.ay);
+    const int nx = T.nx, ny = T.ny, nz = T.nz;
+    const int kx = ax.M / 2 + 1, my = ay.M;
     const int local = b - T.plane0;
-    const int f = local / T.nz, z = local % T.nz;
-    const int my = T.ay.M;
+    const int f = local / nz, z = local % nz;
     const int ps = my | 1;
 
     float2 *twx = sm;
-    float2 *twy = twx + T.ax.M;
+    float2 *twy = twx + ax.M;
     float2 *P = twy + my;                                   // [kx][ps]
-    float *O = reinterpret_cast<float *>(P + T.kx * ps);    // [ny][nx]
-    load_twiddles(twx, T.tw_x, T.ax.M);
+    float *O = reinterpret_cast<float *>(P + kx * ps);      // [ny][nx]
+    load_twiddles(twx, T.tw_x, ax.M);
     load_twiddles(twy, T.tw_y, my);
-    const float2 *src = T.t2 + ((long long)f * T.kx * T.nz + z) * my;
-    const long long row_stride = (long long)T.nz * my;
-    for (int i = threadIdx.x; i < T.kx * my; i += blockDim.x) {
-        const int kxi = i / my, ky = i % my;
-        P[kxi * ps + ky] = src[kxi * row_stride + ky];
+    const float2 *src = T.t2 + ((long long)f * kx * nz + z) * my;
+    const long long row_stride = (long long)nz * my;
+    if constexpr (M > 0) {
+        for (int i = threadIdx.x; i < kx * (M / 2); i += blockDim.x) {
+            const int kxi = i / (M / 2), q = i % (M / 2);
+            const float4 v = ldg4(src + kxi * row_stride + 2 * q);
+            P[kxi * ps + 2 * q] = make_float2(v.x, v.y);
+            P[kxi * ps + 2 * q + 1] = make_float2(v.z, v.w);
+        }
+    } else {
+        for (int i = threadIdx.x; i < kx * my; i += blockDim.x) {
+            const int kxi = i / my, ky = i % my;
+            P[kxi * ps + ky] = src[kxi * row_stride + ky];
+        }
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    InvPlaneY py{T, P, ps, twy, lane, warp, nwarps};
-    dispatch_radix(T.ay.R, py);
+    InvPlaneY py{ay, kx, ny, P, ps, twy, lane, warp, nwarps};
+    run_radix<M>(ay.R, py);
     __syncthreads();
-    InvPlaneX px{T, P, ps, O, f == 0 ? 1.0f : inv_c, twx, lane, warp, nwarps};
-    dispatch_radix(T.ax.R, px);
+    InvPlaneX px{ax, nx, ny, P, ps, O, f == 0 ? 1.0f : inv_c, twx, lane, warp, nwarps};
+    run_radix<M>(ax.R, px);
     __syncthreads();
-    const long long N = (long long)T.nx * T.ny * T.nz;
-    float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * N) +
-                 (long long)z * T.nx * T.ny;
-    for (int i = threadIdx.x; i < T.nx * T.ny; i += blockDim.x) dst[i] = O[i];
+    const long long N = (long long)nx * ny * nz;
+    float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * N) + (long long)z * nx * ny;
+    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) dst[i] = O[i];
 }
+
+#define RP_FOR_EACH_CLASS(X) X(0) X(32) X(48) X(64) X(96) X(128) X(192)
 
 }  // namespace
 
-// ---------------------------------------------------------------- launchers
+// ---------------------------------------------------------------- host side
+
+int size_class(const Axis &ax, const Axis &ay, const Axis &az)
+{
+    if (ax.M != ay.M || ax.M != az.M) return 0;
+    switch (ax.M) {
+    case 32: case 48: case 64: case 96: case 128: case 192: return ax.M;
+    default: return 0;
+    }
+}
 
 size_t smem_fwd_plane(int ny, const Axis &ax)
 {
@@ -467,7 +650,7 @@ size_t smem_fwd_plane(int ny, const Axis &ax)
     return sizeof(float2) * (2 * kMaxFFT + (size_t)ny * qs + (size_t)(kThreads / 32) * 32 * ax.R);
 }
 
-size_t smem_fwd_column(const Axis &az) { return sizeof(float2) * ((size_t)az.M + (size_t)az.M * kTileYPad); }
+size_t smem_fwd_column(const Axis &az) { return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad); }
 
 size_t smem_mac_inv_column(const Axis &az)
 {
@@ -487,10 +670,18 @@ size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay)
 cudaError_t open_kernel_smem_limits(int max_optin)
 {
     cudaError_t e;
-    if ((e = cudaFuncSetAttribute(k_fwd_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
-    if ((e = cudaFuncSetAttribute(k_fwd_column, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
-    if ((e = cudaFuncSetAttribute(k_mac_inv_column, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
-    if ((e = cudaFuncSetAttribute(k_inv_plane, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) return e;
+#define RP_OPEN(M)                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_fwd_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
+        return e;                                                                                           \
+    if ((e = cudaFuncSetAttribute(k_fwd_column<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
+        return e;                                                                                           \
+    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+                                  max_optin)))                                                              \
+        return e;                                                                                           \
+    if ((e = cudaFuncSetAttribute(k_inv_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
+        return e;
+    RP_FOR_EACH_CLASS(RP_OPEN)
+#undef RP_OPEN
     return cudaSuccess;
 }
 
@@ -505,35 +696,59 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_plane(const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
+#define RP_CASE(M, KERNEL, ...) \
+    case M: KERNEL<M><<<nblocks, kThreads, smem, s>>>(__VA_ARGS__); break;
+
+cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
                              int nblocks, size_t smem, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    k_fwd_plane<<<nblocks, kThreads, smem, s>>>(d_rings, in, r0, r1, block_lo);
+    switch (cls) {
+#define X(M) RP_CASE(M, k_fwd_plane, d_rings, in, r0, r1, block_lo)
+        RP_FOR_EACH_CLASS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fwd_column(const FwdRing *d_rings, int r0, int r1, int block_lo, int nblocks,
+cudaError_t launch_fwd_column(int cls, const FwdRing *d_rings, int r0, int r1, int block_lo, int nblocks,
                               size_t smem, long long step, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    k_fwd_column<<<nblocks, kThreads, smem, s>>>(d_rings, r0, r1, block_lo, step);
+    switch (cls) {
+#define X(M) RP_CASE(M, k_fwd_column, d_rings, r0, r1, block_lo, step)
+        RP_FOR_EACH_CLASS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_mac_inv_column(const InvTarget *d_tgts, int ntgt, const MacEntry *d_entries, int nblocks,
-                                  size_t smem, long long step, int clamp, cudaStream_t s)
+cudaError_t launch_mac_inv_column(int cls, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+                                  const MacEntry *d_entries, int nblocks, size_t smem, long long step, int clamp,
+                                  cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    k_mac_inv_column<<<nblocks, kThreads, smem, s>>>(d_tgts, ntgt, d_entries, step, clamp);
+    switch (cls) {
+#define X(M) RP_CASE(M, k_mac_inv_column, d_tgts, t0, t1, block_lo, d_entries, step, clamp)
+        RP_FOR_EACH_CLASS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 
-cudaError_t launch_inv_plane(const InvTarget *d_tgts, int ntgt, const OutPtrs &out, int nblocks, size_t smem,
-                             float inv_c, cudaStream_t s)
+cudaError_t launch_inv_plane(int cls, const InvTarget *d_tgts, int t0, int t1, int block_lo, const OutPtrs &out,
+                             int nblocks, size_t smem, float inv_c, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
-    k_inv_plane<<<nblocks, kThreads, smem, s>>>(d_tgts, ntgt, out, inv_c);
+    switch (cls) {
+#define X(M) RP_CASE(M, k_inv_plane, d_tgts, t0, t1, block_lo, out, inv_c)
+        RP_FOR_EACH_CLASS(X)
+#undef X
+    default: return cudaErrorInvalidValue;
+    }
     return cudaGetLastError();
 }
 

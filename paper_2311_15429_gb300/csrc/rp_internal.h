@@ -31,8 +31,8 @@ struct FwdRing {
     float2 *t1;              // scratch after the plane pass: [4][kx][nz][my]
     long long slot_elems;    // float2 per slot = 4*kx*mz*my
     const float2 *tw_x, *tw_y, *tw_z;  // twiddles exp(-2 pi i j/M), j < M
-    int plane0;              // first block of this ring in the plane-pass grid
-    int tile0;               // first block of this ring in the column-pass grid
+    int plane0;              // first block of this ring in the plane-pass grid (4 fields x nz planes)
+    int tile0;               // first block of this ring in the column-pass grid (kx x ky tiles)
 };
 
 // One (source, lag) term of a target's spectral sum: G_m (kernel spectrum of
@@ -55,6 +55,7 @@ struct InvTarget {
     int kx;
     int dom;                 // domain id
     int e0, e1;              // its MacEntry range
+    int er;                  // entries e0..er-1 have real kernels (self pair), er..e1-1 complex
     float2 *t2;              // scratch after the column pass: [4][kx][nz][my]
     const float2 *tw_x, *tw_y, *tw_z;
     int tile0;               // first block in the MAC/column grid
@@ -109,26 +110,33 @@ struct OutPtrs {
 };
 
 // ---- launchers (rp_fft_kernels.cu, rp_direct.cu) ----
+//
+// `size_class` selects the kernel instantiation: a cubic padded size M in
+// {32, 48, 64, 96, 128, 192} compiled with constant shapes, or 0 for the
+// general runtime-shaped kernels.  Rings [r0, r1) / targets [t0, t1) of one
+// launch share the class; `block_lo` is the first block of the range.
+
+int size_class(const Axis &ax, const Axis &ay, const Axis &az);
 
 cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, int d1,
                              const int *h_block0, int nblocks, long long step,
                              cudaStream_t s);
-cudaError_t launch_fwd_plane(const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
+cudaError_t launch_fwd_plane(int size_class, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
                              int block_lo, int nblocks, size_t smem, cudaStream_t s);
-cudaError_t launch_fwd_column(const FwdRing *d_rings, int r0, int r1, int block_lo,
+cudaError_t launch_fwd_column(int size_class, const FwdRing *d_rings, int r0, int r1, int block_lo,
                               int nblocks, size_t smem, long long step, cudaStream_t s);
-cudaError_t launch_mac_inv_column(const InvTarget *d_tgts, int ntgt, const MacEntry *d_entries,
-                                  int nblocks, size_t smem, long long step, int clamp,
-                                  cudaStream_t s);
-cudaError_t launch_inv_plane(const InvTarget *d_tgts, int ntgt, const OutPtrs &out,
-                             int nblocks, size_t smem, float inv_c, cudaStream_t s);
+cudaError_t launch_mac_inv_column(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+                                  const MacEntry *d_entries, int nblocks, size_t smem, long long step,
+                                  int clamp, cudaStream_t s);
+cudaError_t launch_inv_plane(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+                             const OutPtrs &out, int nblocks, size_t smem, float inv_c, cudaStream_t s);
 cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair *d_pairs,
                           const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
                           float inv_cdt, float inv_c, cudaStream_t s);
 
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);
-size_t smem_fwd_column(const Axis &az);
+size_t smem_fwd_column(const Axis &az);   // four fields per block
 size_t smem_mac_inv_column(const Axis &az);
 size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay);
 cudaError_t open_kernel_smem_limits(int max_optin);

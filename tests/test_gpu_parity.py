@@ -85,6 +85,22 @@ def test_cfg2_full_size_sampled():
     _score(w.domains, hists, j0, w.c, w.dt, res, nodes=nodes)
 
 
+@pytest.mark.parametrize("n", [24, 32, 64, 96])
+def test_cubic_size_classes(n):
+    """Two n^3 domains 30 bohr apart: padded sizes 48, 64, 128 and 192 (the
+    compiled-shape kernels), checked at corners, centre and seeded nodes."""
+    w = synth.two_domain(n, 0.25, 30.0, f"cube{n}", offset=(3.0, -2.0))
+    T = 16
+    hists = histories(w.sources, 0, T, w.dt)
+    res = run_library(w.domains, w.c, w.dt, hists, 0, [T - 2, T - 1])
+    rng = np.random.default_rng(n)
+    nodes = []
+    for d in w.domains:
+        corners = [i + n * (j + n * k) for i in (0, n - 1) for j in (0, n - 1) for k in (0, n - 1)]
+        nodes.append(np.array(corners + [n // 2 + n * (n // 2 + n * (n // 2))] + list(rng.integers(0, d.N, 40))))
+    _score(w.domains, hists, 0, w.c, w.dt, res, nodes=nodes)
+
+
 def test_ground_state_clamp():
     """Under RP_FLAG_GROUND_STATE_CLAMP, samples before the first push equal it."""
     w = synth.workload("cfg1")
