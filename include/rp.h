@@ -114,6 +114,8 @@ typedef struct {
     long long spectral_bytes; /* of which: spectral history rings */
     long long kernel_bytes;   /* of which: kernel spectra */
     long long points;         /* sum of grid points over all domains */
+    int mac_tma;              /* 1: the spectral MAC of cubic targets is fed by TMA copies */
+    int reserved[7];
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */

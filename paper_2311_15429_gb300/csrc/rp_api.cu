@@ -12,6 +12,9 @@
 #include <thread>
 #include <vector>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
 #include "../../include/rp.h"
 #include "rp_internal.h"
 
@@ -115,6 +118,12 @@ struct rp_ctx {
     DirectTarget *d_dtg = nullptr;
     DirectPair *d_dpairs = nullptr;
     RawRing *d_raw = nullptr;
+    CUtensorMap *d_maps = nullptr;   // TMA descriptors: rings, then (real, complex) kernels per target
+    bool tma = false;                // TMA-fed MAC available for the cubic classes
+    int nmaps = 0;
+    int mac_stages[7] = {};          // pipeline depth per class (index by class_slot)
+    int sm_count = 0;
+    int *d_err = nullptr;            // set by a kernel whose bounded wait ran out
     std::vector<void *> allocs;
     std::vector<float *> in_stage;    // per domain [4][N], for host pushes
     std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
@@ -283,6 +292,93 @@ rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
         if (st) return st;
         kv.second = d;
     }
+    return RP_OK;
+}
+
+}  // namespace
+
+namespace {
+
+int class_slot(int cls)
+{
+    switch (cls) {
+    case 32: return 1; case 48: return 2; case 64: return 3; case 96: return 4; case 128: return 5; case 192: return 6;
+    default: return 0;
+    }
+}
+
+// One 4-D descriptor over float32 data: dims (d0 floats, d1, d2, d3), dense,
+// box (b0 floats, b1 rows, 1, 1).
+bool encode_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, void *base, uint64_t d0, uint64_t d1,
+                uint64_t d2, uint64_t d3, uint32_t b0, uint32_t b1)
+{
+    const cuuint64_t dims[4] = {d0, d1, d2, d3};
+    const cuuint64_t strides[3] = {d0 * 4, d0 * d1 * 4, d0 * d1 * d2 * 4};
+    const cuuint32_t box[4] = {b0, b1, 1, 1};
+    const cuuint32_t estr[4] = {1, 1, 1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Descriptors for every ring and target kernel set of a cubic class; the
+// TMA-fed MAC is used only if all of them encode.
+rp_status build_tensor_maps(rp_ctx *ctx, const std::vector<float *> &treal, const std::vector<float2 *> &tcplx,
+                            int max_optin)
+{
+    const int nrings = (int)ctx->fwd.size();
+    std::vector<CUtensorMap> maps((size_t)nrings + 2 * ctx->inv.size());
+    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
+    ctx->tma = false;
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        ctx->last_error = "cuTensorMapEncodeTiled unavailable: register-blocked MAC in use";
+        return RP_OK;   // no descriptors: the register-blocked MAC serves every class
+    }
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+    bool ok = true;
+    for (int r = 0; r < nrings && ok; ++r) {
+        const FwdRing &R = ctx->fwd[r];
+        const int M = size_class(R.ax, R.ay, R.az);
+        if (!M) continue;
+        const uint64_t tiles = (uint64_t)R.kx * (M / kTileY);
+        ok = encode_map(enc, &maps[r], R.ring, 2 * kTileY, M, tiles, 4ULL * R.depth, 2 * kTileY, M);
+    }
+    for (size_t ti = 0; ti < ctx->inv.size() && ok; ++ti) {
+        const InvTarget &I = ctx->inv[ti];
+        const int M = size_class(I.ax, I.ay, I.az);
+        if (!M) continue;
+        const int nr = I.er - I.e0, nc = I.e1 - I.er;
+        const uint64_t tiles = (uint64_t)I.kx * (M / kTileY);
+        if (nr > 0) ok = ok && encode_map(enc, &maps[nrings + 2 * ti], treal[ti], kTileY, M, tiles, nr, kTileY, M);
+        if (nc > 0)
+            ok = ok && encode_map(enc, &maps[nrings + 2 * ti + 1], tcplx[ti], 2 * kTileY, M, tiles, nc, 2 * kTileY, M);
+    }
+    if (!ok) {
+        ctx->last_error = "a TMA descriptor did not encode: register-blocked MAC in use";
+        return RP_OK;
+    }
+    for (int cls : {32, 48, 64, 96, 128, 192}) {
+        const int n = mac_tma_stages(cls, max_optin);
+        ctx->mac_stages[class_slot(cls)] = n;
+        if (n < 5 && cls > 0) {
+            for (const InvTarget &I : ctx->inv)
+                if (size_class(I.ax, I.ay, I.az) == cls) {
+                    ctx->last_error = "TMA pipeline too shallow: register-blocked MAC in use";
+                    return RP_OK;
+                }
+        }
+    }
+    CUtensorMap *d = nullptr;
+    rp_status st = dev_alloc(ctx, &d, maps.size());
+    if (st) return st;
+    RP_CUDA(ctx, cudaMemcpy(d, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
+    ctx->d_maps = d;
+    ctx->nmaps = (int)maps.size();
+    ctx->tma = true;
     return RP_OK;
 }
 
@@ -462,7 +558,7 @@ rp_status rp_finalize(rp_ctx *ctx)
         R.kx = m[0] / 2 + 1;
         R.src = s;
         R.depth = ring_depth[r];
-        R.slot_elems = 4LL * R.kx * m[2] * m[1];
+        R.slot_elems = 4LL * spec_cells(R.kx, m[1], m[2]);
         R.plane0 = ctx->plane_blocks;
         R.tile0 = ctx->col_blocks;
         ctx->plane_blocks += 4 * R.nz;
@@ -531,7 +627,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     }
     for (const EntryPlan &e : eplan) {
         const auto &m = tm[e.t];
-        const long long cells = (long long)(m[0] / 2 + 1) * m[1] * m[2];
+        const long long cells = spec_cells(m[0] / 2 + 1, m[1], m[2]);
         ctx->kernel_bytes += cells * (long long)(e.real_g ? sizeof(float) : sizeof(float2));
     }
 
@@ -634,19 +730,22 @@ rp_status rp_finalize(rp_ctx *ctx)
         P.depth = ctx->raw[P.src].depth;
     }
 
-    // ---- kernel spectra (FP64 on the host, stored FP32), built in parallel
+    // ---- kernel spectra (FP64 on the host, stored FP32), built in parallel;
+    // each target's real and complex kernels are contiguous (one TMA
+    // descriptor each)
     std::vector<void *> gptr(eplan.size(), nullptr);
-    for (size_t i = 0; i < eplan.size(); ++i) {
-        const auto &m = tm[eplan[i].t];
-        const size_t cells = (size_t)(m[0] / 2 + 1) * m[1] * m[2];
-        if (eplan[i].real_g) {
-            float *p = nullptr;
-            if ((st = dev_alloc(ctx, &p, cells))) return st;
-            gptr[i] = p;
-        } else {
-            float2 *p = nullptr;
-            if ((st = dev_alloc(ctx, &p, cells))) return st;
-            gptr[i] = p;
+    std::vector<int> gidx(eplan.size(), 0);
+    std::vector<float *> treal(ctx->inv.size(), nullptr);
+    std::vector<float2 *> tcplx(ctx->inv.size(), nullptr);
+    for (size_t ti = 0; ti < ctx->inv.size(); ++ti) {
+        const InvTarget &I = ctx->inv[ti];
+        const size_t cells = (size_t)spec_cells(I.kx, I.ay.M, I.az.M);
+        const int nr = I.er - I.e0, nc = I.e1 - I.er;
+        if (nr > 0 && (st = dev_alloc(ctx, &treal[ti], (size_t)nr * cells))) return st;
+        if (nc > 0 && (st = dev_alloc(ctx, &tcplx[ti], (size_t)nc * cells))) return st;
+        for (int e = I.e0; e < I.e1; ++e) {
+            if (e < I.er) { gidx[e] = e - I.e0; gptr[e] = treal[ti] + (size_t)gidx[e] * cells; }
+            else { gidx[e] = e - I.er; gptr[e] = tcplx[ti] + (size_t)gidx[e] * cells; }
         }
     }
     {
@@ -663,7 +762,7 @@ rp_status rp_finalize(rp_ctx *ctx)
                 const EntryPlan &e = eplan[i];
                 const DomainDesc &T = ctx->doms[e.t], &S = ctx->doms[e.s];
                 const int *m = tm[e.t].data();
-                const size_t cells = (size_t)(m[0] / 2 + 1) * m[1] * m[2];
+                const size_t cells = (size_t)spec_cells(m[0] / 2 + 1, m[1], m[2]);
                 if (e.real_g) hr.resize(cells); else hc.resize(cells);
                 build_kernel_spectrum(T.o, T.n, S.o, S.n, S.h, e.t == e.s, e.lag, ctx->cfg.c, ctx->cfg.dt, m,
                                       e.real_g, hr.data(), hc.data());
@@ -679,18 +778,28 @@ rp_status rp_finalize(rp_ctx *ctx)
         for (auto &th : pool) th.join();
         if (err.load()) return cuda_fail(ctx, (cudaError_t)err.load(), "kernel spectrum upload");
     }
-    for (size_t i = 0; i < eplan.size(); ++i) {
-        const EntryPlan &e = eplan[i];
-        const FwdRing &R = ctx->fwd[e.ring];
-        MacEntry E{};
-        E.g = gptr[i];
-        E.ring = R.ring;
-        E.slot_elems = R.slot_elems;
-        E.depth = R.depth;
-        E.lag = e.lag;
-        E.is_real = e.real_g ? 1 : 0;
-        ctx->entries.push_back(E);
+    const int nrings = (int)ctx->fwd.size();
+    for (size_t ti = 0; ti < ctx->inv.size(); ++ti) {
+        const InvTarget &I = ctx->inv[ti];
+        for (int i = I.e0; i < I.e1; ++i) {
+            const EntryPlan &e = eplan[i];
+            const FwdRing &R = ctx->fwd[e.ring];
+            MacEntry E{};
+            E.g = gptr[i];
+            E.ring = R.ring;
+            E.slot_elems = R.slot_elems;
+            E.depth = R.depth;
+            E.lag = e.lag;
+            E.is_real = e.real_g ? 1 : 0;
+            E.smap = e.ring;
+            E.gmap = nrings + 2 * (int)ti + (e.real_g ? 0 : 1);
+            E.gidx = gidx[i];
+            ctx->entries.push_back(E);
+        }
     }
+
+    // ---- TMA descriptors for the cubic classes
+    if ((st = build_tensor_maps(ctx, treal, tcplx, max_optin))) return st;
 
     // ---- device tables and kernel limits
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
@@ -701,6 +810,10 @@ rp_status rp_finalize(rp_ctx *ctx)
     if ((st = upload(ctx, &ctx->d_raw, ctx->raw))) return st;
     RP_CUDA(ctx, open_kernel_smem_limits(max_optin));
     RP_CUDA(ctx, open_direct_smem_limit(max_optin));
+    RP_CUDA(ctx, open_mac_tma_smem_limit(max_optin));
+    if ((st = dev_alloc(ctx, &ctx->d_err, 1))) return st;
+    RP_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+    RP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
     RP_CUDA(ctx, cudaDeviceSynchronize());
     ctx->finalized = true;
     return RP_OK;
@@ -844,8 +957,14 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     const int clamp = ctx->clamp ? 1 : 0;
     const float inv_c = (float)(1.0 / ctx->cfg.c);
     for (const LaunchGroup &g : ctx->inv_groups) {
+        const int ntiles = g.blk1 - g.blk0;
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
-                 return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, g.blk1 - g.blk0,
+                 if (ctx->tma && g.cls > 0)
+                     return launch_mac_tma(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries,
+                                           ctx->d_maps, ctx->nmaps, step, clamp,
+                                           ctx->mac_stages[class_slot(g.cls)],
+                                           std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
+                 return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,
                                               ctx->smem_mac, step, clamp, ctx->stream);
              })))
             return st;
@@ -978,6 +1097,14 @@ rp_status rp_sync(rp_ctx *ctx)
     if (st) return st;
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     RP_CUDA(ctx, cudaGetLastError());
+    if (ctx->d_err) {
+        int flag = 0;
+        RP_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+        if (flag) {
+            RP_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+            return fail(ctx, RP_ERR_TIMEOUT, "a bounded device wait ran out; results of the affected steps are invalid");
+        }
+    }
     return RP_OK;
 }
 
@@ -1000,6 +1127,7 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->spectral_bytes = ctx->spectral_bytes;
     out->kernel_bytes = ctx->kernel_bytes;
     for (const DomainDesc &d : ctx->doms) out->points += d.N;
+    out->mac_tma = ctx->tma ? 1 : 0;
     return RP_OK;
 }
 

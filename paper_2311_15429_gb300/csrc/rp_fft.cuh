@@ -94,6 +94,114 @@ __device__ __forceinline__ void line_fft(float2 (&v)[R], int g, const Axis &a, c
     }
 }
 
+// ---------------------------------------------------------------- compiled-size line FFT
+//
+// The same transform for a length M known at compile time.  The twiddles a
+// lane needs (W_M^{g k} for its R registers, and one multiplier per lane
+// butterfly stage) are read once per kernel into a LaneTw, and the R-point
+// DFTs are written out as butterflies.
+
+__host__ __device__ constexpr int lane_radix(int M)
+{
+    return M % 3 == 0 ? (M / 3 <= 32 ? 3 : 6) : (M <= 32 ? 1 : M / 32);
+}
+__host__ __device__ constexpr int lane_count(int M) { return M / lane_radix(M); }
+__host__ __device__ constexpr int lane_log2(int x) { return x <= 1 ? 0 : 1 + lane_log2(x / 2); }
+
+constexpr float kSin60 = 0.866025403784438647f;   // sqrt(3)/2
+
+template <int M, bool INV>
+struct LaneTw {
+    static constexpr int R = lane_radix(M), L = lane_count(M), LOGL = lane_log2(L);
+    float2 b[R > 1 ? R - 1 : 1];        // W_M^{g k}, k = 1..R-1
+    float2 s[LOGL > 0 ? LOGL : 1];      // stage h = L/2 >> i: w for upper lanes, 1 for lower
+    float sg[LOGL > 0 ? LOGL : 1];      // -1 for upper lanes, +1 for lower
+
+    __device__ __forceinline__ void init(const float2 *tw, int g)
+    {
+#pragma unroll
+        for (int k = 1; k < R; ++k) b[k - 1] = twid<INV>(tw, g * k);
+#pragma unroll
+        for (int i = 0; i < LOGL; ++i) {
+            const int h = (L >> 1) >> i;
+            const bool upper = (g & h) != 0;
+            s[i] = upper ? twid<INV>(tw, (g & (h - 1)) * (M / (2 * h))) : make_float2(1.0f, 0.0f);
+            sg[i] = upper ? -1.0f : 1.0f;
+        }
+    }
+};
+
+// radix 3: W = exp(-+2 pi i/3) = -1/2 -+ i sqrt3/2
+template <bool INV>
+__device__ __forceinline__ void dft3(float2 &a, float2 &b, float2 &c)
+{
+    const float2 s = cadd(b, c), d = csub(b, c);
+    const float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
+    a = cadd(a, s);
+    // forward: X1 = m - i sqrt3/2 d, X2 = m + i sqrt3/2 d (inverse: swapped)
+    const float2 t = make_float2(kSin60 * d.y, -kSin60 * d.x);   // -i sqrt3/2 d
+    if (INV) { b = csub(m, t); c = cadd(m, t); }
+    else { b = cadd(m, t); c = csub(m, t); }
+}
+
+template <int R, bool INV>
+__device__ __forceinline__ void small_dft_c(float2 (&v)[R])
+{
+    if constexpr (R == 2) {
+        const float2 a = v[0], b = v[1];
+        v[0] = cadd(a, b);
+        v[1] = csub(a, b);
+    } else if constexpr (R == 3) {
+        dft3<INV>(v[0], v[1], v[2]);
+    } else if constexpr (R == 4) {
+        float2 a0 = cadd(v[0], v[2]), a1 = csub(v[0], v[2]);
+        float2 b0 = cadd(v[1], v[3]), b1 = csub(v[1], v[3]);
+        float2 jb1 = INV ? make_float2(-b1.y, b1.x) : make_float2(b1.y, -b1.x);
+        v[0] = cadd(a0, b0);
+        v[2] = csub(a0, b0);
+        v[1] = cadd(a1, jb1);
+        v[3] = csub(a1, jb1);
+    } else if constexpr (R == 6) {
+        // n = 3a + b, k = c + 2d: radix 2 over a, twiddle W_6^{bc}, radix 3 over b
+        float2 y0[3], y1[3];
+#pragma unroll
+        for (int b = 0; b < 3; ++b) {
+            y0[b] = cadd(v[b], v[b + 3]);
+            y1[b] = csub(v[b], v[b + 3]);
+        }
+        // W_6^1 = 1/2 -+ i sqrt3/2, W_6^2 = -1/2 -+ i sqrt3/2
+        const float sgn = INV ? 1.0f : -1.0f;
+        y1[1] = cmul(y1[1], make_float2(0.5f, sgn * kSin60));
+        y1[2] = cmul(y1[2], make_float2(-0.5f, sgn * kSin60));
+        dft3<INV>(y0[0], y0[1], y0[2]);
+        dft3<INV>(y1[0], y1[1], y1[2]);
+        v[0] = y0[0]; v[2] = y0[1]; v[4] = y0[2];
+        v[1] = y1[0]; v[3] = y1[1]; v[5] = y1[2];
+    }
+}
+
+// Lane g holds x[n L + g] in v[n]; afterwards X[k + R bitrev_L(g)] in v[k].
+template <int M, bool INV>
+__device__ __forceinline__ void line_fft_c(float2 (&v)[LaneTw<M, INV>::R], const LaneTw<M, INV> &t)
+{
+    constexpr int R = LaneTw<M, INV>::R, L = LaneTw<M, INV>::L, LOGL = LaneTw<M, INV>::LOGL;
+    small_dft_c<R, INV>(v);
+#pragma unroll
+    for (int k = 1; k < R; ++k) v[k] = cmul(v[k], t.b[k - 1]);
+#pragma unroll
+    for (int i = 0; i < LOGL; ++i) {
+        const int h = (L >> 1) >> i;
+#pragma unroll
+        for (int k = 0; k < R; ++k) {
+            float2 p;
+            p.x = __shfl_xor_sync(0xffffffffu, v[k].x, h);
+            p.y = __shfl_xor_sync(0xffffffffu, v[k].y, h);
+            const float2 u = make_float2(fmaf(t.sg[i], v[k].x, p.x), fmaf(t.sg[i], v[k].y, p.y));
+            v[k] = (i == LOGL - 1) ? u : cmul(u, t.s[i]);   // last stage: w = 1
+        }
+    }
+}
+
 // Runtime dispatch on R for a functor templated on R:  f.template run<R>().
 template <class F>
 __device__ __forceinline__ void dispatch_radix(int R, F &f)

@@ -48,6 +48,18 @@ __device__ __forceinline__ void run_radix(int R_rt, F &f)
     else f.template run<radix_R(M)>();
 }
 
+__host__ __device__ constexpr int lane_class(int M) { return M > 0 ? M : 32; }
+
+// One line FFT: the compiled-size transform with precomputed lane twiddles
+// for M > 0, else the table-driven runtime transform.
+template <int M, bool INV, int RR>
+__device__ __forceinline__ void do_line(float2 (&v)[RR], int g, const Axis &a, const float2 *tw,
+                                        const LaneTw<lane_class(M), INV> *lt)
+{
+    if constexpr (M > 0) line_fft_c<M, INV>(v, *lt);
+    else line_fft<RR, INV>(v, g, a, tw);
+}
+
 // index r in [lo, hi) of the last record whose first block (field) is <= b
 template <class T>
 __device__ __forceinline__ int owner_of(const T *arr, int lo, int hi, int b, int T::*field)
@@ -91,7 +103,9 @@ __global__ void __launch_bounds__(kThreads) k_ring_push(const RawRing *__restric
 
 // ---------------------------------------------------------------- forward plane pass
 
+template <int M>
 struct FwdPlaneX {
+    const LaneTw<lane_class(M), false> *lt;
     Axis a;
     int nx, ny, kx;
     const float *plane;
@@ -122,7 +136,7 @@ struct FwdPlaneX {
                 v[n].x = (valid && in_x) ? plane[ya * nx + xi] : 0.0f;
                 v[n].y = (vb && in_x) ? plane[yb * nx + xi] : 0.0f;
             }
-            line_fft<RX, false>(v, g, a, tw);
+            do_line<M, false>(v, g, a, tw, lt);
             const int kb = bitrev_lanes(g, a.logL) * RX;
 #pragma unroll
             for (int k1 = 0; k1 < RX; ++k1) Wg[k1 + kb] = v[k1];
@@ -143,7 +157,9 @@ struct FwdPlaneX {
     }
 };
 
+template <int M>
 struct FwdPlaneY {
+    const LaneTw<lane_class(M), false> *lt;
     Axis a;
     int ny, kx, nz;
     const float2 *Q;
@@ -168,7 +184,7 @@ struct FwdPlaneY {
                 const int yi = n * a.L + g;
                 v[n] = (valid && yi < ny) ? Q[yi * qs + kxi] : make_float2(0.0f, 0.0f);
             }
-            line_fft<RY, false>(v, g, a, tw);
+            do_line<M, false>(v, g, a, tw, lt);
             const int kb = bitrev_lanes(g, a.logL) * RY;
             if (valid) {
                 float2 *row = out + kxi * row_stride;
@@ -208,18 +224,22 @@ __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restric
     const float *plane = src + (long long)z * nx * ny;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
 
-    FwdPlaneX px{ax, nx, ny, kx, plane, Q, qs, W, twx, lane, warp, nwarps};
+    LaneTw<lane_class(M), false> lt;
+    if constexpr (M > 0) lt.init(twx, lane & (ax.L - 1));
+    FwdPlaneX<M> px{&lt, ax, nx, ny, kx, plane, Q, qs, W, twx, lane, warp, nwarps};
     run_radix<M>(ax.R, px);
     __syncthreads();
     float2 *out = R.t1 + ((long long)f * kx * nz + z) * ay.M;
-    FwdPlaneY py{ay, ny, kx, nz, Q, qs, out, twy, lane, warp, nwarps};
+    FwdPlaneY<M> py{&lt, ay, ny, kx, nz, Q, qs, out, twy, lane, warp, nwarps};
     run_radix<M>(ay.R, py);
 }
 
 // ---------------------------------------------------------------- column passes
 
 // Line FFTs down the columns of a shared-memory tile [field][M][kTileYPad].
+template <int M, bool INV>
 struct ColumnFFT {
+    const LaneTw<lane_class(M), INV> *lt;
     Axis a;
     float2 *V;
     int field_stride;  // float2 between fields in V
@@ -227,7 +247,6 @@ struct ColumnFFT {
     int nfields;
     int keep;          // outputs kept: index < keep
     const float2 *tw;
-    bool inverse;
     int lane, warp, nwarps;
 
     template <int RR>
@@ -245,7 +264,7 @@ struct ColumnFFT {
             float2 v[RR];
 #pragma unroll
             for (int n = 0; n < RR; ++n) v[n] = col[(n * a.L + g) * kTileYPad];
-            if (inverse) line_fft<RR, true>(v, g, a, tw); else line_fft<RR, false>(v, g, a, tw);
+            do_line<M, INV>(v, g, a, tw, lt);
             __syncwarp();
             const int kb = bitrev_lanes(g, a.logL) * RR;
             if (valid) {
@@ -304,24 +323,26 @@ __global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restri
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    ColumnFFT cf{az, V, fs, ncols, 4, mz, tw, false, lane, warp, nwarps};
+    LaneTw<lane_class(M), false> lt;
+    if constexpr (M > 0) lt.init(tw, lane & (az.L - 1));
+    ColumnFFT<M, false> cf{&lt, az, V, fs, ncols, 4, mz, tw, lane, warp, nwarps};
     run_radix<M>(az.R, cf);
     __syncthreads();
-    const long long ring_field = (long long)kx * mz * my;
-    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems + (long long)kxi * mz * my + ky0;
+    const long long ring_field = spec_cells(kx, my, mz);
+    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems + (long long)(kxi * ntile + ky0 / kTileY) * mz * kTileY;
     if constexpr (M > 0) {
         for (int i = threadIdx.x; i < 4 * mz * (kTileY / 2); i += blockDim.x) {
             const int f = i / (mz * (kTileY / 2)), rem = i % (mz * (kTileY / 2));
             const int kz = rem / (kTileY / 2), p = rem % (kTileY / 2);
             const float2 *s = V + f * fs + kz * kTileYPad + 2 * p;
-            *reinterpret_cast<float4 *>(dst + f * ring_field + (long long)kz * my + 2 * p) =
+            *reinterpret_cast<float4 *>(dst + f * ring_field + kz * kTileY + 2 * p) =
                 make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
         }
     } else {
         for (int i = threadIdx.x; i < 4 * mz * kTileY; i += blockDim.x) {
             const int f = i / (mz * kTileY), rem = i % (mz * kTileY);
             const int kz = rem / kTileY, c = rem % kTileY;
-            if (c < ncols) dst[f * ring_field + (long long)kz * my + c] = V[f * fs + kz * kTileYPad + c];
+            dst[f * ring_field + kz * kTileY + c] = c < ncols ? V[f * fs + kz * kTileYPad + c] : make_float2(0.f, 0.f);
         }
     }
 }
@@ -346,8 +367,8 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     const int local = b - T.tile0;
     const int kxi = local / ntile, ky0 = (local % ntile) * kTileY;
     const int ncols = min(kTileY, my - ky0);
-    const long long fstride = (long long)kx * mz * my;
-    const long long col0 = (long long)kxi * mz * my + ky0;
+    const long long fstride = spec_cells(kx, my, mz);
+    const long long col0 = (long long)(kxi * ntile + ky0 / kTileY) * mz * kTileY;
     const int fs = mz * kTileYPad;
 
     float2 *tw = sm;
@@ -375,7 +396,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
             for (int j = 0; j < CH; ++j) {
                 const int row = r0 + 32 * (ch * CH + j);
                 ok[j] = row < M;
-                off[j] = col0 + (long long)(ok[j] ? row : 0) * my + 2 * p;
+                off[j] = col0 + (ok[j] ? row : 0) * kTileY + 2 * p;
             }
 #pragma unroll 2
             for (int e = T.e0; e < T.er; ++e) {   // self pair: real kernel
@@ -456,7 +477,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
             for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
                 const int kz = i / kTileY, c = i % kTileY;
                 if (c >= ncols) continue;
-                const long long off = (long long)kz * my + c;
+                const long long off = kz * kTileY + c;
                 const float2 g = E.is_real ? make_float2(__ldg(Gr + off), 0.0f) : __ldg(Gc + off);
                 const int a_ = kz * kTileYPad + c;
 #pragma unroll
@@ -467,7 +488,9 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    ColumnFFT cf{az, acc, fs, ncols, 4, T.nz, tw, true, lane, warp, nwarps};
+    LaneTw<lane_class(M), true> lt;
+    if constexpr (M > 0) lt.init(tw, lane & (az.L - 1));
+    ColumnFFT<M, true> cf{&lt, az, acc, fs, ncols, 4, T.nz, tw, lane, warp, nwarps};
     run_radix<M>(az.R, cf);
     __syncthreads();
     const int nz = T.nz;
@@ -492,7 +515,9 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
 
 // ---------------------------------------------------------------- inverse plane pass
 
+template <int M>
 struct InvPlaneY {
+    const LaneTw<lane_class(M), true> *lt;
     Axis a;
     int kx, ny;
     float2 *P;
@@ -513,7 +538,7 @@ struct InvPlaneY {
             float2 v[RY];
 #pragma unroll
             for (int n = 0; n < RY; ++n) v[n] = row[n * a.L + g];
-            line_fft<RY, true>(v, g, a, tw);
+            do_line<M, true>(v, g, a, tw, lt);
             __syncwarp();
             const int kb = bitrev_lanes(g, a.logL) * RY;
             if (valid) {
@@ -526,7 +551,9 @@ struct InvPlaneY {
     }
 };
 
+template <int M>
 struct InvPlaneX {
+    const LaneTw<lane_class(M), true> *lt;
     Axis a;
     int nx, ny;
     const float2 *P;
@@ -561,7 +588,7 @@ struct InvPlaneX {
                 if (k == 0 || k == half) { A.y = 0.0f; B.y = 0.0f; }
                 v[n] = make_float2(A.x - B.y, A.y + B.x);   // A + iB
             }
-            line_fft<RX, true>(v, g, a, tw);
+            do_line<M, true>(v, g, a, tw, lt);
             const int kb = bitrev_lanes(g, a.logL) * RX;
             if (valid) {
 #pragma unroll
@@ -616,10 +643,12 @@ __global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restr
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    InvPlaneY py{ay, kx, ny, P, ps, twy, lane, warp, nwarps};
+    LaneTw<lane_class(M), true> lt;
+    if constexpr (M > 0) lt.init(twx, lane & (ax.L - 1));
+    InvPlaneY<M> py{&lt, ay, kx, ny, P, ps, twy, lane, warp, nwarps};
     run_radix<M>(ay.R, py);
     __syncthreads();
-    InvPlaneX px{ax, nx, ny, P, ps, O, f == 0 ? 1.0f : inv_c, twx, lane, warp, nwarps};
+    InvPlaneX<M> px{&lt, ax, nx, ny, P, ps, O, f == 0 ? 1.0f : inv_c, twx, lane, warp, nwarps};
     run_radix<M>(ax.R, px);
     __syncthreads();
     const long long N = (long long)nx * ny * nz;

@@ -12,6 +12,15 @@ constexpr int kThreads = 256;  // threads per block of every FFT-path kernel
 constexpr int kTileY = 16;     // ky columns per block of the column passes
 constexpr int kTileYPad = 17;  // shared-memory row stride of a column tile (bank spread)
 
+// Spectra (source rings and lag kernels) are stored tile-major:
+// [kx][ky tile][kz][16 ky], so that the block of one (kx, 16-ky tile) over all
+// kz -- what one column pass reads or writes -- is contiguous in memory.
+// Columns past my in the last tile are padding (zero).
+inline __host__ __device__ long long spec_cells(int kx, int my, int mz)
+{
+    return (long long)kx * ((my + kTileY - 1) / kTileY) * mz * kTileY;
+}
+
 // Radix split of one FFT axis: M = R * L with L a power of two (lanes) and
 // R in {1, 2, 3, 4, 6} (registers per lane).
 struct Axis {
@@ -19,17 +28,17 @@ struct Axis {
 };
 
 // One (source domain, padded size) spectral history ring and its forward
-// transform.  Spectra are stored [4 fields][kx][kz][ky] (ky fastest), kx in
-// [0, mx/2], as complex64.
+// transform.  Spectra are stored [4 fields][spec_cells] complex64 (tile-major,
+// see spec_cells), kx in [0, mx/2].
 struct FwdRing {
     int nx, ny, nz;          // source grid
     Axis ax, ay, az;         // padded sizes
     int kx;                  // mx/2 + 1
     int src;                 // source domain id
     int depth;               // ring depth in steps
-    float2 *ring;            // [depth][4][kx][mz][my]
+    float2 *ring;            // [depth][4][spec_cells]
     float2 *t1;              // scratch after the plane pass: [4][kx][nz][my]
-    long long slot_elems;    // float2 per slot = 4*kx*mz*my
+    long long slot_elems;    // float2 per slot = 4 * spec_cells
     const float2 *tw_x, *tw_y, *tw_z;  // twiddles exp(-2 pi i j/M), j < M
     int plane0;              // first block of this ring in the plane-pass grid (4 fields x nz planes)
     int tile0;               // first block of this ring in the column-pass grid (kx x ky tiles)
@@ -39,13 +48,15 @@ struct FwdRing {
 // Eq. 11 for lag m, scaled by 1/(mx my mz)) times the source spectrum of
 // step l - m.
 struct MacEntry {
-    const void *g;           // [kx][mz][my] float (is_real) or float2
+    const void *g;           // [spec_cells] float (is_real) or float2
     const float2 *ring;      // the source's spectral ring at this target's size
     long long slot_elems;
     int depth;
     int lag;
     int is_real;
-    int pad_;
+    int smap;                // tensor map of the source ring (TMA path)
+    int gmap;                // tensor map of the target's real or complex kernels
+    int gidx;                // index of this kernel within that map
 };
 
 // A target domain evaluated by the FFT path.
@@ -134,6 +145,14 @@ cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair
                           const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
                           float inv_cdt, float inv_c, cudaStream_t s);
 
+// TMA-fed MAC (rp_mac_tma.cu): cubic classes 32..192 only.
+int mac_tma_stages(int M, int smem_optin);
+size_t mac_tma_smem(int M, int nstages);
+cudaError_t open_mac_tma_smem_limit(int max_optin);
+cudaError_t launch_mac_tma(int cls, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
+                           const MacEntry *d_entries, const struct CUtensorMap_st *d_maps, int nmaps,
+                           long long step, int clamp, int nstages, int grid, int *d_err, cudaStream_t s);
+
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);
 size_t smem_fwd_column(const Axis &az);   // four fields per block
@@ -145,8 +164,8 @@ cudaError_t open_kernel_smem_limits(int max_optin);
 
 // The kernel of Eq. 11 for one lag m of the pair (target t, source s),
 // placed for a linear (non-cyclic) convolution on an mx x my x mz grid and
-// transformed with an FP64 FFT; returns the half spectrum [kx][kz][ky],
-// kx <= mx/2, scaled by 1/(mx my mz).  If real_out, only real parts are
+// transformed with an FP64 FFT; returns the half spectrum (kx <= mx/2) in the
+// tile-major layout of spec_cells, scaled by 1/(mx my mz).  If real_out, only real parts are
 // written to out_real (the self pair's kernel is even, so its spectrum is real).
 void build_kernel_spectrum(const double o_t[3], const int n_t[3], const double o_s[3],
                            const int n_s[3], double h, bool self_pair, int lag, double c,

@@ -127,12 +127,16 @@ void build_kernel_spectrum(const double o_t[3], const int n_t[3], const double o
         for (long long xy = 0; xy < (long long)my * mx; ++xy) fz.run(grid.data() + xy, (long long)my * mx);
     }
     const int kx = mx / 2 + 1;
+    const int ntile = (my + kTileY - 1) / kTileY;
+    const long long cells = spec_cells(kx, my, mz);
+    if (real_out) std::memset(out_real, 0, cells * sizeof(float));
+    else std::memset(out_cplx, 0, cells * sizeof(float2));
     const double scale = 1.0 / (double)total;
     for (int k0 = 0; k0 < kx; ++k0)
         for (int kz = 0; kz < mz; ++kz)
             for (int ky = 0; ky < my; ++ky) {
                 const cd v = grid[((long long)kz * my + ky) * mx + k0] * scale;
-                const long long o = ((long long)k0 * mz + kz) * my + ky;
+                const long long o = (((long long)k0 * ntile + ky / kTileY) * mz + kz) * kTileY + ky % kTileY;
                 if (real_out)
                     out_real[o] = (float)v.real();
                 else

@@ -40,7 +40,7 @@ class rp_stats(ctypes.Structure):
                 ("raw_depth", ctypes.c_int), ("spectral_depth", ctypes.c_int),
                 ("step", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
-                ("points", ctypes.c_longlong)]
+                ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
 
 
 class RPError(RuntimeError):
@@ -214,7 +214,7 @@ def rp_sync(ctx):
 def rp_query(ctx) -> dict:
     s = rp_stats()
     _check(load().rp_query(ctx, ctypes.byref(s)), ctx)
-    return {name: getattr(s, name) for name, _ in rp_stats._fields_}
+    return {name: getattr(s, name) for name, _ in rp_stats._fields_ if name != "reserved"}
 
 
 def rp_pair_info(ctx, target: int, source: int) -> dict:

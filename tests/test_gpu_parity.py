@@ -35,6 +35,14 @@ def test_cfg1_full_grids(mode):
     _score(w.domains, hists, 0, w.c, w.dt, res)
 
 
+def test_tma_mac_path_is_active():
+    """Cubic targets (padded 32..192) use the TMA-fed spectral MAC."""
+    w = synth.workload("cfg1")
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        q = lib.query()
+        assert q["mac_tma"] == 1, rp.rp_last_error(lib.ctx)
+
+
 def test_ragged_grids_fft():
     """Non-cubic, unequal grids (FFT sizes 12/16/... with ragged tails)."""
     doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3),
