@@ -228,6 +228,22 @@ rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
  */
 rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 
+/*
+ * rp_gemm_bf16 -- D = A B^T on the tensor cores (tcgen05.mma, bf16 operands,
+ * fp32 accumulation in tensor memory).  A is M x K and B is N x K, bf16,
+ * row-major with K contiguous; D is M x N fp32 row-major.  All three are
+ * device pointers on `device`; `stream` is a cudaStream_t (NULL = legacy).
+ * Shapes: M a multiple of 128, K a multiple of 64, N a multiple of 32 up to
+ * 256.  This is the contraction the low-rank far field applies (skeleton rows
+ * of the lag-stacked kernel of Eq. 11 against a batch of source slices); it
+ * is exposed so that the tensor-core path can be checked on its own.
+ * Synchronous.  RP_ERR_ARG for other shapes or NULL pointers, RP_ERR_CUDA if
+ * the device or the tensor-map encoder is unusable, RP_ERR_TIMEOUT if a
+ * bounded device wait ran out.
+ */
+rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device,
+                       void *stream);
+
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);
 

@@ -1089,6 +1089,46 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
     return RP_OK;
 }
 
+rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device, void *stream)
+{
+    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 256)
+        return RP_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    void *fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    CUtensorMap ma, mb;
+    if (!encode_bf16_rows(fn, &ma, d_A, (uint64_t)M, (uint64_t)K, 128) ||
+        !encode_bf16_rows(fn, &mb, d_B, (uint64_t)N, (uint64_t)K, (uint32_t)N))
+        return RP_ERR_ARG;
+    int optin = 0;
+    int *d_err = nullptr;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
+        cudaMalloc(&d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) {
+        cudaGetLastError();
+        if (d_err) cudaFree(d_err);
+        return RP_ERR_CUDA;
+    }
+    int flag = 0;
+    cudaError_t e = launch_gemm_bf16_tn(ma, mb, d_D, M, N, K, N, optin, d_err, s);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = cudaMemcpy(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    cudaFree(d_err);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    return flag ? RP_ERR_TIMEOUT : RP_OK;
+}
+
 rp_status rp_sync(rp_ctx *ctx)
 {
     if (!ctx) return RP_ERR_ARG;

@@ -1,0 +1,287 @@
+// BF16 tensor-core GEMM on the 5th-generation tensor cores (tcgen05), FP32
+// accumulation in tensor memory:
+//
+//   D[m][n] = sum_k A[m][k] * B[n][k]        A: M x K, B: N x K (bf16, K contiguous)
+//                                            D: M x N fp32 (row stride ldd)
+//
+// This is the contraction of the far-field operator: the skeleton rows of the
+// lag-stacked kernel [G_lo ... G_hi] (A) against a batch of source slices (B).
+//
+// One CTA computes a 128 x BN tile (BN = N <= 256) over the whole K range:
+//   warp 0      TMA producer: 128 x 64 and BN x 64 bf16 boxes, 128-byte swizzle,
+//               into a ring of shared-memory stages ("full" mbarriers carry the
+//               transaction bytes);
+//   warp 1      allocates BN columns of tensor memory; one lane issues
+//               tcgen05.mma (128 x BN x 16, bf16 x bf16 -> fp32) four times per
+//               stage and commits each stage back to its "empty" mbarrier;
+//   warps 2-5   epilogue: wait for the final commit, tcgen05.ld the 128 x BN
+//               fp32 accumulator (each warp its 32 tensor-memory lanes) and
+//               store D.
+// Waits are bounded (clock64); a timeout sets *err and the CTA drains and exits.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rp_internal.h"
+
+namespace rp {
+
+namespace {
+
+constexpr int kBM = 128, kBK = 64;
+constexpr int kGemmThreads = 192;
+constexpr long long kGemmWait = 4000000000LL;
+
+__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void bar_init(uint64_t *b, int n)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
+}
+__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(su32(b)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity)
+{
+    if (bar_try(b, parity)) return true;
+    const long long t0 = clock64();
+    while (!bar_try(b, parity))
+        if (clock64() - t0 > kGemmWait) return false;
+    return true;
+}
+
+__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *b)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+            su32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(su32(b))
+        : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand written by TMA with the
+// 128-byte swizzle (8 rows x 128 B atoms, 1024 B apart).
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
+{
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
+    d |= (uint64_t)1 << 16;                     // leading byte offset (unused with this swizzle)
+    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row group
+    d |= (uint64_t)1 << 46;                     // descriptor version for this architecture
+    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128.
+__host__ __device__ constexpr uint32_t idesc_bf16(int BN)
+{
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc)
+{
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(ad), "l"(bd), "r"(id), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t *b)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
+                 : "memory");
+}
+
+template <int BN>
+__device__ __forceinline__ constexpr int tmem_cols()
+{
+    return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
+}
+
+template <int BN>
+__global__ void __launch_bounds__(kGemmThreads, 1)
+    k_gemm_bf16_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *D,
+                   int K, int ldd, int stages, int *err)
+{
+    constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
+    constexpr int STAGE = A_BYTES + B_BYTES;       // multiple of 1024
+    constexpr int TCOLS = tmem_cols<BN>();
+    extern __shared__ __align__(1024) unsigned char smem[];
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * STAGE);
+    uint64_t *empty = full + stages;
+    uint64_t *done = empty + stages;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(done + 1);
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * kBM;
+    const int ktiles = K / kBK;
+    // the swizzled operand descriptors assume 1024-byte aligned stages
+    if (su32(smem) & 1023u) {
+        if (threadIdx.x == 0) atomicExch(err, 2);
+        return;
+    }
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < stages; ++s) {
+            bar_init(&full[s], 1);
+            bar_init(&empty[s], 1);
+        }
+        bar_init(done, 1);
+        *abort_flag = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                     "r"(TCOLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tmem_slot;
+
+    if (warp == 0 && lane == 0) {
+        // ---------------------------------------------------------------- producer
+        int kt = 0;
+        for (; kt < ktiles; ++kt) {
+            const int s = kt % stages;
+            if (*abort_flag || !bar_wait(&empty[s], ((kt / stages) & 1) ^ 1)) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                break;
+            }
+            unsigned char *st = smem + (size_t)s * STAGE;
+            bar_expect(&full[s], STAGE);
+            tma_2d(st, &mapA, kt * kBK, m0, &full[s]);
+            tma_2d(st + A_BYTES, &mapB, kt * kBK, 0, &full[s]);
+        }
+        // every copy issued has landed before the CTA may exit
+        for (int r = kt > stages ? kt - stages : 0; r < kt; ++r)
+            if (!bar_wait(&full[r % stages], (r / stages) & 1)) atomicExch(err, 1);
+    } else if (warp == 1 && lane == 0) {
+        // ---------------------------------------------------------------- MMA issue
+        constexpr uint32_t ID = idesc_bf16(BN);
+        for (int kt = 0; kt < ktiles; ++kt) {
+            const int s = kt % stages;
+            if (*abort_flag || !bar_wait(&full[s], (kt / stages) & 1)) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                break;
+            }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a = su32(smem + (size_t)s * STAGE), b = a + A_BYTES;
+#pragma unroll
+            for (int kk = 0; kk < kBK / 16; ++kk)   // 16 bf16 = 32 bytes along K per instruction
+                mma_bf16(tmem, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), ID, (kt | kk) ? 1u : 0u);
+            mma_commit(&empty[s]);                  // the stage is free once these complete
+        }
+        mma_commit(done);                           // all issued MMAs complete
+    } else if (warp >= 2) {
+        // ---------------------------------------------------------------- epilogue
+        const bool ok = bar_wait(done, 0);
+        if (!ok) atomicExch(err, 1);
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int quarter = warp & 3;               // tensor-memory lanes 32*quarter .. +31
+        const int row = m0 + 32 * quarter + lane;
+        if (ok && !*abort_flag) {
+#pragma unroll 1
+            for (int c = 0; c < BN; c += 32) {
+                uint32_t r[32];
+                const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c;
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float4 *out = reinterpret_cast<float4 *>(D + (size_t)row * ldd + c);
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+                    out[j] = make_float4(__uint_as_float(r[4 * j]), __uint_as_float(r[4 * j + 1]),
+                                         __uint_as_float(r[4 * j + 2]), __uint_as_float(r[4 * j + 3]));
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 1) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS) : "memory");
+    }
+}
+
+template <int BN>
+size_t gemm_smem(int stages)
+{
+    return (size_t)stages * (kBM * kBK * 2 + BN * kBK * 2) + 8 * (2 * (size_t)stages + 1) + 16;
+}
+
+}  // namespace
+
+// 2-D bf16 descriptor over a row-major rows x cols matrix, box (64 cols, box_rows), 128-byte swizzle.
+bool encode_bf16_rows(void *encode_fn, CUtensorMap *map, const void *base, uint64_t rows, uint64_t cols,
+                      uint32_t box_rows)
+{
+    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(encode_fn);
+    const cuuint64_t dims[2] = {cols, rows};
+    const cuuint64_t strides[1] = {cols * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)kBK, box_rows};
+    const cuuint32_t estr[2] = {1, 1};
+    return enc(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// D (M x N fp32, row stride ldd) = A (M x K bf16) * B (N x K bf16)^T, with
+// M % 128 == 0, K % 64 == 0, N a multiple of 32 up to 256.
+cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB, float *D, int M, int N, int K,
+                                int ldd, int smem_optin, int *d_err, cudaStream_t s)
+{
+    if (M % kBM || K % kBK || N % 32 || N <= 0 || N > 256) return cudaErrorInvalidValue;
+    const int grid = M / kBM;
+#define RP_GEMM_CASE(BN)                                                                             \
+    case BN: {                                                                                       \
+        int stages = (int)((smem_optin - 64) / (kBM * kBK * 2 + BN * kBK * 2));                      \
+        if (stages > 8) stages = 8;                                                                  \
+        if (stages < 2) return cudaErrorInvalidValue;                                                \
+        const size_t smem = gemm_smem<BN>(stages);                                                   \
+        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                             (int)smem);                                             \
+        if (e) return e;                                                                             \
+        k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(mapA, mapB, D, K, ldd, stages, d_err);   \
+        return cudaGetLastError();                                                                   \
+    }
+    switch (N) {
+        RP_GEMM_CASE(32)
+        RP_GEMM_CASE(64)
+        RP_GEMM_CASE(96)
+        RP_GEMM_CASE(128)
+        RP_GEMM_CASE(160)
+        RP_GEMM_CASE(192)
+        RP_GEMM_CASE(224)
+        RP_GEMM_CASE(256)
+    default: return cudaErrorInvalidValue;
+    }
+#undef RP_GEMM_CASE
+}
+
+}  // namespace rp

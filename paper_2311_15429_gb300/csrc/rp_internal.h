@@ -153,6 +153,12 @@ cudaError_t launch_mac_tma(int cls, const InvTarget *d_tgts, int t0, int t1, int
                            const MacEntry *d_entries, const struct CUtensorMap_st *d_maps, int nmaps,
                            long long step, int clamp, int nstages, int grid, int *d_err, cudaStream_t s);
 
+// tcgen05 bf16 GEMM (rp_gemm_tc.cu): D (M x N fp32) = A (M x K) * B (N x K)^T
+bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *base, uint64_t rows,
+                      uint64_t cols, uint32_t box_rows);
+cudaError_t launch_gemm_bf16_tn(const struct CUtensorMap_st &mapA, const struct CUtensorMap_st &mapB, float *D,
+                                int M, int N, int K, int ldd, int smem_optin, int *d_err, cudaStream_t s);
+
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);
 size_t smem_fwd_column(const Axis &az);   // four fields per block

@@ -66,6 +66,7 @@ SIGNATURES = {
     "rp_evaluate": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
+    "rp_gemm_bf16": (_I, [_V, _V, _V, _I, _I, _I, _I, _V]),
     "rp_sync": (_I, [_V]),
     "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
@@ -205,6 +206,20 @@ def rp_evaluate_host_noalloc(ctx, phis: Sequence, As: Sequence):
     pp, _a = _ptr_array(phis)
     pa, _b = _ptr_array(As)
     _check(load().rp_evaluate_host_noalloc(ctx, pp, pa), ctx)
+
+
+def rp_gemm_bf16(A, B, D, device: int = 0, stream=None):
+    """D = A @ B.T on the tensor cores: A (M x K) and B (N x K) bfloat16 CUDA
+    tensors, D (M x N) float32."""
+    M, K = A.shape
+    N = B.shape[0]
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    for t in (A, B, D):
+        if not t.is_contiguous():
+            raise ValueError("operands must be contiguous")
+    _check(load().rp_gemm_bf16(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, device, stream))
 
 
 def rp_sync(ctx):
