@@ -64,7 +64,18 @@ typedef enum {
     RP_MODE_FFT = 0,
     /* Every pair by the direct retarded sum in FP32 with compensated
      * accumulation (the plain path). */
-    RP_MODE_DIRECT = 1
+    RP_MODE_DIRECT = 1,
+    /* As RP_MODE_FFT, but pairs at least far_distance apart go through an
+     * interpolative low-rank factorisation of their lag-stacked operator
+     * [G_lo ... G_hi] (Eq. 11): the target's potential is represented by its
+     * values at far_points^3 Chebyshev nodes of the target box and
+     * interpolated (tensor-product Lagrange) to the grid; the node values are
+     * contracted with the source history as time-batched bf16 tensor-core
+     * GEMMs with fp32 accumulation.  Its accuracy rests on the far potential
+     * being smooth across the target box (sources slow on the light-crossing
+     * time of a box); it is not an extension in the paper (its Summary only
+     * mentions a multipole approximation as a further speed-up). */
+    RP_MODE_LOWRANK = 2
 } rp_mode;
 
 /* Samples before the first push equal the first push: S(t <= 0) = S(0), the
@@ -85,13 +96,17 @@ typedef struct {
     int history_depth;   /* minimum history ring depth in steps (0: what the geometry needs) */
     int mode;            /* rp_mode */
     unsigned int flags;  /* RP_FLAG_* */
-    int reserved[9];     /* set to zero */
+    int far_points;      /* RP_MODE_LOWRANK: interpolation nodes per axis, 2..8 (0: 4) */
+    double far_distance; /* RP_MODE_LOWRANK: smallest box distance of a far pair (bohr, > 0) */
+    int far_batch;       /* RP_MODE_LOWRANK: source slices per GEMM, multiple of 8 in 8..64 (0: 32);
+                          * a far pair also needs lag_lo >= far_batch - 1 */
+    int reserved[5];     /* set to zero */
 } rp_config;
 
 typedef struct rp_ctx rp_ctx;
 
 /* Pair kinds reported by rp_pair_info. */
-typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1 } rp_pair_kind;
+typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1, RP_PAIR_LOWRANK = 2 } rp_pair_kind;
 
 typedef struct {
     int kind;          /* rp_pair_kind */
@@ -115,7 +130,9 @@ typedef struct {
     long long kernel_bytes;   /* of which: kernel spectra */
     long long points;         /* sum of grid points over all domains */
     int mac_tma;              /* 1: the spectral MAC of cubic targets is fed by TMA copies */
-    int reserved[7];
+    int npairs_far;           /* pairs on the low-rank far path */
+    long long far_bytes;      /* device memory of the far path (factors, batches, rings) */
+    int reserved[4];
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -126,7 +143,11 @@ typedef enum {
     RP_K_MAC_INV_COLUMN = 3,/* spectral multiply-accumulate over (source, lag) + inverse FFT along z */
     RP_K_INV_PLANE = 4,     /* inverse FFT along y and x, crop, scale, write phi/A */
     RP_K_DIRECT = 5,        /* direct retarded sum */
-    RP_K_COUNT = 6
+    RP_K_FAR_CONVERT = 6,   /* far path: slice to bf16 batch matrix */
+    RP_K_FAR_GEMM = 7,      /* far path: tcgen05 GEMM of factors and batch */
+    RP_K_FAR_SCATTER = 8,   /* far path: node values into coefficient rings */
+    RP_K_FAR_INTERP = 9,    /* far path: coefficients interpolated onto the target grid */
+    RP_K_COUNT = 10
 } rp_kernel_kind;
 
 /*

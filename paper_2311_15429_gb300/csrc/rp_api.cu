@@ -124,6 +124,20 @@ struct rp_ctx {
     int mac_stages[7] = {};          // pipeline depth per class (index by class_slot)
     int sm_count = 0;
     int *d_err = nullptr;            // set by a kernel whose bounded wait ran out
+    // far pairs (low-rank path)
+    std::vector<FarSource> far_src;
+    std::vector<FarTarget> far_tgt;
+    std::vector<FarLink> far_links;
+    std::vector<int> far_link0, far_link1, far_link_threads;   // per far source
+    std::vector<float *> far_Z;
+    std::vector<int> far_rows;                                  // padded W rows per far source
+    std::vector<CUtensorMap> far_mapW, far_mapX;
+    std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
+    FarSource *d_far_src = nullptr;
+    FarTarget *d_far_tgt = nullptr;
+    FarLink *d_far_links = nullptr;
+    int far_planes = 0, far_max_r = 0, npairs_far = 0;
+    long long far_bytes = 0, far_max_n = 0, far_zeroed_step = -1;
     std::vector<void *> allocs;
     std::vector<float *> in_stage;    // per domain [4][N], for host pushes
     std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
@@ -384,6 +398,153 @@ rp_status build_tensor_maps(rp_ctx *ctx, const std::vector<float *> &treal, cons
 
 }  // namespace
 
+namespace {
+
+// Chebyshev nodes (first kind) of [a, b], or the grid nodes when the axis has
+// no more than p of them; and the Lagrange weights of every grid node.
+void far_axis(double o, double h, int n, int p, std::vector<double> &nodes, std::vector<float> &L)
+{
+    const int q = std::min(n, p);
+    nodes.resize(q);
+    if (n <= p) {
+        for (int a = 0; a < q; ++a) nodes[a] = o + h * a;
+    } else {
+        const double lo = o, hi = o + h * (n - 1);
+        for (int a = 0; a < q; ++a)
+            nodes[a] = 0.5 * (lo + hi) - 0.5 * (hi - lo) * std::cos((2.0 * a + 1.0) * M_PI / (2.0 * q));
+    }
+    L.assign((size_t)n * q, 0.0f);
+    for (int i = 0; i < n; ++i) {
+        const double x = o + h * i;
+        for (int a = 0; a < q; ++a) {
+            double w = 1.0;
+            for (int b = 0; b < q; ++b)
+                if (b != a) w *= (x - nodes[b]) / (nodes[a] - nodes[b]);
+            L[(size_t)i * q + a] = (float)w;
+        }
+    }
+}
+
+// Factors, batch buffers, coefficient rings and descriptors of the far pairs.
+rp_status build_far(rp_ctx *ctx, int max_optin)
+{
+    const int nd = (int)ctx->doms.size();
+    const int batch = ctx->cfg.far_batch, P = ctx->cfg.far_points;
+    const double inv_cdt = 1.0 / (ctx->cfg.c * ctx->cfg.dt);
+    rp_status st;
+    ctx->far_src_of_dom.assign(nd, -1);
+    // targets
+    std::vector<int> tidx(nd, -1);
+    std::vector<std::array<std::vector<double>, 3>> tnodes(nd);
+    for (int t = 0; t < nd; ++t) {
+        int hi = -1;
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind == RP_PAIR_LOWRANK) hi = std::max(hi, p.lag_hi);
+        }
+        if (hi < 0) continue;
+        const DomainDesc &T = ctx->doms[t];
+        FarTarget F{};
+        F.dom = t;
+        F.nx = T.n[0]; F.ny = T.n[1]; F.nz = T.n[2];
+        std::vector<float> L[3];
+        for (int a = 0; a < 3; ++a) far_axis(T.o[a], T.h, T.n[a], P, tnodes[t][a], L[a]);
+        F.px = (int)tnodes[t][0].size(); F.py = (int)tnodes[t][1].size(); F.pz = (int)tnodes[t][2].size();
+        F.r = F.px * F.py * F.pz;
+        F.lag_hi_max = hi;
+        F.depth = hi + batch + 1;
+        float *Lx, *Ly, *Lz;
+        if ((st = upload(ctx, &Lx, L[0])) || (st = upload(ctx, &Ly, L[1])) || (st = upload(ctx, &Lz, L[2]))) return st;
+        F.Lx = Lx; F.Ly = Ly; F.Lz = Lz;
+        if ((st = dev_alloc(ctx, &F.cring, (size_t)F.depth * F.r * 4))) return st;
+        RP_CUDA(ctx, cudaMemset(F.cring, 0, (size_t)F.depth * F.r * 4 * sizeof(float)));
+        ctx->far_bytes += (long long)F.depth * F.r * 16 + 4LL * (T.n[0] * F.px + T.n[1] * F.py + T.n[2] * F.pz);
+        ctx->far_planes += F.nz;
+        ctx->far_max_r = std::max(ctx->far_max_r, F.r);
+        tidx[t] = (int)ctx->far_tgt.size();
+        ctx->far_tgt.push_back(F);
+    }
+    if (ctx->far_tgt.empty()) return RP_OK;
+    void *enc = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !enc) {
+        cudaGetLastError();
+        return fail(ctx, RP_ERR_UNSUPPORTED, "far path needs cuTensorMapEncodeTiled");
+    }
+    // sources
+    for (int s = 0; s < nd; ++s) {
+        std::vector<FarRow> rows;
+        std::vector<FarLink> links;
+        for (int t = 0; t < nd; ++t) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_LOWRANK) continue;
+            const FarTarget &F = ctx->far_tgt[tidx[t]];
+            FarLink Lk{};
+            Lk.row0 = (int)rows.size();
+            Lk.r = F.r;
+            Lk.nlag = p.lag_hi - p.lag_lo + 1;
+            Lk.lag_lo = p.lag_lo;
+            Lk.cring = F.cring;
+            Lk.depth = F.depth;
+            links.push_back(Lk);
+            const auto &nx = tnodes[t];
+            const DomainDesc &S = ctx->doms[s];
+            for (int m = p.lag_lo; m <= p.lag_hi; ++m)
+                for (int c = 0; c < F.pz; ++c)
+                    for (int b = 0; b < F.py; ++b)
+                        for (int a = 0; a < F.px; ++a)
+                            rows.push_back({(float)(nx[0][a] - S.o[0]), (float)(nx[1][b] - S.o[1]),
+                                            (float)(nx[2][c] - S.o[2]), m});
+        }
+        if (links.empty()) continue;
+        ctx->npairs_far += (int)links.size();
+        const int nrows = (int)((rows.size() + 127) / 128 * 128);
+        while ((int)rows.size() < nrows) rows.push_back({0.0f, 0.0f, 0.0f, -1});
+        const DomainDesc &S = ctx->doms[s];
+        FarSource F{};
+        F.dom = s;
+        F.n = S.N;
+        F.ks = (int)((S.N + 63) / 64 * 64);
+        FarRow *d_rows = nullptr;
+        __nv_bfloat16 *W = nullptr;
+        float *Z = nullptr;
+        if ((st = upload(ctx, &d_rows, rows))) return st;
+        if ((st = dev_alloc(ctx, &W, (size_t)nrows * F.ks))) return st;
+        if ((st = dev_alloc(ctx, &F.X, (size_t)4 * batch * F.ks))) return st;
+        if ((st = dev_alloc(ctx, &Z, (size_t)nrows * 4 * batch))) return st;
+        RP_CUDA(ctx, cudaMemset(F.X, 0, (size_t)4 * batch * F.ks * sizeof(__nv_bfloat16)));
+        RP_CUDA(ctx, launch_far_build_w(d_rows, nrows, S.n, S.h, inv_cdt, F.ks, W, ctx->stream));
+        ctx->far_bytes += (long long)nrows * F.ks * 2 + 8LL * batch * F.ks + 16LL * nrows * batch;
+        CUtensorMap mw, mx;
+        if (!encode_bf16_rows(enc, &mw, W, (uint64_t)nrows, (uint64_t)F.ks, 128) ||
+            !encode_bf16_rows(enc, &mx, F.X, (uint64_t)4 * batch, (uint64_t)F.ks, (uint32_t)(4 * batch)))
+            return fail(ctx, RP_ERR_UNSUPPORTED, "far path: a tensor map did not encode");
+        ctx->far_mapW.push_back(mw);
+        ctx->far_mapX.push_back(mx);
+        ctx->far_Z.push_back(Z);
+        ctx->far_rows.push_back(nrows);
+        ctx->far_link0.push_back((int)ctx->far_links.size());
+        int thr = 0;
+        for (const FarLink &Lk : links) {
+            thr += Lk.r * 4 * (Lk.nlag + batch - 1);
+            ctx->far_links.push_back(Lk);
+        }
+        ctx->far_link1.push_back((int)ctx->far_links.size());
+        ctx->far_link_threads.push_back(thr);
+        ctx->far_max_n = std::max(ctx->far_max_n, S.N);
+        ctx->far_src_of_dom[s] = (int)ctx->far_src.size();
+        ctx->far_src.push_back(F);
+    }
+    (void)max_optin;
+    if ((st = upload(ctx, &ctx->d_far_src, ctx->far_src))) return st;
+    if ((st = upload(ctx, &ctx->d_far_tgt, ctx->far_tgt))) return st;
+    if ((st = upload(ctx, &ctx->d_far_links, ctx->far_links))) return st;
+    return RP_OK;
+}
+
+}  // namespace
+
 // =========================================================================== C-ABI
 
 extern "C" {
@@ -407,8 +568,9 @@ const char *rp_last_error(rp_ctx *ctx) { return ctx ? ctx->last_error.c_str() : 
 
 const char *rp_kernel_name(int kind)
 {
-    static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column",
-                                            "mac_inv_column", "inv_plane", "direct"};
+    static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column", "mac_inv_column",
+                                            "inv_plane", "direct", "far_convert", "far_gemm",
+                                            "far_scatter", "far_interp"};
     return (kind >= 0 && kind < RP_K_COUNT) ? names[kind] : nullptr;
 }
 
@@ -417,9 +579,16 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     if (!cfg || !out) return RP_ERR_ARG;
     *out = nullptr;
     if (!(cfg->c > 0.0) || !(cfg->dt > 0.0) || cfg->history_depth < 0) return RP_ERR_ARG;
-    if (cfg->mode != RP_MODE_FFT && cfg->mode != RP_MODE_DIRECT) return RP_ERR_ARG;
+    if (cfg->mode != RP_MODE_FFT && cfg->mode != RP_MODE_DIRECT && cfg->mode != RP_MODE_LOWRANK) return RP_ERR_ARG;
+    if (cfg->mode == RP_MODE_LOWRANK) {
+        if (!(cfg->far_distance > 0.0)) return RP_ERR_ARG;
+        if (cfg->far_points != 0 && (cfg->far_points < 2 || cfg->far_points > kMaxFarPts)) return RP_ERR_ARG;
+        if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
+    }
     rp_ctx *ctx = new rp_ctx();
     ctx->cfg = *cfg;
+    if (ctx->cfg.far_points == 0) ctx->cfg.far_points = 4;
+    if (ctx->cfg.far_batch == 0) ctx->cfg.far_batch = 32;
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0;
     ctx->profile = (cfg->flags & RP_FLAG_PROFILE) != 0 && !ctx->plan_only;
@@ -466,7 +635,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     const int nd = (int)ctx->doms.size();
     if (nd == 0) return fail(ctx, RP_ERR_STATE, "no domains");
     const double cdt = ctx->cfg.c * ctx->cfg.dt;
-    const bool fft_mode = ctx->cfg.mode == RP_MODE_FFT;
+    const bool fft_mode = ctx->cfg.mode == RP_MODE_FFT || ctx->cfg.mode == RP_MODE_LOWRANK;
 
     // ---- pairs: lag windows and kinds
     ctx->pairs.assign((size_t)nd * nd, PairPlan{});
@@ -493,6 +662,9 @@ rp_status rp_finalize(rp_ctx *ctx)
                     for (int a = 0; a < 3; ++a) p.m[a] = m[a];
                 }
             }
+            if (ctx->cfg.mode == RP_MODE_LOWRANK && t != s && p.rmin >= ctx->cfg.far_distance &&
+                p.lag_lo >= ctx->cfg.far_batch - 1)
+                p.kind = RP_PAIR_LOWRANK;
             if (t == s && fft_mode && p.kind != RP_PAIR_FFT)
                 return fail(ctx, RP_ERR_UNSUPPORTED, "domain " + std::to_string(t) +
                                                          " exceeds 96 nodes per axis (FFT self term)");
@@ -684,6 +856,13 @@ rp_status rp_finalize(rp_ctx *ctx)
         ctx->raw_block0[d + 1] = ctx->raw_block0[d] + nb;
     }
     ctx->pushed.assign(nd, 0);
+    {
+        int nfar = 0;
+        for (const PairPlan &p : ctx->pairs) nfar += p.kind == RP_PAIR_LOWRANK;
+        if (nfar && ctx->clamp)
+            return fail(ctx, RP_ERR_UNSUPPORTED, "the far path needs a pushed history (no RP_FLAG_GROUND_STATE_CLAMP)");
+        if (ctx->plan_only) ctx->npairs_far = nfar;
+    }
 
     if (ctx->plan_only) {
         long long raw_bytes = 0;
@@ -801,6 +980,9 @@ rp_status rp_finalize(rp_ctx *ctx)
     // ---- TMA descriptors for the cubic classes
     if ((st = build_tensor_maps(ctx, treal, tcplx, max_optin))) return st;
 
+    // ---- far pairs
+    if ((st = build_far(ctx, max_optin))) return st;
+
     // ---- device tables and kernel limits
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
     if ((st = upload(ctx, &ctx->d_inv, ctx->inv))) return st;
@@ -889,6 +1071,52 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
              })))
             return st;
     }
+    // far path: stage the slices of far sources; every far_batch steps run
+    // the factor GEMM of each source and add its node values to the rings
+    if (!ctx->far_src.empty()) {
+        int f0 = -1, f1 = -1;
+        for (int d = d0; d < d1; ++d) {
+            const int fi = ctx->far_src_of_dom[d];
+            if (fi < 0) continue;
+            if (f0 < 0) f0 = fi;
+            f1 = fi + 1;
+        }
+        if (f0 >= 0) {
+            const int batch = ctx->cfg.far_batch;
+            const int slot = (int)(step % batch);
+            if ((st = timed_launch(ctx, RP_K_FAR_CONVERT, "far slice staging", [&] {
+                     return launch_far_convert(ctx->d_far_src + f0, f1 - f0, in, slot, ctx->far_max_n, ctx->stream);
+                 })))
+                return st;
+            if (slot == batch - 1) {
+                if (ctx->far_zeroed_step != step) {
+                    if ((st = timed_launch(ctx, RP_K_FAR_SCATTER, "far ring zero", [&] {
+                             return launch_far_zero(ctx->d_far_tgt, (int)ctx->far_tgt.size(), step, batch,
+                                                    ctx->far_max_r, ctx->stream);
+                         })))
+                        return st;
+                    ctx->far_zeroed_step = step;
+                }
+                int optin = 0;
+                RP_CUDA(ctx, cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+                for (int fi = f0; fi < f1; ++fi) {
+                    if ((st = timed_launch(ctx, RP_K_FAR_GEMM, "far GEMM", [&] {
+                             return launch_gemm_bf16_tn(ctx->far_mapW[fi], ctx->far_mapX[fi], ctx->far_Z[fi],
+                                                        ctx->far_rows[fi], 4 * batch, ctx->far_src[fi].ks, 4 * batch,
+                                                        optin, ctx->d_err, ctx->stream);
+                         })))
+                        return st;
+                    if ((st = timed_launch(ctx, RP_K_FAR_SCATTER, "far scatter", [&] {
+                             return launch_far_scatter(ctx->d_far_links + ctx->far_link0[fi],
+                                                       ctx->far_link1[fi] - ctx->far_link0[fi],
+                                                       ctx->far_link_threads[fi], ctx->far_Z[fi], 4 * batch,
+                                                       step - batch + 1, batch, ctx->stream);
+                         })))
+                        return st;
+                }
+            }
+        }
+    }
     return RP_OK;
 }
 
@@ -973,6 +1201,13 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
                  return launch_inv_plane(g.cls, ctx->d_inv, g.i0, g.i1, g.blk2_0, out, g.blk2_1 - g.blk2_0,
                                          ctx->smem_inv, inv_c, ctx->stream);
+             })))
+            return st;
+    }
+    if (!ctx->far_tgt.empty()) {
+        if ((st = timed_launch(ctx, RP_K_FAR_INTERP, "far interpolation", [&] {
+                 return launch_far_interp(ctx->d_far_tgt, (int)ctx->far_tgt.size(), ctx->far_planes, out, step,
+                                          inv_c, ctx->stream);
              })))
             return st;
     }
@@ -1155,10 +1390,6 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     std::memset(out, 0, sizeof(*out));
     const int nd = (int)ctx->doms.size();
     out->ndomains = nd;
-    for (const PairPlan &p : ctx->pairs) {
-        if (p.kind == RP_PAIR_FFT) out->npairs_fft++;
-        else out->npairs_direct++;
-    }
     out->max_lag = ctx->max_lag;
     out->raw_depth = ctx->raw_depth;
     out->spectral_depth = ctx->spec_depth;
@@ -1168,6 +1399,14 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->kernel_bytes = ctx->kernel_bytes;
     for (const DomainDesc &d : ctx->doms) out->points += d.N;
     out->mac_tma = ctx->tma ? 1 : 0;
+    out->npairs_far = ctx->npairs_far;
+    out->far_bytes = ctx->far_bytes;
+    out->npairs_direct = 0;
+    out->npairs_fft = 0;
+    for (const PairPlan &p : ctx->pairs) {
+        if (p.kind == RP_PAIR_FFT) out->npairs_fft++;
+        else if (p.kind == RP_PAIR_DIRECT) out->npairs_direct++;
+    }
     return RP_OK;
 }
 
@@ -1236,6 +1475,10 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
         if (r.ring && (st = fn((void *)r.ring, (size_t)r.depth * 4 * r.n * sizeof(float)))) return st;
     for (const FwdRing &R : ctx->fwd)
         if ((st = fn((void *)R.ring, (size_t)R.depth * R.slot_elems * sizeof(float2)))) return st;
+    for (const FarSource &F : ctx->far_src)
+        if ((st = fn((void *)F.X, (size_t)4 * ctx->cfg.far_batch * F.ks * sizeof(__nv_bfloat16)))) return st;
+    for (const FarTarget &F : ctx->far_tgt)
+        if ((st = fn((void *)F.cring, (size_t)F.depth * F.r * 4 * sizeof(float)))) return st;
     return RP_OK;
 }
 

@@ -1,6 +1,7 @@
 // Internal structures shared by the host planner (rp_api.cu) and the kernels.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -110,6 +111,47 @@ struct RawRing {
     int pad_;
 };
 
+// ---- far pairs (rp_far.cu): interpolative low-rank factors
+
+constexpr int kMaxFarPts = 8;   // interpolation nodes per axis of a target box
+
+// One row of a source's factor matrix W: the node of a far target, relative
+// to the source's origin, and a lag (lag < 0: padding row).
+struct FarRow {
+    float x, y, z;
+    int lag;
+};
+
+// A source with far pairs: its batch matrix X (rows slice*4 + field, ks columns).
+struct FarSource {
+    int dom;
+    int ks;                  // columns of W and X: node count rounded up to 64
+    long long n;
+    __nv_bfloat16 *X;
+};
+
+// A target with far pairs: interpolation weights and its coefficient ring.
+struct FarTarget {
+    int dom;
+    int nx, ny, nz;
+    int px, py, pz, r;       // nodes per axis, r = px*py*pz
+    const float *Lx, *Ly, *Lz;   // [n][p] Lagrange weights per axis
+    float *cring;            // [depth][r][4]
+    int depth;
+    int lag_hi_max;          // largest lag of the target's far pairs
+};
+
+// Rows of source n's W that belong to target t: row0 + (m - lag_lo) * r + a.
+struct FarLink {
+    int row0;
+    int r;
+    int nlag;
+    int lag_lo;
+    float *cring;
+    int depth;
+    int pad_;
+};
+
 struct IoPtrs {
     const float *rho[kMaxDomains];
     const float *J[kMaxDomains];
@@ -158,6 +200,17 @@ bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *b
                       uint64_t cols, uint32_t box_rows);
 cudaError_t launch_gemm_bf16_tn(const struct CUtensorMap_st &mapA, const struct CUtensorMap_st &mapB, float *D,
                                 int M, int N, int K, int ldd, int smem_optin, int *d_err, cudaStream_t s);
+
+// far-pair kernels (rp_far.cu)
+cudaError_t launch_far_build_w(const FarRow *d_rows, int nrows, const int n[3], double h, double inv_cdt, int ks,
+                               __nv_bfloat16 *W, cudaStream_t s);
+cudaError_t launch_far_convert(const FarSource *d_srcs, int nsrc, const IoPtrs &in, int slot, long long max_n,
+                               cudaStream_t s);
+cudaError_t launch_far_zero(const FarTarget *d_tgts, int ntgt, long long j1, int batch, int max_r, cudaStream_t s);
+cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads, const float *Z, int ldz, long long j0,
+                               int batch, cudaStream_t s);
+cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
+                              float inv_c, cudaStream_t s);
 
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);

@@ -16,17 +16,19 @@ from . import build as _build
 
 RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_HISTORY, RP_ERR_CUDA, RP_ERR_OOM, \
     RP_ERR_UNSUPPORTED, RP_ERR_TIMEOUT = range(8)
-RP_MODE_FFT, RP_MODE_DIRECT = 0, 1
+RP_MODE_FFT, RP_MODE_DIRECT, RP_MODE_LOWRANK = 0, 1, 2
 RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE = 0x1, 0x2, 0x4
-RP_PAIR_FFT, RP_PAIR_DIRECT = 0, 1
+RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK = 0, 1, 2
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
- RP_K_DIRECT, RP_K_COUNT) = range(7)
+ RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_COUNT) = range(11)
 MAX_DOMAINS = 256
 
 
 class rp_config(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("history_depth", ctypes.c_int),
-                ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("reserved", ctypes.c_int * 9)]
+                ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("far_points", ctypes.c_int),
+                ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int),
+                ("reserved", ctypes.c_int * 5)]
 
 
 class rp_pair_info_t(ctypes.Structure):
@@ -40,7 +42,8 @@ class rp_stats(ctypes.Structure):
                 ("raw_depth", ctypes.c_int), ("spectral_depth", ctypes.c_int),
                 ("step", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
-                ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("reserved", ctypes.c_int * 7)]
+                ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
+                ("far_bytes", ctypes.c_longlong), ("reserved", ctypes.c_int * 4)]
 
 
 class RPError(RuntimeError):
@@ -146,10 +149,11 @@ def rp_last_error(ctx) -> str:
 
 
 def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
-              flags: int = 0, device: int = 0, stream=None):
+              flags: int = 0, device: int = 0, stream=None, far_distance: float = 0.0,
+              far_points: int = 0, far_batch: int = 0):
     """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream (NULL without torch)."""
-    cfg = rp_config(c, dt, history_depth, mode, flags)
+    cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch)
     if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
         try:
             import torch
@@ -265,10 +269,12 @@ class RetardedPotentials:
     calls of a time step."""
 
     def __init__(self, domains, c: float, dt: float, history_depth: int = 0,
-                 mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None):
+                 mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
+                 far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0):
         import torch
         self.domains = list(domains)
-        self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream)
+        self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
+                             far_points, far_batch)
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)

@@ -1,0 +1,83 @@
+"""The low-rank far path (RP_MODE_LOWRANK) against the FP64 oracle.
+
+Three 12^3 domains: two 8 bohr apart (FFT path) and one about 600 bohr away
+(far pairs: interpolative factors, time-batched bf16 tcgen05 GEMMs).  The bar
+for the bf16 far field is 1e-3 rel-L2, on the total and on the far field
+alone (only the far source active).
+"""
+import numpy as np
+import pytest
+
+from paper_2311_15429_gb300 import rp, synth
+
+from _harness import oracle_values, rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+def _setup():
+    doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.25), synth.cubic((8.0, 0.5, -0.3), 12, 0.25),
+            synth.cubic((600.0, 50.0, -30.0), 12, 0.25)]
+    return doms, synth._sources(doms)
+
+
+def _run(doms, hists, eval_at, batch=16):
+    import torch
+    dev = torch.device("cuda", 0)
+    out = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=100.0,
+                               far_batch=batch) as lib:
+        kinds = {(t, s): lib.pair_info(t, s)["kind"] for t in range(3) for s in range(3)}
+        for i in range(hists[0].shape[0]):
+            lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
+                         [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists])
+            if i in eval_at:
+                phi, A = lib.evaluate()
+                torch.cuda.synchronize()
+                out[i] = [np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)])
+                          for d in range(3)]
+        lib.sync()
+        q = lib.query()
+    return out, kinds, q
+
+
+def test_far_pairs_planned_lowrank():
+    doms, _ = _setup()
+    ctx = rp.rp_create(synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, flags=rp.RP_FLAG_PLAN_ONLY, far_distance=100.0,
+                       far_batch=16)
+    try:
+        for d in doms:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        for t in range(3):
+            for s in range(3):
+                k = rp.rp_pair_info(ctx, t, s)["kind"]
+                far = (t == 2) != (s == 2)
+                assert k == (rp.RP_PAIR_LOWRANK if far else rp.RP_PAIR_FFT), (t, s, k)
+        assert rp.rp_query(ctx)["npairs_far"] == 4
+    finally:
+        rp.rp_destroy(ctx)
+
+
+@pytest.mark.parametrize("batch", [16, 32])
+def test_far_path_total_and_far_field(batch):
+    doms, srcs = _setup()
+    T = 104
+    hists = [s.history(0, T, 0.05) for s in srcs]
+    steps = [T - 4, T - 1]
+    out, kinds, q = _run(doms, hists, steps, batch)
+    assert q["npairs_far"] == 4
+    for step in steps:
+        for t, d in enumerate(doms):
+            want = oracle_values(doms, hists, 0, synth.C_AU, 0.05, t, step, np.arange(d.N))
+            errs = rel_l2(out[step][t], want)
+            assert max(errs) <= TOL, ("total", step, t, errs)
+    # far field alone: only domain 2 active, seen from domains 0 and 1
+    far_only = [np.zeros_like(hists[0]), np.zeros_like(hists[1]), hists[2]]
+    out, _, _ = _run(doms, far_only, steps, batch)
+    for step in steps:
+        for t in (0, 1):
+            want = oracle_values(doms, far_only, 0, synth.C_AU, 0.05, t, step, np.arange(doms[t].N))
+            errs = rel_l2(out[step][t], want)
+            assert max(errs) <= TOL, ("far only", step, t, errs)
