@@ -46,6 +46,10 @@ def parse():
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--oracle-nodes", type=int, default=8192, help="oracle sample per domain")
+    p.add_argument("--mode", choices=["fft", "lowrank"], default="fft",
+                   help="fft: every pair by FFT (FP32); lowrank: far pairs by bf16 tensor-core factors")
+    p.add_argument("--far-distance", type=float, default=1000.0)
+    p.add_argument("--far-batch", type=int, default=32)
     return p.parse_args()
 
 
@@ -184,6 +188,30 @@ def algorithmic_bytes(w, info):
     return out
 
 
+def far_gemm_bytes(w, info, points, batch):
+    """Bytes of one far GEMM launch (averaged over the far sources): the
+    factor rows and batch matrix read (bf16 hi and lo planes, 4 bytes per
+    element each), the fp32 node values written."""
+    nd = len(w.domains)
+    tot, n = 0, 0
+    for s in range(nd):
+        rows = 0
+        for t in range(nd):
+            p = info[(t, s)]
+            if p["kind"] == 2:
+                r = 1
+                for a in range(3):
+                    r *= min(points, w.domains[t].n[a])
+                rows += (p["lag_hi"] - p["lag_lo"] + 1) * r
+        if not rows:
+            continue
+        rows = (rows + 127) // 128 * 128
+        ks = (w.domains[s].N + 63) // 64 * 64
+        tot += rows * ks * 4 + 4 * batch * ks * 4 + rows * 4 * batch * 4
+        n += 1
+    return tot / max(n, 1)
+
+
 def measured_peak():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -289,8 +317,10 @@ def run_ours(args, rank, world, local):
     J = [[dev_in[d][i, 1:].reshape(-1) for d in range(len(w.domains))] for i in range(pre + ncycle)]
     in_bytes = sum(x.numel() * 4 for x in dev_in)
 
-    lib = rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=rp.RP_MODE_FFT,
-                                flags=rp.RP_FLAG_PROFILE, device=local, stream=stream)
+    mode = rp.RP_MODE_LOWRANK if args.mode == "lowrank" else rp.RP_MODE_FFT
+    lib = rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=mode,
+                                flags=rp.RP_FLAG_PROFILE, device=local, stream=stream,
+                                far_distance=args.far_distance, far_batch=args.far_batch)
     info = {(t, s): lib.pair_info(t, s) for t in range(len(w.domains)) for s in range(len(w.domains))}
     for i in range(pre):
         lib.push_all(rho[i], J[i])
@@ -316,6 +346,9 @@ def run_ours(args, rank, world, local):
         npts = sum(len(n) for n in onodes)
         acc = {"rel_l2_max": max(errs), "rel_l2_per_field_domain": errs,
                "checked": f"{npts} sampled nodes at step t={check_step * w.dt:.2f} vs FP64 oracle"}
+        if args.mode == "lowrank" and lib.query()["npairs_far"]:
+            acc["far_field_only"] = far_only_error(args, w, hists, rho, J, pre, check_step, depth, local,
+                                                   stream, info)
         cpu = {"value": npts / t_or, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.oracle_nodes} seeded target nodes per domain x all {w.points} "
                          f"source nodes at one step ({t_or:.1f} s wall)"}
@@ -353,6 +386,7 @@ def run_ours(args, rank, world, local):
             kstats[rp.rp_kernel_name(kind)] = {"launches": n, "avg_us": 1e3 * t / n, "total_ms": t}
             launches += n
     alg = algorithmic_bytes(w, info)
+    alg["far_gemm"] = far_gemm_bytes(w, info, 4, args.far_batch)
     dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
     peak, peak_kind = measured_peak()
     ach = alg[dom] / (kstats[dom]["avg_us"] * 1e-6) / 1e9
@@ -434,7 +468,10 @@ def run_ours(args, rank, world, local):
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "description": w.description, "points_per_step": q_points,
-                   "path": "FFT: Hockney self term + delay-binned cross pairs, spectral history ring",
+                   "path": ("FFT: Hockney self term + delay-binned cross pairs, spectral history ring"
+                            if args.mode == "fft" else
+                            f"FFT self/near pairs; pairs >= {args.far_distance} bohr apart by bf16 tcgen05 "
+                            f"low-rank factors (4^3 interpolation nodes, {args.far_batch}-step batches)"),
                    "l2": f"inputs larger than L2: {ncycle} distinct input slices per domain cycled "
                          f"({in_bytes / 2**20:.0f} MiB), spectral ring "
                          f"{lib_bytes_str(w, info, depth)} read per step",
@@ -449,6 +486,34 @@ def run_ours(args, rank, world, local):
         "clocks": clk,
     }
     print(json.dumps(line), flush=True)
+
+
+def far_only_error(args, w, hists, rho, J, pre, check_step, depth, local, stream, info):
+    """rel-L2 of the far field alone: domain 0 the only active source, seen
+    from the domains it reaches by the far path (sampled nodes, FP64 oracle)."""
+    import torch
+    from paper_2311_15429_gb300 import rp
+    tg = [t for t in range(1, len(w.domains)) if info[(t, 0)]["kind"] == 2]
+    if not tg:
+        return None
+    zr = [torch.zeros_like(x) for x in rho[0]]
+    zJ = [torch.zeros_like(x) for x in J[0]]
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=rp.RP_MODE_LOWRANK,
+                               device=local, stream=stream, far_distance=args.far_distance,
+                               far_batch=args.far_batch) as lf:
+        for i in range(pre + check_step + 1):
+            lf.push_all([rho[i][0]] + zr[1:], [J[i][0]] + zJ[1:])
+        lf.evaluate()
+        lf.sync()
+        vals = [torch.cat([lf.phi[d][None], lf.A[d].reshape(3, -1)]).cpu().numpy() for d in tg]
+    only = [hists[0]] + [np.zeros_like(h) for h in hists[1:]]
+    ovals, onodes, _, _ = oracle_sample(w, only, -pre, check_step, 1024, seed=5)
+    errs = []
+    for k, t in enumerate(tg):
+        g = vals[k][:, onodes[t]]
+        for f in range(4):
+            errs.append(float(np.linalg.norm(g[f] - ovals[t][:, f]) / np.linalg.norm(ovals[t][:, f])))
+    return {"rel_l2_max": max(errs), "per_field": errs, "source": 0, "targets": tg}
 
 
 def lib_bytes_str(w, info, depth):

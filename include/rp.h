@@ -265,6 +265,25 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
 rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device,
                        void *stream);
 
+/*
+ * rp_gemm_bf16_split -- the same contraction in the two forms the far field
+ * uses (Eq. 11 applied through skeleton rows, as for rp_gemm_bf16).
+ *   terms = 1: A is M x K, B is N x K; D = A B^T.
+ *   terms = 3: A is M x 2K holding [A_hi | A_lo] per row and B is N x 2K
+ *              holding [B_hi | B_lo]; D = A_hi B_hi^T + A_hi B_lo^T +
+ *              A_lo B_hi^T, i.e. the product of A_hi + A_lo and B_hi + B_lo
+ *              less the lo*lo term (about 16 significant bits per operand).
+ * `splits` cuts the K range (3K k-values for terms = 3) into that many chunks
+ * run by separate CTAs whose fp32 partial products are then summed in a fixed
+ * order (deterministic); 0 picks the count the far path uses (about two CTAs
+ * per SM).  The partial products need splits x M x N floats of device memory,
+ * which this call allocates and frees.  Shapes as for rp_gemm_bf16; D is
+ * M x N fp32.  Synchronous.  Errors as for rp_gemm_bf16; RP_ERR_ARG also for
+ * terms other than 1 or 3 and splits outside [0, 4096].
+ */
+rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int terms,
+                             int splits, int device, void *stream);
+
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);
 

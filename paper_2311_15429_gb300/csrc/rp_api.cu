@@ -131,6 +131,8 @@ struct rp_ctx {
     std::vector<int> far_link0, far_link1, far_link_threads;   // per far source
     std::vector<float *> far_Z;
     std::vector<int> far_rows;                                  // padded W rows per far source
+    std::vector<int> far_splits;                                // split-K count per far source
+    float *far_work = nullptr;                                  // split-K partial products
     std::vector<CUtensorMap> far_mapW, far_mapX;
     std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
     FarSource *d_far_src = nullptr;
@@ -473,6 +475,7 @@ rp_status build_far(rp_ctx *ctx, int max_optin)
         return fail(ctx, RP_ERR_UNSUPPORTED, "far path needs cuTensorMapEncodeTiled");
     }
     // sources
+    size_t work_floats = 0;
     for (int s = 0; s < nd; ++s) {
         std::vector<FarRow> rows;
         std::vector<FarLink> links;
@@ -510,15 +513,18 @@ rp_status build_far(rp_ctx *ctx, int max_optin)
         __nv_bfloat16 *W = nullptr;
         float *Z = nullptr;
         if ((st = upload(ctx, &d_rows, rows))) return st;
-        if ((st = dev_alloc(ctx, &W, (size_t)nrows * F.ks))) return st;
-        if ((st = dev_alloc(ctx, &F.X, (size_t)4 * batch * F.ks))) return st;
+        if ((st = dev_alloc(ctx, &W, (size_t)nrows * 2 * F.ks))) return st;
+        if ((st = dev_alloc(ctx, &F.X, (size_t)4 * batch * 2 * F.ks))) return st;
         if ((st = dev_alloc(ctx, &Z, (size_t)nrows * 4 * batch))) return st;
-        RP_CUDA(ctx, cudaMemset(F.X, 0, (size_t)4 * batch * F.ks * sizeof(__nv_bfloat16)));
+        RP_CUDA(ctx, cudaMemset(F.X, 0, (size_t)4 * batch * 2 * F.ks * sizeof(__nv_bfloat16)));
         RP_CUDA(ctx, launch_far_build_w(d_rows, nrows, S.n, S.h, inv_cdt, F.ks, W, ctx->stream));
-        ctx->far_bytes += (long long)nrows * F.ks * 2 + 8LL * batch * F.ks + 16LL * nrows * batch;
+        const int splits = gemm_splits(nrows, F.ks, 1, ctx->sm_count, 16);
+        work_floats = std::max(work_floats, splits > 1 ? (size_t)splits * nrows * 4 * batch : 0);
+        ctx->far_splits.push_back(splits);
+        ctx->far_bytes += (long long)nrows * F.ks * 4 + 16LL * batch * F.ks + 16LL * nrows * batch;
         CUtensorMap mw, mx;
-        if (!encode_bf16_rows(enc, &mw, W, (uint64_t)nrows, (uint64_t)F.ks, 128) ||
-            !encode_bf16_rows(enc, &mx, F.X, (uint64_t)4 * batch, (uint64_t)F.ks, (uint32_t)(4 * batch)))
+        if (!encode_bf16_rows(enc, &mw, W, (uint64_t)nrows, (uint64_t)2 * F.ks, 128) ||
+            !encode_bf16_rows(enc, &mx, F.X, (uint64_t)4 * batch, (uint64_t)2 * F.ks, (uint32_t)(4 * batch)))
             return fail(ctx, RP_ERR_UNSUPPORTED, "far path: a tensor map did not encode");
         ctx->far_mapW.push_back(mw);
         ctx->far_mapX.push_back(mx);
@@ -537,6 +543,10 @@ rp_status build_far(rp_ctx *ctx, int max_optin)
         ctx->far_src.push_back(F);
     }
     (void)max_optin;
+    if (work_floats) {
+        if ((st = dev_alloc(ctx, &ctx->far_work, work_floats))) return st;
+        ctx->far_bytes += (long long)work_floats * 4;
+    }
     if ((st = upload(ctx, &ctx->d_far_src, ctx->far_src))) return st;
     if ((st = upload(ctx, &ctx->d_far_tgt, ctx->far_tgt))) return st;
     if ((st = upload(ctx, &ctx->d_far_links, ctx->far_links))) return st;
@@ -981,6 +991,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     if ((st = build_tensor_maps(ctx, treal, tcplx, max_optin))) return st;
 
     // ---- far pairs
+    RP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
     if ((st = build_far(ctx, max_optin))) return st;
 
     // ---- device tables and kernel limits
@@ -995,7 +1006,6 @@ rp_status rp_finalize(rp_ctx *ctx)
     RP_CUDA(ctx, open_mac_tma_smem_limit(max_optin));
     if ((st = dev_alloc(ctx, &ctx->d_err, 1))) return st;
     RP_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
-    RP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
     RP_CUDA(ctx, cudaDeviceSynchronize());
     ctx->finalized = true;
     return RP_OK;
@@ -1103,7 +1113,8 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
                     if ((st = timed_launch(ctx, RP_K_FAR_GEMM, "far GEMM", [&] {
                              return launch_gemm_bf16_tn(ctx->far_mapW[fi], ctx->far_mapX[fi], ctx->far_Z[fi],
                                                         ctx->far_rows[fi], 4 * batch, ctx->far_src[fi].ks, 4 * batch,
-                                                        optin, ctx->d_err, ctx->stream);
+                                                        optin, ctx->d_err, ctx->stream, ctx->far_splits[fi],
+                                                        ctx->far_work, 1);
                          })))
                         return st;
                     if ((st = timed_launch(ctx, RP_K_FAR_SCATTER, "far scatter", [&] {
@@ -1324,9 +1335,11 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
     return RP_OK;
 }
 
-rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device, void *stream)
+rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int terms,
+                             int splits, int device, void *stream)
 {
-    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 256)
+    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 256 ||
+        (terms != 1 && terms != 3) || splits < 0 || splits > 4096)
         return RP_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
@@ -1339,29 +1352,43 @@ rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
         cudaGetLastError();
         return RP_ERR_CUDA;
     }
+    const int width = terms == 3 ? 2 * K : K;
     CUtensorMap ma, mb;
-    if (!encode_bf16_rows(fn, &ma, d_A, (uint64_t)M, (uint64_t)K, 128) ||
-        !encode_bf16_rows(fn, &mb, d_B, (uint64_t)N, (uint64_t)K, (uint32_t)N))
+    if (!encode_bf16_rows(fn, &ma, d_A, (uint64_t)M, (uint64_t)width, 128) ||
+        !encode_bf16_rows(fn, &mb, d_B, (uint64_t)N, (uint64_t)width, (uint32_t)N))
         return RP_ERR_ARG;
-    int optin = 0;
+    int optin = 0, sms = 0;
     int *d_err = nullptr;
+    float *work = nullptr;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device) != cudaSuccess ||
-        cudaMalloc(&d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) {
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    if (splits == 0) splits = gemm_splits(M, K, terms == 3, sms, 16);
+    if (cudaMalloc(&d_err, sizeof(int)) != cudaSuccess || cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess ||
+        (splits > 1 && cudaMalloc(&work, (size_t)splits * M * N * sizeof(float)) != cudaSuccess)) {
         cudaGetLastError();
         if (d_err) cudaFree(d_err);
         return RP_ERR_CUDA;
     }
     int flag = 0;
-    cudaError_t e = launch_gemm_bf16_tn(ma, mb, d_D, M, N, K, N, optin, d_err, s);
+    cudaError_t e = launch_gemm_bf16_tn(ma, mb, d_D, M, N, K, N, optin, d_err, s, splits, work, terms == 3);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d_err);
+    if (work) cudaFree(work);
     if (e != cudaSuccess) {
         cudaGetLastError();
         return RP_ERR_CUDA;
     }
     return flag ? RP_ERR_TIMEOUT : RP_OK;
+}
+
+rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device, void *stream)
+{
+    return rp_gemm_bf16_split(d_A, d_B, d_D, M, N, K, 1, 1, device, stream);
 }
 
 rp_status rp_sync(rp_ctx *ctx)
@@ -1476,7 +1503,7 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
     for (const FwdRing &R : ctx->fwd)
         if ((st = fn((void *)R.ring, (size_t)R.depth * R.slot_elems * sizeof(float2)))) return st;
     for (const FarSource &F : ctx->far_src)
-        if ((st = fn((void *)F.X, (size_t)4 * ctx->cfg.far_batch * F.ks * sizeof(__nv_bfloat16)))) return st;
+        if ((st = fn((void *)F.X, (size_t)8 * ctx->cfg.far_batch * F.ks * sizeof(__nv_bfloat16)))) return st;
     for (const FarTarget &F : ctx->far_tgt)
         if ((st = fn((void *)F.cring, (size_t)F.depth * F.r * 4 * sizeof(float)))) return st;
     return RP_OK;

@@ -10,8 +10,9 @@
 //   W_{tn,m}[a][k'] = h^3 T(m dt - R(x_a, r_k')/c) / R(x_a, r_k')   (Eq. 11 at the nodes).
 //
 // The source-side contraction runs time-batched: every `batch` pushes, the
-// GEMM  Z_n = W_n X_n^T  (W_n: rows (t, m, a) x source nodes, bf16; X_n: the
-// batch's slices, one row per (slice, field), bf16; fp32 accumulation) gives
+// GEMM  Z_n = W_n X_n^T  (W_n: rows (t, m, a) x source nodes; X_n: the
+// batch's slices, one row per (slice, field); both as bf16 hi/lo pairs, with
+// the three products hi*hi + hi*lo + lo*hi accumulated in fp32) gives
 // every node value for every (lag, slice) pair; k_far_scatter then adds
 // Z[(t, m, a)][(k, f)] into the coefficient ring of target t at step
 // j0 + k + m.  A far pair needs lag_lo >= batch - 1 so that step l's
@@ -28,12 +29,13 @@ namespace {
 constexpr int kFarThreads = 256;
 
 // W rows of one source: row r has the node position (relative to the source
-// origin) and the lag of the row (lag < 0: padding row).  FP32 arithmetic:
-// its error (about 1e-4 bohr in R at 5000 bohr) is far below the bf16
-// rounding of the stored factor.
+// origin) and the lag of the row (lag < 0: padding row).  The factor is
+// computed in FP64 and stored as two bf16 planes, W = W_hi + W_lo with
+// W_hi = bf16(W) and W_lo = bf16(W - W_hi) (row layout [W_hi | W_lo], each
+// half `ks` wide), which carries about 16 significant bits.
 __global__ void __launch_bounds__(kFarThreads) k_far_build_w(const FarRow *__restrict__ rows, int nrows, int nx,
-                                                              int ny, int nz, float h, float inv_cdt, float vol, int ks,
-                                                              __nv_bfloat16 *W)
+                                                              int ny, int nz, double h, double inv_cdt, double vol,
+                                                              int ks, __nv_bfloat16 *W)
 {
     const long long ns = (long long)nx * ny * nz;
     const long long total = (long long)nrows * ks;
@@ -41,20 +43,24 @@ __global__ void __launch_bounds__(kFarThreads) k_far_build_w(const FarRow *__res
          i += (long long)gridDim.x * blockDim.x) {
         const int r = (int)(i / ks);
         const long long q = i % ks;
-        float w = 0.0f;
+        double w = 0.0;
         const FarRow fr = rows[r];
         if (fr.lag >= 0 && q < ns) {
             const int ix = (int)(q % nx), iy = (int)((q / nx) % ny), iz = (int)(q / ((long long)nx * ny));
-            const float dx = fr.x - h * ix, dy = fr.y - h * iy, dz = fr.z - h * iz;
-            const float R = sqrtf(dx * dx + dy * dy + dz * dz);
-            const float T = 1.0f - fabsf((float)fr.lag - R * inv_cdt);
-            if (T > 0.0f) w = vol * T / R;
+            const double dx = fr.x - h * ix, dy = fr.y - h * iy, dz = fr.z - h * iz;
+            const double R = sqrt(dx * dx + dy * dy + dz * dz);
+            const double T = 1.0 - fabs((double)fr.lag - R * inv_cdt);
+            if (T > 0.0) w = vol * T / R;
         }
-        W[i] = __float2bfloat16(w);
+        const __nv_bfloat16 hi = __float2bfloat16((float)w);
+        const __nv_bfloat16 lo = __float2bfloat16((float)(w - (double)__bfloat162float(hi)));
+        W[(long long)r * 2 * ks + q] = hi;
+        W[(long long)r * 2 * ks + ks + q] = lo;
     }
 }
 
-// One slice of each far source into row block (slot) of its batch matrix X.
+// One slice of each far source into row block (slot) of its batch matrix X,
+// split like W into [X_hi | X_lo] (the low part is exact in fp32: v - hi).
 __global__ void __launch_bounds__(kFarThreads) k_far_convert(const FarSource *__restrict__ srcs, int nsrc, IoPtrs in,
                                                               int slot)
 {
@@ -69,7 +75,10 @@ __global__ void __launch_bounds__(kFarThreads) k_far_convert(const FarSource *__
         const int f = (int)(i / n);
         const long long q = i % n;
         const float v = f == 0 ? rho[q] : J[(long long)(f - 1) * n + q];
-        S.X[((long long)slot * 4 + f) * S.ks + q] = __float2bfloat16(v);
+        const __nv_bfloat16 hi = __float2bfloat16(v);
+        __nv_bfloat16 *row = S.X + ((long long)slot * 4 + f) * 2 * S.ks;
+        row[q] = hi;
+        row[S.ks + q] = __float2bfloat16(v - __bfloat162float(hi));
     }
 }
 
@@ -168,8 +177,7 @@ cudaError_t launch_far_build_w(const FarRow *d_rows, int nrows, const int n[3], 
 {
     const long long total = (long long)nrows * ks;
     const int blocks = (int)std::min<long long>((total + kFarThreads - 1) / kFarThreads, 65535LL * 16);
-    k_far_build_w<<<blocks, kFarThreads, 0, s>>>(d_rows, nrows, n[0], n[1], n[2], (float)h, (float)inv_cdt,
-                                                  (float)(h * h * h), ks, W);
+    k_far_build_w<<<blocks, kFarThreads, 0, s>>>(d_rows, nrows, n[0], n[1], n[2], h, inv_cdt, h * h * h, ks, W);
     return cudaGetLastError();
 }
 

@@ -18,6 +18,7 @@
 //               fp32 accumulator (each warp its 32 tensor-memory lanes) and
 //               store D.
 // Waits are bounded (clock64); a timeout sets *err and the CTA drains and exits.
+#include <algorithm>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -111,10 +112,16 @@ __device__ __forceinline__ constexpr int tmem_cols()
     return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 }
 
+// blockIdx.y selects a K range [k0, k1) of `kchunk` k-tiles (split-K); each
+// split writes its own M x N slice of D (D + split * split_stride).  With
+// `split3` the K range is three times the operand width `K`: k-tiles
+// [0, K) pair A[:, :K] with B[:, :K], [K, 2K) pair A[:, :K] with B[:, K:2K],
+// and [2K, 3K) pair A[:, K:2K] with B[:, :K] -- so that with A = [A_hi | A_lo]
+// and B = [B_hi | B_lo] the product is A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.
 template <int BN>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *D,
-                   int K, int ldd, int stages, int *err)
+                   int K, int ldd, int stages, int *err, int kchunk, long long split_stride, int split3)
 {
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
     constexpr int STAGE = A_BYTES + B_BYTES;       // multiple of 1024
@@ -128,7 +135,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
-    const int ktiles = K / kBK;
+    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
+    const int kt0 = blockIdx.y * kchunk;
+    const int ktiles = max(0, min(kchunk, kt_all - kt0));
+    D += (long long)blockIdx.y * split_stride;
     // the swizzled operand descriptors assume 1024-byte aligned stages
     if (su32(smem) & 1023u) {
         if (threadIdx.x == 0) atomicExch(err, 2);
@@ -166,9 +176,13 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             unsigned char *st = smem + (size_t)s * STAGE;
+            const int g = kt0 + kt;                  // global k-tile
+            const int w = K / kBK, part = g / w, kk = (g % w) * kBK;
+            const int ka = (split3 && part == 2) ? K + kk : kk;   // A_lo in the third part
+            const int kb = (split3 && part == 1) ? K + kk : kk;   // B_lo in the second part
             bar_expect(&full[s], STAGE);
-            tma_2d(st, &mapA, kt * kBK, m0, &full[s]);
-            tma_2d(st + A_BYTES, &mapB, kt * kBK, 0, &full[s]);
+            tma_2d(st, &mapA, split3 ? ka : g * kBK, m0, &full[s]);
+            tma_2d(st + A_BYTES, &mapB, split3 ? kb : g * kBK, 0, &full[s]);
         }
         // every copy issued has landed before the CTA may exit
         for (int r = kt > stages ? kt - stages : 0; r < kt; ++r)
@@ -198,7 +212,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const int quarter = warp & 3;               // tensor-memory lanes 32*quarter .. +31
         const int row = m0 + 32 * quarter + lane;
-        if (ok && !*abort_flag) {
+        if (ktiles == 0) {
+            for (int c = 0; c < BN; c += 4)
+                *reinterpret_cast<float4 *>(D + (size_t)row * ldd + c) = make_float4(0.f, 0.f, 0.f, 0.f);
+        } else if (ok && !*abort_flag) {
 #pragma unroll 1
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
@@ -229,6 +246,16 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
 }
 
+// Z[i] = sum over splits of P[split][i]
+__global__ void k_split_reduce(const float *__restrict__ P, float *__restrict__ Z, long long n, int splits)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        float s = 0.0f;
+        for (int k = 0; k < splits; ++k) s += P[(long long)k * n + i];
+        Z[i] = s;
+    }
+}
+
 template <int BN>
 size_t gemm_smem(int stages)
 {
@@ -252,12 +279,20 @@ bool encode_bf16_rows(void *encode_fn, CUtensorMap *map, const void *base, uint6
 }
 
 // D (M x N fp32, row stride ldd) = A (M x K bf16) * B (N x K bf16)^T, with
-// M % 128 == 0, K % 64 == 0, N a multiple of 32 up to 256.
+// M % 128 == 0, K % 64 == 0, N a multiple of 32 up to 256.  `splits` > 1
+// runs split-K: partial products go to `work` (splits x M x N floats) and a
+// reduction writes D (then ldd must be N).  `split3`: see k_gemm_bf16_tn.
 cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB, float *D, int M, int N, int K,
-                                int ldd, int smem_optin, int *d_err, cudaStream_t s)
+                                int ldd, int smem_optin, int *d_err, cudaStream_t s, int splits, float *work,
+                                int split3)
 {
-    if (M % kBM || K % kBK || N % 32 || N <= 0 || N > 256) return cudaErrorInvalidValue;
-    const int grid = M / kBM;
+    if (M % kBM || K % kBK || N % 32 || N <= 0 || N > 256 || splits < 1) return cudaErrorInvalidValue;
+    if (splits > 1 && (!work || ldd != N)) return cudaErrorInvalidValue;
+    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
+    const int kchunk = (kt_all + splits - 1) / splits;
+    const dim3 grid(M / kBM, splits);
+    float *out = splits > 1 ? work : D;
+    const long long stride = splits > 1 ? (long long)M * N : 0;
 #define RP_GEMM_CASE(BN)                                                                             \
     case BN: {                                                                                       \
         int stages = (int)((smem_optin - 64) / (kBM * kBK * 2 + BN * kBK * 2));                      \
@@ -267,8 +302,9 @@ cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB
         cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
                                              (int)smem);                                             \
         if (e) return e;                                                                             \
-        k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(mapA, mapB, D, K, ldd, stages, d_err);   \
-        return cudaGetLastError();                                                                   \
+        k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, \
+                                                             stride, split3);                        \
+        break;                                                                                       \
     }
     switch (N) {
         RP_GEMM_CASE(32)
@@ -282,6 +318,22 @@ cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB
     default: return cudaErrorInvalidValue;
     }
 #undef RP_GEMM_CASE
+    cudaError_t e = cudaGetLastError();
+    if (e || splits == 1) return e;
+    const long long n = (long long)M * N;
+    k_split_reduce<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(work, D, n, splits);
+    return cudaGetLastError();
+}
+
+// Number of K splits that gives about two CTAs per SM, each with at least
+// `min_tiles` k-tiles.
+int gemm_splits(int M, int K, int split3, int sms, int min_tiles)
+{
+    const int mtiles = M / kBM;
+    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
+    int splits = std::max(1, (2 * sms + mtiles - 1) / mtiles);
+    splits = std::min(splits, std::max(1, kt_all / std::max(1, min_tiles)));
+    return splits;
 }
 
 }  // namespace rp

@@ -199,7 +199,9 @@ cudaError_t launch_mac_tma(int cls, const InvTarget *d_tgts, int t0, int t1, int
 bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *base, uint64_t rows,
                       uint64_t cols, uint32_t box_rows);
 cudaError_t launch_gemm_bf16_tn(const struct CUtensorMap_st &mapA, const struct CUtensorMap_st &mapB, float *D,
-                                int M, int N, int K, int ldd, int smem_optin, int *d_err, cudaStream_t s);
+                                int M, int N, int K, int ldd, int smem_optin, int *d_err, cudaStream_t s,
+                                int splits = 1, float *work = nullptr, int split3 = 0);
+int gemm_splits(int M, int K, int split3, int sms, int min_tiles);
 
 // far-pair kernels (rp_far.cu)
 cudaError_t launch_far_build_w(const FarRow *d_rows, int nrows, const int n[3], double h, double inv_cdt, int ks,

@@ -70,6 +70,7 @@ SIGNATURES = {
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
     "rp_gemm_bf16": (_I, [_V, _V, _V, _I, _I, _I, _I, _V]),
+    "rp_gemm_bf16_split": (_I, [_V, _V, _V, _I, _I, _I, _I, _I, _I, _V]),
     "rp_sync": (_I, [_V]),
     "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
@@ -224,6 +225,23 @@ def rp_gemm_bf16(A, B, D, device: int = 0, stream=None):
         if not t.is_contiguous():
             raise ValueError("operands must be contiguous")
     _check(load().rp_gemm_bf16(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, device, stream))
+
+
+def rp_gemm_bf16_split(A, B, D, terms: int = 1, splits: int = 0, device: int = 0, stream=None):
+    """Split-K form of rp_gemm_bf16.  terms=1: D = A @ B.T.  terms=3: A is
+    (M x 2K) = [A_hi | A_lo], B is (N x 2K) = [B_hi | B_lo], and
+    D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.  splits=0 picks the count."""
+    M, W = A.shape
+    N = B.shape[0]
+    K = W // 2 if terms == 3 else W
+    if stream is None:
+        import torch
+        stream = torch.cuda.current_stream(device).cuda_stream
+    for t in (A, B, D):
+        if not t.is_contiguous():
+            raise ValueError("operands must be contiguous")
+    _check(load().rp_gemm_bf16_split(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, terms, splits, device,
+                                     stream))
 
 
 def rp_sync(ctx):
