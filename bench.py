@@ -223,17 +223,19 @@ def measured_peak():
 
 def committed_traffic(kernel, workload):
     """dram bytes per launch from the committed ncu summary, if it was taken
-    on the current kernel source (else None)."""
+    on the current source of the kernel (the file its summary names under
+    ``kernel_source:``), else None."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_{workload}.md")
     if not os.path.exists(path):
         return None
     txt = open(path).read()
     m1 = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
     m2 = re.search(r"kernel_source_sha256:\s*([0-9a-f]{64})", txt)
-    if not m1 or not m2:
+    m3 = re.search(r"kernel_source:\s*(\S+)", txt)
+    if not m1 or not m2 or not m3:
         return None
-    src = os.path.join(ROOT, "paper_2311_15429_gb300", "csrc", "rp_fft_kernels.cu")
-    if hashlib.sha256(open(src, "rb").read()).hexdigest() != m2.group(1):
+    src = os.path.join(ROOT, "paper_2311_15429_gb300", "csrc", os.path.basename(m3.group(1)))
+    if not os.path.exists(src) or hashlib.sha256(open(src, "rb").read()).hexdigest() != m2.group(1):
         return None
     return float(m1.group(1))
 
@@ -322,6 +324,7 @@ def run_ours(args, rank, world, local):
                                 flags=rp.RP_FLAG_PROFILE, device=local, stream=stream,
                                 far_distance=args.far_distance, far_batch=args.far_batch)
     info = {(t, s): lib.pair_info(t, s) for t in range(len(w.domains)) for s in range(len(w.domains))}
+    mac_warps = lib.query()["mac_warps"]
     for i in range(pre):
         lib.push_all(rho[i], J[i])
     # warm-up on continuous time (t = 0, dt, ...), the accuracy check on the
@@ -475,6 +478,7 @@ def run_ours(args, rank, world, local):
                    "l2": f"inputs larger than L2: {ncycle} distinct input slices per domain cycled "
                          f"({in_bytes / 2**20:.0f} MiB), spectral ring "
                          f"{lib_bytes_str(w, info, depth)} read per step",
+                   "mac_consumer_warps": mac_warps,
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "accuracy": acc,
         "plain_path": plain,

@@ -100,7 +100,11 @@ typedef struct {
     double far_distance; /* RP_MODE_LOWRANK: smallest box distance of a far pair (bohr, > 0) */
     int far_batch;       /* RP_MODE_LOWRANK: source slices per GEMM, multiple of 8 in 8..64 (0: 32);
                           * a far pair also needs lag_lo >= far_batch - 1 */
-    int reserved[5];     /* set to zero */
+    int mac_warps;       /* consumer warps of the TMA-fed spectral MAC: 8, 12 or 16, or 0 to let
+                          * rp_finalize time the three variants on this plan (two launches each
+                          * per FFT size class) and keep the fastest.  The variants sum the same
+                          * terms in the same order: the choice changes timing, never results. */
+    int reserved[4];     /* set to zero */
 } rp_config;
 
 typedef struct rp_ctx rp_ctx;
@@ -132,7 +136,8 @@ typedef struct {
     int mac_tma;              /* 1: the spectral MAC of cubic targets is fed by TMA copies */
     int npairs_far;           /* pairs on the low-rank far path */
     long long far_bytes;      /* device memory of the far path (factors, batches, rings) */
-    int reserved[4];
+    int mac_warps;            /* consumer warps of the MAC variant in use (last size class), 0 if none */
+    int reserved[3];
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -273,13 +278,16 @@ rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
  *              holding [B_hi | B_lo]; D = A_hi B_hi^T + A_hi B_lo^T +
  *              A_lo B_hi^T, i.e. the product of A_hi + A_lo and B_hi + B_lo
  *              less the lo*lo term (about 16 significant bits per operand).
- * `splits` cuts the K range (3K k-values for terms = 3) into that many chunks
- * run by separate CTAs whose fp32 partial products are then summed in a fixed
- * order (deterministic); 0 picks the count the far path uses (about two CTAs
- * per SM).  The partial products need splits x M x N floats of device memory,
+ * For terms = 3 each pipeline stage holds the four tiles of a K step and the
+ * three products accumulate in one fp32 accumulator, so every operand byte
+ * is read once.  `splits` cuts the K range into that many chunks run by
+ * separate CTAs whose fp32 partial products are then summed in a fixed order
+ * (deterministic); 0 picks the count the far path uses (one wave of CTAs,
+ * one per SM).  The partial products need splits x M x N floats of device memory,
  * which this call allocates and frees.  Shapes as for rp_gemm_bf16; D is
  * M x N fp32.  Synchronous.  Errors as for rp_gemm_bf16; RP_ERR_ARG also for
- * terms other than 1 or 3 and splits outside [0, 4096].
+ * terms other than 1 or 3, splits outside [0, 4096] and pointers that are not
+ * 16-byte aligned.
  */
 rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int terms,
                              int splits, int device, void *stream);

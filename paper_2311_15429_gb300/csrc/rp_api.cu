@@ -122,6 +122,7 @@ struct rp_ctx {
     bool tma = false;                // TMA-fed MAC available for the cubic classes
     int nmaps = 0;
     int mac_stages[7] = {};          // pipeline depth per class (index by class_slot)
+    int mac_cw[7] = {16, 16, 16, 16, 16, 16, 16};   // consumer warps of the MAC per class
     int sm_count = 0;
     int *d_err = nullptr;            // set by a kernel whose bounded wait ran out
     // far pairs (low-rank path)
@@ -137,6 +138,13 @@ struct rp_ctx {
     std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
     FarSource *d_far_src = nullptr;
     FarTarget *d_far_tgt = nullptr;
+    // far sources / targets with no forward ring / inverse target of their
+    // own: staged and interpolated by separate kernels
+    std::vector<FarSource> far_src_alone;
+    std::vector<FarTarget> far_tgt_alone;
+    std::vector<int> far_src_alone_of_dom;
+    FarSource *d_far_src_alone = nullptr;
+    FarTarget *d_far_tgt_alone = nullptr;
     FarLink *d_far_links = nullptr;
     int far_planes = 0, far_max_r = 0, npairs_far = 0;
     long long far_bytes = 0, far_max_n = 0, far_zeroed_step = -1;
@@ -550,6 +558,86 @@ rp_status build_far(rp_ctx *ctx, int max_optin)
     if ((st = upload(ctx, &ctx->d_far_src, ctx->far_src))) return st;
     if ((st = upload(ctx, &ctx->d_far_tgt, ctx->far_tgt))) return st;
     if ((st = upload(ctx, &ctx->d_far_links, ctx->far_links))) return st;
+    // staging rides on the source's first forward ring, interpolation on the
+    // target's inverse plane pass
+    ctx->far_src_alone_of_dom.assign(nd, -1);
+    for (const FarSource &F : ctx->far_src) {
+        bool done = false;
+        for (FwdRing &R : ctx->fwd)
+            if (R.src == F.dom && !done) {
+                R.far_x = F.X;
+                R.far_ks = F.ks;
+                done = true;
+            }
+        if (!done) {
+            ctx->far_src_alone_of_dom[F.dom] = (int)ctx->far_src_alone.size();
+            ctx->far_src_alone.push_back(F);
+        }
+    }
+    ctx->far_planes = 0;
+    for (size_t k = 0; k < ctx->far_tgt.size(); ++k) {
+        const FarTarget &F = ctx->far_tgt[k];
+        bool done = false;
+        for (InvTarget &I : ctx->inv)
+            if (I.dom == F.dom && !done) {
+                I.far = ctx->d_far_tgt + k;
+                done = true;
+            }
+        if (!done) {
+            ctx->far_tgt_alone.push_back(F);
+            ctx->far_planes += F.nz;
+        }
+    }
+    if (!ctx->far_src_alone.empty() && (st = upload(ctx, &ctx->d_far_src_alone, ctx->far_src_alone))) return st;
+    if (!ctx->far_tgt_alone.empty() && (st = upload(ctx, &ctx->d_far_tgt_alone, ctx->far_tgt_alone))) return st;
+    return RP_OK;
+}
+
+// Launch-shape autotuning: time each consumer-warp variant of the TMA-fed MAC
+// on this plan (two launches after one warm-up, on the context stream, over
+// rings whose contents do not matter for timing) and keep the fastest per
+// size class.  Every variant reads the same data and sums in the same order.
+rp_status autotune_mac(rp_ctx *ctx)
+{
+    if (!ctx->tma || ctx->cfg.mac_warps) return RP_OK;
+    cudaEvent_t a = nullptr, b = nullptr;
+    RP_CUDA(ctx, cudaEventCreate(&a));
+    RP_CUDA(ctx, cudaEventCreate(&b));
+    rp_status st = RP_OK;
+    const long long step = ctx->max_lag;   // every (step - lag) is a valid slot
+    for (const LaunchGroup &g : ctx->inv_groups) {
+        if (g.cls <= 0 || st) continue;
+        const int slot = class_slot(g.cls), ntiles = g.blk1 - g.blk0;
+        float best = 1e30f;
+        for (int cw : {8, 12, 16}) {
+            auto go = [&] {
+                return launch_mac_tma(g.cls, cw, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries, ctx->d_maps,
+                                      ctx->nmaps, step, 0, ctx->mac_stages[slot], std::min(ntiles, ctx->sm_count),
+                                      ctx->d_err, ctx->stream);
+            };
+            cudaError_t e = go();
+            if (!e) e = cudaEventRecord(a, ctx->stream);
+            for (int r = 0; r < 2 && !e; ++r) e = go();
+            if (!e) e = cudaEventRecord(b, ctx->stream);
+            if (!e) e = cudaEventSynchronize(b);
+            float ms = 0.0f;
+            if (!e) e = cudaEventElapsedTime(&ms, a, b);
+            if (e) {
+                st = cuda_fail(ctx, e, "MAC autotuning");
+                break;
+            }
+            if (ms < best) {
+                best = ms;
+                ctx->mac_cw[slot] = cw;
+            }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (st) return st;
+    int flag = 0;
+    RP_CUDA(ctx, cudaMemcpy(&flag, ctx->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) return fail(ctx, RP_ERR_TIMEOUT, "a bounded device wait ran out during MAC autotuning");
     return RP_OK;
 }
 
@@ -595,10 +683,12 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (cfg->far_points != 0 && (cfg->far_points < 2 || cfg->far_points > kMaxFarPts)) return RP_ERR_ARG;
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
     }
+    if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
     rp_ctx *ctx = new rp_ctx();
     ctx->cfg = *cfg;
     if (ctx->cfg.far_points == 0) ctx->cfg.far_points = 4;
     if (ctx->cfg.far_batch == 0) ctx->cfg.far_batch = 32;
+    if (ctx->cfg.mac_warps) std::fill(std::begin(ctx->mac_cw), std::end(ctx->mac_cw), ctx->cfg.mac_warps);
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0;
     ctx->profile = (cfg->flags & RP_FLAG_PROFILE) != 0 && !ctx->plan_only;
@@ -1007,6 +1097,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     if ((st = dev_alloc(ctx, &ctx->d_err, 1))) return st;
     RP_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
     RP_CUDA(ctx, cudaDeviceSynchronize());
+    if ((st = autotune_mac(ctx))) return st;
     ctx->finalized = true;
     return RP_OK;
 }
@@ -1070,7 +1161,7 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "forward plane pass", [&] {
                  return launch_fwd_plane(g.cls, ctx->d_fwd, in, g.i0, g.i1, g.blk0, g.blk1 - g.blk0, ctx->smem_plane,
-                                         ctx->stream);
+                                         (int)(step % std::max(1, ctx->cfg.far_batch)), ctx->stream);
              })))
             return st;
     }
@@ -1094,9 +1185,17 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
         if (f0 >= 0) {
             const int batch = ctx->cfg.far_batch;
             const int slot = (int)(step % batch);
-            if ((st = timed_launch(ctx, RP_K_FAR_CONVERT, "far slice staging", [&] {
-                     return launch_far_convert(ctx->d_far_src + f0, f1 - f0, in, slot, ctx->far_max_n, ctx->stream);
-                 })))
+            int a0 = -1, a1 = -1;
+            for (int d = d0; d < d1; ++d) {
+                const int ai = ctx->far_src_alone_of_dom[d];
+                if (ai < 0) continue;
+                if (a0 < 0) a0 = ai;
+                a1 = ai + 1;
+            }
+            if (a0 >= 0 && (st = timed_launch(ctx, RP_K_FAR_CONVERT, "far slice staging", [&] {
+                                 return launch_far_convert(ctx->d_far_src_alone + a0, a1 - a0, in, slot,
+                                                           ctx->far_max_n, ctx->stream);
+                             })))
                 return st;
             if (slot == batch - 1) {
                 if (ctx->far_zeroed_step != step) {
@@ -1199,7 +1298,8 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         const int ntiles = g.blk1 - g.blk0;
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
                  if (ctx->tma && g.cls > 0)
-                     return launch_mac_tma(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries,
+                     return launch_mac_tma(g.cls, ctx->mac_cw[class_slot(g.cls)], ctx->d_inv, g.i0, g.i1, g.blk0,
+                                           ntiles, ctx->d_entries,
                                            ctx->d_maps, ctx->nmaps, step, clamp,
                                            ctx->mac_stages[class_slot(g.cls)],
                                            std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
@@ -1211,14 +1311,14 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     for (const LaunchGroup &g : ctx->inv_groups) {
         if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
                  return launch_inv_plane(g.cls, ctx->d_inv, g.i0, g.i1, g.blk2_0, out, g.blk2_1 - g.blk2_0,
-                                         ctx->smem_inv, inv_c, ctx->stream);
+                                         ctx->smem_inv, inv_c, step, ctx->stream);
              })))
             return st;
     }
-    if (!ctx->far_tgt.empty()) {
+    if (!ctx->far_tgt_alone.empty()) {
         if ((st = timed_launch(ctx, RP_K_FAR_INTERP, "far interpolation", [&] {
-                 return launch_far_interp(ctx->d_far_tgt, (int)ctx->far_tgt.size(), ctx->far_planes, out, step,
-                                          inv_c, ctx->stream);
+                 return launch_far_interp(ctx->d_far_tgt_alone, (int)ctx->far_tgt_alone.size(), ctx->far_planes, out,
+                                          step, inv_c, ctx->stream);
              })))
             return st;
     }
@@ -1339,7 +1439,8 @@ rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M
                              int splits, int device, void *stream)
 {
     if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 256 ||
-        (terms != 1 && terms != 3) || splits < 0 || splits > 4096)
+        (terms != 1 && terms != 3) || splits < 0 || splits > 4096 || (reinterpret_cast<uintptr_t>(d_D) & 15) ||
+        (reinterpret_cast<uintptr_t>(d_A) & 15) || (reinterpret_cast<uintptr_t>(d_B) & 15))
         return RP_ERR_ARG;
     if (cudaSetDevice(device) != cudaSuccess) {
         cudaGetLastError();
@@ -1428,6 +1529,9 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->mac_tma = ctx->tma ? 1 : 0;
     out->npairs_far = ctx->npairs_far;
     out->far_bytes = ctx->far_bytes;
+    out->mac_warps = 0;
+    for (const LaunchGroup &g : ctx->inv_groups)
+        if (g.cls > 0 && ctx->tma) out->mac_warps = ctx->mac_cw[class_slot(g.cls)];
     out->npairs_direct = 0;
     out->npairs_fft = 0;
     for (const PairPlan &p : ctx->pairs) {

@@ -197,7 +197,7 @@ struct FwdPlaneY {
 
 template <int M>
 __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restrict__ rings, IoPtrs in,
-                                                          int r0, int r1, int block_lo)
+                                                          int r0, int r1, int block_lo, int far_slot)
 {
     extern __shared__ float4 smem_f4[];
     float2 *sm = reinterpret_cast<float2 *>(smem_f4);
@@ -232,6 +232,16 @@ __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restric
     float2 *out = R.t1 + ((long long)f * kx * nz + z) * ay.M;
     FwdPlaneY<M> py{&lt, ay, ny, kx, nz, Q, qs, out, twy, lane, warp, nwarps};
     run_radix<M>(ay.R, py);
+    if (R.far_x) {
+        // far path: this plane as bf16 hi/lo into row (slot, field) of the batch matrix
+        __nv_bfloat16 *row = R.far_x + ((long long)far_slot * 4 + f) * 2 * R.far_ks + (long long)z * nx * ny;
+        for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+            const float v = __ldg(plane + i);
+            const __nv_bfloat16 hi = __float2bfloat16(v);
+            row[i] = hi;
+            row[R.far_ks + i] = __float2bfloat16(v - __bfloat162float(hi));
+        }
+    }
 }
 
 // ---------------------------------------------------------------- column passes
@@ -606,7 +616,7 @@ struct InvPlaneX {
 
 template <int M>
 __global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restrict__ tgts, int t0, int t1,
-                                                          int block_lo, OutPtrs out, float inv_c)
+                                                          int block_lo, OutPtrs out, float inv_c, long long step)
 {
     extern __shared__ float4 smem_f4[];
     float2 *sm = reinterpret_cast<float2 *>(smem_f4);
@@ -653,7 +663,37 @@ __global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restr
     __syncthreads();
     const long long N = (long long)nx * ny * nz;
     float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * N) + (long long)z * nx * ny;
-    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) dst[i] = O[i];
+    if (!T.far) {
+        for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) dst[i] = O[i];
+        return;
+    }
+    // far pairs: tensor-product Lagrange interpolation of this step's node
+    // coefficients (field f), contracted over z first
+    const FarTarget &F = *T.far;
+    float *cz = O + nx * ny;                                // [py][px]
+    float *ux = cz + kMaxFarPts * kMaxFarPts;               // [py][nx]
+    const float *c = F.cring + (step % F.depth) * (F.r * 4);
+    const int pxy = F.px * F.py;
+    for (int i = threadIdx.x; i < pxy; i += blockDim.x) {
+        float s = 0.0f;
+        for (int cc = 0; cc < F.pz; ++cc) s = fmaf(F.Lz[z * F.pz + cc], c[(cc * pxy + i) * 4 + f], s);
+        cz[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < F.py * nx; i += blockDim.x) {
+        const int bb = i / nx, x = i % nx;
+        float u = 0.0f;
+        for (int aa = 0; aa < F.px; ++aa) u = fmaf(F.Lx[x * F.px + aa], cz[bb * F.px + aa], u);
+        ux[i] = u;
+    }
+    __syncthreads();
+    const float scale = f == 0 ? 1.0f : inv_c;
+    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+        const int x = i % nx, y = i / nx;
+        float v = 0.0f;
+        for (int bb = 0; bb < F.py; ++bb) v = fmaf(__ldg(F.Ly + y * F.py + bb), ux[bb * nx + x], v);
+        dst[i] = fmaf(scale, v, O[i]);
+    }
 }
 
 #define RP_FOR_EACH_CLASS(X) X(0) X(32) X(48) X(64) X(96) X(128) X(192)
@@ -690,7 +730,9 @@ size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay)
 {
     const int kx = ax.M / 2 + 1;
     const int ps = ay.M | 1;
-    return sizeof(float2) * ((size_t)ax.M + ay.M + (size_t)kx * ps) + sizeof(float) * (size_t)nx * ny;
+    // + the far-path coefficients contracted over z, then over x
+    return sizeof(float2) * ((size_t)ax.M + ay.M + (size_t)kx * ps) + sizeof(float) * (size_t)nx * ny +
+           sizeof(float) * kMaxFarPts * (kMaxFarPts + (size_t)nx);
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
@@ -729,11 +771,11 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
     case M: KERNEL<M><<<nblocks, kThreads, smem, s>>>(__VA_ARGS__); break;
 
 cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
-                             int nblocks, size_t smem, cudaStream_t s)
+                             int nblocks, size_t smem, int far_slot, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_fwd_plane, d_rings, in, r0, r1, block_lo)
+#define X(M) RP_CASE(M, k_fwd_plane, d_rings, in, r0, r1, block_lo, far_slot)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -769,11 +811,11 @@ cudaError_t launch_mac_inv_column(int cls, const InvTarget *d_tgts, int t0, int 
 }
 
 cudaError_t launch_inv_plane(int cls, const InvTarget *d_tgts, int t0, int t1, int block_lo, const OutPtrs &out,
-                             int nblocks, size_t smem, float inv_c, cudaStream_t s)
+                             int nblocks, size_t smem, float inv_c, long long step, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_inv_plane, d_tgts, t0, t1, block_lo, out, inv_c)
+#define X(M) RP_CASE(M, k_inv_plane, d_tgts, t0, t1, block_lo, out, inv_c, step)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;

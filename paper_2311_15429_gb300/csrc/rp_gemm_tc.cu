@@ -112,19 +112,21 @@ __device__ __forceinline__ constexpr int tmem_cols()
     return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
 }
 
-// blockIdx.y selects a K range [k0, k1) of `kchunk` k-tiles (split-K); each
-// split writes its own M x N slice of D (D + split * split_stride).  With
-// `split3` the K range is three times the operand width `K`: k-tiles
-// [0, K) pair A[:, :K] with B[:, :K], [K, 2K) pair A[:, :K] with B[:, K:2K],
-// and [2K, 3K) pair A[:, K:2K] with B[:, :K] -- so that with A = [A_hi | A_lo]
-// and B = [B_hi | B_lo] the product is A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.
-template <int BN>
+// blockIdx.y selects a K range of `kchunk` k-tiles (split-K); each split
+// writes its own M x N slice of D (D + split * split_stride).  TERMS = 3:
+// the operands are [A_hi | A_lo] and [B_hi | B_lo] (each half K wide); one
+// stage holds the four tiles of a k-tile and the three products
+// A_hi B_hi^T, A_hi B_lo^T and A_lo B_hi^T accumulate into one tensor-memory
+// accumulator, so every operand byte is read once.
+template <int BN, int TERMS>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *D,
-                   int K, int ldd, int stages, int *err, int kchunk, long long split_stride, int split3)
+                   int K, int ldd, int stages, int *err, int kchunk, long long split_stride)
 {
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
-    constexpr int STAGE = A_BYTES + B_BYTES;       // multiple of 1024
+    constexpr int HALVES = TERMS == 3 ? 2 : 1;
+    constexpr int B_OFF = HALVES * A_BYTES;
+    constexpr int STAGE = HALVES * (A_BYTES + B_BYTES);   // multiple of 1024
     constexpr int TCOLS = tmem_cols<BN>();
     extern __shared__ __align__(1024) unsigned char smem[];
     uint64_t *full = reinterpret_cast<uint64_t *>(smem + (size_t)stages * STAGE);
@@ -135,7 +137,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * kBM;
-    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
+    const int kt_all = K / kBK;
     const int kt0 = blockIdx.y * kchunk;
     const int ktiles = max(0, min(kchunk, kt_all - kt0));
     D += (long long)blockIdx.y * split_stride;
@@ -176,13 +178,14 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             unsigned char *st = smem + (size_t)s * STAGE;
-            const int g = kt0 + kt;                  // global k-tile
-            const int w = K / kBK, part = g / w, kk = (g % w) * kBK;
-            const int ka = (split3 && part == 2) ? K + kk : kk;   // A_lo in the third part
-            const int kb = (split3 && part == 1) ? K + kk : kk;   // B_lo in the second part
+            const int k = (kt0 + kt) * kBK;
             bar_expect(&full[s], STAGE);
-            tma_2d(st, &mapA, split3 ? ka : g * kBK, m0, &full[s]);
-            tma_2d(st + A_BYTES, &mapB, split3 ? kb : g * kBK, 0, &full[s]);
+            tma_2d(st, &mapA, k, m0, &full[s]);
+            tma_2d(st + B_OFF, &mapB, k, 0, &full[s]);
+            if constexpr (TERMS == 3) {
+                tma_2d(st + A_BYTES, &mapA, K + k, m0, &full[s]);
+                tma_2d(st + B_OFF + B_BYTES, &mapB, K + k, 0, &full[s]);
+            }
         }
         // every copy issued has landed before the CTA may exit
         for (int r = kt > stages ? kt - stages : 0; r < kt; ++r)
@@ -198,10 +201,15 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
                 break;
             }
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-            const uint32_t a = su32(smem + (size_t)s * STAGE), b = a + A_BYTES;
+            const uint32_t a = su32(smem + (size_t)s * STAGE), b = a + B_OFF;
 #pragma unroll
-            for (int kk = 0; kk < kBK / 16; ++kk)   // 16 bf16 = 32 bytes along K per instruction
+            for (int kk = 0; kk < kBK / 16; ++kk) {   // 16 bf16 = 32 bytes along K per instruction
                 mma_bf16(tmem, desc_sw128(a + kk * 32), desc_sw128(b + kk * 32), ID, (kt | kk) ? 1u : 0u);
+                if constexpr (TERMS == 3) {
+                    mma_bf16(tmem, desc_sw128(a + kk * 32), desc_sw128(b + B_BYTES + kk * 32), ID, 1u);
+                    mma_bf16(tmem, desc_sw128(a + A_BYTES + kk * 32), desc_sw128(b + kk * 32), ID, 1u);
+                }
+            }
             mma_commit(&empty[s]);                  // the stage is free once these complete
         }
         mma_commit(done);                           // all issued MMAs complete
@@ -246,20 +254,37 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     }
 }
 
-// Z[i] = sum over splits of P[split][i]
-__global__ void k_split_reduce(const float *__restrict__ P, float *__restrict__ Z, long long n, int splits)
+// Z[i] = sum over splits of P[split][i], in a fixed order: a block covers 32
+// float4 outputs; its 8 thread groups take the splits g, g + 8, ... and the
+// 8 partial sums are added in group order.
+constexpr int kReduceGroups = 8;
+__global__ void __launch_bounds__(256) k_split_reduce(const float4 *__restrict__ P, float4 *__restrict__ Z,
+                                                      long long n4, int splits)
 {
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-        float s = 0.0f;
-        for (int k = 0; k < splits; ++k) s += P[(long long)k * n + i];
+    __shared__ float4 part[kReduceGroups][32];
+    const int g = threadIdx.x >> 5, j = threadIdx.x & 31;
+    const long long i = blockIdx.x * 32LL + j;
+    float4 s = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (i < n4)
+        for (int k = g; k < splits; k += kReduceGroups) {
+            const float4 v = __ldg(P + (long long)k * n4 + i);
+            s.x += v.x; s.y += v.y; s.z += v.z; s.w += v.w;
+        }
+    part[g][j] = s;
+    __syncthreads();
+    if (g == 0 && i < n4) {
+        for (int k = 1; k < kReduceGroups; ++k) {
+            s.x += part[k][j].x; s.y += part[k][j].y; s.z += part[k][j].z; s.w += part[k][j].w;
+        }
         Z[i] = s;
     }
 }
 
-template <int BN>
+template <int BN, int TERMS>
 size_t gemm_smem(int stages)
 {
-    return (size_t)stages * (kBM * kBK * 2 + BN * kBK * 2) + 8 * (2 * (size_t)stages + 1) + 16;
+    return (size_t)stages * (TERMS == 3 ? 2 : 1) * (kBM * kBK * 2 + BN * kBK * 2) + 8 * (2 * (size_t)stages + 1) +
+           16;
 }
 
 }  // namespace
@@ -281,31 +306,33 @@ bool encode_bf16_rows(void *encode_fn, CUtensorMap *map, const void *base, uint6
 // D (M x N fp32, row stride ldd) = A (M x K bf16) * B (N x K bf16)^T, with
 // M % 128 == 0, K % 64 == 0, N a multiple of 32 up to 256.  `splits` > 1
 // runs split-K: partial products go to `work` (splits x M x N floats) and a
-// reduction writes D (then ldd must be N).  `split3`: see k_gemm_bf16_tn.
+// reduction writes D (then ldd must be N).  `split3`: A and B are
+// [hi | lo] pairs (2K wide) and D is the three-product sum.
 cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB, float *D, int M, int N, int K,
                                 int ldd, int smem_optin, int *d_err, cudaStream_t s, int splits, float *work,
                                 int split3)
 {
     if (M % kBM || K % kBK || N % 32 || N <= 0 || N > 256 || splits < 1) return cudaErrorInvalidValue;
     if (splits > 1 && (!work || ldd != N)) return cudaErrorInvalidValue;
-    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
+    const int kt_all = K / kBK;
     const int kchunk = (kt_all + splits - 1) / splits;
     const dim3 grid(M / kBM, splits);
     float *out = splits > 1 ? work : D;
     const long long stride = splits > 1 ? (long long)M * N : 0;
+    const int halves = split3 ? 2 : 1;
+    int stages = (int)((smem_optin - 64) / (halves * (kBM * kBK * 2 + N * kBK * 2)));
+    if (stages > 8) stages = 8;
+    if (stages < 2) return cudaErrorInvalidValue;
+    cudaError_t e = cudaSuccess;
+    auto go = [&](auto kern, size_t smem) {
+        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (!e) kern<<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, stride);
+    };
 #define RP_GEMM_CASE(BN)                                                                             \
-    case BN: {                                                                                       \
-        int stages = (int)((smem_optin - 64) / (kBM * kBK * 2 + BN * kBK * 2));                      \
-        if (stages > 8) stages = 8;                                                                  \
-        if (stages < 2) return cudaErrorInvalidValue;                                                \
-        const size_t smem = gemm_smem<BN>(stages);                                                   \
-        cudaError_t e = cudaFuncSetAttribute(k_gemm_bf16_tn<BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                             (int)smem);                                             \
-        if (e) return e;                                                                             \
-        k_gemm_bf16_tn<BN><<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, \
-                                                             stride, split3);                        \
-        break;                                                                                       \
-    }
+    case BN:                                                                                         \
+        if (split3) go(k_gemm_bf16_tn<BN, 3>, gemm_smem<BN, 3>(stages));                             \
+        else go(k_gemm_bf16_tn<BN, 1>, gemm_smem<BN, 1>(stages));                                    \
+        break;
     switch (N) {
         RP_GEMM_CASE(32)
         RP_GEMM_CASE(64)
@@ -318,20 +345,24 @@ cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB
     default: return cudaErrorInvalidValue;
     }
 #undef RP_GEMM_CASE
-    cudaError_t e = cudaGetLastError();
+    if (e) return e;
+    e = cudaGetLastError();
     if (e || splits == 1) return e;
-    const long long n = (long long)M * N;
-    k_split_reduce<<<(int)std::min<long long>((n + 255) / 256, 4096), 256, 0, s>>>(work, D, n, splits);
+    const long long n4 = (long long)M * N / 4;   // N is a multiple of 32
+    k_split_reduce<<<(unsigned)((n4 + 31) / 32), 256, 0, s>>>(reinterpret_cast<const float4 *>(work),
+                                                               reinterpret_cast<float4 *>(D), n4, splits);
     return cudaGetLastError();
 }
 
-// Number of K splits that gives about two CTAs per SM, each with at least
+// Number of K splits that fills the SMs with one wave (one CTA per SM: the
+// stage ring takes most of the shared memory), each split with at least
 // `min_tiles` k-tiles.
 int gemm_splits(int M, int K, int split3, int sms, int min_tiles)
 {
+    (void)split3;
     const int mtiles = M / kBM;
-    const int kt_all = (split3 ? 3 : 1) * (K / kBK);
-    int splits = std::max(1, (2 * sms + mtiles - 1) / mtiles);
+    const int kt_all = K / kBK;
+    int splits = std::max(1, sms / mtiles);
     splits = std::min(splits, std::max(1, kt_all / std::max(1, min_tiles)));
     return splits;
 }

@@ -31,6 +31,8 @@ struct Axis {
 // One (source domain, padded size) spectral history ring and its forward
 // transform.  Spectra are stored [4 fields][spec_cells] complex64 (tile-major,
 // see spec_cells), kx in [0, mx/2].
+struct FarTarget;
+
 struct FwdRing {
     int nx, ny, nz;          // source grid
     Axis ax, ay, az;         // padded sizes
@@ -43,6 +45,9 @@ struct FwdRing {
     const float2 *tw_x, *tw_y, *tw_z;  // twiddles exp(-2 pi i j/M), j < M
     int plane0;              // first block of this ring in the plane-pass grid (4 fields x nz planes)
     int tile0;               // first block of this ring in the column-pass grid (kx x ky tiles)
+    __nv_bfloat16 *far_x;    // far-path batch matrix [4 batch][2 ks] of this source (one ring per source), or null
+    int far_ks;              // its half row width
+    int pad_;
 };
 
 // One (source, lag) term of a target's spectral sum: G_m (kernel spectrum of
@@ -74,6 +79,7 @@ struct InvTarget {
     int plane0;              // first block in the plane grid
     int has_direct;          // direct pairs add onto this target afterwards
     int pad_;
+    const FarTarget *far;    // far-path coefficients interpolated onto this target here, or null
 };
 
 // A (target, source) pair evaluated by the direct retarded sum.
@@ -175,14 +181,15 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
                              const int *h_block0, int nblocks, long long step,
                              cudaStream_t s);
 cudaError_t launch_fwd_plane(int size_class, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
-                             int block_lo, int nblocks, size_t smem, cudaStream_t s);
+                             int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s);
 cudaError_t launch_fwd_column(int size_class, const FwdRing *d_rings, int r0, int r1, int block_lo,
                               int nblocks, size_t smem, long long step, cudaStream_t s);
 cudaError_t launch_mac_inv_column(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
                                   const MacEntry *d_entries, int nblocks, size_t smem, long long step,
                                   int clamp, cudaStream_t s);
 cudaError_t launch_inv_plane(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
-                             const OutPtrs &out, int nblocks, size_t smem, float inv_c, cudaStream_t s);
+                             const OutPtrs &out, int nblocks, size_t smem, float inv_c, long long step,
+                             cudaStream_t s);
 cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair *d_pairs,
                           const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
                           float inv_cdt, float inv_c, cudaStream_t s);
@@ -191,8 +198,8 @@ cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair
 int mac_tma_stages(int M, int smem_optin);
 size_t mac_tma_smem(int M, int nstages);
 cudaError_t open_mac_tma_smem_limit(int max_optin);
-cudaError_t launch_mac_tma(int cls, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
-                           const MacEntry *d_entries, const struct CUtensorMap_st *d_maps, int nmaps,
+cudaError_t launch_mac_tma(int cls, int consumer_warps, const InvTarget *d_tgts, int t0, int t1, int tile_lo,
+                           int ntiles, const MacEntry *d_entries, const struct CUtensorMap_st *d_maps, int nmaps,
                            long long step, int clamp, int nstages, int grid, int *d_err, cudaStream_t s);
 
 // tcgen05 bf16 GEMM (rp_gemm_tc.cu): D (M x N fp32) = A (M x K) * B (N x K)^T

@@ -12,7 +12,8 @@
 //     a ring of shared-memory stages, each stage guarded by a "full" mbarrier
 //     (transaction bytes) and an "empty" mbarrier (one arrival per consumer
 //     warp);
-//   * the other 16 warps are consumers: they multiply-accumulate in registers,
+//   * the other CW warps (8, 12 or 16, picked per size class by timing the
+//     variants on the context's own plan) are consumers: they multiply-accumulate in registers,
 //     then write the tile to a separate shared-memory region for the column
 //     FFT (two columns per warp at a time), so the producer keeps prefetching
 //     the next tile's operands meanwhile.
@@ -31,8 +32,6 @@ namespace rp {
 
 namespace {
 
-constexpr int kConsumerWarps = 16;
-constexpr int kTmaThreads = (kConsumerWarps + 1) * 32;
 constexpr long long kWaitLimit = 4000000000LL;   // SM clock cycles (about 2 s)
 constexpr int kMaxStages = 24;
 
@@ -77,16 +76,6 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
     return true;
 }
 
-__device__ __forceinline__ void tma_load_4d(void *dst, const CUtensorMap *map, int c0, int c1, int c2, int c3,
-                                            uint64_t *bar)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(smem_u32(bar))
-        : "memory");
-}
-
 // Contiguous copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
 // by the bulk-copy engine, completing on `bar`.
 __device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
@@ -108,15 +97,18 @@ __device__ __forceinline__ int owner(const T *arr, int lo, int hi, int b, int T:
     return lo;
 }
 
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kConsumerWarps * 32) : "memory"); }
+template <int CW>
+__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(CW * 32) : "memory"); }
 
-template <int M>
-__global__ void __launch_bounds__(kTmaThreads, 1)
+// M: padded FFT size of the class; CW: consumer warps (the block has CW + 1).
+template <int M, int CW>
+__global__ void __launch_bounds__((CW + 1) * 32, 1)
     k_mac_tma(const InvTarget *__restrict__ tgts, int t0, int t1, int tile_lo, int ntiles,
               const MacEntry *__restrict__ entries, const CUtensorMap *__restrict__ maps, int nmaps, long long step,
               int clamp, int nstages, int *err)
 {
     constexpr int STAGE = M * 128;                  // one M x 16 complex tile
+    constexpr int kConsumerWarps = CW;
     constexpr int RSTEP = kConsumerWarps * 32 / 8;   // rows covered by one pass of the consumers
     constexpr int ROWS = (M + RSTEP - 1) / RSTEP;
     constexpr int NTY = M / kTileY;
@@ -295,7 +287,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 d[1] = make_float2(a[i][f].z, a[i][f].w);
             }
         }
-        consumer_sync();
+        consumer_sync<CW>();
         {
             // 64 columns; each warp transforms two at a time (independent
             // instruction streams for the scheduler to interleave)
@@ -329,7 +321,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
                 __syncwarp();
             }
         }
-        consumer_sync();
+        consumer_sync<CW>();
         const int nz = T.nz;
         const long long t2_field = (long long)(M / 2 + 1) * nz * M;
         float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
@@ -340,7 +332,7 @@ __global__ void __launch_bounds__(kTmaThreads, 1)
             *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
                 make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
         }
-        consumer_sync();   // the FFT tile is rewritten by the next tile
+        consumer_sync<CW>();   // the FFT tile is rewritten by the next tile
     }
 }
 
@@ -365,30 +357,39 @@ size_t mac_tma_smem(int M, int nstages)
 cudaError_t open_mac_tma_smem_limit(int max_optin)
 {
     cudaError_t e;
-#define X(M)                                                                                         \
-    if ((e = cudaFuncSetAttribute(k_mac_tma<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
+#define X(M)                                                                                            \
+    if ((e = cudaFuncSetAttribute(k_mac_tma<M, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
         return e;
     RP_TMA_CLASSES(X)
 #undef X
     return cudaSuccess;
 }
 
-cudaError_t launch_mac_tma(int cls, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
+cudaError_t launch_mac_tma(int cls, int cw, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
                            const MacEntry *d_entries, const CUtensorMap *d_maps, int nmaps, long long step, int clamp,
                            int nstages, int grid, int *d_err, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
+    if (cw != 8 && cw != 12 && cw != 16) return cudaErrorInvalidValue;
     const size_t smem = mac_tma_smem(cls, nstages);
+    const int threads = (cw + 1) * 32;
+#define RP_GO(M, CW)                                                                                      \
+    k_mac_tma<M, CW><<<grid, threads, smem, s>>>(d_tgts, t0, t1, tile_lo, ntiles, d_entries, d_maps, nmaps, step, \
+                                                 clamp, nstages, d_err)
     switch (cls) {
-#define X(M)                                                                                                  \
-    case M:                                                                                                   \
-        k_mac_tma<M><<<grid, kTmaThreads, smem, s>>>(d_tgts, t0, t1, tile_lo, ntiles, d_entries, d_maps, nmaps, \
-                                                      step, clamp, nstages, d_err);                                 \
+#define X(M)                                                                                            \
+    case M:                                                                                             \
+        if (cw == 8) RP_GO(M, 8);                                                                       \
+        else if (cw == 12) RP_GO(M, 12);                                                                \
+        else RP_GO(M, 16);                                                                              \
         break;
         RP_TMA_CLASSES(X)
 #undef X
     default: return cudaErrorInvalidValue;
     }
+#undef RP_GO
     return cudaGetLastError();
 }
 

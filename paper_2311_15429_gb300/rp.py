@@ -27,8 +27,8 @@ MAX_DOMAINS = 256
 class rp_config(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("history_depth", ctypes.c_int),
                 ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("far_points", ctypes.c_int),
-                ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int),
-                ("reserved", ctypes.c_int * 5)]
+                ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int), ("mac_warps", ctypes.c_int),
+                ("reserved", ctypes.c_int * 4)]
 
 
 class rp_pair_info_t(ctypes.Structure):
@@ -43,7 +43,7 @@ class rp_stats(ctypes.Structure):
                 ("step", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
                 ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
-                ("far_bytes", ctypes.c_longlong), ("reserved", ctypes.c_int * 4)]
+                ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class RPError(RuntimeError):
@@ -151,10 +151,10 @@ def rp_last_error(ctx) -> str:
 
 def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
               flags: int = 0, device: int = 0, stream=None, far_distance: float = 0.0,
-              far_points: int = 0, far_batch: int = 0):
+              far_points: int = 0, far_batch: int = 0, mac_warps: int = 0):
     """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream (NULL without torch)."""
-    cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch)
+    cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch, mac_warps)
     if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
         try:
             import torch
@@ -288,11 +288,12 @@ class RetardedPotentials:
 
     def __init__(self, domains, c: float, dt: float, history_depth: int = 0,
                  mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
-                 far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0):
+                 far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0,
+                 mac_warps: int = 0):
         import torch
         self.domains = list(domains)
         self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
-                             far_points, far_batch)
+                             far_points, far_batch, mac_warps)
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)

@@ -12,7 +12,7 @@ def histories(sources, j0, j1, dt):
 
 
 def run_library(domains, c, dt, hists, j0, eval_at, mode=rp.RP_MODE_FFT, flags=0, depth=0,
-                push="all"):
+                push="all", mac_warps=0):
     """Push every sample of ``hists`` (time index j0 + i) and evaluate at the
     time indices in ``eval_at``.  Returns {time index: [domain][4][N] float32}."""
     import torch
@@ -20,7 +20,8 @@ def run_library(domains, c, dt, hists, j0, eval_at, mode=rp.RP_MODE_FFT, flags=0
     T = hists[0].shape[0]
     eval_at = set(eval_at)
     out = {}
-    with rp.RetardedPotentials(domains, c, dt, history_depth=depth, mode=mode, flags=flags) as lib:
+    with rp.RetardedPotentials(domains, c, dt, history_depth=depth, mode=mode, flags=flags,
+                               mac_warps=mac_warps) as lib:
         for i in range(T):
             j = j0 + i
             slices = [torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists]

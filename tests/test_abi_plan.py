@@ -184,3 +184,16 @@ def test_no_gpu_create_fails_cleanly():
     with pytest.raises(rp.RPError) as e:
         rp.rp_create(137.0, 0.05, stream=0)
     assert e.value.status == rp.RP_ERR_CUDA
+
+
+def test_config_validation():
+    """Out-of-range configuration fields are refused at rp_create."""
+    bad = [dict(mac_warps=10), dict(mac_warps=-8), dict(mode=rp.RP_MODE_LOWRANK, far_distance=0.0),
+           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=12),
+           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9)]
+    for kw in bad:
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, **kw)
+        assert e.value.status == rp.RP_ERR_ARG, kw
+    for cw in (0, 8, 12, 16):
+        rp.rp_destroy(rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_warps=cw))

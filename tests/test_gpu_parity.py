@@ -242,3 +242,21 @@ def test_contexts_coexist():
     finally:
         a.close()
         b.close()
+
+
+@pytest.mark.parametrize("n", [16, 24, 48])
+def test_mac_variants_agree_bitwise(n):
+    """The consumer-warp variants of the TMA-fed MAC (8, 12, 16) sum the same
+    terms in the same order: bitwise equal outputs, and the autotuned choice
+    is one of them.  Padded sizes 32, 48 and 96."""
+    w = synth.two_domain(n, 0.25, 3.0 * n * 0.25, f"variants{n}", offset=(1.0, 0.5))
+    T = 10
+    hists = histories(w.sources, 0, T, w.dt)
+    outs = {cw: run_library(w.domains, w.c, w.dt, hists, 0, [T - 1], mac_warps=cw) for cw in (8, 12, 16)}
+    for cw in (8, 12):
+        for t in range(2):
+            assert np.array_equal(outs[cw][T - 1][t], outs[16][T - 1][t]), (cw, t)
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        q = lib.query()
+        assert q["mac_tma"] == 1 and q["mac_warps"] in (8, 12, 16), q
+    _score(w.domains, hists, 0, w.c, w.dt, outs[12], nodes=[np.arange(0, d.N, 97) for d in w.domains])
