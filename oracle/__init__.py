@@ -8,6 +8,12 @@ time interpolation of Eq. 7; Eqs. 11-12 give the same number), written in C
 the CUDA library neither links nor imports it, and it shares no code with it.
 
 Parity status per function:
+  * ``eval_positions`` -- the same sums at arbitrary points; pinned by the
+    static Coulomb limit and the retarded phase lag at far points, and by
+    agreement with ``eval_points`` where the points are grid nodes of a
+    domain with no own source (``tests/test_oracle_learned.py``).
+  * ``learned`` -- the learned far field's steps (moments, canonical frame,
+    delay window, network, re-interpolation); see that module's header.
   * ``eval_points`` -- pinned by the closed forms and brute-force forms in
     ``tests/test_oracle_pins.py`` (static Coulomb limit of a Gaussian, the
     O(h^2) self-cell constant, retarded phase lag of a breathing monopole,
@@ -63,6 +69,12 @@ def _bind(path: str):
         ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
         ctypes.c_double, ctypes.c_double, ctypes.c_int,
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rpo_eval_positions.restype = ctypes.c_int
+    lib.rpo_eval_positions.argtypes = [
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+        ctypes.c_double, ctypes.c_double, ctypes.c_int,
+        ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.rpo_cube_average_constant.restype = ctypes.c_double
     lib.rpo_cube_average_constant.argtypes = []
     return lib
@@ -113,6 +125,34 @@ def eval_points(origins: np.ndarray, ns: np.ndarray, hs: Sequence[float],
                       ctypes.cast(ptrs, ctypes.c_void_p), int(is_f64), int(hist_first), int(T),
                       float(c), float(dt), int(bool(clamp)), int(target), int(step),
                       int(nodes.size), nodes.ctypes.data, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc)
+    return out
+
+
+def eval_positions(origins, ns, hs, hists, hist_first: int, c: float, dt: float, step: int,
+                   positions, clamp: bool = False) -> np.ndarray:
+    """Retarded (phi, Ax, Ay, Az) at arbitrary points ``positions`` [P][3]
+    (bohr) from every domain, at time index ``step``.  Returns [P][4] float64."""
+    lib = _load()
+    ndom = len(hists)
+    origins = np.ascontiguousarray(origins, dtype=np.float64).reshape(ndom, 3)
+    ns = np.ascontiguousarray(ns, dtype=np.int32).reshape(ndom, 3)
+    hs = np.ascontiguousarray(hs, dtype=np.float64).reshape(ndom)
+    is_f64 = hists[0].dtype == np.float64
+    want = np.float64 if is_f64 else np.float32
+    T = hists[0].shape[0]
+    arrs = [np.ascontiguousarray(a, dtype=want) for a in hists]
+    for d, a in enumerate(arrs):
+        if a.shape != (T, 4, int(np.prod(ns[d]))):
+            raise ValueError(f"history of domain {d} has shape {a.shape}")
+    ptrs = (ctypes.c_void_p * ndom)(*[a.ctypes.data for a in arrs])
+    pos = np.ascontiguousarray(positions, dtype=np.float64).reshape(-1, 3)
+    out = np.zeros((pos.shape[0], 4), dtype=np.float64)
+    rc = lib.rpo_eval_positions(ndom, origins.ctypes.data, ns.ctypes.data, hs.ctypes.data,
+                                ctypes.cast(ptrs, ctypes.c_void_p), int(is_f64), int(hist_first), int(T),
+                                float(c), float(dt), int(bool(clamp)), int(step), int(pos.shape[0]),
+                                pos.ctypes.data, out.ctypes.data)
     if rc != OK:
         raise OracleError(rc)
     return out

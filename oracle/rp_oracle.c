@@ -190,5 +190,63 @@ int rpo_eval(int ndom, const double *origin, const int *nn, const double *h,
     return RPO_OK;
 }
 
+/*
+ * rpo_eval_positions -- the same retarded sums at arbitrary points (not grid
+ * nodes): every node of every domain is a source with weight h_n^3 / R and
+ * the hat-interpolated sample at the retarded time (Eqs. 2, 7, 8).  There is
+ * no self cell; a point on a source node is RPO_ERR_COINCIDENT.
+ *
+ *   pos[3*p]        position of point p (bohr)
+ *   out[4*npos]     phi, Ax, Ay, Az per point (A with the 1/c factor)
+ *
+ * Other arguments as for rpo_eval.
+ */
+int rpo_eval_positions(int ndom, const double *origin, const int *nn, const double *h,
+                       const void *const *hist, int hist_is_f64, int hist_first, int hist_len,
+                       double c, double dt, int clamp, int step, int npos, const double *pos, double *out)
+{
+    if (ndom <= 0 || npos < 0 || hist_len <= 0 || !(dt > 0.0) || !(c > 0.0))
+        return RPO_ERR_ARG;
+    for (int p = 0; p < npos; ++p) {
+        const double rx = pos[3 * p + 0], ry = pos[3 * p + 1], rz = pos[3 * p + 2];
+        rpo_acc acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};
+        for (int n = 0; n < ndom; ++n) {
+            const int sx = nn[3 * n + 0], sy = nn[3 * n + 1], sz = nn[3 * n + 2];
+            const long long Ns = (long long)sx * sy * sz;
+            const double hs = h[n];
+            const double vol = hs * hs * hs;
+            for (long long q = 0; q < Ns; ++q) {
+                int jx = (int)(q % sx), jy = (int)((q / sx) % sy), jz = (int)(q / ((long long)sx * sy));
+                double dx = rx - (origin[3 * n + 0] + hs * jx);
+                double dy = ry - (origin[3 * n + 1] + hs * jy);
+                double dz = rz - (origin[3 * n + 2] + hs * jz);
+                double R = sqrt(dx * dx + dy * dy + dz * dz);
+                if (R == 0.0)
+                    return RPO_ERR_COINCIDENT;
+                double tau = R / (c * dt);
+                double m = floor(tau);
+                double w = tau - m;
+                long long j0 = (long long)step - (long long)m;
+                for (int f = 0; f < 4; ++f) {
+                    double a, b = 0.0;
+                    int e = fetch(hist, hist_is_f64, hist_first, hist_len, clamp, n, Ns, f, q, j0, &a);
+                    if (e)
+                        return e;
+                    if (w > 0.0) {
+                        e = fetch(hist, hist_is_f64, hist_first, hist_len, clamp, n, Ns, f, q, j0 - 1, &b);
+                        if (e)
+                            return e;
+                    }
+                    acc_add(&acc[f], vol * ((1.0 - w) * a + w * b) / R);
+                }
+            }
+        }
+        out[4 * p + 0] = acc_value(&acc[0]);
+        for (int f = 1; f < 4; ++f)
+            out[4 * p + f] = acc_value(&acc[f]) / c;
+    }
+    return RPO_OK;
+}
+
 /* The value of C used above, for the tests that pin it. */
 double rpo_cube_average_constant(void) { return cube_average_constant(); }
