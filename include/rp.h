@@ -270,9 +270,16 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
 rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device,
                        void *stream);
 
+/* Operand types of rp_gemm_tn. */
+#define RP_DTYPE_BF16 0
+#define RP_DTYPE_FP16 1
+
 /*
- * rp_gemm_bf16_split -- the same contraction in the two forms the far field
- * uses (Eq. 11 applied through skeleton rows, as for rp_gemm_bf16).
+ * rp_gemm_tn -- the tensor-core contraction in the forms the far field and
+ * the learned far field use (Eq. 11 applied through skeleton rows, as for
+ * rp_gemm_bf16; and the layers of the learned stand-in's network).
+ *   dtype: RP_DTYPE_BF16 or RP_DTYPE_FP16 -- both operands of that type
+ *          (tcgen05.mma kind::f16, fp32 accumulation in tensor memory).
  *   terms = 1: A is M x K, B is N x K; D = A B^T.
  *   terms = 3: A is M x 2K holding [A_hi | A_lo] per row and B is N x 2K
  *              holding [B_hi | B_lo]; D = A_hi B_hi^T + A_hi B_lo^T +
@@ -280,17 +287,56 @@ rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
  *              less the lo*lo term (about 16 significant bits per operand).
  * For terms = 3 each pipeline stage holds the four tiles of a K step and the
  * three products accumulate in one fp32 accumulator, so every operand byte
- * is read once.  `splits` cuts the K range into that many chunks run by
- * separate CTAs whose fp32 partial products are then summed in a fixed order
- * (deterministic); 0 picks the count the far path uses (one wave of CTAs,
- * one per SM).  The partial products need splits x M x N floats of device memory,
- * which this call allocates and frees.  Shapes as for rp_gemm_bf16; D is
- * M x N fp32.  Synchronous.  Errors as for rp_gemm_bf16; RP_ERR_ARG also for
- * terms other than 1 or 3, splits outside [0, 4096] and pointers that are not
- * 16-byte aligned.
+ * is read once.  N may exceed 256: it runs in column tiles of the widest
+ * multiple of 32 up to 256 that divides N.  `splits` cuts the K range into
+ * that many chunks run by separate CTAs whose fp32 partial products are then
+ * summed in a fixed order (deterministic); 0 picks the count the far path
+ * uses (one wave of CTAs, one per SM).  The partial products need
+ * splits x M x N floats of device memory, which this call allocates and
+ * frees.  Shapes: M a multiple of 128, K of 64, N of 32 (N <= 4096); D is
+ * M x N fp32 row-major, all device pointers on `device`.  Synchronous.
+ * RP_ERR_ARG for other shapes, an unknown dtype, terms other than 1 or 3,
+ * splits outside [0, 4096] or pointers that are not 16-byte aligned;
+ * RP_ERR_CUDA if the device or the tensor-map encoder is unusable;
+ * RP_ERR_TIMEOUT if a bounded device wait ran out.
  */
-rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int terms,
-                             int splits, int device, void *stream);
+rp_status rp_gemm_tn(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int dtype, int terms,
+                     int splits, int device, void *stream);
+
+/*
+ * Learned far field: the network on its own.
+ *
+ * The learned stand-in for far pairs (north of the low-rank path; see
+ * rp_train_far_model) is a bias-free multilayer perceptron
+ *     x -> W1 -> leaky -> W2 -> leaky -> W3 -> leaky -> W4 -> y
+ * with leaky(z) = z for z >= 0 and 0.2 z otherwise, fp16 weights and
+ * activations as tensor-core operands (tcgen05.mma kind::f16) and fp32
+ * accumulation.  Its inputs are a source's monopole, dipole and quadrupole
+ * moments over a delay window and its outputs the potentials at 64 nodes of
+ * the target (the multipole description of the far interaction, Sec. IV).
+ * These three calls exist so that the network's kernels can be checked on
+ * their own; all are synchronous and allocate and free their own device
+ * memory on `device`.
+ *
+ * rp_mlp_layout -- writes the five layer widths (input, three hidden,
+ * output) to dims[5] if dims is not NULL; returns the number of weights.
+ * Weights are passed as one float array: W1 [d1][d0], W2 [d2][d1],
+ * W3 [d3][d2], W4 [d4][d3], each row-major (output index major).
+ *
+ * rp_mlp_forward -- y[rows][d4] = network(x[rows][d0]) for host arrays, with
+ * rows a multiple of 128.  Weights and inputs are rounded to fp16 on the way
+ * in.  RP_ERR_ARG for NULL pointers or rows, RP_ERR_CUDA on a device error,
+ * RP_ERR_TIMEOUT if a bounded device wait ran out.
+ *
+ * rp_mlp_grad -- the loss L = (1 / 2 rows) sum |y - t|^2 over the rows
+ * (t: host targets [rows][d4]) and dL/dW for every weight (host g, the
+ * weight layout), from the network's own backward pass.  Errors as for
+ * rp_mlp_forward.
+ */
+int rp_mlp_layout(int *dims);
+rp_status rp_mlp_forward(const float *h_w, const float *h_x, int rows, float *h_y, int device);
+rp_status rp_mlp_grad(const float *h_w, const float *h_x, const float *h_t, int rows, float *h_g, float *h_loss,
+                      int device);
 
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);

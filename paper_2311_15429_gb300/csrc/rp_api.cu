@@ -1435,10 +1435,11 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
     return RP_OK;
 }
 
-rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int terms,
-                             int splits, int device, void *stream)
+rp_status rp_gemm_tn(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int dtype, int terms,
+                     int splits, int device, void *stream)
 {
-    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 256 ||
+    if (!d_A || !d_B || !d_D || M <= 0 || N <= 0 || K <= 0 || M % 128 || K % 64 || N % 32 || N > 4096 ||
+        (dtype != RP_DTYPE_BF16 && dtype != RP_DTYPE_FP16) ||
         (terms != 1 && terms != 3) || splits < 0 || splits > 4096 || (reinterpret_cast<uintptr_t>(d_D) & 15) ||
         (reinterpret_cast<uintptr_t>(d_A) & 15) || (reinterpret_cast<uintptr_t>(d_B) & 15))
         return RP_ERR_ARG;
@@ -1456,7 +1457,7 @@ rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M
     const int width = terms == 3 ? 2 * K : K;
     CUtensorMap ma, mb;
     if (!encode_bf16_rows(fn, &ma, d_A, (uint64_t)M, (uint64_t)width, 128) ||
-        !encode_bf16_rows(fn, &mb, d_B, (uint64_t)N, (uint64_t)width, (uint32_t)N))
+        !encode_bf16_rows(fn, &mb, d_B, (uint64_t)N, (uint64_t)width, (uint32_t)gemm_tile_n(N)))
         return RP_ERR_ARG;
     int optin = 0, sms = 0;
     int *d_err = nullptr;
@@ -1475,7 +1476,8 @@ rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M
         return RP_ERR_CUDA;
     }
     int flag = 0;
-    cudaError_t e = launch_gemm_bf16_tn(ma, mb, d_D, M, N, K, N, optin, d_err, s, splits, work, terms == 3);
+    cudaError_t e = launch_gemm_bf16_tn(ma, mb, d_D, M, N, K, N, optin, d_err, s, splits, work, terms == 3,
+                                        dtype == RP_DTYPE_FP16);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e == cudaSuccess) e = cudaMemcpy(&flag, d_err, sizeof(int), cudaMemcpyDeviceToHost);
     cudaFree(d_err);
@@ -1489,7 +1491,8 @@ rp_status rp_gemm_bf16_split(const void *d_A, const void *d_B, float *d_D, int M
 
 rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int N, int K, int device, void *stream)
 {
-    return rp_gemm_bf16_split(d_A, d_B, d_D, M, N, K, 1, 1, device, stream);
+    if (N > 256) return RP_ERR_ARG;
+    return rp_gemm_tn(d_A, d_B, d_D, M, N, K, RP_DTYPE_BF16, 1, 1, device, stream);
 }
 
 rp_status rp_sync(rp_ctx *ctx)

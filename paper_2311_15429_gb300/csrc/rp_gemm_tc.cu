@@ -85,10 +85,12 @@ __device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
     return d;
 }
 
-// Instruction descriptor, kind::f16: D fp32, A and B bf16, both K-major, M = 128.
-__host__ __device__ constexpr uint32_t idesc_bf16(int BN)
+// Instruction descriptor, kind::f16: D fp32, A and B both bf16 (f16 = 0) or
+// both fp16 (f16 = 1), both K-major, M = 128, N = BN.
+__host__ __device__ constexpr uint32_t idesc_16bit(int BN, int f16)
 {
-    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+    return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) |
+           ((uint32_t)(kBM >> 4) << 24);
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc)
@@ -121,7 +123,7 @@ __device__ __forceinline__ constexpr int tmem_cols()
 template <int BN, int TERMS>
 __global__ void __launch_bounds__(kGemmThreads, 1)
     k_gemm_bf16_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, float *D,
-                   int K, int ldd, int stages, int *err, int kchunk, long long split_stride)
+                   int K, int ldd, int stages, int *err, int kchunk, long long split_stride, uint32_t idesc)
 {
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
     constexpr int HALVES = TERMS == 3 ? 2 : 1;
@@ -140,7 +142,8 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
     const int kt_all = K / kBK;
     const int kt0 = blockIdx.y * kchunk;
     const int ktiles = max(0, min(kchunk, kt_all - kt0));
-    D += (long long)blockIdx.y * split_stride;
+    const int n0 = blockIdx.z * BN;                 // column tile
+    D += (long long)blockIdx.y * split_stride + n0;
     // the swizzled operand descriptors assume 1024-byte aligned stages
     if (su32(smem) & 1023u) {
         if (threadIdx.x == 0) atomicExch(err, 2);
@@ -181,10 +184,10 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             const int k = (kt0 + kt) * kBK;
             bar_expect(&full[s], STAGE);
             tma_2d(st, &mapA, k, m0, &full[s]);
-            tma_2d(st + B_OFF, &mapB, k, 0, &full[s]);
+            tma_2d(st + B_OFF, &mapB, k, n0, &full[s]);
             if constexpr (TERMS == 3) {
                 tma_2d(st + A_BYTES, &mapA, K + k, m0, &full[s]);
-                tma_2d(st + B_OFF + B_BYTES, &mapB, K + k, 0, &full[s]);
+                tma_2d(st + B_OFF + B_BYTES, &mapB, K + k, n0, &full[s]);
             }
         }
         // every copy issued has landed before the CTA may exit
@@ -192,7 +195,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             if (!bar_wait(&full[r % stages], (r / stages) & 1)) atomicExch(err, 1);
     } else if (warp == 1 && lane == 0) {
         // ---------------------------------------------------------------- MMA issue
-        constexpr uint32_t ID = idesc_bf16(BN);
+        const uint32_t ID = idesc;
         for (int kt = 0; kt < ktiles; ++kt) {
             const int s = kt % stages;
             if (*abort_flag || !bar_wait(&full[s], (kt / stages) & 1)) {
@@ -303,37 +306,51 @@ bool encode_bf16_rows(void *encode_fn, CUtensorMap *map, const void *base, uint6
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// D (M x N fp32, row stride ldd) = A (M x K bf16) * B (N x K bf16)^T, with
-// M % 128 == 0, K % 64 == 0, N a multiple of 32 up to 256.  `splits` > 1
-// runs split-K: partial products go to `work` (splits x M x N floats) and a
-// reduction writes D (then ldd must be N).  `split3`: A and B are
-// [hi | lo] pairs (2K wide) and D is the three-product sum.
+// D (M x N fp32, row stride ldd) = A (M x K) * B (N x K)^T, 16-bit operands
+// (bf16, or fp16 with `f16`), with M % 128 == 0, K % 64 == 0 and N a
+// multiple of 32; N above 256 runs in column tiles of the largest width
+// <= 256 that divides it (the B map's box must be that many rows).
+// `splits` > 1 runs split-K: partial products go to `work`
+// (splits x M x N floats) and a reduction writes D (then ldd must be N).
+// `split3`: A and B are [hi | lo] pairs (2K wide) and D is the
+// three-product sum.
+int gemm_tile_n(int N)
+{
+    if (N <= 0 || N % 32) return 0;
+    for (int bn = std::min(N, 256); bn >= 32; bn -= 32)
+        if (N % bn == 0) return bn;
+    return 0;
+}
+
 cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB, float *D, int M, int N, int K,
                                 int ldd, int smem_optin, int *d_err, cudaStream_t s, int splits, float *work,
-                                int split3)
+                                int split3, int f16)
 {
-    if (M % kBM || K % kBK || N % 32 || N <= 0 || N > 256 || splits < 1) return cudaErrorInvalidValue;
+    const int BNv = gemm_tile_n(N);
+    if (M % kBM || K % kBK || !BNv || splits < 1) return cudaErrorInvalidValue;
     if (splits > 1 && (!work || ldd != N)) return cudaErrorInvalidValue;
     const int kt_all = K / kBK;
     const int kchunk = (kt_all + splits - 1) / splits;
-    const dim3 grid(M / kBM, splits);
+    const dim3 grid(M / kBM, splits, N / BNv);
     float *out = splits > 1 ? work : D;
     const long long stride = splits > 1 ? (long long)M * N : 0;
     const int halves = split3 ? 2 : 1;
-    int stages = (int)((smem_optin - 64) / (halves * (kBM * kBK * 2 + N * kBK * 2)));
+    int stages = (int)((smem_optin - 64) / (halves * (kBM * kBK * 2 + BNv * kBK * 2)));
     if (stages > 8) stages = 8;
     if (stages < 2) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
-    auto go = [&](auto kern, size_t smem) {
+    auto go = [&](auto kern, size_t smem, int bn) {
         e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (!e) kern<<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, stride);
+        if (!e)
+            kern<<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, stride,
+                                                  idesc_16bit(bn, f16));
     };
 #define RP_GEMM_CASE(BN)                                                                             \
     case BN:                                                                                         \
-        if (split3) go(k_gemm_bf16_tn<BN, 3>, gemm_smem<BN, 3>(stages));                             \
-        else go(k_gemm_bf16_tn<BN, 1>, gemm_smem<BN, 1>(stages));                                    \
+        if (split3) go(k_gemm_bf16_tn<BN, 3>, gemm_smem<BN, 3>(stages), BN);                         \
+        else go(k_gemm_bf16_tn<BN, 1>, gemm_smem<BN, 1>(stages), BN);                                \
         break;
-    switch (N) {
+    switch (BNv) {
         RP_GEMM_CASE(32)
         RP_GEMM_CASE(64)
         RP_GEMM_CASE(96)

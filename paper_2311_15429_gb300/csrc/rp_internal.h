@@ -207,7 +207,8 @@ bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *b
                       uint64_t cols, uint32_t box_rows);
 cudaError_t launch_gemm_bf16_tn(const struct CUtensorMap_st &mapA, const struct CUtensorMap_st &mapB, float *D,
                                 int M, int N, int K, int ldd, int smem_optin, int *d_err, cudaStream_t s,
-                                int splits = 1, float *work = nullptr, int split3 = 0);
+                                int splits = 1, float *work = nullptr, int split3 = 0, int f16 = 0);
+int gemm_tile_n(int N);   // column tile width of an N-wide GEMM (the B map's box rows), 0 if unsupported
 int gemm_splits(int M, int K, int split3, int sms, int min_tiles);
 
 // far-pair kernels (rp_far.cu)

@@ -70,7 +70,10 @@ SIGNATURES = {
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
     "rp_gemm_bf16": (_I, [_V, _V, _V, _I, _I, _I, _I, _V]),
-    "rp_gemm_bf16_split": (_I, [_V, _V, _V, _I, _I, _I, _I, _I, _I, _V]),
+    "rp_gemm_tn": (_I, [_V, _V, _V, _I, _I, _I, _I, _I, _I, _I, _V]),
+    "rp_mlp_layout": (_I, [_V]),
+    "rp_mlp_forward": (_I, [_V, _V, _I, _V, _I]),
+    "rp_mlp_grad": (_I, [_V, _V, _V, _I, _V, _V, _I]),
     "rp_sync": (_I, [_V]),
     "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
@@ -227,21 +230,64 @@ def rp_gemm_bf16(A, B, D, device: int = 0, stream=None):
     _check(load().rp_gemm_bf16(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, device, stream))
 
 
-def rp_gemm_bf16_split(A, B, D, terms: int = 1, splits: int = 0, device: int = 0, stream=None):
-    """Split-K form of rp_gemm_bf16.  terms=1: D = A @ B.T.  terms=3: A is
-    (M x 2K) = [A_hi | A_lo], B is (N x 2K) = [B_hi | B_lo], and
-    D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.  splits=0 picks the count."""
+RP_DTYPE_BF16, RP_DTYPE_FP16 = 0, 1
+
+
+def rp_gemm_tn(A, B, D, terms: int = 1, splits: int = 0, device: int = 0, stream=None):
+    """D = A @ B.T on the tensor cores for bfloat16 or float16 A and B (the
+    same type).  terms=3: A is (M x 2K) = [A_hi | A_lo], B is (N x 2K) =
+    [B_hi | B_lo], and D = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T.
+    splits=0 picks the split-K count."""
+    import torch
     M, W = A.shape
     N = B.shape[0]
     K = W // 2 if terms == 3 else W
+    if A.dtype != B.dtype or A.dtype not in (torch.bfloat16, torch.float16):
+        raise ValueError("A and B must both be bfloat16 or both float16")
+    dtype = RP_DTYPE_FP16 if A.dtype == torch.float16 else RP_DTYPE_BF16
     if stream is None:
-        import torch
         stream = torch.cuda.current_stream(device).cuda_stream
     for t in (A, B, D):
         if not t.is_contiguous():
             raise ValueError("operands must be contiguous")
-    _check(load().rp_gemm_bf16_split(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, terms, splits, device,
-                                     stream))
+    _check(load().rp_gemm_tn(A.data_ptr(), B.data_ptr(), D.data_ptr(), M, N, K, dtype, terms, splits, device,
+                             stream))
+
+
+def rp_mlp_layout():
+    """(layer widths [5], number of weights) of the learned far field's network."""
+    dims = (ctypes.c_int * 5)()
+    n = load().rp_mlp_layout(dims)
+    return list(dims), n
+
+
+def _f32(a):
+    import numpy as _np
+    return _np.ascontiguousarray(a, dtype=_np.float32)
+
+
+def rp_mlp_forward(weights, x, device: int = 0):
+    """Network outputs [rows][d4] for inputs x [rows][d0] (host arrays)."""
+    import numpy as _np
+    dims, nw = rp_mlp_layout()
+    w, x = _f32(weights), _f32(x)
+    if w.size != nw or x.ndim != 2 or x.shape[1] != dims[0]:
+        raise ValueError("shape mismatch")
+    y = _np.zeros((x.shape[0], dims[4]), dtype=_np.float32)
+    _check(load().rp_mlp_forward(w.ctypes.data, x.ctypes.data, x.shape[0], y.ctypes.data, device))
+    return y
+
+
+def rp_mlp_grad(weights, x, t, device: int = 0):
+    """(loss, dL/dW as one array) of the network on inputs x and targets t."""
+    import numpy as _np
+    dims, nw = rp_mlp_layout()
+    w, x, t = _f32(weights), _f32(x), _f32(t)
+    g = _np.zeros(nw, dtype=_np.float32)
+    loss = ctypes.c_float()
+    _check(load().rp_mlp_grad(w.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], g.ctypes.data,
+                              ctypes.byref(loss), device))
+    return float(loss.value), g
 
 
 def rp_sync(ctx):

@@ -41,12 +41,12 @@ def test_split_k_matches_fp32_reference(M, N, K, splits):
     A = torch.randn(M, K, device="cuda", generator=g).to(torch.bfloat16)
     B = torch.randn(N, K, device="cuda", generator=g).to(torch.bfloat16)
     D = torch.full((M, N), float("nan"), device="cuda")
-    rp.rp_gemm_bf16_split(A, B, D, terms=1, splits=splits)
+    rp.rp_gemm_tn(A, B, D, terms=1, splits=splits)
     ref = A.float() @ B.float().T
     err = (D - ref).abs().max().item() / ref.abs().max().item()
     assert err < 1e-5, err
     D2 = torch.full((M, N), float("nan"), device="cuda")
-    rp.rp_gemm_bf16_split(A, B, D2, terms=1, splits=splits)
+    rp.rp_gemm_tn(A, B, D2, terms=1, splits=splits)
     assert torch.equal(D, D2)   # deterministic
 
 
@@ -65,7 +65,7 @@ def test_three_term_split_matches_fp64_product(M, N, K, splits):
     A = torch.cat([ah, al], 1).contiguous()
     B = torch.cat([bh, bl], 1).contiguous()
     D = torch.full((M, N), float("nan"), device="cuda")
-    rp.rp_gemm_bf16_split(A, B, D, terms=3, splits=splits)
+    rp.rp_gemm_tn(A, B, D, terms=3, splits=splits)
     ref = (a.double() @ b.double().T)
     expect = (ah.double() @ bh.double().T + ah.double() @ bl.double().T + al.double() @ bh.double().T)
     scale = ref.abs().max().item()
@@ -73,3 +73,19 @@ def test_three_term_split_matches_fp64_product(M, N, K, splits):
     single = (ah.double() @ bh.double().T - ref).abs().max().item() / scale
     three = (D.double() - ref).abs().max().item() / scale
     assert three < single / 20, (three, single)
+
+
+@pytest.mark.parametrize("M,N,K,splits", [(256, 320, 256, 1), (128, 64, 2048, 0), (384, 256, 640, 3),
+                                          (128, 512, 128, 1)])
+def test_fp16_and_column_tiles_match_fp32_reference(M, N, K, splits):
+    """fp16 operands; N above 256 runs in column tiles (320 = 2 x 160,
+    512 = 2 x 256)."""
+    import torch
+    g = torch.Generator(device="cuda").manual_seed(11 * M + N + K)
+    A = torch.randn(M, K, device="cuda", generator=g).to(torch.float16)
+    B = torch.randn(N, K, device="cuda", generator=g).to(torch.float16)
+    D = torch.full((M, N), float("nan"), device="cuda")
+    rp.rp_gemm_tn(A, B, D, terms=1, splits=splits)
+    ref = A.float() @ B.float().T
+    err = (D - ref).abs().max().item() / ref.abs().max().item()
+    assert err < 1e-5, err
