@@ -338,6 +338,38 @@ rp_status rp_mlp_forward(const float *h_w, const float *h_x, int rows, float *h_
 rp_status rp_mlp_grad(const float *h_w, const float *h_x, const float *h_t, int rows, float *h_g, float *h_loss,
                       int device);
 
+/*
+ * rp_learned_dataset -- the learned field's training data for one fixed
+ * geometry, exposed so that its data path can be checked against a plain
+ * implementation.  A source box of n_s[3] nodes at spacing h_s holds, per
+ * history, three Gaussians with amplitudes a (1 + e sin(w t + phi)) and the
+ * continuity-consistent current (dA/dt / 4 pi) grad Phi of each Gaussian
+ * (seeded); the target box has extents Lt[3] and its centre lies Rc bohr
+ * from the source centre in direction dir.  For each history and each of
+ * `samples` consecutive steps the call writes four network rows (phi and
+ * the current's three components in the pair's canonical frame):
+ *   h_x [histories * samples * 4][d0]  inputs: the canonical moment window
+ *                                      (moments l <= 2, Sec. IV), as fp16
+ *                                      values widened to float;
+ *   h_y [same][d4]                     targets: R_a times the direct
+ *                                      retarded sum (Eqs. 2, 7, 8) at the 64
+ *                                      canonical nodes, divided by the row's
+ *                                      input scale;
+ *   h_desc [histories][rp_learned_desc_size()] each history's description:
+ *     for g in 0..2: centre (x, y, z) relative to the source origin, sigma;
+ *     amplitude A_g(t_j) for g in 0..2, j in 0..63 (t_j a step index);
+ *     dA_g/dt(t_j) / (4 pi) for g in 0..2, j in 0..63;
+ *     t0 (window centre time of sample 0, in steps of the tables),
+ *     dir (unit, 3 values), Rc.
+ * Synchronous; allocates and frees its own device memory.  RP_ERR_ARG for
+ * NULL pointers, non-positive sizes, n_s < 2, or more samples than the
+ * 64-step tables allow for this geometry; RP_ERR_CUDA on a device error.
+ */
+int rp_learned_desc_size(void);
+rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], const double dir[3], double Rc,
+                             unsigned long long seed, int histories, int samples, double c, double dt, float *h_x,
+                             float *h_y, double *h_desc, int device);
+
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);
 

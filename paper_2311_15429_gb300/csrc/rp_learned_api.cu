@@ -7,6 +7,7 @@
 
 #include "rp.h"
 #include "rp_learned.h"
+#include "rp_learned_train.h"
 
 namespace rp {
 namespace {
@@ -119,6 +120,51 @@ rp_status rp_mlp_grad(const float *h_w, const float *h_x, const float *h_t, int 
     cudaFree(dx);
     cudaFree(dt);
     return finish(n, e);
+}
+
+int rp_learned_desc_size() { return kLDesc; }
+
+rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], const double dir[3], double Rc,
+                             unsigned long long seed, int histories, int samples, double c, double dt, float *h_x,
+                             float *h_y, double *h_desc, int device)
+{
+    if (!n_s || !Lt || !dir || !h_x || !h_y || !h_desc || histories <= 0 || samples <= 0 || !(h_s > 0.0) ||
+        !(c > 0.0) || !(dt > 0.0) || !(Rc > 0.0))
+        return RP_ERR_ARG;
+    for (int k = 0; k < 3; ++k)
+        if (n_s[k] < 2 || !(Lt[k] >= 0.0)) return RP_ERR_ARG;
+    LGeom g{};
+    for (int k = 0; k < 3; ++k) {
+        g.n_s[k] = n_s[k];
+        g.Lt[k] = Lt[k];
+        g.dir[k] = dir[k];
+    }
+    g.h_s = h_s;
+    g.Rc = Rc;
+    g.random = false;
+    if (samples > max_samples(g, c * dt)) return RP_ERR_ARG;
+    if (cudaSetDevice(device) != cudaSuccess) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    const size_t rows = (size_t)histories * samples * 4;
+    __half *X = nullptr;
+    float *Y = nullptr;
+    std::vector<__half> hx(rows * kLIn);
+    cudaError_t e = cudaMalloc(&X, rows * kLIn * sizeof(__half));
+    if (!e) e = cudaMalloc(&Y, rows * kLOut * sizeof(float));
+    if (!e) e = learned_dataset(g, seed, histories, samples, c, dt, X, Y, nullptr, h_desc);
+    if (!e) e = cudaMemcpy(hx.data(), X, rows * kLIn * sizeof(__half), cudaMemcpyDeviceToHost);
+    if (!e) e = cudaMemcpy(h_y, Y, rows * kLOut * sizeof(float), cudaMemcpyDeviceToHost);
+    if (!e)
+        for (size_t i = 0; i < hx.size(); ++i) h_x[i] = __half2float(hx[i]);
+    cudaFree(X);
+    cudaFree(Y);
+    if (e) {
+        cudaGetLastError();
+        return RP_ERR_CUDA;
+    }
+    return RP_OK;
 }
 
 }  // extern "C"

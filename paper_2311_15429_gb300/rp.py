@@ -74,6 +74,9 @@ SIGNATURES = {
     "rp_mlp_layout": (_I, [_V]),
     "rp_mlp_forward": (_I, [_V, _V, _I, _V, _I]),
     "rp_mlp_grad": (_I, [_V, _V, _V, _I, _V, _V, _I]),
+    "rp_learned_desc_size": (_I, []),
+    "rp_learned_dataset": (_I, [_V, ctypes.c_double, _V, _V, ctypes.c_double, ctypes.c_ulonglong, _I, _I,
+                                ctypes.c_double, ctypes.c_double, _V, _V, _V, _I]),
     "rp_sync": (_I, [_V]),
     "rp_query": (_I, [_V, ctypes.POINTER(rp_stats)]),
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
@@ -288,6 +291,23 @@ def rp_mlp_grad(weights, x, t, device: int = 0):
     _check(load().rp_mlp_grad(w.ctypes.data, x.ctypes.data, t.ctypes.data, x.shape[0], g.ctypes.data,
                               ctypes.byref(loss), device))
     return float(loss.value), g
+
+
+def rp_learned_dataset(n_s, h_s, Lt, direction, Rc, seed, histories, samples, c, dt, device: int = 0):
+    """(X [rows][d0], Y [rows][d4], desc [histories][rp_learned_desc_size()])
+    of the learned field's training data for one geometry."""
+    import numpy as _np
+    dims, _ = rp_mlp_layout()
+    rows = histories * samples * 4
+    X = _np.zeros((rows, dims[0]), dtype=_np.float32)
+    Y = _np.zeros((rows, dims[4]), dtype=_np.float32)
+    D = _np.zeros((histories, load().rp_learned_desc_size()), dtype=_np.float64)
+    ns = (ctypes.c_int * 3)(*[int(v) for v in n_s])
+    lt = (ctypes.c_double * 3)(*[float(v) for v in Lt])
+    dr = (ctypes.c_double * 3)(*[float(v) for v in direction])
+    _check(load().rp_learned_dataset(ns, float(h_s), lt, dr, float(Rc), int(seed), int(histories), int(samples),
+                                     float(c), float(dt), X.ctypes.data, Y.ctypes.data, D.ctypes.data, device))
+    return X, Y, D
 
 
 def rp_sync(ctx):
