@@ -110,7 +110,7 @@ typedef struct {
 typedef struct rp_ctx rp_ctx;
 
 /* Pair kinds reported by rp_pair_info. */
-typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1, RP_PAIR_LOWRANK = 2 } rp_pair_kind;
+typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1, RP_PAIR_LOWRANK = 2, RP_PAIR_LEARNED = 3 } rp_pair_kind;
 
 typedef struct {
     int kind;          /* rp_pair_kind */
@@ -137,7 +137,8 @@ typedef struct {
     int npairs_far;           /* pairs on the low-rank far path */
     long long far_bytes;      /* device memory of the far path (factors, batches, rings) */
     int mac_warps;            /* consumer warps of the MAC variant in use (last size class), 0 if none */
-    int reserved[3];
+    int npairs_learned;       /* pairs on the learned far path (after rp_train_far_model) */
+    int reserved[2];
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -152,7 +153,9 @@ typedef enum {
     RP_K_FAR_GEMM = 7,      /* far path: tcgen05 GEMM of factors and batch */
     RP_K_FAR_SCATTER = 8,   /* far path: node values into coefficient rings */
     RP_K_FAR_INTERP = 9,    /* far path: coefficients interpolated onto the target grid */
-    RP_K_COUNT = 10
+    RP_K_MOMENTS = 10,      /* learned path: moments of the pushed slices */
+    RP_K_LEARNED = 11,      /* learned path: network rows, network, output into the coefficients */
+    RP_K_COUNT = 12
 } rp_kernel_kind;
 
 /*
@@ -369,6 +372,67 @@ int rp_learned_desc_size(void);
 rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], const double dir[3], double Rc,
                              unsigned long long seed, int histories, int samples, double c, double dt, float *h_x,
                              float *h_y, double *h_desc, int device);
+
+/*
+ * rp_train_far_model -- train the learned far field and move the far pairs
+ * it reproduces onto it.
+ *
+ * Candidates are the context's low-rank far pairs (RP_MODE_LOWRANK) whose
+ * boxes are at least learned_distance apart and whose source and target
+ * grids have the sizes of the first candidate.  The network (see
+ * rp_mlp_layout) maps the source's monopole, dipole and quadrupole moments
+ * (the multipole description of the far interaction, Sec. IV) over a
+ * 16-step delay window, in the pair's canonical frame, to the potentials at
+ * 64 canonical nodes around the target.  Its output is added to a linear
+ * skip: an fp32 linear map of the same inputs fitted first by least squares
+ * (FP64 normal equations); the network is then trained on what the skip
+ * leaves, on the GPU with its own forward, backward and Adam kernels, on
+ * synthetic histories (Gaussian
+ * charges with oscillating amplitudes and their continuity-consistent
+ * currents, random directions and distances spanning the candidates'),
+ * whose targets are the direct retarded sums (Eqs. 2, 7, 8) at those nodes.
+ * Each candidate is then validated on fresh histories in its own geometry;
+ * if the network's rel-L2 error (worst of the four fields) is at most
+ * `gate`, the pair becomes RP_PAIR_LEARNED: its low-rank factors are
+ * dropped, its source's moments are taken at every push, and each
+ * rp_evaluate runs the network for it.  Otherwise it stays on the low-rank
+ * path, which remains the fallback and the judge of the network's error.
+ *
+ * Call after rp_finalize and before the first push, on a context that has
+ * not been trained.  Synchronous on the context's stream.  Zero fields of
+ * the configuration take the defaults given.  RP_ERR_STATE if called at
+ * another time or on a plan-only context, RP_ERR_UNSUPPORTED outside
+ * RP_MODE_LOWRANK, RP_ERR_ARG for bad fields, RP_ERR_CUDA / RP_ERR_OOM /
+ * RP_ERR_TIMEOUT on device errors.  A context with learned pairs does not
+ * support rp_save_state.
+ */
+typedef struct {
+    double learned_distance; /* smallest box distance of a candidate (bohr, > 0) */
+    double gate;             /* largest validation rel-L2 of a learned pair (0: 1e-3) */
+    int histories;           /* training histories (0: 256) */
+    int samples;             /* samples per history (0: 32, capped by the delay tables) */
+    int iterations;          /* Adam steps (0: 3000) */
+    int batch;               /* rows per step, a multiple of 128 (0: 1024) */
+    float lr;                /* peak learning rate, cosine decay (0: 1e-3) */
+    int validation;          /* validation histories per candidate (0: 4) */
+    unsigned long long seed; /* seed of the histories and the initial weights */
+    int reserved[8];         /* set to zero */
+} rp_train_config;
+
+typedef struct {
+    int candidates;          /* pairs considered */
+    int learned;             /* pairs moved onto the network */
+    long long train_rows;    /* network rows in the training set */
+    float final_loss;        /* training loss of the last minibatch */
+    float train_seconds;     /* wall time of data generation and training */
+    double val_max;          /* largest validation rel-L2 over the candidates */
+    double val_mean;         /* mean validation rel-L2 */
+    double val_linear_max;   /* the same with the linear skip alone (no network) */
+    double val_linear_mean;
+    int reserved[4];
+} rp_train_report;
+
+rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg, rp_train_report *report);
 
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);

@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <array>
 #include <atomic>
+#include <chrono>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -17,6 +18,9 @@
 
 #include "../../include/rp.h"
 #include "rp_internal.h"
+#include "rp_learned.h"
+#include "rp_learned_data.h"
+#include "rp_learned_train.h"
 
 namespace rp {
 size_t smem_direct(int max_nlag);
@@ -149,6 +153,25 @@ struct rp_ctx {
     int far_planes = 0, far_max_r = 0, npairs_far = 0;
     long long far_bytes = 0, far_max_n = 0, far_zeroed_step = -1;
     std::vector<void *> allocs;
+    std::vector<void *> *alloc_sink = nullptr;   // where dev_alloc records (the far path's own list while built)
+    std::vector<void *> far_allocs;
+    long long far_alloc_bytes = 0;
+    std::vector<std::array<std::vector<double>, 3>> far_tnodes;   // far targets' per-axis nodes, by domain
+    // learned far field
+    bool trained = false;
+    Mlp net;                          // inference network
+    bool net_open = false;
+    std::vector<LPair> lpairs;        // sorted by target
+    std::vector<LTarget> ltgts;
+    std::vector<MomentJob> mjobs;     // sorted by source domain
+    std::vector<int> mjob_of_dom;
+    LPair *d_lpairs = nullptr;
+    LTarget *d_ltgts = nullptr;
+    MomentJob *d_mjobs = nullptr;
+    float *d_lnu = nullptr;
+    float *d_lxf = nullptr, *d_lylin = nullptr;   // fp32 network rows and linear-skip outputs
+    int lrows = 0, npairs_learned = 0, mjob_max_nz = 0;
+    int smem_optin = 0;
     std::vector<float *> in_stage;    // per domain [4][N], for host pushes
     std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
 
@@ -201,7 +224,8 @@ rp_status dev_alloc(rp_ctx *ctx, T **p, size_t count)
     const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
-    ctx->allocs.push_back(q);
+    (ctx->alloc_sink ? *ctx->alloc_sink : ctx->allocs).push_back(q);
+    if (ctx->alloc_sink) ctx->far_alloc_bytes += (long long)bytes;
     ctx->device_bytes += (long long)bytes;
     *p = static_cast<T *>(q);
     return RP_OK;
@@ -435,30 +459,68 @@ void far_axis(double o, double h, int n, int p, std::vector<double> &nodes, std:
     }
 }
 
-// Factors, batch buffers, coefficient rings and descriptors of the far pairs.
+// Factors, batch buffers, coefficient rings and descriptors of the far pairs
+// (low-rank pairs get factor rows; targets of low-rank or learned pairs get
+// coefficient rings).  Every allocation goes to the far path's own list, so
+// that the structures can be rebuilt when pairs move to the learned path.
+rp_status build_far_impl(rp_ctx *ctx, int max_optin);
+
 rp_status build_far(rp_ctx *ctx, int max_optin)
+{
+    ctx->alloc_sink = &ctx->far_allocs;
+    const rp_status st = build_far_impl(ctx, max_optin);
+    ctx->alloc_sink = nullptr;
+    return st;
+}
+
+// Frees the far path's structures (before a rebuild).
+void clear_far(rp_ctx *ctx)
+{
+    for (void *p : ctx->far_allocs) cudaFree(p);
+    ctx->far_allocs.clear();
+    ctx->device_bytes -= ctx->far_alloc_bytes;
+    ctx->far_alloc_bytes = 0;
+    ctx->far_src.clear(); ctx->far_tgt.clear(); ctx->far_links.clear();
+    ctx->far_link0.clear(); ctx->far_link1.clear(); ctx->far_link_threads.clear();
+    ctx->far_Z.clear(); ctx->far_rows.clear(); ctx->far_splits.clear(); ctx->far_work = nullptr;
+    ctx->far_mapW.clear(); ctx->far_mapX.clear(); ctx->far_src_of_dom.clear();
+    ctx->d_far_src = nullptr; ctx->d_far_tgt = nullptr; ctx->d_far_links = nullptr;
+    ctx->far_src_alone.clear(); ctx->far_tgt_alone.clear(); ctx->far_src_alone_of_dom.clear();
+    ctx->d_far_src_alone = nullptr; ctx->d_far_tgt_alone = nullptr;
+    ctx->far_planes = ctx->far_max_r = ctx->npairs_far = 0;
+    ctx->far_bytes = ctx->far_max_n = 0;
+    ctx->far_zeroed_step = -1;
+    for (FwdRing &R : ctx->fwd) { R.far_x = nullptr; R.far_ks = 0; }
+    for (InvTarget &I : ctx->inv) I.far = nullptr;
+}
+
+rp_status build_far_impl(rp_ctx *ctx, int max_optin)
 {
     const int nd = (int)ctx->doms.size();
     const int batch = ctx->cfg.far_batch, P = ctx->cfg.far_points;
     const double inv_cdt = 1.0 / (ctx->cfg.c * ctx->cfg.dt);
     rp_status st;
     ctx->far_src_of_dom.assign(nd, -1);
+    ctx->far_tnodes.assign(nd, {});
     // targets
     std::vector<int> tidx(nd, -1);
     std::vector<std::array<std::vector<double>, 3>> tnodes(nd);
     for (int t = 0; t < nd; ++t) {
         int hi = -1;
+        bool learned = false;
         for (int s = 0; s < nd; ++s) {
             const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
             if (p.kind == RP_PAIR_LOWRANK) hi = std::max(hi, p.lag_hi);
+            learned = learned || p.kind == RP_PAIR_LEARNED;
         }
-        if (hi < 0) continue;
+        if (hi < 0 && !learned) continue;
         const DomainDesc &T = ctx->doms[t];
         FarTarget F{};
         F.dom = t;
         F.nx = T.n[0]; F.ny = T.n[1]; F.nz = T.n[2];
         std::vector<float> L[3];
         for (int a = 0; a < 3; ++a) far_axis(T.o[a], T.h, T.n[a], P, tnodes[t][a], L[a]);
+        ctx->far_tnodes[t] = tnodes[t];
         F.px = (int)tnodes[t][0].size(); F.py = (int)tnodes[t][1].size(); F.pz = (int)tnodes[t][2].size();
         F.r = F.px * F.py * F.pz;
         F.lag_hi_max = hi;
@@ -593,6 +655,139 @@ rp_status build_far(rp_ctx *ctx, int max_optin)
     return RP_OK;
 }
 
+void *tensor_encoder()
+{
+    void *enc = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &enc, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return enc;
+}
+
+void box_centre(const DomainDesc &d, double c[3])
+{
+    for (int a = 0; a < 3; ++a) c[a] = d.o[a] + 0.5 * d.h * (d.n[a] - 1);
+}
+
+void box_extent(const DomainDesc &d, double L[3])
+{
+    for (int a = 0; a < 3; ++a) L[a] = d.h * (d.n[a] - 1);
+}
+
+// Inference structures of the learned pairs (after build_far): moment rings
+// and jobs per source, pair records (sorted by target), target records and
+// the inference network with the trained weights.
+rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const std::vector<float> &wlin)
+{
+    const int nd = (int)ctx->doms.size();
+    const double cdt = ctx->cfg.c * ctx->cfg.dt;
+    rp_status st;
+    std::vector<int> mdepth(nd, 0);
+    for (int t = 0; t < nd; ++t)
+        for (int s = 0; s < nd; ++s) {
+            if (ctx->pairs[(size_t)t * nd + s].kind != RP_PAIR_LEARNED) continue;
+            double ct[3], cs[3];
+            box_centre(ctx->doms[t], ct);
+            box_centre(ctx->doms[s], cs);
+            const double tau = std::sqrt((ct[0] - cs[0]) * (ct[0] - cs[0]) + (ct[1] - cs[1]) * (ct[1] - cs[1]) +
+                                         (ct[2] - cs[2]) * (ct[2] - cs[2])) / cdt;
+            mdepth[s] = std::max(mdepth[s], (int)std::ceil(tau) + kLWin / 2 + 3);
+            ctx->max_lag = std::max(ctx->max_lag, (int)std::ceil(tau) + kLWin / 2 + 1);
+        }
+    ctx->mjob_of_dom.assign(nd, -1);
+    std::vector<float *> ring(nd, nullptr);
+    for (int s = 0; s < nd; ++s) {
+        if (!mdepth[s]) continue;
+        const DomainDesc &D = ctx->doms[s];
+        if ((st = dev_alloc(ctx, &ring[s], (size_t)mdepth[s] * 4 * kLMom))) return st;
+        RP_CUDA(ctx, cudaMemset(ring[s], 0, (size_t)mdepth[s] * 4 * kLMom * sizeof(float)));
+        MomentJob J{};
+        J.dom = s;
+        J.nx = D.n[0]; J.ny = D.n[1]; J.nz = D.n[2];
+        J.h = D.h;
+        J.ox = -0.5 * D.h * (D.n[0] - 1); J.oy = -0.5 * D.h * (D.n[1] - 1); J.oz = -0.5 * D.h * (D.n[2] - 1);
+        if ((st = dev_alloc(ctx, &J.part, (size_t)4 * D.n[2] * kLMom))) return st;
+        J.out = ring[s];
+        J.out_depth = mdepth[s];
+        ctx->mjob_of_dom[s] = (int)ctx->mjobs.size();
+        ctx->mjob_max_nz = std::max(ctx->mjob_max_nz, D.n[2]);
+        ctx->mjobs.push_back(J);
+    }
+    std::map<int, int> ftgt;   // domain -> far target index
+    for (size_t k = 0; k < ctx->far_tgt.size(); ++k) ftgt[ctx->far_tgt[k].dom] = (int)k;
+    for (int t = 0; t < nd; ++t) {
+        const int p0 = (int)ctx->lpairs.size();
+        double ct[3], Lt[3];
+        box_centre(ctx->doms[t], ct);
+        box_extent(ctx->doms[t], Lt);
+        double cn[kLOut][3];
+        canonical_nodes(Lt, cn);
+        for (int s = 0; s < nd; ++s) {
+            if (ctx->pairs[(size_t)t * nd + s].kind != RP_PAIR_LEARNED) continue;
+            double cs[3], n[3], R[9];
+            box_centre(ctx->doms[s], cs);
+            for (int a = 0; a < 3; ++a) n[a] = ct[a] - cs[a];
+            const double Rc = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+            canonical_frame(n, R);
+            LPair P{};
+            for (int k = 0; k < 9; ++k) P.R[k] = (float)R[k];
+            P.tau_c = Rc / cdt;
+            P.Rc = (float)Rc;
+            P.mom = ring[s];
+            P.mdepth = mdepth[s];
+            for (int a = 0; a < kLOut; ++a) {
+                double d2 = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double v = n[k] + R[k] * cn[a][0] + R[3 + k] * cn[a][1] + R[6 + k] * cn[a][2];
+                    d2 += v * v;
+                }
+                P.Ra[a] = (float)std::sqrt(d2);
+            }
+            std::vector<float> Pm;
+            reinterp_matrix(Lt, R, ct, ctx->far_tnodes[t].data(), Pm);
+            float *dP = nullptr;
+            if ((st = upload(ctx, &dP, Pm))) return st;
+            P.P = dP;
+            ctx->lpairs.push_back(P);
+        }
+        const int p1 = (int)ctx->lpairs.size();
+        if (p1 == p0) continue;
+        const FarTarget &F = ctx->far_tgt[ftgt.at(t)];
+        LTarget T{};
+        T.cring = F.cring;
+        T.depth = F.depth;
+        T.r = F.r;
+        T.p0 = p0;
+        T.p1 = p1;
+        T.overwrite = F.lag_hi_max < 0 ? 1 : 0;
+        ctx->ltgts.push_back(T);
+    }
+    ctx->npairs_learned = (int)ctx->lpairs.size();
+    if ((st = upload(ctx, &ctx->d_lpairs, ctx->lpairs)) || (st = upload(ctx, &ctx->d_ltgts, ctx->ltgts)) ||
+        (st = upload(ctx, &ctx->d_mjobs, ctx->mjobs)) || (st = dev_alloc(ctx, &ctx->d_lnu, 4 * ctx->lpairs.size())))
+        return st;
+    ctx->lrows = (int)((4 * ctx->lpairs.size() + 127) / 128 * 128);
+    if ((st = dev_alloc(ctx, &ctx->d_lxf, (size_t)ctx->lrows * kLIn)) ||
+        (st = dev_alloc(ctx, &ctx->d_lylin, (size_t)ctx->lrows * kLOut)))
+        return st;
+    void *enc = tensor_encoder();
+    if (!enc) return fail(ctx, RP_ERR_UNSUPPORTED, "learned path needs cuTensorMapEncodeTiled");
+    cudaError_t e = mlp_create(ctx->net, ctx->lrows, 1, enc);
+    ctx->net_open = true;
+    if (e) return cuda_fail(ctx, e, "learned network");
+    cudaFree(ctx->net.d_err);
+    ctx->net.d_err = ctx->d_err;
+    RP_CUDA(ctx, mlp_set_weights(ctx->net, weights.data(), ctx->stream));
+    RP_CUDA(ctx, cudaMemcpyAsync(ctx->net.Wlin, wlin.data(), wlin.size() * sizeof(float), cudaMemcpyHostToDevice,
+                                 ctx->stream));
+    RP_CUDA(ctx, cudaMemsetAsync(ctx->net.X16, 0, (size_t)ctx->lrows * kLIn * sizeof(__half), ctx->stream));
+    RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    return RP_OK;
+}
+
 // Launch-shape autotuning: time each consumer-warp variant of the TMA-fed MAC
 // on this plan (two launches after one warm-up, on the context stream, over
 // rings whose contents do not matter for timing) and keep the fastest per
@@ -668,7 +863,7 @@ const char *rp_kernel_name(int kind)
 {
     static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column", "mac_inv_column",
                                             "inv_plane", "direct", "far_convert", "far_gemm",
-                                            "far_scatter", "far_interp"};
+                                            "far_scatter", "far_interp", "moments", "learned"};
     return (kind >= 0 && kind < RP_K_COUNT) ? names[kind] : nullptr;
 }
 
@@ -977,6 +1172,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     if (st) return st;
     int max_optin = 0;
     RP_CUDA(ctx, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    ctx->smem_optin = max_optin;
     {
         const size_t need = std::max({ctx->smem_plane, ctx->smem_col, ctx->smem_mac, ctx->smem_inv, ctx->smem_dir});
         if (need > (size_t)max_optin)
@@ -1227,6 +1423,21 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
             }
         }
     }
+    // learned path: moments of the pushed slices of its sources
+    if (!ctx->mjobs.empty()) {
+        int j0 = -1, j1 = -1;
+        for (int d = d0; d < d1; ++d) {
+            const int ji = ctx->mjob_of_dom[d];
+            if (ji < 0) continue;
+            if (j0 < 0) j0 = ji;
+            j1 = ji + 1;
+        }
+        if (j0 >= 0 && (st = timed_launch(ctx, RP_K_MOMENTS, "source moments", [&] {
+                             return launch_moments(ctx->d_mjobs + j0, j1 - j0, ctx->mjob_max_nz, step, &in,
+                                                   ctx->stream);
+                         })))
+            return st;
+    }
     return RP_OK;
 }
 
@@ -1305,6 +1516,21 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
                                            std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
                  return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,
                                               ctx->smem_mac, step, clamp, ctx->stream);
+             })))
+            return st;
+    }
+    if (!ctx->lpairs.empty()) {
+        // learned pairs: network rows, network, node values into the coefficients
+        if ((st = timed_launch(ctx, RP_K_LEARNED, "learned far field", [&] {
+                 const int nrows = 4 * (int)ctx->lpairs.size();
+                 cudaError_t e = launch_features(ctx->d_lpairs, nullptr, (int)ctx->lpairs.size(), step,
+                                                 ctx->net.X16, ctx->d_lxf, ctx->d_lnu, ctx->stream);
+                 if (!e) e = linear_apply(ctx->net.Wlin, ctx->d_lxf, nrows, nullptr, 1.0f, ctx->d_lylin, ctx->stream);
+                 if (!e) e = mlp_forward(ctx->net, ctx->lrows, false, ctx->smem_optin, ctx->sm_count, ctx->stream);
+                 if (!e)
+                     e = launch_learned_out(ctx->d_ltgts, (int)ctx->ltgts.size(), ctx->d_lpairs, ctx->net.Z[3],
+                                            ctx->d_lylin, ctx->net.out_scale, ctx->d_lnu, step, ctx->stream);
+                 return e;
              })))
             return st;
     }
@@ -1495,6 +1721,145 @@ rp_status rp_gemm_bf16(const void *d_A, const void *d_B, float *d_D, int M, int 
     return rp_gemm_tn(d_A, d_B, d_D, M, N, K, RP_DTYPE_BF16, 1, 1, device, stream);
 }
 
+rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_train_report *rep)
+{
+    if (!ctx || !cfg_in) return RP_ERR_ARG;
+    if (!ctx->finalized || ctx->plan_only || ctx->trained || ctx->step >= 0 || ctx->npushed)
+        return fail(ctx, RP_ERR_STATE, "rp_train_far_model: call once, after rp_finalize and before the first push");
+    if (ctx->cfg.mode != RP_MODE_LOWRANK) return fail(ctx, RP_ERR_UNSUPPORTED, "the learned far field needs RP_MODE_LOWRANK");
+    rp_train_config cfg = *cfg_in;
+    if (!(cfg.learned_distance > 0.0) || cfg.gate < 0.0 || cfg.histories < 0 || cfg.samples < 0 ||
+        cfg.iterations < 0 || cfg.batch < 0 || cfg.batch % 128 || cfg.lr < 0.0f || cfg.validation < 0)
+        return fail(ctx, RP_ERR_ARG, "rp_train_far_model: bad configuration");
+    if (cfg.gate == 0.0) cfg.gate = 1e-3;
+    if (!cfg.histories) cfg.histories = 256;
+    if (!cfg.samples) cfg.samples = 32;
+    if (!cfg.iterations) cfg.iterations = 3000;
+    if (!cfg.batch) cfg.batch = 1024;
+    if (cfg.lr == 0.0f) cfg.lr = 1e-3f;
+    if (!cfg.validation) cfg.validation = 4;
+    rp_train_report report{};
+    rp_status st = use_device(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    const double c = ctx->cfg.c, dt = ctx->cfg.dt;
+    // candidates
+    std::vector<std::pair<int, int>> cand;
+    for (int t = 0; t < nd; ++t)
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind == RP_PAIR_LOWRANK && p.rmin >= cfg.learned_distance) cand.push_back({t, s});
+        }
+    report.candidates = (int)cand.size();
+    ctx->trained = true;
+    if (cand.empty()) {
+        if (rep) *rep = report;
+        return RP_OK;
+    }
+    auto same = [](const DomainDesc &a, const DomainDesc &b) {
+        return a.n[0] == b.n[0] && a.n[1] == b.n[1] && a.n[2] == b.n[2] && a.h == b.h;
+    };
+    const DomainDesc &S0 = ctx->doms[cand[0].second], &T0 = ctx->doms[cand[0].first];
+    LGeom geo{};
+    for (int a = 0; a < 3; ++a) geo.n_s[a] = S0.n[a];
+    geo.h_s = S0.h;
+    box_extent(T0, geo.Lt);
+    geo.random = true;
+    std::vector<std::pair<int, int>> elig;
+    std::vector<double> dist;
+    for (auto [t, s] : cand) {
+        if (!same(ctx->doms[s], S0) || !same(ctx->doms[t], T0)) continue;
+        double ct[3], cs[3];
+        box_centre(ctx->doms[t], ct);
+        box_centre(ctx->doms[s], cs);
+        elig.push_back({t, s});
+        dist.push_back(std::sqrt((ct[0] - cs[0]) * (ct[0] - cs[0]) + (ct[1] - cs[1]) * (ct[1] - cs[1]) +
+                                 (ct[2] - cs[2]) * (ct[2] - cs[2])));
+    }
+    geo.R_lo = 0.9 * *std::min_element(dist.begin(), dist.end());
+    geo.R_hi = 1.1 * *std::max_element(dist.begin(), dist.end());
+    const int samples = std::min(cfg.samples, max_samples(geo, c * dt));
+    if (samples < 1) return fail(ctx, RP_ERR_UNSUPPORTED, "boxes too large for the learned path's delay tables");
+    void *enc = tensor_encoder();
+    if (!enc) return fail(ctx, RP_ERR_UNSUPPORTED, "learned path needs cuTensorMapEncodeTiled");
+    const auto t_start = std::chrono::steady_clock::now();
+    const long long rows = (long long)cfg.histories * samples * 4;
+    const long long vrows = (long long)cfg.validation * samples * 4;
+    __half *X = nullptr, *VX = nullptr;
+    float *Y = nullptr, *VY = nullptr, *Xf = nullptr, *VXf = nullptr, *Yres = nullptr;
+    Mlp tnet;
+    std::vector<float> weights(mlp_weight_count()), wlin((size_t)kLOut * kLIn);
+    std::vector<double> verr, verr_lin;
+    cudaError_t e = cudaMalloc(&X, rows * kLIn * sizeof(__half));
+    if (!e) e = cudaMalloc(&Xf, rows * kLIn * sizeof(float));
+    if (!e) e = cudaMalloc(&Y, rows * kLOut * sizeof(float));
+    if (!e) e = cudaMalloc(&Yres, rows * kLOut * sizeof(float));
+    if (!e) e = cudaMalloc(&VX, vrows * kLIn * sizeof(__half));
+    if (!e) e = cudaMalloc(&VXf, vrows * kLIn * sizeof(float));
+    if (!e) e = cudaMalloc(&VY, vrows * kLOut * sizeof(float));
+    if (!e) e = learned_dataset(geo, cfg.seed, cfg.histories, samples, c, dt, X, Xf, Y, ctx->stream);
+    if (!e) e = mlp_create(tnet, cfg.batch, cfg.seed ^ 0xA5A5A5A5ull, enc);
+    if (!e) e = mlp_zero_last(tnet, ctx->stream);
+    if (!e) e = learned_fit_linear(tnet, Xf, Y, (int)rows, Yres, ctx->stream);
+    float loss = 0.0f;
+    if (!e) e = learned_train(tnet, X, Yres, (int)rows, cfg.iterations, cfg.batch, cfg.lr, cfg.seed, ctx->smem_optin,
+                              ctx->sm_count, ctx->stream, &loss);
+    report.train_seconds = std::chrono::duration<float>(std::chrono::steady_clock::now() - t_start).count();
+    report.train_rows = rows;
+    report.final_loss = loss;
+    // validation in each candidate's own geometry
+    for (size_t i = 0; i < elig.size() && !e; ++i) {
+        const auto [t, s] = elig[i];
+        LGeom vg = geo;
+        vg.random = false;
+        double ct[3], cs[3];
+        box_centre(ctx->doms[t], ct);
+        box_centre(ctx->doms[s], cs);
+        for (int a = 0; a < 3; ++a) vg.dir[a] = (ct[a] - cs[a]) / dist[i];
+        vg.Rc = dist[i];
+        double err[4] = {}, errl[4] = {};
+        e = learned_dataset(vg, cfg.seed + 7919ull * (i + 1), cfg.validation, samples, c, dt, VX, VXf, VY,
+                            ctx->stream);
+        if (!e) e = learned_eval(tnet, VX, VXf, VY, (int)vrows, ctx->smem_optin, ctx->sm_count, ctx->stream, err, errl);
+        verr.push_back(std::max(std::max(err[0], err[1]), std::max(err[2], err[3])));
+        verr_lin.push_back(std::max(std::max(errl[0], errl[1]), std::max(errl[2], errl[3])));
+    }
+    if (!e) e = cudaMemcpy(wlin.data(), tnet.Wlin, wlin.size() * sizeof(float), cudaMemcpyDeviceToHost);
+    const float out_scale = tnet.out_scale;
+    if (!e) e = mlp_get_weights(tnet, weights.data(), ctx->stream);
+    int flag = 0;
+    if (!e) e = cudaMemcpy(&flag, tnet.d_err, sizeof(int), cudaMemcpyDeviceToHost);
+    mlp_destroy(tnet);
+    cudaFree(X); cudaFree(Xf); cudaFree(Y); cudaFree(Yres); cudaFree(VX); cudaFree(VXf); cudaFree(VY);
+    if (e) return cuda_fail(ctx, e, "learned far field training");
+    if (flag) return fail(ctx, RP_ERR_TIMEOUT, "a bounded device wait ran out during training");
+    double vsum = 0.0, lsum = 0.0;
+    report.val_max = 0.0;
+    report.val_linear_max = 0.0;
+    for (size_t i = 0; i < elig.size(); ++i) {
+        report.val_max = std::max(report.val_max, verr[i]);
+        report.val_linear_max = std::max(report.val_linear_max, verr_lin[i]);
+        vsum += verr[i];
+        lsum += verr_lin[i];
+        if (verr[i] <= cfg.gate) {
+            ctx->pairs[(size_t)elig[i].first * nd + elig[i].second].kind = RP_PAIR_LEARNED;
+            ++report.learned;
+        }
+    }
+    report.val_mean = elig.empty() ? 0.0 : vsum / (double)elig.size();
+    report.val_linear_mean = elig.empty() ? 0.0 : lsum / (double)elig.size();
+    if (report.learned) {
+        clear_far(ctx);
+        if ((st = build_far(ctx, ctx->smem_optin))) return st;
+        if ((st = build_learned(ctx, weights, wlin))) return st;
+        ctx->net.out_scale = out_scale;
+        RP_CUDA(ctx, cudaMemcpy(ctx->d_fwd, ctx->fwd.data(), ctx->fwd.size() * sizeof(FwdRing), cudaMemcpyHostToDevice));
+        RP_CUDA(ctx, cudaMemcpy(ctx->d_inv, ctx->inv.data(), ctx->inv.size() * sizeof(InvTarget), cudaMemcpyHostToDevice));
+    }
+    if (rep) *rep = report;
+    return RP_OK;
+}
+
 rp_status rp_sync(rp_ctx *ctx)
 {
     if (!ctx) return RP_ERR_ARG;
@@ -1532,6 +1897,7 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->mac_tma = ctx->tma ? 1 : 0;
     out->npairs_far = ctx->npairs_far;
     out->far_bytes = ctx->far_bytes;
+    out->npairs_learned = ctx->npairs_learned;
     out->mac_warps = 0;
     for (const LaunchGroup &g : ctx->inv_groups)
         if (g.cls > 0 && ctx->tma) out->mac_warps = ctx->mac_cw[class_slot(g.cls)];
@@ -1625,6 +1991,7 @@ rp_status rp_save_state(rp_ctx *ctx, const char *path)
     rp_status st = check_ready(ctx);
     if (st) return st;
     if (!path) return fail(ctx, RP_ERR_ARG, "NULL path");
+    if (!ctx->lpairs.empty()) return fail(ctx, RP_ERR_UNSUPPORTED, "a context with learned pairs has no saved state");
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(ctx, RP_ERR_ARG, std::string("cannot open ") + path);
@@ -1695,6 +2062,11 @@ void rp_destroy(rp_ctx *ctx)
         for (const ProfRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
         for (void *p : ctx->allocs) cudaFree(p);
+        for (void *p : ctx->far_allocs) cudaFree(p);
+        if (ctx->net_open) {
+            if (ctx->net.d_err == ctx->d_err) ctx->net.d_err = nullptr;
+            mlp_destroy(ctx->net);
+        }
         cudaGetLastError();
         if (cur >= 0) cudaSetDevice(cur);
     }

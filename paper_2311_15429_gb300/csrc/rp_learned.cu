@@ -166,6 +166,61 @@ __global__ void k_gather(const __half *__restrict__ Xall, const float *__restric
         Xt16[(size_t)(c0 + i) * ldt + r0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
+// out[r][o] = sign * sum_i W[o][i] X[r][i] (+ add): one block per 4 rows, W in shared memory chunks.
+__global__ void __launch_bounds__(256) k_linear(const float *__restrict__ W, const float *__restrict__ X, int rows,
+                                                const float *__restrict__ add, float sign, float *__restrict__ out,
+                                                float scale)
+{
+    __shared__ float xs[4][kLIn];
+    const int r0 = blockIdx.x * 4;
+    for (int i = threadIdx.x; i < 4 * kLIn; i += blockDim.x) {
+        const int rr = r0 + i / kLIn;
+        xs[i / kLIn][i % kLIn] = rr < rows ? X[(size_t)rr * kLIn + i % kLIn] : 0.0f;
+    }
+    __syncthreads();
+    const int rr = threadIdx.x / kLOut, o = threadIdx.x % kLOut;
+    if (r0 + rr >= rows) return;
+    float acc = 0.0f;
+    const float *w = W + (size_t)o * kLIn;
+    for (int i = 0; i < kLIn; ++i) acc = fmaf(w[i], xs[rr][i], acc);
+    const size_t oi = (size_t)(r0 + rr) * kLOut + o;
+    out[oi] = scale * (sign * acc + (add ? add[oi] : 0.0f));
+}
+
+// G[i][j] = sum_r X[r][i] X[r][j] and B[i][o] = sum_r X[r][i] Y[r][o] in FP64;
+// a block owns a 32 x 32 tile of [G | B] and sums the rows in a fixed order.
+__global__ void __launch_bounds__(256) k_normal(const float *__restrict__ X, const float *__restrict__ Y, int rows,
+                                                double *__restrict__ G, double *__restrict__ B)
+{
+    __shared__ float xa[32][33], xb[32][33];
+    const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;       // columns of [X | Y]
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;      // 32 x 8
+    double acc[4] = {0.0, 0.0, 0.0, 0.0};
+    auto col = [&](int r, int j) -> float {
+        return j < kLIn ? X[(size_t)r * kLIn + j] : Y[(size_t)r * kLOut + (j - kLIn)];
+    };
+    for (int r0 = 0; r0 < rows; r0 += 32) {
+        for (int k = ty; k < 32; k += 8) {
+            const int r = r0 + k;
+            xa[k][tx] = r < rows ? X[(size_t)r * kLIn + i0 + tx] : 0.0f;
+            xb[k][tx] = r < rows ? col(r, j0 + tx) : 0.0f;
+        }
+        __syncthreads();
+        for (int q = 0; q < 4; ++q) {
+            const int ii = ty + 8 * q;
+            double s = 0.0;
+            for (int k = 0; k < 32; ++k) s += (double)xa[k][ii] * (double)xb[k][tx];
+            acc[q] += s;
+        }
+        __syncthreads();
+    }
+    for (int q = 0; q < 4; ++q) {
+        const int i = i0 + ty + 8 * q, j = j0 + tx;
+        if (j < kLIn) G[(size_t)i * kLIn + j] = acc[q];
+        else B[(size_t)i * kLOut + (j - kLIn)] = acc[q];
+    }
+}
+
 // splitmix64: the seeded weight initialisation
 uint64_t splitmix(uint64_t &x)
 {
@@ -231,6 +286,8 @@ cudaError_t mlp_create(Mlp &n, int cap, uint64_t seed, void *enc)
     RP_TRY(alloc(&n.Xt16, (size_t)cap * kLIn));
     RP_TRY(alloc(&n.dA, (size_t)cap * kLHid));
     RP_TRY(alloc(&n.Y, (size_t)cap * kLOut));
+    RP_TRY(alloc(&n.Wlin, (size_t)kLOut * kLIn));
+    RP_TRY(cudaMemset(n.Wlin, 0, (size_t)kLOut * kLIn * sizeof(float)));
     RP_TRY(alloc(&n.loss_part, (size_t)cap / 32 * (kLOut / 32)));
     n.work_floats = 76 * 256 * 320;
     RP_TRY(alloc(&n.work, (size_t)n.work_floats));
@@ -278,7 +335,7 @@ void mlp_destroy(Mlp &n)
         cudaFree(n.W16[l]); cudaFree(n.Wt16[l]); cudaFree(n.Z[l]); cudaFree(n.dZ16[l]); cudaFree(n.dZt16[l]);
     }
     for (int l = 0; l < 3; ++l) { cudaFree(n.A16[l]); cudaFree(n.At16[l]); }
-    cudaFree(n.X16); cudaFree(n.Xt16); cudaFree(n.dA); cudaFree(n.Y); cudaFree(n.loss_part);
+    cudaFree(n.X16); cudaFree(n.Xt16); cudaFree(n.dA); cudaFree(n.Y); cudaFree(n.loss_part); cudaFree(n.Wlin);
     cudaFree(n.work); cudaFree(n.d_err);
     n = Mlp{};
 }
@@ -323,6 +380,29 @@ cudaError_t mlp_gather(Mlp &n, const __half *Xall, const float *Yall, const int 
 {
     if (rows <= 0 || rows % 128 || rows > n.cap) return cudaErrorInvalidValue;
     k_gather<<<dim3(kLIn / 32, rows / 32), dim3(32, 8), 0, s>>>(Xall, Yall, idx, n.X16, n.Xt16, n.Y, n.cap);
+    return cudaGetLastError();
+}
+
+cudaError_t linear_apply(const float *Wlin, const float *X, int rows, const float *add, float sign, float *out,
+                         cudaStream_t s, float scale)
+{
+    if (rows <= 0) return cudaSuccess;
+    k_linear<<<(rows + 3) / 4, 4 * kLOut, 0, s>>>(Wlin, X, rows, add, sign, out, scale);
+    return cudaGetLastError();
+}
+
+cudaError_t mlp_zero_last(Mlp &n, cudaStream_t s)
+{
+    const size_t w = (size_t)kDims[3] * kDims[4];
+    cudaError_t e = cudaMemsetAsync(n.W[3], 0, w * sizeof(float), s);
+    if (!e) e = cudaMemsetAsync(n.W16[3], 0, w * sizeof(__half), s);
+    if (!e) e = cudaMemsetAsync(n.Wt16[3], 0, w * sizeof(__half), s);
+    return e;
+}
+
+cudaError_t linear_normal(const float *X, const float *Y, int rows, double *G, double *B, cudaStream_t s)
+{
+    k_normal<<<dim3((kLIn + kLOut) / 32, kLIn / 32), 256, 0, s>>>(X, Y, rows, G, B);
     return cudaGetLastError();
 }
 

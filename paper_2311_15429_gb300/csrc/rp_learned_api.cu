@@ -153,7 +153,7 @@ rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], c
     std::vector<__half> hx(rows * kLIn);
     cudaError_t e = cudaMalloc(&X, rows * kLIn * sizeof(__half));
     if (!e) e = cudaMalloc(&Y, rows * kLOut * sizeof(float));
-    if (!e) e = learned_dataset(g, seed, histories, samples, c, dt, X, Y, nullptr, h_desc);
+    if (!e) e = learned_dataset(g, seed, histories, samples, c, dt, X, nullptr, Y, nullptr, h_desc);
     if (!e) e = cudaMemcpy(hx.data(), X, rows * kLIn * sizeof(__half), cudaMemcpyDeviceToHost);
     if (!e) e = cudaMemcpy(h_y, Y, rows * kLOut * sizeof(float), cudaMemcpyDeviceToHost);
     if (!e)

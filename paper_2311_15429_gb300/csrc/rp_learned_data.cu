@@ -104,7 +104,7 @@ __device__ void rotate_moments(const float *M, const float *R, float *out)
 // One block per (pair, sample): the window of canonical moments, then the
 // four fields' rows X16[4 * row + f] and scales nu.
 __global__ void k_features(const LPair *__restrict__ pairs, const FeatRow *__restrict__ rows, int nrows,
-                           long long step, __half *__restrict__ X16, float *__restrict__ nu)
+                           long long step, __half *__restrict__ X16, float *__restrict__ Xf, float *__restrict__ nu)
 {
     __shared__ float win[kLWin][4 * kLMom];
     __shared__ float scale[4];
@@ -142,6 +142,7 @@ __global__ void k_features(const LPair *__restrict__ pairs, const FeatRow *__res
         float x = win[k][f * kLMom + m] * inv;
         if (c >= kLWin * kLMom) x *= lr;
         X16[(size_t)(4 * r + f) * kLIn + c] = __float2half_rn(x);
+        if (Xf) Xf[(size_t)(4 * r + f) * kLIn + c] = x;
     }
 }
 
@@ -289,7 +290,8 @@ __global__ void k_label_rows(const TrainHist *__restrict__ hist, const float *__
 // One block per far target with learned pairs, pairs in a fixed order:
 // c[b][f] += sum over its pairs of the re-interpolated, rotated-back values.
 __global__ void k_learned_out(const LTarget *__restrict__ tgts, const LPair *__restrict__ pairs,
-                              const float *__restrict__ Y, const float *__restrict__ nu, long long step)
+                              const float *__restrict__ Y, const float *__restrict__ Ylin, float yscale,
+                              const float *__restrict__ nu, long long step)
 {
     __shared__ float v[4][kLOut];
     const LTarget T = tgts[blockIdx.x];
@@ -301,7 +303,8 @@ __global__ void k_learned_out(const LTarget *__restrict__ tgts, const LPair *__r
         __syncthreads();
         for (int i = threadIdx.x; i < 4 * kLOut; i += blockDim.x) {
             const int f = i / kLOut, a = i % kLOut;
-            v[f][a] = nu[4 * pi + f] * Y[(long long)(4 * pi + f) * kLOut + a] / P.Ra[a];
+            const long long o = (long long)(4 * pi + f) * kLOut + a;
+            v[f][a] = nu[4 * pi + f] * fmaf(yscale, Y[o], Ylin[o]) / P.Ra[a];
         }
         __syncthreads();
         if (b < T.r) {
@@ -332,10 +335,10 @@ cudaError_t launch_moments(const MomentJob *d_jobs, int njobs, int max_nz, long 
 }
 
 cudaError_t launch_features(const LPair *d_pairs, const FeatRow *d_rows, int nrows, long long step, __half *X16,
-                            float *nu, cudaStream_t s)
+                            float *Xf, float *nu, cudaStream_t s)
 {
     if (nrows <= 0) return cudaSuccess;
-    k_features<<<nrows, 128, 0, s>>>(d_pairs, d_rows, nrows, step, X16, nu);
+    k_features<<<nrows, 128, 0, s>>>(d_pairs, d_rows, nrows, step, X16, Xf, nu);
     return cudaGetLastError();
 }
 
@@ -368,11 +371,11 @@ cudaError_t launch_label_rows(const TrainHist *d_hist, int nhist, const float *l
     return cudaGetLastError();
 }
 
-cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *nu,
-                               long long step, cudaStream_t s)
+cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *Ylin,
+                               float yscale, const float *nu, long long step, cudaStream_t s)
 {
     if (ntgt <= 0) return cudaSuccess;
-    k_learned_out<<<ntgt, 512, 0, s>>>(d_tgts, d_pairs, Y, nu, step);
+    k_learned_out<<<ntgt, 512, 0, s>>>(d_tgts, d_pairs, Y, Ylin, yscale, nu, step);
     return cudaGetLastError();
 }
 

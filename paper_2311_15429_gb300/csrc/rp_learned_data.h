@@ -70,7 +70,7 @@ struct TrainHist {
 cudaError_t launch_moments(const MomentJob *d_jobs, int njobs, int max_nz, long long slot, const IoPtrs *in,
                            cudaStream_t s);
 cudaError_t launch_features(const LPair *d_pairs, const FeatRow *d_rows, int nrows, long long step, __half *X16,
-                            float *nu, cudaStream_t s);
+                            float *Xf, float *nu, cudaStream_t s);
 cudaError_t launch_train_basis(const TrainHist *d_hist, int nhist, const int n[3], float h, float *B, cudaStream_t s);
 cudaError_t launch_train_moments(const TrainHist *d_hist, int nhist, const float *Mb, int T, float *mom,
                                  cudaStream_t s);
@@ -78,7 +78,8 @@ cudaError_t launch_train_labels(const TrainHist *d_hist, int nhist, const float 
                                 int samples, double cdt, float *labels, cudaStream_t s);
 cudaError_t launch_label_rows(const TrainHist *d_hist, int nhist, const float *labels, const float *nu, int samples,
                               float *Y, cudaStream_t s);
-cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *nu,
-                               long long step, cudaStream_t s);
+// c += re-interpolated nu * (yscale * Y + Ylin) / R_a (network output plus linear skip)
+cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *Ylin,
+                               float yscale, const float *nu, long long step, cudaStream_t s);
 
 }  // namespace rp

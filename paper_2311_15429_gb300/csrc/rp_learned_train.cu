@@ -152,7 +152,7 @@ int max_samples(const LGeom &g, double cdt)
 
 // Histories [h0, h0 + nh) of a data set: rows X (fp16) and targets Y.
 static cudaError_t make_chunk(const LGeom &geo, Rng &rng, int nh, int samples, double c, double dt, __half *X,
-                              float *Y, double *desc, cudaStream_t s)
+                              float *Xf, float *Y, double *desc, cudaStream_t s)
 {
     const double cdt = c * dt;
     const long long N = (long long)geo.n_s[0] * geo.n_s[1] * geo.n_s[2];
@@ -276,14 +276,14 @@ static cudaError_t make_chunk(const LGeom &geo, Rng &rng, int nh, int samples, d
         (e = launch_moments(dJ.p, (int)jobs.size(), geo.n_s[2], 0, nullptr, s)) ||
         (e = launch_train_moments(dH.p, nh, Mb.p, kLHistT, mom.p, s)) ||
         (e = launch_train_labels(dH.p, nh, B.p, geo.n_s, (float)geo.h_s, samples, cdt, labels.p, s)) ||
-        (e = launch_features(dP.p, dR.p, (int)rows.size(), 0, X, nu.p, s)) ||
+        (e = launch_features(dP.p, dR.p, (int)rows.size(), 0, X, Xf, nu.p, s)) ||
         (e = launch_label_rows(dH.p, nh, labels.p, nu.p, samples, Y, s)))
         return e;
     return cudaStreamSynchronize(s);   // the chunk's scratch is freed on return
 }
 
 cudaError_t learned_dataset(const LGeom &geo, uint64_t seed, int nh, int samples, double c, double dt, __half *X,
-                            float *Y, cudaStream_t s, double *desc)
+                            float *Xf, float *Y, cudaStream_t s, double *desc)
 {
     Rng rng{seed};
     const long long N = (long long)geo.n_s[0] * geo.n_s[1] * geo.n_s[2];
@@ -292,8 +292,8 @@ cudaError_t learned_dataset(const LGeom &geo, uint64_t seed, int nh, int samples
     for (int h0 = 0; h0 < nh; h0 += chunk) {
         const int n = std::min(chunk, nh - h0);
         const size_t r0 = (size_t)h0 * samples * 4;
-        cudaError_t e = make_chunk(geo, rng, n, samples, c, dt, X + r0 * kLIn, Y + r0 * kLOut,
-                                   desc ? desc + (size_t)h0 * kLDesc : nullptr, s);
+        cudaError_t e = make_chunk(geo, rng, n, samples, c, dt, X + r0 * kLIn, Xf ? Xf + r0 * kLIn : nullptr,
+                                   Y + r0 * kLOut, desc ? desc + (size_t)h0 * kLDesc : nullptr, s);
         if (e) return e;
     }
     return cudaSuccess;
@@ -324,14 +324,76 @@ cudaError_t learned_train(Mlp &net, const __half *X, const float *Y, int rows, i
     return cudaStreamSynchronize(s);
 }
 
-cudaError_t learned_eval(Mlp &net, const __half *X, const float *Y, int rows, int optin, int sms, cudaStream_t s,
-                         double err[4])
+cudaError_t learned_fit_linear(Mlp &net, const float *Xf, const float *Y, int rows, float *Yres, cudaStream_t s)
 {
-    std::vector<double> num(4, 0.0), den(4, 0.0);
+    DevBuf<double> G, B;
+    cudaError_t e;
+    if ((e = G.alloc((size_t)kLIn * kLIn)) || (e = B.alloc((size_t)kLIn * kLOut)) ||
+        (e = linear_normal(Xf, Y, rows, G.p, B.p, s)))
+        return e;
+    std::vector<double> A((size_t)kLIn * kLIn), b((size_t)kLIn * kLOut);
+    if ((e = cudaMemcpyAsync(A.data(), G.p, A.size() * sizeof(double), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaMemcpyAsync(b.data(), B.p, b.size() * sizeof(double), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return e;
+    // ridge-regularised normal equations (A + lambda I) w = b, Cholesky in FP64
+    double tr = 0.0;
+    for (int i = 0; i < kLIn; ++i) tr += A[(size_t)i * kLIn + i];
+    const double lambda = 1e-9 * tr / kLIn + 1e-300;
+    for (int i = 0; i < kLIn; ++i) A[(size_t)i * kLIn + i] += lambda;
+    for (int j = 0; j < kLIn; ++j) {
+        double d = A[(size_t)j * kLIn + j];
+        for (int k = 0; k < j; ++k) d -= A[(size_t)j * kLIn + k] * A[(size_t)j * kLIn + k];
+        if (!(d > 0.0)) return cudaErrorInvalidValue;
+        const double l = std::sqrt(d);
+        A[(size_t)j * kLIn + j] = l;
+        for (int i = j + 1; i < kLIn; ++i) {
+            double v = A[(size_t)i * kLIn + j];
+            for (int k = 0; k < j; ++k) v -= A[(size_t)i * kLIn + k] * A[(size_t)j * kLIn + k];
+            A[(size_t)i * kLIn + j] = v / l;
+        }
+    }
+    std::vector<float> W((size_t)kLOut * kLIn);
+    std::vector<double> z(kLIn);
+    for (int o = 0; o < kLOut; ++o) {
+        for (int i = 0; i < kLIn; ++i) {          // L z = b
+            double v = b[(size_t)i * kLOut + o];
+            for (int k = 0; k < i; ++k) v -= A[(size_t)i * kLIn + k] * z[k];
+            z[i] = v / A[(size_t)i * kLIn + i];
+        }
+        for (int i = kLIn - 1; i >= 0; --i) {     // L^T w = z
+            double v = z[i];
+            for (int k = i + 1; k < kLIn; ++k) v -= A[(size_t)k * kLIn + i] * z[k];
+            z[i] = v / A[(size_t)i * kLIn + i];
+        }
+        for (int i = 0; i < kLIn; ++i) W[(size_t)o * kLIn + i] = (float)z[i];
+    }
+    if ((e = cudaMemcpyAsync(net.Wlin, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
+    if (!Yres) return cudaStreamSynchronize(s);
+    // the network's targets: what the skip leaves, Y - Wlin x, scaled to unit RMS
+    if ((e = linear_apply(net.Wlin, Xf, rows, Y, -1.0f, Yres, s))) return e;
+    std::vector<float> r((size_t)rows * kLOut);
+    if ((e = cudaMemcpyAsync(r.data(), Yres, r.size() * sizeof(float), cudaMemcpyDeviceToHost, s)) ||
+        (e = cudaStreamSynchronize(s)))
+        return e;
+    double ss = 0.0;
+    for (float v : r) ss += (double)v * v;
+    const double rms = std::sqrt(ss / (double)r.size());
+    net.out_scale = rms > 0.0 ? (float)rms : 1.0f;
+    if ((e = linear_apply(net.Wlin, Xf, rows, Y, -1.0f, Yres, s, 1.0f / net.out_scale))) return e;
+    return cudaStreamSynchronize(s);
+}
+
+cudaError_t learned_eval(Mlp &net, const __half *X, const float *Xf, const float *Y, int rows, int optin, int sms,
+                         cudaStream_t s, double err[4], double err_lin[4])
+{
+    std::vector<double> num(4, 0.0), numl(4, 0.0), den(4, 0.0);
     std::vector<int> idx(net.cap);
-    std::vector<float> out((size_t)net.cap * kLOut), want((size_t)net.cap * kLOut);
+    std::vector<float> out((size_t)net.cap * kLOut), lin((size_t)net.cap * kLOut), want((size_t)net.cap * kLOut);
     DevBuf<int> d_idx;
+    DevBuf<float> d_lin;
     cudaError_t e = d_idx.alloc(net.cap);
+    if (!e) e = d_lin.alloc((size_t)net.cap * kLOut);
     if (e) return e;
     for (int r0 = 0; r0 < rows; r0 += net.cap) {
         const int n = std::min(net.cap, rows - r0);
@@ -339,20 +401,28 @@ cudaError_t learned_eval(Mlp &net, const __half *X, const float *Y, int rows, in
         for (int i = 0; i < padded; ++i) idx[i] = r0 + std::min(i, n - 1);
         if ((e = cudaMemcpyAsync(d_idx.p, idx.data(), padded * sizeof(int), cudaMemcpyHostToDevice, s)) ||
             (e = mlp_gather(net, X, Y, d_idx.p, padded, s)) || (e = mlp_forward(net, padded, false, optin, sms, s)) ||
+            (e = linear_apply(net.Wlin, Xf + (size_t)r0 * kLIn, n, nullptr, 1.0f, d_lin.p, s)) ||
             (e = cudaMemcpyAsync(out.data(), net.Z[3], (size_t)n * kLOut * sizeof(float), cudaMemcpyDeviceToHost, s)) ||
+            (e = cudaMemcpyAsync(lin.data(), d_lin.p, (size_t)n * kLOut * sizeof(float), cudaMemcpyDeviceToHost, s)) ||
             (e = cudaMemcpyAsync(want.data(), net.Y, (size_t)n * kLOut * sizeof(float), cudaMemcpyDeviceToHost, s)) ||
             (e = cudaStreamSynchronize(s)))
             return e;
         for (int i = 0; i < n; ++i) {
             const int f = (r0 + i) % 4;   // rows are (sample, field) with the field fastest
             for (int a = 0; a < kLOut; ++a) {
-                const double d = (double)out[(size_t)i * kLOut + a] - want[(size_t)i * kLOut + a];
+                const size_t o = (size_t)i * kLOut + a;
+                const double w = want[o];
+                const double d = (double)net.out_scale * out[o] + lin[o] - w, dl = (double)lin[o] - w;
                 num[f] += d * d;
-                den[f] += (double)want[(size_t)i * kLOut + a] * want[(size_t)i * kLOut + a];
+                numl[f] += dl * dl;
+                den[f] += w * w;
             }
         }
     }
-    for (int f = 0; f < 4; ++f) err[f] = den[f] > 0.0 ? std::sqrt(num[f] / den[f]) : 0.0;
+    for (int f = 0; f < 4; ++f) {
+        err[f] = den[f] > 0.0 ? std::sqrt(num[f] / den[f]) : 0.0;
+        if (err_lin) err_lin[f] = den[f] > 0.0 ? std::sqrt(numl[f] / den[f]) : 0.0;
+    }
     return cudaSuccess;
 }
 

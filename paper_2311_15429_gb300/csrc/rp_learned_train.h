@@ -44,16 +44,22 @@ int max_samples(const LGeom &g, double cdt);
 // distance between them.
 constexpr int kLDesc = 4 * kLGauss + 2 * kLGauss * kLHistT + 5;
 
-// nh histories x samples samples: rows X [nh * samples * 4][kLIn] (fp16) and
-// targets Y [same][kLOut] (fp32), device arrays the caller allocates; desc
+// nh histories x samples samples: rows X [nh * samples * 4][kLIn] (fp16;
+// Xf the same rows in fp32, optional) and targets Y [same][kLOut] (fp32),
+// device arrays the caller allocates; desc
 // (host, optional) receives the histories' descriptions.
 cudaError_t learned_dataset(const LGeom &geo, uint64_t seed, int nh, int samples, double c, double dt, __half *X,
-                            float *Y, cudaStream_t s, double *desc = nullptr);
+                            float *Xf, float *Y, cudaStream_t s, double *desc = nullptr);
+// The linear skip: least squares (FP64 normal equations, small ridge) of Y
+// on the fp32 rows Xf, into net.Wlin; Yres (optional) receives Y - Wlin x,
+// the network's training targets.
+cudaError_t learned_fit_linear(Mlp &net, const float *Xf, const float *Y, int rows, float *Yres, cudaStream_t s);
 // Adam on minibatches drawn with replacement; cosine learning-rate decay.
 cudaError_t learned_train(Mlp &net, const __half *X, const float *Y, int rows, int iterations, int batch, float lr,
                           uint64_t seed, int optin, int sms, cudaStream_t s, float *final_loss);
-// rel-L2 of the network's outputs against Y per field (rows are field-fastest).
-cudaError_t learned_eval(Mlp &net, const __half *X, const float *Y, int rows, int optin, int sms, cudaStream_t s,
-                         double err[4]);
+// rel-L2 against Y per field (rows are field-fastest) of the linear skip
+// plus the network (err) and of the linear skip alone (err_lin, optional).
+cudaError_t learned_eval(Mlp &net, const __half *X, const float *Xf, const float *Y, int rows, int optin, int sms,
+                         cudaStream_t s, double err[4], double err_lin[4]);
 
 }  // namespace rp

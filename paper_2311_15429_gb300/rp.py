@@ -18,9 +18,10 @@ RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_HISTORY, RP_ERR_CUDA, RP_ERR_OOM, \
     RP_ERR_UNSUPPORTED, RP_ERR_TIMEOUT = range(8)
 RP_MODE_FFT, RP_MODE_DIRECT, RP_MODE_LOWRANK = 0, 1, 2
 RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE = 0x1, 0x2, 0x4
-RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK = 0, 1, 2
+RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
- RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_COUNT) = range(11)
+ RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_MOMENTS, RP_K_LEARNED,
+ RP_K_COUNT) = range(13)
 MAX_DOMAINS = 256
 
 
@@ -36,6 +37,20 @@ class rp_pair_info_t(ctypes.Structure):
                 ("fft_m", ctypes.c_int * 3), ("r_min", ctypes.c_double), ("r_max", ctypes.c_double)]
 
 
+class rp_train_config(ctypes.Structure):
+    _fields_ = [("learned_distance", ctypes.c_double), ("gate", ctypes.c_double), ("histories", ctypes.c_int),
+                ("samples", ctypes.c_int), ("iterations", ctypes.c_int), ("batch", ctypes.c_int),
+                ("lr", ctypes.c_float), ("validation", ctypes.c_int), ("seed", ctypes.c_ulonglong),
+                ("reserved", ctypes.c_int * 8)]
+
+
+class rp_train_report(ctypes.Structure):
+    _fields_ = [("candidates", ctypes.c_int), ("learned", ctypes.c_int), ("train_rows", ctypes.c_longlong),
+                ("final_loss", ctypes.c_float), ("train_seconds", ctypes.c_float), ("val_max", ctypes.c_double),
+                ("val_mean", ctypes.c_double), ("val_linear_max", ctypes.c_double),
+                ("val_linear_mean", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+
+
 class rp_stats(ctypes.Structure):
     _fields_ = [("ndomains", ctypes.c_int), ("npairs_fft", ctypes.c_int),
                 ("npairs_direct", ctypes.c_int), ("max_lag", ctypes.c_int),
@@ -43,7 +58,8 @@ class rp_stats(ctypes.Structure):
                 ("step", ctypes.c_longlong), ("device_bytes", ctypes.c_longlong),
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
                 ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
-                ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("npairs_learned", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 class RPError(RuntimeError):
@@ -75,6 +91,7 @@ SIGNATURES = {
     "rp_mlp_forward": (_I, [_V, _V, _I, _V, _I]),
     "rp_mlp_grad": (_I, [_V, _V, _V, _I, _V, _V, _I]),
     "rp_learned_desc_size": (_I, []),
+    "rp_train_far_model": (_I, [_V, _V, _V]),
     "rp_learned_dataset": (_I, [_V, ctypes.c_double, _V, _V, ctypes.c_double, ctypes.c_ulonglong, _I, _I,
                                 ctypes.c_double, ctypes.c_double, _V, _V, _V, _I]),
     "rp_sync": (_I, [_V]),
@@ -310,6 +327,15 @@ def rp_learned_dataset(n_s, h_s, Lt, direction, Rc, seed, histories, samples, c,
     return X, Y, D
 
 
+def rp_train_far_model(ctx, learned_distance: float, gate: float = 0.0, histories: int = 0, samples: int = 0,
+                       iterations: int = 0, batch: int = 0, lr: float = 0.0, validation: int = 0, seed: int = 1):
+    """Train the learned far field on the context's far pairs; returns the report as a dict."""
+    cfg = rp_train_config(learned_distance, gate, histories, samples, iterations, batch, lr, validation, seed)
+    rep = rp_train_report()
+    _check(load().rp_train_far_model(ctx, ctypes.byref(cfg), ctypes.byref(rep)), ctx)
+    return {name: getattr(rep, name) for name, _ in rp_train_report._fields_ if name != "reserved"}
+
+
 def rp_sync(ctx):
     _check(load().rp_sync(ctx), ctx)
 
@@ -387,6 +413,9 @@ class RetardedPotentials:
 
     def sync(self):
         rp_sync(self.ctx)
+
+    def train_far_model(self, learned_distance: float, **kw):
+        return rp_train_far_model(self.ctx, learned_distance, **kw)
 
     def query(self):
         return rp_query(self.ctx)

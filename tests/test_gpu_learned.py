@@ -133,3 +133,97 @@ def test_dataset_rows_and_targets_match_oracle():
                 worst_y = max(worst_y, np.linalg.norm(Y[row + f] - want) / np.linalg.norm(want))
     assert worst_x < 2e-3, worst_x      # fp16 rows
     assert worst_y < 1e-4, worst_y      # fp32 sums of the direct retarded sum
+
+
+def _far_setup(n=16, dist=3000.0):
+    from paper_2311_15429_gb300 import synth
+    doms = [synth.cubic((0.0, 0.0, 0.0), n, 0.25), synth.cubic((8.0, 0.5, -0.3), n, 0.25),
+            synth.cubic((dist * 0.6, dist * 0.48, -dist * 0.64), n, 0.25)]
+    return doms, synth._sources(doms)
+
+
+def _run_far(doms, hists, train, **kw):
+    import torch
+    from paper_2311_15429_gb300 import synth
+    dev = torch.device("cuda", 0)
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
+                               far_batch=16) as lib:
+        report = lib.train_far_model(500.0, **kw) if train else None
+        q = lib.query()
+        kinds = {(t, s): lib.pair_info(t, s)["kind"] for t in range(3) for s in range(3)}
+        T = hists[0].shape[0]
+        for i in range(T):
+            lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
+                         [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists])
+        phi, A = lib.evaluate()
+        lib.sync()
+        out = [np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)]) for d in range(3)]
+    return out, report, q, kinds
+
+
+def test_trained_far_pairs_match_oracle():
+    """rp_train_far_model moves the four far pairs onto the network (the
+    linear skip plus the MLP); the far field alone (only the far domain
+    active) and the total field then match the FP64 oracle within 1e-3."""
+    from paper_2311_15429_gb300 import synth
+    from _harness import oracle_values, rel_l2
+    doms, srcs = _far_setup()
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
+                               far_batch=16) as lib:
+        T = lib.query()["max_lag"] + 24
+    hists = [s.history(0, T, 0.05) for s in srcs]
+    zero = [np.zeros_like(hists[0]), np.zeros_like(hists[1]), hists[2]]
+    out, rep, q, kinds = _run_far(doms, zero, True)
+    assert rep["candidates"] == 4 and rep["learned"] == 4, rep
+    assert q["npairs_learned"] == 4 and q["npairs_far"] == 0
+    for (t, s), k in kinds.items():
+        assert k == (rp.RP_PAIR_LEARNED if (t == 2) != (s == 2) else rp.RP_PAIR_FFT), (t, s, k)
+    nodes = np.arange(0, doms[0].N, 5)
+    for t in (0, 1):
+        want = oracle_values(doms, zero, 0, synth.C_AU, 0.05, t, T - 1, nodes)
+        errs = rel_l2(out[t][:, nodes], want)
+        assert max(errs) <= 1e-3, ("far only", t, errs)
+    out, rep, q, _ = _run_far(doms, hists, True)
+    for t in range(3):
+        want = oracle_values(doms, hists, 0, synth.C_AU, 0.05, t, T - 1, nodes)
+        errs = rel_l2(out[t][:, nodes], want)
+        assert max(errs) <= 1e-3, ("total", t, errs)
+
+
+def test_learned_gain_over_the_low_rank_path():
+    """What the trained stand-in gains over the method without it (the
+    low-rank far path of the same pairs): the far path's device memory drops
+    from the factor matrices to a few kB of moment rings and node tables,
+    at a far-field error inside the same 1e-3 bar; the training report gives
+    the validation error of the linear skip alone and with the network."""
+    from paper_2311_15429_gb300 import synth
+    doms, _ = _far_setup(24, 3000.0)
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
+                               far_batch=16) as lib:
+        before = lib.query()["far_bytes"]
+        rep = lib.train_far_model(500.0)
+        after = lib.query()["far_bytes"]
+    assert rep["learned"] == 4, rep
+    assert after * 100 < before, (before, after)
+    assert rep["val_max"] <= 1e-3 and rep["val_linear_max"] <= 1e-3, rep
+    print("far-path bytes low-rank %d -> learned %d; validation rel-L2 linear skip %.3g, with network %.3g"
+          % (before, after, rep["val_linear_max"], rep["val_max"]))
+
+
+def test_training_errors_and_state():
+    from paper_2311_15429_gb300 import synth
+    doms, _ = _far_setup()
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05) as lib:     # FFT mode
+        with pytest.raises(rp.RPError) as e:
+            lib.train_far_model(500.0)
+        assert e.value.status == rp.RP_ERR_UNSUPPORTED
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
+                               far_batch=16) as lib:
+        with pytest.raises(rp.RPError) as e:
+            lib.train_far_model(500.0, batch=100)                   # not a multiple of 128
+        assert e.value.status == rp.RP_ERR_ARG
+        rep = lib.train_far_model(1e6)                               # no candidates
+        assert rep["candidates"] == 0 and rep["learned"] == 0
+        with pytest.raises(rp.RPError) as e:
+            lib.train_far_model(500.0)                               # only once
+        assert e.value.status == rp.RP_ERR_STATE
