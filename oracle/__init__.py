@@ -8,6 +8,9 @@ time interpolation of Eq. 7; Eqs. 11-12 give the same number), written in C
 the CUDA library neither links nor imports it, and it shares no code with it.
 
 Parity status per function:
+  * ``eval_points_windows`` -- ``eval_points`` with a stored window per
+    domain (so that a far source needs only the samples around its delay);
+    the same code path as ``eval_points``, which calls it with one window.
   * ``eval_positions`` -- the same sums at arbitrary points; pinned by the
     static Coulomb limit and the retarded phase lag at far points, and by
     agreement with ``eval_points`` where the points are grid nodes of a
@@ -69,6 +72,12 @@ def _bind(path: str):
         ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
         ctypes.c_double, ctypes.c_double, ctypes.c_int,
         ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
+    lib.rpo_eval_windows.restype = ctypes.c_int
+    lib.rpo_eval_windows.argtypes = [
+        ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_void_p, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p,
+        ctypes.c_double, ctypes.c_double, ctypes.c_int,
+        ctypes.c_int, ctypes.c_longlong, ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p]
     lib.rpo_eval_positions.restype = ctypes.c_int
     lib.rpo_eval_positions.argtypes = [
         ctypes.c_int, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p,
@@ -128,6 +137,49 @@ def eval_points(origins: np.ndarray, ns: np.ndarray, hs: Sequence[float],
     if rc != OK:
         raise OracleError(rc)
     return out
+
+
+def eval_points_windows(origins, ns, hs, hists, firsts, c: float, dt: float, target: int, step: int,
+                        nodes, clamp: bool = False) -> np.ndarray:
+    """``eval_points`` with a separate stored window per domain: ``hists[n]``
+    [T_n][4][N_n] holds the samples of time indices firsts[n] .. firsts[n]+T_n-1
+    (one dtype for all).  Returns [len(nodes)][4] float64."""
+    lib = _load()
+    ndom = len(hists)
+    origins = np.ascontiguousarray(origins, dtype=np.float64).reshape(ndom, 3)
+    ns = np.ascontiguousarray(ns, dtype=np.int32).reshape(ndom, 3)
+    hs = np.ascontiguousarray(hs, dtype=np.float64).reshape(ndom)
+    is_f64 = hists[0].dtype == np.float64
+    want = np.float64 if is_f64 else np.float32
+    arrs = [np.ascontiguousarray(a, dtype=want) for a in hists]
+    for d, a in enumerate(arrs):
+        if a.ndim != 3 or a.shape[1:] != (4, int(np.prod(ns[d]))):
+            raise ValueError(f"history of domain {d} has shape {a.shape}")
+    first = np.ascontiguousarray(firsts, dtype=np.int64).reshape(ndom)
+    lens = np.ascontiguousarray([a.shape[0] for a in arrs], dtype=np.int32)
+    ptrs = (ctypes.c_void_p * ndom)(*[a.ctypes.data for a in arrs])
+    nodes = np.ascontiguousarray(nodes, dtype=np.int64).reshape(-1)
+    out = np.zeros((nodes.size, 4), dtype=np.float64)
+    rc = lib.rpo_eval_windows(ndom, origins.ctypes.data, ns.ctypes.data, hs.ctypes.data,
+                              ctypes.cast(ptrs, ctypes.c_void_p), int(is_f64), first.ctypes.data, lens.ctypes.data,
+                              float(c), float(dt), int(bool(clamp)), int(target), int(step),
+                              int(nodes.size), nodes.ctypes.data, out.ctypes.data)
+    if rc != OK:
+        raise OracleError(rc)
+    return out
+
+
+def eval_points_windows_parallel(origins, ns, hs, hists, firsts, c, dt, target, step, nodes, threads=None):
+    """``eval_points_windows`` with the nodes split across host threads
+    (ctypes releases the GIL).  Returns (values, threads used)."""
+    from concurrent.futures import ThreadPoolExecutor
+    nodes = np.asarray(nodes, dtype=np.int64).reshape(-1)
+    nthr = max(1, min(threads or os.cpu_count() or 1, nodes.size))
+    chunks = np.array_split(nodes, nthr)
+    with ThreadPoolExecutor(nthr) as ex:
+        parts = list(ex.map(lambda ch: eval_points_windows(origins, ns, hs, hists, firsts, c, dt, target, step, ch),
+                            chunks))
+    return np.concatenate(parts, axis=0), nthr
 
 
 def eval_positions(origins, ns, hs, hists, hist_first: int, c: float, dt: float, step: int,

@@ -34,11 +34,12 @@
  *   The charge q_e of the paper's four-vector source (Sec. II, before Eq. 2)
  *   is not applied: the caller multiplies by q_e = -1 if wanted.
  *
- * History: the caller passes, per domain, the samples for steps
- * hist_first .. hist_first + hist_len - 1, each sample laid out as
- * [4][N_n] (rho, Jx, Jy, Jz; x fastest within a field).  A sample older than
- * hist_first is an error unless `clamp` is set, in which case it equals the
- * sample at hist_first -- the paper's S(t <= 0) = S(0) of Eqs. 7 and 9.
+ * History: the caller passes, per domain n, the samples for steps
+ * hist_first[n] .. hist_first[n] + hist_len[n] - 1 (rpo_eval: one window
+ * for all domains), each sample laid out as [4][N_n] (rho, Jx, Jy, Jz;
+ * x fastest within a field).  A sample outside the window is an error,
+ * except that with `clamp` a sample older than the window equals its first
+ * sample -- the paper's S(t <= 0) = S(0) of Eqs. 7 and 9.
  *
  * Arithmetic: every sample is promoted to double; each of the four sums is
  * Neumaier-compensated.  c may be +INFINITY (instantaneous limit: tau = 0).
@@ -75,10 +76,14 @@ static double cube_average_constant(void)
     return 3.0 * log(2.0 + sqrt(3.0)) - 0.5 * M_PI;
 }
 
-/* Sample (field f, node q) of domain n at time index j, promoted to double. */
-static int fetch(const void *const *hist, int is_f64, int hist_first, int hist_len, int clamp,
+/* Sample (field f, node q) of domain n at time index j, promoted to double;
+ * domain n's stored window starts at time index first[n] and holds len[n]
+ * samples. */
+static int fetch(const void *const *hist, int is_f64, const long long *first, const int *len, int clamp,
                  int n, long long N, int f, long long q, long long j, double *out)
 {
+    const long long hist_first = first[n];
+    const int hist_len = len[n];
     long long idx = j - hist_first;
     if (idx < 0) {
         if (!clamp)
@@ -96,16 +101,16 @@ static int fetch(const void *const *hist, int is_f64, int hist_first, int hist_l
 }
 
 /*
- * rpo_eval -- retarded phi and A at a list of nodes of one target domain.
+ * rpo_eval_windows -- retarded phi and A at a list of nodes of one target domain.
  *
  *   ndom            number of domains
  *   origin[3*n]     position of node (0,0,0) of domain n
  *   nn[3*n]         grid points (nx, ny, nz) of domain n; node id = x + nx*(y + ny*z)
  *   h[n]            grid spacing of domain n
- *   hist[n]         samples of domain n, [hist_len][4][N_n], float or double
+ *   hist[n]         samples of domain n, [hist_len[n]][4][N_n], float or double
  *   hist_is_f64     nonzero: hist holds doubles
- *   hist_first      time index of hist[n][0]
- *   hist_len        number of stored samples per domain
+ *   hist_first[n]   time index of hist[n][0]
+ *   hist_len[n]     number of stored samples of domain n
  *   c, dt           speed of light and time step (atomic units)
  *   clamp           nonzero: samples before hist_first equal hist_first's
  *   target, step    target domain and the time index l evaluated
@@ -116,14 +121,16 @@ static int fetch(const void *const *hist, int is_f64, int hist_first, int hist_l
  * RPO_ERR_ARG, or RPO_ERR_COINCIDENT (nodes of two different domains at the
  * same place, where 1/R has no defined value).
  */
-int rpo_eval(int ndom, const double *origin, const int *nn, const double *h,
-             const void *const *hist, int hist_is_f64, int hist_first, int hist_len,
-             double c, double dt, int clamp,
-             int target, int step, int npts, const long long *nodes, double *out)
+int rpo_eval_windows(int ndom, const double *origin, const int *nn, const double *h,
+                     const void *const *hist, int hist_is_f64, const long long *hist_first,
+                     const int *hist_len, double c, double dt, int clamp,
+                     int target, long long step, int npts, const long long *nodes, double *out)
 {
-    if (ndom <= 0 || target < 0 || target >= ndom || npts < 0 || hist_len <= 0 || !(dt > 0.0) ||
-        !(c > 0.0))
+    if (ndom <= 0 || target < 0 || target >= ndom || npts < 0 || !(dt > 0.0) || !(c > 0.0))
         return RPO_ERR_ARG;
+    for (int n = 0; n < ndom; ++n)
+        if (hist_len[n] <= 0)
+            return RPO_ERR_ARG;
     const double C = cube_average_constant();
     const int tx = nn[3 * target + 0], ty = nn[3 * target + 1], tz = nn[3 * target + 2];
     const long long Nt = (long long)tx * ty * tz;
@@ -191,6 +198,27 @@ int rpo_eval(int ndom, const double *origin, const int *nn, const double *h,
 }
 
 /*
+ * rpo_eval -- rpo_eval_windows with one stored window for every domain:
+ * samples hist_first .. hist_first + hist_len - 1.
+ */
+int rpo_eval(int ndom, const double *origin, const int *nn, const double *h,
+             const void *const *hist, int hist_is_f64, int hist_first, int hist_len,
+             double c, double dt, int clamp,
+             int target, int step, int npts, const long long *nodes, double *out)
+{
+    if (ndom <= 0 || ndom > 4096)
+        return RPO_ERR_ARG;
+    long long first[4096];
+    int len[4096];
+    for (int n = 0; n < ndom; ++n) {
+        first[n] = hist_first;
+        len[n] = hist_len;
+    }
+    return rpo_eval_windows(ndom, origin, nn, h, hist, hist_is_f64, first, len, c, dt, clamp, target,
+                            step, npts, nodes, out);
+}
+
+/*
  * rpo_eval_positions -- the same retarded sums at arbitrary points (not grid
  * nodes): every node of every domain is a source with weight h_n^3 / R and
  * the hat-interpolated sample at the retarded time (Eqs. 2, 7, 8).  There is
@@ -202,11 +230,17 @@ int rpo_eval(int ndom, const double *origin, const int *nn, const double *h,
  * Other arguments as for rpo_eval.
  */
 int rpo_eval_positions(int ndom, const double *origin, const int *nn, const double *h,
-                       const void *const *hist, int hist_is_f64, int hist_first, int hist_len,
+                       const void *const *hist, int hist_is_f64, int hist_first_in, int hist_len_in,
                        double c, double dt, int clamp, int step, int npos, const double *pos, double *out)
 {
-    if (ndom <= 0 || npos < 0 || hist_len <= 0 || !(dt > 0.0) || !(c > 0.0))
+    if (ndom <= 0 || ndom > 4096 || npos < 0 || hist_len_in <= 0 || !(dt > 0.0) || !(c > 0.0))
         return RPO_ERR_ARG;
+    long long hist_first[4096];
+    int hist_len[4096];
+    for (int n = 0; n < ndom; ++n) {
+        hist_first[n] = hist_first_in;
+        hist_len[n] = hist_len_in;
+    }
     for (int p = 0; p < npos; ++p) {
         const double rx = pos[3 * p + 0], ry = pos[3 * p + 1], rz = pos[3 * p + 2];
         rpo_acc acc[4] = {{0, 0}, {0, 0}, {0, 0}, {0, 0}};

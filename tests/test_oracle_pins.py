@@ -316,3 +316,21 @@ def test_coincident_nodes_rejected():
     with pytest.raises(oracle.OracleError) as e:
         oracle.eval_points(origins, ns, hs, hist, 0, INF, 0.05, 0, 0, [7])
     assert e.value.code == oracle.ERR_COINCIDENT
+
+
+def test_per_domain_windows_match_one_window():
+    """Per-domain stored windows hold the same samples as one common window,
+    so the sums agree exactly; a sample outside a domain's window is an error."""
+    import oracle
+    rng = np.random.default_rng(11)
+    origins = [np.zeros(3), np.array([30.0, 2.0, -1.0])]
+    ns, hs = [(4, 3, 3), (3, 3, 2)], [0.4, 0.5]
+    c, dt, T, step = 137.036, 0.05, 40, 39
+    hists = [rng.standard_normal((T, 4, 36)), rng.standard_normal((T, 4, 18))]
+    nodes = np.arange(18)
+    a = oracle.eval_points(origins, ns, hs, hists, 0, c, dt, 1, step, nodes)
+    w = [hists[0][25:], hists[1][36:]]
+    b = oracle.eval_points_windows(origins, ns, hs, w, [25, 36], c, dt, 1, step, nodes)
+    assert np.array_equal(a, b)
+    with pytest.raises(oracle.OracleError):
+        oracle.eval_points_windows(origins, ns, hs, [hists[0][36:], hists[1][36:]], [36, 36], c, dt, 1, step, nodes)
