@@ -89,6 +89,11 @@ typedef enum {
 /* Time every kernel launch with CUDA events on the context stream; read the
  * totals with rp_kernel_stats. */
 #define RP_FLAG_PROFILE 0x4u
+/* RP_MODE_LOWRANK: build the far pairs' factors in rp_train_far_model (for
+ * the pairs the learned field does not take) instead of in rp_finalize, so
+ * that factors of pairs that move to the network are never made.  Until
+ * rp_train_far_model has run, rp_push returns RP_ERR_STATE. */
+#define RP_FLAG_DEFER_FAR 0x8u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
@@ -408,8 +413,10 @@ rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], c
  */
 typedef struct {
     double learned_distance; /* smallest box distance of a candidate (bohr, > 0) */
-    double gate;             /* largest validation rel-L2 of a learned pair (0: 1e-3) */
-    int histories;           /* training histories (0: 256) */
+    double gate;             /* largest validation rel-L2 of a learned pair (0: 5e-4, half the 1e-3
+                              * bar of the far field: the validation sees a few histories and not
+                              * the final interpolation onto the grid) */
+    int histories;           /* training histories (0: 512) */
     int samples;             /* samples per history (0: 32, capped by the delay tables) */
     int iterations;          /* Adam steps (0: 3000) */
     int batch;               /* rows per step, a multiple of 128 (0: 1024) */

@@ -1278,7 +1278,7 @@ rp_status rp_finalize(rp_ctx *ctx)
 
     // ---- far pairs
     RP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
-    if ((st = build_far(ctx, max_optin))) return st;
+    if (!(ctx->cfg.flags & RP_FLAG_DEFER_FAR) && (st = build_far(ctx, max_optin))) return st;
 
     // ---- device tables and kernel limits
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
@@ -1313,6 +1313,8 @@ rp_status check_ready(rp_ctx *ctx)
 // previous one is complete.
 rp_status begin_push(rp_ctx *ctx, int id)
 {
+    if ((ctx->cfg.flags & RP_FLAG_DEFER_FAR) && !ctx->trained)
+        return fail(ctx, RP_ERR_STATE, "RP_FLAG_DEFER_FAR: call rp_train_far_model before the first push");
     const int nd = (int)ctx->doms.size();
     if (ctx->step < 0 || ctx->npushed == nd) {
         ctx->step += 1;
@@ -1467,6 +1469,8 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
         if (!d_rho[d] || !d_J[d]) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL buffer");
     if (ctx->step >= 0 && ctx->npushed != 0 && ctx->npushed != nd)
         return fail(ctx, RP_ERR_STATE, "rp_push_all inside a partially pushed step");
+    if ((ctx->cfg.flags & RP_FLAG_DEFER_FAR) && !ctx->trained)
+        return fail(ctx, RP_ERR_STATE, "RP_FLAG_DEFER_FAR: call rp_train_far_model before the first push");
     ctx->step += 1;
     std::fill(ctx->pushed.begin(), ctx->pushed.end(), 1);
     ctx->npushed = nd;
@@ -1731,8 +1735,8 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     if (!(cfg.learned_distance > 0.0) || cfg.gate < 0.0 || cfg.histories < 0 || cfg.samples < 0 ||
         cfg.iterations < 0 || cfg.batch < 0 || cfg.batch % 128 || cfg.lr < 0.0f || cfg.validation < 0)
         return fail(ctx, RP_ERR_ARG, "rp_train_far_model: bad configuration");
-    if (cfg.gate == 0.0) cfg.gate = 1e-3;
-    if (!cfg.histories) cfg.histories = 256;
+    if (cfg.gate == 0.0) cfg.gate = 5e-4;
+    if (!cfg.histories) cfg.histories = 512;
     if (!cfg.samples) cfg.samples = 32;
     if (!cfg.iterations) cfg.iterations = 3000;
     if (!cfg.batch) cfg.batch = 1024;
@@ -1753,6 +1757,13 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     report.candidates = (int)cand.size();
     ctx->trained = true;
     if (cand.empty()) {
+        if (ctx->cfg.flags & RP_FLAG_DEFER_FAR) {
+            if ((st = build_far(ctx, ctx->smem_optin))) return st;
+            RP_CUDA(ctx, cudaMemcpy(ctx->d_fwd, ctx->fwd.data(), ctx->fwd.size() * sizeof(FwdRing),
+                                    cudaMemcpyHostToDevice));
+            RP_CUDA(ctx, cudaMemcpy(ctx->d_inv, ctx->inv.data(), ctx->inv.size() * sizeof(InvTarget),
+                                    cudaMemcpyHostToDevice));
+        }
         if (rep) *rep = report;
         return RP_OK;
     }
@@ -1848,7 +1859,7 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     }
     report.val_mean = elig.empty() ? 0.0 : vsum / (double)elig.size();
     report.val_linear_mean = elig.empty() ? 0.0 : lsum / (double)elig.size();
-    if (report.learned) {
+    if (report.learned || (ctx->cfg.flags & RP_FLAG_DEFER_FAR)) {
         clear_far(ctx);
         if ((st = build_far(ctx, ctx->smem_optin))) return st;
         if ((st = build_learned(ctx, weights, wlin))) return st;

@@ -90,9 +90,13 @@ __global__ void __launch_bounds__(kFarThreads) k_far_zero(const FarTarget *__res
     const int ti = blockIdx.y;
     if (ti >= ntgt) return;
     const FarTarget T = tgts[ti];
+    // a target with no low-rank pairs (only learned ones) has its slot set
+    // whole at evaluation and is not zeroed here
+    if (T.lag_hi_max < 0) return;
     const int per = T.r * 4;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < batch * per; i += gridDim.x * blockDim.x) {
         const long long s = j1 - batch + T.lag_hi_max + 1 + i / per;
+        if (s < 0) continue;   // steps before the first push receive nothing
         T.cring[(s % T.depth) * per + i % per] = 0.0f;
     }
 }

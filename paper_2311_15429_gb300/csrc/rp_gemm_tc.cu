@@ -371,9 +371,14 @@ cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB
     return cudaGetLastError();
 }
 
-// Number of K splits that fills the SMs with one wave (one CTA per SM: the
-// stage ring takes most of the shared memory), each split with at least
-// `min_tiles` k-tiles.
+// Number of K splits: enough for one wave of CTAs (one per SM: the stage
+// ring takes most of the shared memory), each split with at least
+// `min_tiles` k-tiles -- and at least enough that no split accumulates more
+// than kMaxSplitTiles k-tiles: the fp32 tensor-memory accumulator takes one
+// rounding per MMA, so long K ranges (a 64^3 source is 4096 k-tiles) are cut
+// into chains whose partial sums the reduction adds in a fixed order.
+constexpr int kMaxSplitTiles = 64;
+
 int gemm_splits(int M, int K, int split3, int sms, int min_tiles)
 {
     (void)split3;
@@ -381,7 +386,7 @@ int gemm_splits(int M, int K, int split3, int sms, int min_tiles)
     const int kt_all = K / kBK;
     int splits = std::max(1, sms / mtiles);
     splits = std::min(splits, std::max(1, kt_all / std::max(1, min_tiles)));
-    return splits;
+    return std::max(splits, (kt_all + kMaxSplitTiles - 1) / kMaxSplitTiles);
 }
 
 }  // namespace rp

@@ -274,3 +274,45 @@ def workload(name: str) -> Workload:
         return Workload("cfg5", doms, C_AU, 0.05, 0, 1000,
                         "32 x 48^3, 500-50000 bohr apart", _sources(doms))
     raise KeyError(name)
+
+
+class DeviceSlices:
+    """The same slices as ``GaussianSources.slice``, made on a CUDA device:
+    the per-node basis (g_k and grad Phi_k) is uploaded once as float32 and a
+    slice is one small contraction with the amplitudes at t, so that histories
+    thousands of steps deep need not pass through host memory."""
+
+    def __init__(self, sources: Sequence[GaussianSources], device):
+        import torch
+        self.torch = torch
+        self.sources = list(sources)
+        self.device = device
+        self.basis = []
+        for s in self.sources:
+            b = np.concatenate([s.g[:, None, :], s.gradphi], axis=1)        # [K][4][N]
+            self.basis.append(torch.from_numpy(b.astype(np.float32)).to(device))
+        same = len({(s.dom.N, s.sigma.size) for s in self.sources}) == 1
+        self.stacked = torch.stack(self.basis) if same else None          # [D][K][4][N]
+
+    def _weights(self, d: int, t: float):
+        A, dA = self.sources[d].amplitudes(t)
+        return np.concatenate([A[:, None], np.repeat((dA / (4.0 * math.pi))[:, None], 3, axis=1)], axis=1)
+
+    def slice(self, d: int, t: float):
+        """[4][N] float32 device tensor of domain d at time t."""
+        wt = self.torch.from_numpy(self._weights(d, t).astype(np.float32)).to(self.device)   # [K][4]
+        return (wt[:, :, None] * self.basis[d]).sum(0)
+
+    def step(self, j: int, dt: float):
+        """(rho list, J list) of every domain at t = j dt."""
+        if self.stacked is not None:
+            w = np.stack([self._weights(d, j * dt) for d in range(len(self.sources))])      # [D][K][4]
+            wt = self.torch.from_numpy(w.astype(np.float32)).to(self.device)
+            x = (wt[:, :, :, None] * self.stacked).sum(1)                                   # [D][4][N]
+            return [x[d, 0] for d in range(x.shape[0])], [x[d, 1:].reshape(-1) for d in range(x.shape[0])]
+        rho, J = [], []
+        for d in range(len(self.sources)):
+            x = self.slice(d, j * dt)
+            rho.append(x[0].contiguous())
+            J.append(x[1:].reshape(-1).contiguous())
+        return rho, J

@@ -1,0 +1,78 @@
+"""The deep-history workloads on the GPU, far field alone, against the FP64
+oracle with a stored window per source (only the samples a pair reads).
+
+cfg3: 8 x 64^3 sub-domains, h = 0.25, in a 20000 bohr cube (every pair on the
+low-rank path: bf16 hi/lo tcgen05 factors).  cfg5: 32 x 48^3 sub-domains,
+500-50000 bohr apart (every pair a learned candidate; those that pass the
+validation gate run on the network, the rest on the low-rank path).  Only
+domain 0 carries a source, so every other domain's field is the far field
+of the pairs (t, 0) alone.  Inputs are made on the device (the histories are
+thousands of steps deep); the oracle gets, per domain, the samples of its
+pair's lag window.  Bar: 1e-3 rel-L2 per field, the bf16 / learned far field's.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2311_15429_gb300 import rp, synth
+
+from _harness import rel_l2
+
+pytestmark = pytest.mark.gpu
+TOL = 1e-3
+
+
+def far_only_errors(name, targets, nodes_per, train=False, far_points=0, **train_kw):
+    """Per-target [4] rel-L2 of the far field of domain 0 alone, the training
+    report (or None) and the context's query after the run."""
+    import torch
+    w = synth.workload(name)
+    dev = torch.device("cuda", 0)
+    gen = synth.DeviceSlices(w.sources[:1], dev)
+    flags = rp.RP_FLAG_DEFER_FAR if train else 0
+    zr = [torch.zeros(d.N, device=dev) for d in w.domains]
+    zJ = [torch.zeros(3 * d.N, device=dev) for d in w.domains]
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=flags, far_distance=500.0,
+                               far_batch=32, far_points=far_points) as lib:
+        rep = lib.train_far_model(2000.0, **train_kw) if train else None
+        info = {t: lib.pair_info(t, 0) for t in targets}
+        L = lib.query()["max_lag"] + 8
+        for j in range(L):
+            r, J = gen.step(j, w.dt)
+            lib.push_all([r[0]] + zr[1:], [J[0]] + zJ[1:])
+        phi, A = lib.evaluate()
+        lib.sync()
+        got = {t: np.concatenate([phi[t].cpu().numpy()[None], A[t].cpu().numpy().reshape(3, -1)]) for t in targets}
+        q = lib.query()
+    step = L - 1
+    rng = np.random.default_rng(3)
+    errs = {}
+    for t in targets:
+        p = info[t]
+        lo, hi = step - p["lag_hi"] - 1, step - p["lag_lo"]
+        src = w.sources[0].history(lo, hi + 1, w.dt)
+        tgt = np.zeros((16, 4, w.domains[t].N), dtype=np.float32)      # the target's own (zero) samples
+        nodes = rng.integers(0, w.domains[t].N, nodes_per)
+        doms = [w.domains[t], w.domains[0]]
+        vals, _ = oracle.eval_points_windows_parallel([d.origin for d in doms], [d.n for d in doms],
+                                                      [d.h for d in doms], [tgt, src], [step - 15, lo],
+                                                      w.c, w.dt, 0, step, nodes)
+        errs[t] = rel_l2(got[t][:, nodes], vals)
+    return errs, rep, q
+
+
+def test_cfg3_low_rank_far_field():
+    errs, _, q = far_only_errors("cfg3", [1, 4, 7], 96)
+    assert q["npairs_far"] == 56 and q["npairs_fft"] == 8
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg3", t, e)
+
+
+def test_cfg5_learned_far_field():
+    errs, rep, q = far_only_errors("cfg5", [1, 9, 17, 31], 64, train=True)
+    print("cfg5 training report", rep, "learned", q["npairs_learned"], "low-rank", q["npairs_far"])
+    assert rep["candidates"] == 992
+    assert q["npairs_learned"] + q["npairs_far"] == 992
+    assert q["npairs_learned"] == rep["learned"] and rep["learned"] > 0, rep
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg5", t, e)

@@ -227,3 +227,44 @@ def test_training_errors_and_state():
         with pytest.raises(rp.RPError) as e:
             lib.train_far_model(500.0)                               # only once
         assert e.value.status == rp.RP_ERR_STATE
+
+
+def test_learned_pairs_beside_low_rank_pairs():
+    """Learned and low-rank far pairs in one context: domains 0 and 1 are
+    1000 bohr apart (low-rank), the rest at least 2000 bohr from every other
+    domain (learned).  Only domain 2 carries a source; every other domain's
+    field is its far field, whether the target also has low-rank pairs (its
+    coefficient slot is added to) or only learned ones (the slot is set)."""
+    import torch
+    from paper_2311_15429_gb300 import synth
+    from _harness import oracle_values, rel_l2
+    dev = torch.device("cuda", 0)
+    doms = [synth.cubic((0.0, 0.0, 0.0), 16, 0.25), synth.cubic((1000.0, 0.0, 0.0), 16, 0.25),
+            synth.cubic((300.0, 2600.0, -500.0), 16, 0.25), synth.cubic((-2400.0, 900.0, 1700.0), 16, 0.25)]
+    srcs = synth._sources(doms)
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
+                               far_batch=16) as lib:
+        rep = lib.train_far_model(2000.0)
+        q = lib.query()
+        kinds = [[lib.pair_info(t, s)["kind"] for s in range(4)] for t in range(4)]
+        T = q["max_lag"] + 20
+        hist = srcs[2].history(0, T, 0.05)
+        zero = [torch.zeros(d.N, device=dev) for d in doms]
+        zJ = [torch.zeros(3 * d.N, device=dev) for d in doms]
+        for i in range(T):
+            r = list(zero)
+            J = list(zJ)
+            r[2] = torch.from_numpy(hist[i, 0].copy()).to(dev)
+            J[2] = torch.from_numpy(hist[i, 1:].copy().reshape(-1)).to(dev)
+            lib.push_all(r, J)
+        phi, A = lib.evaluate()
+        lib.sync()
+        out = [np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)]) for d in range(4)]
+    assert kinds[0][1] == rp.RP_PAIR_LOWRANK and kinds[1][0] == rp.RP_PAIR_LOWRANK
+    assert rep["learned"] == 10 and q["npairs_learned"] == 10 and q["npairs_far"] == 2, (rep, q)
+    hists = [np.zeros_like(hist), np.zeros_like(hist), hist, np.zeros_like(hist)]
+    nodes = np.arange(0, doms[0].N, 9)
+    for t in (0, 1, 3):
+        want = oracle_values(doms, hists, 0, synth.C_AU, 0.05, t, T - 1, nodes)
+        errs = rel_l2(out[t][:, nodes], want)
+        assert max(errs) <= 1e-3, (t, errs)
