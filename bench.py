@@ -41,19 +41,32 @@ def parse():
     p.add_argument("--steps", type=int, default=2000)
     p.add_argument("--warmup", type=int, default=20)
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    p.add_argument("--workload", default="cfg2", help="cfg1 | cfg2 | near48 (48^3 pair 200 bohr apart)")
+    p.add_argument("--workload", default="cfg2",
+                   help="cfg1 | cfg2 | near48 (48^3 pair 200 bohr apart) | cfg3 | cfg5 | cfg5x8 (first 8 "
+                        "domains of cfg5); cfg3 and cfg5* have thousands-deep histories and run the far path")
     p.add_argument("--no-plain", action="store_true", help="skip timing the plain direct path")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--oracle-nodes", type=int, default=8192, help="oracle sample per domain")
-    p.add_argument("--mode", choices=["fft", "lowrank"], default="fft",
-                   help="fft: every pair by FFT (FP32); lowrank: far pairs by bf16 tensor-core factors")
+    p.add_argument("--mode", choices=["fft", "lowrank", "learned"], default="fft",
+                   help="fft: every pair by FFT (FP32); lowrank: far pairs by bf16 tensor-core factors; "
+                        "learned: far pairs by the trained stand-in (low-rank where the gate refuses)")
+    p.add_argument("--learned-distance", type=float, default=2000.0)
     p.add_argument("--far-distance", type=float, default=1000.0)
     p.add_argument("--far-batch", type=int, default=32)
     return p.parse_args()
 
 
+DEEP = ("cfg3", "cfg5", "cfg5x8")
+
+
 def get_workload(name):
+    if name == "cfg5x8":
+        w = synth.workload("cfg5")
+        w.name = "cfg5x8"
+        w.domains, w.sources = w.domains[:8], w.sources[:8]
+        w.description = "first 8 of cfg5's 32 x 48^3 sub-domains (3000-38000 bohr apart)"
+        return w
     if name == "near48":
         w = synth.two_domain(48, 0.25, 200.0, "near48", steps=100, history=40)
         w.description = "2 x 48^3, h=0.25 bohr, centres 200 bohr apart on x (small ring, for profiling)"
@@ -525,11 +538,122 @@ def lib_bytes_str(w, info, depth):
     return f"{alg['mac_inv_column'] / 2**20:.0f} MiB"
 
 
+def run_deep(args, rank, world, local):
+    """cfg3 / cfg5: every cross pair is far.  Inputs are made on the device
+    (histories thousands of steps deep); the accuracy check samples target
+    nodes against the FP64 oracle with a stored window per source."""
+    import torch
+    import oracle
+    from paper_2311_15429_gb300 import rp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = get_workload(args.workload)
+    mode = "lowrank" if args.mode == "fft" else args.mode
+    flags = rp.RP_FLAG_PROFILE | (rp.RP_FLAG_DEFER_FAR if mode == "learned" else 0)
+    gen = synth.DeviceSlices(w.sources, dev)
+    lib = rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=flags, device=local,
+                                stream=stream, far_distance=args.far_distance, far_batch=args.far_batch)
+    train = lib.train_far_model(args.learned_distance) if mode == "learned" else None
+    q = lib.query()
+    nd = len(w.domains)
+    info = {(t, s): lib.pair_info(t, s) for t in range(nd) for s in range(nd)}
+    pre = q["max_lag"] + 1
+    W, K = args.warmup, args.steps
+    for j in range(pre + W):
+        r, J = gen.step(j - pre, w.dt)
+        lib.push_all(r, J)
+        if j >= pre:
+            lib.evaluate()
+    lib.sync()
+    check = pre + W - 1 - pre               # time index of the last continuous step
+    acc = None
+    if rank == 0 and not args.no_cpu:
+        tgts = [1, nd // 2]
+        errs = []
+        rng = np.random.default_rng(0)
+        got = {t: torch.cat([lib.phi[t][None], lib.A[t].reshape(3, -1)]).cpu().numpy() for t in tgts}
+        t0 = time.perf_counter()
+        for t in tgts:
+            hists, firsts = [], []
+            for s in range(nd):
+                p = info[(t, s)]
+                lo, hi = check - p["lag_hi"] - 1, check - p["lag_lo"]
+                hists.append(w.sources[s].history(lo, hi + 1, w.dt))
+                firsts.append(lo)
+            nodes = np.sort(rng.choice(w.domains[t].N, 48, replace=False))
+            vals, threads = oracle.eval_points_windows_parallel([d.origin for d in w.domains],
+                                                                [d.n for d in w.domains], [d.h for d in w.domains],
+                                                                hists, firsts, w.c, w.dt, t, check, nodes)
+            g = got[t][:, nodes]
+            errs += [float(np.linalg.norm(g[f] - vals[:, f]) / np.linalg.norm(vals[:, f])) for f in range(4)]
+        acc = {"rel_l2_max": max(errs), "rel_l2_per_field_domain": errs,
+               "checked": f"48 seeded nodes of domains {tgts} at t={check * w.dt:.2f}, total field, vs FP64 oracle "
+                          f"({time.perf_counter() - t0:.1f} s)"}
+    # timed region: cycled device inputs
+    ncycle = 16
+    cyc = [gen.step(pre + W + i, w.dt) for i in range(ncycle)]
+    rp.rp_kernel_stats(lib.ctx, 0, reset=True)
+    clocks = ClockSampler(local)
+    barrier(world)
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.15)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        r, J = cyc[i % ncycle]
+        lib.push_all(r, J)
+        lib.evaluate()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    kstats, launches = {}, 0
+    for kind in range(rp.RP_K_COUNT):
+        n, t = rp.rp_kernel_stats(lib.ctx, kind)
+        if n:
+            kstats[rp.rp_kernel_name(kind)] = {"launches": n, "avg_us": 1e3 * t / n, "total_ms": t}
+            launches += n
+    alg = algorithmic_bytes(w, info)
+    peak, peak_kind = measured_peak()
+    for k in kstats:
+        if k in alg:
+            kstats[k]["algorithmic_GBps"] = alg[k] / (kstats[k]["avg_us"] * 1e-6) / 1e9
+    dom = max(kstats, key=lambda k: kstats[k]["total_ms"])
+    roof = None
+    if dom in alg:
+        ach = alg[dom] / (kstats[dom]["avg_us"] * 1e-6) / 1e9
+        roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
+                "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": committed_traffic(dom, w.name),
+                "algorithmic_bytes_per_launch": alg[dom]}
+    q = lib.query()
+    lib.close()
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": world * w.points * K / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
+        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic",
+        "config": {"workload": w.name, "description": w.description, "points_per_step": w.points,
+                   "path": f"FFT self terms; far pairs {mode}", "far_pairs": q["npairs_far"],
+                   "learned_pairs": q["npairs_learned"], "far_bytes": q["far_bytes"],
+                   "l2": f"{ncycle} device-made input slices per domain cycled ({w.points * 16 * ncycle / 2**20:.0f} MiB)",
+                   "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
+        "training": train, "accuracy": acc, "roofline": roof, "kernels": kstats, "gpu_launches": launches,
+        "clocks": clk, "e2e": None, "cpu_baseline": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload in DEEP:
+        run_deep(args, rank, world, local)
     else:
         run_ours(args, rank, world, local)
     if world > 1:

@@ -396,11 +396,12 @@ rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], c
  * charges with oscillating amplitudes and their continuity-consistent
  * currents, random directions and distances spanning the candidates'),
  * whose targets are the direct retarded sums (Eqs. 2, 7, 8) at those nodes.
- * Each candidate is then validated on fresh histories in its own geometry;
- * if the network's rel-L2 error (worst of the four fields) is at most
- * `gate`, the pair becomes RP_PAIR_LEARNED: its low-rank factors are
+ * Each candidate is then validated on fresh histories in its own geometry,
+ * with and without the network's output; the pair keeps the network only if
+ * it lowers the error, and if the better rel-L2 error (worst of the four
+ * fields) is at most `gate`, the pair becomes RP_PAIR_LEARNED: its low-rank factors are
  * dropped, its source's moments are taken at every push, and each
- * rp_evaluate runs the network for it.  Otherwise it stays on the low-rank
+ * rp_evaluate runs the learned stand-in for it.  Otherwise it stays on the low-rank
  * path, which remains the fallback and the judge of the network's error.
  *
  * Call after rp_finalize and before the first push, on a context that has
@@ -436,7 +437,10 @@ typedef struct {
     double val_mean;         /* mean validation rel-L2 */
     double val_linear_max;   /* the same with the linear skip alone (no network) */
     double val_linear_mean;
-    int reserved[4];
+    int network_pairs;       /* learned pairs that add the network's output (the others use the
+                              * linear skip alone, where the network did not lower their
+                              * validation error) */
+    int reserved[3];
 } rp_train_report;
 
 rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg, rp_train_report *report);

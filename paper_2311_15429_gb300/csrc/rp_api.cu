@@ -170,7 +170,11 @@ struct rp_ctx {
     MomentJob *d_mjobs = nullptr;
     float *d_lnu = nullptr;
     float *d_lxf = nullptr, *d_lylin = nullptr;   // fp32 network rows and linear-skip outputs
+    float *d_lcontrib = nullptr;      // per-pair contributions [pairs][64][4]
+    int *d_lpair_r = nullptr;         // per-pair target node count
     int lrows = 0, npairs_learned = 0, mjob_max_nz = 0;
+    bool net_used = false;            // some learned pair adds the network's output
+    std::vector<char> net_pair;       // [t * ndom + s]: the pair uses the network (else the linear skip alone)
     int smem_optin = 0;
     std::vector<float *> in_stage;    // per domain [4][N], for host pushes
     std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
@@ -680,7 +684,8 @@ void box_extent(const DomainDesc &d, double L[3])
 // Inference structures of the learned pairs (after build_far): moment rings
 // and jobs per source, pair records (sorted by target), target records and
 // the inference network with the trained weights.
-rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const std::vector<float> &wlin)
+rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const std::vector<float> &wlin,
+                        float out_scale)
 {
     const int nd = (int)ctx->doms.size();
     const double cdt = ctx->cfg.c * ctx->cfg.dt;
@@ -746,11 +751,18 @@ rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const st
                 }
                 P.Ra[a] = (float)std::sqrt(d2);
             }
-            std::vector<float> Pm;
+            std::vector<float> Pm, PT;
             reinterp_matrix(Lt, R, ct, ctx->far_tnodes[t].data(), Pm);
+            const int r = (int)(Pm.size() / kLOut);
+            PT.resize(Pm.size());
+            for (int b = 0; b < r; ++b)
+                for (int a = 0; a < kLOut; ++a) PT[(size_t)a * r + b] = Pm[(size_t)b * kLOut + a];
             float *dP = nullptr;
-            if ((st = upload(ctx, &dP, Pm))) return st;
+            if ((st = upload(ctx, &dP, PT))) return st;
             P.P = dP;
+            const bool use = ctx->net_pair.size() == (size_t)nd * nd && ctx->net_pair[(size_t)t * nd + s];
+            P.yscale = use ? out_scale : 0.0f;
+            ctx->net_used = ctx->net_used || use;
             ctx->lpairs.push_back(P);
         }
         const int p1 = (int)ctx->lpairs.size();
@@ -766,6 +778,14 @@ rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const st
         ctx->ltgts.push_back(T);
     }
     ctx->npairs_learned = (int)ctx->lpairs.size();
+    {
+        std::vector<int> pr(ctx->lpairs.size());
+        for (const LTarget &T : ctx->ltgts)
+            for (int p = T.p0; p < T.p1; ++p) pr[p] = T.r;
+        if ((st = upload(ctx, &ctx->d_lpair_r, pr)) ||
+            (st = dev_alloc(ctx, &ctx->d_lcontrib, ctx->lpairs.size() * kLOut * 4)))
+            return st;
+    }
     if ((st = upload(ctx, &ctx->d_lpairs, ctx->lpairs)) || (st = upload(ctx, &ctx->d_ltgts, ctx->ltgts)) ||
         (st = upload(ctx, &ctx->d_mjobs, ctx->mjobs)) || (st = dev_alloc(ctx, &ctx->d_lnu, 4 * ctx->lpairs.size())))
         return st;
@@ -1530,10 +1550,12 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
                  cudaError_t e = launch_features(ctx->d_lpairs, nullptr, (int)ctx->lpairs.size(), step,
                                                  ctx->net.X16, ctx->d_lxf, ctx->d_lnu, ctx->stream);
                  if (!e) e = linear_apply(ctx->net.Wlin, ctx->d_lxf, nrows, nullptr, 1.0f, ctx->d_lylin, ctx->stream);
-                 if (!e) e = mlp_forward(ctx->net, ctx->lrows, false, ctx->smem_optin, ctx->sm_count, ctx->stream);
+                 if (!e && ctx->net_used)
+                     e = mlp_forward(ctx->net, ctx->lrows, false, ctx->smem_optin, ctx->sm_count, ctx->stream);
                  if (!e)
-                     e = launch_learned_out(ctx->d_ltgts, (int)ctx->ltgts.size(), ctx->d_lpairs, ctx->net.Z[3],
-                                            ctx->d_lylin, ctx->net.out_scale, ctx->d_lnu, step, ctx->stream);
+                     e = launch_learned_out(ctx->d_ltgts, (int)ctx->ltgts.size(), ctx->d_lpairs,
+                                            (int)ctx->lpairs.size(), ctx->d_lpair_r, ctx->net.Z[3], ctx->d_lylin,
+                                            ctx->d_lnu, ctx->d_lcontrib, step, ctx->stream);
                  return e;
              })))
             return st;
@@ -1828,10 +1850,49 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
         box_centre(ctx->doms[s], cs);
         for (int a = 0; a < 3; ++a) vg.dir[a] = (ct[a] - cs[a]) / dist[i];
         vg.Rc = dist[i];
+        // validated at the target's own far-path nodes (the canonical values
+        // carried there as evaluation does), so that the re-interpolation's
+        // error is part of what the gate judges
+        std::vector<double> ax[3];
+        std::vector<float> Lw;
+        const DomainDesc &TD = ctx->doms[t];
+        for (int a = 0; a < 3; ++a) far_axis(TD.o[a], TD.h, TD.n[a], ctx->cfg.far_points, ax[a], Lw);
+        double lnodes[kLOut][3];
+        std::vector<float> Pm, Ra(kLOut), Dn(kLOut);
+        NodeMap nm{};
+        const bool at_nodes = ax[0].size() * ax[1].size() * ax[2].size() == (size_t)kLOut;
+        if (at_nodes) {
+            int b = 0;
+            for (size_t kz = 0; kz < ax[2].size(); ++kz)
+                for (size_t ky = 0; ky < ax[1].size(); ++ky)
+                    for (size_t kx = 0; kx < ax[0].size(); ++kx, ++b) {
+                        lnodes[b][0] = ax[0][kx] - ct[0];
+                        lnodes[b][1] = ax[1][ky] - ct[1];
+                        lnodes[b][2] = ax[2][kz] - ct[2];
+                    }
+            double Rr[9], cn[kLOut][3];
+            canonical_frame(vg.dir, Rr);
+            canonical_nodes(geo.Lt, cn);
+            reinterp_matrix(geo.Lt, Rr, ct, ax, Pm);
+            for (int a = 0; a < kLOut; ++a) {
+                double ra = 0.0, dn = 0.0;
+                for (int k = 0; k < 3; ++k) {
+                    const double x = dist[i] * vg.dir[k] + Rr[k] * cn[a][0] + Rr[3 + k] * cn[a][1] + Rr[6 + k] * cn[a][2];
+                    const double y = dist[i] * vg.dir[k] + lnodes[a][k];
+                    ra += x * x;
+                    dn += y * y;
+                }
+                Ra[a] = (float)std::sqrt(ra);
+                Dn[a] = (float)std::sqrt(dn);
+            }
+            vg.label_nodes = lnodes;
+            nm = NodeMap{Pm.data(), Ra.data(), Dn.data()};
+        }
         double err[4] = {}, errl[4] = {};
         e = learned_dataset(vg, cfg.seed + 7919ull * (i + 1), cfg.validation, samples, c, dt, VX, VXf, VY,
                             ctx->stream);
-        if (!e) e = learned_eval(tnet, VX, VXf, VY, (int)vrows, ctx->smem_optin, ctx->sm_count, ctx->stream, err, errl);
+        if (!e) e = learned_eval(tnet, VX, VXf, VY, (int)vrows, ctx->smem_optin, ctx->sm_count, ctx->stream, err, errl,
+                                 at_nodes ? &nm : nullptr);
         verr.push_back(std::max(std::max(err[0], err[1]), std::max(err[2], err[3])));
         verr_lin.push_back(std::max(std::max(errl[0], errl[1]), std::max(errl[2], errl[3])));
     }
@@ -1847,14 +1908,21 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     double vsum = 0.0, lsum = 0.0;
     report.val_max = 0.0;
     report.val_linear_max = 0.0;
+    ctx->net_pair.assign((size_t)nd * nd, 0);
     for (size_t i = 0; i < elig.size(); ++i) {
         report.val_max = std::max(report.val_max, verr[i]);
         report.val_linear_max = std::max(report.val_linear_max, verr_lin[i]);
         vsum += verr[i];
         lsum += verr_lin[i];
-        if (verr[i] <= cfg.gate) {
-            ctx->pairs[(size_t)elig[i].first * nd + elig[i].second].kind = RP_PAIR_LEARNED;
+        // the network is used for a pair only where it lowers that pair's
+        // validation error; the gate judges the better of the two
+        const bool use = verr[i] < verr_lin[i];
+        if (std::min(verr[i], verr_lin[i]) <= cfg.gate) {
+            const size_t k = (size_t)elig[i].first * nd + elig[i].second;
+            ctx->pairs[k].kind = RP_PAIR_LEARNED;
+            ctx->net_pair[k] = use ? 1 : 0;
             ++report.learned;
+            report.network_pairs += use ? 1 : 0;
         }
     }
     report.val_mean = elig.empty() ? 0.0 : vsum / (double)elig.size();
@@ -1862,7 +1930,7 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     if (report.learned || (ctx->cfg.flags & RP_FLAG_DEFER_FAR)) {
         clear_far(ctx);
         if ((st = build_far(ctx, ctx->smem_optin))) return st;
-        if ((st = build_learned(ctx, weights, wlin))) return st;
+        if ((st = build_learned(ctx, weights, wlin, out_scale))) return st;
         ctx->net.out_scale = out_scale;
         RP_CUDA(ctx, cudaMemcpy(ctx->d_fwd, ctx->fwd.data(), ctx->fwd.size() * sizeof(FwdRing), cudaMemcpyHostToDevice));
         RP_CUDA(ctx, cudaMemcpy(ctx->d_inv, ctx->inv.data(), ctx->inv.size() * sizeof(InvTarget), cudaMemcpyHostToDevice));

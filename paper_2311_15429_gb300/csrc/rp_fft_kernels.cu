@@ -27,10 +27,7 @@ namespace rp {
 
 namespace {
 
-__host__ __device__ constexpr int radix_R(int M)
-{
-    return M % 3 == 0 ? (M / 3 <= 32 ? 3 : 6) : (M <= 32 ? 1 : M / 32);
-}
+__host__ __device__ constexpr int radix_R(int M) { return lane_radix(M); }
 __host__ __device__ constexpr int radix_L(int M) { return M / radix_R(M); }
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x / 2); }
 

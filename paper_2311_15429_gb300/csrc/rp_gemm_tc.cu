@@ -19,6 +19,9 @@
 //               store D.
 // Waits are bounded (clock64); a timeout sets *err and the CTA drains and exits.
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <utility>
 #include <cuda.h>
 #include <cudaTypedefs.h>
 #include <cuda_runtime.h>
@@ -283,6 +286,26 @@ __global__ void __launch_bounds__(256) k_split_reduce(const float4 *__restrict__
     }
 }
 
+// Raises a kernel's dynamic shared-memory limit to `smem` on the current
+// device the first time it is needed (a host call per launch would leave the
+// GPU idle between the small launches of the learned field's network).
+template <class K>
+cudaError_t open_smem(K kern, size_t smem)
+{
+    static std::mutex mu;
+    static std::map<std::pair<const void *, int>, int> opened;   // (kernel, device) -> bytes
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e) return e;
+    std::lock_guard<std::mutex> lock(mu);
+    const auto key = std::make_pair(reinterpret_cast<const void *>(kern), dev);
+    auto it = opened.find(key);
+    if (it != opened.end() && it->second >= (int)smem) return cudaSuccess;
+    e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (!e) opened[key] = (int)smem;
+    return e;
+}
+
 template <int BN, int TERMS>
 size_t gemm_smem(int stages)
 {
@@ -340,7 +363,7 @@ cudaError_t launch_gemm_bf16_tn(const CUtensorMap &mapA, const CUtensorMap &mapB
     if (stages < 2) return cudaErrorInvalidValue;
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern, size_t smem, int bn) {
-        e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        e = open_smem(kern, smem);
         if (!e)
             kern<<<grid, kGemmThreads, smem, s>>>(mapA, mapB, out, K, ldd, stages, d_err, kchunk, stride,
                                                   idesc_16bit(bn, f16));

@@ -166,25 +166,44 @@ __global__ void k_gather(const __half *__restrict__ Xall, const float *__restric
         Xt16[(size_t)(c0 + i) * ldt + r0 + threadIdx.x] = t[threadIdx.x][i];
 }
 
-// out[r][o] = sign * sum_i W[o][i] X[r][i] (+ add): one block per 4 rows, W in shared memory chunks.
-__global__ void __launch_bounds__(256) k_linear(const float *__restrict__ W, const float *__restrict__ X, int rows,
-                                                const float *__restrict__ add, float sign, float *__restrict__ out,
-                                                float scale)
+// out[r][o] = scale (sign * sum_i WT[i][o] X[r][i] + add): a block takes 8
+// rows into shared memory; thread (q, o) sums the i of k-slice q for all 8
+// rows (WT[i][o] read once, coalesced across o), and the 4 slices are added
+// in a fixed order.
+constexpr int kLinRows = 8, kLinSlices = 4;
+__global__ void __launch_bounds__(kLinSlices * kLOut) k_linear(const float *__restrict__ WT,
+                                                               const float *__restrict__ X, int rows,
+                                                               const float *__restrict__ add, float sign,
+                                                               float *__restrict__ out, float scale)
 {
-    __shared__ float xs[4][kLIn];
-    const int r0 = blockIdx.x * 4;
-    for (int i = threadIdx.x; i < 4 * kLIn; i += blockDim.x) {
+    __shared__ float xs[kLinRows][kLIn];
+    __shared__ float part[kLinSlices][kLinRows][kLOut];
+    const int r0 = blockIdx.x * kLinRows;
+    for (int i = threadIdx.x; i < kLinRows * kLIn; i += blockDim.x) {
         const int rr = r0 + i / kLIn;
         xs[i / kLIn][i % kLIn] = rr < rows ? X[(size_t)rr * kLIn + i % kLIn] : 0.0f;
     }
     __syncthreads();
-    const int rr = threadIdx.x / kLOut, o = threadIdx.x % kLOut;
-    if (r0 + rr >= rows) return;
-    float acc = 0.0f;
-    const float *w = W + (size_t)o * kLIn;
-    for (int i = 0; i < kLIn; ++i) acc = fmaf(w[i], xs[rr][i], acc);
-    const size_t oi = (size_t)(r0 + rr) * kLOut + o;
-    out[oi] = scale * (sign * acc + (add ? add[oi] : 0.0f));
+    const int q = threadIdx.x / kLOut, o = threadIdx.x % kLOut;
+    constexpr int per = kLIn / kLinSlices;
+    float acc[kLinRows] = {};
+#pragma unroll 4
+    for (int i = q * per; i < (q + 1) * per; ++i) {
+        const float w = __ldg(WT + (size_t)i * kLOut + o);
+#pragma unroll
+        for (int rr = 0; rr < kLinRows; ++rr) acc[rr] = fmaf(w, xs[rr][i], acc[rr]);
+    }
+#pragma unroll
+    for (int rr = 0; rr < kLinRows; ++rr) part[q][rr][o] = acc[rr];
+    __syncthreads();
+    for (int t = threadIdx.x; t < kLinRows * kLOut; t += blockDim.x) {
+        const int rr = t / kLOut, oo = t % kLOut;
+        if (r0 + rr >= rows) continue;
+        float a = 0.0f;
+        for (int k = 0; k < kLinSlices; ++k) a += part[k][rr][oo];
+        const size_t oi = (size_t)(r0 + rr) * kLOut + oo;
+        out[oi] = scale * (sign * a + (add ? add[oi] : 0.0f));
+    }
 }
 
 // G[i][j] = sum_r X[r][i] X[r][j] and B[i][o] = sum_r X[r][i] Y[r][o] in FP64;
@@ -387,7 +406,7 @@ cudaError_t linear_apply(const float *Wlin, const float *X, int rows, const floa
                          cudaStream_t s, float scale)
 {
     if (rows <= 0) return cudaSuccess;
-    k_linear<<<(rows + 3) / 4, 4 * kLOut, 0, s>>>(Wlin, X, rows, add, sign, out, scale);
+    k_linear<<<(rows + kLinRows - 1) / kLinRows, kLinSlices * kLOut, 0, s>>>(Wlin, X, rows, add, sign, out, scale);
     return cudaGetLastError();
 }
 

@@ -34,7 +34,7 @@ struct Mlp {
     __half *dZ16[4] = {}, *dZt16[4] = {};    // output gradients; dZt16[3] is [128][cap], rows >= 64 zero
     float *dA = nullptr;                 // [cap][256]
     float *Y = nullptr;                  // targets [cap][kLOut]
-    float *Wlin = nullptr;               // linear skip [kLOut][kLIn] fp32 (y = Wlin x + out_scale * network(x))
+    float *Wlin = nullptr;               // linear skip, transposed: [kLIn][kLOut] fp32 (y = Wlin x + out_scale * network(x))
     float out_scale = 1.0f;              // the network's output scale (RMS of what the skip leaves)
     float *loss_part = nullptr;          // per-block loss partials
     float *work = nullptr;               // split-K partials
@@ -70,8 +70,8 @@ cudaError_t mlp_load_rows(Mlp &n, const float *X, const float *Y, int rows, cuda
 // fp16 rows gathered by index from a data set: X16/Xt16/Y of the batch.
 cudaError_t mlp_gather(Mlp &n, const __half *Xall, const float *Yall, const int *idx, int rows, cudaStream_t s);
 
-// The linear skip: out[r][o] = scale * (sign * sum_i Wlin[o][i] X[r][i] + add[r][o]),
-// fp32 rows X [rows][kLIn] (add optional).
+// The linear skip: out[r][o] = scale * (sign * sum_i WlinT[i][o] X[r][i] + add[r][o]),
+// fp32 rows X [rows][kLIn] (add optional); the map is stored transposed.
 cudaError_t linear_apply(const float *Wlin, const float *X, int rows, const float *add, float sign, float *out,
                          cudaStream_t s, float scale = 1.0f);
 // Zero the last layer (the network then starts as the zero function).

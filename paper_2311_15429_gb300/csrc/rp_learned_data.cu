@@ -2,7 +2,8 @@
 // training labels from the direct retarded sum, and the output stage that
 // adds the network's node values to the far path's target coefficients.
 //
-// Moments (l <= 2) of a slice about its box centre c_s, per field:
+// Moments (l <= 2) of a slice about its box centre c_s, per field (FP32 per
+// thread, FP64 across warps and planes):
 //   Q = sum S h^3,  p_i = sum S d_i h^3,  q_ij = sum S d_i d_j h^3
 // (d = r - c_s; q as xx xy xz yy yz zz), the monopole, dipole and quadrupole
 // that carry the far interaction (Sec. IV).  A pair's network rows are these
@@ -29,37 +30,43 @@ constexpr int kMomThreads = 256;
 
 // ---------------------------------------------------------------- moments
 
-// Partial moments of one z-plane of one field: FP64, fixed-order reduction.
+// Partial moments of one z-plane of one field: each thread sums its few
+// points in FP32 (coordinates relative to the box centre), the warps reduce
+// by shuffles, and the warp partials are added in FP64 in a fixed order.
 __global__ void __launch_bounds__(kMomThreads) k_moment_part(const MomentJob *__restrict__ jobs, IoPtrs in)
 {
-    __shared__ double red[kMomThreads];
-    const MomentJob J = jobs[blockIdx.z];
+    __shared__ double red[kMomThreads / 32][kLMom];
+    const MomentJob &J = jobs[blockIdx.z];
     const int z = blockIdx.x, f = blockIdx.y;
     if (z >= J.nz) return;
     const long long N = (long long)J.nx * J.ny * J.nz;
     const float *rho = J.rho ? J.rho : in.rho[J.dom];
     const float *cur = J.rho ? J.J : in.J[J.dom];
     const float *S = (f == 0 ? rho : cur + (long long)(f - 1) * N) + (long long)z * J.nx * J.ny;
-    const double dz = J.oz + J.h * z;
-    double acc[kLMom] = {};
+    const float h = (float)J.h, ox = (float)J.ox, oy = (float)J.oy;
+    const float dz = (float)(J.oz + J.h * z);
+    float acc[kLMom] = {};
     for (int i = threadIdx.x; i < J.nx * J.ny; i += blockDim.x) {
-        const double dx = J.ox + J.h * (i % J.nx), dy = J.oy + J.h * (i / J.nx);
-        const double s = (double)S[i];
+        const float dx = fmaf(h, (float)(i % J.nx), ox), dy = fmaf(h, (float)(i / J.nx), oy);
+        const float s = __ldg(S + i);
+        const float sx = s * dx, sy = s * dy, sz = s * dz;
         acc[0] += s;
-        acc[1] += s * dx; acc[2] += s * dy; acc[3] += s * dz;
-        acc[4] += s * dx * dx; acc[5] += s * dx * dy; acc[6] += s * dx * dz;
-        acc[7] += s * dy * dy; acc[8] += s * dy * dz; acc[9] += s * dz * dz;
+        acc[1] += sx; acc[2] += sy; acc[3] += sz;
+        acc[4] = fmaf(sx, dx, acc[4]); acc[5] = fmaf(sx, dy, acc[5]); acc[6] = fmaf(sx, dz, acc[6]);
+        acc[7] = fmaf(sy, dy, acc[7]); acc[8] = fmaf(sy, dz, acc[8]); acc[9] = fmaf(sz, dz, acc[9]);
     }
-    const double vol = J.h * J.h * J.h;
-    for (int m = 0; m < kLMom; ++m) {
-        red[threadIdx.x] = acc[m];
-        __syncthreads();
-        for (int w = kMomThreads / 2; w > 0; w >>= 1) {
-            if ((int)threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) J.part[((long long)f * J.nz + z) * kLMom + m] = red[0] * vol;
-        __syncthreads();
+#pragma unroll
+    for (int m = 0; m < kLMom; ++m)
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc[m] += __shfl_xor_sync(0xffffffffu, acc[m], o);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0)
+        for (int m = 0; m < kLMom; ++m) red[warp][m] = acc[m];
+    __syncthreads();
+    if (threadIdx.x < kLMom) {
+        double t = 0.0;
+        for (int w = 0; w < kMomThreads / 32; ++w) t += red[w][threadIdx.x];
+        J.part[((long long)f * J.nz + z) * kLMom + threadIdx.x] = t * J.h * J.h * J.h;
     }
 }
 
@@ -112,26 +119,34 @@ __global__ void k_features(const LPair *__restrict__ pairs, const FeatRow *__res
     if (r >= nrows) return;
     const FeatRow fr = rows ? rows[r] : FeatRow{r, (double)step - pairs[r].tau_c};
     const LPair &P = pairs[fr.pair];
-    if (threadIdx.x < kLWin) {
-        const int k = threadIdx.x;
+    __shared__ float raw[kLWin][4 * kLMom];
+    if (threadIdx.x < 4 * kLWin) {
+        // thread (k, f): field f of window sample k, linear in time between steps j and j + 1
+        const int k = threadIdx.x >> 2, f = threadIdx.x & 3;
         const double s = fr.tc - (double)(k - (kLWin / 2 - 1));
         const long long j = (long long)floor(s);
         const float w = (float)(s - (double)j);
-        const float *a = P.mom + (j % P.mdepth) * 4 * kLMom;
-        const float *b = P.mom + ((j + 1) % P.mdepth) * 4 * kLMom;
-        float M[4 * kLMom];
-        for (int i = 0; i < 4 * kLMom; ++i) M[i] = w == 0.0f ? a[i] : (1.0f - w) * a[i] + w * b[i];
-        rotate_moments(M, P.R, win[k]);
+        const float *a = P.mom + (j % P.mdepth) * 4 * kLMom + f * kLMom;
+        const float *b = P.mom + ((j + 1) % P.mdepth) * 4 * kLMom + f * kLMom;
+        for (int i = 0; i < kLMom; ++i) raw[k][f * kLMom + i] = w == 0.0f ? a[i] : (1.0f - w) * a[i] + w * b[i];
     }
     __syncthreads();
-    if (threadIdx.x < 4) {
-        const int f = threadIdx.x;
-        double ss = 0.0;
-        for (int k = 0; k < kLWin; ++k)
-            for (int m = 0; m < kLMom; ++m) ss += (double)win[k][f * kLMom + m] * win[k][f * kLMom + m];
-        const float v = (float)sqrt(ss / (kLWin * kLMom));
-        scale[f] = v;
-        nu[4 * r + f] = v;
+    if (threadIdx.x < kLWin) rotate_moments(raw[threadIdx.x], P.R, win[threadIdx.x]);
+    __syncthreads();
+    if (threadIdx.x < 4 * 32) {
+        // warp f: the RMS of field f's window
+        const int f = threadIdx.x >> 5, lane = threadIdx.x & 31;
+        float ss = 0.0f;
+        for (int i = lane; i < kLWin * kLMom; i += 32) {
+            const float x = win[i / kLMom][f * kLMom + i % kLMom];
+            ss = fmaf(x, x, ss);
+        }
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        if (lane == 0) {
+            const float v = sqrtf(ss / (kLWin * kLMom));
+            scale[f] = v;
+            nu[4 * r + f] = v;
+        }
     }
     __syncthreads();
     const float lr = (float)(kLL0 / P.Rc);
@@ -287,39 +302,60 @@ __global__ void k_label_rows(const TrainHist *__restrict__ hist, const float *__
 
 // ---------------------------------------------------------------- output stage
 
-// One block per far target with learned pairs, pairs in a fixed order:
-// c[b][f] += sum over its pairs of the re-interpolated, rotated-back values.
-__global__ void k_learned_out(const LTarget *__restrict__ tgts, const LPair *__restrict__ pairs,
-                              const float *__restrict__ Y, const float *__restrict__ Ylin, float yscale,
-                              const float *__restrict__ nu, long long step)
+// Output stage, part 1: one block per learned pair.  Thread (f, b) forms the
+// pair's value of canonical field f at target node b by re-interpolation,
+// then, after the block has all four fields of b, writes the rotated-back
+// field f of node b to the pair's contribution contrib[pair][b][f].
+__global__ void __launch_bounds__(4 * kLOut) k_learned_pair(const LPair *__restrict__ pairs, int npairs,
+                                                            const int *__restrict__ pair_r,
+                                                            const float *__restrict__ Y,
+                                                            const float *__restrict__ Ylin,
+                                                            const float *__restrict__ nu, float *__restrict__ contrib)
 {
     __shared__ float v[4][kLOut];
-    const LTarget T = tgts[blockIdx.x];
-    float *c = T.cring + (step % T.depth) * (T.r * 4);   // r <= 64 <= blockDim
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
-    const int b = threadIdx.x;
-    for (int pi = T.p0; pi < T.p1; ++pi) {
-        const LPair &P = pairs[pi];
-        __syncthreads();
-        for (int i = threadIdx.x; i < 4 * kLOut; i += blockDim.x) {
-            const int f = i / kLOut, a = i % kLOut;
-            const long long o = (long long)(4 * pi + f) * kLOut + a;
-            v[f][a] = nu[4 * pi + f] * fmaf(yscale, Y[o], Ylin[o]) / P.Ra[a];
-        }
-        __syncthreads();
-        if (b < T.r) {
-            float u[4] = {0.f, 0.f, 0.f, 0.f};
-            const float *Pm = P.P + (long long)b * kLOut;
-            for (int a = 0; a < kLOut; ++a) {
-                const float w = Pm[a];
-                for (int f = 0; f < 4; ++f) u[f] = fmaf(w, v[f][a], u[f]);
-            }
-            acc[0] += u[0];
-            for (int i = 0; i < 3; ++i) acc[1 + i] += P.R[i] * u[1] + P.R[3 + i] * u[2] + P.R[6 + i] * u[3];
-        }
+    __shared__ float u[4][kLOut];
+    const int pi = blockIdx.x;
+    if (pi >= npairs) return;
+    const LPair &P = pairs[pi];
+    const int r = pair_r[pi];
+    const int f = threadIdx.x / kLOut, b = threadIdx.x % kLOut;
+    {
+        const long long o = (long long)(4 * pi + f) * kLOut + b;   // canonical node a = b here
+        float y = Ylin[o];
+        if (P.yscale != 0.0f) y = fmaf(P.yscale, Y[o], y);
+        v[f][b] = nu[4 * pi + f] * y / P.Ra[b];
     }
-    if (b < T.r)
-        for (int f = 0; f < 4; ++f) c[b * 4 + f] = T.overwrite ? acc[f] : c[b * 4 + f] + acc[f];
+    __syncthreads();
+    if (b < r) {
+        float s0 = 0.0f, s1 = 0.0f;
+#pragma unroll 8
+        for (int a = 0; a < kLOut; a += 2) {
+            s0 = fmaf(__ldg(P.P + (long long)a * r + b), v[f][a], s0);
+            s1 = fmaf(__ldg(P.P + (long long)(a + 1) * r + b), v[f][a + 1], s1);
+        }
+        u[f][b] = s0 + s1;
+    }
+    __syncthreads();
+    if (b < r) {
+        const float x = f == 0 ? u[0][b]
+                               : P.R[f - 1] * u[1][b] + P.R[3 + f - 1] * u[2][b] + P.R[6 + f - 1] * u[3][b];
+        contrib[((long long)pi * kLOut + b) * 4 + f] = x;
+    }
+}
+
+// Output stage, part 2: one block per target; thread (b, f) sums its pairs'
+// contributions in pair order and sets (no low-rank pairs) or adds to the
+// coefficient slot of this step.
+__global__ void __launch_bounds__(4 * kLOut) k_learned_out(const LTarget *__restrict__ tgts,
+                                                           const float *__restrict__ contrib, long long step)
+{
+    const LTarget T = tgts[blockIdx.x];
+    const int b = threadIdx.x / 4, f = threadIdx.x % 4;
+    if (b >= T.r) return;
+    float acc = 0.0f;
+    for (int pi = T.p0; pi < T.p1; ++pi) acc += contrib[((long long)pi * kLOut + b) * 4 + f];
+    float *c = T.cring + (step % T.depth) * (T.r * 4) + b * 4 + f;
+    *c = T.overwrite ? acc : *c + acc;
 }
 
 }  // namespace
@@ -371,11 +407,13 @@ cudaError_t launch_label_rows(const TrainHist *d_hist, int nhist, const float *l
     return cudaGetLastError();
 }
 
-cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *Ylin,
-                               float yscale, const float *nu, long long step, cudaStream_t s)
+cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, int npairs, const int *d_pair_r,
+                               const float *Y, const float *Ylin, const float *nu, float *contrib, long long step,
+                               cudaStream_t s)
 {
-    if (ntgt <= 0) return cudaSuccess;
-    k_learned_out<<<ntgt, 512, 0, s>>>(d_tgts, d_pairs, Y, Ylin, yscale, nu, step);
+    if (ntgt <= 0 || npairs <= 0) return cudaSuccess;
+    k_learned_pair<<<npairs, 4 * kLOut, 0, s>>>(d_pairs, npairs, d_pair_r, Y, Ylin, nu, contrib);
+    k_learned_out<<<ntgt, 4 * kLOut, 0, s>>>(d_tgts, contrib, step);
     return cudaGetLastError();
 }
 

@@ -33,8 +33,8 @@ struct LPair {
     float Rc;                // centre-to-centre distance
     const float *mom;        // moment history [mdepth][4][10] (ring or array)
     int mdepth;
-    int pad_;
-    const float *P;          // [r][64] canonical -> target-node interpolation
+    float yscale;            // weight of the network's output (0: the linear skip alone)
+    const float *P;          // [64][r] canonical -> target-node interpolation, transposed
     float Ra[kLOut];         // distances from c_s to the canonical nodes
 };
 
@@ -78,8 +78,11 @@ cudaError_t launch_train_labels(const TrainHist *d_hist, int nhist, const float 
                                 int samples, double cdt, float *labels, cudaStream_t s);
 cudaError_t launch_label_rows(const TrainHist *d_hist, int nhist, const float *labels, const float *nu, int samples,
                               float *Y, cudaStream_t s);
-// c += re-interpolated nu * (yscale * Y + Ylin) / R_a (network output plus linear skip)
-cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, const float *Y, const float *Ylin,
-                               float yscale, const float *nu, long long step, cudaStream_t s);
+// c += re-interpolated nu * (pair.yscale * Y + Ylin) / R_a (network output
+// plus linear skip), summed over each target's pairs in pair order; pair_r[p]
+// is the pair's target node count, contrib scratch [npairs][64][4].
+cudaError_t launch_learned_out(const LTarget *d_tgts, int ntgt, const LPair *d_pairs, int npairs, const int *d_pair_r,
+                               const float *Y, const float *Ylin, const float *nu, float *contrib, long long step,
+                               cudaStream_t s);
 
 }  // namespace rp

@@ -208,7 +208,9 @@ static cudaError_t make_chunk(const LGeom &geo, Rng &rng, int nh, int samples, d
         for (int a = 0; a < kLOut; ++a) {
             double D[3];
             for (int k = 0; k < 3; ++k)
-                D[k] = Rc * n[k] + R[k] * cn[a][0] + R[3 + k] * cn[a][1] + R[6 + k] * cn[a][2];
+                D[k] = Rc * n[k] + (geo.label_nodes && !geo.random
+                                        ? geo.label_nodes[a][k]
+                                        : R[k] * cn[a][0] + R[3 + k] * cn[a][1] + R[6 + k] * cn[a][2]);
             const double Dn = std::sqrt(D[0] * D[0] + D[1] * D[1] + D[2] * D[2]);
             for (int k = 0; k < 3; ++k) T.D[a][k] = (float)D[k];
             T.Dn[a] = (float)Dn;
@@ -366,7 +368,7 @@ cudaError_t learned_fit_linear(Mlp &net, const float *Xf, const float *Y, int ro
             for (int k = i + 1; k < kLIn; ++k) v -= A[(size_t)k * kLIn + i] * z[k];
             z[i] = v / A[(size_t)i * kLIn + i];
         }
-        for (int i = 0; i < kLIn; ++i) W[(size_t)o * kLIn + i] = (float)z[i];
+        for (int i = 0; i < kLIn; ++i) W[(size_t)i * kLOut + o] = (float)z[i];   // stored transposed
     }
     if ((e = cudaMemcpyAsync(net.Wlin, W.data(), W.size() * sizeof(float), cudaMemcpyHostToDevice, s))) return e;
     if (!Yres) return cudaStreamSynchronize(s);
@@ -385,7 +387,7 @@ cudaError_t learned_fit_linear(Mlp &net, const float *Xf, const float *Y, int ro
 }
 
 cudaError_t learned_eval(Mlp &net, const __half *X, const float *Xf, const float *Y, int rows, int optin, int sms,
-                         cudaStream_t s, double err[4], double err_lin[4])
+                         cudaStream_t s, double err[4], double err_lin[4], const NodeMap *to_nodes)
 {
     std::vector<double> num(4, 0.0), numl(4, 0.0), den(4, 0.0);
     std::vector<int> idx(net.cap);
@@ -407,12 +409,32 @@ cudaError_t learned_eval(Mlp &net, const __half *X, const float *Xf, const float
             (e = cudaMemcpyAsync(want.data(), net.Y, (size_t)n * kLOut * sizeof(float), cudaMemcpyDeviceToHost, s)) ||
             (e = cudaStreamSynchronize(s)))
             return e;
+        std::vector<double> pn(kLOut), pl(kLOut);
         for (int i = 0; i < n; ++i) {
             const int f = (r0 + i) % 4;   // rows are (sample, field) with the field fastest
             for (int a = 0; a < kLOut; ++a) {
                 const size_t o = (size_t)i * kLOut + a;
+                pn[a] = (double)net.out_scale * out[o] + lin[o];
+                pl[a] = lin[o];
+            }
+            if (to_nodes) {
+                std::vector<double> qn(kLOut, 0.0), ql(kLOut, 0.0);
+                for (int b = 0; b < kLOut; ++b) {
+                    for (int a = 0; a < kLOut; ++a) {
+                        const double w = (double)to_nodes->P[(size_t)b * kLOut + a] / to_nodes->Ra[a];
+                        qn[b] += w * pn[a];
+                        ql[b] += w * pl[a];
+                    }
+                    qn[b] *= to_nodes->Dn[b];
+                    ql[b] *= to_nodes->Dn[b];
+                }
+                pn.swap(qn);
+                pl.swap(ql);
+            }
+            for (int a = 0; a < kLOut; ++a) {
+                const size_t o = (size_t)i * kLOut + a;
                 const double w = want[o];
-                const double d = (double)net.out_scale * out[o] + lin[o] - w, dl = (double)lin[o] - w;
+                const double d = pn[a] - w, dl = pl[a] - w;
                 num[f] += d * d;
                 numl[f] += dl * dl;
                 den[f] += w * w;

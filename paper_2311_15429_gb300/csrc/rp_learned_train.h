@@ -22,6 +22,9 @@ struct LGeom {
     bool random;
     double dir[3], Rc;     // fixed geometry
     double R_lo, R_hi;     // random geometry
+    // fixed geometry only: the label nodes, as world-axis offsets from the
+    // target centre (kLOut of them); null: the canonical nodes
+    const double (*label_nodes)[3] = nullptr;
 };
 
 // Rotation whose first row is n / |n| (see rp_learned_data.cu).
@@ -59,7 +62,13 @@ cudaError_t learned_train(Mlp &net, const __half *X, const float *Y, int rows, i
                           uint64_t seed, int optin, int sms, cudaStream_t s, float *final_loss);
 // rel-L2 against Y per field (rows are field-fastest) of the linear skip
 // plus the network (err) and of the linear skip alone (err_lin, optional).
+// With `to_nodes` the predictions at the canonical nodes are first carried
+// to the label nodes the way evaluation does: y_b = Dn_b sum_a P[b][a] y_a / Ra_a
+// (P [kLOut][kLOut] row b, Ra canonical-node and Dn label-node distances).
+struct NodeMap {
+    const float *P, *Ra, *Dn;
+};
 cudaError_t learned_eval(Mlp &net, const __half *X, const float *Xf, const float *Y, int rows, int optin, int sms,
-                         cudaStream_t s, double err[4], double err_lin[4]);
+                         cudaStream_t s, double err[4], double err_lin[4], const NodeMap *to_nodes = nullptr);
 
 }  // namespace rp

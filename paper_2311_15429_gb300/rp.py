@@ -48,7 +48,8 @@ class rp_train_report(ctypes.Structure):
     _fields_ = [("candidates", ctypes.c_int), ("learned", ctypes.c_int), ("train_rows", ctypes.c_longlong),
                 ("final_loss", ctypes.c_float), ("train_seconds", ctypes.c_float), ("val_max", ctypes.c_double),
                 ("val_mean", ctypes.c_double), ("val_linear_max", ctypes.c_double),
-                ("val_linear_mean", ctypes.c_double), ("reserved", ctypes.c_int * 4)]
+                ("val_linear_mean", ctypes.c_double), ("network_pairs", ctypes.c_int),
+                ("reserved", ctypes.c_int * 3)]
 
 
 class rp_stats(ctypes.Structure):
