@@ -122,9 +122,7 @@ struct rp_ctx {
     DirectTarget *d_dtg = nullptr;
     DirectPair *d_dpairs = nullptr;
     RawRing *d_raw = nullptr;
-    CUtensorMap *d_maps = nullptr;   // TMA descriptors: rings, then (real, complex) kernels per target
     bool tma = false;                // TMA-fed MAC available for the cubic classes
-    int nmaps = 0;
     int mac_stages[7] = {};          // pipeline depth per class (index by class_slot)
     int mac_cw[7] = {16, 16, 16, 16, 16, 16, 16};   // consumer warps of the MAC per class
     int sm_count = 0;
@@ -359,77 +357,23 @@ int class_slot(int cls)
     }
 }
 
-// One 4-D descriptor over float32 data: dims (d0 floats, d1, d2, d3), dense,
-// box (b0 floats, b1 rows, 1, 1).
-bool encode_map(PFN_cuTensorMapEncodeTiled_v12000 enc, CUtensorMap *map, void *base, uint64_t d0, uint64_t d1,
-                uint64_t d2, uint64_t d3, uint32_t b0, uint32_t b1)
+// Pipeline depth of the bulk-copy-fed MAC for every cubic class of the plan;
+// the register-blocked MAC serves the plan if some class cannot hold two
+// field stages.
+rp_status plan_mac_tma(rp_ctx *ctx, int max_optin)
 {
-    const cuuint64_t dims[4] = {d0, d1, d2, d3};
-    const cuuint64_t strides[3] = {d0 * 4, d0 * d1 * 4, d0 * d1 * d2 * 4};
-    const cuuint32_t box[4] = {b0, b1, 1, 1};
-    const cuuint32_t estr[4] = {1, 1, 1, 1};
-    return enc(map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 4, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
-}
-
-// Descriptors for every ring and target kernel set of a cubic class; the
-// TMA-fed MAC is used only if all of them encode.
-rp_status build_tensor_maps(rp_ctx *ctx, const std::vector<float *> &treal, const std::vector<float2 *> &tcplx,
-                            int max_optin)
-{
-    const int nrings = (int)ctx->fwd.size();
-    std::vector<CUtensorMap> maps((size_t)nrings + 2 * ctx->inv.size());
-    std::memset(maps.data(), 0, maps.size() * sizeof(CUtensorMap));
     ctx->tma = false;
-    void *fn = nullptr;
-    cudaDriverEntryPointQueryResult q{};
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn) {
-        cudaGetLastError();
-        ctx->last_error = "cuTensorMapEncodeTiled unavailable: register-blocked MAC in use";
-        return RP_OK;   // no descriptors: the register-blocked MAC serves every class
-    }
-    auto enc = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
-    bool ok = true;
-    for (int r = 0; r < nrings && ok; ++r) {
-        const FwdRing &R = ctx->fwd[r];
-        const int M = size_class(R.ax, R.ay, R.az);
-        if (!M) continue;
-        const uint64_t tiles = (uint64_t)R.kx * (M / kTileY);
-        ok = encode_map(enc, &maps[r], R.ring, 2 * kTileY, M, tiles, 4ULL * R.depth, 2 * kTileY, M);
-    }
-    for (size_t ti = 0; ti < ctx->inv.size() && ok; ++ti) {
-        const InvTarget &I = ctx->inv[ti];
-        const int M = size_class(I.ax, I.ay, I.az);
-        if (!M) continue;
-        const int nr = I.er - I.e0, nc = I.e1 - I.er;
-        const uint64_t tiles = (uint64_t)I.kx * (M / kTileY);
-        if (nr > 0) ok = ok && encode_map(enc, &maps[nrings + 2 * ti], treal[ti], kTileY, M, tiles, nr, kTileY, M);
-        if (nc > 0)
-            ok = ok && encode_map(enc, &maps[nrings + 2 * ti + 1], tcplx[ti], 2 * kTileY, M, tiles, nc, 2 * kTileY, M);
-    }
-    if (!ok) {
-        ctx->last_error = "a TMA descriptor did not encode: register-blocked MAC in use";
-        return RP_OK;
-    }
     for (int cls : {32, 48, 64, 96, 128, 192}) {
         const int n = mac_tma_stages(cls, max_optin);
         ctx->mac_stages[class_slot(cls)] = n;
-        if (n < 5 && cls > 0) {
+        if (n < 2) {
             for (const InvTarget &I : ctx->inv)
                 if (size_class(I.ax, I.ay, I.az) == cls) {
-                    ctx->last_error = "TMA pipeline too shallow: register-blocked MAC in use";
+                    ctx->last_error = "bulk-copy pipeline too shallow: register-blocked MAC in use";
                     return RP_OK;
                 }
         }
     }
-    CUtensorMap *d = nullptr;
-    rp_status st = dev_alloc(ctx, &d, maps.size());
-    if (st) return st;
-    RP_CUDA(ctx, cudaMemcpy(d, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice));
-    ctx->d_maps = d;
-    ctx->nmaps = (int)maps.size();
     ctx->tma = true;
     return RP_OK;
 }
@@ -826,9 +770,9 @@ rp_status autotune_mac(rp_ctx *ctx)
         float best = 1e30f;
         for (int cw : {8, 12, 16}) {
             auto go = [&] {
-                return launch_mac_tma(g.cls, cw, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries, ctx->d_maps,
-                                      ctx->nmaps, step, 0, ctx->mac_stages[slot], std::min(ntiles, ctx->sm_count),
-                                      ctx->d_err, ctx->stream);
+                return launch_mac_tma(g.cls, cw, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries, step, 0,
+                                      ctx->mac_stages[slot], std::min(ntiles, ctx->sm_count), ctx->d_err,
+                                      ctx->stream);
             };
             cudaError_t e = go();
             if (!e) e = cudaEventRecord(a, ctx->stream);
@@ -1226,10 +1170,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     }
 
     // ---- kernel spectra (FP64 on the host, stored FP32), built in parallel;
-    // each target's real and complex kernels are contiguous (one TMA
-    // descriptor each)
+    // each target's real and complex kernels are contiguous
     std::vector<void *> gptr(eplan.size(), nullptr);
-    std::vector<int> gidx(eplan.size(), 0);
     std::vector<float *> treal(ctx->inv.size(), nullptr);
     std::vector<float2 *> tcplx(ctx->inv.size(), nullptr);
     for (size_t ti = 0; ti < ctx->inv.size(); ++ti) {
@@ -1239,8 +1181,8 @@ rp_status rp_finalize(rp_ctx *ctx)
         if (nr > 0 && (st = dev_alloc(ctx, &treal[ti], (size_t)nr * cells))) return st;
         if (nc > 0 && (st = dev_alloc(ctx, &tcplx[ti], (size_t)nc * cells))) return st;
         for (int e = I.e0; e < I.e1; ++e) {
-            if (e < I.er) { gidx[e] = e - I.e0; gptr[e] = treal[ti] + (size_t)gidx[e] * cells; }
-            else { gidx[e] = e - I.er; gptr[e] = tcplx[ti] + (size_t)gidx[e] * cells; }
+            if (e < I.er) gptr[e] = treal[ti] + (size_t)(e - I.e0) * cells;
+            else gptr[e] = tcplx[ti] + (size_t)(e - I.er) * cells;
         }
     }
     {
@@ -1273,7 +1215,6 @@ rp_status rp_finalize(rp_ctx *ctx)
         for (auto &th : pool) th.join();
         if (err.load()) return cuda_fail(ctx, (cudaError_t)err.load(), "kernel spectrum upload");
     }
-    const int nrings = (int)ctx->fwd.size();
     for (size_t ti = 0; ti < ctx->inv.size(); ++ti) {
         const InvTarget &I = ctx->inv[ti];
         for (int i = I.e0; i < I.e1; ++i) {
@@ -1286,15 +1227,12 @@ rp_status rp_finalize(rp_ctx *ctx)
             E.depth = R.depth;
             E.lag = e.lag;
             E.is_real = e.real_g ? 1 : 0;
-            E.smap = e.ring;
-            E.gmap = nrings + 2 * (int)ti + (e.real_g ? 0 : 1);
-            E.gidx = gidx[i];
             ctx->entries.push_back(E);
         }
     }
 
-    // ---- TMA descriptors for the cubic classes
-    if ((st = build_tensor_maps(ctx, treal, tcplx, max_optin))) return st;
+    // ---- bulk-copy MAC pipeline for the cubic classes
+    if ((st = plan_mac_tma(ctx, max_optin))) return st;
 
     // ---- far pairs
     RP_CUDA(ctx, cudaDeviceGetAttribute(&ctx->sm_count, cudaDevAttrMultiProcessorCount, ctx->device));
@@ -1534,8 +1472,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
                  if (ctx->tma && g.cls > 0)
                      return launch_mac_tma(g.cls, ctx->mac_cw[class_slot(g.cls)], ctx->d_inv, g.i0, g.i1, g.blk0,
-                                           ntiles, ctx->d_entries,
-                                           ctx->d_maps, ctx->nmaps, step, clamp,
+                                           ntiles, ctx->d_entries, step, clamp,
                                            ctx->mac_stages[class_slot(g.cls)],
                                            std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
                  return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,

@@ -335,8 +335,10 @@ __global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restri
     ColumnFFT<M, false> cf{&lt, az, V, fs, ncols, 4, mz, tw, lane, warp, nwarps};
     run_radix<M>(az.R, cf);
     __syncthreads();
-    const long long ring_field = spec_cells(kx, my, mz);
-    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems + (long long)(kxi * ntile + ky0 / kTileY) * mz * kTileY;
+    // the tile's four field tiles sit next to each other in the slot
+    const long long ring_field = (long long)mz * kTileY;
+    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems +
+                  (long long)(kxi * ntile + ky0 / kTileY) * 4 * ring_field;
     if constexpr (M > 0) {
         for (int i = threadIdx.x; i < 4 * mz * (kTileY / 2); i += blockDim.x) {
             const int f = i / (mz * (kTileY / 2)), rem = i % (mz * (kTileY / 2));
@@ -374,8 +376,9 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     const int local = b - T.tile0;
     const int kxi = local / ntile, ky0 = (local % ntile) * kTileY;
     const int ncols = min(kTileY, my - ky0);
-    const long long fstride = spec_cells(kx, my, mz);
-    const long long col0 = (long long)(kxi * ntile + ky0 / kTileY) * mz * kTileY;
+    const long long col0 = (long long)(kxi * ntile + ky0 / kTileY) * mz * kTileY;   // tile in a kernel spectrum
+    const long long fstride = (long long)mz * kTileY;                             // field tile in a ring slot
+    const long long sbase = 3 * col0;   // + col0: the tile's first field tile in a ring slot (4 per tile)
     const int fs = mz * kTileYPad;
 
     float2 *tw = sm;
@@ -410,7 +413,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
                 const MacEntry E = entries[e];
                 long long j = step - E.lag;
                 if (clamp && j < 0) j = 0;
-                const float2 *S = E.ring + (j % E.depth) * E.slot_elems;
+                const float2 *S = E.ring + (j % E.depth) * E.slot_elems + sbase;
                 const float *G = static_cast<const float *>(E.g);
                 float2 g[CH];
                 float4 s[4][CH];
@@ -435,7 +438,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
                 const MacEntry E = entries[e];
                 long long j = step - E.lag;
                 if (clamp && j < 0) j = 0;
-                const float2 *S = E.ring + (j % E.depth) * E.slot_elems;
+                const float2 *S = E.ring + (j % E.depth) * E.slot_elems + sbase;
                 const float2 *G = static_cast<const float2 *>(E.g);
                 float4 g[CH];
                 float4 s[4][CH];
@@ -478,7 +481,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
             const MacEntry E = entries[e];
             long long j = step - E.lag;
             if (clamp && j < 0) j = 0;
-            const float2 *S = E.ring + (j % E.depth) * E.slot_elems + col0;
+            const float2 *S = E.ring + (j % E.depth) * E.slot_elems + 4 * col0;
             const float *Gr = static_cast<const float *>(E.g) + col0;
             const float2 *Gc = static_cast<const float2 *>(E.g) + col0;
             for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {

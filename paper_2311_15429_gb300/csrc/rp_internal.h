@@ -29,8 +29,9 @@ struct Axis {
 };
 
 // One (source domain, padded size) spectral history ring and its forward
-// transform.  Spectra are stored [4 fields][spec_cells] complex64 (tile-major,
-// see spec_cells), kx in [0, mx/2].
+// transform.  A slot holds one step's spectra, complex64, tile by tile:
+// [kx][ky tile of 16][4 fields][kz][16] (4 * spec_cells in all), kx in
+// [0, mx/2], so the four field tiles of one (kx, ky) tile are contiguous.
 struct FarTarget;
 
 struct FwdRing {
@@ -39,7 +40,7 @@ struct FwdRing {
     int kx;                  // mx/2 + 1
     int src;                 // source domain id
     int depth;               // ring depth in steps
-    float2 *ring;            // [depth][4][spec_cells]
+    float2 *ring;            // [depth][tiles][4 fields][mz][16]
     float2 *t1;              // scratch after the plane pass: [4][kx][nz][my]
     long long slot_elems;    // float2 per slot = 4 * spec_cells
     const float2 *tw_x, *tw_y, *tw_z;  // twiddles exp(-2 pi i j/M), j < M
@@ -60,9 +61,6 @@ struct MacEntry {
     int depth;
     int lag;
     int is_real;
-    int smap;                // tensor map of the source ring (TMA path)
-    int gmap;                // tensor map of the target's real or complex kernels
-    int gidx;                // index of this kernel within that map
 };
 
 // A target domain evaluated by the FFT path.
@@ -199,8 +197,8 @@ int mac_tma_stages(int M, int smem_optin);
 size_t mac_tma_smem(int M, int nstages);
 cudaError_t open_mac_tma_smem_limit(int max_optin);
 cudaError_t launch_mac_tma(int cls, int consumer_warps, const InvTarget *d_tgts, int t0, int t1, int tile_lo,
-                           int ntiles, const MacEntry *d_entries, const struct CUtensorMap_st *d_maps, int nmaps,
-                           long long step, int clamp, int nstages, int grid, int *d_err, cudaStream_t s);
+                           int ntiles, const MacEntry *d_entries, long long step, int clamp, int nstages, int grid,
+                           int *d_err, cudaStream_t s);
 
 // tcgen05 bf16 GEMM (rp_gemm_tc.cu): D (M x N fp32) = A (M x K) * B (N x K)^T
 bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *base, uint64_t rows,

@@ -7,11 +7,15 @@
 // operands stream through shared memory asynchronously:
 //
 //   * persistent blocks, one per SM, each walking (kx, 16-ky) column tiles;
-//   * the last warp is the producer: one lane issues cp.async.bulk.tensor copies of
-//     each entry's kernel tile and its four field tiles (M rows x 128 B) into
-//     a ring of shared-memory stages, each stage guarded by a "full" mbarrier
-//     (transaction bytes) and an "empty" mbarrier (one arrival per consumer
-//     warp);
+//   * the last warp is the producer: one lane issues bulk copies
+//     (cp.async.bulk) into two rings of shared-memory stages, one for the
+//     entries' kernel tiles (M rows x 128 B, or 64 B for a real kernel) and
+//     one for their source field tiles.  The ring stores a tile's four field
+//     tiles next to each other, so one copy brings FPC of them (4 up to
+//     M = 96, 2 at 128, 1 at 192): the copy engine spends a roughly fixed time
+//     per copy, and copies under about 16 KB leave HBM bandwidth unused.  Each
+//     stage is guarded by a "full" mbarrier (transaction bytes) and an "empty"
+//     mbarrier (one arrival per consumer warp);
 //   * the other CW warps (8, 12 or 16, picked per size class by timing the
 //     variants on the context's own plan) are consumers: they multiply-accumulate in registers,
 //     then write the tile to a separate shared-memory region for the column
@@ -34,6 +38,9 @@ namespace {
 
 constexpr long long kWaitLimit = 4000000000LL;   // SM clock cycles (about 2 s)
 constexpr int kMaxStages = 24;
+constexpr int kKernelStages = 2;   // depth of the kernel-tile ring
+constexpr int kFftWarps = 3;       // warps of the inverse column FFT and the T2 store (with the
+                                   // producer, a whole warp per scheduler for the register split)
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -77,14 +84,29 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Contiguous copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
-// by the bulk-copy engine, completing on `bar`.
-__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar)
+// by the bulk-copy engine, completing on `bar`, with an L2 eviction-priority
+// policy for the source lines.
+__device__ __forceinline__ void bulk_load(void *dst, const void *src, uint32_t bytes, uint64_t *bar, uint64_t policy)
 {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], %2, [%3], %4;" ::"r"(
             smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar))
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
         : "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+    return p;
+}
+
+__device__ __forceinline__ uint64_t policy_evict_last()
+{
+    uint64_t p;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(p));
+    return p;
 }
 
 template <class T>
@@ -97,52 +119,85 @@ __device__ __forceinline__ int owner(const T *arr, int lo, int hi, int b, int T:
     return lo;
 }
 
-template <int CW>
-__device__ __forceinline__ void consumer_sync() { asm volatile("bar.sync 1, %0;" ::"n"(CW * 32) : "memory"); }
+// barrier among the FFT warps only
+__device__ __forceinline__ void fft_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFftWarps * 32) : "memory"); }
 
-// M: padded FFT size of the class; CW: consumer warps (the block has CW + 1).
-template <int M, int CW>
-__global__ void __launch_bounds__((CW + 1) * 32, 1)
+// M: padded FFT size of the class; CW: multiply-accumulate warps (the block
+// has CW + kFftWarps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
+// are contiguous in the ring).
+template <int M, int CW, int FPC>
+__global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
     k_mac_tma(const InvTarget *__restrict__ tgts, int t0, int t1, int tile_lo, int ntiles,
-              const MacEntry *__restrict__ entries, const CUtensorMap *__restrict__ maps, int nmaps, long long step,
-              int clamp, int nstages, int *err)
+              const MacEntry *__restrict__ entries, long long step, int clamp, int ns, int *err)
 {
     constexpr int STAGE = M * 128;                  // one M x 16 complex tile
+    constexpr int SSTAGE = FPC * STAGE;             // FPC field tiles of one entry
+    constexpr int NG = kKernelStages;
     constexpr int kConsumerWarps = CW;
+    constexpr int FW = kFftWarps;
     constexpr int RSTEP = kConsumerWarps * 32 / 8;   // rows covered by one pass of the consumers
     constexpr int ROWS = (M + RSTEP - 1) / RSTEP;
     constexpr int NTY = M / kTileY;
     constexpr int FS = M * kTileYPad;                // float2 per field of the FFT tile
     extern __shared__ __align__(128) unsigned char smem[];
-    unsigned char *stages = smem;
-    float2 *acc = reinterpret_cast<float2 *>(smem + (size_t)nstages * STAGE);
+    unsigned char *sstages = smem;                                   // [ns][SSTAGE]
+    unsigned char *gstages = smem + (size_t)ns * SSTAGE;             // [NG][STAGE]
+    float2 *acc = reinterpret_cast<float2 *>(gstages + (size_t)NG * STAGE);
     float2 *tw = acc + 4 * FS;
-    uint64_t *full = reinterpret_cast<uint64_t *>(tw + M);
-    uint64_t *empty = full + nstages;
-    volatile int *abort_flag = reinterpret_cast<volatile int *>(empty + nstages);
+    uint64_t *sfull = reinterpret_cast<uint64_t *>(tw + M);
+    uint64_t *sempty = sfull + ns;
+    uint64_t *gfull = sempty + ns;
+    uint64_t *gempty = gfull + NG;
+    uint64_t *accfull = gempty + NG;    // the FFT tile holds a tile's sums (one arrival per MAC warp)
+    uint64_t *accempty = accfull + 1;   // the FFT warps are done with it (one arrival per FFT warp)
+    volatile int *abort_flag = reinterpret_cast<volatile int *>(accempty + 1);
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     if (threadIdx.x == 0) {
-        for (int s = 0; s < nstages; ++s) {
-            mbar_init(&full[s], 1);
-            mbar_init(&empty[s], kConsumerWarps);
+        for (int s = 0; s < ns; ++s) {
+            mbar_init(&sfull[s], 1);
+            mbar_init(&sempty[s], kConsumerWarps);
         }
+        for (int s = 0; s < NG; ++s) {
+            mbar_init(&gfull[s], 1);
+            mbar_init(&gempty[s], kConsumerWarps);
+        }
+        mbar_init(accfull, kConsumerWarps);
+        mbar_init(accempty, FW);
         *abort_flag = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     load_twiddles(tw, tgts[t0].tw_z, M);
     __syncthreads();
 
-    if (warp == kConsumerWarps) {
+    // wait for a phase; false (and the error raised) on abort/timeout
+    auto wait_or_abort = [&](uint64_t *bar, uint32_t parity) {
+        if (*abort_flag) return false;
+        if (!mbar_wait(bar, parity)) {
+            *abort_flag = 1;
+            atomicExch(err, 1);
+            return false;
+        }
+        return true;
+    };
+
+    if (warp == kConsumerWarps + FW) {
         // ------------------------------------------------------------ producer
         if (lane != 0) return;
-        // the descriptors were written through the generic proxy (host copy)
-        for (int m = 0; m < nmaps; ++m)
-            asm volatile("fence.proxy.tensormap::generic.acquire.gpu [%0], 128;" ::"l"(
-                             reinterpret_cast<uint64_t>(maps + m))
-                         : "memory");
-        uint32_t q = 0;
+        uint32_t qg = 0, qs = 0;
         bool ok = true;
+        // The kernel tiles (tens of MB, read every step) stay in L2; the ring
+        // tiles (read once per step per entry) pass through without evicting them.
+        const uint64_t keep = policy_evict_last(), stream = policy_evict_first();
+        // wait until stage q of a ring is free; false (and the error raised) on abort/timeout
+        auto acquire = [&](uint64_t *empty, int n, uint32_t q) {
+            if (*abort_flag || !mbar_wait(&empty[q % n], ((q / n) & 1) ^ 1)) {
+                *abort_flag = 1;
+                atomicExch(err, 1);
+                return false;
+            }
+            return true;
+        };
         for (int tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
             const int b = tile + tile_lo;
             const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
@@ -153,63 +208,118 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
                 long long j = step - E.lag;
                 if (clamp && j < 0) j = 0;
                 const int slot = (int)(j % E.depth);
-                for (int o = 0; o < 5; ++o, ++q) {
-                    const int s = q % nstages;
-                    if (*abort_flag || !mbar_wait(&empty[s], ((q / nstages) & 1) ^ 1)) {
-                        ok = false;
-                        *abort_flag = 1;
-                        atomicExch(err, 1);
-                        break;
-                    }
-                    void *dst = stages + (size_t)s * STAGE;
-                    if (o == 0) {
-                        const uint32_t bytes = E.is_real ? M * 64 : M * 128;
-                        mbar_expect_tx(&full[s], bytes);
-                        const void *src = E.is_real ? (const void *)(static_cast<const float *>(E.g) + tile_off)
-                                                    : (const void *)(static_cast<const float2 *>(E.g) + tile_off);
-                        bulk_load(dst, src, bytes, &full[s]);
-                    } else {
-                        mbar_expect_tx(&full[s], M * 128);
-                        const float2 *src = E.ring + (long long)slot * E.slot_elems +
-                                            (long long)(o - 1) * (E.slot_elems / 4) + tile_off;
-                        bulk_load(dst, src, M * 128, &full[s]);
-                    }
+                // the kernel tile
+                if (!(ok = acquire(gempty, NG, qg))) break;
+                {
+                    const int s = qg % NG;
+                    const uint32_t bytes = E.is_real ? M * 64 : M * 128;
+                    const void *src = E.is_real ? (const void *)(static_cast<const float *>(E.g) + tile_off)
+                                                : (const void *)(static_cast<const float2 *>(E.g) + tile_off);
+                    mbar_expect_tx(&gfull[s], bytes);
+                    bulk_load(gstages + (size_t)s * STAGE, src, bytes, &gfull[s], keep);
+                    ++qg;
+                }
+                // the four field tiles of the source spectrum, FPC per copy
+                const float2 *fields = E.ring + (long long)slot * E.slot_elems + 4 * tile_off;
+                for (int o = 0; o < 4 / FPC; ++o) {
+                    if (!(ok = acquire(sempty, ns, qs))) break;
+                    const int s = qs % ns;
+                    mbar_expect_tx(&sfull[s], SSTAGE);
+                    bulk_load(sstages + (size_t)s * SSTAGE, fields + (long long)o * FPC * M * kTileY, SSTAGE,
+                              &sfull[s], stream);
+                    ++qs;
                 }
             }
         }
         // no copy may still be landing when the block exits
-        const uint32_t first = q > (uint32_t)nstages ? q - nstages : 0;
-        for (uint32_t r = first; r < q; ++r)
-            if (!mbar_wait(&full[r % nstages], (r / nstages) & 1)) atomicExch(err, 1);
+        for (uint32_t r = qg > (uint32_t)NG ? qg - NG : 0; r < qg; ++r)
+            if (!mbar_wait(&gfull[r % NG], (r / NG) & 1)) atomicExch(err, 1);
+        for (uint32_t r = qs > (uint32_t)ns ? qs - ns : 0; r < qs; ++r)
+            if (!mbar_wait(&sfull[r % ns], (r / ns) & 1)) atomicExch(err, 1);
         return;
     }
 
-    // ---------------------------------------------------------------- consumers
-    const int p = threadIdx.x & 7, r0 = threadIdx.x >> 3;   // ky pair p, rows r0 + RSTEP i
-    LaneTw<M, true> lt;
-    lt.init(tw, lane & (LaneTw<M, true>::L - 1));
-    uint32_t q = 0;
-
-    // wait for stage q; returns its address (or nullptr after an abort/timeout)
-    auto take = [&](uint32_t qq) -> const unsigned char * {
-        const int s = qq % nstages;
-        if (*abort_flag) return nullptr;
-        if (!mbar_wait(&full[s], (qq / nstages) & 1)) {
-            *abort_flag = 1;
-            atomicExch(err, 1);
-            return nullptr;
+    if (warp >= kConsumerWarps) {
+        // ------------------------------------------------------------ FFT warps
+        // inverse FFT along z of the 64 columns of each tile the MAC warps
+        // hand over, then rows z < nz to T2, while the MAC warps accumulate
+        // the next tile
+        const int fw = warp - kConsumerWarps;
+        LaneTw<M, true> lt;
+        lt.init(tw, lane & (LaneTw<M, true>::L - 1));
+        constexpr int R = LaneTw<M, true>::R, L = LaneTw<M, true>::L, LOGL = LaneTw<M, true>::LOGL;
+        constexpr int G = 32 / L;
+        constexpr int PER = 2 * FW * G;   // columns per pass, two per lane group at a time
+        const int grp = lane / L, g = lane % L;
+        const int kb = bitrev_lanes(g, LOGL) * R;
+        uint32_t it = 0;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+            const int b = tile + tile_lo;
+            const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
+            const int local = b - T.tile0, kxi = local / NTY, ky0 = (local % NTY) * kTileY;
+            const int nz = T.nz;
+            const bool have = wait_or_abort(accfull, it & 1);
+            if (have) {
+                for (int base = 0; base < 4 * kTileY; base += PER) {
+                    const int l0 = base + (fw * G + grp) * 2;
+                    float2 *c0 = acc + (l0 / kTileY) * FS + l0 % kTileY;
+                    float2 *c1 = acc + ((l0 + 1) / kTileY) * FS + (l0 + 1) % kTileY;
+                    const bool ok = l0 < 4 * kTileY;
+                    float2 v0[R], v1[R];
+#pragma unroll
+                    for (int n = 0; n < R; ++n) {
+                        v0[n] = ok ? c0[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
+                        v1[n] = ok ? c1[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
+                    }
+                    line_fft_c<M, true>(v0, lt);
+                    line_fft_c<M, true>(v1, lt);
+                    __syncwarp();
+                    if (ok) {
+#pragma unroll
+                        for (int k1 = 0; k1 < R; ++k1)
+                            if (k1 + kb < nz) {
+                                c0[(k1 + kb) * kTileYPad] = v0[k1];
+                                c1[(k1 + kb) * kTileYPad] = v1[k1];
+                            }
+                    }
+                    __syncwarp();
+                }
+            }
+            fft_sync();
+            if (have) {
+                const long long t2_field = (long long)(M / 2 + 1) * nz * M;
+                float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
+                for (int i = fw * 32 + lane; i < 4 * nz * (kTileY / 2); i += FW * 32) {
+                    const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
+                    const int zi = rem / (kTileY / 2), pp = rem % (kTileY / 2);
+                    const float2 *sp = acc + f * FS + zi * kTileYPad + 2 * pp;
+                    *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
+                        make_float4(sp[0].x, sp[0].y, sp[1].x, sp[1].y);
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(accempty);
         }
-        return stages + (size_t)s * STAGE;
+        return;
+    }
+
+    // ---------------------------------------------------------------- MAC warps
+    const int p = threadIdx.x & 7, r0 = threadIdx.x >> 3;   // ky pair p, rows r0 + RSTEP i
+    uint32_t qg = 0, qs = 0, it = 0;
+
+    // wait for stage q of a ring; its address (or nullptr after an abort/timeout)
+    auto take = [&](unsigned char *base, int bytes, uint64_t *full, int n, uint32_t q) -> const unsigned char * {
+        if (!wait_or_abort(&full[q % n], (q / n) & 1)) return nullptr;
+        return base + (size_t)(q % n) * bytes;
     };
-    auto give = [&](uint32_t qq) {
+    auto give = [&](uint64_t *empty, int n, uint32_t q) {
         __syncwarp();
-        if (lane == 0) mbar_arrive(&empty[qq % nstages]);
+        if (lane == 0) mbar_arrive(&empty[q % n]);
     };
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
         const int b = tile + tile_lo;
         const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
-        const int local = b - T.tile0, kxi = local / NTY, ky0 = (local % NTY) * kTileY;
 
         float4 a[ROWS][4];
 #pragma unroll
@@ -219,148 +329,119 @@ __global__ void __launch_bounds__((CW + 1) * 32, 1)
 
         for (int e = T.e0; e < T.er; ++e) {   // real kernels (self pair)
             float2 g[ROWS];
-            const unsigned char *st = take(q);
+            const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
             const float *Gt = reinterpret_cast<const float *>(st);   // [M][16]
 #pragma unroll
             for (int i = 0; i < ROWS; ++i) {
                 const int r = r0 + RSTEP * i;
                 g[i] = (st && r < M) ? *reinterpret_cast<const float2 *>(Gt + r * 16 + 2 * p) : make_float2(0.f, 0.f);
             }
-            give(q++);
+            give(gempty, NG, qg++);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const unsigned char *sf = take(q);
-                const float4 *S4 = reinterpret_cast<const float4 *>(sf);   // [M][8]
+            for (int o = 0; o < 4 / FPC; ++o) {
+                const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
 #pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = r0 + RSTEP * i;
-                    if (sf && r < M) {
-                        const float4 s = S4[r * 8 + p];
-                        a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
-                        a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
-                        a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
-                        a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                for (int ff = 0; ff < FPC; ++ff) {
+                    const int f = o * FPC + ff;
+                    const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);   // [M][8]
+#pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = r0 + RSTEP * i;
+                        if (sf && r < M) {
+                            const float4 s = S4[r * 8 + p];
+                            a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
+                            a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
+                            a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
+                            a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                        }
                     }
                 }
-                give(q++);
+                give(sempty, ns, qs++);
             }
         }
         for (int e = T.er; e < T.e1; ++e) {   // complex kernels (other sources)
             float4 g[ROWS];
-            const unsigned char *st = take(q);
+            const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
             const float4 *G4 = reinterpret_cast<const float4 *>(st);
 #pragma unroll
             for (int i = 0; i < ROWS; ++i) {
                 const int r = r0 + RSTEP * i;
                 g[i] = (st && r < M) ? G4[r * 8 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
             }
-            give(q++);
+            give(gempty, NG, qg++);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                const unsigned char *sf = take(q);
-                const float4 *S4 = reinterpret_cast<const float4 *>(sf);
+            for (int o = 0; o < 4 / FPC; ++o) {
+                const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
 #pragma unroll
-                for (int i = 0; i < ROWS; ++i) {
-                    const int r = r0 + RSTEP * i;
-                    if (sf && r < M) {
-                        const float4 s = S4[r * 8 + p];
-                        float4 &x = a[i][f];
-                        x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
-                        x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
-                        x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
-                        x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                for (int ff = 0; ff < FPC; ++ff) {
+                    const int f = o * FPC + ff;
+                    const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);
+#pragma unroll
+                    for (int i = 0; i < ROWS; ++i) {
+                        const int r = r0 + RSTEP * i;
+                        if (sf && r < M) {
+                            const float4 s = S4[r * 8 + p];
+                            float4 &x = a[i][f];
+                            x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
+                            x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
+                            x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
+                            x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                        }
                     }
                 }
-                give(q++);
+                give(sempty, ns, qs++);
             }
         }
 
-        // inverse FFT along z of the 64 columns, then rows z < nz to T2
+        // hand the sums to the FFT warps once they are done with the previous tile
+        if (it == 0 || wait_or_abort(accempty, (it - 1) & 1)) {
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i) {
-            const int r = r0 + RSTEP * i;
-            if (r >= M) continue;
+            for (int i = 0; i < ROWS; ++i) {
+                const int r = r0 + RSTEP * i;
+                if (r >= M) continue;
 #pragma unroll
-            for (int f = 0; f < 4; ++f) {
-                float2 *d = acc + f * FS + r * kTileYPad + 2 * p;
-                d[0] = make_float2(a[i][f].x, a[i][f].y);
-                d[1] = make_float2(a[i][f].z, a[i][f].w);
+                for (int f = 0; f < 4; ++f) {
+                    float2 *d = acc + f * FS + r * kTileYPad + 2 * p;
+                    d[0] = make_float2(a[i][f].x, a[i][f].y);
+                    d[1] = make_float2(a[i][f].z, a[i][f].w);
+                }
             }
         }
-        consumer_sync<CW>();
-        {
-            // 64 columns; each warp transforms two at a time (independent
-            // instruction streams for the scheduler to interleave)
-            constexpr int R = LaneTw<M, true>::R, L = LaneTw<M, true>::L, LOGL = LaneTw<M, true>::LOGL;
-            constexpr int G = 32 / L;
-            constexpr int PER = 2 * kConsumerWarps * G;   // columns per pass
-            const int grp = lane / L, g = lane % L;
-            const int kb = bitrev_lanes(g, LOGL) * R;
-            for (int base = 0; base < 4 * kTileY; base += PER) {
-                const int l0 = base + (warp * G + grp) * 2;
-                float2 *c0 = acc + (l0 / kTileY) * FS + l0 % kTileY;
-                float2 *c1 = acc + ((l0 + 1) / kTileY) * FS + (l0 + 1) % kTileY;
-                const bool ok = l0 < 4 * kTileY;
-                float2 v0[R], v1[R];
-#pragma unroll
-                for (int n = 0; n < R; ++n) {
-                    v0[n] = ok ? c0[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-                    v1[n] = ok ? c1[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-                }
-                line_fft_c<M, true>(v0, lt);
-                line_fft_c<M, true>(v1, lt);
-                __syncwarp();
-                if (ok) {
-#pragma unroll
-                    for (int k1 = 0; k1 < R; ++k1)
-                        if (k1 + kb < T.nz) {
-                            c0[(k1 + kb) * kTileYPad] = v0[k1];
-                            c1[(k1 + kb) * kTileYPad] = v1[k1];
-                        }
-                }
-                __syncwarp();
-            }
-        }
-        consumer_sync<CW>();
-        const int nz = T.nz;
-        const long long t2_field = (long long)(M / 2 + 1) * nz * M;
-        float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
-        for (int i = threadIdx.x; i < 4 * nz * (kTileY / 2); i += kConsumerWarps * 32) {
-            const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
-            const int zi = rem / (kTileY / 2), pp = rem % (kTileY / 2);
-            const float2 *s = acc + f * FS + zi * kTileYPad + 2 * pp;
-            *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
-                make_float4(s[0].x, s[0].y, s[1].x, s[1].y);
-        }
-        consumer_sync<CW>();   // the FFT tile is rewritten by the next tile
+        __syncwarp();
+        if (lane == 0) mbar_arrive(accfull);
     }
 }
 
-#define RP_TMA_CLASSES(X) X(32) X(48) X(64) X(96) X(128) X(192)
+// (class, field tiles per ring copy): must match mac_tma_fields_per_copy
+#define RP_TMA_CLASSES(X) X(32, 4) X(48, 4) X(64, 4) X(96, 4) X(128, 2) X(192, 1)
 
 }  // namespace
 
+int mac_tma_fields_per_copy(int M) { return M <= 96 ? 4 : (M == 128 ? 2 : 1); }
+
 int mac_tma_stages(int M, int smem_optin)
 {
-    const long long stage = (long long)M * 128;
-    const long long fixed = sizeof(float2) * (4LL * M * kTileYPad + M) + 16;   // FFT tile, twiddles, abort flag
-    long long n = (smem_optin - fixed) / (stage + 16);                          // + two mbarriers per stage
+    const long long sstage = (long long)mac_tma_fields_per_copy(M) * M * 128;
+    const long long fixed = (long long)mac_tma_smem(M, 0);   // kernel-tile ring, FFT tile, twiddles, barriers
+    long long n = (smem_optin - fixed) / (sstage + 16);      // + two mbarriers per stage
     if (n > kMaxStages) n = kMaxStages;
     return (int)n;
 }
 
 size_t mac_tma_smem(int M, int nstages)
 {
-    return (size_t)nstages * M * 128 + sizeof(float2) * (4 * (size_t)M * kTileYPad + M) + 16 * (size_t)nstages + 16;
+    const size_t stage = (size_t)M * 128;
+    return (size_t)nstages * mac_tma_fields_per_copy(M) * stage + kKernelStages * stage +
+           sizeof(float2) * (4 * (size_t)M * kTileYPad + M) + 16 * ((size_t)nstages + kKernelStages) + 16 + 16;
 }
 
 cudaError_t open_mac_tma_smem_limit(int max_optin)
 {
     cudaError_t e;
-#define X(M)                                                                                            \
-    if ((e = cudaFuncSetAttribute(k_mac_tma<M, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
-        (e = cudaFuncSetAttribute(k_mac_tma<M, 12>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
-        (e = cudaFuncSetAttribute(k_mac_tma<M, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
+#define X(M, F)                                                                                            \
+    if ((e = cudaFuncSetAttribute(k_mac_tma<M, 8, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||  \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 12, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 16, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))   \
         return e;
     RP_TMA_CLASSES(X)
 #undef X
@@ -368,22 +449,23 @@ cudaError_t open_mac_tma_smem_limit(int max_optin)
 }
 
 cudaError_t launch_mac_tma(int cls, int cw, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
-                           const MacEntry *d_entries, const CUtensorMap *d_maps, int nmaps, long long step, int clamp,
-                           int nstages, int grid, int *d_err, cudaStream_t s)
+                           const MacEntry *d_entries, long long step, int clamp, int nstages, int grid, int *d_err,
+                           cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
     if (cw != 8 && cw != 12 && cw != 16) return cudaErrorInvalidValue;
+    if (nstages < 2 || nstages > kMaxStages) return cudaErrorInvalidValue;
     const size_t smem = mac_tma_smem(cls, nstages);
-    const int threads = (cw + 1) * 32;
-#define RP_GO(M, CW)                                                                                      \
-    k_mac_tma<M, CW><<<grid, threads, smem, s>>>(d_tgts, t0, t1, tile_lo, ntiles, d_entries, d_maps, nmaps, step, \
-                                                 clamp, nstages, d_err)
+    const int threads = (cw + kFftWarps + 1) * 32;
+#define RP_GO(M, CW, F)                                                                                   \
+    k_mac_tma<M, CW, F><<<grid, threads, smem, s>>>(d_tgts, t0, t1, tile_lo, ntiles, d_entries, step, clamp, \
+                                                    nstages, d_err)
     switch (cls) {
-#define X(M)                                                                                            \
+#define X(M, F)                                                                                         \
     case M:                                                                                             \
-        if (cw == 8) RP_GO(M, 8);                                                                       \
-        else if (cw == 12) RP_GO(M, 12);                                                                \
-        else RP_GO(M, 16);                                                                              \
+        if (cw == 8) RP_GO(M, 8, F);                                                                    \
+        else if (cw == 12) RP_GO(M, 12, F);                                                             \
+        else RP_GO(M, 16, F);                                                                           \
         break;
         RP_TMA_CLASSES(X)
 #undef X
