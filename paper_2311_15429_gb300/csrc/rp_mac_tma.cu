@@ -119,8 +119,61 @@ __device__ __forceinline__ int owner(const T *arr, int lo, int hi, int b, int T:
     return lo;
 }
 
-// barrier among the FFT warps only
-__device__ __forceinline__ void fft_sync() { asm volatile("bar.sync 1, %0;" ::"n"(kFftWarps * 32) : "memory"); }
+// barrier `id` among the first (or last) `threads` threads of the block
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+// Inverse FFT along z of the 64 columns of the FFT tile `acc` (4 fields x
+// 16 ky), shared by warps w = 0 .. nw-1 (this one is w), then rows z < nz
+// to T2; barrier `bar` (nw warps) separates the two.
+template <int M>
+__device__ __forceinline__ void column_fft_store(float2 *acc, const InvTarget &T, int kxi, int ky0, int w, int nw,
+                                                 int lane, const LaneTw<M, true> &lt, int bar)
+{
+    constexpr int R = LaneTw<M, true>::R, L = LaneTw<M, true>::L, LOGL = LaneTw<M, true>::LOGL;
+    constexpr int G = 32 / L;
+    constexpr int FS = M * kTileYPad;
+    const int per = 2 * nw * G;   // columns per pass, two per lane group at a time
+    const int grp = lane / L, g = lane % L;
+    const int kb = bitrev_lanes(g, LOGL) * R;
+    const int nz = T.nz;
+    for (int base = 0; base < 4 * kTileY; base += per) {
+        const int l0 = base + (w * G + grp) * 2;
+        const bool ok = l0 < 4 * kTileY;
+        float2 *c0 = acc + (ok ? (l0 / kTileY) * FS + l0 % kTileY : 0);
+        float2 *c1 = acc + (ok ? ((l0 + 1) / kTileY) * FS + (l0 + 1) % kTileY : 0);
+        float2 v0[R], v1[R];
+#pragma unroll
+        for (int n = 0; n < R; ++n) {
+            v0[n] = ok ? c0[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
+            v1[n] = ok ? c1[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
+        }
+        line_fft_c<M, true>(v0, lt);
+        line_fft_c<M, true>(v1, lt);
+        __syncwarp();
+        if (ok) {
+#pragma unroll
+            for (int k1 = 0; k1 < R; ++k1)
+                if (k1 + kb < nz) {
+                    c0[(k1 + kb) * kTileYPad] = v0[k1];
+                    c1[(k1 + kb) * kTileYPad] = v1[k1];
+                }
+        }
+        __syncwarp();
+    }
+    named_sync(bar, nw * 32);
+    const long long t2_field = (long long)(M / 2 + 1) * nz * M;
+    float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
+    for (int i = w * 32 + lane; i < 4 * nz * (kTileY / 2); i += nw * 32) {
+        const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
+        const int zi = rem / (kTileY / 2), pp = rem % (kTileY / 2);
+        const float2 *sp = acc + f * FS + zi * kTileYPad + 2 * pp;
+        *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
+            make_float4(sp[0].x, sp[0].y, sp[1].x, sp[1].y);
+    }
+}
 
 // M: padded FFT size of the class; CW: multiply-accumulate warps (the block
 // has CW + kFftWarps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
@@ -239,64 +292,31 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
         return;
     }
 
+    // Tile hand-over: the MAC warps accumulate a tile in registers, store it
+    // to the FFT tile and signal accfull; the FFT warps transform and store it
+    // while the MAC warps accumulate the next one, then signal accempty.  A
+    // block's last tile has no successor, so all its consumer warps share
+    // that transform (barrier 2 in place of the two signals).
+    constexpr int kBarFft = 1, kBarAll = 2;
     if (warp >= kConsumerWarps) {
         // ------------------------------------------------------------ FFT warps
-        // inverse FFT along z of the 64 columns of each tile the MAC warps
-        // hand over, then rows z < nz to T2, while the MAC warps accumulate
-        // the next tile
         const int fw = warp - kConsumerWarps;
         LaneTw<M, true> lt;
         lt.init(tw, lane & (LaneTw<M, true>::L - 1));
-        constexpr int R = LaneTw<M, true>::R, L = LaneTw<M, true>::L, LOGL = LaneTw<M, true>::LOGL;
-        constexpr int G = 32 / L;
-        constexpr int PER = 2 * FW * G;   // columns per pass, two per lane group at a time
-        const int grp = lane / L, g = lane % L;
-        const int kb = bitrev_lanes(g, LOGL) * R;
         uint32_t it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int b = tile + tile_lo;
             const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
             const int local = b - T.tile0, kxi = local / NTY, ky0 = (local % NTY) * kTileY;
-            const int nz = T.nz;
+            if (tile + (int)gridDim.x >= ntiles) {
+                named_sync(kBarAll, (kConsumerWarps + FW) * 32);
+                column_fft_store<M>(acc, T, kxi, ky0, warp, kConsumerWarps + FW, lane, lt, kBarAll);
+                break;
+            }
             const bool have = wait_or_abort(accfull, it & 1);
-            if (have) {
-                for (int base = 0; base < 4 * kTileY; base += PER) {
-                    const int l0 = base + (fw * G + grp) * 2;
-                    float2 *c0 = acc + (l0 / kTileY) * FS + l0 % kTileY;
-                    float2 *c1 = acc + ((l0 + 1) / kTileY) * FS + (l0 + 1) % kTileY;
-                    const bool ok = l0 < 4 * kTileY;
-                    float2 v0[R], v1[R];
-#pragma unroll
-                    for (int n = 0; n < R; ++n) {
-                        v0[n] = ok ? c0[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-                        v1[n] = ok ? c1[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-                    }
-                    line_fft_c<M, true>(v0, lt);
-                    line_fft_c<M, true>(v1, lt);
-                    __syncwarp();
-                    if (ok) {
-#pragma unroll
-                        for (int k1 = 0; k1 < R; ++k1)
-                            if (k1 + kb < nz) {
-                                c0[(k1 + kb) * kTileYPad] = v0[k1];
-                                c1[(k1 + kb) * kTileYPad] = v1[k1];
-                            }
-                    }
-                    __syncwarp();
-                }
-            }
-            fft_sync();
-            if (have) {
-                const long long t2_field = (long long)(M / 2 + 1) * nz * M;
-                float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
-                for (int i = fw * 32 + lane; i < 4 * nz * (kTileY / 2); i += FW * 32) {
-                    const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
-                    const int zi = rem / (kTileY / 2), pp = rem % (kTileY / 2);
-                    const float2 *sp = acc + f * FS + zi * kTileYPad + 2 * pp;
-                    *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
-                        make_float4(sp[0].x, sp[0].y, sp[1].x, sp[1].y);
-                }
-            }
+            // on an abort the sums are not used: skip the transform, keep the barriers
+            if (have) column_fft_store<M>(acc, T, kxi, ky0, fw, FW, lane, lt, kBarFft);
+            else named_sync(kBarFft, FW * 32);
             __syncwarp();
             if (lane == 0) mbar_arrive(accempty);
         }
@@ -406,6 +426,15 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
                     d[1] = make_float2(a[i][f].z, a[i][f].w);
                 }
             }
+        }
+        if (tile + (int)gridDim.x >= ntiles) {
+            named_sync(kBarAll, (kConsumerWarps + FW) * 32);
+            LaneTw<M, true> lt;
+            lt.init(tw, lane & (LaneTw<M, true>::L - 1));
+            const int local = b - T.tile0;
+            column_fft_store<M>(acc, T, local / NTY, (local % NTY) * kTileY, warp, kConsumerWarps + FW, lane, lt,
+                                kBarAll);
+            break;
         }
         __syncwarp();
         if (lane == 0) mbar_arrive(accfull);
