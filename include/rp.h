@@ -86,8 +86,9 @@ typedef enum {
  * computes the pair plan (see rp_pair_info / rp_query) and push/evaluate
  * return RP_ERR_STATE.  Usable on a host without a GPU. */
 #define RP_FLAG_PLAN_ONLY 0x2u
-/* Time every kernel launch with CUDA events on the context stream; read the
- * totals with rp_kernel_stats. */
+/* Time kernel launches with CUDA events on the context stream (all of them,
+ * or those of one step in every rp_config.profile_every); read the totals
+ * with rp_kernel_stats and the launch counts with rp_kernel_count. */
 #define RP_FLAG_PROFILE 0x4u
 /* RP_MODE_LOWRANK: build the far pairs' factors in rp_train_far_model (for
  * the pairs the learned field does not take) instead of in rp_finalize, so
@@ -109,7 +110,11 @@ typedef struct {
                           * rp_finalize time the three variants on this plan (two launches each
                           * per FFT size class) and keep the fastest.  The variants sum the same
                           * terms in the same order: the choice changes timing, never results. */
-    int reserved[4];     /* set to zero */
+    int profile_every;   /* RP_FLAG_PROFILE: time the launches of step s only when s % profile_every == 0
+                          * (launches outside the step cycle always), >= 0; 0 or 1: every step.  The
+                          * events sit between kernels and hold back the next launch, so sampling
+                          * keeps them off most steps. */
+    int reserved[3];     /* set to zero */
 } rp_config;
 
 typedef struct rp_ctx rp_ctx;
@@ -211,11 +216,21 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
 
 /*
  * rp_push_host -- rp_push from HOST buffers h_rho[N], h_J[3][N] (pinned
- * memory recommended): the library copies them to the device on the stream.
- * The host buffers must stay valid and unchanged until the stream has
- * passed the call (rp_sync).
+ * memory recommended; one copy when h_J == h_rho + N).  The library copies
+ * them to device staging of its own on a host-to-device copy stream of the
+ * context, ordered before the push's kernels by an event, so that the copy
+ * overlaps kernels of earlier steps still running.  The host buffers must
+ * stay valid and unchanged until rp_sync.
  */
 rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J);
+
+/*
+ * rp_push_all_host -- rp_push_all from HOST buffers: h_rho[n] (N_n floats)
+ * and h_J[n] (3*N_n floats) of every domain n, copied as in rp_push_host,
+ * then one batched push.  Only at the start of a round.  The host buffers
+ * must stay valid and unchanged until rp_sync.
+ */
+rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *const *h_J);
 
 /*
  * rp_evaluate -- the retarded phi and A of the last complete step l on every
@@ -231,8 +246,12 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
 
 /*
  * rp_evaluate_host -- rp_evaluate into HOST buffers h_phi[n] (N_n floats) and
- * h_A[n] (3*N_n floats): the results are copied device-to-host on the
- * stream; they are valid after rp_sync.
+ * h_A[n] (3*N_n floats; one copy when h_A[n] == h_phi[n] + N_n): the results
+ * are staged in device memory of the library (two sets, alternating by step)
+ * and copied device-to-host on a device-to-host copy stream of the context
+ * (apart from the host-to-device one), overlapping the next step's kernels.
+ * They are valid after rp_sync (which waits for every stream of the
+ * context), not after a synchronisation of the context stream alone.
  */
 rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 
@@ -455,13 +474,19 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out);
 rp_status rp_pair_info(rp_ctx *ctx, int target, int source, rp_pair_info_t *out);
 
 /*
- * rp_kernel_stats -- under RP_FLAG_PROFILE: launches and summed device time
- * (ms, CUDA events on the context stream) of kernel class `kind` since the
- * last reset; waits for the stream.  reset != 0 clears all counters after
- * reading.
+ * rp_kernel_stats -- under RP_FLAG_PROFILE: timed launches and their summed
+ * device time (ms, CUDA events on the context stream) of kernel class `kind`
+ * since the last reset; waits for the stream.  reset != 0 clears all
+ * counters (these and rp_kernel_count's) after reading.
  */
 rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *total_ms,
                           int reset);
+
+/*
+ * rp_kernel_count -- under RP_FLAG_PROFILE: every launch of kernel class
+ * `kind` since the last reset, timed or not (host-side count, no wait).
+ */
+rp_status rp_kernel_count(rp_ctx *ctx, int kind, long long *launches);
 
 /* rp_kernel_name -- short name of a kernel class (NULL if out of range). */
 const char *rp_kernel_name(int kind);

@@ -174,8 +174,19 @@ struct rp_ctx {
     bool net_used = false;            // some learned pair adds the network's output
     std::vector<char> net_pair;       // [t * ndom + s]: the pair uses the network (else the linear skip alone)
     int smem_optin = 0;
-    std::vector<float *> in_stage;    // per domain [4][N], for host pushes
-    std::vector<float *> out_stage;   // per domain [4][N], for host evaluations
+    // Host-buffer calls: device staging per domain ([4][N]), two sets
+    // alternating by step parity, and a copy stream, so that a step's copies
+    // run while the kernels of the steps around it do; events order the two
+    // streams.
+    std::vector<float *> in_stage[2];
+    std::vector<float *> out_stage[2];
+    cudaStream_t copy_in = nullptr;            // host-to-device copies
+    cudaStream_t copy_out = nullptr;           // device-to-host copies (apart, so that a step's
+                                               // inputs never queue behind the last step's results)
+    cudaEvent_t in_ready = nullptr;            // the last host push's copy is done
+    std::vector<cudaEvent_t> in_free[2];       // per domain: the push that read in_stage[b][d] has run
+    cudaEvent_t out_ready = nullptr;           // the last host evaluation's results are staged
+    cudaEvent_t out_free[2] = {nullptr, nullptr};   // the copy out of out_stage[b] is done
 
     // step state
     long long step = -1;
@@ -185,8 +196,9 @@ struct rp_ctx {
     // profiling
     std::vector<ProfRec> pending;
     std::vector<cudaEvent_t> spare_events;
-    long long launches[RP_K_COUNT] = {};
+    long long launches[RP_K_COUNT] = {};   // timed launches
     double ms[RP_K_COUNT] = {};
+    long long count[RP_K_COUNT] = {};      // every launch
 
     std::string last_error;
 };
@@ -254,19 +266,23 @@ cudaEvent_t take_event(rp_ctx *ctx)
     return e;
 }
 
-// Runs `launch` (returns cudaError_t) bracketed by events when profiling.
+// Runs `launch` (returns cudaError_t), bracketed by events when profiling
+// and the current step is sampled.
 template <class F>
 rp_status timed_launch(rp_ctx *ctx, int kind, const char *what, F &&launch)
 {
     cudaEvent_t a = nullptr, b = nullptr;
-    if (ctx->profile) {
+    const int every = ctx->cfg.profile_every;
+    const bool timed = ctx->profile && (every <= 1 || ctx->step < 0 || ctx->step % every == 0);
+    if (ctx->profile) ctx->count[kind] += 1;
+    if (timed) {
         a = take_event(ctx);
         b = take_event(ctx);
         RP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
     }
     cudaError_t e = launch();
     if (e != cudaSuccess) return cuda_fail(ctx, e, what);
-    if (ctx->profile) {
+    if (timed) {
         RP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
         ctx->pending.push_back({kind, a, b});
     }
@@ -843,6 +859,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
     }
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
+    if (cfg->profile_every < 0) return RP_ERR_ARG;
     rp_ctx *ctx = new rp_ctx();
     ctx->cfg = *cfg;
     if (ctx->cfg.far_points == 0) ctx->cfg.far_points = 4;
@@ -1437,17 +1454,92 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     return enqueue_push(ctx, 0, nd, in);
 }
 
+// The copy stream, events and staging vectors of the host-buffer calls, on
+// first use.
+static rp_status open_host_copies(rp_ctx *ctx)
+{
+    if (ctx->copy_in) return RP_OK;
+    const int nd = (int)ctx->doms.size();
+    cudaStream_t a = nullptr, b = nullptr;
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
+    ctx->copy_in = a;
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
+    ctx->copy_out = b;
+    auto event = [&](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
+    RP_CUDA(ctx, event(&ctx->in_ready));
+    RP_CUDA(ctx, event(&ctx->out_ready));
+    for (int b = 0; b < 2; ++b) {
+        RP_CUDA(ctx, event(&ctx->out_free[b]));
+        ctx->in_stage[b].assign(nd, nullptr);
+        ctx->out_stage[b].assign(nd, nullptr);
+        ctx->in_free[b].assign(nd, nullptr);
+        for (int d = 0; d < nd; ++d) RP_CUDA(ctx, event(&ctx->in_free[b][d]));
+    }
+    return RP_OK;
+}
+
+// Copies domain id's host inputs of step parity b into its device staging on
+// the copy stream, after the push two steps back that read that staging.
+static rp_status stage_host_input(rp_ctx *ctx, int id, int b, const float *h_rho, const float *h_J)
+{
+    rp_status st;
+    const long long N = ctx->doms[id].N;
+    if (!ctx->in_stage[b][id] && (st = dev_alloc(ctx, &ctx->in_stage[b][id], 4 * (size_t)N))) return st;
+    float *dst = ctx->in_stage[b][id];
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b][id], 0));
+    if (h_J == h_rho + N) {
+        RP_CUDA(ctx, cudaMemcpyAsync(dst, h_rho, 4 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_in));
+    } else {
+        RP_CUDA(ctx, cudaMemcpyAsync(dst, h_rho, N * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_in));
+        RP_CUDA(ctx, cudaMemcpyAsync(dst + N, h_J, 3 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_in));
+    }
+    return RP_OK;
+}
+
 rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J)
 {
     rp_status st = check_ready(ctx);
     if (st) return st;
-    if (id < 0 || id >= (int)ctx->doms.size() || !h_rho || !h_J) return fail(ctx, RP_ERR_ARG, "rp_push_host: bad id or pointer");
-    if (ctx->in_stage.empty()) ctx->in_stage.assign(ctx->doms.size(), nullptr);
-    const long long N = ctx->doms[id].N;
-    if (!ctx->in_stage[id] && (st = dev_alloc(ctx, &ctx->in_stage[id], 4 * (size_t)N))) return st;
-    RP_CUDA(ctx, cudaMemcpyAsync(ctx->in_stage[id], h_rho, N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    RP_CUDA(ctx, cudaMemcpyAsync(ctx->in_stage[id] + N, h_J, 3 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->stream));
-    return rp_push(ctx, id, ctx->in_stage[id], ctx->in_stage[id] + N);
+    const int nd = (int)ctx->doms.size();
+    if (id < 0 || id >= nd || !h_rho || !h_J) return fail(ctx, RP_ERR_ARG, "rp_push_host: bad id or pointer");
+    if ((st = open_host_copies(ctx))) return st;
+    // the step this push belongs to (a complete round starts the next one)
+    const long long step = (ctx->step < 0 || ctx->npushed == nd) ? ctx->step + 1 : ctx->step;
+    const int b = (int)(step & 1);
+    if ((st = stage_host_input(ctx, id, b, h_rho, h_J))) return st;
+    RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
+    float *dst = ctx->in_stage[b][id];
+    if ((st = rp_push(ctx, id, dst, dst + ctx->doms[id].N))) return st;
+    RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b][id], ctx->stream));
+    return RP_OK;
+}
+
+rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *const *h_J)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!h_rho || !h_J) return fail(ctx, RP_ERR_ARG, "rp_push_all_host: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!h_rho[d] || !h_J[d]) return fail(ctx, RP_ERR_ARG, "rp_push_all_host: NULL buffer");
+    if (ctx->step >= 0 && ctx->npushed != 0 && ctx->npushed != nd)
+        return fail(ctx, RP_ERR_STATE, "rp_push_all_host inside a partially pushed step");
+    if ((st = open_host_copies(ctx))) return st;
+    const int b = (int)((ctx->step + 1) & 1);
+    for (int d = 0; d < nd; ++d)
+        if ((st = stage_host_input(ctx, d, b, h_rho[d], h_J[d]))) return st;
+    RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
+    std::vector<const float *> rho(nd), J(nd);
+    for (int d = 0; d < nd; ++d) {
+        rho[d] = ctx->in_stage[b][d];
+        J[d] = ctx->in_stage[b][d] + ctx->doms[d].N;
+    }
+    if ((st = rp_push_all(ctx, rho.data(), J.data()))) return st;
+    // one event would do for all domains; the per-domain ones keep rp_push_host's bookkeeping
+    for (int d = 0; d < nd; ++d) RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b][d], ctx->stream));
+    return RP_OK;
 }
 
 rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
@@ -1530,19 +1622,33 @@ rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A)
     if (!h_phi || !h_A) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host: NULL pointer array");
     for (int d = 0; d < nd; ++d)
         if (!h_phi[d] || !h_A[d]) return fail(ctx, RP_ERR_ARG, "rp_evaluate_host: NULL output buffer");
-    if (ctx->out_stage.empty()) ctx->out_stage.assign(nd, nullptr);
+    if ((st = open_host_copies(ctx))) return st;
+    const int b = (int)(std::max(ctx->step, 0LL) & 1);
     std::vector<float *> phi(nd), A(nd);
     for (int d = 0; d < nd; ++d) {
-        if (!ctx->out_stage[d] && (st = dev_alloc(ctx, &ctx->out_stage[d], 4 * (size_t)ctx->doms[d].N))) return st;
-        phi[d] = ctx->out_stage[d];
-        A[d] = ctx->out_stage[d] + ctx->doms[d].N;
+        if (!ctx->out_stage[b][d] && (st = dev_alloc(ctx, &ctx->out_stage[b][d], 4 * (size_t)ctx->doms[d].N)))
+            return st;
+        phi[d] = ctx->out_stage[b][d];
+        A[d] = ctx->out_stage[b][d] + ctx->doms[d].N;
     }
+    // the evaluation waits for the copy out of this buffer two steps back
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->out_free[b], 0));
     if ((st = rp_evaluate(ctx, phi.data(), A.data()))) return st;
+    RP_CUDA(ctx, cudaEventRecord(ctx->out_ready, ctx->stream));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_out, ctx->out_ready, 0));
     for (int d = 0; d < nd; ++d) {
         const long long N = ctx->doms[d].N;
-        RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
-        RP_CUDA(ctx, cudaMemcpyAsync(h_A[d], A[d], 3 * N * sizeof(float), cudaMemcpyDeviceToHost, ctx->stream));
+        if (h_A[d] == h_phi[d] + N) {
+            RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], 4 * N * sizeof(float), cudaMemcpyDeviceToHost,
+                                         ctx->copy_out));
+        } else {
+            RP_CUDA(ctx, cudaMemcpyAsync(h_phi[d], phi[d], N * sizeof(float), cudaMemcpyDeviceToHost,
+                                         ctx->copy_out));
+            RP_CUDA(ctx, cudaMemcpyAsync(h_A[d], A[d], 3 * N * sizeof(float), cudaMemcpyDeviceToHost,
+                                         ctx->copy_out));
+        }
     }
+    RP_CUDA(ctx, cudaEventRecord(ctx->out_free[b], ctx->copy_out));
     return RP_OK;
 }
 
@@ -1883,6 +1989,8 @@ rp_status rp_sync(rp_ctx *ctx)
     rp_status st = use_device(ctx);
     if (st) return st;
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->copy_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_in));
+    if (ctx->copy_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_out));
     RP_CUDA(ctx, cudaGetLastError());
     if (ctx->d_err) {
         int flag = 0;
@@ -1953,8 +2061,16 @@ rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *to
     if (launches) *launches = ctx->launches[kind];
     if (total_ms) *total_ms = ctx->ms[kind];
     if (reset) {
-        for (int k = 0; k < RP_K_COUNT; ++k) { ctx->launches[k] = 0; ctx->ms[k] = 0.0; }
+        for (int k = 0; k < RP_K_COUNT; ++k) { ctx->launches[k] = 0; ctx->ms[k] = 0.0; ctx->count[k] = 0; }
     }
+    return RP_OK;
+}
+
+rp_status rp_kernel_count(rp_ctx *ctx, int kind, long long *launches)
+{
+    if (!ctx || kind < 0 || kind >= RP_K_COUNT || !launches) return RP_ERR_ARG;
+    if (!ctx->profile) return fail(ctx, RP_ERR_STATE, "context created without RP_FLAG_PROFILE");
+    *launches = ctx->count[kind];
     return RP_OK;
 }
 
@@ -2075,6 +2191,17 @@ void rp_destroy(rp_ctx *ctx)
         cudaGetDevice(&cur);
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->copy_in) {
+            cudaStreamSynchronize(ctx->copy_in);
+            cudaStreamSynchronize(ctx->copy_out);
+            for (cudaEvent_t e : {ctx->in_ready, ctx->out_ready, ctx->out_free[0], ctx->out_free[1]})
+                if (e) cudaEventDestroy(e);
+            for (int b = 0; b < 2; ++b)
+                for (cudaEvent_t e : ctx->in_free[b])
+                    if (e) cudaEventDestroy(e);
+            cudaStreamDestroy(ctx->copy_in);
+            cudaStreamDestroy(ctx->copy_out);
+        }
         for (const ProfRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
         for (void *p : ctx->allocs) cudaFree(p);

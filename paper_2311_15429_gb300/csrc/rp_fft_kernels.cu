@@ -215,6 +215,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restric
     float2 *W = Q + ny * qs;
     load_twiddles(twx, R.tw_x, ax.M);
     load_twiddles(twy, R.tw_y, ay.M);
+    pdl_trigger();
+    pdl_wait();   // the input slice may come from the previous kernel; t1 was read by it
     __syncthreads();
 
     const float *src = f == 0 ? in.rho[R.src] : in.J[R.src] + (long long)(f - 1) * N;
@@ -306,6 +308,8 @@ __global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restri
     float2 *tw = sm;
     float2 *V = tw + mz;
     load_twiddles(tw, R.tw_z, mz);
+    pdl_trigger();
+    pdl_wait();   // t1 is written by the plane pass
     const long long t1_field = (long long)kx * nz * my;
     const float2 *src = R.t1 + (long long)kxi * nz * my + ky0;
     if constexpr (M > 0) {
@@ -384,6 +388,8 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     float2 *tw = sm;
     float2 *acc = tw + mz;                 // [4][mz][kTileYPad]
     load_twiddles(tw, T.tw_z, mz);
+    pdl_trigger();
+    pdl_wait();   // the newest ring slot is written by the column pass
 
     if constexpr (M > 0) {
         // Thread (p, r0) owns ky columns 2p, 2p+1 and kz rows r0 + 32 i.  All
@@ -636,6 +642,8 @@ __global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restr
     float *O = reinterpret_cast<float *>(P + kx * ps);      // [ny][nx]
     load_twiddles(twx, T.tw_x, ax.M);
     load_twiddles(twy, T.tw_y, my);
+    pdl_trigger();
+    pdl_wait();   // T2 is written by the MAC
     const float2 *src = T.t2 + ((long long)f * kx * nz + z) * my;
     const long long row_stride = (long long)nz * my;
     if constexpr (M > 0) {
@@ -768,7 +776,7 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
 }
 
 #define RP_CASE(M, KERNEL, ...) \
-    case M: KERNEL<M><<<nblocks, kThreads, smem, s>>>(__VA_ARGS__); break;
+    case M: if (cudaError_t e_ = launch_pdl(KERNEL<M>, dim3(nblocks), dim3(kThreads), smem, s, __VA_ARGS__)) return e_; break;
 
 cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
                              int nblocks, size_t smem, int far_slot, cudaStream_t s)

@@ -221,6 +221,8 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     load_twiddles(tw, tgts[t0].tw_z, M);
+    pdl_trigger();
+    pdl_wait();   // the newest ring slot is written by the column pass; T2 was read by the last plane pass
     __syncthreads();
 
     // wait for a phase; false (and the error raised) on abort/timeout
@@ -486,9 +488,10 @@ cudaError_t launch_mac_tma(int cls, int cw, const InvTarget *d_tgts, int t0, int
     if (nstages < 2 || nstages > kMaxStages) return cudaErrorInvalidValue;
     const size_t smem = mac_tma_smem(cls, nstages);
     const int threads = (cw + kFftWarps + 1) * 32;
+    cudaError_t e = cudaSuccess;
 #define RP_GO(M, CW, F)                                                                                   \
-    k_mac_tma<M, CW, F><<<grid, threads, smem, s>>>(d_tgts, t0, t1, tile_lo, ntiles, d_entries, step, clamp, \
-                                                    nstages, d_err)
+    e = launch_pdl(k_mac_tma<M, CW, F>, dim3(grid), dim3(threads), smem, s, d_tgts, t0, t1, tile_lo, ntiles, \
+                   d_entries, step, clamp, nstages, d_err)
     switch (cls) {
 #define X(M, F)                                                                                         \
     case M:                                                                                             \
@@ -501,7 +504,7 @@ cudaError_t launch_mac_tma(int cls, int cw, const InvTarget *d_tgts, int t0, int
     default: return cudaErrorInvalidValue;
     }
 #undef RP_GO
-    return cudaGetLastError();
+    return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 }  // namespace rp

@@ -29,7 +29,7 @@ class rp_config(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("history_depth", ctypes.c_int),
                 ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("far_points", ctypes.c_int),
                 ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int), ("mac_warps", ctypes.c_int),
-                ("reserved", ctypes.c_int * 4)]
+                ("profile_every", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class rp_pair_info_t(ctypes.Structure):
@@ -83,6 +83,7 @@ SIGNATURES = {
     "rp_push": (_I, [_V, _I, _V, _V]),
     "rp_push_all": (_I, [_V, _PP, _PP]),
     "rp_push_host": (_I, [_V, _I, _V, _V]),
+    "rp_push_all_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
@@ -100,6 +101,7 @@ SIGNATURES = {
     "rp_pair_info": (_I, [_V, _I, _I, ctypes.POINTER(rp_pair_info_t)]),
     "rp_kernel_stats": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double), _I]),
+    "rp_kernel_count": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "rp_kernel_name": (ctypes.c_char_p, [_I]),
     "rp_save_state": (_I, [_V, ctypes.c_char_p]),
     "rp_load_state": (_I, [_V, ctypes.c_char_p]),
@@ -150,8 +152,18 @@ def _ptr(x) -> int:
 
 
 def _ptr_array(xs: Sequence):
+    if isinstance(xs, ctypes.Array):   # made by pointer_array
+        return ctypes.cast(xs, _PP), xs
     arr = (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
     return ctypes.cast(arr, _PP), arr
+
+
+def pointer_array(xs: Sequence):
+    """The per-domain pointer array of a call taking one buffer per domain
+    (rp_push_all, rp_push_all_host, rp_evaluate, rp_evaluate_host), built
+    once for buffers that are reused: those calls accept it in place of the
+    list.  The buffers must outlive it."""
+    return (ctypes.c_void_p * len(xs))(*[_ptr(x) for x in xs])
 
 
 def _check(st: int, ctx=None):
@@ -175,10 +187,11 @@ def rp_last_error(ctx) -> str:
 
 def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
               flags: int = 0, device: int = 0, stream=None, far_distance: float = 0.0,
-              far_points: int = 0, far_batch: int = 0, mac_warps: int = 0):
+              far_points: int = 0, far_batch: int = 0, mac_warps: int = 0, profile_every: int = 0):
     """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream (NULL without torch)."""
-    cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch, mac_warps)
+    cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch, mac_warps,
+                    profile_every)
     if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
         try:
             import torch
@@ -217,6 +230,12 @@ def rp_push_all(ctx, rhos: Sequence, Js: Sequence):
 
 def rp_push_host(ctx, dom: int, rho, J):
     _check(load().rp_push_host(ctx, dom, _ptr(rho), _ptr(J)), ctx)
+
+
+def rp_push_all_host(ctx, rhos: Sequence, Js: Sequence):
+    pr, _a = _ptr_array(rhos)
+    pj, _b = _ptr_array(Js)
+    _check(load().rp_push_all_host(ctx, pr, pj), ctx)
 
 
 def rp_evaluate(ctx, phis: Sequence, As: Sequence):
@@ -361,6 +380,12 @@ def rp_kernel_stats(ctx, kind: int, reset: bool = False):
     return n.value, ms.value
 
 
+def rp_kernel_count(ctx, kind: int) -> int:
+    n = ctypes.c_longlong()
+    _check(load().rp_kernel_count(ctx, kind, ctypes.byref(n)), ctx)
+    return n.value
+
+
 def rp_save_state(ctx, path: str):
     _check(load().rp_save_state(ctx, path.encode()), ctx)
 
@@ -382,11 +407,11 @@ class RetardedPotentials:
     def __init__(self, domains, c: float, dt: float, history_depth: int = 0,
                  mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
                  far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0,
-                 mac_warps: int = 0):
+                 mac_warps: int = 0, profile_every: int = 0):
         import torch
         self.domains = list(domains)
         self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
-                             far_points, far_batch, mac_warps)
+                             far_points, far_batch, mac_warps, profile_every)
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)

@@ -190,7 +190,7 @@ def test_config_validation():
     """Out-of-range configuration fields are refused at rp_create."""
     bad = [dict(mac_warps=10), dict(mac_warps=-8), dict(mode=rp.RP_MODE_LOWRANK, far_distance=0.0),
            dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=12),
-           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9)]
+           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9), dict(profile_every=-1)]
     for kw in bad:
         with pytest.raises(rp.RPError) as e:
             rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, **kw)

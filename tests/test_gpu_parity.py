@@ -260,3 +260,83 @@ def test_mac_variants_agree_bitwise(n):
         q = lib.query()
         assert q["mac_tma"] == 1 and q["mac_warps"] in (8, 12, 16), q
     _score(w.domains, hists, 0, w.c, w.dt, outs[12], nodes=[np.arange(0, d.N, 97) for d in w.domains])
+
+
+def test_sampled_kernel_timing():
+    """profile_every = 4: every launch is counted, only those of steps
+    s % 4 == 0 are timed; results are unchanged by the sampling."""
+    import torch
+    w = synth.workload("cfg1")
+    hists = histories(w.sources, 0, 24, w.dt)
+    dev = torch.device("cuda", 0)
+    outs = {}
+    for every in (0, 4):
+        flags = rp.RP_FLAG_PROFILE | rp.RP_FLAG_GROUND_STATE_CLAMP
+        with rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=64, flags=flags,
+                                   profile_every=every) as lib:
+            for i in range(24):
+                lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
+                             [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists])
+                if i == 0:
+                    rp.rp_kernel_stats(lib.ctx, 0, reset=True)   # after finalize-time launches
+                    continue
+                lib.evaluate()
+            torch.cuda.synchronize()
+            outs[every] = [lib.phi[t].cpu().numpy().copy() for t in range(len(w.domains))]
+            for kind in (rp.RP_K_MAC_INV_COLUMN, rp.RP_K_INV_PLANE):
+                n_timed, ms = rp.rp_kernel_stats(lib.ctx, kind)
+                n_all = rp.rp_kernel_count(lib.ctx, kind)
+                assert n_all == 23, (kind, n_all)               # steps 1 .. 23 evaluated
+                assert n_timed == (23 if every == 0 else 5), (kind, n_timed)   # 4, 8, .., 20
+                assert ms > 0.0
+    for a, b in zip(outs[0], outs[4]):
+        assert np.array_equal(a, b)
+
+
+@pytest.mark.parametrize("adjacent,push_all", [(True, False), (False, False), (True, True)])
+def test_host_path_pipelined_steps(adjacent, push_all):
+    """rp_push_host / rp_evaluate_host on consecutive steps with no rp_sync in
+    between (the copies run on the context's copy stream, staging alternates
+    by step): every step's host results equal the device path's bits.
+    adjacent: rho/J and phi/A in one pinned buffer each (one copy), else in
+    separate pinned buffers (two copies).  push_all: rp_push_all_host with
+    pointer arrays made once per step, else rp_push_host per domain."""
+    import torch
+    w = synth.workload("cfg1")
+    T, first = 14, 6
+    hists = histories(w.sources, 0, T, w.dt)
+    want = run_library(w.domains, w.c, w.dt, hists, 0, range(first, T), push="all")
+    nd = len(w.domains)
+    pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()
+    if adjacent:
+        hin = [[pin(hists[d][i]) for d in range(nd)] for i in range(T)]     # [4][N] per (step, domain)
+        rhos = [[hin[i][d][0] for d in range(nd)] for i in range(T)]
+        Js = [[hin[i][d][1:].reshape(-1) for d in range(nd)] for i in range(T)]
+        hout = {i: [torch.zeros(4 * dd.N).pin_memory() for dd in w.domains] for i in range(first, T)}
+        phis = {i: [hout[i][d][: w.domains[d].N] for d in range(nd)] for i in hout}
+        As = {i: [hout[i][d][w.domains[d].N:] for d in range(nd)] for i in hout}
+    else:
+        rhos = [[pin(hists[d][i, 0]) for d in range(nd)] for i in range(T)]
+        Js = [[pin(hists[d][i, 1:].reshape(-1)) for d in range(nd)] for i in range(T)]
+        phis = {i: [torch.zeros(dd.N).pin_memory() for dd in w.domains] for i in range(first, T)}
+        As = {i: [torch.zeros(3 * dd.N).pin_memory() for dd in w.domains] for i in range(first, T)}
+    ctx = rp.rp_create(w.c, w.dt)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        for i in range(T):
+            if push_all:
+                rp.rp_push_all_host(ctx, rp.pointer_array(rhos[i]), rp.pointer_array(Js[i]))
+            else:
+                for d in range(nd):
+                    rp.rp_push_host(ctx, d, rhos[i][d], Js[i][d])
+            if i >= first:
+                rp.rp_evaluate_host(ctx, phis[i], As[i])
+        rp.rp_sync(ctx)
+    finally:
+        rp.rp_destroy(ctx)
+    for i in range(first, T):
+        for d in range(nd):
+            got = np.concatenate([phis[i][d].numpy(), As[i][d].numpy()])
+            np.testing.assert_array_equal(got, want[i][d].reshape(-1), err_msg=f"step {i} domain {d}")
