@@ -35,6 +35,11 @@ UNIT = "updates/s"
 # per-kernel CUDA events on steps s % PROFILE_EVERY == 0 only: events between
 # kernels hold back the next launch, so timing every step slows the step itself
 PROFILE_EVERY = 15
+
+
+def profile_every(steps):
+    """Sampling period of the per-kernel events: every step on short runs."""
+    return PROFILE_EVERY if steps >= 10 * PROFILE_EVERY else 1
 L2_BYTES = 129 * 2 ** 20
 
 
@@ -337,7 +342,7 @@ def run_ours(args, rank, world, local):
 
     mode = rp.RP_MODE_LOWRANK if args.mode == "lowrank" else rp.RP_MODE_FFT
     lib = rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, mode=mode,
-                                flags=rp.RP_FLAG_PROFILE, profile_every=PROFILE_EVERY, device=local, stream=stream,
+                                flags=rp.RP_FLAG_PROFILE, profile_every=profile_every(K), device=local, stream=stream,
                                 far_distance=args.far_distance, far_batch=args.far_batch)
     info = {(t, s): lib.pair_info(t, s) for t in range(len(w.domains)) for s in range(len(w.domains))}
     mac_warps = lib.query()["mac_warps"]
@@ -503,7 +508,7 @@ def run_ours(args, rank, world, local):
                          f"({in_bytes / 2**20:.0f} MiB), spectral ring "
                          f"{lib_bytes_str(w, info, depth)} read per step",
                    "mac_consumer_warps": mac_warps,
-                   "kernel_timing": f"CUDA events around each kernel on the steps s % {PROFILE_EVERY} == 0 "
+                   "kernel_timing": f"CUDA events around each kernel on the steps s % {profile_every(K)} == 0 "
                                     f"of the timed region; launches counted on every step",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "accuracy": acc,
@@ -630,6 +635,8 @@ def run_deep(args, rank, world, local):
             kstats[rp.rp_kernel_name(kind)] = {"launches": n, "avg_us": 1e3 * t / n, "total_ms": t}
             launches += n
     alg = algorithmic_bytes(w, info)
+    if mode == "lowrank":
+        alg["far_gemm"] = far_gemm_bytes(w, info, 4, args.far_batch)
     peak, peak_kind = measured_peak()
     for k in kstats:
         if k in alg:
