@@ -193,7 +193,7 @@ struct FwdPlaneY {
 };
 
 template <int M>
-__global__ void __launch_bounds__(kThreads) k_fwd_plane(const FwdRing *__restrict__ rings, IoPtrs in,
+__global__ void __launch_bounds__(kPlaneThreads) k_fwd_plane(const FwdRing *__restrict__ rings, IoPtrs in,
                                                           int r0, int r1, int block_lo, int far_slot)
 {
     extern __shared__ float4 smem_f4[];
@@ -288,7 +288,7 @@ struct ColumnFFT {
 
 // Forward FFT along z of the four fields of one (kx, 16-ky) column block.
 template <int M>
-__global__ void __launch_bounds__(kThreads) k_fwd_column(const FwdRing *__restrict__ rings, int r0, int r1,
+__global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__restrict__ rings, int r0, int r1,
                                                            int block_lo, long long step)
 {
     extern __shared__ float4 smem_f4[];
@@ -621,7 +621,7 @@ struct InvPlaneX {
 };
 
 template <int M>
-__global__ void __launch_bounds__(kThreads) k_inv_plane(const InvTarget *__restrict__ tgts, int t0, int t1,
+__global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__restrict__ tgts, int t0, int t1,
                                                           int block_lo, OutPtrs out, float inv_c, long long step)
 {
     extern __shared__ float4 smem_f4[];
@@ -724,7 +724,7 @@ size_t smem_fwd_plane(int ny, const Axis &ax)
     const int kx = ax.M / 2 + 1;
     const int qs = kx | 1;
     // twiddles (x and y, bounded by kMaxFFT each) + Q + per-group scratch
-    return sizeof(float2) * (2 * kMaxFFT + (size_t)ny * qs + (size_t)(kThreads / 32) * 32 * ax.R);
+    return sizeof(float2) * (2 * kMaxFFT + (size_t)ny * qs + (size_t)(kPlaneThreads / 32) * 32 * ax.R);
 }
 
 size_t smem_fwd_column(const Axis &az) { return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad); }
@@ -775,15 +775,15 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
     return cudaGetLastError();
 }
 
-#define RP_CASE(M, KERNEL, ...) \
-    case M: if (cudaError_t e_ = launch_pdl(KERNEL<M>, dim3(nblocks), dim3(kThreads), smem, s, __VA_ARGS__)) return e_; break;
+#define RP_CASE(M, KERNEL, THREADS, ...) \
+    case M: if (cudaError_t e_ = launch_pdl(KERNEL<M>, dim3(nblocks), dim3(THREADS), smem, s, __VA_ARGS__)) return e_; break;
 
 cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
                              int nblocks, size_t smem, int far_slot, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_fwd_plane, d_rings, in, r0, r1, block_lo, far_slot)
+#define X(M) RP_CASE(M, k_fwd_plane, kPlaneThreads, d_rings, in, r0, r1, block_lo, far_slot)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -796,7 +796,7 @@ cudaError_t launch_fwd_column(int cls, const FwdRing *d_rings, int r0, int r1, i
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_fwd_column, d_rings, r0, r1, block_lo, step)
+#define X(M) RP_CASE(M, k_fwd_column, kColumnThreads, d_rings, r0, r1, block_lo, step)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -810,7 +810,7 @@ cudaError_t launch_mac_inv_column(int cls, const InvTarget *d_tgts, int t0, int 
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_mac_inv_column, d_tgts, t0, t1, block_lo, d_entries, step, clamp)
+#define X(M) RP_CASE(M, k_mac_inv_column, kThreads, d_tgts, t0, t1, block_lo, d_entries, step, clamp)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -823,7 +823,7 @@ cudaError_t launch_inv_plane(int cls, const InvTarget *d_tgts, int t0, int t1, i
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_inv_plane, d_tgts, t0, t1, block_lo, out, inv_c, step)
+#define X(M) RP_CASE(M, k_inv_plane, kPlaneThreads, d_tgts, t0, t1, block_lo, out, inv_c, step)
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;

@@ -9,7 +9,9 @@ namespace rp {
 
 constexpr int kMaxDomains = 256;
 constexpr int kMaxFFT = 192;   // largest padded FFT length per axis
-constexpr int kThreads = 256;  // threads per block of every FFT-path kernel
+constexpr int kThreads = 256;        // threads per block: ring push, register-blocked MAC
+constexpr int kPlaneThreads = 256;   // threads per block of the forward and inverse plane passes
+constexpr int kColumnThreads = 256;  // threads per block of the forward column pass
 constexpr int kTileY = 16;     // ky columns per block of the column passes
 constexpr int kTileYPad = 17;  // shared-memory row stride of a column tile (bank spread)
 

@@ -39,8 +39,10 @@ namespace {
 constexpr long long kWaitLimit = 4000000000LL;   // SM clock cycles (about 2 s)
 constexpr int kMaxStages = 24;
 constexpr int kKernelStages = 2;   // depth of the kernel-tile ring
-constexpr int kFftWarps = 3;       // warps of the inverse column FFT and the T2 store (with the
-                                   // producer, a whole warp per scheduler for the register split)
+constexpr int kFftWarps = 7;       // warps of the inverse column FFT and the T2 store: with the
+                                   // producer, 8 + 8/12/16 MAC warps, a whole number of warps per
+                                   // scheduler for the register split; 7 keep up with tiles of few
+                                   // entries (the self lags alone), where 3 left the MAC warps waiting
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
