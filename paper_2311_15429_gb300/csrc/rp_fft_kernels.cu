@@ -642,8 +642,25 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
     float *O = reinterpret_cast<float *>(P + kx * ps);      // [ny][nx]
     load_twiddles(twx, T.tw_x, ax.M);
     load_twiddles(twy, T.tw_y, my);
+    // far pairs: the target's Lagrange weights (constant) into shared memory
+    // now, so that the interpolation at the end reads no global table
+    const FarTarget *Fp = T.far;
+    int fpx = 0, fpy = 0, fpz = 0, fr = 0, fdepth = 1;
+    const float *fcring = nullptr;
+    float *cz = O + nx * ny;                                // [py][px]
+    float *ux = cz + kMaxFarPts * kMaxFarPts;               // [py][nx]
+    float *sLx = ux + kMaxFarPts * nx;                      // [nx][px]
+    float *sLy = sLx + kMaxFarPts * nx;                     // [ny][py]
+    float *sLz = sLy + kMaxFarPts * ny;                     // [pz], row z
+    float *sc = sLz + kMaxFarPts;                           // [r]: this step's coefficients of field f
+    if (Fp) {
+        fpx = Fp->px; fpy = Fp->py; fpz = Fp->pz; fr = Fp->r; fdepth = Fp->depth; fcring = Fp->cring;
+        for (int i = threadIdx.x; i < nx * fpx; i += blockDim.x) sLx[i] = __ldg(Fp->Lx + i);
+        for (int i = threadIdx.x; i < ny * fpy; i += blockDim.x) sLy[i] = __ldg(Fp->Ly + i);
+        for (int i = threadIdx.x; i < fpz; i += blockDim.x) sLz[i] = __ldg(Fp->Lz + z * fpz + i);
+    }
     pdl_trigger();
-    pdl_wait();   // T2 is written by the MAC
+    pdl_wait();   // T2 is written by the MAC, the coefficient ring by the far scatter or the learned field
     const float2 *src = T.t2 + ((long long)f * kx * nz + z) * my;
     const long long row_stride = (long long)nz * my;
     if constexpr (M > 0) {
@@ -671,27 +688,26 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
     __syncthreads();
     const long long N = (long long)nx * ny * nz;
     float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * N) + (long long)z * nx * ny;
-    if (!T.far) {
+    if (!Fp) {
         for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) dst[i] = O[i];
         return;
     }
     // far pairs: tensor-product Lagrange interpolation of this step's node
     // coefficients (field f), contracted over z first
-    const FarTarget &F = *T.far;
-    float *cz = O + nx * ny;                                // [py][px]
-    float *ux = cz + kMaxFarPts * kMaxFarPts;               // [py][nx]
-    const float *c = F.cring + (step % F.depth) * (F.r * 4);
-    const int pxy = F.px * F.py;
+    const float *c = fcring + (step % fdepth) * (fr * 4);
+    for (int i = threadIdx.x; i < fr; i += blockDim.x) sc[i] = c[i * 4 + f];
+    __syncthreads();
+    const int pxy = fpx * fpy;
     for (int i = threadIdx.x; i < pxy; i += blockDim.x) {
         float s = 0.0f;
-        for (int cc = 0; cc < F.pz; ++cc) s = fmaf(F.Lz[z * F.pz + cc], c[(cc * pxy + i) * 4 + f], s);
+        for (int cc = 0; cc < fpz; ++cc) s = fmaf(sLz[cc], sc[cc * pxy + i], s);
         cz[i] = s;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < F.py * nx; i += blockDim.x) {
+    for (int i = threadIdx.x; i < fpy * nx; i += blockDim.x) {
         const int bb = i / nx, x = i % nx;
         float u = 0.0f;
-        for (int aa = 0; aa < F.px; ++aa) u = fmaf(F.Lx[x * F.px + aa], cz[bb * F.px + aa], u);
+        for (int aa = 0; aa < fpx; ++aa) u = fmaf(sLx[x * fpx + aa], cz[bb * fpx + aa], u);
         ux[i] = u;
     }
     __syncthreads();
@@ -699,7 +715,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
     for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
         const int x = i % nx, y = i / nx;
         float v = 0.0f;
-        for (int bb = 0; bb < F.py; ++bb) v = fmaf(__ldg(F.Ly + y * F.py + bb), ux[bb * nx + x], v);
+        for (int bb = 0; bb < fpy; ++bb) v = fmaf(sLy[y * fpy + bb], ux[bb * nx + x], v);
         dst[i] = fmaf(scale, v, O[i]);
     }
 }
@@ -738,9 +754,10 @@ size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay)
 {
     const int kx = ax.M / 2 + 1;
     const int ps = ay.M | 1;
-    // + the far-path coefficients contracted over z, then over x
+    // + the far path: coefficients contracted over z, then over x; the
+    // Lagrange weights per axis; this step's node coefficients
     return sizeof(float2) * ((size_t)ax.M + ay.M + (size_t)kx * ps) + sizeof(float) * (size_t)nx * ny +
-           sizeof(float) * kMaxFarPts * (kMaxFarPts + (size_t)nx);
+           sizeof(float) * kMaxFarPts * (kMaxFarPts + 2 * (size_t)nx + ny + 1 + kMaxFarPts * kMaxFarPts);
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel function,
