@@ -340,3 +340,36 @@ def test_host_path_pipelined_steps(adjacent, push_all):
         for d in range(nd):
             got = np.concatenate([phis[i][d].numpy(), As[i][d].numpy()])
             np.testing.assert_array_equal(got, want[i][d].reshape(-1), err_msg=f"step {i} domain {d}")
+
+
+def test_inputs_and_outputs_next_to_other_kernels():
+    """The per-step kernels start early (programmatic dependent launch) and
+    wait for the previous kernel before touching its data: inputs written by
+    a kernel on the same stream just before each push, and outputs read by a
+    kernel just after each evaluation, give the bits of the plain run."""
+    import torch
+    w = synth.workload("cfg1")
+    T = 12
+    hists = histories(w.sources, 0, T, w.dt)
+    want = run_library(w.domains, w.c, w.dt, hists, 0, range(6, T), push="all")
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    got = {}
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, stream=stream) as lib:
+        host = [torch.from_numpy(np.ascontiguousarray(h)).to(dev) for h in hists]   # [T][4][N]
+        rho = [torch.empty(d.N, device=dev) for d in w.domains]
+        J = [torch.empty(3 * d.N, device=dev) for d in w.domains]
+        for i in range(T):
+            for d in range(len(w.domains)):
+                # a long elementwise kernel writes this step's inputs
+                torch.mul(host[d][i, 0], 1.0, out=rho[d])
+                torch.mul(host[d][i, 1:].reshape(-1), 1.0, out=J[d])
+            lib.push_all(rho, J)
+            if i >= 6:
+                phi, A = lib.evaluate()
+                # kernels read the outputs right away, before any host sync
+                got[i] = [torch.cat([phi[d][None] * 1.0, (A[d] * 1.0).reshape(3, -1)]) for d in range(len(w.domains))]
+        torch.cuda.synchronize()
+        for i in got:
+            for d in range(len(w.domains)):
+                np.testing.assert_array_equal(got[i][d].cpu().numpy(), want[i][d], err_msg=f"step {i} domain {d}")
