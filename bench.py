@@ -51,7 +51,8 @@ def parse():
     p.add_argument("--impl", choices=["ours", "reference"], default="ours")
     p.add_argument("--workload", default="cfg2",
                    help="cfg1 | cfg2 | near48 (48^3 pair 200 bohr apart) | cfg3 | cfg5 | cfg5x8 (first 8 "
-                        "domains of cfg5); cfg3 and cfg5* have thousands-deep histories and run the far path")
+                        "domains of cfg5); cfg3 and cfg5* have thousands-deep histories and run the far path; "
+                        "split: one enclosing domain against two sub-domains over a sweep of sizes (Eq. 13)")
     p.add_argument("--no-plain", action="store_true", help="skip timing the plain direct path")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     p.add_argument("--no-e2e", action="store_true")
@@ -667,11 +668,132 @@ def run_deep(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+SPLIT_SWEEP = [(8, 32, 24), (8, 32, 48), (8, 32, 96), (8, 96, 24), (8, 96, 48), (8, 96, 96),
+               (16, 96, 48), (16, 96, 96)]   # (W', L', d') in nodes, h = 0.25 bohr
+
+
+def eq13_speedup(W, L, d):
+    """Sec. III, Eq. 13: the paper's complexity ratio of one enclosing domain
+    (W' d' L' nodes, N_R from its diagonal) to two W' x W' x L' sub-domains
+    (cross pairs over Delta N_R = diagonal - (d' - 2W'), self terms over the
+    sub-domain's diagonal), each lag costing N log N."""
+    D = math.sqrt(d * d + L * L + W * W)
+    sub = W * W * L * math.log(W * W * L)
+    num = 2 * D * sub - 2 * (d - 2 * W) * sub + 2 * math.sqrt(2 * W * W + L * L) * sub
+    den = D * W * d * L * math.log(W * d * L)
+    return den / num
+
+
+def run_split(args, rank, world, local):
+    """Single enclosing domain against two sub-domains (Sec. III, Eq. 13):
+    measured step times of both layouts on the FFT path, their ratio beside
+    the paper's complexity ratio, both layouts checked against each other and
+    against the FP64 oracle at seeded nodes."""
+    import torch
+    import oracle
+    from paper_2311_15429_gb300 import rp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    h, c, dt = 0.25, synth.C_AU, 0.01
+    K, W = args.steps, max(args.warmup, 3)
+    rows = []
+    rng = np.random.default_rng(5)
+    for (Wn, Ln, dn) in SPLIT_SWEEP:
+        g = synth.split_geometry(Wn, Ln, dn, h)
+        layouts = {"multi": g.subs, "single": [g.enclosing]}
+        libs = {k: rp.RetardedPotentials(v, c, dt, device=local, stream=stream) for k, v in layouts.items()}
+        lags = {k: lib.query()["max_lag"] for k, lib in libs.items()}
+        T = max(lags.values()) + 1 + W
+        hist = [s.history(0, T, dt) for s in g.sources]
+        dev_in = {"multi": [torch.from_numpy(x).to(dev) for x in hist],
+                  "single": [torch.from_numpy(g.embed(hist)).to(dev)]}
+        out = {}
+        for k, lib in libs.items():
+            xs = dev_in[k]
+            for i in range(T):
+                lib.push_all([x[i, 0] for x in xs], [x[i, 1:].reshape(-1) for x in xs])
+                if i >= T - W:
+                    lib.evaluate()
+            lib.sync()
+            out[k] = [torch.cat([lib.phi[d][None], lib.A[d].reshape(3, -1)]).cpu().numpy()
+                      for d in range(len(layouts[k]))]
+        # agreement at the sub-domains' nodes, and the FP64 oracle at seeded nodes
+        agree, err_multi, err_single = 0.0, 0.0, 0.0
+        for k in range(2):
+            a, b = out["single"][0][:, g.sub_nodes(k)], out["multi"][k]
+            agree = max(agree, max(float(np.linalg.norm(a[f] - b[f]) / np.linalg.norm(b[f])) for f in range(4)))
+            nodes = np.sort(rng.choice(g.subs[k].N, 32, replace=False))
+            want = oracle.eval_points([x.origin for x in g.subs], [x.n for x in g.subs], [x.h for x in g.subs],
+                                      hist, 0, c, dt, k, T - 1, nodes)
+            for got, acc in ((b[:, nodes], "m"), (a[:, nodes], "s")):
+                e = max(float(np.linalg.norm(got[f] - want[:, f]) / np.linalg.norm(want[:, f])) for f in range(4))
+                if acc == "m":
+                    err_multi = max(err_multi, e)
+                else:
+                    err_single = max(err_single, e)
+        # timed: K steps each, cycled device inputs (the last W slices)
+        ms = {}
+        for k, lib in libs.items():
+            xs = dev_in[k]
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for i in range(K):
+                j = T - W + i % W
+                lib.push_all([x[j, 0] for x in xs], [x[j, 1:].reshape(-1) for x in xs])
+                lib.evaluate()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms[k] = e0.elapsed_time(e1) / K
+        fft = {k: [tuple(lib.pair_info(t, s)["fft_m"]) for t in range(len(layouts[k])) for s in range(len(layouts[k]))]
+               for k, lib in libs.items()}
+        # this implementation's per-step MAC bytes: per (pair, lag) the kernel
+        # spectrum (real for a self pair) and four field spectra, plus T2
+        mac = {}
+        for k, lib in libs.items():
+            n = len(layouts[k])
+            tot = 0
+            for t in range(n):
+                for s_ in range(n):
+                    p = lib.pair_info(t, s_)
+                    m = p["fft_m"]
+                    cells = (m[0] // 2 + 1) * m[1] * m[2]
+                    tot += (p["lag_hi"] - p["lag_lo"] + 1) * cells * ((4 if s_ == t else 8) + 4 * 8)
+                tm = lib.pair_info(t, t)["fft_m"]
+                tot += 4 * (tm[0] // 2 + 1) * tm[1] * layouts[k][t].n[2] * 8
+            mac[k] = tot
+        for lib in libs.values():
+            lib.close()
+        rows.append({"W": Wn, "L": Ln, "d": dn, "points_multi": 2 * g.subs[0].N, "points_single": g.enclosing.N,
+                     "max_lag_multi": lags["multi"], "max_lag_single": lags["single"],
+                     "fft_m_multi": fft["multi"][0], "fft_m_single": fft["single"][0],
+                     "ms_multi": ms["multi"], "ms_single": ms["single"],
+                     "speedup_measured": ms["single"] / ms["multi"], "speedup_eq13": eq13_speedup(Wn, Ln, dn),
+                     "mac_bytes_multi": mac["multi"], "mac_bytes_single": mac["single"],
+                     "speedup_mac_bytes": mac["single"] / mac["multi"],
+                     "rel_l2_single_vs_multi": agree, "rel_l2_multi_vs_oracle": err_multi,
+                     "rel_l2_single_vs_oracle": err_single})
+    if rank != 0:
+        return
+    line = {"metric": "single-domain / two-sub-domain step time (Sec. III speedup, Eq. 13)", "unit": "ratio",
+            "n_gpus": world, "steps": K, "warmup": W, "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": "split", "h": h, "dt": dt,
+                       "description": "two W' x W' x L' sub-domains with outer faces d' nodes apart on x, against "
+                                      "the d' x W' x L' domain enclosing them (zero sources in the gap); FFT path, "
+                                      "device-resident inputs, CUDA events; oracle: 32 seeded nodes per sub-domain"},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     rank, world, local = dist_init(args)
     if args.impl == "reference":
         run_reference(args, rank, world)
+    elif args.workload == "split":
+        run_split(args, rank, world, local)
     elif args.workload in DEEP:
         run_deep(args, rank, world, local)
     else:

@@ -236,6 +236,51 @@ def two_domain(n: int, h: float, distance: float, name: str = "custom", steps: i
                     f"2 x {n}^3, h={h}, {distance} bohr apart", _sources(doms))
 
 
+@dataclass
+class SplitGeometry:
+    """Two elongated sub-domains of W' x W' x L' nodes whose outer faces are
+    d' nodes apart along x (the gap between them is d' - 2W'), and the single
+    domain of d' x W' x L' nodes that encloses both (Sec. III's comparison of a
+    multi-domain and a single large domain, Eq. 13).  The enclosing domain's
+    nodes include every node of both sub-domains."""
+    W: int
+    L: int
+    d: int
+    h: float
+    subs: List[Domain]
+    enclosing: Domain
+    sources: List[GaussianSources]
+
+    def embed(self, slices: Sequence[np.ndarray]) -> np.ndarray:
+        """The enclosing domain's slice [..., 4, N]: each sub-domain's slice
+        (shape [..., 4, N_sub]) at its own nodes, zero elsewhere."""
+        lead = slices[0].shape[:-2]
+        W, L, d = self.W, self.L, self.d
+        out = np.zeros(lead + (4, L, W, d), dtype=slices[0].dtype)
+        for k, sl in enumerate(slices):
+            x0 = 0 if k == 0 else d - W
+            out[..., x0:x0 + W] = sl.reshape(lead + (4, L, W, W))
+        return out.reshape(lead + (4, L * W * d))
+
+    def sub_nodes(self, k: int) -> np.ndarray:
+        """Node ids, in the enclosing domain, of sub-domain k's nodes (in its
+        own node order)."""
+        W, L, d = self.W, self.L, self.d
+        x0 = 0 if k == 0 else d - W
+        z, y, x = np.meshgrid(np.arange(L), np.arange(W), np.arange(W), indexing="ij")
+        return ((x + x0) + d * (y + W * z)).reshape(-1)
+
+
+def split_geometry(W: int, L: int, d: int, h: float, seed: int = SOURCE_SEED) -> SplitGeometry:
+    """Sub-domains of W x W x L nodes (x, y, z) at x-node offsets 0 and d - W
+    of a d x W x L enclosing domain; three seeded Gaussians in each."""
+    if not 2 * W <= d:
+        raise ValueError("the sub-domains must not overlap: need 2W <= d")
+    subs = [Domain((0.0, 0.0, 0.0), (W, W, L), h), Domain((h * (d - W), 0.0, 0.0), (W, W, L), h)]
+    enclosing = Domain((0.0, 0.0, 0.0), (d, W, L), h)
+    return SplitGeometry(W, L, d, h, subs, enclosing, _sources(subs, seed))
+
+
 def workload(name: str) -> Workload:
     """The named synthetic workload.
 
