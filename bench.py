@@ -425,6 +425,34 @@ def run_ours(args, rank, world, local):
         if k in alg:
             kstats[k]["algorithmic_GBps"] = alg[k] / (kstats[k]["avg_us"] * 1e-6) / 1e9
 
+    # ---- the fields of App. B from the last potentials (rp_fields), timed alone:
+    # per point it reads phi and three A's (10 floats) and writes E and B (6)
+    fields = None
+    if rank == 0:
+        nd = len(w.domains)
+        A1 = [lib.A[d].clone() for d in range(nd)]
+        A2 = [lib.A[d].clone() for d in range(nd)]
+        E = [torch.empty_like(lib.A[d]) for d in range(nd)]
+        B = [torch.empty_like(lib.A[d]) for d in range(nd)]
+        reps = 200
+        for _ in range(3):
+            for d in range(nd):
+                rp.rp_fields(lib.ctx, d, lib.phi[d], lib.A[d], A1[d], A2[d], E[d], B[d])
+        torch.cuda.synchronize()
+        fa, fb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fa.record(stream)
+        for _ in range(reps):
+            for d in range(nd):
+                rp.rp_fields(lib.ctx, d, lib.phi[d], lib.A[d], A1[d], A2[d], E[d], B[d])
+        fb.record(stream)
+        torch.cuda.synchronize()
+        us = 1e3 * fa.elapsed_time(fb) / (reps * nd)
+        fbytes = 64 * w.points / nd
+        fields = {"kernel": "k_fields (E and B, one launch per domain)", "avg_us": us,
+                  "algorithmic_bytes_per_launch": fbytes, "achieved_GBps": fbytes / (us * 1e-6) / 1e9,
+                  "frac_of_peak": fbytes / (us * 1e-6) / 1e9 / peak, "launches": reps * nd,
+                  "note": "timed alone after the step loop, 64 B per point (phi, 3 x A in; E, B out)"}
+
     # ---- plain path: direct FP32 sum of every pair
     plain = None
     if not args.no_plain and rank == 0:
@@ -516,6 +544,7 @@ def run_ours(args, rank, world, local):
         "plain_path": plain,
         "roofline": roof,
         "kernels": kstats,
+        "fields": fields,
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -282,6 +282,22 @@ rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 
 /*
+ * rp_fields -- the fields of App. B (Eqs. B1a, B1b) on domain `id`'s grid from
+ * its potentials as rp_evaluate writes them (atomic units):
+ *     E = -grad phi - (1/c) dA/dt,    B = curl A.
+ * Space derivatives are second-order central differences, second-order
+ * one-sided on the grid faces (each axis needs >= 3 nodes).  The time
+ * derivative is (3 A_l - 4 A_{l-1} + A_{l-2}) / (2 dt), or (A_l - A_{l-1})/dt
+ * when d_A2 is NULL.  Device pointers of domain `id`: d_phi [N] (step l),
+ * d_A, d_A1, d_A2 [3][N] (steps l, l-1, l-2), d_E [3][N], d_B [3][N] or NULL
+ * (not computed); node id = x + nx (y + ny z).  The caller owns every buffer;
+ * nothing is allocated.  On the context stream; after rp_finalize.
+ * RP_ERR_ARG for a bad id, a NULL required pointer or an axis under 3 nodes.
+ */
+rp_status rp_fields(rp_ctx *ctx, int id, const float *d_phi, const float *d_A, const float *d_A1,
+                    const float *d_A2, float *d_E, float *d_B);
+
+/*
  * rp_gemm_bf16 -- D = A B^T on the tensor cores (tcgen05.mma, bf16 operands,
  * fp32 accumulation in tensor memory).  A is M x K and B is N x K, bf16,
  * row-major with K contiguous; D is M x N fp32 row-major.  All three are

@@ -1982,6 +1982,20 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
     return RP_OK;
 }
 
+rp_status rp_fields(rp_ctx *ctx, int id, const float *d_phi, const float *d_A, const float *d_A1,
+                    const float *d_A2, float *d_E, float *d_B)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (id < 0 || id >= (int)ctx->doms.size() || !d_phi || !d_A || !d_A1 || !d_E)
+        return fail(ctx, RP_ERR_ARG, "rp_fields: bad id or NULL pointer");
+    const DomainDesc &D = ctx->doms[id];
+    if (D.n[0] < 3 || D.n[1] < 3 || D.n[2] < 3) return fail(ctx, RP_ERR_ARG, "rp_fields: an axis has fewer than 3 nodes");
+    RP_CUDA(ctx, launch_fields(D.n[0], D.n[1], D.n[2], D.h, ctx->cfg.c, ctx->cfg.dt, d_phi, d_A, d_A1, d_A2, d_E, d_B,
+                               ctx->stream));
+    return RP_OK;
+}
+
 rp_status rp_sync(rp_ctx *ctx)
 {
     if (!ctx) return RP_ERR_ARG;

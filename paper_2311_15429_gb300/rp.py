@@ -87,6 +87,7 @@ SIGNATURES = {
     "rp_evaluate": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
+    "rp_fields": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
     "rp_gemm_bf16": (_I, [_V, _V, _V, _I, _I, _I, _I, _V]),
     "rp_gemm_tn": (_I, [_V, _V, _V, _I, _I, _I, _I, _I, _I, _I, _V]),
     "rp_mlp_layout": (_I, [_V]),
@@ -254,6 +255,13 @@ def rp_evaluate_host_noalloc(ctx, phis: Sequence, As: Sequence):
     pp, _a = _ptr_array(phis)
     pa, _b = _ptr_array(As)
     _check(load().rp_evaluate_host_noalloc(ctx, pp, pa), ctx)
+
+
+def rp_fields(ctx, dom: int, phi, A, A1, A2, E, B=None):
+    """E = -grad phi - (1/c) dA/dt and B = curl A on domain ``dom`` (App. B):
+    device buffers phi [N], A / A1 / A2 [3N] (steps l, l-1, l-2; A2 may be
+    None), E [3N], B [3N] or None."""
+    _check(load().rp_fields(ctx, dom, _ptr(phi), _ptr(A), _ptr(A1), _ptr(A2), _ptr(E), _ptr(B)), ctx)
 
 
 def rp_gemm_bf16(A, B, D, device: int = 0, stream=None):
