@@ -95,6 +95,21 @@ typedef enum {
  * that factors of pairs that move to the network are never made.  Until
  * rp_train_far_model has run, rp_push returns RP_ERR_STATE. */
 #define RP_FLAG_DEFER_FAR 0x8u
+/* The ground-state split of Eqs. 9-12.  The first push of every domain is
+ * its ground state S(0).  When that first round is complete the library
+ * computes the static potential P(0) = sum_m G_m S(0) of every target (the
+ * c -> infinity sum h^3 S(0)/R, since the hat weights of a pair's lags sum to
+ * one; read it with rp_ground_potential) and from then on keeps
+ * Delta S = S - S(0) in its histories, zero before the first push.
+ * rp_evaluate then returns the induced part sum_m G_m Delta S(l-m), so that
+ * P(l) = P(0) + rp_evaluate's output equals the plain sum under
+ * RP_FLAG_GROUND_STATE_CLAMP (implied) up to rounding.  The FP32 rounding of
+ * the history, the per-step sums and the output then scales with |Delta S|
+ * rather than |S|: the induced part keeps its digits when a large static
+ * density carries a small response.  FFT and direct pairs only: rp_finalize
+ * returns RP_ERR_UNSUPPORTED with far pairs.  Costs one elementwise pass per
+ * push. */
+#define RP_FLAG_GROUND_STATE_SPLIT 0x10u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
@@ -243,6 +258,15 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
  * push and RP_FLAG_GROUND_STATE_CLAMP is not set.
  */
 rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
+
+/*
+ * rp_ground_potential -- under RP_FLAG_GROUND_STATE_SPLIT: the static
+ * potential P(0) of the ground state (the first pushed round), Eq. 12's
+ * P~_n(0) summed over sources, into d_phi[n] (N_n floats) and d_A[n]
+ * (3*N_n floats), device memory, written; on the context stream.
+ * RP_ERR_STATE without the flag or before the first round is complete.
+ */
+rp_status rp_ground_potential(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
 
 /*
  * rp_evaluate_host -- rp_evaluate into HOST buffers h_phi[n] (N_n floats) and

@@ -96,6 +96,10 @@ struct rp_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;
     bool plan_only = false, clamp = false, profile = false;
+    // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
+    // and the static potential P(0), [4][N] per domain
+    bool split = false, static_done = false, computing_static = false;
+    std::vector<float *> ground, delta, pstatic;
     bool finalized = false;
     std::vector<DomainDesc> doms;
     std::vector<PairPlan> pairs;   // [t * ndom + s]
@@ -866,7 +870,10 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     if (ctx->cfg.far_batch == 0) ctx->cfg.far_batch = 32;
     if (ctx->cfg.mac_warps) std::fill(std::begin(ctx->mac_cw), std::end(ctx->mac_cw), ctx->cfg.mac_warps);
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
-    ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0;
+    ctx->split = (cfg->flags & RP_FLAG_GROUND_STATE_SPLIT) != 0;
+    // the split's histories are zero before the first push: the clamped reads
+    // of steps before it read the zeroed slot of step 0
+    ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0 || ctx->split;
     ctx->profile = (cfg->flags & RP_FLAG_PROFILE) != 0 && !ctx->plan_only;
     if (!ctx->plan_only) {
         int count = 0;
@@ -1136,7 +1143,8 @@ rp_status rp_finalize(rp_ctx *ctx)
         int nfar = 0;
         for (const PairPlan &p : ctx->pairs) nfar += p.kind == RP_PAIR_LOWRANK;
         if (nfar && ctx->clamp)
-            return fail(ctx, RP_ERR_UNSUPPORTED, "the far path needs a pushed history (no RP_FLAG_GROUND_STATE_CLAMP)");
+            return fail(ctx, RP_ERR_UNSUPPORTED, "the far path needs a pushed history (no RP_FLAG_GROUND_STATE_CLAMP "
+                                                 "or RP_FLAG_GROUND_STATE_SPLIT)");
         if (ctx->plan_only) ctx->npairs_far = nfar;
     }
 
@@ -1166,6 +1174,17 @@ rp_status rp_finalize(rp_ctx *ctx)
         RP_CUDA(ctx, cudaMemset(R.ring, 0, (size_t)R.depth * R.slot_elems * sizeof(float2)));
         if ((st = dev_alloc(ctx, &R.t1, 4ULL * R.kx * R.nz * R.ay.M))) return st;
         R.tw_x = tw[R.ax.M]; R.tw_y = tw[R.ay.M]; R.tw_z = tw[R.az.M];
+    }
+    if (ctx->split) {
+        ctx->ground.assign(nd, nullptr);
+        ctx->delta.assign(nd, nullptr);
+        ctx->pstatic.assign(nd, nullptr);
+        for (int d = 0; d < nd; ++d) {
+            const size_t n4 = 4 * (size_t)ctx->doms[d].N;
+            if ((st = dev_alloc(ctx, &ctx->ground[d], n4)) || (st = dev_alloc(ctx, &ctx->delta[d], n4)) ||
+                (st = dev_alloc(ctx, &ctx->pstatic[d], n4)))
+                return st;
+        }
     }
     for (InvTarget &I : ctx->inv) {
         if ((st = dev_alloc(ctx, &I.t2, 4ULL * I.kx * I.nz * I.ay.M))) return st;
@@ -1422,6 +1441,53 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
 
 extern "C" {
 
+// Ground-state split, at a push of domains [d0, d1): on the first step keep
+// S(0) (pushed as it is, for the static potential); later, push Delta S.
+static rp_status split_inputs(rp_ctx *ctx, int d0, int d1, IoPtrs &in)
+{
+    if (!ctx->split) return RP_OK;
+    for (int d = d0; d < d1; ++d) {
+        const long long N = ctx->doms[d].N;
+        if (ctx->step == 0) {
+            RP_CUDA(ctx, cudaMemcpyAsync(ctx->ground[d], in.rho[d], N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+            RP_CUDA(ctx, cudaMemcpyAsync(ctx->ground[d] + N, in.J[d], 3 * N * sizeof(float),
+                                         cudaMemcpyDeviceToDevice, ctx->stream));
+        } else {
+            RP_CUDA(ctx, launch_ground_delta(in.rho[d], in.J[d], ctx->ground[d], ctx->delta[d], N, ctx->sm_count,
+                                             ctx->stream));
+            in.rho[d] = ctx->delta[d];
+            in.J[d] = ctx->delta[d] + N;
+        }
+    }
+    return RP_OK;
+}
+
+// Ground-state split, after a push: once the first round is complete, the
+// static potential P(0) = sum_m G_m S(0) (a clamped evaluation over the
+// history that holds S(0) alone), then the history of step 0 becomes
+// Delta S(0) = 0.
+static rp_status split_round_done(rp_ctx *ctx)
+{
+    const int nd = (int)ctx->doms.size();
+    if (!ctx->split || ctx->static_done || ctx->step != 0 || ctx->npushed != nd) return RP_OK;
+    std::vector<float *> phi(nd), A(nd);
+    for (int d = 0; d < nd; ++d) {
+        phi[d] = ctx->pstatic[d];
+        A[d] = ctx->pstatic[d] + ctx->doms[d].N;
+    }
+    ctx->computing_static = true;
+    rp_status st = rp_evaluate(ctx, phi.data(), A.data());
+    ctx->computing_static = false;
+    if (st) return st;
+    for (const FwdRing &R : ctx->fwd)
+        RP_CUDA(ctx, cudaMemsetAsync(R.ring, 0, R.slot_elems * sizeof(float2), ctx->stream));   // slot of step 0
+    for (const RawRing &r : ctx->raw)
+        if (r.ring) RP_CUDA(ctx, cudaMemsetAsync(r.ring, 0, 4 * r.n * sizeof(float), ctx->stream));
+    ctx->static_done = true;
+    return RP_OK;
+}
+
 rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J)
 {
     rp_status st = check_ready(ctx);
@@ -1431,7 +1497,9 @@ rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J)
     IoPtrs in{};
     in.rho[id] = d_rho;
     in.J[id] = d_J;
-    return enqueue_push(ctx, id, id + 1, in);
+    if ((st = split_inputs(ctx, id, id + 1, in))) return st;
+    if ((st = enqueue_push(ctx, id, id + 1, in))) return st;
+    return split_round_done(ctx);
 }
 
 rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J)
@@ -1451,7 +1519,10 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     ctx->npushed = nd;
     IoPtrs in{};
     for (int d = 0; d < nd; ++d) { in.rho[d] = d_rho[d]; in.J[d] = d_J[d]; }
-    return enqueue_push(ctx, 0, nd, in);
+    rp_status st2;
+    if ((st2 = split_inputs(ctx, 0, nd, in))) return st2;
+    if ((st2 = enqueue_push(ctx, 0, nd, in))) return st2;
+    return split_round_done(ctx);
 }
 
 // The copy stream, events and staging vectors of the host-buffer calls, on
@@ -1610,6 +1681,26 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
                                       ctx->smem_dir, step, clamp, inv_cdt, inv_c, ctx->stream);
              })))
             return st;
+    }
+    return RP_OK;
+}
+
+rp_status rp_ground_potential(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!d_phi || !d_A) return fail(ctx, RP_ERR_ARG, "rp_ground_potential: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_ground_potential: NULL output buffer");
+    if (!ctx->split) return fail(ctx, RP_ERR_STATE, "rp_ground_potential needs RP_FLAG_GROUND_STATE_SPLIT");
+    if (!ctx->static_done) return fail(ctx, RP_ERR_STATE, "rp_ground_potential before the first round is complete");
+    for (int d = 0; d < nd; ++d) {
+        const long long N = ctx->doms[d].N;
+        RP_CUDA(ctx, cudaMemcpyAsync(d_phi[d], ctx->pstatic[d], N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
+        RP_CUDA(ctx, cudaMemcpyAsync(d_A[d], ctx->pstatic[d] + N, 3 * N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                     ctx->stream));
     }
     return RP_OK;
 }
@@ -2108,6 +2199,7 @@ unsigned long long layout_hash(const rp_ctx *ctx)
     mix(&ctx->cfg.c, sizeof(double));
     mix(&ctx->cfg.dt, sizeof(double));
     mix(&ctx->cfg.mode, sizeof(int));
+    mix(&ctx->split, sizeof(bool));
     for (const FwdRing &R : ctx->fwd) { mix(&R.depth, sizeof(int)); mix(&R.slot_elems, sizeof(long long)); }
     for (const RawRing &r : ctx->raw) { mix(&r.depth, sizeof(int)); mix(&r.n, sizeof(long long)); }
     return h;
@@ -2125,6 +2217,10 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
         if ((st = fn((void *)F.X, (size_t)8 * ctx->cfg.far_batch * F.ks * sizeof(__nv_bfloat16)))) return st;
     for (const FarTarget &F : ctx->far_tgt)
         if ((st = fn((void *)F.cring, (size_t)F.depth * F.r * 4 * sizeof(float)))) return st;
+    for (size_t d = 0; d < ctx->ground.size(); ++d) {
+        const size_t bytes = 4 * (size_t)ctx->doms[d].N * sizeof(float);
+        if ((st = fn((void *)ctx->ground[d], bytes)) || (st = fn((void *)ctx->pstatic[d], bytes))) return st;
+    }
     return RP_OK;
 }
 
@@ -2193,6 +2289,7 @@ rp_status rp_load_state(rp_ctx *ctx, const char *path)
     if (st) return st;
     ctx->step = step;
     ctx->npushed = npushed;
+    ctx->static_done = step > 0 || (step == 0 && npushed == nd);   // P(0) came with the state
     ctx->pushed = pushed;
     return RP_OK;
 }

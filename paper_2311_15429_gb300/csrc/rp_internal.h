@@ -194,6 +194,10 @@ cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair
                           const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
                           float inv_cdt, float inv_c, cudaStream_t s);
 
+// Ground-state split (rp_ground.cu).
+cudaError_t launch_ground_delta(const float *rho, const float *J, const float *ground, float *delta, long long N,
+                                int sms, cudaStream_t s);
+
 // Fields from the potentials (rp_fields.cu).
 cudaError_t launch_fields(int nx, int ny, int nz, double h, double c, double dt, const float *phi, const float *A,
                           const float *A1, const float *A2, float *E, float *B, cudaStream_t s);

@@ -18,6 +18,7 @@ RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_HISTORY, RP_ERR_CUDA, RP_ERR_OOM, \
     RP_ERR_UNSUPPORTED, RP_ERR_TIMEOUT = range(8)
 RP_MODE_FFT, RP_MODE_DIRECT, RP_MODE_LOWRANK = 0, 1, 2
 RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE, RP_FLAG_DEFER_FAR = 0x1, 0x2, 0x4, 0x8
+RP_FLAG_GROUND_STATE_SPLIT = 0x10
 RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
  RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_MOMENTS, RP_K_LEARNED,
@@ -88,6 +89,7 @@ SIGNATURES = {
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
     "rp_fields": (_I, [_V, _I, _V, _V, _V, _V, _V, _V]),
+    "rp_ground_potential": (_I, [_V, _PP, _PP]),
     "rp_gemm_bf16": (_I, [_V, _V, _V, _I, _I, _I, _I, _V]),
     "rp_gemm_tn": (_I, [_V, _V, _V, _I, _I, _I, _I, _I, _I, _I, _V]),
     "rp_mlp_layout": (_I, [_V]),
@@ -255,6 +257,14 @@ def rp_evaluate_host_noalloc(ctx, phis: Sequence, As: Sequence):
     pp, _a = _ptr_array(phis)
     pa, _b = _ptr_array(As)
     _check(load().rp_evaluate_host_noalloc(ctx, pp, pa), ctx)
+
+
+def rp_ground_potential(ctx, phis: Sequence, As: Sequence):
+    """Under RP_FLAG_GROUND_STATE_SPLIT: the static potential P(0) into device
+    buffers phis[n] (N_n floats) and As[n] (3 N_n floats)."""
+    pp, _a = _ptr_array(phis)
+    pa, _b = _ptr_array(As)
+    _check(load().rp_ground_potential(ctx, pp, pa), ctx)
 
 
 def rp_fields(ctx, dom: int, phi, A, A1, A2, E, B=None):

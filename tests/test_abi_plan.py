@@ -197,3 +197,27 @@ def test_config_validation():
         assert e.value.status == rp.RP_ERR_ARG, kw
     for cw in (0, 8, 12, 16):
         rp.rp_destroy(rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_warps=cw))
+
+
+def test_ground_split_refuses_far_pairs():
+    """RP_FLAG_GROUND_STATE_SPLIT works on FFT and direct pairs; a plan with
+    far pairs is refused at rp_finalize."""
+    w = synth.workload("cfg2")
+    ctx = rp.rp_create(w.c, w.dt, mode=rp.RP_MODE_LOWRANK, far_distance=1000.0,
+                       flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_GROUND_STATE_SPLIT)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_finalize(ctx)
+        assert e.value.status == rp.RP_ERR_UNSUPPORTED
+    finally:
+        rp.rp_destroy(ctx)
+    ctx = rp.rp_create(w.c, w.dt, flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_GROUND_STATE_SPLIT)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+    finally:
+        rp.rp_destroy(ctx)
+
