@@ -2,7 +2,9 @@
 oracle with a stored window per source (only the samples a pair reads).
 
 cfg3: 8 x 64^3 sub-domains, h = 0.25, in a 20000 bohr cube (every pair on the
-low-rank path: bf16 hi/lo tcgen05 factors).  cfg5: 32 x 48^3 sub-domains,
+low-rank path: bf16 hi/lo tcgen05 factors).  cfg4x8: the first 8 of cfg4's 64
+sub-domains -- grids of 24^3 to 96^3 nodes, spacings 0.225 to 0.33 bohr --
+every cross pair low-rank (the factors of all 4032 pairs would need terabytes).  cfg5: 32 x 48^3 sub-domains,
 500-50000 bohr apart (every pair a learned candidate; those that pass the
 validation gate run on the network, the rest on the low-rank path).  Only
 domain 0 carries a source, so every other domain's field is the far field
@@ -22,11 +24,19 @@ pytestmark = pytest.mark.gpu
 TOL = 1e-3
 
 
+def workload(name):
+    if name == "cfg4x8":
+        w = synth.workload("cfg4")
+        w.domains, w.sources = w.domains[:8], w.sources[:8]
+        return w
+    return synth.workload(name)
+
+
 def far_only_errors(name, targets, nodes_per, train=False, far_points=0, **train_kw):
     """Per-target [4] rel-L2 of the far field of domain 0 alone, the training
     report (or None) and the context's query after the run."""
     import torch
-    w = synth.workload(name)
+    w = workload(name)
     dev = torch.device("cuda", 0)
     gen = synth.DeviceSlices(w.sources[:1], dev)
     flags = rp.RP_FLAG_DEFER_FAR if train else 0
@@ -76,3 +86,14 @@ def test_cfg5_learned_far_field():
     assert q["npairs_learned"] == rep["learned"] and rep["learned"] > 0, rep
     for t, e in errs.items():
         assert max(e) <= TOL, ("cfg5", t, e)
+
+
+def test_cfg4_subset_mixed_sizes_and_spacings():
+    """Far field of a 64^3, h = 0.33 source on 48^3, 24^3 and 96^3 targets of
+    other spacings (0.225-0.30 bohr): the factors' nodes live on each target's
+    own grid and the source sum uses the source's h^3."""
+    errs, _, q = far_only_errors("cfg4x8", [1, 3, 5, 7], 96)
+    assert q["npairs_far"] == 56 and q["npairs_fft"] == 8
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg4x8", t, e)
+

@@ -79,6 +79,7 @@ def test_split_keeps_the_digits_of_a_small_response():
         err_split = max(err_split, max(rel_l2(split[T - 1][0][t].astype(np.float64), ref)))
         got = plain[T - 1][t].astype(np.float64) - plain[0][t].astype(np.float64)
         err_plain = max(err_plain, max(rel_l2(got, ref)))
+    print("induced-part rel-L2: split %.2e, plain %.2e" % (err_split, err_plain))
     assert err_split <= 2e-6, (err_split, err_plain)
     assert err_plain >= 20 * err_split, (err_split, err_plain)
 
