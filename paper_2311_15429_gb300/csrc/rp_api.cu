@@ -188,7 +188,8 @@ struct rp_ctx {
     cudaStream_t copy_out = nullptr;           // device-to-host copies (apart, so that a step's
                                                // inputs never queue behind the last step's results)
     cudaEvent_t in_ready = nullptr;            // the last host push's copy is done
-    std::vector<cudaEvent_t> in_free[2];       // per domain: the push that read in_stage[b][d] has run
+    cudaEvent_t in_free[2] = {nullptr, nullptr};    // the last push that read in_stage[b] has run
+                                                    // (pushes run in order on the context stream)
     cudaEvent_t out_ready = nullptr;           // the last host evaluation's results are staged
     cudaEvent_t out_free[2] = {nullptr, nullptr};   // the copy out of out_stage[b] is done
 
@@ -1531,11 +1532,11 @@ static rp_status open_host_copies(rp_ctx *ctx)
 {
     if (ctx->copy_in) return RP_OK;
     const int nd = (int)ctx->doms.size();
-    cudaStream_t a = nullptr, b = nullptr;
-    RP_CUDA(ctx, cudaStreamCreateWithFlags(&a, cudaStreamNonBlocking));
-    ctx->copy_in = a;
-    RP_CUDA(ctx, cudaStreamCreateWithFlags(&b, cudaStreamNonBlocking));
-    ctx->copy_out = b;
+    cudaStream_t s_in = nullptr, s_out = nullptr;
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&s_in, cudaStreamNonBlocking));
+    ctx->copy_in = s_in;
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&s_out, cudaStreamNonBlocking));
+    ctx->copy_out = s_out;
     auto event = [&](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
     RP_CUDA(ctx, event(&ctx->in_ready));
     RP_CUDA(ctx, event(&ctx->out_ready));
@@ -1543,21 +1544,20 @@ static rp_status open_host_copies(rp_ctx *ctx)
         RP_CUDA(ctx, event(&ctx->out_free[b]));
         ctx->in_stage[b].assign(nd, nullptr);
         ctx->out_stage[b].assign(nd, nullptr);
-        ctx->in_free[b].assign(nd, nullptr);
-        for (int d = 0; d < nd; ++d) RP_CUDA(ctx, event(&ctx->in_free[b][d]));
+        RP_CUDA(ctx, event(&ctx->in_free[b]));
     }
     return RP_OK;
 }
 
 // Copies domain id's host inputs of step parity b into its device staging on
-// the copy stream, after the push two steps back that read that staging.
+// the copy stream (the caller has made the stream wait for the last push that
+// read that staging).
 static rp_status stage_host_input(rp_ctx *ctx, int id, int b, const float *h_rho, const float *h_J)
 {
     rp_status st;
     const long long N = ctx->doms[id].N;
     if (!ctx->in_stage[b][id] && (st = dev_alloc(ctx, &ctx->in_stage[b][id], 4 * (size_t)N))) return st;
     float *dst = ctx->in_stage[b][id];
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b][id], 0));
     if (h_J == h_rho + N) {
         RP_CUDA(ctx, cudaMemcpyAsync(dst, h_rho, 4 * N * sizeof(float), cudaMemcpyHostToDevice, ctx->copy_in));
     } else {
@@ -1577,12 +1577,13 @@ rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J
     // the step this push belongs to (a complete round starts the next one)
     const long long step = (ctx->step < 0 || ctx->npushed == nd) ? ctx->step + 1 : ctx->step;
     const int b = (int)(step & 1);
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b], 0));
     if ((st = stage_host_input(ctx, id, b, h_rho, h_J))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
     float *dst = ctx->in_stage[b][id];
     if ((st = rp_push(ctx, id, dst, dst + ctx->doms[id].N))) return st;
-    RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b][id], ctx->stream));
+    RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->stream));
     return RP_OK;
 }
 
@@ -1598,6 +1599,7 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
         return fail(ctx, RP_ERR_STATE, "rp_push_all_host inside a partially pushed step");
     if ((st = open_host_copies(ctx))) return st;
     const int b = (int)((ctx->step + 1) & 1);
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b], 0));   // the push two steps back
     for (int d = 0; d < nd; ++d)
         if ((st = stage_host_input(ctx, d, b, h_rho[d], h_J[d]))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
@@ -1608,8 +1610,7 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
         J[d] = ctx->in_stage[b][d] + ctx->doms[d].N;
     }
     if ((st = rp_push_all(ctx, rho.data(), J.data()))) return st;
-    // one event would do for all domains; the per-domain ones keep rp_push_host's bookkeeping
-    for (int d = 0; d < nd; ++d) RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b][d], ctx->stream));
+    RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->stream));
     return RP_OK;
 }
 
@@ -2305,11 +2306,9 @@ void rp_destroy(rp_ctx *ctx)
         if (ctx->copy_in) {
             cudaStreamSynchronize(ctx->copy_in);
             cudaStreamSynchronize(ctx->copy_out);
-            for (cudaEvent_t e : {ctx->in_ready, ctx->out_ready, ctx->out_free[0], ctx->out_free[1]})
+            for (cudaEvent_t e : {ctx->in_ready, ctx->out_ready, ctx->out_free[0], ctx->out_free[1], ctx->in_free[0],
+                                  ctx->in_free[1]})
                 if (e) cudaEventDestroy(e);
-            for (int b = 0; b < 2; ++b)
-                for (cudaEvent_t e : ctx->in_free[b])
-                    if (e) cudaEventDestroy(e);
             cudaStreamDestroy(ctx->copy_in);
             cudaStreamDestroy(ctx->copy_out);
         }
