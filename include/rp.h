@@ -528,6 +528,17 @@ rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *to
  */
 rp_status rp_kernel_count(rp_ctx *ctx, int kind, long long *launches);
 
+/*
+ * rp_selftest_wait -- a library self-test, no counterpart in the paper.  One
+ * block waits, through the same bounded mbarrier wait as the spectral MAC's
+ * pipeline, on a barrier that nothing arrives on, for at most limit_cycles
+ * SM clock cycles (1 .. 4e9; about 1 ms is 2e6 at 2 GHz).  The wait runs out,
+ * sets the context's device error flag and the block exits: nothing faults
+ * or hangs, and the next rp_sync returns RP_ERR_TIMEOUT and clears the flag,
+ * leaving the context usable.  RP_ERR_ARG for a limit out of range.
+ */
+rp_status rp_selftest_wait(rp_ctx *ctx, long long limit_cycles);
+
 /* rp_kernel_name -- short name of a kernel class (NULL if out of range). */
 const char *rp_kernel_name(int kind);
 

@@ -2088,6 +2088,15 @@ rp_status rp_fields(rp_ctx *ctx, int id, const float *d_phi, const float *d_A, c
     return RP_OK;
 }
 
+rp_status rp_selftest_wait(rp_ctx *ctx, long long limit_cycles)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    if (limit_cycles < 1 || limit_cycles > 4000000000LL) return fail(ctx, RP_ERR_ARG, "rp_selftest_wait: limit out of range");
+    RP_CUDA(ctx, launch_wait_selftest(limit_cycles, ctx->d_err, ctx->stream));
+    return RP_OK;
+}
+
 rp_status rp_sync(rp_ctx *ctx)
 {
     if (!ctx) return RP_ERR_ARG;

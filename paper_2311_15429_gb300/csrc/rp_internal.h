@@ -204,6 +204,7 @@ cudaError_t launch_fields(int nx, int ny, int nz, double h, double c, double dt,
 
 // TMA-fed MAC (rp_mac_tma.cu): cubic classes 32..192 only.
 int mac_tma_stages(int M, int smem_optin);
+cudaError_t launch_wait_selftest(long long limit_cycles, int *d_err, cudaStream_t s);
 size_t mac_tma_smem(int M, int nstages);
 cudaError_t open_mac_tma_smem_limit(int max_optin);
 cudaError_t launch_mac_tma(int cls, int consumer_warps, const InvTarget *d_tgts, int t0, int t1, int tile_lo,

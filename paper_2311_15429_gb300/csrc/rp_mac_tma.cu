@@ -76,13 +76,27 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t parity)
 }
 
 // Wait for the phase of `parity` to complete; false after kWaitLimit cycles.
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity)
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, long long limit = kWaitLimit)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > kWaitLimit) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
+}
+
+// Self-test of the bounded wait: one mbarrier that nothing arrives on, waited
+// through mbar_wait with a short limit; it runs out, raises the error flag
+// and the block exits.
+__global__ void k_wait_selftest(long long limit, int *err)
+{
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && !mbar_wait(&bar, 0, limit)) atomicExch(err, 1);
 }
 
 // Contiguous copy of `bytes` (multiple of 16, both addresses 16-byte aligned)
@@ -449,6 +463,12 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
 #define RP_TMA_CLASSES(X) X(32, 4) X(48, 4) X(64, 4) X(96, 4) X(128, 2) X(192, 1)
 
 }  // namespace
+
+cudaError_t launch_wait_selftest(long long limit_cycles, int *d_err, cudaStream_t s)
+{
+    k_wait_selftest<<<1, 32, 0, s>>>(limit_cycles, d_err);
+    return cudaGetLastError();
+}
 
 int mac_tma_fields_per_copy(int M) { return M <= 96 ? 4 : (M == 128 ? 2 : 1); }
 

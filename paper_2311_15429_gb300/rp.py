@@ -105,6 +105,7 @@ SIGNATURES = {
     "rp_kernel_stats": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double), _I]),
     "rp_kernel_count": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong)]),
+    "rp_selftest_wait": (_I, [_V, ctypes.c_longlong]),
     "rp_kernel_name": (ctypes.c_char_p, [_I]),
     "rp_save_state": (_I, [_V, ctypes.c_char_p]),
     "rp_load_state": (_I, [_V, ctypes.c_char_p]),
@@ -396,6 +397,10 @@ def rp_kernel_stats(ctx, kind: int, reset: bool = False):
     ms = ctypes.c_double()
     _check(load().rp_kernel_stats(ctx, kind, ctypes.byref(n), ctypes.byref(ms), int(reset)), ctx)
     return n.value, ms.value
+
+
+def rp_selftest_wait(ctx, limit_cycles: int):
+    _check(load().rp_selftest_wait(ctx, int(limit_cycles)), ctx)
 
 
 def rp_kernel_count(ctx, kind: int) -> int:

@@ -373,3 +373,33 @@ def test_inputs_and_outputs_next_to_other_kernels():
         for i in got:
             for d in range(len(w.domains)):
                 np.testing.assert_array_equal(got[i][d].cpu().numpy(), want[i][d], err_msg=f"step {i} domain {d}")
+
+
+def test_bounded_wait_runs_out_and_the_context_stays_usable():
+    """A device wait that nothing satisfies (rp_selftest_wait, through the
+    MAC pipeline's bounded mbarrier wait, ~1 ms limit) ends by itself: rp_sync
+    reports RP_ERR_TIMEOUT once, clears it, and the next steps still match the
+    plain run bit for bit."""
+    import torch
+    dev = torch.device("cuda", 0)
+    w = synth.workload("cfg1")
+    T = 10
+    hists = histories(w.sources, 0, T, w.dt)
+    want = run_library(w.domains, w.c, w.dt, hists, 0, [T - 1])
+    with rp.RetardedPotentials(w.domains, w.c, w.dt) as lib:
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_selftest_wait(lib.ctx, 0)
+        assert e.value.status == rp.RP_ERR_ARG
+        rp.rp_selftest_wait(lib.ctx, 2_000_000)
+        with pytest.raises(rp.RPError) as e:
+            lib.sync()
+        assert e.value.status == rp.RP_ERR_TIMEOUT
+        lib.sync()                                   # the flag was cleared
+        for i in range(T):
+            lib.push_all([torch.from_numpy(np.ascontiguousarray(h[i, 0])).to(dev) for h in hists],
+                         [torch.from_numpy(np.ascontiguousarray(h[i, 1:]).reshape(-1)).to(dev) for h in hists])
+        phi, A = lib.evaluate()
+        lib.sync()
+        for d in range(2):
+            got = np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)])
+            np.testing.assert_array_equal(got, want[T - 1][d])
