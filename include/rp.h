@@ -260,6 +260,31 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
 rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
 
 /*
+ * rp_graph_capture -- record one whole step (rp_push_all of d_rho / d_J, then
+ * rp_evaluate into d_phi / d_A; arrays of device pointers, one per domain, as
+ * for those calls) as a CUDA graph, without running it (the recording uses a
+ * stream of its own; the replays run on the context stream).
+ * The buffers are fixed: each rp_graph_step replays the step on their current
+ * contents.  Call at a step boundary.  FFT and direct pairs only, without
+ * RP_FLAG_PROFILE or RP_FLAG_GROUND_STATE_SPLIT (RP_ERR_UNSUPPORTED
+ * otherwise): the far path's launches change from step to step.  A new
+ * capture replaces the previous graph.  (No counterpart in the paper: a
+ * property of the library.)
+ */
+rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J,
+                           float *const *d_phi, float *const *d_A);
+
+/*
+ * rp_graph_step -- the next step by one replay of the captured graph: the
+ * same result as rp_push_all + rp_evaluate on the captured buffers, with one
+ * launch from the host.  Steps made by the other calls in between are allowed
+ * (the device step counter is re-synchronised, which waits for the stream).
+ * RP_ERR_STATE without a graph or inside a partially pushed step,
+ * RP_ERR_HISTORY as for rp_evaluate.
+ */
+rp_status rp_graph_step(rp_ctx *ctx);
+
+/*
  * rp_ground_potential -- under RP_FLAG_GROUND_STATE_SPLIT: the static
  * potential P(0) of the ground state (the first pushed round), Eq. 12's
  * P~_n(0) summed over sources, into d_phi[n] (N_n floats) and d_A[n]

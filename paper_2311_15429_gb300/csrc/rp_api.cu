@@ -99,6 +99,16 @@ struct rp_ctx {
     // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
     // and the static potential P(0), [4][N] per domain
     bool split = false, static_done = false, computing_static = false;
+    // graph replay of a step (rp_graph_capture / rp_graph_step): the step as
+    // the step-dependent kernels read it on replay, and the captured graph
+    long long *d_step = nullptr;
+    long long *h_step_pin = nullptr;          // pinned source of the counter's re-sync
+    cudaStream_t capture_stream = nullptr;    // the recording's own stream (the context stream may be
+                                              // the legacy default stream, which cannot be captured)
+    bool capturing = false;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    long long graph_synced = -2;              // host step the device counter holds (-2: unknown)
     std::vector<float *> ground, delta, pstatic;
     bool finalized = false;
     std::vector<DomainDesc> doms;
@@ -1276,6 +1286,12 @@ rp_status rp_finalize(rp_ctx *ctx)
     if (!(ctx->cfg.flags & RP_FLAG_DEFER_FAR) && (st = build_far(ctx, max_optin))) return st;
 
     // ---- device tables and kernel limits
+    if ((st = dev_alloc(ctx, &ctx->d_step, 1))) return st;
+    RP_CUDA(ctx, cudaMemset(ctx->d_step, 0, sizeof(long long)));
+    for (FwdRing &R : ctx->fwd) R.d_step = ctx->d_step;
+    for (InvTarget &I : ctx->inv) I.d_step = ctx->d_step;
+    for (DirectTarget &D : ctx->dtg) D.d_step = ctx->d_step;
+    for (RawRing &r : ctx->raw) r.d_step = ctx->d_step;
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
     if ((st = upload(ctx, &ctx->d_inv, ctx->inv))) return st;
     if ((st = upload(ctx, &ctx->d_entries, ctx->entries))) return st;
@@ -1326,13 +1342,14 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
 {
     rp_status st;
     const long long step = ctx->step;
+    const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
     // raw ring
     int blk = ctx->raw_block0[d1] - ctx->raw_block0[d0];
     if (blk > 0) {
         std::vector<int> b0(kMaxDomains + 1, 0);
         for (int d = d0; d <= d1; ++d) b0[d] = ctx->raw_block0[d] - ctx->raw_block0[d0];
         if ((st = timed_launch(ctx, RP_K_RING_PUSH, "ring push", [&] {
-                 return launch_ring_push(ctx->d_raw, in, d0, d1, b0.data(), blk, step, ctx->stream);
+                 return launch_ring_push(ctx->d_raw, in, d0, d1, b0.data(), blk, kstep, ctx->stream);
              })))
             return st;
     }
@@ -1361,7 +1378,7 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_COLUMN, "forward column pass", [&] {
                  return launch_fwd_column(g.cls, ctx->d_fwd, g.i0, g.i1, g.blk2_0, g.blk2_1 - g.blk2_0,
-                                          ctx->smem_col, step, ctx->stream);
+                                          ctx->smem_col, kstep, ctx->stream);
              })))
             return st;
     }
@@ -1623,12 +1640,13 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     for (int d = 0; d < nd; ++d)
         if (!d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_evaluate: NULL output buffer");
     if (ctx->step < 0 || ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_evaluate before every domain pushed the step");
-    if (!ctx->clamp && ctx->step - ctx->max_lag < 0)
+    if (!ctx->clamp && !ctx->capturing && ctx->step - ctx->max_lag < 0)
         return fail(ctx, RP_ERR_HISTORY, "step " + std::to_string(ctx->step) + " needs samples " +
                                              std::to_string(ctx->max_lag) + " steps back");
     OutPtrs out{};
     for (int d = 0; d < nd; ++d) { out.phi[d] = d_phi[d]; out.A[d] = d_A[d]; }
     const long long step = ctx->step;
+    const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
     const int clamp = ctx->clamp ? 1 : 0;
     const float inv_c = (float)(1.0 / ctx->cfg.c);
     for (const LaunchGroup &g : ctx->inv_groups) {
@@ -1636,11 +1654,11 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
                  if (ctx->tma && g.cls > 0)
                      return launch_mac_tma(g.cls, ctx->mac_cw[class_slot(g.cls)], ctx->d_inv, g.i0, g.i1, g.blk0,
-                                           ntiles, ctx->d_entries, step, clamp,
+                                           ntiles, ctx->d_entries, kstep, clamp,
                                            ctx->mac_stages[class_slot(g.cls)],
                                            std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
                  return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,
-                                              ctx->smem_mac, step, clamp, ctx->stream);
+                                              ctx->smem_mac, kstep, clamp, ctx->stream);
              })))
             return st;
     }
@@ -1664,7 +1682,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     for (const LaunchGroup &g : ctx->inv_groups) {
         if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
                  return launch_inv_plane(g.cls, ctx->d_inv, g.i0, g.i1, g.blk2_0, out, g.blk2_1 - g.blk2_0,
-                                         ctx->smem_inv, inv_c, step, ctx->stream);
+                                         ctx->smem_inv, inv_c, kstep, ctx->stream);
              })))
             return st;
     }
@@ -1679,7 +1697,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         const float inv_cdt = (float)(1.0 / (ctx->cfg.c * ctx->cfg.dt));
         if ((st = timed_launch(ctx, RP_K_DIRECT, "direct sum", [&] {
                  return launch_direct(ctx->d_dtg, (int)ctx->dtg.size(), ctx->d_dpairs, out, ctx->dir_blocks,
-                                      ctx->smem_dir, step, clamp, inv_cdt, inv_c, ctx->stream);
+                                      ctx->smem_dir, kstep, clamp, inv_cdt, inv_c, ctx->stream);
              })))
             return st;
     }
@@ -2088,6 +2106,78 @@ rp_status rp_fields(rp_ctx *ctx, int id, const float *d_phi, const float *d_A, c
     return RP_OK;
 }
 
+rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J,
+                           float *const *d_phi, float *const *d_A)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!d_rho || !d_J || !d_phi || !d_A) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL pointer array");
+    for (int d = 0; d < nd; ++d)
+        if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
+    if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || !ctx->lpairs.empty() ||
+        (ctx->cfg.flags & RP_FLAG_DEFER_FAR))
+        return fail(ctx, RP_ERR_UNSUPPORTED, "rp_graph_capture: FFT and direct pairs only, without profiling or split");
+    if (ctx->step >= 0 && ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_graph_capture inside a partially pushed step");
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    if (!ctx->h_step_pin) RP_CUDA(ctx, cudaHostAlloc(&ctx->h_step_pin, sizeof(long long), cudaHostAllocDefault));
+    // record with the host state of a step; the replays keep it themselves
+    const long long step0 = ctx->step;
+    const int npushed0 = ctx->npushed;
+    const std::vector<char> pushed0 = ctx->pushed;
+    if (!ctx->capture_stream) RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking));
+    cudaStream_t user_stream = ctx->stream;
+    RP_CUDA(ctx, cudaStreamBeginCapture(ctx->capture_stream, cudaStreamCaptureModeThreadLocal));
+    ctx->stream = ctx->capture_stream;   // every launch of the step goes into the recording
+    ctx->capturing = true;
+    cudaError_t e = launch_step_advance(ctx->d_step, ctx->stream);
+    if (!e && !(st = rp_push_all(ctx, d_rho, d_J))) st = rp_evaluate(ctx, d_phi, d_A);
+    ctx->capturing = false;
+    ctx->stream = user_stream;
+    cudaGraph_t g = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(ctx->capture_stream, &g);
+    ctx->step = step0;
+    ctx->npushed = npushed0;
+    ctx->pushed = pushed0;
+    if (e || st || e2 || !g) {
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        if (st) return st;
+        return cuda_fail(ctx, e ? e : (e2 ? e2 : cudaErrorStreamCaptureInvalidated), "graph capture");
+    }
+    ctx->graph = g;
+    RP_CUDA(ctx, cudaGraphInstantiate(&ctx->graph_exec, g, 0));
+    ctx->graph_synced = -2;   // the first replay sets the device counter
+    return RP_OK;
+}
+
+rp_status rp_graph_step(rp_ctx *ctx)
+{
+    rp_status st = check_ready(ctx);
+    if (st) return st;
+    const int nd = (int)ctx->doms.size();
+    if (!ctx->graph_exec) return fail(ctx, RP_ERR_STATE, "rp_graph_step before rp_graph_capture");
+    if (ctx->step >= 0 && ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_graph_step inside a partially pushed step");
+    const long long next = ctx->step + 1;
+    if (!ctx->clamp && next - ctx->max_lag < 0)
+        return fail(ctx, RP_ERR_HISTORY, "step " + std::to_string(next) + " needs samples " +
+                                             std::to_string(ctx->max_lag) + " steps back");
+    if (ctx->graph_synced != ctx->step) {
+        // the counter holds the step of the last replay: set it to this one
+        RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+        *ctx->h_step_pin = ctx->step;
+        RP_CUDA(ctx, cudaMemcpyAsync(ctx->d_step, ctx->h_step_pin, sizeof(long long), cudaMemcpyHostToDevice,
+                                     ctx->stream));
+    }
+    RP_CUDA(ctx, cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->step = next;
+    ctx->npushed = nd;
+    std::fill(ctx->pushed.begin(), ctx->pushed.end(), 1);
+    ctx->graph_synced = next;
+    return RP_OK;
+}
+
 rp_status rp_selftest_wait(rp_ctx *ctx, long long limit_cycles)
 {
     rp_status st = check_ready(ctx);
@@ -2312,6 +2402,10 @@ void rp_destroy(rp_ctx *ctx)
         cudaGetDevice(&cur);
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+        if (ctx->graph) cudaGraphDestroy(ctx->graph);
+        if (ctx->h_step_pin) cudaFreeHost(ctx->h_step_pin);
+        if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
         if (ctx->copy_in) {
             cudaStreamSynchronize(ctx->copy_in);
             cudaStreamSynchronize(ctx->copy_out);

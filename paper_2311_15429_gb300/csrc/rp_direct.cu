@@ -40,6 +40,7 @@ __global__ void __launch_bounds__(kDirThreads) k_direct(const DirectTarget *__re
         if (tgts[mid].block0 <= b) lo = mid; else hi = mid;
     }
     const DirectTarget T = tgts[lo];
+    if (step < 0) step = *T.d_step;   // graph replay: the step from the device counter
     const long long k = (long long)(b - T.block0) * kDirThreads + threadIdx.x;
     const bool valid = k < T.n;
     const int ix = (int)(k % T.nx), iy = (int)((k / T.nx) % T.ny), iz = (int)(k / ((long long)T.nx * T.ny));

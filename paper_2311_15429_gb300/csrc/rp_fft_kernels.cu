@@ -88,6 +88,7 @@ __global__ void __launch_bounds__(kThreads) k_ring_push(const RawRing *__restric
     const int d = lo;
     const RawRing rr = rings[d];
     if (rr.ring == nullptr) return;
+    if (step < 0) step = *rr.d_step;   // graph replay: the step from the device counter
     const long long n = rr.n;
     float *dst = rr.ring + (long long)(step % rr.depth) * 4 * n;
     const long long chunk = (long long)kThreads * 8;
@@ -310,6 +311,7 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
     load_twiddles(tw, R.tw_z, mz);
     pdl_trigger();
     pdl_wait();   // t1 is written by the plane pass
+    if (step < 0) step = *R.d_step;   // graph replay: the step from the device counter
     const long long t1_field = (long long)kx * nz * my;
     const float2 *src = R.t1 + (long long)kxi * nz * my + ky0;
     if constexpr (M > 0) {
@@ -390,6 +392,7 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     load_twiddles(tw, T.tw_z, mz);
     pdl_trigger();
     pdl_wait();   // the newest ring slot is written by the column pass
+    if (step < 0) step = *T.d_step;   // graph replay: the step from the device counter
 
     if constexpr (M > 0) {
         // Thread (p, r0) owns ky columns 2p, 2p+1 and kz rows r0 + 32 i.  All
@@ -661,6 +664,7 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
     }
     pdl_trigger();
     pdl_wait();   // T2 is written by the MAC, the coefficient ring by the far scatter or the learned field
+    if (step < 0) step = *T.d_step;   // graph replay: the step from the device counter
     const float2 *src = T.t2 + ((long long)f * kx * nz + z) * my;
     const long long row_stride = (long long)nz * my;
     if constexpr (M > 0) {

@@ -1,8 +1,11 @@
-// The ground-state split of Eqs. 9-12: with the first sample S(0) taken as
-// the ground state, the histories hold Delta S = S - S(0).
+// Small elementwise kernels of the step bookkeeping.
 //
-//   k_ground_delta: Delta S of one domain's pushed slice (rho and J at their
-//                   own pointers) into the library's [4][N] scratch.
+//   k_ground_delta: the ground-state split of Eqs. 9-12 -- with the first
+//                   sample S(0) taken as the ground state, the histories hold
+//                   Delta S = S - S(0): Delta S of one domain's pushed slice
+//                   (rho and J at their own pointers) into the library's
+//                   [4][N] scratch;
+//   k_step_advance: graph replay -- the device step counter, +1 per replay.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,7 +35,16 @@ int grid_for(long long n, int sms)
                                                            8LL * std::max(sms, 1)));
 }
 
+// Graph replay: the step the replayed kernels read.
+__global__ void k_step_advance(long long *d_step) { *d_step += 1; }
+
 }  // namespace
+
+cudaError_t launch_step_advance(long long *d_step, cudaStream_t s)
+{
+    k_step_advance<<<1, 1, 0, s>>>(d_step);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_ground_delta(const float *rho, const float *J, const float *ground, float *delta, long long N,
                                 int sms, cudaStream_t s)

@@ -51,6 +51,7 @@ struct FwdRing {
     __nv_bfloat16 *far_x;    // far-path batch matrix [4 batch][2 ks] of this source (one ring per source), or null
     int far_ks;              // its half row width
     int pad_;
+    const long long *d_step; // the step, for launches made with step < 0 (graph replay)
 };
 
 // One (source, lag) term of a target's spectral sum: G_m (kernel spectrum of
@@ -80,6 +81,7 @@ struct InvTarget {
     int has_direct;          // direct pairs add onto this target afterwards
     int pad_;
     const FarTarget *far;    // far-path coefficients interpolated onto this target here, or null
+    const long long *d_step; // the step, for launches made with step < 0 (graph replay)
 };
 
 // A (target, source) pair evaluated by the direct retarded sum.
@@ -107,6 +109,7 @@ struct DirectTarget {
     int p0, p1;              // DirectPair range
     int block0;              // first block in the direct grid
     int accumulate;          // add onto the output (FFT pairs wrote it) instead of writing
+    const long long *d_step; // the step, for launches made with step < 0 (graph replay)
 };
 
 // A raw history ring (rho, Jx, Jy, Jz per slot).
@@ -115,6 +118,7 @@ struct RawRing {
     long long n;
     int depth;
     int pad_;
+    const long long *d_step; // the step, for launches made with step < 0 (graph replay)
 };
 
 // ---- far pairs (rp_far.cu): interpolative low-rank factors
@@ -194,7 +198,8 @@ cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair
                           const OutPtrs &out, int nblocks, size_t smem, long long step, int clamp,
                           float inv_cdt, float inv_c, cudaStream_t s);
 
-// Ground-state split (rp_ground.cu).
+// Ground-state split and graph-replay step counter (rp_ground.cu).
+cudaError_t launch_step_advance(long long *d_step, cudaStream_t s);
 cudaError_t launch_ground_delta(const float *rho, const float *J, const float *ground, float *delta, long long N,
                                 int sms, cudaStream_t s);
 

@@ -239,6 +239,7 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
     load_twiddles(tw, tgts[t0].tw_z, M);
     pdl_trigger();
     pdl_wait();   // the newest ring slot is written by the column pass; T2 was read by the last plane pass
+    if (step < 0) step = *tgts[t0].d_step;   // graph replay: the step from the device counter
     __syncthreads();
 
     // wait for a phase; false (and the error raised) on abort/timeout

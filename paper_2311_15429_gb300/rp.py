@@ -106,6 +106,8 @@ SIGNATURES = {
                              ctypes.POINTER(ctypes.c_double), _I]),
     "rp_kernel_count": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "rp_selftest_wait": (_I, [_V, ctypes.c_longlong]),
+    "rp_graph_capture": (_I, [_V, _PP, _PP, _PP, _PP]),
+    "rp_graph_step": (_I, [_V]),
     "rp_kernel_name": (ctypes.c_char_p, [_I]),
     "rp_save_state": (_I, [_V, ctypes.c_char_p]),
     "rp_load_state": (_I, [_V, ctypes.c_char_p]),
@@ -397,6 +399,19 @@ def rp_kernel_stats(ctx, kind: int, reset: bool = False):
     ms = ctypes.c_double()
     _check(load().rp_kernel_stats(ctx, kind, ctypes.byref(n), ctypes.byref(ms), int(reset)), ctx)
     return n.value, ms.value
+
+
+def rp_graph_capture(ctx, rhos: Sequence, Js: Sequence, phis: Sequence, As: Sequence):
+    """Record push_all + evaluate on these device buffers as a CUDA graph."""
+    a, _a = _ptr_array(rhos)
+    b, _b = _ptr_array(Js)
+    c, _c = _ptr_array(phis)
+    d, _d = _ptr_array(As)
+    _check(load().rp_graph_capture(ctx, a, b, c, d), ctx)
+
+
+def rp_graph_step(ctx):
+    _check(load().rp_graph_step(ctx), ctx)
 
 
 def rp_selftest_wait(ctx, limit_cycles: int):

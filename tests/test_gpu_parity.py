@@ -403,3 +403,56 @@ def test_bounded_wait_runs_out_and_the_context_stays_usable():
         for d in range(2):
             got = np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)])
             np.testing.assert_array_equal(got, want[T - 1][d])
+
+
+@pytest.mark.parametrize("mode", [rp.RP_MODE_FFT, rp.RP_MODE_DIRECT])
+def test_graph_replay_matches_the_calls(mode):
+    """rp_graph_capture records push_all + evaluate on fixed buffers; each
+    rp_graph_step replays it (one launch) and gives the bits of the plain
+    calls, also after a step made by the plain calls in between (the device
+    step counter is re-synchronised)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    w = synth.workload("cfg1")
+    T, pre = 16, 6
+    hists = histories(w.sources, 0, T, w.dt)
+    want = run_library(w.domains, w.c, w.dt, hists, 0, range(pre, T), mode=mode)
+    slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=mode) as lib:
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_graph_step(lib.ctx)
+        assert e.value.status == rp.RP_ERR_STATE
+        rho = [torch.empty(d.N, device=dev) for d in w.domains]
+        J = [torch.empty(3 * d.N, device=dev) for d in w.domains]
+        phi = [torch.empty(d.N, device=dev) for d in w.domains]
+        A = [torch.empty(3 * d.N, device=dev) for d in w.domains]
+        for i in range(pre):
+            lib.push_all([s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+        rp.rp_graph_capture(lib.ctx, rho, J, phi, A)
+        got = {}
+        for i in range(pre, T):
+            if i == pre + 4:                       # one step by the plain calls
+                lib.push_all([s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+                p_, a_ = lib.evaluate()
+                got[i] = [torch.cat([p_[d][None], a_[d].reshape(3, -1)]).clone() for d in range(2)]
+                continue
+            for d in range(2):
+                rho[d].copy_(slices[i][d][0])
+                J[d].copy_(slices[i][d][1:].reshape(-1))
+            rp.rp_graph_step(lib.ctx)
+            got[i] = [torch.cat([phi[d][None], A[d].reshape(3, -1)]).clone() for d in range(2)]
+        lib.sync()
+        for i in range(pre, T):
+            for d in range(2):
+                np.testing.assert_array_equal(got[i][d].cpu().numpy(), want[i][d], err_msg=f"step {i} domain {d}")
+
+
+def test_graph_capture_refuses_profiling():
+    import torch
+    dev = torch.device("cuda", 0)
+    w = synth.workload("cfg1")
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, flags=rp.RP_FLAG_PROFILE) as lib:
+        bufs = [[torch.empty(k * d.N, device=dev) for d in w.domains] for k in (1, 3, 1, 3)]
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_graph_capture(lib.ctx, *bufs)
+        assert e.value.status == rp.RP_ERR_UNSUPPORTED
