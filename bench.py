@@ -580,6 +580,7 @@ def run_ours(args, rank, world, local):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": ms_max / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "pair_points_per_s": world * sum(t.N * s_.N for t in w.domains for s_ in w.domains) * K / (ms_max / 1e3),
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": w.name, "description": w.description, "points_per_step": q_points,
                    "path": ("FFT: Hockney self term + delay-binned cross pairs, spectral history ring"
