@@ -395,9 +395,12 @@ def run_ours(args, rank, world, local):
         if args.mode == "lowrank" and lib.query()["npairs_far"]:
             acc["far_field_only"] = far_only_error(args, w, hists, rho, J, pre, check_step, depth, local,
                                                    stream, info)
+        pair_points = npts * w.points                 # every sampled target node sums every source node
         cpu = {"value": npts / t_or, "unit": UNIT, "cores": threads, "kind": "oracle",
                "sample": f"{args.oracle_nodes} seeded target nodes per domain x all {w.points} "
-                         f"source nodes at one step ({t_or:.1f} s wall)"}
+                         f"source nodes at one step ({t_or:.1f} s wall)",
+               "pair_points_per_s_per_core": pair_points / t_or / max(threads, 1),
+               "full_step_s_extrapolated": w.points * w.points / (pair_points / t_or)}
     for i in range(W - nwc):
         k = pre + (nwc + i) % ncycle
         lib.push_all(rho[k], J[k])
