@@ -486,7 +486,8 @@ rp_status rp_learned_dataset(const int n_s[3], double h_s, const double Lt[3], c
  * fields) is at most `gate`, the pair becomes RP_PAIR_LEARNED: its low-rank factors are
  * dropped, its source's moments are taken at every push, and each
  * rp_evaluate runs the learned stand-in for it.  Otherwise it stays on the low-rank
- * path, which remains the fallback and the judge of the network's error.
+ * path, which remains the fallback and the reference the network's error is
+ * measured against.
  *
  * Call after rp_finalize and before the first push, on a context that has
  * not been trained.  Synchronous on the context's stream.  Zero fields of
