@@ -110,11 +110,29 @@ typedef enum {
  * returns RP_ERR_UNSUPPORTED with far pairs.  Costs one elementwise pass per
  * push. */
 #define RP_FLAG_GROUND_STATE_SPLIT 0x10u
+/* History spill to host memory (Sec. IV: every sample of the window
+ * [l - N_R,max, l] is kept for the steps to come, while a step reads only a
+ * pair's Delta N_R of them, and the store need not be the fast memory).
+ * A pair whose lag window [lag_lo, lag_hi] starts far back
+ * (lag_lo >= 2 (lag_hi - lag_lo + 2)) reads its source's spectra from a
+ * small device window ring of lag_hi - lag_lo + 2 slots instead of the
+ * full-depth spectral ring.  Each step's spectra are copied once into a
+ * pinned host ring (depth max(history_depth, largest spilled lag_hi + 1));
+ * one slot per spilled window is copied back a step ahead of use.  The
+ * device rings keep only the unspilled lags (plus two slots of slack).  The
+ * kernels and the sums are unchanged, so results are bit-identical to the
+ * unspilled context; the copies ride on two streams of the context's own,
+ * ordered against the kernels by events.  FFT pairs only (direct and far
+ * pairs are unaffected); not with rp_graph_capture (RP_ERR_UNSUPPORTED).
+ * rp_stats.host_bytes and spill_windows report the host ring and the number
+ * of windows. */
+#define RP_FLAG_HISTORY_SPILL 0x20u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
     double dt;           /* time step, > 0 */
-    int history_depth;   /* minimum history ring depth in steps (0: what the geometry needs) */
+    int history_depth;   /* minimum history ring depth in steps (0: what the geometry needs); under
+                          * RP_FLAG_HISTORY_SPILL, of the host ring */
     int mode;            /* rp_mode */
     unsigned int flags;  /* RP_FLAG_* */
     int far_points;      /* RP_MODE_LOWRANK: interpolation nodes per axis, 2..8 (0: 4) */
@@ -163,7 +181,9 @@ typedef struct {
     long long far_bytes;      /* device memory of the far path (factors, batches, rings) */
     int mac_warps;            /* consumer warps of the MAC variant in use (last size class), 0 if none */
     int npairs_learned;       /* pairs on the learned far path (after rp_train_far_model) */
-    int reserved[2];
+    int spill_windows;        /* RP_FLAG_HISTORY_SPILL: lag windows read from host-refilled window rings */
+    int reserved;
+    long long host_bytes;     /* pinned host memory of the spilled spectral history */
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -268,7 +288,8 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
  * contents.  Call at a step boundary.  FFT and direct pairs only, without
  * RP_FLAG_PROFILE or RP_FLAG_GROUND_STATE_SPLIT (RP_ERR_UNSUPPORTED
  * otherwise): the far path's launches change from step to step.  A new
- * capture replaces the previous graph.  (No counterpart in the paper: a
+ * capture replaces the previous graph.  Not with RP_FLAG_HISTORY_SPILL (its
+ * copies address the slots of the current step).  (No counterpart in the paper: a
  * property of the library.)
  */
 rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J,

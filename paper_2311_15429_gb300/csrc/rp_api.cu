@@ -61,6 +61,30 @@ struct LaunchGroup {
     int blk2_0, blk2_1;
 };
 
+// History spill (RP_FLAG_HISTORY_SPILL).  A spectral ring whose source has a
+// spilled pair: its pinned host copy, [host depth][slot_elems] float2.
+struct SpillRing {
+    int ring;                // index into the forward rings
+    float2 *host;
+};
+
+// A spilled lag window [lo, hi] of one spectral ring: a device ring of
+// depth B + 1 = hi - lo + 2 holding the source spectra of steps j at slot j % depth;
+// `have` is the newest step copied in (-1: none).
+struct SpillWindow {
+    int ring, sr;            // forward ring, and its SpillRing
+    int lo, hi, depth;
+    float2 *dev;
+    long long have;
+};
+
+constexpr int kSpillSlack = 2;   // device slots kept past a spilled ring's own lags, so that a
+                                 // step's copy out has two steps to finish before its slot is reused
+
+// A pair's lag window is spilled when its window ring is at most half the
+// ring depth it would otherwise need.
+bool spill_window(int lo, int hi) { return lo >= 2 * (hi - lo + 2); }
+
 // Supported padded lengths: R * L with R in {1,2,3,4,6}, L a power of two <= 32.
 const int kSizes[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192};
 
@@ -110,6 +134,23 @@ struct rp_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_synced = -2;              // host step the device counter holds (-2: unknown)
     std::vector<float *> ground, delta, pstatic;
+    // history spill to host memory (RP_FLAG_HISTORY_SPILL): the spilled rings
+    // (device depth spill_dd, host depth spill_hd), the window rings, and the
+    // copy streams with their events:
+    //   sp_pushed   on the context stream when a round's spectra are written;
+    //   sp_out[k]   on spill_out after the copy out of step s, k = s % spill_dd
+    //               (the push of step s + spill_dd waits for it before reusing the slot);
+    //   sp_in       on spill_in after the last copy into the windows;
+    //   sp_mac[2]   on the context stream after the MAC of the last two evaluations.
+    bool spill = false;
+    int spill_dd = 0, spill_hd = 0;
+    std::vector<SpillRing> spill_rings;
+    std::vector<SpillWindow> spill_wins;
+    long long host_bytes = 0;
+    cudaStream_t spill_out = nullptr, spill_in = nullptr;
+    cudaEvent_t sp_pushed = nullptr, sp_in = nullptr, sp_mac[2] = {nullptr, nullptr};
+    std::vector<cudaEvent_t> sp_out;
+    int sp_mac_next = 0;
     bool finalized = false;
     std::vector<DomainDesc> doms;
     std::vector<PairPlan> pairs;   // [t * ndom + s]
@@ -379,6 +420,36 @@ rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
 }  // namespace
 
 namespace {
+
+// History spill: the window rings (device, zeroed), the pinned host rings,
+// the two copy streams and their events.
+rp_status open_spill(rp_ctx *ctx)
+{
+    if (ctx->spill_rings.empty()) return RP_OK;
+    rp_status st;
+    for (SpillWindow &W : ctx->spill_wins) {
+        const size_t elems = (size_t)W.depth * ctx->fwd[W.ring].slot_elems;
+        if ((st = dev_alloc(ctx, &W.dev, elems))) return st;
+        RP_CUDA(ctx, cudaMemset(W.dev, 0, elems * sizeof(float2)));
+    }
+    for (SpillRing &S : ctx->spill_rings) {
+        const size_t bytes = (size_t)ctx->spill_hd * ctx->fwd[S.ring].slot_elems * sizeof(float2);
+        void *p = nullptr;
+        RP_CUDA(ctx, cudaHostAlloc(&p, bytes, cudaHostAllocDefault));
+        S.host = static_cast<float2 *>(p);
+        std::memset(p, 0, bytes);
+    }
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_out, cudaStreamNonBlocking));
+    RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_in, cudaStreamNonBlocking));
+    auto event = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
+    RP_CUDA(ctx, event(&ctx->sp_pushed));
+    RP_CUDA(ctx, event(&ctx->sp_in));
+    RP_CUDA(ctx, event(&ctx->sp_mac[0]));
+    RP_CUDA(ctx, event(&ctx->sp_mac[1]));
+    ctx->sp_out.assign(ctx->spill_dd, nullptr);
+    for (cudaEvent_t &e : ctx->sp_out) RP_CUDA(ctx, event(&e));
+    return RP_OK;
+}
 
 int class_slot(int cls)
 {
@@ -882,6 +953,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     if (ctx->cfg.mac_warps) std::fill(std::begin(ctx->mac_cw), std::end(ctx->mac_cw), ctx->cfg.mac_warps);
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
     ctx->split = (cfg->flags & RP_FLAG_GROUND_STATE_SPLIT) != 0;
+    ctx->spill = (cfg->flags & RP_FLAG_HISTORY_SPILL) != 0;
     // the split's histories are zero before the first push: the clamped reads
     // of steps before it read the zeroed slot of step 0
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0 || ctx->split;
@@ -985,6 +1057,12 @@ rp_status rp_finalize(rp_ctx *ctx)
     std::map<std::pair<int, std::array<int, 3>>, int> ring_of;
     std::vector<std::pair<int, std::array<int, 3>>> ring_keys;
     std::vector<int> ring_depth;
+    std::vector<char> ring_spilled;
+    // history spill: a spilled pair's lags leave the device ring's depth
+    // alone; rings with a spilled pair all take one device depth (their own
+    // lags plus slack) and one host depth
+    std::vector<char> pair_spilled(ctx->pairs.size(), 0);
+    int host_depth = ctx->cfg.history_depth;
     for (int s = 0; s < nd; ++s)
         for (int t = 0; t < nd; ++t) {
             const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
@@ -994,11 +1072,26 @@ rp_status rp_finalize(rp_ctx *ctx)
             if (it == ring_of.end()) {
                 ring_of[key] = (int)ring_keys.size();
                 ring_keys.push_back(key);
-                ring_depth.push_back(std::max(ctx->cfg.history_depth, 1));
+                ring_depth.push_back(ctx->spill ? 1 : std::max(ctx->cfg.history_depth, 1));
+                ring_spilled.push_back(0);
                 it = ring_of.find(key);
+            }
+            if (ctx->spill && spill_window(p.lag_lo, p.lag_hi)) {
+                pair_spilled[(size_t)t * nd + s] = 1;
+                ring_spilled[it->second] = 1;
+                host_depth = std::max(host_depth, p.lag_hi + 1);
+                continue;
             }
             ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1);
         }
+    if (ctx->spill) {
+        for (size_t r = 0; r < ring_keys.size(); ++r)
+            if (ring_spilled[r]) ctx->spill_dd = std::max(ctx->spill_dd, ring_depth[r] + kSpillSlack);
+        for (size_t r = 0; r < ring_keys.size(); ++r)
+            if (ring_spilled[r]) ring_depth[r] = ctx->spill_dd;
+            else ring_depth[r] = std::max(ring_depth[r], ctx->cfg.history_depth);
+        ctx->spill_hd = host_depth;
+    }
     // order rings by (kernel size class, source): each class is one launch
     std::vector<int> ring_order(ring_keys.size());
     for (size_t r = 0; r < ring_keys.size(); ++r) ring_order[r] = (int)r;
@@ -1032,6 +1125,10 @@ rp_status rp_finalize(rp_ctx *ctx)
         tw[m[0]]; tw[m[1]]; tw[m[2]];
         ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
         ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
+        if (ctx->spill && ring_spilled[r]) {
+            ctx->spill_rings.push_back({(int)i, nullptr});
+            ctx->host_bytes += (long long)ctx->spill_hd * R.slot_elems * (long long)sizeof(float2);
+        }
         ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(R.ny, R.ax));
         ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
         const int cls = ring_class(r);
@@ -1047,7 +1144,7 @@ rp_status rp_finalize(rp_ctx *ctx)
 
     // ---- FFT targets, ordered by size class, and their (source, lag)
     // entries: the self pair's real kernels first, then the complex ones
-    struct EntryPlan { int t, s, lag, ring; bool real_g; };
+    struct EntryPlan { int t, s, lag, ring; bool real_g; int win; };   // win: spill window, or -1
     std::vector<EntryPlan> eplan;
     std::vector<int> tgt_order;
     for (int t = 0; t < nd; ++t)
@@ -1070,7 +1167,22 @@ rp_status rp_finalize(rp_ctx *ctx)
                 const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
                 if (p.kind != RP_PAIR_FFT || (pass == 0) != (s == t)) continue;
                 const int ring = ring_of[std::make_pair(s, tm[t])];
-                for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s});
+                int win = -1;
+                if (pair_spilled[(size_t)t * nd + s]) {
+                    for (size_t w = 0; w < ctx->spill_wins.size(); ++w) {
+                        const SpillWindow &W = ctx->spill_wins[w];
+                        if (W.ring == ring && W.lo == p.lag_lo && W.hi == p.lag_hi) win = (int)w;
+                    }
+                    if (win < 0) {
+                        win = (int)ctx->spill_wins.size();
+                        int sr = 0;
+                        while (ctx->spill_rings[sr].ring != ring) ++sr;
+                        const SpillWindow W{ring, sr, p.lag_lo, p.lag_hi, p.lag_hi - p.lag_lo + 2, nullptr, -1};
+                        ctx->spill_wins.push_back(W);
+                        ctx->spectral_bytes += (long long)W.depth * ctx->fwd[ring].slot_elems * (long long)sizeof(float2);
+                    }
+                }
+                for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s, win});
             }
             if (pass == 0) I.er = (int)eplan.size();
         }
@@ -1186,6 +1298,7 @@ rp_status rp_finalize(rp_ctx *ctx)
         if ((st = dev_alloc(ctx, &R.t1, 4ULL * R.kx * R.nz * R.ay.M))) return st;
         R.tw_x = tw[R.ax.M]; R.tw_y = tw[R.ay.M]; R.tw_z = tw[R.az.M];
     }
+    if ((st = open_spill(ctx))) return st;
     if (ctx->split) {
         ctx->ground.assign(nd, nullptr);
         ctx->delta.assign(nd, nullptr);
@@ -1272,6 +1385,10 @@ rp_status rp_finalize(rp_ctx *ctx)
             E.ring = R.ring;
             E.slot_elems = R.slot_elems;
             E.depth = R.depth;
+            if (e.win >= 0) {   // a spilled window: its own ring, same slot layout
+                E.ring = ctx->spill_wins[e.win].dev;
+                E.depth = ctx->spill_wins[e.win].depth;
+            }
             E.lag = e.lag;
             E.is_real = e.real_g ? 1 : 0;
             ctx->entries.push_back(E);
@@ -1343,6 +1460,10 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     rp_status st;
     const long long step = ctx->step;
     const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
+    // history spill: this step's spectra go to the device slot of step
+    // step - spill_dd, whose copy to the host must be done
+    if (!ctx->spill_rings.empty() && step >= ctx->spill_dd)
+        RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_out[step % ctx->spill_dd], 0));
     // raw ring
     int blk = ctx->raw_block0[d1] - ctx->raw_block0[d0];
     if (blk > 0) {
@@ -1459,6 +1580,100 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
 
 extern "C" {
 
+// History spill, once a round's pushes are queued: copy the round's spectra
+// of the spilled rings into their host rings (spill_out waits for the
+// kernels that wrote them, and for the copies into the windows queued so far,
+// the last readers of the host slot it overwrites).
+static rp_status spill_round_done(rp_ctx *ctx)
+{
+    if (ctx->spill_rings.empty() || ctx->npushed != (int)ctx->doms.size()) return RP_OK;
+    const long long l = ctx->step;
+    RP_CUDA(ctx, cudaEventRecord(ctx->sp_pushed, ctx->stream));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_pushed, 0));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_in, 0));
+    for (const SpillRing &S : ctx->spill_rings) {
+        const FwdRing &R = ctx->fwd[S.ring];
+        RP_CUDA(ctx, cudaMemcpyAsync(S.host + (size_t)(l % ctx->spill_hd) * R.slot_elems,
+                                     R.ring + (size_t)(l % ctx->spill_dd) * R.slot_elems,
+                                     (size_t)R.slot_elems * sizeof(float2), cudaMemcpyDeviceToHost, ctx->spill_out));
+    }
+    RP_CUDA(ctx, cudaEventRecord(ctx->sp_out[l % ctx->spill_dd], ctx->spill_out));
+    return RP_OK;
+}
+
+// History spill: the host slot of step j into window W's slot j % depth.
+static rp_status spill_copy_in(rp_ctx *ctx, const SpillWindow &W, long long j)
+{
+    const long long n = ctx->fwd[W.ring].slot_elems;
+    RP_CUDA(ctx, cudaMemcpyAsync(W.dev + (size_t)(j % W.depth) * n,
+                                 ctx->spill_rings[W.sr].host + (size_t)(j % ctx->spill_hd) * n,
+                                 (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, ctx->spill_in));
+    return RP_OK;
+}
+
+// History spill, before the MAC of step l: every window must hold source
+// steps l - hi .. l - lo (clamped at 0 under RP_FLAG_GROUND_STATE_CLAMP).
+// Normally the previous evaluation fetched them ahead; what is missing (the
+// first steps, skipped evaluations, a loaded state) is copied here, after the
+// copies out up to step l and the last MAC.  The MAC then waits for sp_in.
+// The newly written slots j % depth held steps at least depth = B + 1 before
+// j, which no MAC from step l on reads.
+static rp_status spill_fetch(rp_ctx *ctx)
+{
+    if (ctx->spill_rings.empty()) return RP_OK;
+    const long long l = ctx->step;
+    bool any = false;
+    rp_status st;
+    for (SpillWindow &W : ctx->spill_wins) {
+        long long a = l - W.hi, b = l - W.lo;
+        if (ctx->clamp) { a = std::max(a, 0LL); b = std::max(b, 0LL); }
+        if (a < 0) return fail(ctx, RP_ERR_HISTORY, "spilled window before the first push");
+        const long long from = std::max(a, W.have + 1);
+        if (from > b) continue;
+        if (!any) {
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[l % ctx->spill_dd], 0));
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_mac[ctx->sp_mac_next ^ 1], 0));
+            any = true;
+        }
+        for (long long j = from; j <= b; ++j)
+            if ((st = spill_copy_in(ctx, W, j))) return st;
+        W.have = b;
+    }
+    if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
+    return RP_OK;
+}
+
+// History spill, after the MAC of step l: mark it, then fetch the one source
+// step each window adds at step l + 1, j = l + 1 - lo (<= l - 3, as a spilled
+// window has lo >= 4), so that the copy runs under this step's remaining
+// kernels.  It waits for the copy out of step l - 1 (which follows that of
+// j on spill_out) and for the MAC before this one: slot j % depth held step
+// j - (B + 1) = l - hi - 1, which only MACs up to step l - 1 read.
+static rp_status spill_after_mac(rp_ctx *ctx)
+{
+    if (ctx->spill_rings.empty()) return RP_OK;
+    const long long l = ctx->step;
+    RP_CUDA(ctx, cudaEventRecord(ctx->sp_mac[ctx->sp_mac_next], ctx->stream));
+    ctx->sp_mac_next ^= 1;
+    if (l < 1) return RP_OK;
+    bool any = false;
+    rp_status st;
+    for (SpillWindow &W : ctx->spill_wins) {
+        const long long j = l + 1 - W.lo;
+        if (j < 0 || j != W.have + 1) continue;
+        if (!any) {
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[(l - 1) % ctx->spill_dd], 0));
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_mac[ctx->sp_mac_next], 0));
+            any = true;
+        }
+        if ((st = spill_copy_in(ctx, W, j))) return st;
+        W.have = j;
+    }
+    if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
+    return RP_OK;
+}
+
 // Ground-state split, at a push of domains [d0, d1): on the first step keep
 // S(0) (pushed as it is, for the static potential); later, push Delta S.
 static rp_status split_inputs(rp_ctx *ctx, int d0, int d1, IoPtrs &in)
@@ -1502,6 +1717,10 @@ static rp_status split_round_done(rp_ctx *ctx)
         RP_CUDA(ctx, cudaMemsetAsync(R.ring, 0, R.slot_elems * sizeof(float2), ctx->stream));   // slot of step 0
     for (const RawRing &r : ctx->raw)
         if (r.ring) RP_CUDA(ctx, cudaMemsetAsync(r.ring, 0, 4 * r.n * sizeof(float), ctx->stream));
+    // history spill: the host copy of step 0 becomes zero too, and the
+    // windows fetch it again
+    if ((st = spill_round_done(ctx))) return st;
+    for (SpillWindow &W : ctx->spill_wins) W.have = -1;
     ctx->static_done = true;
     return RP_OK;
 }
@@ -1517,6 +1736,7 @@ rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J)
     in.J[id] = d_J;
     if ((st = split_inputs(ctx, id, id + 1, in))) return st;
     if ((st = enqueue_push(ctx, id, id + 1, in))) return st;
+    if ((st = spill_round_done(ctx))) return st;
     return split_round_done(ctx);
 }
 
@@ -1540,6 +1760,7 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     rp_status st2;
     if ((st2 = split_inputs(ctx, 0, nd, in))) return st2;
     if ((st2 = enqueue_push(ctx, 0, nd, in))) return st2;
+    if ((st2 = spill_round_done(ctx))) return st2;
     return split_round_done(ctx);
 }
 
@@ -1649,6 +1870,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
     const int clamp = ctx->clamp ? 1 : 0;
     const float inv_c = (float)(1.0 / ctx->cfg.c);
+    if ((st = spill_fetch(ctx))) return st;
     for (const LaunchGroup &g : ctx->inv_groups) {
         const int ntiles = g.blk1 - g.blk0;
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
@@ -1662,6 +1884,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
              })))
             return st;
     }
+    if ((st = spill_after_mac(ctx))) return st;
     if (!ctx->lpairs.empty()) {
         // learned pairs: network rows, network, node values into the coefficients
         if ((st = timed_launch(ctx, RP_K_LEARNED, "learned far field", [&] {
@@ -2116,8 +2339,9 @@ rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *
     for (int d = 0; d < nd; ++d)
         if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
     if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || !ctx->lpairs.empty() ||
-        (ctx->cfg.flags & RP_FLAG_DEFER_FAR))
-        return fail(ctx, RP_ERR_UNSUPPORTED, "rp_graph_capture: FFT and direct pairs only, without profiling or split");
+        (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_rings.empty())
+        return fail(ctx, RP_ERR_UNSUPPORTED,
+                    "rp_graph_capture: FFT and direct pairs only, without profiling, split or history spill");
     if (ctx->step >= 0 && ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_graph_capture inside a partially pushed step");
     if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
     if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
@@ -2196,6 +2420,8 @@ rp_status rp_sync(rp_ctx *ctx)
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
     if (ctx->copy_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_in));
     if (ctx->copy_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_out));
+    if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
+    if (ctx->spill_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_in));
     RP_CUDA(ctx, cudaGetLastError());
     if (ctx->d_err) {
         int flag = 0;
@@ -2227,6 +2453,8 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->npairs_far = ctx->npairs_far;
     out->far_bytes = ctx->far_bytes;
     out->npairs_learned = ctx->npairs_learned;
+    out->spill_windows = (int)ctx->spill_wins.size();
+    out->host_bytes = ctx->host_bytes;
     out->mac_warps = 0;
     for (const LaunchGroup &g : ctx->inv_groups)
         if (g.cls > 0 && ctx->tma) out->mac_warps = ctx->mac_cw[class_slot(g.cls)];
@@ -2302,6 +2530,8 @@ unsigned long long layout_hash(const rp_ctx *ctx)
     mix(&ctx->split, sizeof(bool));
     for (const FwdRing &R : ctx->fwd) { mix(&R.depth, sizeof(int)); mix(&R.slot_elems, sizeof(long long)); }
     for (const RawRing &r : ctx->raw) { mix(&r.depth, sizeof(int)); mix(&r.n, sizeof(long long)); }
+    for (const SpillRing &S : ctx->spill_rings) mix(&S.ring, sizeof(int));
+    mix(&ctx->spill_hd, sizeof(int));
     return h;
 }
 
@@ -2321,6 +2551,9 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
         const size_t bytes = 4 * (size_t)ctx->doms[d].N * sizeof(float);
         if ((st = fn((void *)ctx->ground[d], bytes)) || (st = fn((void *)ctx->pstatic[d], bytes))) return st;
     }
+    // the spilled history (pinned host memory); the window rings are fetched again
+    for (const SpillRing &S : ctx->spill_rings)
+        if ((st = fn((void *)S.host, (size_t)ctx->spill_hd * ctx->fwd[S.ring].slot_elems * sizeof(float2)))) return st;
     return RP_OK;
 }
 
@@ -2335,6 +2568,8 @@ rp_status rp_save_state(rp_ctx *ctx, const char *path)
     if (!path) return fail(ctx, RP_ERR_ARG, "NULL path");
     if (!ctx->lpairs.empty()) return fail(ctx, RP_ERR_UNSUPPORTED, "a context with learned pairs has no saved state");
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
+    if (ctx->spill_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_in));
     FILE *f = std::fopen(path, "wb");
     if (!f) return fail(ctx, RP_ERR_ARG, std::string("cannot open ") + path);
     const unsigned long long h = layout_hash(ctx);
@@ -2347,7 +2582,7 @@ rp_status rp_save_state(rp_ctx *ctx, const char *path)
     if (ok)
         st = for_each_ring(ctx, [&](void *dptr, size_t bytes) -> rp_status {
             buf.resize(bytes);
-            RP_CUDA(ctx, cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDeviceToHost));
+            RP_CUDA(ctx, cudaMemcpy(buf.data(), dptr, bytes, cudaMemcpyDefault));   // device or pinned host
             if (std::fwrite(buf.data(), 1, bytes, f) != bytes) return fail(ctx, RP_ERR_ARG, "write failed");
             return RP_OK;
         });
@@ -2378,15 +2613,18 @@ rp_status rp_load_state(rp_ctx *ctx, const char *path)
         return fail(ctx, RP_ERR_STATE, "state file does not match this context");
     }
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
+    if (ctx->spill_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_in));
     std::vector<char> buf;
     st = for_each_ring(ctx, [&](void *dptr, size_t bytes) -> rp_status {
         buf.resize(bytes);
         if (std::fread(buf.data(), 1, bytes, f) != bytes) return fail(ctx, RP_ERR_STATE, "state file truncated");
-        RP_CUDA(ctx, cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyHostToDevice));
+        RP_CUDA(ctx, cudaMemcpy(dptr, buf.data(), bytes, cudaMemcpyDefault));   // device or pinned host
         return RP_OK;
     });
     std::fclose(f);
     if (st) return st;
+    for (SpillWindow &W : ctx->spill_wins) W.have = -1;
     ctx->step = step;
     ctx->npushed = npushed;
     ctx->static_done = step > 0 || (step == 0 && npushed == nd);   // P(0) came with the state
@@ -2415,6 +2653,16 @@ void rp_destroy(rp_ctx *ctx)
             cudaStreamDestroy(ctx->copy_in);
             cudaStreamDestroy(ctx->copy_out);
         }
+        if (ctx->spill_out) {
+            cudaStreamSynchronize(ctx->spill_out);
+            cudaStreamSynchronize(ctx->spill_in);
+            for (cudaEvent_t e : ctx->sp_out) if (e) cudaEventDestroy(e);
+            for (cudaEvent_t e : {ctx->sp_pushed, ctx->sp_in, ctx->sp_mac[0], ctx->sp_mac[1]})
+                if (e) cudaEventDestroy(e);
+            cudaStreamDestroy(ctx->spill_out);
+            if (ctx->spill_in) cudaStreamDestroy(ctx->spill_in);
+        }
+        for (const SpillRing &S : ctx->spill_rings) if (S.host) cudaFreeHost(S.host);
         for (const ProfRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
         for (void *p : ctx->allocs) cudaFree(p);

@@ -19,6 +19,7 @@ RP_OK, RP_ERR_ARG, RP_ERR_STATE, RP_ERR_HISTORY, RP_ERR_CUDA, RP_ERR_OOM, \
 RP_MODE_FFT, RP_MODE_DIRECT, RP_MODE_LOWRANK = 0, 1, 2
 RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE, RP_FLAG_DEFER_FAR = 0x1, 0x2, 0x4, 0x8
 RP_FLAG_GROUND_STATE_SPLIT = 0x10
+RP_FLAG_HISTORY_SPILL = 0x20
 RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
  RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_MOMENTS, RP_K_LEARNED,
@@ -61,7 +62,7 @@ class rp_stats(ctypes.Structure):
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
                 ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
                 ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("npairs_learned", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("spill_windows", ctypes.c_int), ("reserved", ctypes.c_int), ("host_bytes", ctypes.c_longlong)]
 
 
 class RPError(RuntimeError):

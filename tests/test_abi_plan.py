@@ -221,3 +221,36 @@ def test_ground_split_refuses_far_pairs():
     finally:
         rp.rp_destroy(ctx)
 
+
+
+def test_history_spill_plan():
+    """RP_FLAG_HISTORY_SPILL on the 2 x 48^3 workload (cross lags 290..294):
+    each cross pair reads a 6-slot window ring (B + 1), the spectral rings keep
+    the self lags 0..3 plus two slots, and the 320-step history moves to a
+    pinned host ring.  A neighbouring pair (lags from 0) stays on the device."""
+    w = synth.workload("cfg2")
+    slot = 4 * 49 * 96 * 96 * 8
+    ctx = rp.rp_create(w.c, w.dt, w.history, flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_HISTORY_SPILL)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        q = rp.rp_query(ctx)
+        assert q["spill_windows"] == 2
+        assert q["spectral_depth"] == 4 + 2
+        assert q["spectral_bytes"] == 2 * (6 + 6) * slot
+        assert q["host_bytes"] == 2 * w.history * slot
+        assert rp.rp_pair_info(ctx, 0, 1)["lag_lo"] == 290   # the pair plan itself is unchanged
+    finally:
+        rp.rp_destroy(ctx)
+    # neighbours 1 bohr apart: every window starts near lag 0, nothing spills
+    doms = [synth.Domain((0.0, 0.0, 0.0), (8, 8, 8), 0.25), synth.Domain((3.0, 0.0, 0.0), (8, 8, 8), 0.25)]
+    ctx = rp.rp_create(synth.C_AU, 0.05, flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_HISTORY_SPILL)
+    try:
+        for d in doms:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        q = rp.rp_query(ctx)
+        assert q["spill_windows"] == 0 and q["host_bytes"] == 0
+    finally:
+        rp.rp_destroy(ctx)
