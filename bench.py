@@ -913,8 +913,8 @@ def run_spill(args, rank, world, local):
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / K
             outs[name] = [torch.cat([lib.phi[d], lib.A[d]]).clone() for d in range(len(w.domains))]
-            slot = 4 * 49 * 96 * 96 * 8
-            link = (len(w.domains) + q["spill_windows"]) * slot if q["spill_windows"] else 0
+            # per step: each spilled source's slice to the host, each window's slice back
+            link = (len(w.domains) + q["spill_windows"]) * 16 * w.domains[0].N if q["spill_windows"] else 0
             res[name] = {"ms_per_step": ms, "device_bytes": q["device_bytes"], "spectral_bytes": q["spectral_bytes"],
                          "host_bytes": q["host_bytes"], "spill_windows": q["spill_windows"],
                          "spectral_depth_device": q["spectral_depth"], "host_link_bytes_per_step": link,
@@ -926,8 +926,9 @@ def run_spill(args, rank, world, local):
             "value": res["spill"]["ms_per_step"], "n_gpus": world, "steps": K, "warmup": W,
             "higher_is_better": False, "dtype": "f32", "data": "synthetic",
             "config": {"workload": "cfg2-spill", "description": w.description + "; clamped history, every step "
-                       "evaluated; the spilled context keeps the 290-294-step cross windows in 6-slot device "
-                       "rings refilled from a pinned host ring", "ncycle_inputs": ncycle},
+                       "evaluated; the spilled context keeps the 290-294-step cross windows in 5-slot spectral "
+                       "rings, fed one (rho, J) slice a step from a pinned host ring through the forward "
+                       "passes", "ncycle_inputs": ncycle},
             "device": res["device"], "spill": res["spill"], "bit_identical": bool(same),
             "device_bytes_saved": res["device"]["device_bytes"] - res["spill"]["device_bytes"]}
     print(json.dumps(line), flush=True)

@@ -115,17 +115,20 @@ typedef enum {
  * pair's Delta N_R of them, and the store need not be the fast memory).
  * A pair whose lag window [lag_lo, lag_hi] starts far back
  * (lag_lo >= 2 (lag_hi - lag_lo + 2)) reads its source's spectra from a
- * small device window ring of lag_hi - lag_lo + 2 slots instead of the
- * full-depth spectral ring.  Each step's spectra are copied once into a
- * pinned host ring (depth max(history_depth, largest spilled lag_hi + 1));
- * one slot per spilled window is copied back a step ahead of use.  The
- * device rings keep only the unspilled lags (plus two slots of slack).  The
- * kernels and the sums are unchanged, so results are bit-identical to the
- * unspilled context; the copies ride on two streams of the context's own,
+ * device window ring of B = lag_hi - lag_lo + 1 slots instead of the
+ * full-depth spectral ring.  The (rho, J) slices of such a source, 16 B per
+ * point (an eighth of its doubled-size spectrum), are copied once each round
+ * into a pinned host ring of depth max(history_depth, largest spilled
+ * lag_hi + 1); each step, every window gets back the one slice it newly
+ * needs, a step ahead, and transforms it into its ring with the same forward
+ * passes as a push.  The device spectral rings keep only the unspilled lags.
+ * Same kernels, same summation order: results are bit-identical to the
+ * unspilled context.  The copies ride on two streams of the context's own,
  * ordered against the kernels by events.  FFT pairs only (direct and far
  * pairs are unaffected); not with rp_graph_capture (RP_ERR_UNSUPPORTED).
  * rp_stats.host_bytes and spill_windows report the host ring and the number
- * of windows. */
+ * of windows; spectral_bytes then includes the window rings, their input
+ * slices and a three-slot staging ring per spilled source. */
 #define RP_FLAG_HISTORY_SPILL 0x20u
 
 typedef struct {

@@ -61,25 +61,32 @@ struct LaunchGroup {
     int blk2_0, blk2_1;
 };
 
-// History spill (RP_FLAG_HISTORY_SPILL).  A spectral ring whose source has a
-// spilled pair: its pinned host copy, [host depth][slot_elems] float2.
-struct SpillRing {
-    int ring;                // index into the forward rings
-    float2 *host;
+// History spill (RP_FLAG_HISTORY_SPILL).  A source domain with a spilled
+// pair: device staging of its last kSpillStage pushed slices and the pinned
+// host ring of its history, [depth][4][N] float each.
+struct SpillSource {
+    int dom;
+    float *stage;
+    float *host;
 };
 
-// A spilled lag window [lo, hi] of one spectral ring: a device ring of
-// depth B + 1 = hi - lo + 2 holding the source spectra of steps j at slot j % depth;
-// `have` is the newest step copied in (-1: none).
+// A spilled lag window [lo, hi] of one spectral ring: a device spectral ring
+// of depth B = hi - lo + 1 holding the source spectra of steps j at slot
+// j % B.  The forward passes make them (window descriptor w of the window
+// ring table: the ring's sizes, this ring as output) from raw slices copied
+// in from the host ring into one of two input buffers, by parity of j.
+// `have`: the newest step transformed in (-1: none); raw_step: the step each
+// input buffer holds.
 struct SpillWindow {
-    int ring, sr;            // forward ring, and its SpillRing
+    int ring, ss;            // forward ring, SpillSource
     int lo, hi, depth;
     float2 *dev;
+    float *raw;              // [2][4][N of the source]
     long long have;
+    long long raw_step[2];
 };
 
-constexpr int kSpillSlack = 2;   // device slots kept past a spilled ring's own lags, so that a
-                                 // step's copy out has two steps to finish before its slot is reused
+constexpr int kSpillStage = 3;   // staging slots: a round's copy to the host has two more rounds to finish
 
 // A pair's lag window is spilled when its window ring is at most half the
 // ring depth it would otherwise need.
@@ -134,23 +141,25 @@ struct rp_ctx {
     cudaGraphExec_t graph_exec = nullptr;
     long long graph_synced = -2;              // host step the device counter holds (-2: unknown)
     std::vector<float *> ground, delta, pstatic;
-    // history spill to host memory (RP_FLAG_HISTORY_SPILL): the spilled rings
-    // (device depth spill_dd, host depth spill_hd), the window rings, and the
-    // copy streams with their events:
-    //   sp_pushed   on the context stream when a round's spectra are written;
-    //   sp_out[k]   on spill_out after the copy out of step s, k = s % spill_dd
-    //               (the push of step s + spill_dd waits for it before reusing the slot);
-    //   sp_in       on spill_in after the last copy into the windows;
-    //   sp_mac[2]   on the context stream after the MAC of the last two evaluations.
+    // history spill to host memory (RP_FLAG_HISTORY_SPILL): the spilled
+    // sources (host ring depth spill_hd), the windows with their descriptors
+    // for the forward passes, and the copy streams with their events:
+    //   sp_pushed   on the context stream once a round's slices are staged;
+    //   sp_out[k]   on spill_out after the copy to the host of step s, k = s % kSpillStage
+    //               (the push of step s + kSpillStage waits for it before reusing the staging slot);
+    //   sp_in       on spill_in after the last copy into a window's input buffer;
+    //   sp_wfft     on the context stream after the last window transform (the
+    //               input buffers' last reader).
     bool spill = false;
-    int spill_dd = 0, spill_hd = 0;
-    std::vector<SpillRing> spill_rings;
+    int spill_hd = 0;
+    std::vector<SpillSource> spill_srcs;
     std::vector<SpillWindow> spill_wins;
+    std::vector<FwdRing> wfwd;
+    FwdRing *d_wfwd = nullptr;
     long long host_bytes = 0;
     cudaStream_t spill_out = nullptr, spill_in = nullptr;
-    cudaEvent_t sp_pushed = nullptr, sp_in = nullptr, sp_mac[2] = {nullptr, nullptr};
+    cudaEvent_t sp_pushed = nullptr, sp_in = nullptr, sp_wfft = nullptr;
     std::vector<cudaEvent_t> sp_out;
-    int sp_mac_next = 0;
     bool finalized = false;
     std::vector<DomainDesc> doms;
     std::vector<PairPlan> pairs;   // [t * ndom + s]
@@ -421,32 +430,48 @@ rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
 
 namespace {
 
-// History spill: the window rings (device, zeroed), the pinned host rings,
-// the two copy streams and their events.
+// History spill: the staging and window rings (device, zeroed), the pinned
+// host rings, the window descriptors (after the forward rings' buffers), the
+// two copy streams and their events.
 rp_status open_spill(rp_ctx *ctx)
 {
-    if (ctx->spill_rings.empty()) return RP_OK;
+    if (ctx->spill_srcs.empty()) return RP_OK;
     rp_status st;
-    for (SpillWindow &W : ctx->spill_wins) {
-        const size_t elems = (size_t)W.depth * ctx->fwd[W.ring].slot_elems;
-        if ((st = dev_alloc(ctx, &W.dev, elems))) return st;
-        RP_CUDA(ctx, cudaMemset(W.dev, 0, elems * sizeof(float2)));
-    }
-    for (SpillRing &S : ctx->spill_rings) {
-        const size_t bytes = (size_t)ctx->spill_hd * ctx->fwd[S.ring].slot_elems * sizeof(float2);
+    for (SpillSource &S : ctx->spill_srcs) {
+        const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
+        if ((st = dev_alloc(ctx, &S.stage, kSpillStage * n4))) return st;
+        RP_CUDA(ctx, cudaMemset(S.stage, 0, kSpillStage * n4 * sizeof(float)));
         void *p = nullptr;
-        RP_CUDA(ctx, cudaHostAlloc(&p, bytes, cudaHostAllocDefault));
-        S.host = static_cast<float2 *>(p);
-        std::memset(p, 0, bytes);
+        RP_CUDA(ctx, cudaHostAlloc(&p, (size_t)ctx->spill_hd * n4 * sizeof(float), cudaHostAllocDefault));
+        S.host = static_cast<float *>(p);
+        std::memset(p, 0, (size_t)ctx->spill_hd * n4 * sizeof(float));
+    }
+    int plane0 = 0, tile0 = 0;
+    for (SpillWindow &W : ctx->spill_wins) {
+        const FwdRing &R = ctx->fwd[W.ring];
+        const size_t elems = (size_t)W.depth * R.slot_elems;
+        const size_t n4 = 4 * (size_t)ctx->doms[R.src].N;
+        if ((st = dev_alloc(ctx, &W.dev, elems)) || (st = dev_alloc(ctx, &W.raw, 2 * n4))) return st;
+        RP_CUDA(ctx, cudaMemset(W.dev, 0, elems * sizeof(float2)));
+        FwdRing F = R;            // same sizes, twiddles and scratch (the passes run on the context stream)
+        F.src = (int)ctx->wfwd.size() % kMaxDomains;   // its input's slot in a launch's pointer table
+        F.depth = W.depth;
+        F.ring = W.dev;
+        F.far_x = nullptr;
+        F.far_ks = 0;
+        F.plane0 = plane0;
+        F.tile0 = tile0;
+        plane0 += 4 * F.nz;
+        tile0 += F.kx * ((F.ay.M + kTileY - 1) / kTileY);
+        ctx->wfwd.push_back(F);
     }
     RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_out, cudaStreamNonBlocking));
     RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_in, cudaStreamNonBlocking));
     auto event = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
     RP_CUDA(ctx, event(&ctx->sp_pushed));
     RP_CUDA(ctx, event(&ctx->sp_in));
-    RP_CUDA(ctx, event(&ctx->sp_mac[0]));
-    RP_CUDA(ctx, event(&ctx->sp_mac[1]));
-    ctx->sp_out.assign(ctx->spill_dd, nullptr);
+    RP_CUDA(ctx, event(&ctx->sp_wfft));
+    ctx->sp_out.assign(kSpillStage, nullptr);
     for (cudaEvent_t &e : ctx->sp_out) RP_CUDA(ctx, event(&e));
     return RP_OK;
 }
@@ -1057,11 +1082,10 @@ rp_status rp_finalize(rp_ctx *ctx)
     std::map<std::pair<int, std::array<int, 3>>, int> ring_of;
     std::vector<std::pair<int, std::array<int, 3>>> ring_keys;
     std::vector<int> ring_depth;
-    std::vector<char> ring_spilled;
     // history spill: a spilled pair's lags leave the device ring's depth
-    // alone; rings with a spilled pair all take one device depth (their own
-    // lags plus slack) and one host depth
-    std::vector<char> pair_spilled(ctx->pairs.size(), 0);
+    // alone (its window ring holds them); the history depth then applies to
+    // the host ring of a spilled source, and to the device rings of the others
+    std::vector<char> pair_spilled(ctx->pairs.size(), 0), src_spilled(nd, 0);
     int host_depth = ctx->cfg.history_depth;
     for (int s = 0; s < nd; ++s)
         for (int t = 0; t < nd; ++t) {
@@ -1072,26 +1096,26 @@ rp_status rp_finalize(rp_ctx *ctx)
             if (it == ring_of.end()) {
                 ring_of[key] = (int)ring_keys.size();
                 ring_keys.push_back(key);
-                ring_depth.push_back(ctx->spill ? 1 : std::max(ctx->cfg.history_depth, 1));
-                ring_spilled.push_back(0);
+                ring_depth.push_back(1);
                 it = ring_of.find(key);
             }
             if (ctx->spill && spill_window(p.lag_lo, p.lag_hi)) {
                 pair_spilled[(size_t)t * nd + s] = 1;
-                ring_spilled[it->second] = 1;
+                src_spilled[s] = 1;
                 host_depth = std::max(host_depth, p.lag_hi + 1);
                 continue;
             }
             ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1);
         }
-    if (ctx->spill) {
-        for (size_t r = 0; r < ring_keys.size(); ++r)
-            if (ring_spilled[r]) ctx->spill_dd = std::max(ctx->spill_dd, ring_depth[r] + kSpillSlack);
-        for (size_t r = 0; r < ring_keys.size(); ++r)
-            if (ring_spilled[r]) ring_depth[r] = ctx->spill_dd;
-            else ring_depth[r] = std::max(ring_depth[r], ctx->cfg.history_depth);
-        ctx->spill_hd = host_depth;
-    }
+    for (size_t r = 0; r < ring_keys.size(); ++r)
+        if (!src_spilled[ring_keys[r].first]) ring_depth[r] = std::max(ring_depth[r], ctx->cfg.history_depth);
+    for (int s = 0; s < nd; ++s)
+        if (src_spilled[s]) {
+            ctx->spill_srcs.push_back({s, nullptr, nullptr});
+            ctx->host_bytes += (long long)host_depth * 16 * ctx->doms[s].N;
+            ctx->spectral_bytes += (long long)kSpillStage * 16 * ctx->doms[s].N;
+        }
+    ctx->spill_hd = host_depth;
     // order rings by (kernel size class, source): each class is one launch
     std::vector<int> ring_order(ring_keys.size());
     for (size_t r = 0; r < ring_keys.size(); ++r) ring_order[r] = (int)r;
@@ -1125,10 +1149,6 @@ rp_status rp_finalize(rp_ctx *ctx)
         tw[m[0]]; tw[m[1]]; tw[m[2]];
         ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
         ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
-        if (ctx->spill && ring_spilled[r]) {
-            ctx->spill_rings.push_back({(int)i, nullptr});
-            ctx->host_bytes += (long long)ctx->spill_hd * R.slot_elems * (long long)sizeof(float2);
-        }
         ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(R.ny, R.ax));
         ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
         const int cls = ring_class(r);
@@ -1175,11 +1195,13 @@ rp_status rp_finalize(rp_ctx *ctx)
                     }
                     if (win < 0) {
                         win = (int)ctx->spill_wins.size();
-                        int sr = 0;
-                        while (ctx->spill_rings[sr].ring != ring) ++sr;
-                        const SpillWindow W{ring, sr, p.lag_lo, p.lag_hi, p.lag_hi - p.lag_lo + 2, nullptr, -1};
+                        int ss = 0;
+                        while (ctx->spill_srcs[ss].dom != s) ++ss;
+                        const SpillWindow W{ring, ss, p.lag_lo, p.lag_hi, p.lag_hi - p.lag_lo + 1, nullptr, nullptr,
+                                            -1, {-1, -1}};
                         ctx->spill_wins.push_back(W);
-                        ctx->spectral_bytes += (long long)W.depth * ctx->fwd[ring].slot_elems * (long long)sizeof(float2);
+                        ctx->spectral_bytes += (long long)W.depth * ctx->fwd[ring].slot_elems * (long long)sizeof(float2) +
+                                               2LL * 16 * ctx->doms[s].N;
                     }
                 }
                 for (int lag = p.lag_lo; lag <= p.lag_hi; ++lag) eplan.push_back({t, s, lag, ring, t == s, win});
@@ -1410,6 +1432,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     for (DirectTarget &D : ctx->dtg) D.d_step = ctx->d_step;
     for (RawRing &r : ctx->raw) r.d_step = ctx->d_step;
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
+    for (FwdRing &F : ctx->wfwd) F.d_step = ctx->d_step;
+    if (!ctx->wfwd.empty() && (st = upload(ctx, &ctx->d_wfwd, ctx->wfwd))) return st;
     if ((st = upload(ctx, &ctx->d_inv, ctx->inv))) return st;
     if ((st = upload(ctx, &ctx->d_entries, ctx->entries))) return st;
     if ((st = upload(ctx, &ctx->d_dtg, ctx->dtg))) return st;
@@ -1460,10 +1484,25 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     rp_status st;
     const long long step = ctx->step;
     const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
-    // history spill: this step's spectra go to the device slot of step
-    // step - spill_dd, whose copy to the host must be done
-    if (!ctx->spill_rings.empty() && step >= ctx->spill_dd)
-        RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_out[step % ctx->spill_dd], 0));
+    // history spill: the slices of spilled sources into the staging slot of
+    // step - kSpillStage, once its copy to the host is done
+    bool staged_wait = false;
+    for (const SpillSource &S : ctx->spill_srcs) {
+        if (S.dom < d0 || S.dom >= d1) continue;
+        if (!staged_wait && step >= kSpillStage)
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_out[step % kSpillStage], 0));
+        staged_wait = true;
+        const long long N = ctx->doms[S.dom].N;
+        float *dst = S.stage + (size_t)(step % kSpillStage) * 4 * N;
+        if (in.J[S.dom] == in.rho[S.dom] + N) {   // one [4][N] buffer
+            RP_CUDA(ctx, cudaMemcpyAsync(dst, in.rho[S.dom], 4 * N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+        } else {
+            RP_CUDA(ctx, cudaMemcpyAsync(dst, in.rho[S.dom], N * sizeof(float), cudaMemcpyDeviceToDevice, ctx->stream));
+            RP_CUDA(ctx, cudaMemcpyAsync(dst + N, in.J[S.dom], 3 * N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                         ctx->stream));
+        }
+    }
     // raw ring
     int blk = ctx->raw_block0[d1] - ctx->raw_block0[d0];
     if (blk > 0) {
@@ -1580,95 +1619,144 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
 
 extern "C" {
 
-// History spill, once a round's pushes are queued: copy the round's spectra
-// of the spilled rings into their host rings (spill_out waits for the
-// kernels that wrote them, and for the copies into the windows queued so far,
-// the last readers of the host slot it overwrites).
+// History spill, once a round's pushes are queued: the round's staged slices
+// of the spilled sources into their host rings (spill_out waits for the
+// staging copies, and for the copies out of the host ring queued so far, the
+// last readers of the host slot it overwrites).
 static rp_status spill_round_done(rp_ctx *ctx)
 {
-    if (ctx->spill_rings.empty() || ctx->npushed != (int)ctx->doms.size()) return RP_OK;
+    if (ctx->spill_srcs.empty() || ctx->npushed != (int)ctx->doms.size()) return RP_OK;
     const long long l = ctx->step;
     RP_CUDA(ctx, cudaEventRecord(ctx->sp_pushed, ctx->stream));
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_pushed, 0));
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_in, 0));
-    for (const SpillRing &S : ctx->spill_rings) {
-        const FwdRing &R = ctx->fwd[S.ring];
-        RP_CUDA(ctx, cudaMemcpyAsync(S.host + (size_t)(l % ctx->spill_hd) * R.slot_elems,
-                                     R.ring + (size_t)(l % ctx->spill_dd) * R.slot_elems,
-                                     (size_t)R.slot_elems * sizeof(float2), cudaMemcpyDeviceToHost, ctx->spill_out));
+    for (const SpillSource &S : ctx->spill_srcs) {
+        const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
+        RP_CUDA(ctx, cudaMemcpyAsync(S.host + (size_t)(l % ctx->spill_hd) * n4, S.stage + (size_t)(l % kSpillStage) * n4,
+                                     n4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->spill_out));
     }
-    RP_CUDA(ctx, cudaEventRecord(ctx->sp_out[l % ctx->spill_dd], ctx->spill_out));
+    RP_CUDA(ctx, cudaEventRecord(ctx->sp_out[l % kSpillStage], ctx->spill_out));
     return RP_OK;
 }
 
-// History spill: the host slot of step j into window W's slot j % depth.
-static rp_status spill_copy_in(rp_ctx *ctx, const SpillWindow &W, long long j)
+// History spill: the host slice of step j into input buffer j % 2 of window
+// W on spill_in (the caller has made spill_in wait for the copy out of j and
+// for the buffer's last reader, and records sp_in after).
+static rp_status spill_raw_in(rp_ctx *ctx, SpillWindow &W, long long j)
 {
-    const long long n = ctx->fwd[W.ring].slot_elems;
-    RP_CUDA(ctx, cudaMemcpyAsync(W.dev + (size_t)(j % W.depth) * n,
-                                 ctx->spill_rings[W.sr].host + (size_t)(j % ctx->spill_hd) * n,
-                                 (size_t)n * sizeof(float2), cudaMemcpyHostToDevice, ctx->spill_in));
+    const SpillSource &S = ctx->spill_srcs[W.ss];
+    const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
+    RP_CUDA(ctx, cudaMemcpyAsync(W.raw + (size_t)(j & 1) * n4, S.host + (size_t)(j % ctx->spill_hd) * n4,
+                                 n4 * sizeof(float), cudaMemcpyHostToDevice, ctx->spill_in));
+    W.raw_step[j & 1] = j;
     return RP_OK;
 }
 
-// History spill, before the MAC of step l: every window must hold source
-// steps l - hi .. l - lo (clamped at 0 under RP_FLAG_GROUND_STATE_CLAMP).
-// Normally the previous evaluation fetched them ahead; what is missing (the
-// first steps, skipped evaluations, a loaded state) is copied here, after the
-// copies out up to step l and the last MAC.  The MAC then waits for sp_in.
-// The newly written slots j % depth held steps at least depth = B + 1 before
-// j, which no MAC from step l on reads.
+// History spill: the forward passes of windows [w0, w1) (one size class,
+// fewer than kMaxDomains of them), each on the slice of step j in its input
+// buffer j % 2, into slot j % B of its ring.
+static rp_status spill_transform(rp_ctx *ctx, int w0, int w1, long long j)
+{
+    rp_status st;
+    IoPtrs in{};
+    for (int w = w0; w < w1; ++w) {
+        const SpillWindow &W = ctx->spill_wins[w];
+        const long long Ns = ctx->doms[ctx->spill_srcs[W.ss].dom].N;
+        const FwdRing &F = ctx->wfwd[w];
+        in.rho[F.src] = W.raw + (size_t)(j & 1) * 4 * Ns;
+        in.J[F.src] = in.rho[F.src] + Ns;
+    }
+    const FwdRing &F0 = ctx->wfwd[w0], &F1 = ctx->wfwd[w1 - 1];
+    const int cls = size_class(F0.ax, F0.ay, F0.az);
+    const int planes = F1.plane0 + 4 * F1.nz - F0.plane0;
+    const int tiles = F1.tile0 + F1.kx * ((F1.ay.M + kTileY - 1) / kTileY) - F0.tile0;
+    if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "window forward plane pass", [&] {
+             return launch_fwd_plane(cls, ctx->d_wfwd, in, w0, w1, F0.plane0, planes, ctx->smem_plane, 0, ctx->stream);
+         })))
+        return st;
+    return timed_launch(ctx, RP_K_FWD_COLUMN, "window forward column pass", [&] {
+        return launch_fwd_column(cls, ctx->d_wfwd, w0, w1, F0.tile0, tiles, ctx->smem_col, j, ctx->stream);
+    });
+}
+
+// History spill, before the MAC of step l: every window must hold the
+// spectra of source steps l - hi .. l - lo (clamped at 0 under
+// RP_FLAG_GROUND_STATE_CLAMP).  Normally each window lacks only step l - lo,
+// whose slice was fetched during the previous step: then one pair of forward
+// passes per run of windows of one size class and one such step transforms
+// them into the windows' rings, on the context stream where the MAC reads
+// them (slot j % B held step j - B < l - hi, which this and later MACs do not
+// read).  Otherwise (the first steps, skipped evaluations, a loaded state)
+// the missing steps go one at a time: slice in, transform.  Then each
+// window's slice for step l + 1 (j = l + 1 - lo <= l - 3, as a spilled window
+// has lo >= 4) is fetched, after the copy out of step l - 1 and the last
+// transform (the reader of its buffer), to arrive under this step's
+// remaining kernels.
 static rp_status spill_fetch(rp_ctx *ctx)
 {
-    if (ctx->spill_rings.empty()) return RP_OK;
+    if (ctx->spill_srcs.empty()) return RP_OK;
     const long long l = ctx->step;
-    bool any = false;
+    const int nw = (int)ctx->spill_wins.size();
     rp_status st;
-    for (SpillWindow &W : ctx->spill_wins) {
+    std::vector<long long> next(nw, -1);   // the one step a window lacks, or -1
+    bool steady = true;
+    for (int w = 0; w < nw; ++w) {
+        const SpillWindow &W = ctx->spill_wins[w];
         long long a = l - W.hi, b = l - W.lo;
         if (ctx->clamp) { a = std::max(a, 0LL); b = std::max(b, 0LL); }
         if (a < 0) return fail(ctx, RP_ERR_HISTORY, "spilled window before the first push");
         const long long from = std::max(a, W.have + 1);
         if (from > b) continue;
-        if (!any) {
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[l % ctx->spill_dd], 0));
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_mac[ctx->sp_mac_next ^ 1], 0));
-            any = true;
-        }
-        for (long long j = from; j <= b; ++j)
-            if ((st = spill_copy_in(ctx, W, j))) return st;
-        W.have = b;
+        if (from == b && W.raw_step[b & 1] == b) next[w] = b;
+        else steady = false;
     }
-    if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
-    return RP_OK;
-}
-
-// History spill, after the MAC of step l: mark it, then fetch the one source
-// step each window adds at step l + 1, j = l + 1 - lo (<= l - 3, as a spilled
-// window has lo >= 4), so that the copy runs under this step's remaining
-// kernels.  It waits for the copy out of step l - 1 (which follows that of
-// j on spill_out) and for the MAC before this one: slot j % depth held step
-// j - (B + 1) = l - hi - 1, which only MACs up to step l - 1 read.
-static rp_status spill_after_mac(rp_ctx *ctx)
-{
-    if (ctx->spill_rings.empty()) return RP_OK;
-    const long long l = ctx->step;
-    RP_CUDA(ctx, cudaEventRecord(ctx->sp_mac[ctx->sp_mac_next], ctx->stream));
-    ctx->sp_mac_next ^= 1;
+    if (steady) {
+        bool any = false;
+        for (int w = 0; w < nw;) {
+            if (next[w] < 0) { ++w; continue; }
+            if (!any) RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
+            any = true;
+            const FwdRing &F = ctx->wfwd[w];
+            const int cls = size_class(F.ax, F.ay, F.az);
+            int w1 = w + 1;
+            while (w1 < nw && w1 - w < kMaxDomains && next[w1] == next[w] &&
+                   size_class(ctx->wfwd[w1].ax, ctx->wfwd[w1].ay, ctx->wfwd[w1].az) == cls)
+                ++w1;
+            if ((st = spill_transform(ctx, w, w1, next[w]))) return st;
+            for (int v = w; v < w1; ++v) ctx->spill_wins[v].have = next[w];
+            w = w1;
+        }
+        if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
+    } else {
+        for (int w = 0; w < nw; ++w) {
+            SpillWindow &W = ctx->spill_wins[w];
+            long long a = l - W.hi, b = l - W.lo;
+            if (ctx->clamp) { a = std::max(a, 0LL); b = std::max(b, 0LL); }
+            for (long long j = std::max(a, W.have + 1); j <= b; ++j) {
+                if (W.raw_step[j & 1] != j) {
+                    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[l % kSpillStage], 0));
+                    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_wfft, 0));
+                    if ((st = spill_raw_in(ctx, W, j))) return st;
+                    RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
+                }
+                RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
+                if ((st = spill_transform(ctx, w, w + 1, j))) return st;
+                RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
+                W.have = j;
+            }
+        }
+    }
     if (l < 1) return RP_OK;
     bool any = false;
-    rp_status st;
     for (SpillWindow &W : ctx->spill_wins) {
         const long long j = l + 1 - W.lo;
-        if (j < 0 || j != W.have + 1) continue;
+        if (j < 0 || j != W.have + 1 || W.raw_step[j & 1] == j) continue;
         if (!any) {
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[(l - 1) % ctx->spill_dd], 0));
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_mac[ctx->sp_mac_next], 0));
-            any = true;
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[(l - 1) % kSpillStage], 0));
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_wfft, 0));
         }
-        if ((st = spill_copy_in(ctx, W, j))) return st;
-        W.have = j;
+        any = true;
+        if ((st = spill_raw_in(ctx, W, j))) return st;
     }
     if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
     return RP_OK;
@@ -1717,10 +1805,12 @@ static rp_status split_round_done(rp_ctx *ctx)
         RP_CUDA(ctx, cudaMemsetAsync(R.ring, 0, R.slot_elems * sizeof(float2), ctx->stream));   // slot of step 0
     for (const RawRing &r : ctx->raw)
         if (r.ring) RP_CUDA(ctx, cudaMemsetAsync(r.ring, 0, 4 * r.n * sizeof(float), ctx->stream));
-    // history spill: the host copy of step 0 becomes zero too, and the
-    // windows fetch it again
+    // history spill: the staged and host slices of step 0 become zero too,
+    // and the windows fetch them again
+    for (const SpillSource &S : ctx->spill_srcs)
+        RP_CUDA(ctx, cudaMemsetAsync(S.stage, 0, 16 * (size_t)ctx->doms[S.dom].N, ctx->stream));
     if ((st = spill_round_done(ctx))) return st;
-    for (SpillWindow &W : ctx->spill_wins) W.have = -1;
+    for (SpillWindow &W : ctx->spill_wins) W.have = W.raw_step[0] = W.raw_step[1] = -1;
     ctx->static_done = true;
     return RP_OK;
 }
@@ -1884,7 +1974,6 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
              })))
             return st;
     }
-    if ((st = spill_after_mac(ctx))) return st;
     if (!ctx->lpairs.empty()) {
         // learned pairs: network rows, network, node values into the coefficients
         if ((st = timed_launch(ctx, RP_K_LEARNED, "learned far field", [&] {
@@ -2339,7 +2428,7 @@ rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *
     for (int d = 0; d < nd; ++d)
         if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
     if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || !ctx->lpairs.empty() ||
-        (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_rings.empty())
+        (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_srcs.empty())
         return fail(ctx, RP_ERR_UNSUPPORTED,
                     "rp_graph_capture: FFT and direct pairs only, without profiling, split or history spill");
     if (ctx->step >= 0 && ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_graph_capture inside a partially pushed step");
@@ -2530,7 +2619,7 @@ unsigned long long layout_hash(const rp_ctx *ctx)
     mix(&ctx->split, sizeof(bool));
     for (const FwdRing &R : ctx->fwd) { mix(&R.depth, sizeof(int)); mix(&R.slot_elems, sizeof(long long)); }
     for (const RawRing &r : ctx->raw) { mix(&r.depth, sizeof(int)); mix(&r.n, sizeof(long long)); }
-    for (const SpillRing &S : ctx->spill_rings) mix(&S.ring, sizeof(int));
+    for (const SpillSource &S : ctx->spill_srcs) mix(&S.dom, sizeof(int));
     mix(&ctx->spill_hd, sizeof(int));
     return h;
 }
@@ -2551,9 +2640,12 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
         const size_t bytes = 4 * (size_t)ctx->doms[d].N * sizeof(float);
         if ((st = fn((void *)ctx->ground[d], bytes)) || (st = fn((void *)ctx->pstatic[d], bytes))) return st;
     }
-    // the spilled history (pinned host memory); the window rings are fetched again
-    for (const SpillRing &S : ctx->spill_rings)
-        if ((st = fn((void *)S.host, (size_t)ctx->spill_hd * ctx->fwd[S.ring].slot_elems * sizeof(float2)))) return st;
+    // the spilled history: staged slices (device) and the host rings; the
+    // windows are fetched again
+    for (const SpillSource &S : ctx->spill_srcs) {
+        const size_t bytes = 16 * (size_t)ctx->doms[S.dom].N;
+        if ((st = fn((void *)S.stage, kSpillStage * bytes)) || (st = fn((void *)S.host, ctx->spill_hd * bytes))) return st;
+    }
     return RP_OK;
 }
 
@@ -2624,7 +2716,7 @@ rp_status rp_load_state(rp_ctx *ctx, const char *path)
     });
     std::fclose(f);
     if (st) return st;
-    for (SpillWindow &W : ctx->spill_wins) W.have = -1;
+    for (SpillWindow &W : ctx->spill_wins) W.have = W.raw_step[0] = W.raw_step[1] = -1;
     ctx->step = step;
     ctx->npushed = npushed;
     ctx->static_done = step > 0 || (step == 0 && npushed == nd);   // P(0) came with the state
@@ -2657,12 +2749,12 @@ void rp_destroy(rp_ctx *ctx)
             cudaStreamSynchronize(ctx->spill_out);
             cudaStreamSynchronize(ctx->spill_in);
             for (cudaEvent_t e : ctx->sp_out) if (e) cudaEventDestroy(e);
-            for (cudaEvent_t e : {ctx->sp_pushed, ctx->sp_in, ctx->sp_mac[0], ctx->sp_mac[1]})
+            for (cudaEvent_t e : {ctx->sp_pushed, ctx->sp_in, ctx->sp_wfft})
                 if (e) cudaEventDestroy(e);
             cudaStreamDestroy(ctx->spill_out);
             if (ctx->spill_in) cudaStreamDestroy(ctx->spill_in);
         }
-        for (const SpillRing &S : ctx->spill_rings) if (S.host) cudaFreeHost(S.host);
+        for (const SpillSource &S : ctx->spill_srcs) if (S.host) cudaFreeHost(S.host);
         for (const ProfRec &r : ctx->pending) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
         for (cudaEvent_t e : ctx->spare_events) cudaEventDestroy(e);
         for (void *p : ctx->allocs) cudaFree(p);

@@ -225,11 +225,13 @@ def test_ground_split_refuses_far_pairs():
 
 def test_history_spill_plan():
     """RP_FLAG_HISTORY_SPILL on the 2 x 48^3 workload (cross lags 290..294):
-    each cross pair reads a 6-slot window ring (B + 1), the spectral rings keep
-    the self lags 0..3 plus two slots, and the 320-step history moves to a
-    pinned host ring.  A neighbouring pair (lags from 0) stays on the device."""
+    each cross pair reads a 5-slot window ring (B), the spectral rings keep
+    only the self lags 0..3, and the 320-step history moves to a pinned host
+    ring of (rho, J) slices.  A neighbouring pair (lags from 0) stays on the
+    device."""
     w = synth.workload("cfg2")
     slot = 4 * 49 * 96 * 96 * 8
+    sl = 16 * 48 ** 3                      # one (rho, J) slice
     ctx = rp.rp_create(w.c, w.dt, w.history, flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_HISTORY_SPILL)
     try:
         for d in w.domains:
@@ -237,9 +239,10 @@ def test_history_spill_plan():
         rp.rp_finalize(ctx)
         q = rp.rp_query(ctx)
         assert q["spill_windows"] == 2
-        assert q["spectral_depth"] == 4 + 2
-        assert q["spectral_bytes"] == 2 * (6 + 6) * slot
-        assert q["host_bytes"] == 2 * w.history * slot
+        assert q["spectral_depth"] == 4
+        # per source: ring 4 + window 5 spectra, 2 window input and 3 staging slices
+        assert q["spectral_bytes"] == 2 * ((4 + 5) * slot + (2 + 3) * sl)
+        assert q["host_bytes"] == 2 * w.history * sl
         assert rp.rp_pair_info(ctx, 0, 1)["lag_lo"] == 290   # the pair plan itself is unchanged
     finally:
         rp.rp_destroy(ctx)

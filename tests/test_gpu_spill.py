@@ -2,11 +2,12 @@
 
 Sec. IV keeps every sample of [l - N_R,max, l] while a step reads only each
 pair's Delta N_R of them.  With the flag, a pair whose lag window starts far
-back reads its source spectra from a small device window ring that two copy
-streams keep filled from a pinned host copy of the history.  The kernels and
-their summation order do not change, so the spilled context must reproduce
-the unspilled one bit for bit, whatever the call pattern (per-domain pushes,
-skipped evaluations, the ground-state split, a saved and reloaded state).
+back reads its source spectra from a small device window ring; the source's
+(rho, J) slices go to a pinned host ring and come back, one a step, through
+the same forward passes as a push.  The kernels and their summation order do
+not change, so the spilled context must reproduce the unspilled one bit for
+bit, whatever the call pattern (per-domain pushes, skipped evaluations, the
+ground-state split, a saved and reloaded state).
 """
 import os
 import tempfile
@@ -25,7 +26,7 @@ SPLIT = rp.RP_FLAG_GROUND_STATE_SPLIT
 
 
 def two_far():
-    """2 x 16^3 at 205 bohr: cross lags 29..31 (window ring of 4 slots)."""
+    """2 x 16^3 at 205 bohr: cross lags 29..31 (window ring of 3 slots)."""
     return synth.two_domain(16, 0.25, 205.0)
 
 
