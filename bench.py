@@ -70,6 +70,16 @@ def parse():
 
 DEEP = ("cfg3", "cfg4x8", "cfg5", "cfg5x8")
 
+# The direct sum's arithmetic per (target node, source node) pair: the offset
+# (3 subtractions) and R^2 (one multiply, two FMAs: 5 flops), rsqrt, tau (two
+# multiplies), floor and the hat weight (one subtraction), the 1/R volume
+# factor (one multiply); per field the hat interpolation (one subtraction, one
+# FMA: 3 flops), the scaling (one multiply) and the accumulation (one add),
+# 5 flops x 4 fields.  Kahan compensation (3 more adds per field) is not
+# counted: it is accuracy, not the sum.
+DIRECT_FLOPS_PER_PAIR_POINT = 3 + 5 + 1 + 2 + 2 + 1 + 4 * 5     # = 34
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12              # 80.6
+
 
 def get_workload(name):
     if name == "cfg5x8":
@@ -531,9 +541,20 @@ def run_ours(args, rank, world, local):
             b.record(stream)
             torch.cuda.synchronize()
             pms = a.elapsed_time(b) / nplain
+            # ALU roofline of the direct sum: pair-points per step (every
+            # target node against every source node), 32 algorithmic flops
+            # each, against the FP32 pipes' peak at the SM clock
+            pp = sum(t.N for t in w.domains) * sum(s_.N for s_ in w.domains)
+            achieved = pp * DIRECT_FLOPS_PER_PAIR_POINT / (pms * 1e-3) / 1e12
             plain = {"path": "direct FP32 retarded sum, every pair (Kahan-compensated)",
                      "value": w.points / (pms / 1e3), "unit": UNIT, "ms_per_step": pms, "steps": nplain,
-                     "speedup_of_ours": (w.points / (ms / K / 1e3)) / (w.points / (pms / 1e3))}
+                     "speedup_of_ours": (w.points / (ms / K / 1e3)) / (w.points / (pms / 1e3)),
+                     "pair_points_per_s": pp / (pms * 1e-3),
+                     "roofline": {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS,
+                                  "unit": "TFLOP/s", "frac": achieved / FP32_PEAK_TFLOPS,
+                                  "flops_per_pair_point": DIRECT_FLOPS_PER_PAIR_POINT,
+                                  "peak_source": "152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2070 MHz: nominal "
+                                                 "unit counts at the maximum SM clock (derived, not measured)"}}
 
     # ---- end to end through the C-ABI with host buffers
     e2e = None
