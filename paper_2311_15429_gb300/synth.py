@@ -211,7 +211,9 @@ class Workload:
         return sum(d.N for d in self.domains)
 
 
-def _sources(domains: Sequence[Domain], seed: int = SOURCE_SEED) -> List[GaussianSources]:
+def seeded_sources(domains: Sequence[Domain], seed: int = SOURCE_SEED) -> List[GaussianSources]:
+    """Three random Gaussians per domain (``random_gaussians``), each domain
+    drawing from its own child of one seed sequence."""
     ss = np.random.SeedSequence(seed)
     return [random_gaussians(d, np.random.default_rng(s))
             for d, s in zip(domains, ss.spawn(len(domains)))]
@@ -233,7 +235,7 @@ def two_domain(n: int, h: float, distance: float, name: str = "custom", steps: i
     doms = [cubic((-distance / 2, 0.0, 0.0), n, h),
             cubic((distance / 2, offset[0], offset[1]), n, h)]
     return Workload(name, doms, c, dt, history, steps,
-                    f"2 x {n}^3, h={h}, {distance} bohr apart", _sources(doms))
+                    f"2 x {n}^3, h={h}, {distance} bohr apart", seeded_sources(doms))
 
 
 @dataclass
@@ -278,7 +280,7 @@ def split_geometry(W: int, L: int, d: int, h: float, seed: int = SOURCE_SEED) ->
         raise ValueError("the sub-domains must not overlap: need 2W <= d")
     subs = [Domain((0.0, 0.0, 0.0), (W, W, L), h), Domain((h * (d - W), 0.0, 0.0), (W, W, L), h)]
     enclosing = Domain((0.0, 0.0, 0.0), (d, W, L), h)
-    return SplitGeometry(W, L, d, h, subs, enclosing, _sources(subs, seed))
+    return SplitGeometry(W, L, d, h, subs, enclosing, seeded_sources(subs, seed))
 
 
 def workload(name: str) -> Workload:
@@ -305,19 +307,19 @@ def workload(name: str) -> Workload:
         cs = _scatter_centres(8, 20000.0, 100.0, rng)
         doms = [cubic(c, 64, 0.25) for c in cs]
         return Workload("cfg3", doms, C_AU, 0.05, 0, 200,
-                        "8 x 64^3, h=0.25, 20000 bohr cube, min separation 100", _sources(doms))
+                        "8 x 64^3, h=0.25, 20000 bohr cube, min separation 100", seeded_sources(doms))
     if name == "cfg4":
         cs = _scatter_centres(64, 20000.0 / math.sqrt(3.0), 50.0, rng)
         ns = rng.choice([24, 32, 48, 64, 96], 64)
         hs = rng.uniform(0.2, 0.35, 64)
         doms = [cubic(c, int(n), float(h)) for c, n, h in zip(cs, ns, hs)]
         return Workload("cfg4", doms, C_AU, 0.05, 0, 500,
-                        "64 mixed domains, n in {24..96}^3, h in [0.2,0.35]", _sources(doms))
+                        "64 mixed domains, n in {24..96}^3, h in [0.2,0.35]", seeded_sources(doms))
     if name == "cfg5":
         cs = _scatter_centres(32, 50000.0 / math.sqrt(3.0), 500.0, rng)
         doms = [cubic(c, 48, 0.25) for c in cs]
         return Workload("cfg5", doms, C_AU, 0.05, 0, 1000,
-                        "32 x 48^3, 500-50000 bohr apart", _sources(doms))
+                        "32 x 48^3, 500-50000 bohr apart", seeded_sources(doms))
     raise KeyError(name)
 
 

@@ -19,7 +19,7 @@ TOL = 1e-3
 def _setup():
     doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.25), synth.cubic((8.0, 0.5, -0.3), 12, 0.25),
             synth.cubic((600.0, 50.0, -30.0), 12, 0.25)]
-    return doms, synth._sources(doms)
+    return doms, synth.seeded_sources(doms)
 
 
 def _run(doms, hists, eval_at, batch=16):

@@ -139,7 +139,7 @@ def _far_setup(n=16, dist=3000.0):
     from paper_2311_15429_gb300 import synth
     doms = [synth.cubic((0.0, 0.0, 0.0), n, 0.25), synth.cubic((8.0, 0.5, -0.3), n, 0.25),
             synth.cubic((dist * 0.6, dist * 0.48, -dist * 0.64), n, 0.25)]
-    return doms, synth._sources(doms)
+    return doms, synth.seeded_sources(doms)
 
 
 def _run_far(doms, hists, train, **kw):
@@ -241,7 +241,7 @@ def test_learned_pairs_beside_low_rank_pairs():
     dev = torch.device("cuda", 0)
     doms = [synth.cubic((0.0, 0.0, 0.0), 16, 0.25), synth.cubic((1000.0, 0.0, 0.0), 16, 0.25),
             synth.cubic((300.0, 2600.0, -500.0), 16, 0.25), synth.cubic((-2400.0, 900.0, 1700.0), 16, 0.25)]
-    srcs = synth._sources(doms)
+    srcs = synth.seeded_sources(doms)
     with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=500.0,
                                far_batch=16) as lib:
         rep = lib.train_far_model(2000.0)

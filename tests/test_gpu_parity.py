@@ -47,7 +47,7 @@ def test_ragged_grids_fft():
     """Non-cubic, unequal grids (FFT sizes 12/16/... with ragged tails)."""
     doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3),
             synth.Domain((-2.0, 4.0, 1.5), (11, 3, 13), 0.3)]
-    srcs = synth._sources(doms)
+    srcs = synth.seeded_sources(doms)
     hists = histories(srcs, 0, 12, 0.05)
     res = run_library(doms, synth.C_AU, 0.05, hists, 0, [10, 11])
     _score(doms, hists, 0, synth.C_AU, 0.05, res)
@@ -58,7 +58,7 @@ def test_mixed_spacing_direct_fallback():
     the FFT result of the target's other pairs."""
     doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.3), synth.cubic((9.0, 2.0, -1.0), 10, 0.25),
             synth.cubic((-8.0, 0.0, 3.0), 9, 0.3)]
-    srcs = synth._sources(doms)
+    srcs = synth.seeded_sources(doms)
     hists = histories(srcs, 0, 16, 0.05)
     res = run_library(doms, synth.C_AU, 0.05, hists, 0, [15], push="each")
     _score(doms, hists, 0, synth.C_AU, 0.05, res)
@@ -67,7 +67,7 @@ def test_mixed_spacing_direct_fallback():
 def test_slow_light_many_lags():
     """c = 5 a.u.: every pair spans tens of delay bins."""
     doms = [synth.cubic((0.0, 0.0, 0.0), 10, 0.3), synth.cubic((6.0, 1.0, 0.0), 10, 0.3)]
-    srcs = synth._sources(doms)
+    srcs = synth.seeded_sources(doms)
     c, dt = 5.0, 0.05
     hists = histories(srcs, 0, 60, dt)
     res = run_library(doms, c, dt, hists, 0, [58, 59])

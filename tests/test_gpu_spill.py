@@ -36,7 +36,7 @@ def three_mixed():
     doms = [synth.cubic((-100.0, 0.0, 0.0), 16, 0.25), synth.cubic((-92.0, 0.5, 0.0), 16, 0.25),
             synth.cubic((105.0, 0.0, -0.5), 16, 0.25)]
     return synth.Workload("three", doms, synth.C_AU, 0.05, 0, 8, "3 x 16^3, near pair + far domain",
-                          synth._sources(doms))
+                          synth.seeded_sources(doms))
 
 
 def query(w, flags):

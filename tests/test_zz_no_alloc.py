@@ -34,7 +34,7 @@ def test_noalloc_matches_evaluate_host_on_two_calls(geometry):
         doms, srcs, c, dt = w.domains, w.sources, w.c, w.dt
     else:   # an FFT-path target with a direct-path pair added onto it
         doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.3), synth.cubic((9.0, 2.0, -1.0), 10, 0.25)]
-        srcs, c, dt = synth._sources(doms), synth.C_AU, 0.05
+        srcs, c, dt = synth.seeded_sources(doms), synth.C_AU, 0.05
     T = 12
     hists = [s.history(0, T, dt) for s in srcs]
     ctx = rp.rp_create(c, dt)
