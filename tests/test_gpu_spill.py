@@ -170,3 +170,38 @@ def test_spill_state_round_trip_and_graph_refusal():
             for d in range(2):
                 np.testing.assert_array_equal(phi[d].cpu().numpy(), want[n][d][0])
                 np.testing.assert_array_equal(A[d].cpu().numpy(), want[n][d][1])
+
+
+def test_spill_double_evaluation_and_profiling():
+    """Evaluating a step twice fetches nothing the second time and gives the
+    same result; under RP_FLAG_PROFILE the window transforms are timed and
+    counted with the forward passes, and the results do not change."""
+    import torch
+    dev = torch.device("cuda", 0)
+    w = two_far()
+    L = query(w, SPILL)["max_lag"]
+    T = L + 8
+    hists = histories(w.sources, 0, T, w.dt)
+    ref = run_library(w.domains, w.c, w.dt, hists, 0, range(L, T))
+    got = {}
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, flags=SPILL | rp.RP_FLAG_PROFILE) as lib:
+        for i in range(T):
+            lib.push_all([torch.from_numpy(np.ascontiguousarray(h[i, 0])).to(dev) for h in hists],
+                         [torch.from_numpy(np.ascontiguousarray(h[i, 1:]).reshape(-1)).to(dev) for h in hists])
+            if i < L:
+                continue
+            outs = []
+            for _ in range(2):
+                phi, A = lib.evaluate()
+                torch.cuda.synchronize()
+                outs.append([np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)])
+                             for d in range(2)])
+            for d in range(2):
+                np.testing.assert_array_equal(outs[0][d], outs[1][d])
+            got[i] = outs[1]
+        lib.sync()
+        n_push, _ = rp.rp_kernel_stats(lib.ctx, rp.RP_K_FWD_COLUMN)[:2]
+    assert_same(got, ref)
+    # T pushes, one window transform a step from the first evaluation on
+    # (its first evaluation fills each window by one transform a step of lag)
+    assert n_push >= T + (T - L)
