@@ -1621,8 +1621,8 @@ extern "C" {
 
 // History spill, once a round's pushes are queued: the round's staged slices
 // of the spilled sources into their host rings (spill_out waits for the
-// staging copies, and for the copies out of the host ring queued so far, the
-// last readers of the host slot it overwrites).
+// staging copies, and for the copies back from the host ring queued so far,
+// the last readers of the host slot it overwrites).
 static rp_status spill_round_done(rp_ctx *ctx)
 {
     if (ctx->spill_srcs.empty() || ctx->npushed != (int)ctx->doms.size()) return RP_OK;
