@@ -257,3 +257,38 @@ def test_history_spill_plan():
         assert q["spill_windows"] == 0 and q["host_bytes"] == 0
     finally:
         rp.rp_destroy(ctx)
+
+
+@pytest.mark.parametrize("distance", [6.0, 40.0, 60.0, 90.0, 205.0, 2000.0])
+def test_history_spill_follows_each_pairs_lag_window(distance):
+    """The spilled windows are exactly the FFT pairs with
+    lag_lo >= 2 (lag_hi - lag_lo + 2), one per (source ring, window); the
+    spectral bytes drop by the unspilled depth the rings no longer need; the
+    host ring holds max(history_depth, largest spilled lag_hi + 1) slices of
+    each spilled source."""
+    w = synth.two_domain(16, 0.25, distance)
+    flags = rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_HISTORY_SPILL
+    ctx = rp.rp_create(w.c, w.dt, 0, rp.RP_MODE_FFT, flags)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        q = rp.rp_query(ctx)
+        spilled = []
+        for t in range(2):
+            for s in range(2):
+                p = rp.rp_pair_info(ctx, t, s)
+                if p["lag_lo"] >= 2 * (p["lag_hi"] - p["lag_lo"] + 2):
+                    spilled.append((t, s, p["lag_lo"], p["lag_hi"]))
+        assert q["spill_windows"] == len(spilled)
+        assert all(t != s for t, s, _, _ in spilled)
+        N = w.domains[0].N
+        if spilled:
+            hd = max(hi for _, _, _, hi in spilled) + 1
+            assert q["host_bytes"] == len({s for _, s, _, _ in spilled}) * hd * 16 * N
+            self_hi = rp.rp_pair_info(ctx, 0, 0)["lag_hi"]
+            assert q["spectral_depth"] == self_hi + 1
+        else:
+            assert q["host_bytes"] == 0
+    finally:
+        rp.rp_destroy(ctx)
