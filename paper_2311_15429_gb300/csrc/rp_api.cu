@@ -156,6 +156,13 @@ struct rp_ctx {
     std::vector<SpillWindow> spill_wins;
     std::vector<FwdRing> wfwd;
     FwdRing *d_wfwd = nullptr;
+    // the forward rings and, after those of each size class, that class's
+    // windows (lag_off = lo, inputs in pointer slots nd + w): one launch pair
+    // per class pushes a round and transforms the windows' steady-state
+    // slices (empty when the slots do not fit)
+    std::vector<FwdRing> mix;
+    FwdRing *d_mix = nullptr;
+    std::vector<LaunchGroup> mix_groups;
     long long host_bytes = 0;
     cudaStream_t spill_out = nullptr, spill_in = nullptr;
     cudaEvent_t sp_pushed = nullptr, sp_in = nullptr, sp_wfft = nullptr;
@@ -453,10 +460,13 @@ rp_status open_spill(rp_ctx *ctx)
         const size_t n4 = 4 * (size_t)ctx->doms[R.src].N;
         if ((st = dev_alloc(ctx, &W.dev, elems)) || (st = dev_alloc(ctx, &W.raw, 2 * n4))) return st;
         RP_CUDA(ctx, cudaMemset(W.dev, 0, elems * sizeof(float2)));
-        FwdRing F = R;            // same sizes, twiddles and scratch (the passes run on the context stream)
+        FwdRing F = R;            // same sizes and twiddles
         F.src = (int)ctx->wfwd.size() % kMaxDomains;   // its input's slot in a launch's pointer table
         F.depth = W.depth;
         F.ring = W.dev;
+        // its own scratch between the two passes: a push's launch may transform
+        // the window beside the ring it copies
+        if ((st = dev_alloc(ctx, &F.t1, 4ULL * F.kx * F.nz * F.ay.M))) return st;
         F.far_x = nullptr;
         F.far_ks = 0;
         F.plane0 = plane0;
@@ -473,6 +483,46 @@ rp_status open_spill(rp_ctx *ctx)
     RP_CUDA(ctx, event(&ctx->sp_wfft));
     ctx->sp_out.assign(kSpillStage, nullptr);
     for (cudaEvent_t &e : ctx->sp_out) RP_CUDA(ctx, event(&e));
+    return RP_OK;
+}
+
+// History spill: the merged descriptor table (rp_ctx::mix) from the current
+// forward rings and windows, uploaded.  Called once the forward rings'
+// descriptors are final, and again whenever they change (far factors built
+// or rebuilt later).
+rp_status build_mix(rp_ctx *ctx)
+{
+    const int nd = (int)ctx->doms.size(), nw = (int)ctx->spill_wins.size();
+    ctx->mix.clear();
+    ctx->mix_groups.clear();
+    if (nw == 0 || nd + nw > kMaxDomains) return RP_OK;
+    int p0 = 0, t0 = 0;
+    for (const LaunchGroup &g : ctx->fwd_groups) {
+        LaunchGroup m{g.cls, (int)ctx->mix.size(), 0, p0, 0, t0, 0};
+        auto add = [&](FwdRing F) {
+            F.plane0 = p0;
+            F.tile0 = t0;
+            F.d_step = ctx->d_step;
+            p0 += 4 * F.nz;
+            t0 += F.kx * ((F.ay.M + kTileY - 1) / kTileY);
+            ctx->mix.push_back(F);
+        };
+        for (int r = g.i0; r < g.i1; ++r) add(ctx->fwd[r]);
+        for (int w = 0; w < nw; ++w) {
+            FwdRing F = ctx->wfwd[w];
+            if (size_class(F.ax, F.ay, F.az) != g.cls) continue;
+            F.src = nd + w;
+            F.lag_off = ctx->spill_wins[w].lo;
+            add(F);
+        }
+        m.i1 = (int)ctx->mix.size();
+        m.blk1 = p0;
+        m.blk2_1 = t0;
+        ctx->mix_groups.push_back(m);
+    }
+    rp_status st;
+    if (!ctx->d_mix && (st = dev_alloc(ctx, &ctx->d_mix, ctx->mix.size()))) return st;
+    RP_CUDA(ctx, cudaMemcpy(ctx->d_mix, ctx->mix.data(), ctx->mix.size() * sizeof(FwdRing), cudaMemcpyHostToDevice));
     return RP_OK;
 }
 
@@ -1434,6 +1484,7 @@ rp_status rp_finalize(rp_ctx *ctx)
     if ((st = upload(ctx, &ctx->d_fwd, ctx->fwd))) return st;
     for (FwdRing &F : ctx->wfwd) F.d_step = ctx->d_step;
     if (!ctx->wfwd.empty() && (st = upload(ctx, &ctx->d_wfwd, ctx->wfwd))) return st;
+    if ((st = build_mix(ctx))) return st;
     if ((st = upload(ctx, &ctx->d_inv, ctx->inv))) return st;
     if ((st = upload(ctx, &ctx->d_entries, ctx->entries))) return st;
     if ((st = upload(ctx, &ctx->d_dtg, ctx->dtg))) return st;
@@ -1514,11 +1565,32 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
             return st;
     }
     // spectral rings of these sources: one launch pair per size class when
-    // every domain pushes, else one per ring of the pushing domain
+    // every domain pushes, else one per ring of the pushing domain.  History
+    // spill: when every window lacks just step - lo, with its slice already
+    // in, a whole round's launch pairs transform the windows too
     const int nd = (int)ctx->doms.size();
     std::vector<LaunchGroup> launches;
+    const FwdRing *rings = ctx->d_fwd;
+    IoPtrs fin = in;
+    bool merged = false;
     if (d0 == 0 && d1 == nd) {
         launches = ctx->fwd_groups;
+        merged = !ctx->mix.empty() && !ctx->capturing;
+        for (const SpillWindow &W : ctx->spill_wins) {
+            const long long j = step - W.lo;
+            merged = merged && j >= 0 && W.have == j - 1 && W.raw_step[j & 1] == j;
+        }
+        if (merged) {
+            launches = ctx->mix_groups;
+            rings = ctx->d_mix;
+            for (size_t w = 0; w < ctx->spill_wins.size(); ++w) {
+                const SpillWindow &W = ctx->spill_wins[w];
+                const long long Ns = ctx->doms[ctx->spill_srcs[W.ss].dom].N;
+                fin.rho[nd + w] = W.raw + (size_t)((step - W.lo) & 1) * 4 * Ns;
+                fin.J[nd + w] = fin.rho[nd + w] + Ns;
+            }
+            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
+        }
     } else {
         for (int r = 0; r < (int)ctx->fwd.size(); ++r) {
             const FwdRing &R = ctx->fwd[r];
@@ -1530,17 +1602,21 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     }
     for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "forward plane pass", [&] {
-                 return launch_fwd_plane(g.cls, ctx->d_fwd, in, g.i0, g.i1, g.blk0, g.blk1 - g.blk0, ctx->smem_plane,
+                 return launch_fwd_plane(g.cls, rings, fin, g.i0, g.i1, g.blk0, g.blk1 - g.blk0, ctx->smem_plane,
                                          (int)(step % std::max(1, ctx->cfg.far_batch)), ctx->stream);
              })))
             return st;
     }
     for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_COLUMN, "forward column pass", [&] {
-                 return launch_fwd_column(g.cls, ctx->d_fwd, g.i0, g.i1, g.blk2_0, g.blk2_1 - g.blk2_0,
+                 return launch_fwd_column(g.cls, rings, g.i0, g.i1, g.blk2_0, g.blk2_1 - g.blk2_0,
                                           ctx->smem_col, kstep, ctx->stream);
              })))
             return st;
+    }
+    if (merged) {
+        RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
+        for (SpillWindow &W : ctx->spill_wins) W.have = step - W.lo;
     }
     // far path: stage the slices of far sources; every far_batch steps run
     // the factor GEMM of each source and add its node values to the rings
@@ -2248,6 +2324,7 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
             if ((st = build_far(ctx, ctx->smem_optin))) return st;
             RP_CUDA(ctx, cudaMemcpy(ctx->d_fwd, ctx->fwd.data(), ctx->fwd.size() * sizeof(FwdRing),
                                     cudaMemcpyHostToDevice));
+            if ((st = build_mix(ctx))) return st;
             RP_CUDA(ctx, cudaMemcpy(ctx->d_inv, ctx->inv.data(), ctx->inv.size() * sizeof(InvTarget),
                                     cudaMemcpyHostToDevice));
         }
@@ -2399,6 +2476,7 @@ rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg_in, rp_trai
         ctx->net.out_scale = out_scale;
         RP_CUDA(ctx, cudaMemcpy(ctx->d_fwd, ctx->fwd.data(), ctx->fwd.size() * sizeof(FwdRing), cudaMemcpyHostToDevice));
         RP_CUDA(ctx, cudaMemcpy(ctx->d_inv, ctx->inv.data(), ctx->inv.size() * sizeof(InvTarget), cudaMemcpyHostToDevice));
+        if ((st = build_mix(ctx))) return st;
     }
     if (rep) *rep = report;
     return RP_OK;

@@ -343,7 +343,7 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
     __syncthreads();
     // the tile's four field tiles sit next to each other in the slot
     const long long ring_field = (long long)mz * kTileY;
-    float2 *dst = R.ring + (long long)(step % R.depth) * R.slot_elems +
+    float2 *dst = R.ring + (long long)((step - R.lag_off) % R.depth) * R.slot_elems +
                   (long long)(kxi * ntile + ky0 / kTileY) * 4 * ring_field;
     if constexpr (M > 0) {
         for (int i = threadIdx.x; i < 4 * mz * (kTileY / 2); i += blockDim.x) {

@@ -50,7 +50,8 @@ struct FwdRing {
     int tile0;               // first block of this ring in the column-pass grid (kx x ky tiles)
     __nv_bfloat16 *far_x;    // far-path batch matrix [4 batch][2 ks] of this source (one ring per source), or null
     int far_ks;              // its half row width
-    int pad_;
+    int lag_off;             // the column pass of step l writes the slice of step l - lag_off (0 but for
+                             // a spilled window transformed with the push, which writes step l - lo)
     const long long *d_step; // the step, for launches made with step < 0 (graph replay)
 };
 

@@ -175,7 +175,9 @@ def test_spill_state_round_trip_and_graph_refusal():
 def test_spill_double_evaluation_and_profiling():
     """Evaluating a step twice fetches nothing the second time and gives the
     same result; under RP_FLAG_PROFILE the window transforms are timed and
-    counted with the forward passes, and the results do not change."""
+    counted with the forward passes (the first evaluation fills each window by
+    its own launches, later steps ride on the push's launches), and the
+    results do not change."""
     import torch
     dev = torch.device("cuda", 0)
     w = two_far()
@@ -202,6 +204,15 @@ def test_spill_double_evaluation_and_profiling():
         lib.sync()
         n_push, _ = rp.rp_kernel_stats(lib.ctx, rp.RP_K_FWD_COLUMN)[:2]
     assert_same(got, ref)
-    # T pushes, one window transform a step from the first evaluation on
-    # (its first evaluation fills each window by one transform a step of lag)
-    assert n_push >= T + (T - L)
+    # one column pass per push (one size class), plus the first evaluation's
+    # fill of B steps for each of the two windows; every later window step
+    # rides on its push
+    ctx = rp.rp_create(w.c, w.dt, 0, rp.RP_MODE_FFT, rp.RP_FLAG_PLAN_ONLY | SPILL)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        p = rp.rp_pair_info(ctx, 0, 1)
+    finally:
+        rp.rp_destroy(ctx)
+    assert n_push == T + 2 * (p["lag_hi"] - p["lag_lo"] + 1)
