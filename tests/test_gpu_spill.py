@@ -216,3 +216,40 @@ def test_spill_double_evaluation_and_profiling():
     finally:
         rp.rp_destroy(ctx)
     assert n_push == T + 2 * (p["lag_hi"] - p["lag_lo"] + 1)
+
+
+def test_spill_with_lowrank_far_pairs():
+    """RP_MODE_LOWRANK with the spill: two domains 150 bohr apart (their cross
+    windows at lags 21-23 spill) and a third about 900 bohr away (four far
+    pairs on the factors, whose bf16 source rows are staged by the same
+    forward plane pass that now also transforms the windows).  Equal to the
+    unspilled context bit for bit, steps from the deepest lag on."""
+    import torch
+    dev = torch.device("cuda", 0)
+    doms = [synth.cubic((0.0, 0.0, 0.0), 12, 0.25), synth.cubic((150.0, 0.5, -0.3), 12, 0.25),
+            synth.cubic((900.0, 50.0, -30.0), 12, 0.25)]
+    srcs = synth.seeded_sources(doms)
+    T = 160
+    hists = [s.history(0, T, 0.05) for s in srcs]
+
+    def run(flags):
+        out = {}
+        with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, flags=flags,
+                                   far_distance=400.0, far_batch=16) as lib:
+            q = lib.query()
+            for i in range(T):
+                lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
+                             [torch.from_numpy(h[i, 1:].copy().reshape(-1)).to(dev) for h in hists])
+                if i >= q["max_lag"]:
+                    phi, A = lib.evaluate()
+                    torch.cuda.synchronize()
+                    out[i] = [np.concatenate([phi[d].cpu().numpy()[None], A[d].cpu().numpy().reshape(3, -1)])
+                              for d in range(3)]
+            lib.sync()
+        return out, q
+
+    ref, q0 = run(0)
+    got, q1 = run(SPILL)
+    assert q0["npairs_far"] == q1["npairs_far"] == 4
+    assert q1["spill_windows"] == 2 and q0["spill_windows"] == 0
+    assert_same(got, ref)
