@@ -1,5 +1,6 @@
-// C-ABI of the retarded-potential library: context, pair planning, memory,
-// kernel spectra and the push / evaluate launch sequence.  See include/rp.h.
+// C-ABI of the retarded-potential library: pair planning, memory, kernel
+// spectra and the push / evaluate launch sequence.  See include/rp.h; the
+// context and its helpers are in rp_ctx.h, the history spill in rp_spill.cu.
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -16,11 +17,7 @@
 #include <cuda.h>
 #include <cudaTypedefs.h>
 
-#include "../../include/rp.h"
-#include "rp_internal.h"
-#include "rp_learned.h"
-#include "rp_learned_data.h"
-#include "rp_learned_train.h"
+#include "rp_ctx.h"
 
 namespace rp {
 size_t smem_direct(int max_nlag);
@@ -31,66 +28,6 @@ cudaError_t open_direct_smem_limit(int max_optin);
 using namespace rp;
 
 namespace {
-
-struct DomainDesc {
-    double o[3];
-    int n[3];
-    double h;
-    long long N;
-};
-
-struct PairPlan {
-    int kind;       // rp_pair_kind
-    int lag_lo, lag_hi;
-    double rmin, rmax;
-    int m[3];       // FFT size of the target (FFT pairs)
-};
-
-struct ProfRec {
-    int kind;
-    cudaEvent_t a, b;
-};
-
-// One launch of a kernel pair over a contiguous range [i0, i1) of rings (or
-// targets) of one size class: first kernel's blocks [blk0, blk1), second
-// kernel's blocks [blk2_0, blk2_1).
-struct LaunchGroup {
-    int cls;
-    int i0, i1;
-    int blk0, blk1;
-    int blk2_0, blk2_1;
-};
-
-// History spill (RP_FLAG_HISTORY_SPILL).  A source domain with a spilled
-// pair: device staging of its last kSpillStage pushed slices and the pinned
-// host ring of its history, [depth][4][N] float each.
-struct SpillSource {
-    int dom;
-    float *stage;
-    float *host;
-};
-
-// A spilled lag window [lo, hi] of one spectral ring: a device spectral ring
-// of depth B = hi - lo + 1 holding the source spectra of steps j at slot
-// j % B.  The forward passes make them (window descriptor w of the window
-// ring table: the ring's sizes, this ring as output) from raw slices copied
-// in from the host ring into one of two input buffers, by parity of j.
-// `have`: the newest step transformed in (-1: none); raw_step: the step each
-// input buffer holds.
-struct SpillWindow {
-    int ring, ss;            // forward ring, SpillSource
-    int lo, hi, depth;
-    float2 *dev;
-    float *raw;              // [2][4][N of the source]
-    long long have;
-    long long raw_step[2];
-};
-
-constexpr int kSpillStage = 3;   // staging slots: a round's copy to the host has two more rounds to finish
-
-// A pair's lag window is spilled when its window ring is at most half the
-// ring depth it would otherwise need.
-bool spill_window(int lo, int hi) { return lo >= 2 * (hi - lo + 2); }
 
 // Supported padded lengths: R * L with R in {1,2,3,4,6}, L a power of two <= 32.
 const int kSizes[] = {1, 2, 3, 4, 6, 8, 12, 16, 24, 32, 48, 64, 96, 128, 192};
@@ -122,244 +59,8 @@ Axis make_axis(int M)
 
 }  // namespace
 
-struct rp_ctx {
-    rp_config cfg{};
-    int device = -1;
-    cudaStream_t stream = nullptr;
-    bool plan_only = false, clamp = false, profile = false;
-    // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
-    // and the static potential P(0), [4][N] per domain
-    bool split = false, static_done = false, computing_static = false;
-    // graph replay of a step (rp_graph_capture / rp_graph_step): the step as
-    // the step-dependent kernels read it on replay, and the captured graph
-    long long *d_step = nullptr;
-    long long *h_step_pin = nullptr;          // pinned source of the counter's re-sync
-    cudaStream_t capture_stream = nullptr;    // the recording's own stream (the context stream may be
-                                              // the legacy default stream, which cannot be captured)
-    bool capturing = false;
-    cudaGraph_t graph = nullptr;
-    cudaGraphExec_t graph_exec = nullptr;
-    long long graph_synced = -2;              // host step the device counter holds (-2: unknown)
-    std::vector<float *> ground, delta, pstatic;
-    // history spill to host memory (RP_FLAG_HISTORY_SPILL): the spilled
-    // sources (host ring depth spill_hd), the windows with their descriptors
-    // for the forward passes, and the copy streams with their events:
-    //   sp_pushed   on the context stream once a round's slices are staged;
-    //   sp_out[k]   on spill_out after the copy to the host of step s, k = s % kSpillStage
-    //               (the push of step s + kSpillStage waits for it before reusing the staging slot);
-    //   sp_in       on spill_in after the last copy into a window's input buffer;
-    //   sp_wfft     on the context stream after the last window transform (the
-    //               input buffers' last reader).
-    bool spill = false;
-    int spill_hd = 0;
-    std::vector<SpillSource> spill_srcs;
-    std::vector<SpillWindow> spill_wins;
-    std::vector<FwdRing> wfwd;
-    FwdRing *d_wfwd = nullptr;
-    // the forward rings and, after those of each size class, that class's
-    // windows (lag_off = lo, inputs in pointer slots nd + w): one launch pair
-    // per class pushes a round and transforms the windows' steady-state
-    // slices (empty when the slots do not fit)
-    std::vector<FwdRing> mix;
-    FwdRing *d_mix = nullptr;
-    std::vector<LaunchGroup> mix_groups;
-    long long host_bytes = 0;
-    cudaStream_t spill_out = nullptr, spill_in = nullptr;
-    cudaEvent_t sp_pushed = nullptr, sp_in = nullptr, sp_wfft = nullptr;
-    std::vector<cudaEvent_t> sp_out;
-    bool finalized = false;
-    std::vector<DomainDesc> doms;
-    std::vector<PairPlan> pairs;   // [t * ndom + s]
-
-    // plan
-    std::vector<FwdRing> fwd;
-    std::vector<LaunchGroup> fwd_groups;             // (plane pass, column pass) per size class
-    std::vector<LaunchGroup> inv_groups;             // (MAC + column pass, plane pass) per size class
-    std::vector<InvTarget> inv;
-    std::vector<MacEntry> entries;
-    std::vector<DirectTarget> dtg;
-    std::vector<DirectPair> dpairs;
-    std::vector<RawRing> raw;
-    std::vector<int> raw_block0;                     // [ndom + 1], blocks of k_ring_push
-    int plane_blocks = 0, col_blocks = 0, mac_blocks = 0, invp_blocks = 0, dir_blocks = 0;
-    size_t smem_plane = 0, smem_col = 0, smem_mac = 0, smem_inv = 0, smem_dir = 0;
-    int max_lag = 0, raw_depth = 0, spec_depth = 0;
-    long long spectral_bytes = 0, kernel_bytes = 0, device_bytes = 0;
-
-    // device
-    FwdRing *d_fwd = nullptr;
-    InvTarget *d_inv = nullptr;
-    MacEntry *d_entries = nullptr;
-    DirectTarget *d_dtg = nullptr;
-    DirectPair *d_dpairs = nullptr;
-    RawRing *d_raw = nullptr;
-    bool tma = false;                // TMA-fed MAC available for the cubic classes
-    int mac_stages[7] = {};          // pipeline depth per class (index by class_slot)
-    int mac_cw[7] = {16, 16, 16, 16, 16, 16, 16};   // consumer warps of the MAC per class
-    int sm_count = 0;
-    int *d_err = nullptr;            // set by a kernel whose bounded wait ran out
-    // far pairs (low-rank path)
-    std::vector<FarSource> far_src;
-    std::vector<FarTarget> far_tgt;
-    std::vector<FarLink> far_links;
-    std::vector<int> far_link0, far_link1, far_link_threads;   // per far source
-    std::vector<float *> far_Z;
-    std::vector<int> far_rows;                                  // padded W rows per far source
-    std::vector<int> far_splits;                                // split-K count per far source
-    float *far_work = nullptr;                                  // split-K partial products
-    std::vector<CUtensorMap> far_mapW, far_mapX;
-    std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
-    FarSource *d_far_src = nullptr;
-    FarTarget *d_far_tgt = nullptr;
-    // far sources / targets with no forward ring / inverse target of their
-    // own: staged and interpolated by separate kernels
-    std::vector<FarSource> far_src_alone;
-    std::vector<FarTarget> far_tgt_alone;
-    std::vector<int> far_src_alone_of_dom;
-    FarSource *d_far_src_alone = nullptr;
-    FarTarget *d_far_tgt_alone = nullptr;
-    FarLink *d_far_links = nullptr;
-    int far_planes = 0, far_max_r = 0, npairs_far = 0;
-    long long far_bytes = 0, far_max_n = 0, far_zeroed_step = -1;
-    std::vector<void *> allocs;
-    std::vector<void *> *alloc_sink = nullptr;   // where dev_alloc records (the far path's own list while built)
-    std::vector<void *> far_allocs;
-    long long far_alloc_bytes = 0;
-    std::vector<std::array<std::vector<double>, 3>> far_tnodes;   // far targets' per-axis nodes, by domain
-    // learned far field
-    bool trained = false;
-    Mlp net;                          // inference network
-    bool net_open = false;
-    std::vector<LPair> lpairs;        // sorted by target
-    std::vector<LTarget> ltgts;
-    std::vector<MomentJob> mjobs;     // sorted by source domain
-    std::vector<int> mjob_of_dom;
-    LPair *d_lpairs = nullptr;
-    LTarget *d_ltgts = nullptr;
-    MomentJob *d_mjobs = nullptr;
-    float *d_lnu = nullptr;
-    float *d_lxf = nullptr, *d_lylin = nullptr;   // fp32 network rows and linear-skip outputs
-    float *d_lcontrib = nullptr;      // per-pair contributions [pairs][64][4]
-    int *d_lpair_r = nullptr;         // per-pair target node count
-    int lrows = 0, npairs_learned = 0, mjob_max_nz = 0;
-    bool net_used = false;            // some learned pair adds the network's output
-    std::vector<char> net_pair;       // [t * ndom + s]: the pair uses the network (else the linear skip alone)
-    int smem_optin = 0;
-    // Host-buffer calls: device staging per domain ([4][N]), two sets
-    // alternating by step parity, and a copy stream, so that a step's copies
-    // run while the kernels of the steps around it do; events order the two
-    // streams.
-    std::vector<float *> in_stage[2];
-    std::vector<float *> out_stage[2];
-    cudaStream_t copy_in = nullptr;            // host-to-device copies
-    cudaStream_t copy_out = nullptr;           // device-to-host copies (apart, so that a step's
-                                               // inputs never queue behind the last step's results)
-    cudaEvent_t in_ready = nullptr;            // the last host push's copy is done
-    cudaEvent_t in_free[2] = {nullptr, nullptr};    // the last push that read in_stage[b] has run
-                                                    // (pushes run in order on the context stream)
-    cudaEvent_t out_ready = nullptr;           // the last host evaluation's results are staged
-    cudaEvent_t out_free[2] = {nullptr, nullptr};   // the copy out of out_stage[b] is done
-
-    // step state
-    long long step = -1;
-    std::vector<char> pushed;
-    int npushed = 0;
-
-    // profiling
-    std::vector<ProfRec> pending;
-    std::vector<cudaEvent_t> spare_events;
-    long long launches[RP_K_COUNT] = {};   // timed launches
-    double ms[RP_K_COUNT] = {};
-    long long count[RP_K_COUNT] = {};      // every launch
-
-    std::string last_error;
-};
 
 namespace {
-
-rp_status fail(rp_ctx *ctx, rp_status st, const std::string &msg)
-{
-    if (ctx) ctx->last_error = msg;
-    return st;
-}
-
-rp_status cuda_fail(rp_ctx *ctx, cudaError_t e, const char *what)
-{
-    std::string m = std::string(what) + ": " + cudaGetErrorString(e);
-    return fail(ctx, e == cudaErrorMemoryAllocation ? RP_ERR_OOM : RP_ERR_CUDA, m);
-}
-
-#define RP_CUDA(ctx, expr)                                           \
-    do {                                                             \
-        cudaError_t e_ = (expr);                                     \
-        if (e_ != cudaSuccess) return cuda_fail((ctx), e_, #expr);   \
-    } while (0)
-
-rp_status use_device(rp_ctx *ctx)
-{
-    int cur = -1;
-    RP_CUDA(ctx, cudaGetDevice(&cur));
-    if (cur != ctx->device) RP_CUDA(ctx, cudaSetDevice(ctx->device));
-    return RP_OK;
-}
-
-template <class T>
-rp_status dev_alloc(rp_ctx *ctx, T **p, size_t count)
-{
-    void *q = nullptr;
-    const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
-    cudaError_t e = cudaMalloc(&q, bytes);
-    if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
-    (ctx->alloc_sink ? *ctx->alloc_sink : ctx->allocs).push_back(q);
-    if (ctx->alloc_sink) ctx->far_alloc_bytes += (long long)bytes;
-    ctx->device_bytes += (long long)bytes;
-    *p = static_cast<T *>(q);
-    return RP_OK;
-}
-
-template <class T>
-rp_status upload(rp_ctx *ctx, T **dst, const std::vector<T> &v)
-{
-    rp_status st = dev_alloc(ctx, dst, v.size());
-    if (st) return st;
-    if (!v.empty()) RP_CUDA(ctx, cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice));
-    return RP_OK;
-}
-
-cudaEvent_t take_event(rp_ctx *ctx)
-{
-    if (!ctx->spare_events.empty()) {
-        cudaEvent_t e = ctx->spare_events.back();
-        ctx->spare_events.pop_back();
-        return e;
-    }
-    cudaEvent_t e = nullptr;
-    cudaEventCreate(&e);
-    return e;
-}
-
-// Runs `launch` (returns cudaError_t), bracketed by events when profiling
-// and the current step is sampled.
-template <class F>
-rp_status timed_launch(rp_ctx *ctx, int kind, const char *what, F &&launch)
-{
-    cudaEvent_t a = nullptr, b = nullptr;
-    const int every = ctx->cfg.profile_every;
-    const bool timed = ctx->profile && (every <= 1 || ctx->step < 0 || ctx->step % every == 0);
-    if (ctx->profile) ctx->count[kind] += 1;
-    if (timed) {
-        a = take_event(ctx);
-        b = take_event(ctx);
-        RP_CUDA(ctx, cudaEventRecord(a, ctx->stream));
-    }
-    cudaError_t e = launch();
-    if (e != cudaSuccess) return cuda_fail(ctx, e, what);
-    if (timed) {
-        RP_CUDA(ctx, cudaEventRecord(b, ctx->stream));
-        ctx->pending.push_back({kind, a, b});
-    }
-    return RP_OK;
-}
 
 rp_status drain_profile(rp_ctx *ctx)
 {
@@ -436,95 +137,6 @@ rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
 }  // namespace
 
 namespace {
-
-// History spill: the staging and window rings (device, zeroed), the pinned
-// host rings, the window descriptors (after the forward rings' buffers), the
-// two copy streams and their events.
-rp_status open_spill(rp_ctx *ctx)
-{
-    if (ctx->spill_srcs.empty()) return RP_OK;
-    rp_status st;
-    for (SpillSource &S : ctx->spill_srcs) {
-        const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
-        if ((st = dev_alloc(ctx, &S.stage, kSpillStage * n4))) return st;
-        RP_CUDA(ctx, cudaMemset(S.stage, 0, kSpillStage * n4 * sizeof(float)));
-        void *p = nullptr;
-        RP_CUDA(ctx, cudaHostAlloc(&p, (size_t)ctx->spill_hd * n4 * sizeof(float), cudaHostAllocDefault));
-        S.host = static_cast<float *>(p);
-        std::memset(p, 0, (size_t)ctx->spill_hd * n4 * sizeof(float));
-    }
-    int plane0 = 0, tile0 = 0;
-    for (SpillWindow &W : ctx->spill_wins) {
-        const FwdRing &R = ctx->fwd[W.ring];
-        const size_t elems = (size_t)W.depth * R.slot_elems;
-        const size_t n4 = 4 * (size_t)ctx->doms[R.src].N;
-        if ((st = dev_alloc(ctx, &W.dev, elems)) || (st = dev_alloc(ctx, &W.raw, 2 * n4))) return st;
-        RP_CUDA(ctx, cudaMemset(W.dev, 0, elems * sizeof(float2)));
-        FwdRing F = R;            // same sizes and twiddles
-        F.src = (int)ctx->wfwd.size() % kMaxDomains;   // its input's slot in a launch's pointer table
-        F.depth = W.depth;
-        F.ring = W.dev;
-        // its own scratch between the two passes: a push's launch may transform
-        // the window beside the ring it copies
-        if ((st = dev_alloc(ctx, &F.t1, 4ULL * F.kx * F.nz * F.ay.M))) return st;
-        F.far_x = nullptr;
-        F.far_ks = 0;
-        F.plane0 = plane0;
-        F.tile0 = tile0;
-        plane0 += 4 * F.nz;
-        tile0 += F.kx * ((F.ay.M + kTileY - 1) / kTileY);
-        ctx->wfwd.push_back(F);
-    }
-    RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_out, cudaStreamNonBlocking));
-    RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->spill_in, cudaStreamNonBlocking));
-    auto event = [](cudaEvent_t *e) { return cudaEventCreateWithFlags(e, cudaEventDisableTiming); };
-    RP_CUDA(ctx, event(&ctx->sp_pushed));
-    RP_CUDA(ctx, event(&ctx->sp_in));
-    RP_CUDA(ctx, event(&ctx->sp_wfft));
-    ctx->sp_out.assign(kSpillStage, nullptr);
-    for (cudaEvent_t &e : ctx->sp_out) RP_CUDA(ctx, event(&e));
-    return RP_OK;
-}
-
-// History spill: the merged descriptor table (rp_ctx::mix) from the current
-// forward rings and windows, uploaded.  Called once the forward rings'
-// descriptors are final, and again whenever they change (far factors built
-// or rebuilt later).
-rp_status build_mix(rp_ctx *ctx)
-{
-    const int nd = (int)ctx->doms.size(), nw = (int)ctx->spill_wins.size();
-    ctx->mix.clear();
-    ctx->mix_groups.clear();
-    if (nw == 0 || nd + nw > kMaxDomains) return RP_OK;
-    int p0 = 0, t0 = 0;
-    for (const LaunchGroup &g : ctx->fwd_groups) {
-        LaunchGroup m{g.cls, (int)ctx->mix.size(), 0, p0, 0, t0, 0};
-        auto add = [&](FwdRing F) {
-            F.plane0 = p0;
-            F.tile0 = t0;
-            F.d_step = ctx->d_step;
-            p0 += 4 * F.nz;
-            t0 += F.kx * ((F.ay.M + kTileY - 1) / kTileY);
-            ctx->mix.push_back(F);
-        };
-        for (int r = g.i0; r < g.i1; ++r) add(ctx->fwd[r]);
-        for (int w = 0; w < nw; ++w) {
-            FwdRing F = ctx->wfwd[w];
-            if (size_class(F.ax, F.ay, F.az) != g.cls) continue;
-            F.src = nd + w;
-            F.lag_off = ctx->spill_wins[w].lo;
-            add(F);
-        }
-        m.i1 = (int)ctx->mix.size();
-        m.blk1 = p0;
-        m.blk2_1 = t0;
-        ctx->mix_groups.push_back(m);
-    }
-    rp_status st;
-    if (!ctx->d_mix && (st = dev_alloc(ctx, &ctx->d_mix, ctx->mix.size()))) return st;
-    RP_CUDA(ctx, cudaMemcpy(ctx->d_mix, ctx->mix.data(), ctx->mix.size() * sizeof(FwdRing), cudaMemcpyHostToDevice));
-    return RP_OK;
-}
 
 int class_slot(int cls)
 {
@@ -1694,149 +1306,6 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
 }  // namespace
 
 extern "C" {
-
-// History spill, once a round's pushes are queued: the round's staged slices
-// of the spilled sources into their host rings (spill_out waits for the
-// staging copies, and for the copies back from the host ring queued so far,
-// the last readers of the host slot it overwrites).
-static rp_status spill_round_done(rp_ctx *ctx)
-{
-    if (ctx->spill_srcs.empty() || ctx->npushed != (int)ctx->doms.size()) return RP_OK;
-    const long long l = ctx->step;
-    RP_CUDA(ctx, cudaEventRecord(ctx->sp_pushed, ctx->stream));
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_pushed, 0));
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_out, ctx->sp_in, 0));
-    for (const SpillSource &S : ctx->spill_srcs) {
-        const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
-        RP_CUDA(ctx, cudaMemcpyAsync(S.host + (size_t)(l % ctx->spill_hd) * n4, S.stage + (size_t)(l % kSpillStage) * n4,
-                                     n4 * sizeof(float), cudaMemcpyDeviceToHost, ctx->spill_out));
-    }
-    RP_CUDA(ctx, cudaEventRecord(ctx->sp_out[l % kSpillStage], ctx->spill_out));
-    return RP_OK;
-}
-
-// History spill: the host slice of step j into input buffer j % 2 of window
-// W on spill_in (the caller has made spill_in wait for the copy out of j and
-// for the buffer's last reader, and records sp_in after).
-static rp_status spill_raw_in(rp_ctx *ctx, SpillWindow &W, long long j)
-{
-    const SpillSource &S = ctx->spill_srcs[W.ss];
-    const size_t n4 = 4 * (size_t)ctx->doms[S.dom].N;
-    RP_CUDA(ctx, cudaMemcpyAsync(W.raw + (size_t)(j & 1) * n4, S.host + (size_t)(j % ctx->spill_hd) * n4,
-                                 n4 * sizeof(float), cudaMemcpyHostToDevice, ctx->spill_in));
-    W.raw_step[j & 1] = j;
-    return RP_OK;
-}
-
-// History spill: the forward passes of windows [w0, w1) (one size class,
-// fewer than kMaxDomains of them), each on the slice of step j in its input
-// buffer j % 2, into slot j % B of its ring.
-static rp_status spill_transform(rp_ctx *ctx, int w0, int w1, long long j)
-{
-    rp_status st;
-    IoPtrs in{};
-    for (int w = w0; w < w1; ++w) {
-        const SpillWindow &W = ctx->spill_wins[w];
-        const long long Ns = ctx->doms[ctx->spill_srcs[W.ss].dom].N;
-        const FwdRing &F = ctx->wfwd[w];
-        in.rho[F.src] = W.raw + (size_t)(j & 1) * 4 * Ns;
-        in.J[F.src] = in.rho[F.src] + Ns;
-    }
-    const FwdRing &F0 = ctx->wfwd[w0], &F1 = ctx->wfwd[w1 - 1];
-    const int cls = size_class(F0.ax, F0.ay, F0.az);
-    const int planes = F1.plane0 + 4 * F1.nz - F0.plane0;
-    const int tiles = F1.tile0 + F1.kx * ((F1.ay.M + kTileY - 1) / kTileY) - F0.tile0;
-    if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "window forward plane pass", [&] {
-             return launch_fwd_plane(cls, ctx->d_wfwd, in, w0, w1, F0.plane0, planes, ctx->smem_plane, 0, ctx->stream);
-         })))
-        return st;
-    return timed_launch(ctx, RP_K_FWD_COLUMN, "window forward column pass", [&] {
-        return launch_fwd_column(cls, ctx->d_wfwd, w0, w1, F0.tile0, tiles, ctx->smem_col, j, ctx->stream);
-    });
-}
-
-// History spill, before the MAC of step l: every window must hold the
-// spectra of source steps l - hi .. l - lo (clamped at 0 under
-// RP_FLAG_GROUND_STATE_CLAMP).  Normally each window lacks only step l - lo,
-// whose slice was fetched during the previous step: then one pair of forward
-// passes per run of windows of one size class and one such step transforms
-// them into the windows' rings, on the context stream where the MAC reads
-// them (slot j % B held step j - B < l - hi, which this and later MACs do not
-// read).  Otherwise (the first steps, skipped evaluations, a loaded state)
-// the missing steps go one at a time: slice in, transform.  Then each
-// window's slice for step l + 1 (j = l + 1 - lo <= l - 3, as a spilled window
-// has lo >= 4) is fetched, after the copy out of step l - 1 and the last
-// transform (the reader of its buffer), to arrive under this step's
-// remaining kernels.
-static rp_status spill_fetch(rp_ctx *ctx)
-{
-    if (ctx->spill_srcs.empty()) return RP_OK;
-    const long long l = ctx->step;
-    const int nw = (int)ctx->spill_wins.size();
-    rp_status st;
-    std::vector<long long> next(nw, -1);   // the one step a window lacks, or -1
-    bool steady = true;
-    for (int w = 0; w < nw; ++w) {
-        const SpillWindow &W = ctx->spill_wins[w];
-        long long a = l - W.hi, b = l - W.lo;
-        if (ctx->clamp) { a = std::max(a, 0LL); b = std::max(b, 0LL); }
-        if (a < 0) return fail(ctx, RP_ERR_HISTORY, "spilled window before the first push");
-        const long long from = std::max(a, W.have + 1);
-        if (from > b) continue;
-        if (from == b && W.raw_step[b & 1] == b) next[w] = b;
-        else steady = false;
-    }
-    if (steady) {
-        bool any = false;
-        for (int w = 0; w < nw;) {
-            if (next[w] < 0) { ++w; continue; }
-            if (!any) RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
-            any = true;
-            const FwdRing &F = ctx->wfwd[w];
-            const int cls = size_class(F.ax, F.ay, F.az);
-            int w1 = w + 1;
-            while (w1 < nw && w1 - w < kMaxDomains && next[w1] == next[w] &&
-                   size_class(ctx->wfwd[w1].ax, ctx->wfwd[w1].ay, ctx->wfwd[w1].az) == cls)
-                ++w1;
-            if ((st = spill_transform(ctx, w, w1, next[w]))) return st;
-            for (int v = w; v < w1; ++v) ctx->spill_wins[v].have = next[w];
-            w = w1;
-        }
-        if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
-    } else {
-        for (int w = 0; w < nw; ++w) {
-            SpillWindow &W = ctx->spill_wins[w];
-            long long a = l - W.hi, b = l - W.lo;
-            if (ctx->clamp) { a = std::max(a, 0LL); b = std::max(b, 0LL); }
-            for (long long j = std::max(a, W.have + 1); j <= b; ++j) {
-                if (W.raw_step[j & 1] != j) {
-                    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[l % kSpillStage], 0));
-                    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_wfft, 0));
-                    if ((st = spill_raw_in(ctx, W, j))) return st;
-                    RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
-                }
-                RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->sp_in, 0));
-                if ((st = spill_transform(ctx, w, w + 1, j))) return st;
-                RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
-                W.have = j;
-            }
-        }
-    }
-    if (l < 1) return RP_OK;
-    bool any = false;
-    for (SpillWindow &W : ctx->spill_wins) {
-        const long long j = l + 1 - W.lo;
-        if (j < 0 || j != W.have + 1 || W.raw_step[j & 1] == j) continue;
-        if (!any) {
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_out[(l - 1) % kSpillStage], 0));
-            RP_CUDA(ctx, cudaStreamWaitEvent(ctx->spill_in, ctx->sp_wfft, 0));
-        }
-        any = true;
-        if ((st = spill_raw_in(ctx, W, j))) return st;
-    }
-    if (any) RP_CUDA(ctx, cudaEventRecord(ctx->sp_in, ctx->spill_in));
-    return RP_OK;
-}
 
 // Ground-state split, at a push of domains [d0, d1): on the first step keep
 // S(0) (pushed as it is, for the static potential); later, push Delta S.
