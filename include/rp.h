@@ -176,7 +176,8 @@ typedef struct {
     int spectral_depth;       /* largest spectral ring depth in steps */
     long long step;           /* index of the last completed push round, -1 before the first */
     long long device_bytes;   /* device memory held by the context */
-    long long spectral_bytes; /* of which: spectral history rings */
+    long long spectral_bytes; /* of which: spectral history rings (under RP_FLAG_HISTORY_SPILL also the
+                               * window rings, their input slices and the staging rings) */
     long long kernel_bytes;   /* of which: kernel spectra */
     long long points;         /* sum of grid points over all domains */
     int mac_tma;              /* 1: the spectral MAC of cubic targets is fed by TMA copies */
@@ -186,7 +187,7 @@ typedef struct {
     int npairs_learned;       /* pairs on the learned far path (after rp_train_far_model) */
     int spill_windows;        /* RP_FLAG_HISTORY_SPILL: lag windows read from host-refilled window rings */
     int reserved;
-    long long host_bytes;     /* pinned host memory of the spilled spectral history */
+    long long host_bytes;     /* pinned host memory of the spilled history ((rho, J) slices) */
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
