@@ -82,3 +82,26 @@ def test_plain_path_flops_and_alu_peak():
     assert bench.DIRECT_FLOPS_PER_PAIR_POINT == 34
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
     assert bench.profile_every(10) == 1 and bench.profile_every(10 * bench.PROFILE_EVERY) == bench.PROFILE_EVERY
+
+
+def test_cfg2_far_gemm_bytes():
+    """The cross pairs of the 2 x 48^3 workload on the factors (far distance
+    1000 bohr, 4^3 nodes, batches of 32): per source one GEMM of W (5 lags x
+    64 nodes = 320 rows, padded to 384) by X (4 fields x 32 slices = 128
+    rows) over K = 110592, hi and lo bf16 planes (4 B per element), and the
+    fp32 node values written: 170 + 56.6 + 0.2 MB."""
+    w = synth.workload("cfg2")
+    ctx = rp.rp_create(w.c, w.dt, w.history, rp.RP_MODE_LOWRANK, rp.RP_FLAG_PLAN_ONLY,
+                       far_distance=1000.0, far_points=4, far_batch=32)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        info = {(t, s): rp.rp_pair_info(ctx, t, s) for t in range(2) for s in range(2)}
+    finally:
+        rp.rp_destroy(ctx)
+    assert info[(1, 0)]["kind"] == rp.RP_PAIR_LOWRANK and info[(1, 0)]["lag_hi"] - info[(1, 0)]["lag_lo"] == 4
+    K = 48 ** 3
+    want = 384 * K * 4 + 128 * K * 4 + 384 * 128 * 4
+    assert bench.far_gemm_bytes(w, info, 4, 32) == want
+    assert 226e6 < want < 227e6   # 226.7 MB
