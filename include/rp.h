@@ -149,8 +149,18 @@ typedef struct {
     int profile_every;   /* RP_FLAG_PROFILE: time the launches of step s only when s % profile_every == 0
                           * (launches outside the step cycle always), >= 0; 0 or 1: every step.  The
                           * events sit between kernels and hold back the next launch, so sampling
-                          * keeps them off most steps. */
-    int reserved[3];     /* set to zero */
+                          * keeps them off most steps.  rp_set_profiling changes it later. */
+    int far_source_points; /* RP_MODE_LOWRANK: 0 keeps every source node exact in the far factors; 2..8
+                          * interpolates the source side too (two-sided): each far source's slice is
+                          * anterpolated onto far_source_points^3 Chebyshev nodes of its box at push
+                          * (q_b = sum_k' L_b(r_k') h^3 S(k')), and the factors hold Eq. 11 between
+                          * target and source nodes, so that their size no longer grows with the
+                          * source grid */
+    long long device_budget; /* largest device memory the context may hold, in bytes (rp_stats.device_bytes);
+                          * an allocation that would pass it returns RP_ERR_OOM without calling the
+                          * allocator (with RP_FLAG_PLAN_ONLY, rp_finalize compares the planned bytes).
+                          * 0: no limit.  Not in the paper: a resource guard of the library. */
+    int reserved[4];     /* set to zero */
 } rp_config;
 
 typedef struct rp_ctx rp_ctx;
@@ -201,7 +211,7 @@ typedef enum {
     RP_K_FAR_CONVERT = 6,   /* far path: slice to bf16 batch matrix */
     RP_K_FAR_GEMM = 7,      /* far path: tcgen05 GEMM of factors and batch */
     RP_K_FAR_SCATTER = 8,   /* far path: node values into coefficient rings */
-    RP_K_FAR_INTERP = 9,    /* far path: coefficients interpolated onto the target grid */
+    RP_K_FAR_INTERP = 9,    /* far path: source anterpolation onto its nodes (two-sided factors) */
     RP_K_MOMENTS = 10,      /* learned path: moments of the pushed slices */
     RP_K_LEARNED = 11,      /* learned path: network rows, network, output into the coefficients */
     RP_K_COUNT = 12
@@ -345,13 +355,14 @@ rp_status rp_evaluate_host(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
  * until the process exits.
  *
  * Arguments, layout and results are those of rp_evaluate_host: h_phi[n] gets
- * N_n floats and h_A[n] 3*N_n floats, valid after rp_sync.  The first call on
- * a device looks up the array's device address (cudaGetSymbolAddress); make
- * that first call before any stream capture.  All calls in the process on a
- * device share the one array and each call overwrites it, so calls whose work
- * overlaps on the GPU (two contexts on different streams, say) race and may
- * return each other's values: order them on one stream, or synchronise
- * between them.
+ * N_n floats and h_A[n] 3*N_n floats, valid after rp_sync.  The array's
+ * device address is looked up (cudaGetSymbolAddress) by the first
+ * rp_finalize on each device, which is when the 16 MiB are placed in device
+ * memory; this call only reads the address, so device memory in use is the
+ * same before and after it.  All calls in the process on a device share the
+ * one array and each call overwrites it, so calls whose work overlaps on the
+ * GPU (two contexts on different streams, say) race and may return each
+ * other's values: order them on one stream, or synchronise between them.
  */
 rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *const *h_A);
 
@@ -565,19 +576,30 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out);
 rp_status rp_pair_info(rp_ctx *ctx, int target, int source, rp_pair_info_t *out);
 
 /*
- * rp_kernel_stats -- under RP_FLAG_PROFILE: timed launches and their summed
- * device time (ms, CUDA events on the context stream) of kernel class `kind`
- * since the last reset; waits for the stream.  reset != 0 clears all
- * counters (these and rp_kernel_count's) after reading.
+ * rp_kernel_stats -- timed launches (RP_FLAG_PROFILE or rp_set_profiling) and
+ * their summed device time (ms, CUDA events on the context stream) of kernel
+ * class `kind` since the last reset; waits for the stream.  reset != 0 clears
+ * all counters (these and rp_kernel_count's) after reading.
  */
 rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *total_ms,
                           int reset);
 
 /*
- * rp_kernel_count -- under RP_FLAG_PROFILE: every launch of kernel class
- * `kind` since the last reset, timed or not (host-side count, no wait).
+ * rp_kernel_count -- every launch of kernel class `kind` since the last
+ * reset (rp_kernel_stats with reset != 0), timed or not: a host-side count
+ * kept on every context, with or without RP_FLAG_PROFILE; no wait.
  */
 rp_status rp_kernel_count(rp_ctx *ctx, int kind, long long *launches);
+
+/*
+ * rp_set_profiling -- switch the per-launch CUDA events of RP_FLAG_PROFILE on
+ * (every >= 1: the launches of steps s % every == 0) or off (every = 0) for
+ * the launches that follow, on any context that is not plan-only.  Lets a
+ * caller time a run without events between its kernels and then measure the
+ * kernels in a separate pass on the same context.  RP_ERR_ARG for every < 0.
+ * (No counterpart in the paper: a property of the library.)
+ */
+rp_status rp_set_profiling(rp_ctx *ctx, int every);
 
 /*
  * rp_selftest_wait -- a library self-test, no counterpart in the paper.  One

@@ -102,6 +102,26 @@ def cube_average_constant() -> float:
     return _load().rpo_cube_average_constant()
 
 
+def history_needed(origins, ns, hs, c: float, dt: float) -> int:
+    """How many steps back the sums read: the retarded time of the farthest
+    node pair, R_max/c, falls between samples floor(R_max/(c dt)) and that + 1
+    before the evaluated step (Eq. 7's hat interpolation reads both), so the
+    history must reach that many steps back.  R_max is the distance between
+    the farthest corners of two domains' node lattices, over all ordered
+    pairs (self pairs included)."""
+    ndom = len(hs)
+    o = np.asarray(origins, dtype=np.float64).reshape(ndom, 3)
+    n = np.asarray(ns, dtype=np.float64).reshape(ndom, 3)
+    h = np.asarray(hs, dtype=np.float64).reshape(ndom, 1)
+    lo, hi = o, o + h * (n - 1)
+    worst = 0
+    for t in range(ndom):
+        for s in range(ndom):
+            far = np.maximum(np.abs(hi[t] - lo[s]), np.abs(hi[s] - lo[t]))
+            worst = max(worst, int(np.floor(np.sqrt(np.sum(far * far)) / (c * dt))) + 1)
+    return worst
+
+
 def eval_points(origins: np.ndarray, ns: np.ndarray, hs: Sequence[float],
                 hists: Sequence[np.ndarray], hist_first: int,
                 c: float, dt: float, target: int, step: int, nodes,

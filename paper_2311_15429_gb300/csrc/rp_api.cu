@@ -62,6 +62,10 @@ Axis make_axis(int M)
 
 namespace {
 
+// Device address of rp_evaluate_host_noalloc's fixed staging array on
+// ctx->device (defined with the array, below).
+rp_status noalloc_stage_address(rp_ctx *ctx, float **out);
+
 rp_status drain_profile(rp_ctx *ctx)
 {
     for (const ProfRec &r : ctx->pending) {
@@ -222,9 +226,9 @@ void clear_far(rp_ctx *ctx)
     ctx->far_Z.clear(); ctx->far_rows.clear(); ctx->far_splits.clear(); ctx->far_work = nullptr;
     ctx->far_mapW.clear(); ctx->far_mapX.clear(); ctx->far_src_of_dom.clear();
     ctx->d_far_src = nullptr; ctx->d_far_tgt = nullptr; ctx->d_far_links = nullptr;
-    ctx->far_src_alone.clear(); ctx->far_tgt_alone.clear(); ctx->far_src_alone_of_dom.clear();
-    ctx->d_far_src_alone = nullptr; ctx->d_far_tgt_alone = nullptr;
-    ctx->far_planes = ctx->far_max_r = ctx->npairs_far = 0;
+    ctx->far_src_alone.clear(); ctx->far_src_alone_of_dom.clear();
+    ctx->d_far_src_alone = nullptr;
+    ctx->far_max_r = ctx->npairs_far = 0;
     ctx->far_bytes = ctx->far_max_n = 0;
     ctx->far_zeroed_step = -1;
     for (FwdRing &R : ctx->fwd) { R.far_x = nullptr; R.far_ks = 0; }
@@ -268,7 +272,6 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
         if ((st = dev_alloc(ctx, &F.cring, (size_t)F.depth * F.r * 4))) return st;
         RP_CUDA(ctx, cudaMemset(F.cring, 0, (size_t)F.depth * F.r * 4 * sizeof(float)));
         ctx->far_bytes += (long long)F.depth * F.r * 16 + 4LL * (T.n[0] * F.px + T.n[1] * F.py + T.n[2] * F.pz);
-        ctx->far_planes += F.nz;
         ctx->far_max_r = std::max(ctx->far_max_r, F.r);
         tidx[t] = (int)ctx->far_tgt.size();
         ctx->far_tgt.push_back(F);
@@ -373,7 +376,9 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
             ctx->far_src_alone.push_back(F);
         }
     }
-    ctx->far_planes = 0;
+    // every far target is also an FFT target (its self term), and its inverse
+    // plane pass, which writes the output, adds the far coefficients: a far
+    // target without one would have no pass that writes its output first
     for (size_t k = 0; k < ctx->far_tgt.size(); ++k) {
         const FarTarget &F = ctx->far_tgt[k];
         bool done = false;
@@ -382,13 +387,11 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
                 I.far = ctx->d_far_tgt + k;
                 done = true;
             }
-        if (!done) {
-            ctx->far_tgt_alone.push_back(F);
-            ctx->far_planes += F.nz;
-        }
+        if (!done)
+            return fail(ctx, RP_ERR_UNSUPPORTED, "far target " + std::to_string(F.dom) +
+                                                     " has no FFT self term to carry its far coefficients");
     }
     if (!ctx->far_src_alone.empty() && (st = upload(ctx, &ctx->d_far_src_alone, ctx->far_src_alone))) return st;
-    if (!ctx->far_tgt_alone.empty() && (st = upload(ctx, &ctx->d_far_tgt_alone, ctx->far_tgt_alone))) return st;
     return RP_OK;
 }
 
@@ -632,7 +635,9 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
     }
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
-    if (cfg->profile_every < 0) return RP_ERR_ARG;
+    if (cfg->profile_every < 0 || cfg->device_budget < 0) return RP_ERR_ARG;
+    if (cfg->far_source_points != 0 && (cfg->far_source_points < 2 || cfg->far_source_points > kMaxFarPts))
+        return RP_ERR_ARG;
     rp_ctx *ctx = new rp_ctx();
     ctx->cfg = *cfg;
     if (ctx->cfg.far_points == 0) ctx->cfg.far_points = 4;
@@ -959,6 +964,10 @@ rp_status rp_finalize(rp_ctx *ctx)
         long long raw_bytes = 0;
         for (int d = 0; d < nd; ++d) raw_bytes += 16LL * ctx->raw[d].depth * ctx->raw[d].n;
         ctx->device_bytes = ctx->spectral_bytes + ctx->kernel_bytes + raw_bytes;
+        if (ctx->cfg.device_budget > 0 && ctx->device_bytes > ctx->cfg.device_budget)
+            return fail(ctx, RP_ERR_OOM, "planned device memory " + std::to_string(ctx->device_bytes) +
+                                             " B exceeds the device budget of " +
+                                             std::to_string(ctx->cfg.device_budget) + " B");
         ctx->finalized = true;
         return RP_OK;
     }
@@ -1107,6 +1116,10 @@ rp_status rp_finalize(rp_ctx *ctx)
     RP_CUDA(ctx, open_mac_tma_smem_limit(max_optin));
     if ((st = dev_alloc(ctx, &ctx->d_err, 1))) return st;
     RP_CUDA(ctx, cudaMemset(ctx->d_err, 0, sizeof(int)));
+    // the fixed staging array of rp_evaluate_host_noalloc: its address is
+    // looked up here, at set-up, so that the module holding it is loaded (and
+    // the array placed in device memory) now and not at that call's first use
+    if ((st = noalloc_stage_address(ctx, &ctx->noalloc_stage))) return st;
     RP_CUDA(ctx, cudaDeviceSynchronize());
     if ((st = autotune_mac(ctx))) return st;
     ctx->finalized = true;
@@ -1543,13 +1556,6 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
              })))
             return st;
     }
-    if (!ctx->far_tgt_alone.empty()) {
-        if ((st = timed_launch(ctx, RP_K_FAR_INTERP, "far interpolation", [&] {
-                 return launch_far_interp(ctx->d_far_tgt_alone, (int)ctx->far_tgt_alone.size(), ctx->far_planes, out,
-                                          step, inv_c, ctx->stream);
-             })))
-            return st;
-    }
     if (!ctx->dtg.empty()) {
         const float inv_cdt = (float)(1.0 / (ctx->cfg.c * ctx->cfg.dt));
         if ((st = timed_launch(ctx, RP_K_DIRECT, "direct sum", [&] {
@@ -1642,8 +1648,9 @@ std::mutex g_noalloc_mutex;
 float *g_noalloc_addr[kNoAllocMaxDevices] = {};
 
 // Device address of the staging array on ctx->device.  Looked up once per
-// device, with that device current (the host-side symbol is only a stand-in
-// for the device address and must not be handed to a kernel).
+// device, with that device current, at the first rp_finalize on it (the
+// host-side symbol is only a stand-in for the device address and must not be
+// handed to a kernel).
 rp_status noalloc_stage_address(rp_ctx *ctx, float **out)
 {
     if (ctx->device < 0 || ctx->device >= kNoAllocMaxDevices)
@@ -1677,8 +1684,8 @@ rp_status rp_evaluate_host_noalloc(rp_ctx *ctx, float *const *h_phi, float *cons
         return fail(ctx, RP_ERR_UNSUPPORTED, "rp_evaluate_host_noalloc: the domains need " + std::to_string(need) +
                                                  " staging floats, the fixed array holds " +
                                                  std::to_string(kNoAllocFloats));
-    float *stage = nullptr;
-    if ((st = noalloc_stage_address(ctx, &stage))) return st;
+    float *stage = ctx->noalloc_stage;   // looked up at rp_finalize
+    if (!stage) return fail(ctx, RP_ERR_STATE, "rp_evaluate_host_noalloc: staging array not set up");
     // every staged value is written by the evaluation before it is copied out,
     // so nothing left from an earlier call needs clearing
     float *phi[kMaxDomains], *A[kMaxDomains];
@@ -2123,7 +2130,7 @@ rp_status rp_pair_info(rp_ctx *ctx, int target, int source, rp_pair_info_t *out)
 rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *total_ms, int reset)
 {
     if (!ctx || kind < 0 || kind >= RP_K_COUNT) return RP_ERR_ARG;
-    if (!ctx->profile) return fail(ctx, RP_ERR_STATE, "context created without RP_FLAG_PROFILE");
+    if (ctx->plan_only) return fail(ctx, RP_ERR_STATE, "plan-only context");
     rp_status st = use_device(ctx);
     if (st) return st;
     if ((st = drain_profile(ctx))) return st;
@@ -2138,8 +2145,16 @@ rp_status rp_kernel_stats(rp_ctx *ctx, int kind, long long *launches, double *to
 rp_status rp_kernel_count(rp_ctx *ctx, int kind, long long *launches)
 {
     if (!ctx || kind < 0 || kind >= RP_K_COUNT || !launches) return RP_ERR_ARG;
-    if (!ctx->profile) return fail(ctx, RP_ERR_STATE, "context created without RP_FLAG_PROFILE");
     *launches = ctx->count[kind];
+    return RP_OK;
+}
+
+rp_status rp_set_profiling(rp_ctx *ctx, int every)
+{
+    if (!ctx || every < 0) return RP_ERR_ARG;
+    if (ctx->plan_only) return fail(ctx, RP_ERR_STATE, "plan-only context");
+    ctx->profile = every > 0;
+    ctx->cfg.profile_every = every;
     return RP_OK;
 }
 

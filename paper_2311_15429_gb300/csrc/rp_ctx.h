@@ -174,15 +174,12 @@ struct rp_ctx {
     std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
     FarSource *d_far_src = nullptr;
     FarTarget *d_far_tgt = nullptr;
-    // far sources / targets with no forward ring / inverse target of their
-    // own: staged and interpolated by separate kernels
+    // far sources with no forward ring of their own: staged by a separate kernel
     std::vector<FarSource> far_src_alone;
-    std::vector<FarTarget> far_tgt_alone;
     std::vector<int> far_src_alone_of_dom;
     FarSource *d_far_src_alone = nullptr;
-    FarTarget *d_far_tgt_alone = nullptr;
     FarLink *d_far_links = nullptr;
-    int far_planes = 0, far_max_r = 0, npairs_far = 0;
+    int far_max_r = 0, npairs_far = 0;
     long long far_bytes = 0, far_max_n = 0, far_zeroed_step = -1;
     std::vector<void *> allocs;
     std::vector<void *> *alloc_sink = nullptr;   // where dev_alloc records (the far path's own list while built)
@@ -208,6 +205,7 @@ struct rp_ctx {
     bool net_used = false;            // some learned pair adds the network's output
     std::vector<char> net_pair;       // [t * ndom + s]: the pair uses the network (else the linear skip alone)
     int smem_optin = 0;
+    float *noalloc_stage = nullptr;   // device address of rp_evaluate_host_noalloc's fixed array (set at finalize)
     // Host-buffer calls: device staging per domain ([4][N]), two sets
     // alternating by step parity, and a copy stream, so that a step's copies
     // run while the kernels of the steps around it do; events order the two
@@ -271,6 +269,10 @@ rp_status dev_alloc(rp_ctx *ctx, T **p, size_t count)
 {
     void *q = nullptr;
     const size_t bytes = std::max<size_t>(count * sizeof(T), 16);
+    if (ctx->cfg.device_budget > 0 && ctx->device_bytes + (long long)bytes > ctx->cfg.device_budget)
+        return fail(ctx, RP_ERR_OOM, "device budget of " + std::to_string(ctx->cfg.device_budget) +
+                                         " B exceeded: " + std::to_string(ctx->device_bytes) + " B held, " +
+                                         std::to_string(bytes) + " B asked");
     cudaError_t e = cudaMalloc(&q, bytes);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "cudaMalloc");
     (ctx->alloc_sink ? *ctx->alloc_sink : ctx->allocs).push_back(q);
@@ -309,7 +311,7 @@ rp_status timed_launch(rp_ctx *ctx, int kind, const char *what, F &&launch)
     cudaEvent_t a = nullptr, b = nullptr;
     const int every = ctx->cfg.profile_every;
     const bool timed = ctx->profile && (every <= 1 || ctx->step < 0 || ctx->step % every == 0);
-    if (ctx->profile) ctx->count[kind] += 1;
+    ctx->count[kind] += 1;
     if (timed) {
         a = take_event(ctx);
         b = take_event(ctx);

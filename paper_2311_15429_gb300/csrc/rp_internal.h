@@ -234,8 +234,6 @@ cudaError_t launch_far_convert(const FarSource *d_srcs, int nsrc, const IoPtrs &
 cudaError_t launch_far_zero(const FarTarget *d_tgts, int ntgt, long long j1, int batch, int max_r, cudaStream_t s);
 cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads, const float *Z, int ldz, long long j0,
                                int batch, cudaStream_t s);
-cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
-                              float inv_c, cudaStream_t s);
 
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);

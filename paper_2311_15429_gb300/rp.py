@@ -31,7 +31,8 @@ class rp_config(ctypes.Structure):
     _fields_ = [("c", ctypes.c_double), ("dt", ctypes.c_double), ("history_depth", ctypes.c_int),
                 ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("far_points", ctypes.c_int),
                 ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int), ("mac_warps", ctypes.c_int),
-                ("profile_every", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("profile_every", ctypes.c_int), ("far_source_points", ctypes.c_int),
+                ("device_budget", ctypes.c_longlong), ("reserved", ctypes.c_int * 4)]
 
 
 class rp_pair_info_t(ctypes.Structure):
@@ -106,6 +107,7 @@ SIGNATURES = {
     "rp_kernel_stats": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong),
                              ctypes.POINTER(ctypes.c_double), _I]),
     "rp_kernel_count": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong)]),
+    "rp_set_profiling": (_I, [_V, _I]),
     "rp_selftest_wait": (_I, [_V, ctypes.c_longlong]),
     "rp_graph_capture": (_I, [_V, _PP, _PP, _PP, _PP]),
     "rp_graph_step": (_I, [_V]),
@@ -194,11 +196,12 @@ def rp_last_error(ctx) -> str:
 
 def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
               flags: int = 0, device: int = 0, stream=None, far_distance: float = 0.0,
-              far_points: int = 0, far_batch: int = 0, mac_warps: int = 0, profile_every: int = 0):
+              far_points: int = 0, far_batch: int = 0, mac_warps: int = 0, profile_every: int = 0,
+              far_source_points: int = 0, device_budget: int = 0):
     """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream (NULL without torch)."""
     cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch, mac_warps,
-                    profile_every)
+                    profile_every, far_source_points, device_budget)
     if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
         try:
             import torch
@@ -419,6 +422,11 @@ def rp_selftest_wait(ctx, limit_cycles: int):
     _check(load().rp_selftest_wait(ctx, int(limit_cycles)), ctx)
 
 
+def rp_set_profiling(ctx, every: int):
+    """Per-launch CUDA events on the launches of steps s % every == 0 (every >= 1), or off (0)."""
+    _check(load().rp_set_profiling(ctx, int(every)), ctx)
+
+
 def rp_kernel_count(ctx, kind: int) -> int:
     n = ctypes.c_longlong()
     _check(load().rp_kernel_count(ctx, kind, ctypes.byref(n)), ctx)
@@ -446,11 +454,13 @@ class RetardedPotentials:
     def __init__(self, domains, c: float, dt: float, history_depth: int = 0,
                  mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
                  far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0,
-                 mac_warps: int = 0, profile_every: int = 0):
+                 mac_warps: int = 0, profile_every: int = 0, far_source_points: int = 0,
+                 device_budget: int = 0):
         import torch
         self.domains = list(domains)
         self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
-                             far_points, far_batch, mac_warps, profile_every)
+                             far_points, far_batch, mac_warps, profile_every, far_source_points,
+                             device_budget)
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)

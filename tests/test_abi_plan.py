@@ -190,7 +190,8 @@ def test_config_validation():
     """Out-of-range configuration fields are refused at rp_create."""
     bad = [dict(mac_warps=10), dict(mac_warps=-8), dict(mode=rp.RP_MODE_LOWRANK, far_distance=0.0),
            dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=12),
-           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9), dict(profile_every=-1)]
+           dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9), dict(profile_every=-1),
+           dict(far_source_points=1), dict(far_source_points=9), dict(device_budget=-1)]
     for kw in bad:
         with pytest.raises(rp.RPError) as e:
             rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, **kw)
@@ -292,3 +293,33 @@ def test_history_spill_follows_each_pairs_lag_window(distance):
             assert q["host_bytes"] == 0
     finally:
         rp.rp_destroy(ctx)
+
+
+def test_device_budget_refuses_a_plan_beyond_it():
+    """An allocation budget below the planned device memory makes rp_finalize
+    return RP_ERR_OOM (the injected allocation failure: no allocator is
+    called); the same plan passes with a budget at its planned size."""
+    w = synth.workload("cfg2")
+    ctx = rp.rp_create(w.c, w.dt, history_depth=w.history, flags=rp.RP_FLAG_PLAN_ONLY)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        need = rp.rp_query(ctx)["device_bytes"]
+    finally:
+        rp.rp_destroy(ctx)
+    assert need > 2 ** 30
+    for budget, ok in ((need - 1, False), (need, True)):
+        ctx = rp.rp_create(w.c, w.dt, history_depth=w.history, flags=rp.RP_FLAG_PLAN_ONLY, device_budget=budget)
+        try:
+            for d in w.domains:
+                rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+            if ok:
+                rp.rp_finalize(ctx)
+            else:
+                with pytest.raises(rp.RPError) as e:
+                    rp.rp_finalize(ctx)
+                assert e.value.status == rp.RP_ERR_OOM
+                assert "budget" in rp.rp_last_error(ctx)
+        finally:
+            rp.rp_destroy(ctx)

@@ -81,7 +81,8 @@ def test_committed_profiles_name_existing_sources():
 def test_plain_path_flops_and_alu_peak():
     assert bench.DIRECT_FLOPS_PER_PAIR_POINT == 34
     assert bench.FP32_PEAK_TFLOPS == pytest.approx(152 * 128 * 2 * 2.070e9 / 1e12)
-    assert bench.profile_every(10) == 1 and bench.profile_every(10 * bench.PROFILE_EVERY) == bench.PROFILE_EVERY
+    assert bench.kernel_pass_steps(5) == 20 and bench.kernel_pass_steps(20) == 20
+    assert bench.kernel_pass_steps(10 ** 6) == bench.KERNEL_PASS_STEPS
 
 
 def test_cfg2_far_gemm_bytes():

@@ -74,3 +74,20 @@ def test_reference_arm_prints_on_rank_zero_only():
     assert line["cpu_baseline"]["cores"] >= 1 and line["cpu_baseline"]["sample"]
     assert line["e2e"] == {"value": line["value"], "unit": line["unit"], "h2d_bytes_per_step": 0,
                            "d2h_bytes_per_step": 0}
+
+
+def test_reference_arm_loads_only_the_oracle():
+    """The reference arm is the FP64 oracle alone: after a run, the process
+    has mapped the oracle's library and not the product's (the history depth
+    it pre-fills comes from the oracle's own geometry, not from a plan of the
+    product library)."""
+    code = ("import runpy, sys\n"
+            f"sys.argv = ['bench.py', '--impl', 'reference', '--steps', '1', '--warmup', '0', '--workload', 'cfg1']\n"
+            f"runpy.run_path({os.path.join(ROOT, 'bench.py')!r}, run_name='__main__')\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "assert 'librp_oracle.so' in maps, 'oracle not loaded'\n"
+            "assert '/librp.so' not in maps, 'product library loaded by the reference arm'\n"
+            "print('MAPS_OK')\n")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    assert "MAPS_OK" in r.stdout
