@@ -130,6 +130,19 @@ typedef enum {
  * of windows; spectral_bytes then includes the window rings, their input
  * slices and a three-slot staging ring per spilled source. */
 #define RP_FLAG_HISTORY_SPILL 0x20u
+/* FP64 error audit on the GPU (rp_audit, rp_audit_values): every source
+ * keeps a raw (rho, J) ring as deep as its deepest pair reads (16 B per point
+ * and step, in rp_stats.device_bytes), written at every push. */
+#define RP_FLAG_AUDIT 0x40u
+/* Compensated pair sum: the spectral sum over a target's (source, lag)
+ * entries (Eq. 12 per spectral coefficient, before the one inverse FFT per
+ * target and field) is Kahan-compensated in FP32, so that its rounding stays
+ * near one rounding of the sum of magnitudes however many entries a target
+ * has; without the flag it is a plain FP32 multiply-add chain, whose error
+ * grows like the square root of the entry count.  The MAC then runs one
+ * variant (12 multiply-add warps, 3 inverse-FFT warps; rp_config.mac_warps
+ * must be 0 or 12). */
+#define RP_FLAG_COMPENSATED 0x80u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
@@ -198,6 +211,8 @@ typedef struct {
     int spill_windows;        /* RP_FLAG_HISTORY_SPILL: lag windows read from host-refilled window rings */
     int reserved;
     long long host_bytes;     /* pinned host memory of the spilled history ((rho, J) slices) */
+    double audit_rel_l2;      /* largest per-(domain, field) rel-L2 of the last rp_audit, -1 before the first */
+    long long audit_step;     /* the step it audited, -1 before the first */
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -565,6 +580,38 @@ typedef struct {
 } rp_train_report;
 
 rp_status rp_train_far_model(rp_ctx *ctx, const rp_train_config *cfg, rp_train_report *report);
+
+/*
+ * rp_audit_values -- under RP_FLAG_AUDIT: the potentials of the last
+ * complete step at `count` nodes h_nodes[] (host, node ids of domain
+ * `target`) in FP64, into host h_out[count][4] (phi, Ax, Ay, Az): the plain
+ * direct retarded sum of Eq. 8 with the hat interpolation of Eq. 7 over
+ * every source node of every domain (the cell average C h^2 at R = 0, lag
+ * 0), from the context's own history, on the GPU in FP64 (one block per
+ * node, per-thread sums added in a fixed tree order).  It reads the same
+ * FP32 samples as the evaluation, so it scores the path alone.  Under
+ * RP_FLAG_GROUND_STATE_SPLIT it gives the induced part, as rp_evaluate does.
+ * Synchronous on the context stream; allocates its scratch on first use.
+ * RP_ERR_STATE without the flag or inside a partly pushed step,
+ * RP_ERR_HISTORY as for rp_evaluate, RP_ERR_ARG for bad nodes.
+ */
+rp_status rp_audit_values(rp_ctx *ctx, int target, const long long *h_nodes, int count, double *h_out);
+
+/*
+ * rp_audit -- under RP_FLAG_AUDIT: the FP64 error audit of an evaluation.
+ * d_phi / d_A are the device outputs rp_evaluate wrote for the last complete
+ * step (as for rp_evaluate).  In every domain, min(nodes_per_domain, N)
+ * nodes are drawn (one from each of that many equal strata of the node ids,
+ * seeded); the FP64 sums of rp_audit_values there are compared with the
+ * outputs, and h_rel_l2[4 * n + f] (host, may be NULL) gets
+ * ||out - ref||_2 / ||ref||_2 over the sampled nodes of domain n for field
+ * f (phi, Ax, Ay, Az).  The largest is kept for rp_stats.audit_rel_l2.
+ * Synchronous.  Errors as for rp_audit_values; RP_ERR_ARG for
+ * nodes_per_domain < 1 or NULL buffers.  (The final error audit in FP64 on
+ * the GPU is a property of the library; the paper states no error measure.)
+ */
+rp_status rp_audit(rp_ctx *ctx, const float *const *d_phi, const float *const *d_A, int nodes_per_domain,
+                   unsigned long long seed, double *h_rel_l2);
 
 /* rp_sync -- wait for the context's stream; reports asynchronous failures. */
 rp_status rp_sync(rp_ctx *ctx);

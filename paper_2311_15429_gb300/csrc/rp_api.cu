@@ -550,6 +550,10 @@ rp_status build_learned(rp_ctx *ctx, const std::vector<float> &weights, const st
 // size class.  Every variant reads the same data and sums in the same order.
 rp_status autotune_mac(rp_ctx *ctx)
 {
+    if (ctx->comp) {   // one compensated variant
+        std::fill(std::begin(ctx->mac_cw), std::end(ctx->mac_cw), kCompWarps);
+        return RP_OK;
+    }
     if (!ctx->tma || ctx->cfg.mac_warps) return RP_OK;
     cudaEvent_t a = nullptr, b = nullptr;
     RP_CUDA(ctx, cudaEventCreate(&a));
@@ -562,7 +566,7 @@ rp_status autotune_mac(rp_ctx *ctx)
         float best = 1e30f;
         for (int cw : {8, 12, 16}) {
             auto go = [&] {
-                return launch_mac_tma(g.cls, cw, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries, step, 0,
+                return launch_mac_tma(g.cls, cw, false, ctx->d_inv, g.i0, g.i1, g.blk0, ntiles, ctx->d_entries, step, 0,
                                       ctx->mac_stages[slot], std::min(ntiles, ctx->sm_count), ctx->d_err,
                                       ctx->stream);
             };
@@ -635,6 +639,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
     }
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
+    if ((cfg->flags & RP_FLAG_COMPENSATED) && cfg->mac_warps != 0 && cfg->mac_warps != kCompWarps) return RP_ERR_ARG;
     if (cfg->profile_every < 0 || cfg->device_budget < 0) return RP_ERR_ARG;
     if (cfg->far_source_points != 0 && (cfg->far_source_points < 2 || cfg->far_source_points > kMaxFarPts))
         return RP_ERR_ARG;
@@ -646,6 +651,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
     ctx->split = (cfg->flags & RP_FLAG_GROUND_STATE_SPLIT) != 0;
     ctx->spill = (cfg->flags & RP_FLAG_HISTORY_SPILL) != 0;
+    ctx->comp = (cfg->flags & RP_FLAG_COMPENSATED) != 0;
     // the split's histories are zero before the first push: the clamped reads
     // of steps before it read the zeroed slot of step 0
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0 || ctx->split;
@@ -938,6 +944,10 @@ rp_status rp_finalize(rp_ctx *ctx)
         }
     }
     if (max_nlag > 600) return fail(ctx, RP_ERR_UNSUPPORTED, "direct pair lag window above 600 steps");
+    // FP64 audit: every source keeps its raw slices as deep as its deepest pair reads
+    if (ctx->cfg.flags & RP_FLAG_AUDIT)
+        for (int t = 0; t < nd; ++t)
+            for (int s = 0; s < nd; ++s) rdepth[s] = std::max(rdepth[s], ctx->pairs[(size_t)t * nd + s].lag_hi + 1);
     ctx->smem_dir = smem_direct(max_nlag);
     ctx->raw_block0.assign(nd + 1, 0);
     for (int d = 0; d < nd; ++d) {
@@ -1523,11 +1533,12 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         const int ntiles = g.blk1 - g.blk0;
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
                  if (ctx->tma && g.cls > 0)
-                     return launch_mac_tma(g.cls, ctx->mac_cw[class_slot(g.cls)], ctx->d_inv, g.i0, g.i1, g.blk0,
+                     return launch_mac_tma(g.cls, ctx->mac_cw[class_slot(g.cls)], ctx->comp, ctx->d_inv, g.i0, g.i1,
+                                           g.blk0,
                                            ntiles, ctx->d_entries, kstep, clamp,
                                            ctx->mac_stages[class_slot(g.cls)],
                                            std::min(ntiles, ctx->sm_count), ctx->d_err, ctx->stream);
-                 return launch_mac_inv_column(g.cls, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,
+                 return launch_mac_inv_column(g.cls, ctx->comp, ctx->d_inv, g.i0, g.i1, g.blk0, ctx->d_entries, ntiles,
                                               ctx->smem_mac, kstep, clamp, ctx->stream);
              })))
             return st;
@@ -2098,6 +2109,8 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->npairs_learned = ctx->npairs_learned;
     out->spill_windows = (int)ctx->spill_wins.size();
     out->host_bytes = ctx->host_bytes;
+    out->audit_rel_l2 = ctx->audit_rel_l2;
+    out->audit_step = ctx->audit_step;
     out->mac_warps = 0;
     for (const LaunchGroup &g : ctx->inv_groups)
         if (g.cls > 0 && ctx->tma) out->mac_warps = ctx->mac_cw[class_slot(g.cls)];

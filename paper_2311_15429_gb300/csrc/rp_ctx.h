@@ -90,6 +90,7 @@ struct rp_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;
     bool plan_only = false, clamp = false, profile = false;
+    bool comp = false;   // RP_FLAG_COMPENSATED: Kahan-compensated spectral sums
     // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
     // and the static potential P(0), [4][N] per domain
     bool split = false, static_done = false, computing_static = false;
@@ -206,6 +207,11 @@ struct rp_ctx {
     std::vector<char> net_pair;       // [t * ndom + s]: the pair uses the network (else the linear skip alone)
     int smem_optin = 0;
     float *noalloc_stage = nullptr;   // device address of rp_evaluate_host_noalloc's fixed array (set at finalize)
+    // FP64 audit (RP_FLAG_AUDIT): its device scratch and the last result
+    char *audit_buf = nullptr;
+    int audit_cap = 0;                // points the scratch holds
+    double audit_rel_l2 = -1.0;       // largest rel-L2 of the last rp_audit, -1 before the first
+    long long audit_step = -1;
     // Host-buffer calls: device staging per domain ([4][N]), two sets
     // alternating by step parity, and a copy stream, so that a step's copies
     // run while the kernels of the steps around it do; events order the two

@@ -362,10 +362,20 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
     }
 }
 
+// Kahan-compensated addition (the total is s - c; see k_mac_tma).
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // Spectral multiply-accumulate over the target's (source, lag) entries for
 // one (kx, 16-ky) column block and all four fields, then the inverse FFT
-// along z of the 64 columns; rows z < nz of the target go to T2.
-template <int M>
+// along z of the 64 columns; rows z < nz of the target go to T2.  COMP: the
+// sum over entries is Kahan-compensated per spectral coefficient.
+template <int M, bool COMP>
 __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__restrict__ tgts, int t0, int t1,
                                                                int block_lo, const MacEntry *__restrict__ entries,
                                                                long long step, int clamp)
@@ -404,11 +414,15 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
         const int p = threadIdx.x & 7, r0 = threadIdx.x >> 3;
 #pragma unroll 1
         for (int ch = 0; ch < NCH; ++ch) {
-            float4 a[4][CH];
+            float4 a[4][CH], cmp[4][COMP ? CH : 1];
 #pragma unroll
             for (int f = 0; f < 4; ++f)
 #pragma unroll
                 for (int j = 0; j < CH; ++j) a[f][j] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int f = 0; f < 4; ++f)
+#pragma unroll
+                for (int j = 0; j < (COMP ? CH : 1); ++j) cmp[f][j] = make_float4(0.f, 0.f, 0.f, 0.f);
             long long off[CH];
             bool ok[CH];
 #pragma unroll
@@ -436,10 +450,18 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
                 for (int jj = 0; jj < CH; ++jj)
 #pragma unroll
                     for (int f = 0; f < 4; ++f) {
-                        a[f][jj].x = fmaf(g[jj].x, s[f][jj].x, a[f][jj].x);
-                        a[f][jj].y = fmaf(g[jj].x, s[f][jj].y, a[f][jj].y);
-                        a[f][jj].z = fmaf(g[jj].y, s[f][jj].z, a[f][jj].z);
-                        a[f][jj].w = fmaf(g[jj].y, s[f][jj].w, a[f][jj].w);
+                        if constexpr (COMP) {
+                            float4 &c = cmp[f][COMP ? jj : 0];
+                            kahan_add(a[f][jj].x, c.x, g[jj].x * s[f][jj].x);
+                            kahan_add(a[f][jj].y, c.y, g[jj].x * s[f][jj].y);
+                            kahan_add(a[f][jj].z, c.z, g[jj].y * s[f][jj].z);
+                            kahan_add(a[f][jj].w, c.w, g[jj].y * s[f][jj].w);
+                        } else {
+                            a[f][jj].x = fmaf(g[jj].x, s[f][jj].x, a[f][jj].x);
+                            a[f][jj].y = fmaf(g[jj].x, s[f][jj].y, a[f][jj].y);
+                            a[f][jj].z = fmaf(g[jj].y, s[f][jj].z, a[f][jj].z);
+                            a[f][jj].w = fmaf(g[jj].y, s[f][jj].w, a[f][jj].w);
+                        }
                     }
             }
 #pragma unroll 2
@@ -463,10 +485,18 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
                     for (int f = 0; f < 4; ++f) {
                         float4 &x = a[f][jj];
                         const float4 gg = g[jj], ss = s[f][jj];
-                        x.x = fmaf(gg.x, ss.x, fmaf(-gg.y, ss.y, x.x));
-                        x.y = fmaf(gg.x, ss.y, fmaf(gg.y, ss.x, x.y));
-                        x.z = fmaf(gg.z, ss.z, fmaf(-gg.w, ss.w, x.z));
-                        x.w = fmaf(gg.z, ss.w, fmaf(gg.w, ss.z, x.w));
+                        if constexpr (COMP) {
+                            float4 &c = cmp[f][COMP ? jj : 0];
+                            kahan_add(x.x, c.x, fmaf(gg.x, ss.x, -gg.y * ss.y));
+                            kahan_add(x.y, c.y, fmaf(gg.x, ss.y, gg.y * ss.x));
+                            kahan_add(x.z, c.z, fmaf(gg.z, ss.z, -gg.w * ss.w));
+                            kahan_add(x.w, c.w, fmaf(gg.z, ss.w, gg.w * ss.z));
+                        } else {
+                            x.x = fmaf(gg.x, ss.x, fmaf(-gg.y, ss.y, x.x));
+                            x.y = fmaf(gg.x, ss.y, fmaf(gg.y, ss.x, x.y));
+                            x.z = fmaf(gg.z, ss.z, fmaf(-gg.w, ss.w, x.z));
+                            x.w = fmaf(gg.z, ss.w, fmaf(gg.w, ss.z, x.w));
+                        }
                     }
             }
 #pragma unroll
@@ -475,6 +505,10 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
                 const int row = r0 + 32 * (ch * CH + jj);
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
+                    if constexpr (COMP) {
+                        const float4 &c = cmp[f][COMP ? jj : 0];
+                        a[f][jj] = make_float4(a[f][jj].x - c.x, a[f][jj].y - c.y, a[f][jj].z - c.z, a[f][jj].w - c.w);
+                    }
                     float2 *d = acc + f * fs + row * kTileYPad + 2 * p;
                     d[0] = make_float2(a[f][jj].x, a[f][jj].y);
                     d[1] = make_float2(a[f][jj].z, a[f][jj].w);
@@ -484,25 +518,37 @@ __global__ void __launch_bounds__(kThreads) k_mac_inv_column(const InvTarget *__
     } else {
         for (int i = threadIdx.x; i < 4 * fs; i += blockDim.x) acc[i] = make_float2(0.0f, 0.0f);
         __syncthreads();
-        // Each thread owns the (kz, c) cells i = threadIdx.x + k*blockDim.x, the
-        // same for every entry, so no barrier is needed between entries.
-        for (int e = T.e0; e < T.e1; ++e) {
-            const MacEntry E = entries[e];
-            long long j = step - E.lag;
-            if (clamp && j < 0) j = 0;
-            const float2 *S = E.ring + (j % E.depth) * E.slot_elems + 4 * col0;
-            const float *Gr = static_cast<const float *>(E.g) + col0;
-            const float2 *Gc = static_cast<const float2 *>(E.g) + col0;
-            for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
-                const int kz = i / kTileY, c = i % kTileY;
-                if (c >= ncols) continue;
-                const long long off = kz * kTileY + c;
-                const float2 g = E.is_real ? make_float2(__ldg(Gr + off), 0.0f) : __ldg(Gc + off);
-                const int a_ = kz * kTileYPad + c;
+        // Each thread owns the (kz, c) cells i = threadIdx.x + k*blockDim.x and
+        // sums every entry of one cell in registers (entries in order, the
+        // warp's lanes reading consecutive cells of an entry), then stores it.
+        for (int i = threadIdx.x; i < mz * kTileY; i += blockDim.x) {
+            const int kz = i / kTileY, c = i % kTileY;
+            if (c >= ncols) continue;
+            const long long off = kz * kTileY + c;
+            float2 v[4], cv[4];
 #pragma unroll
-                for (int f = 0; f < 4; ++f)
-                    acc[f * fs + a_] = cadd(acc[f * fs + a_], cmul(g, __ldg(S + f * fstride + off)));
+            for (int f = 0; f < 4; ++f) v[f] = cv[f] = make_float2(0.0f, 0.0f);
+            for (int e = T.e0; e < T.e1; ++e) {
+                const MacEntry E = entries[e];
+                long long j = step - E.lag;
+                if (clamp && j < 0) j = 0;
+                const float2 *S = E.ring + (j % E.depth) * E.slot_elems + 4 * col0;
+                const float2 g = E.is_real ? make_float2(__ldg(static_cast<const float *>(E.g) + col0 + off), 0.0f)
+                                           : __ldg(static_cast<const float2 *>(E.g) + col0 + off);
+#pragma unroll
+                for (int f = 0; f < 4; ++f) {
+                    const float2 t = cmul(g, __ldg(S + f * fstride + off));
+                    if constexpr (COMP) {
+                        kahan_add(v[f].x, cv[f].x, t.x);
+                        kahan_add(v[f].y, cv[f].y, t.y);
+                    } else {
+                        v[f] = cadd(v[f], t);
+                    }
+                }
             }
+            const int a_ = kz * kTileYPad + c;
+#pragma unroll
+            for (int f = 0; f < 4; ++f) acc[f * fs + a_] = COMP ? make_float2(v[f].x - cv[f].x, v[f].y - cv[f].y) : v[f];
         }
     }
     __syncthreads();
@@ -775,7 +821,10 @@ cudaError_t open_kernel_smem_limits(int max_optin)
         return e;                                                                                           \
     if ((e = cudaFuncSetAttribute(k_fwd_column<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
         return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M>, cudaFuncAttributeMaxDynamicSharedMemorySize,         \
+    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
+                                  max_optin)))                                                              \
+        return e;                                                                                           \
+    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
                                   max_optin)))                                                              \
         return e;                                                                                           \
     if ((e = cudaFuncSetAttribute(k_inv_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
@@ -825,13 +874,19 @@ cudaError_t launch_fwd_column(int cls, const FwdRing *d_rings, int r0, int r1, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_mac_inv_column(int cls, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+cudaError_t launch_mac_inv_column(int cls, bool comp, const InvTarget *d_tgts, int t0, int t1, int block_lo,
                                   const MacEntry *d_entries, int nblocks, size_t smem, long long step, int clamp,
                                   cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_mac_inv_column, kThreads, d_tgts, t0, t1, block_lo, d_entries, step, clamp)
+#define X(M)                                                                                                   \
+    case M:                                                                                                    \
+        if (cudaError_t e_ = launch_pdl(comp ? k_mac_inv_column<M, true> : k_mac_inv_column<M, false>,        \
+                                        dim3(nblocks), dim3(kThreads), smem, s, d_tgts, t0, t1, block_lo,      \
+                                        d_entries, step, clamp))                                               \
+            return e_;                                                                                         \
+        break;
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;

@@ -189,7 +189,7 @@ cudaError_t launch_fwd_plane(int size_class, const FwdRing *d_rings, const IoPtr
                              int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s);
 cudaError_t launch_fwd_column(int size_class, const FwdRing *d_rings, int r0, int r1, int block_lo,
                               int nblocks, size_t smem, long long step, cudaStream_t s);
-cudaError_t launch_mac_inv_column(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+cudaError_t launch_mac_inv_column(int size_class, bool comp, const InvTarget *d_tgts, int t0, int t1, int block_lo,
                                   const MacEntry *d_entries, int nblocks, size_t smem, long long step,
                                   int clamp, cudaStream_t s);
 cudaError_t launch_inv_plane(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
@@ -213,9 +213,11 @@ int mac_tma_stages(int M, int smem_optin);
 cudaError_t launch_wait_selftest(long long limit_cycles, int *d_err, cudaStream_t s);
 size_t mac_tma_smem(int M, int nstages);
 cudaError_t open_mac_tma_smem_limit(int max_optin);
-cudaError_t launch_mac_tma(int cls, int consumer_warps, const InvTarget *d_tgts, int t0, int t1, int tile_lo,
-                           int ntiles, const MacEntry *d_entries, long long step, int clamp, int nstages, int grid,
-                           int *d_err, cudaStream_t s);
+// comp: the Kahan-compensated variant (consumer_warps must be kCompWarps)
+constexpr int kCompWarps = 12;
+cudaError_t launch_mac_tma(int cls, int consumer_warps, bool comp, const InvTarget *d_tgts, int t0, int t1,
+                           int tile_lo, int ntiles, const MacEntry *d_entries, long long step, int clamp, int nstages,
+                           int grid, int *d_err, cudaStream_t s);
 
 // tcgen05 bf16 GEMM (rp_gemm_tc.cu): D (M x N fp32) = A (M x K) * B (N x K)^T
 bool encode_bf16_rows(void *encode_fn, struct CUtensorMap_st *map, const void *base, uint64_t rows,

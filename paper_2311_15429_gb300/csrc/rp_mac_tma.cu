@@ -135,6 +135,17 @@ __device__ __forceinline__ int owner(const T *arr, int lo, int hi, int b, int T:
     return lo;
 }
 
+// Kahan-compensated addition: s + c carries the sum of the added terms with
+// the rounding of each addition kept in c (the error stays near one rounding
+// of the sum of magnitudes, whatever the number of terms); the total is s - c.
+__device__ __forceinline__ void kahan_add(float &s, float &c, float x)
+{
+    const float y = x - c;
+    const float t = s + y;
+    c = (t - s) - y;
+    s = t;
+}
+
 // barrier `id` among the first (or last) `threads` threads of the block
 __device__ __forceinline__ void named_sync(int id, int threads)
 {
@@ -191,11 +202,17 @@ __device__ __forceinline__ void column_fft_store(float2 *acc, const InvTarget &T
     }
 }
 
+// Warps of the inverse column FFT: fewer in the compensated variant, whose
+// MAC warps hold twice the accumulators and need the registers.
+template <bool COMP>
+__host__ __device__ constexpr int fft_warps() { return COMP ? 3 : kFftWarps; }
+
 // M: padded FFT size of the class; CW: multiply-accumulate warps (the block
-// has CW + kFftWarps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
-// are contiguous in the ring).
-template <int M, int CW, int FPC>
-__global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
+// has CW + fft_warps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
+// are contiguous in the ring); COMP: the sum over (source, lag) entries is
+// Kahan-compensated per spectral coefficient (RP_FLAG_COMPENSATED).
+template <int M, int CW, int FPC, bool COMP>
+__global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
     k_mac_tma(const InvTarget *__restrict__ tgts, int t0, int t1, int tile_lo, int ntiles,
               const MacEntry *__restrict__ entries, long long step, int clamp, int ns, int *err)
 {
@@ -203,7 +220,7 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
     constexpr int SSTAGE = FPC * STAGE;             // FPC field tiles of one entry
     constexpr int NG = kKernelStages;
     constexpr int kConsumerWarps = CW;
-    constexpr int FW = kFftWarps;
+    constexpr int FW = fft_warps<COMP>();
     constexpr int RSTEP = kConsumerWarps * 32 / 8;   // rows covered by one pass of the consumers
     constexpr int ROWS = (M + RSTEP - 1) / RSTEP;
     constexpr int NTY = M / kTileY;
@@ -361,10 +378,15 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
         const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
 
         float4 a[ROWS][4];
+        float4 cmp[COMP ? ROWS : 1][4];   // Kahan compensation (COMP only)
 #pragma unroll
         for (int i = 0; i < ROWS; ++i)
 #pragma unroll
             for (int f = 0; f < 4; ++f) a[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < (COMP ? ROWS : 1); ++i)
+#pragma unroll
+            for (int f = 0; f < 4; ++f) cmp[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
 
         for (int e = T.e0; e < T.er; ++e) {   // real kernels (self pair)
             float2 g[ROWS];
@@ -388,10 +410,18 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
                         const int r = r0 + RSTEP * i;
                         if (sf && r < M) {
                             const float4 s = S4[r * 8 + p];
-                            a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
-                            a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
-                            a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
-                            a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                            if constexpr (COMP) {
+                                float4 &c = cmp[COMP ? i : 0][f];
+                                kahan_add(a[i][f].x, c.x, g[i].x * s.x);
+                                kahan_add(a[i][f].y, c.y, g[i].x * s.y);
+                                kahan_add(a[i][f].z, c.z, g[i].y * s.z);
+                                kahan_add(a[i][f].w, c.w, g[i].y * s.w);
+                            } else {
+                                a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
+                                a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
+                                a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
+                                a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                            }
                         }
                     }
                 }
@@ -421,10 +451,18 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
                         if (sf && r < M) {
                             const float4 s = S4[r * 8 + p];
                             float4 &x = a[i][f];
-                            x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
-                            x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
-                            x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
-                            x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                            if constexpr (COMP) {
+                                float4 &c = cmp[COMP ? i : 0][f];
+                                kahan_add(x.x, c.x, fmaf(g[i].x, s.x, -g[i].y * s.y));
+                                kahan_add(x.y, c.y, fmaf(g[i].x, s.y, g[i].y * s.x));
+                                kahan_add(x.z, c.z, fmaf(g[i].z, s.z, -g[i].w * s.w));
+                                kahan_add(x.w, c.w, fmaf(g[i].z, s.w, g[i].w * s.z));
+                            } else {
+                                x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
+                                x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
+                                x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
+                                x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                            }
                         }
                     }
                 }
@@ -440,6 +478,10 @@ __global__ void __launch_bounds__((CW + kFftWarps + 1) * 32, 1)
                 if (r >= M) continue;
 #pragma unroll
                 for (int f = 0; f < 4; ++f) {
+                    if constexpr (COMP) {   // the compensated total
+                        const float4 &c = cmp[COMP ? i : 0][f];
+                        a[i][f] = make_float4(a[i][f].x - c.x, a[i][f].y - c.y, a[i][f].z - c.z, a[i][f].w - c.w);
+                    }
                     float2 *d = acc + f * FS + r * kTileYPad + 2 * p;
                     d[0] = make_float2(a[i][f].x, a[i][f].y);
                     d[1] = make_float2(a[i][f].z, a[i][f].w);
@@ -492,35 +534,41 @@ size_t mac_tma_smem(int M, int nstages)
 cudaError_t open_mac_tma_smem_limit(int max_optin)
 {
     cudaError_t e;
-#define X(M, F)                                                                                            \
-    if ((e = cudaFuncSetAttribute(k_mac_tma<M, 8, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) ||  \
-        (e = cudaFuncSetAttribute(k_mac_tma<M, 12, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)) || \
-        (e = cudaFuncSetAttribute(k_mac_tma<M, 16, F>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))   \
+#define X(M, F)                                                                                                   \
+    if ((e = cudaFuncSetAttribute(k_mac_tma<M, 8, F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,        \
+                                  max_optin)) ||                                                                  \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 12, F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                  max_optin)) ||                                                                  \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, 16, F, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,       \
+                                  max_optin)) ||                                                                  \
+        (e = cudaFuncSetAttribute(k_mac_tma<M, kCompWarps, F, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                  max_optin)))                                                                    \
         return e;
     RP_TMA_CLASSES(X)
 #undef X
     return cudaSuccess;
 }
 
-cudaError_t launch_mac_tma(int cls, int cw, const InvTarget *d_tgts, int t0, int t1, int tile_lo, int ntiles,
-                           const MacEntry *d_entries, long long step, int clamp, int nstages, int grid, int *d_err,
-                           cudaStream_t s)
+cudaError_t launch_mac_tma(int cls, int cw, bool comp, const InvTarget *d_tgts, int t0, int t1, int tile_lo,
+                           int ntiles, const MacEntry *d_entries, long long step, int clamp, int nstages, int grid,
+                           int *d_err, cudaStream_t s)
 {
     if (ntiles <= 0) return cudaSuccess;
-    if (cw != 8 && cw != 12 && cw != 16) return cudaErrorInvalidValue;
+    if (comp ? cw != kCompWarps : (cw != 8 && cw != 12 && cw != 16)) return cudaErrorInvalidValue;
     if (nstages < 2 || nstages > kMaxStages) return cudaErrorInvalidValue;
     const size_t smem = mac_tma_smem(cls, nstages);
-    const int threads = (cw + kFftWarps + 1) * 32;
+    const int threads = (cw + (comp ? fft_warps<true>() : fft_warps<false>()) + 1) * 32;
     cudaError_t e = cudaSuccess;
-#define RP_GO(M, CW, F)                                                                                   \
-    e = launch_pdl(k_mac_tma<M, CW, F>, dim3(grid), dim3(threads), smem, s, d_tgts, t0, t1, tile_lo, ntiles, \
+#define RP_GO(M, CW, F, C)                                                                                   \
+    e = launch_pdl(k_mac_tma<M, CW, F, C>, dim3(grid), dim3(threads), smem, s, d_tgts, t0, t1, tile_lo, ntiles, \
                    d_entries, step, clamp, nstages, d_err)
     switch (cls) {
 #define X(M, F)                                                                                         \
     case M:                                                                                             \
-        if (cw == 8) RP_GO(M, 8, F);                                                                    \
-        else if (cw == 12) RP_GO(M, 12, F);                                                             \
-        else RP_GO(M, 16, F);                                                                           \
+        if (comp) RP_GO(M, kCompWarps, F, true);                                                        \
+        else if (cw == 8) RP_GO(M, 8, F, false);                                                        \
+        else if (cw == 12) RP_GO(M, 12, F, false);                                                      \
+        else RP_GO(M, 16, F, false);                                                                    \
         break;
         RP_TMA_CLASSES(X)
 #undef X

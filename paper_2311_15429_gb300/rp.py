@@ -20,6 +20,8 @@ RP_MODE_FFT, RP_MODE_DIRECT, RP_MODE_LOWRANK = 0, 1, 2
 RP_FLAG_GROUND_STATE_CLAMP, RP_FLAG_PLAN_ONLY, RP_FLAG_PROFILE, RP_FLAG_DEFER_FAR = 0x1, 0x2, 0x4, 0x8
 RP_FLAG_GROUND_STATE_SPLIT = 0x10
 RP_FLAG_HISTORY_SPILL = 0x20
+RP_FLAG_AUDIT = 0x40
+RP_FLAG_COMPENSATED = 0x80
 RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
  RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_MOMENTS, RP_K_LEARNED,
@@ -63,7 +65,8 @@ class rp_stats(ctypes.Structure):
                 ("spectral_bytes", ctypes.c_longlong), ("kernel_bytes", ctypes.c_longlong),
                 ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
                 ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("npairs_learned", ctypes.c_int),
-                ("spill_windows", ctypes.c_int), ("reserved", ctypes.c_int), ("host_bytes", ctypes.c_longlong)]
+                ("spill_windows", ctypes.c_int), ("reserved", ctypes.c_int), ("host_bytes", ctypes.c_longlong),
+                ("audit_rel_l2", ctypes.c_double), ("audit_step", ctypes.c_longlong)]
 
 
 class RPError(RuntimeError):
@@ -108,6 +111,8 @@ SIGNATURES = {
                              ctypes.POINTER(ctypes.c_double), _I]),
     "rp_kernel_count": (_I, [_V, _I, ctypes.POINTER(ctypes.c_longlong)]),
     "rp_set_profiling": (_I, [_V, _I]),
+    "rp_audit_values": (_I, [_V, _I, _V, _I, _V]),
+    "rp_audit": (_I, [_V, _PP, _PP, _I, ctypes.c_ulonglong, _V]),
     "rp_selftest_wait": (_I, [_V, ctypes.c_longlong]),
     "rp_graph_capture": (_I, [_V, _PP, _PP, _PP, _PP]),
     "rp_graph_step": (_I, [_V]),
@@ -425,6 +430,27 @@ def rp_selftest_wait(ctx, limit_cycles: int):
 def rp_set_profiling(ctx, every: int):
     """Per-launch CUDA events on the launches of steps s % every == 0 (every >= 1), or off (0)."""
     _check(load().rp_set_profiling(ctx, int(every)), ctx)
+
+
+def rp_audit_values(ctx, target: int, nodes):
+    """FP64 potentials [len(nodes)][4] at node ids of domain ``target``
+    (RP_FLAG_AUDIT), computed on the GPU from the context's history."""
+    import numpy as _np
+    n = _np.ascontiguousarray(nodes, dtype=_np.int64).reshape(-1)
+    out = _np.zeros((n.size, 4), dtype=_np.float64)
+    _check(load().rp_audit_values(ctx, int(target), n.ctypes.data, int(n.size), out.ctypes.data), ctx)
+    return out
+
+
+def rp_audit(ctx, phis: Sequence, As: Sequence, nodes_per_domain: int, seed: int = 0):
+    """rel-L2 [ndomains][4] of the outputs against the GPU's FP64 sums at
+    sampled nodes (RP_FLAG_AUDIT)."""
+    import numpy as _np
+    pp, _a = _ptr_array(phis)
+    pa, _b = _ptr_array(As)
+    out = _np.zeros((len(phis), 4), dtype=_np.float64)
+    _check(load().rp_audit(ctx, pp, pa, int(nodes_per_domain), int(seed), out.ctypes.data), ctx)
+    return out
 
 
 def rp_kernel_count(ctx, kind: int) -> int:
