@@ -134,15 +134,15 @@ typedef enum {
  * keeps a raw (rho, J) ring as deep as its deepest pair reads (16 B per point
  * and step, in rp_stats.device_bytes), written at every push. */
 #define RP_FLAG_AUDIT 0x40u
-/* Compensated pair sum: the spectral sum over a target's (source, lag)
- * entries (Eq. 12 per spectral coefficient, before the one inverse FFT per
- * target and field) is Kahan-compensated in FP32, so that its rounding stays
- * near one rounding of the sum of magnitudes however many entries a target
- * has; without the flag it is a plain FP32 multiply-add chain, whose error
- * grows like the square root of the entry count.  The MAC then runs one
- * variant (12 multiply-add warps, 3 inverse-FFT warps; rp_config.mac_warps
- * must be 0 or 12). */
-#define RP_FLAG_COMPENSATED 0x80u
+/* By default the spectral sum over a target's (source, lag) entries (Eq. 12
+ * per spectral coefficient, before the one inverse FFT per target and field)
+ * is Kahan-compensated in FP32: its rounding stays near one rounding of the
+ * sum of magnitudes however many entries a target has (the MAC then runs one
+ * variant, 12 multiply-add warps and 3 inverse-FFT warps; rp_config.mac_warps
+ * must be 0 or 12).  This flag makes it a plain FP32 multiply-add chain,
+ * whose error grows like the square root of the entry count, with the
+ * autotuned 8/12/16-warp variants. */
+#define RP_FLAG_PLAIN_SUM 0x80u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
@@ -158,7 +158,8 @@ typedef struct {
     int mac_warps;       /* consumer warps of the TMA-fed spectral MAC: 8, 12 or 16, or 0 to let
                           * rp_finalize time the three variants on this plan (two launches each
                           * per FFT size class) and keep the fastest.  The variants sum the same
-                          * terms in the same order: the choice changes timing, never results. */
+                          * terms in the same order: the choice changes timing, never results.
+                          * Only with RP_FLAG_PLAIN_SUM; the compensated sum has one variant (12). */
     int profile_every;   /* RP_FLAG_PROFILE: time the launches of step s only when s % profile_every == 0
                           * (launches outside the step cycle always), >= 0; 0 or 1: every step.  The
                           * events sit between kernels and hold back the next launch, so sampling

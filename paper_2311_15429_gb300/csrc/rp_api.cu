@@ -639,7 +639,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
     }
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
-    if ((cfg->flags & RP_FLAG_COMPENSATED) && cfg->mac_warps != 0 && cfg->mac_warps != kCompWarps) return RP_ERR_ARG;
+    if (!(cfg->flags & RP_FLAG_PLAIN_SUM) && cfg->mac_warps != 0 && cfg->mac_warps != kCompWarps) return RP_ERR_ARG;
     if (cfg->profile_every < 0 || cfg->device_budget < 0) return RP_ERR_ARG;
     if (cfg->far_source_points != 0 && (cfg->far_source_points < 2 || cfg->far_source_points > kMaxFarPts))
         return RP_ERR_ARG;
@@ -651,7 +651,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     ctx->plan_only = (cfg->flags & RP_FLAG_PLAN_ONLY) != 0;
     ctx->split = (cfg->flags & RP_FLAG_GROUND_STATE_SPLIT) != 0;
     ctx->spill = (cfg->flags & RP_FLAG_HISTORY_SPILL) != 0;
-    ctx->comp = (cfg->flags & RP_FLAG_COMPENSATED) != 0;
+    ctx->comp = (cfg->flags & RP_FLAG_PLAIN_SUM) == 0;
     // the split's histories are zero before the first push: the clamped reads
     // of steps before it read the zeroed slot of step 0
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0 || ctx->split;

@@ -90,7 +90,7 @@ struct rp_ctx {
     int device = -1;
     cudaStream_t stream = nullptr;
     bool plan_only = false, clamp = false, profile = false;
-    bool comp = false;   // RP_FLAG_COMPENSATED: Kahan-compensated spectral sums
+    bool comp = true;    // Kahan-compensated spectral sums (off under RP_FLAG_PLAIN_SUM)
     // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
     // and the static potential P(0), [4][N] per domain
     bool split = false, static_done = false, computing_static = false;

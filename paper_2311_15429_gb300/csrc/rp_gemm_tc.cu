@@ -28,94 +28,14 @@
 #include <stdint.h>
 
 #include "rp_internal.h"
+#include "rp_tc.cuh"
 
 namespace rp {
 
 namespace {
 
-constexpr int kBM = 128, kBK = 64;
 constexpr int kGemmThreads = 192;
-constexpr long long kGemmWait = 4000000000LL;
-
-__device__ __forceinline__ uint32_t su32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-__device__ __forceinline__ void bar_init(uint64_t *b, int n)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(b)), "r"(n) : "memory");
-}
-__device__ __forceinline__ void bar_expect(uint64_t *b, uint32_t bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(su32(b)), "r"(bytes) : "memory");
-}
-__device__ __forceinline__ bool bar_try(uint64_t *b, uint32_t parity)
-{
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(su32(b)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-__device__ __forceinline__ bool bar_wait(uint64_t *b, uint32_t parity)
-{
-    if (bar_try(b, parity)) return true;
-    const long long t0 = clock64();
-    while (!bar_try(b, parity))
-        if (clock64() - t0 > kGemmWait) return false;
-    return true;
-}
-
-__device__ __forceinline__ void tma_2d(void *dst, const CUtensorMap *map, int c0, int c1, uint64_t *b)
-{
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-            su32(dst)),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(su32(b))
-        : "memory");
-}
-
-// Shared-memory matrix descriptor: K-major operand written by TMA with the
-// 128-byte swizzle (8 rows x 128 B atoms, 1024 B apart).
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr)
-{
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);   // start address
-    d |= (uint64_t)1 << 16;                     // leading byte offset (unused with this swizzle)
-    d |= (uint64_t)(1024 >> 4) << 32;           // stride byte offset: next 8-row group
-    d |= (uint64_t)1 << 46;                     // descriptor version for this architecture
-    d |= (uint64_t)2 << 61;                     // 128-byte swizzle
-    return d;
-}
-
-// Instruction descriptor, kind::f16: D fp32, A and B both bf16 (f16 = 0) or
-// both fp16 (f16 = 1), both K-major, M = 128, N = BN.
-__host__ __device__ constexpr uint32_t idesc_16bit(int BN, int f16)
-{
-    return (1u << 4) | (f16 ? 0u : (1u << 7) | (1u << 10)) | ((uint32_t)(BN >> 3) << 17) |
-           ((uint32_t)(kBM >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t ad, uint64_t bd, uint32_t id, uint32_t acc)
-{
-    asm volatile(
-        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(ad), "l"(bd), "r"(id), "r"(acc)
-        : "memory");
-}
-
-__device__ __forceinline__ void mma_commit(uint64_t *b)
-{
-    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(su32(b))
-                 : "memory");
-}
-
-template <int BN>
-__device__ __forceinline__ constexpr int tmem_cols()
-{
-    return BN <= 32 ? 32 : (BN <= 64 ? 64 : (BN <= 128 ? 128 : 256));
-}
+using namespace tc;
 
 // blockIdx.y selects a K range of `kchunk` k-tiles (split-K); each split
 // writes its own M x N slice of D (D + split * split_stride).  TERMS = 3:
@@ -234,16 +154,7 @@ __global__ void __launch_bounds__(kGemmThreads, 1)
             for (int c = 0; c < BN; c += 32) {
                 uint32_t r[32];
                 const uint32_t taddr = tmem + ((uint32_t)(32 * quarter) << 16) + (uint32_t)c;
-                asm volatile(
-                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-                    "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-                    : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-                      "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-                      "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
-                      "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
-                      "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-                    : "r"(taddr));
-                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                tmem_ld32(taddr, r);
                 float4 *out = reinterpret_cast<float4 *>(D + (size_t)row * ldd + c);
 #pragma unroll
                 for (int j = 0; j < 8; ++j)

@@ -1,6 +1,7 @@
 // Internal structures shared by the host planner (rp_api.cu) and the kernels.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -150,6 +151,53 @@ struct FarTarget {
     float *cring;            // [depth][r][4]
     int depth;
     int lag_hi_max;          // largest lag of the target's far pairs
+    int task0, task1;        // two-sided factors: this target's CTAs of the gathered GEMM
+};
+
+// ---- two-sided far factors (rp_far2.cu, rp_config.far_source_points > 0)
+//
+// A far source's slice is anterpolated onto q^3 Chebyshev nodes y_b of its
+// box at every push, q_b = sum_k' L_b(r_k') S(k') (tensor-product Lagrange
+// weights), into a node-coefficient history ring: bf16 hi/lo rows
+// [2D][4 fields][2 KS] (hi in columns 0..KS-1, lo in KS..2KS-1) with step j
+// at slots j mod D and j mod D + D (mirrored, so that any window of up to D
+// consecutive steps is one contiguous block of 4 * window rows).
+struct FarSrc2 {
+    int dom;
+    int nx, ny, nz;
+    int qx, qy, qz, r;       // nodes per axis, r = qx*qy*qz <= KS
+    const float *Lx, *Ly, *Lz;   // [n][q] Lagrange weights per axis
+    float *part;             // [nz][4][qy*qx]: per-plane partial sums of one push
+    unsigned int *count;     // planes done in this push (the last plane's block reduces over z)
+    __nv_bfloat16 *qring;    // this source's rows of the shared ring array
+    int qrow0;               // its first row there: source index * 2D * 4
+    int pad_;
+};
+
+// One block of a target's factor: Eq. 11 between the target's r_t nodes
+// (rows, padded to BN) and source src's nodes (columns) for lag `lag`,
+// rows fac_row .. fac_row + BN - 1 of the factor array.
+struct FarKBlock {
+    int src;                 // FarSrc2 index
+    int lag;
+    int fac_row;
+    int pad_;
+};
+
+// One CTA of the gathered GEMM: k-blocks [kb0, kb1) of target `tgt`
+// (FarTarget index); its partial sums go to work slot = its index.
+struct FarTask {
+    int tgt;
+    int kb0, kb1;
+    int pad_;
+};
+
+// Node positions of a factor block's build: target nodes t0 .. t0 + rt - 1,
+// source nodes s0 .. s0 + rs - 1 of the node tables (bohr), source volume.
+struct FarBuild {
+    int t0, rt, s0, rs;
+    int lag, fac_row;
+    double vol;
 };
 
 // Rows of source n's W that belong to target t: row0 + (m - lag_lo) * r + a.
@@ -236,6 +284,19 @@ cudaError_t launch_far_convert(const FarSource *d_srcs, int nsrc, const IoPtrs &
 cudaError_t launch_far_zero(const FarTarget *d_tgts, int ntgt, long long j1, int batch, int max_r, cudaStream_t s);
 cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads, const float *Z, int ldz, long long j0,
                                int batch, cudaStream_t s);
+
+// two-sided far factors (rp_far2.cu)
+cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step,
+                              int D, int KS, cudaStream_t s);
+cudaError_t launch_far_build_fac(const FarBuild *d_blocks, int nblocks, const double *d_tnodes,
+                                 const double *d_snodes, int BN, int KS, double inv_cdt, __nv_bfloat16 *fac,
+                                 cudaStream_t s);
+cudaError_t launch_far_gather(const CUtensorMap &mapQ, const CUtensorMap &mapF, const FarTask *d_tasks, int ntasks,
+                              const FarKBlock *d_kb, int BN, int KS, int D, long long l0, float *work,
+                              int smem_optin, int *d_err, cudaStream_t s);
+cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *work, int BN, long long l0, int batch,
+                              int max_r, cudaStream_t s);
+int far_gather_bn(int r);   // gathered-GEMM column tile for r target nodes (0 if more than 256)
 
 // shared-memory sizes the kernels need for the given shapes
 size_t smem_fwd_plane(int ny, const Axis &ax);

@@ -210,7 +210,8 @@ __host__ __device__ constexpr int fft_warps() { return COMP ? 3 : kFftWarps; }
 // M: padded FFT size of the class; CW: multiply-accumulate warps (the block
 // has CW + fft_warps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
 // are contiguous in the ring); COMP: the sum over (source, lag) entries is
-// Kahan-compensated per spectral coefficient (RP_FLAG_COMPENSATED).
+// Kahan-compensated per spectral coefficient (the default; RP_FLAG_PLAIN_SUM
+// selects the plain chain).
 template <int M, int CW, int FPC, bool COMP>
 __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
     k_mac_tma(const InvTarget *__restrict__ tgts, int t0, int t1, int tile_lo, int ntiles,

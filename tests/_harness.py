@@ -15,6 +15,8 @@ def run_library(domains, c, dt, hists, j0, eval_at, mode=rp.RP_MODE_FFT, flags=0
                 push="all", mac_warps=0):
     """Push every sample of ``hists`` (time index j0 + i) and evaluate at the
     time indices in ``eval_at``.  Returns {time index: [domain][4][N] float32}."""
+    if mac_warps:                   # the warp-count variants are those of the plain FP32 sum
+        flags |= rp.RP_FLAG_PLAIN_SUM
     import torch
     dev = torch.device("cuda", 0)
     T = hists[0].shape[0]

@@ -197,7 +197,12 @@ def test_config_validation():
             rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, **kw)
         assert e.value.status == rp.RP_ERR_ARG, kw
     for cw in (0, 8, 12, 16):
+        rp.rp_destroy(rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY | rp.RP_FLAG_PLAIN_SUM, mac_warps=cw))
+    for cw in (0, 12):   # the compensated sum (default) has the 12-warp variant only
         rp.rp_destroy(rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_warps=cw))
+    for cw in (8, 16):
+        with pytest.raises(rp.RPError):
+            rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_warps=cw)
 
 
 def test_ground_split_refuses_far_pairs():

@@ -1,4 +1,4 @@
-"""The compensated pair sum (RP_FLAG_COMPENSATED) against the plain FP32 chain.
+"""The compensated pair sum (the default) against the plain FP32 chain (RP_FLAG_PLAIN_SUM).
 
 A target's spectral sum runs over every (source, lag) entry of its pairs
 before one inverse FFT per field (Eq. 12 per spectral coefficient).  Eight
@@ -38,7 +38,7 @@ def test_compensated_sum_within_the_fp32_bar():
     T = 60
     hists = histories(srcs, 0, T, dt)
     steps = [T - 2, T - 1]
-    res = {comp: run_library(doms, c, dt, hists, 0, steps, flags=rp.RP_FLAG_COMPENSATED if comp else 0)
+    res = {comp: run_library(doms, c, dt, hists, 0, steps, flags=0 if comp else rp.RP_FLAG_PLAIN_SUM)
            for comp in (False, True)}
     rng = np.random.default_rng(7)
     worst = {False: 0.0, True: 0.0}
@@ -65,7 +65,7 @@ def test_compensated_parity_small_and_runtime_shapes(geometry):
         doms = [synth.Domain((0.0, 0.0, 0.0), (7, 5, 6), 0.3), synth.Domain((3.1, -0.7, 0.4), (4, 9, 3), 0.3)]
         srcs, c, dt = synth.seeded_sources(doms), synth.C_AU, 0.05
     hists = histories(srcs, 0, 12, dt)
-    res = run_library(doms, c, dt, hists, 0, [11], flags=rp.RP_FLAG_COMPENSATED)
+    res = run_library(doms, c, dt, hists, 0, [11])
     for t, d in enumerate(doms):
         want = oracle_values(doms, hists, 0, c, dt, t, 11, np.arange(d.N))
         assert max(rel_l2(res[11][t], want)) <= 1e-6
