@@ -225,9 +225,9 @@ typedef enum {
     RP_K_INV_PLANE = 4,     /* inverse FFT along y and x, crop, scale, write phi/A */
     RP_K_DIRECT = 5,        /* direct retarded sum */
     RP_K_FAR_CONVERT = 6,   /* far path: slice to bf16 batch matrix */
-    RP_K_FAR_GEMM = 7,      /* far path: tcgen05 GEMM of factors and batch */
-    RP_K_FAR_SCATTER = 8,   /* far path: node values into coefficient rings */
-    RP_K_FAR_INTERP = 9,    /* far path: source anterpolation onto its nodes (two-sided factors) */
+    RP_K_FAR_GEMM = 7,      /* far path: tcgen05 GEMM of factors and batch (two-sided: the gathered GEMM) */
+    RP_K_FAR_SCATTER = 8,   /* far path: node values into coefficient rings (two-sided: the CTAs' sums) */
+    RP_K_FAR_ANTERP = 9,    /* far path (two-sided factors): a pushed slice anterpolated onto its source's nodes */
     RP_K_MOMENTS = 10,      /* learned path: moments of the pushed slices */
     RP_K_LEARNED = 11,      /* learned path: network rows, network, output into the coefficients */
     RP_K_COUNT = 12

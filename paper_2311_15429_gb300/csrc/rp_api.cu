@@ -205,6 +205,9 @@ void far_axis(double o, double h, int n, int p, std::vector<double> &nodes, std:
 // coefficient rings).  Every allocation goes to the far path's own list, so
 // that the structures can be rebuilt when pairs move to the learned path.
 rp_status build_far_impl(rp_ctx *ctx, int max_optin);
+rp_status attach_far_targets(rp_ctx *ctx);
+rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
+                     const std::vector<std::array<std::vector<double>, 3>> &tnodes);
 
 rp_status build_far(rp_ctx *ctx, int max_optin)
 {
@@ -226,6 +229,11 @@ void clear_far(rp_ctx *ctx)
     ctx->far_Z.clear(); ctx->far_rows.clear(); ctx->far_splits.clear(); ctx->far_work = nullptr;
     ctx->far_mapW.clear(); ctx->far_mapX.clear(); ctx->far_src_of_dom.clear();
     ctx->d_far_src = nullptr; ctx->d_far_tgt = nullptr; ctx->d_far_links = nullptr;
+    ctx->far2 = false;
+    ctx->far2_srcs.clear(); ctx->far2_of_dom.clear(); ctx->far2_tasks.clear(); ctx->far2_kb.clear();
+    ctx->d_far2_srcs = nullptr; ctx->d_far2_tasks = nullptr; ctx->d_far2_kb = nullptr;
+    ctx->far2_qall = ctx->far2_fac = nullptr; ctx->far2_work = nullptr;
+    ctx->far2_BN = ctx->far2_KS = ctx->far2_D = ctx->far2_max_nz = 0; ctx->far2_fac_rows = 0;
     ctx->far_src_alone.clear(); ctx->far_src_alone_of_dom.clear();
     ctx->d_far_src_alone = nullptr;
     ctx->far_max_r = ctx->npairs_far = 0;
@@ -265,7 +273,9 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
         F.px = (int)tnodes[t][0].size(); F.py = (int)tnodes[t][1].size(); F.pz = (int)tnodes[t][2].size();
         F.r = F.px * F.py * F.pz;
         F.lag_hi_max = hi;
-        F.depth = hi + batch + 1;
+        // one-sided factors scatter into steps up to hi + batch ahead; the
+        // two-sided gather writes the next batch of steps at once
+        F.depth = ctx->cfg.far_source_points > 0 ? 2 * batch + 2 : hi + batch + 1;
         float *Lx, *Ly, *Lz;
         if ((st = upload(ctx, &Lx, L[0])) || (st = upload(ctx, &Ly, L[1])) || (st = upload(ctx, &Lz, L[2]))) return st;
         F.Lx = Lx; F.Ly = Ly; F.Lz = Lz;
@@ -283,6 +293,11 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
         q != cudaDriverEntryPointSuccess || !enc) {
         cudaGetLastError();
         return fail(ctx, RP_ERR_UNSUPPORTED, "far path needs cuTensorMapEncodeTiled");
+    }
+    if (ctx->cfg.far_source_points > 0) {
+        if ((st = build_far2(ctx, enc, tidx, tnodes))) return st;
+        if ((st = upload(ctx, &ctx->d_far_tgt, ctx->far_tgt))) return st;
+        return attach_far_targets(ctx);
     }
     // sources
     size_t work_floats = 0;
@@ -360,6 +375,7 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
     if ((st = upload(ctx, &ctx->d_far_src, ctx->far_src))) return st;
     if ((st = upload(ctx, &ctx->d_far_tgt, ctx->far_tgt))) return st;
     if ((st = upload(ctx, &ctx->d_far_links, ctx->far_links))) return st;
+    if ((st = attach_far_targets(ctx))) return st;
     // staging rides on the source's first forward ring, interpolation on the
     // target's inverse plane pass
     ctx->far_src_alone_of_dom.assign(nd, -1);
@@ -376,9 +392,15 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
             ctx->far_src_alone.push_back(F);
         }
     }
-    // every far target is also an FFT target (its self term), and its inverse
-    // plane pass, which writes the output, adds the far coefficients: a far
-    // target without one would have no pass that writes its output first
+    if (!ctx->far_src_alone.empty() && (st = upload(ctx, &ctx->d_far_src_alone, ctx->far_src_alone))) return st;
+    return RP_OK;
+}
+
+// Every far target is also an FFT target (its self term), and its inverse
+// plane pass, which writes the output, adds the far coefficients: a far
+// target without one would have no pass that writes its output first.
+rp_status attach_far_targets(rp_ctx *ctx)
+{
     for (size_t k = 0; k < ctx->far_tgt.size(); ++k) {
         const FarTarget &F = ctx->far_tgt[k];
         bool done = false;
@@ -391,7 +413,142 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
             return fail(ctx, RP_ERR_UNSUPPORTED, "far target " + std::to_string(F.dom) +
                                                      " has no FFT self term to carry its far coefficients");
     }
-    if (!ctx->far_src_alone.empty() && (st = upload(ctx, &ctx->d_far_src_alone, ctx->far_src_alone))) return st;
+    return RP_OK;
+}
+
+// Two-sided factors (rp_far2.cu): the far sources' anterpolation weights,
+// node tables and coefficient rings; every far target's factor blocks, one
+// per (far source, lag), built in FP64 on the GPU; the gathered GEMM's CTAs
+// (a target's blocks in chunks of at most kFar2Chunk) and its tensor maps.
+constexpr int kFar2Chunk = 24;
+
+rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
+                     const std::vector<std::array<std::vector<double>, 3>> &tnodes)
+{
+    const int nd = (int)ctx->doms.size();
+    const int batch = ctx->cfg.far_batch, Q = ctx->cfg.far_source_points;
+    rp_status st;
+    ctx->far2 = true;
+    ctx->far2_of_dom.assign(nd, -1);
+    // sources and their node tables
+    std::vector<double> snodes;
+    std::vector<int> snode0;
+    int KS = 0, D = std::max(32, batch + 1);
+    for (int s = 0; s < nd; ++s) {
+        bool far = false;
+        for (int t = 0; t < nd; ++t) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_LOWRANK) continue;
+            far = true;
+            D = std::max(D, p.lag_hi + 1);
+        }
+        if (!far) continue;
+        const DomainDesc &S = ctx->doms[s];
+        FarSrc2 F{};
+        F.dom = s;
+        F.nx = S.n[0]; F.ny = S.n[1]; F.nz = S.n[2];
+        std::vector<double> nodes[3];
+        std::vector<float> L[3];
+        for (int a = 0; a < 3; ++a) far_axis(S.o[a], S.h, S.n[a], Q, nodes[a], L[a]);
+        F.qx = (int)nodes[0].size(); F.qy = (int)nodes[1].size(); F.qz = (int)nodes[2].size();
+        F.r = F.qx * F.qy * F.qz;
+        float *Lx, *Ly, *Lz;
+        if ((st = upload(ctx, &Lx, L[0])) || (st = upload(ctx, &Ly, L[1])) || (st = upload(ctx, &Lz, L[2]))) return st;
+        F.Lx = Lx; F.Ly = Ly; F.Lz = Lz;
+        if ((st = dev_alloc(ctx, &F.part, (size_t)S.n[2] * 4 * F.qx * F.qy))) return st;
+        if ((st = dev_alloc(ctx, &F.count, 1))) return st;
+        RP_CUDA(ctx, cudaMemset(F.count, 0, sizeof(unsigned int)));
+        snode0.push_back((int)(snodes.size() / 3));
+        for (int c = 0; c < F.qz; ++c)
+            for (int b = 0; b < F.qy; ++b)
+                for (int a = 0; a < F.qx; ++a) {
+                    snodes.push_back(nodes[0][a]);
+                    snodes.push_back(nodes[1][b]);
+                    snodes.push_back(nodes[2][c]);
+                }
+        KS = std::max(KS, (F.r + 63) / 64 * 64);
+        ctx->far2_max_nz = std::max(ctx->far2_max_nz, S.n[2]);
+        ctx->far2_of_dom[s] = (int)ctx->far2_srcs.size();
+        ctx->far2_srcs.push_back(F);
+    }
+    const int nsrc = (int)ctx->far2_srcs.size();
+    ctx->far2_KS = KS;
+    ctx->far2_D = D;
+    // coefficient rings: [source][2 D][4][2 KS], zero before the first push
+    const size_t qrows = (size_t)nsrc * 2 * D * 4;
+    if ((st = dev_alloc(ctx, &ctx->far2_qall, qrows * 2 * KS))) return st;
+    RP_CUDA(ctx, cudaMemset(ctx->far2_qall, 0, qrows * 2 * KS * sizeof(__nv_bfloat16)));
+    for (int i = 0; i < nsrc; ++i) {
+        ctx->far2_srcs[i].qrow0 = i * 2 * D * 4;
+        ctx->far2_srcs[i].qring = ctx->far2_qall + (size_t)ctx->far2_srcs[i].qrow0 * 2 * KS;
+    }
+    // targets: node tables, factor blocks, CTAs
+    int BN = 0;
+    for (const FarTarget &F : ctx->far_tgt) BN = std::max(BN, F.r);
+    BN = far_gather_bn(BN);
+    if (!BN) return fail(ctx, RP_ERR_UNSUPPORTED, "two-sided far factors take at most 256 target nodes");
+    ctx->far2_BN = BN;
+    std::vector<double> tn;
+    std::vector<FarBuild> builds;
+    long long fac_row = 0;
+    for (int t = 0; t < nd; ++t) {
+        if (tidx[t] < 0) continue;
+        FarTarget &F = ctx->far_tgt[tidx[t]];
+        const int t0 = (int)(tn.size() / 3);
+        for (int c = 0; c < F.pz; ++c)
+            for (int b = 0; b < F.py; ++b)
+                for (int a = 0; a < F.px; ++a) {
+                    tn.push_back(tnodes[t][0][a]);
+                    tn.push_back(tnodes[t][1][b]);
+                    tn.push_back(tnodes[t][2][c]);
+                }
+        const int kb0 = (int)ctx->far2_kb.size();
+        for (int s = 0; s < nd; ++s) {
+            const PairPlan &p = ctx->pairs[(size_t)t * nd + s];
+            if (p.kind != RP_PAIR_LOWRANK) continue;
+            const int si = ctx->far2_of_dom[s];
+            const double h = ctx->doms[s].h;
+            ctx->npairs_far += 1;
+            for (int m = p.lag_lo; m <= p.lag_hi; ++m) {
+                if (fac_row > (1LL << 31) - BN) return fail(ctx, RP_ERR_UNSUPPORTED, "far factor rows above 2^31");
+                ctx->far2_kb.push_back({si, m, (int)fac_row, 0});
+                builds.push_back({t0, F.r, snode0[si], ctx->far2_srcs[si].r, m, (int)fac_row, h * h * h});
+                fac_row += BN;
+            }
+        }
+        const int kb1 = (int)ctx->far2_kb.size();
+        F.task0 = (int)ctx->far2_tasks.size();
+        const int nchunk = (kb1 - kb0 + kFar2Chunk - 1) / kFar2Chunk;
+        for (int c = 0; c < nchunk; ++c) {
+            // equal shares of the target's blocks
+            const int a = kb0 + (int)((long long)(kb1 - kb0) * c / nchunk);
+            const int b = kb0 + (int)((long long)(kb1 - kb0) * (c + 1) / nchunk);
+            ctx->far2_tasks.push_back({tidx[t], a, b, 0});
+        }
+        F.task1 = (int)ctx->far2_tasks.size();
+        ctx->far_max_r = std::max(ctx->far_max_r, F.r);
+    }
+    ctx->far2_fac_rows = fac_row;
+    if ((st = dev_alloc(ctx, &ctx->far2_fac, (size_t)std::max<long long>(fac_row, BN) * 2 * KS))) return st;
+    if ((st = dev_alloc(ctx, &ctx->far2_work, (size_t)std::max<size_t>(ctx->far2_tasks.size(), 1) * 128 * BN)))
+        return st;
+    {
+        FarBuild *d_b = nullptr;
+        double *d_tn = nullptr, *d_sn = nullptr;
+        if ((st = upload(ctx, &d_b, builds)) || (st = upload(ctx, &d_tn, tn)) || (st = upload(ctx, &d_sn, snodes)))
+            return st;
+        RP_CUDA(ctx, launch_far_build_fac(d_b, (int)builds.size(), d_tn, d_sn, BN, KS,
+                                          1.0 / (ctx->cfg.c * ctx->cfg.dt), ctx->far2_fac, ctx->stream));
+    }
+    if (!encode_bf16_rows(enc, &ctx->far2_mapQ, ctx->far2_qall, (uint64_t)qrows, (uint64_t)2 * KS, 128) ||
+        !encode_bf16_rows(enc, &ctx->far2_mapF, ctx->far2_fac, (uint64_t)std::max<long long>(fac_row, BN),
+                          (uint64_t)2 * KS, (uint32_t)BN))
+        return fail(ctx, RP_ERR_UNSUPPORTED, "two-sided far factors: a tensor map did not encode");
+    if ((st = upload(ctx, &ctx->d_far2_srcs, ctx->far2_srcs)) || (st = upload(ctx, &ctx->d_far2_tasks, ctx->far2_tasks)) ||
+        (st = upload(ctx, &ctx->d_far2_kb, ctx->far2_kb)))
+        return st;
+    ctx->far_bytes += (long long)qrows * 2 * KS * 2 + fac_row * 2 * KS * 2 +
+                      (long long)ctx->far2_tasks.size() * 128 * BN * 4;
     return RP_OK;
 }
 
@@ -623,7 +780,7 @@ const char *rp_kernel_name(int kind)
 {
     static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column", "mac_inv_column",
                                             "inv_plane", "direct", "far_convert", "far_gemm",
-                                            "far_scatter", "far_interp", "moments", "learned"};
+                                            "far_scatter", "far_anterp", "moments", "learned"};
     return (kind >= 0 && kind < RP_K_COUNT) ? names[kind] : nullptr;
 }
 
@@ -637,6 +794,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
         if (!(cfg->far_distance > 0.0)) return RP_ERR_ARG;
         if (cfg->far_points != 0 && (cfg->far_points < 2 || cfg->far_points > kMaxFarPts)) return RP_ERR_ARG;
         if (cfg->far_batch != 0 && (cfg->far_batch < 8 || cfg->far_batch > 64 || cfg->far_batch % 8)) return RP_ERR_ARG;
+        if (cfg->far_source_points != 0 && cfg->far_batch > 32) return RP_ERR_ARG;   // one 128-row window
     }
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
     if (!(cfg->flags & RP_FLAG_PLAIN_SUM) && cfg->mac_warps != 0 && cfg->mac_warps != kCompWarps) return RP_ERR_ARG;
@@ -726,8 +884,12 @@ rp_status rp_finalize(rp_ctx *ctx)
                     for (int a = 0; a < 3; ++a) p.m[a] = m[a];
                 }
             }
-            if (ctx->cfg.mode == RP_MODE_LOWRANK && t != s && p.rmin >= ctx->cfg.far_distance &&
-                p.lag_lo >= ctx->cfg.far_batch - 1)
+            // a batch of pushes completes before its first target step is
+            // evaluated (one-sided factors, applied at the batch's last push
+            // to the steps it reaches), or before the batch of target steps
+            // it gives is gathered (two-sided factors)
+            const int min_lo = ctx->cfg.far_source_points > 0 ? ctx->cfg.far_batch : ctx->cfg.far_batch - 1;
+            if (ctx->cfg.mode == RP_MODE_LOWRANK && t != s && p.rmin >= ctx->cfg.far_distance && p.lag_lo >= min_lo)
                 p.kind = RP_PAIR_LOWRANK;
             if (t == s && fft_mode && p.kind != RP_PAIR_FFT)
                 return fail(ctx, RP_ERR_UNSUPPORTED, "domain " + std::to_string(t) +
@@ -1252,6 +1414,38 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     if (merged) {
         RP_CUDA(ctx, cudaEventRecord(ctx->sp_wfft, ctx->stream));
         for (SpillWindow &W : ctx->spill_wins) W.have = step - W.lo;
+    }
+    // two-sided far factors: the pushed slices of far sources onto their
+    // nodes; when a round completes the last step of a batch, the gathered
+    // GEMM gives every far target its node values of the next batch of steps
+    if (ctx->far2) {
+        int a0 = -1, a1 = -1;
+        for (int d = d0; d < d1; ++d) {
+            const int ai = ctx->far2_of_dom[d];
+            if (ai < 0) continue;
+            if (a0 < 0) a0 = ai;
+            a1 = ai + 1;
+        }
+        if (a0 >= 0 && (st = timed_launch(ctx, RP_K_FAR_ANTERP, "far anterpolation", [&] {
+                            return launch_far_anterp(ctx->d_far2_srcs + a0, a1 - a0, ctx->far2_max_nz, in, step,
+                                                     ctx->far2_D, ctx->far2_KS, ctx->stream);
+                        })))
+            return st;
+        const int batch = ctx->cfg.far_batch;
+        if (ctx->npushed == nd && step % batch == batch - 1) {
+            if ((st = timed_launch(ctx, RP_K_FAR_GEMM, "far gathered GEMM", [&] {
+                     return launch_far_gather(ctx->far2_mapQ, ctx->far2_mapF, ctx->d_far2_tasks,
+                                              (int)ctx->far2_tasks.size(), ctx->d_far2_kb, ctx->far2_BN, ctx->far2_KS,
+                                              ctx->far2_D, step + 1, ctx->far2_work, ctx->smem_optin, ctx->d_err,
+                                              ctx->stream);
+                 })))
+                return st;
+            if ((st = timed_launch(ctx, RP_K_FAR_SCATTER, "far gathered sums", [&] {
+                     return launch_far_reduce(ctx->d_far_tgt, (int)ctx->far_tgt.size(), ctx->far2_work, ctx->far2_BN,
+                                              step + 1, batch, ctx->far_max_r, ctx->stream);
+                 })))
+                return st;
+        }
     }
     // far path: stage the slices of far sources; every far_batch steps run
     // the factor GEMM of each source and add its node values to the rings
@@ -1992,7 +2186,7 @@ rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *
     if (!d_rho || !d_J || !d_phi || !d_A) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL pointer array");
     for (int d = 0; d < nd; ++d)
         if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
-    if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || !ctx->lpairs.empty() ||
+    if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || ctx->far2 || !ctx->lpairs.empty() ||
         (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_srcs.empty())
         return fail(ctx, RP_ERR_UNSUPPORTED,
                     "rp_graph_capture: FFT and direct pairs only, without profiling, split or history spill");
@@ -2211,6 +2405,10 @@ rp_status for_each_ring(rp_ctx *ctx, Fn &&fn)
         if ((st = fn((void *)F.X, (size_t)8 * ctx->cfg.far_batch * F.ks * sizeof(__nv_bfloat16)))) return st;
     for (const FarTarget &F : ctx->far_tgt)
         if ((st = fn((void *)F.cring, (size_t)F.depth * F.r * 4 * sizeof(float)))) return st;
+    if (ctx->far2_qall &&
+        (st = fn((void *)ctx->far2_qall,
+                 (size_t)ctx->far2_srcs.size() * 2 * ctx->far2_D * 4 * 2 * ctx->far2_KS * sizeof(__nv_bfloat16))))
+        return st;
     for (size_t d = 0; d < ctx->ground.size(); ++d) {
         const size_t bytes = 4 * (size_t)ctx->doms[d].N * sizeof(float);
         if ((st = fn((void *)ctx->ground[d], bytes)) || (st = fn((void *)ctx->pstatic[d], bytes))) return st;

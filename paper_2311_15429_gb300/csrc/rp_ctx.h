@@ -175,6 +175,23 @@ struct rp_ctx {
     std::vector<int> far_src_of_dom;                            // far source index of a domain, -1
     FarSource *d_far_src = nullptr;
     FarTarget *d_far_tgt = nullptr;
+    // two-sided far factors (far_source_points > 0; rp_far2.cu): the far
+    // sources with their anterpolation weights and coefficient rings (one
+    // array, far2_qall: [source][2 D][4][2 KS] bf16), the factor blocks of
+    // every target, the gathered GEMM's CTAs and its partial sums
+    bool far2 = false;
+    std::vector<FarSrc2> far2_srcs;
+    std::vector<int> far2_of_dom;                               // FarSrc2 index of a domain, -1
+    std::vector<FarTask> far2_tasks;
+    std::vector<FarKBlock> far2_kb;
+    FarSrc2 *d_far2_srcs = nullptr;
+    FarTask *d_far2_tasks = nullptr;
+    FarKBlock *d_far2_kb = nullptr;
+    __nv_bfloat16 *far2_qall = nullptr, *far2_fac = nullptr;
+    float *far2_work = nullptr;
+    CUtensorMap far2_mapQ{}, far2_mapF{};
+    int far2_BN = 0, far2_KS = 0, far2_D = 0, far2_max_nz = 0;
+    long long far2_fac_rows = 0;
     // far sources with no forward ring of their own: staged by a separate kernel
     std::vector<FarSource> far_src_alone;
     std::vector<int> far_src_alone_of_dom;

@@ -24,7 +24,7 @@ RP_FLAG_AUDIT = 0x40
 RP_FLAG_PLAIN_SUM = 0x80
 RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
- RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_INTERP, RP_K_MOMENTS, RP_K_LEARNED,
+ RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_ANTERP, RP_K_MOMENTS, RP_K_LEARNED,
  RP_K_COUNT) = range(13)
 MAX_DOMAINS = 256
 

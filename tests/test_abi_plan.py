@@ -328,3 +328,35 @@ def test_device_budget_refuses_a_plan_beyond_it():
                 assert "budget" in rp.rp_last_error(ctx)
         finally:
             rp.rp_destroy(ctx)
+
+
+def test_cfg4_plan_two_sided_every_cross_pair_far():
+    """cfg4 (64 sub-domains of 24^3-96^3 at 0.2-0.35 bohr): with two-sided
+    factors and a 250 bohr far distance every one of the 4032 cross pairs is
+    low-rank (each with lag_lo >= the 32-step batch the gathered GEMM needs)
+    and every self pair is an FFT pair."""
+    w = synth.workload("cfg4")
+    ctx = rp.rp_create(w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=rp.RP_FLAG_PLAN_ONLY, far_distance=250.0,
+                       far_batch=32, far_source_points=4)
+    try:
+        for d in w.domains:
+            rp.rp_add_domain(ctx, d.origin, d.n, d.h)
+        rp.rp_finalize(ctx)
+        q = rp.rp_query(ctx)
+        assert q["ndomains"] == 64 and q["npairs_far"] == 4032 and q["npairs_fft"] == 64 and q["npairs_direct"] == 0
+        for t in range(64):
+            for s in range(64):
+                p = rp.rp_pair_info(ctx, t, s)
+                if t == s:
+                    assert p["kind"] == rp.RP_PAIR_FFT
+                else:
+                    assert p["kind"] == rp.RP_PAIR_LOWRANK and p["lag_lo"] >= 32, (t, s, p)
+    finally:
+        rp.rp_destroy(ctx)
+
+
+def test_two_sided_factors_need_a_batch_of_at_most_32():
+    with pytest.raises(rp.RPError) as e:
+        rp.rp_create(137.0, 0.05, mode=rp.RP_MODE_LOWRANK, flags=rp.RP_FLAG_PLAN_ONLY, far_distance=100.0,
+                     far_batch=40, far_source_points=4)
+    assert e.value.status == rp.RP_ERR_ARG

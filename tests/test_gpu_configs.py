@@ -32,8 +32,10 @@ def workload(name):
     return synth.workload(name)
 
 
-def far_only_errors(name, targets, nodes_per, train=False, far_points=0, **train_kw):
-    """Per-target [4] rel-L2 of the far field of domain 0 alone, the training
+def far_only_errors(name, targets, nodes_per, train=False, far_points=0, source_points=0, far_distance=500.0,
+                    extra_steps=(), **train_kw):
+    """Per-target [4] rel-L2 of the far field of domain 0 alone (worst over
+    the last step and the steps `extra_steps` before it), the training
     report (or None) and the context's query after the run."""
     import torch
     w = workload(name)
@@ -42,32 +44,39 @@ def far_only_errors(name, targets, nodes_per, train=False, far_points=0, **train
     flags = rp.RP_FLAG_DEFER_FAR if train else 0
     zr = [torch.zeros(d.N, device=dev) for d in w.domains]
     zJ = [torch.zeros(3 * d.N, device=dev) for d in w.domains]
-    with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=flags, far_distance=500.0,
-                               far_batch=32, far_points=far_points) as lib:
+    got = {}
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=flags,
+                               far_distance=far_distance, far_batch=32, far_points=far_points,
+                               far_source_points=source_points) as lib:
         rep = lib.train_far_model(2000.0, **train_kw) if train else None
         info = {t: lib.pair_info(t, 0) for t in targets}
-        L = lib.query()["max_lag"] + 8
+        L = lib.query()["max_lag"] + 8 + max(extra_steps, default=0)
+        check = {L - 1 - e for e in extra_steps} | {L - 1}
         for j in range(L):
             r, J = gen.step(j, w.dt)
             lib.push_all([r[0]] + zr[1:], [J[0]] + zJ[1:])
-        phi, A = lib.evaluate()
+            if j in check:
+                phi, A = lib.evaluate()
+                got[j] = {t: np.concatenate([phi[t].cpu().numpy()[None], A[t].cpu().numpy().reshape(3, -1)])
+                          for t in targets}
         lib.sync()
-        got = {t: np.concatenate([phi[t].cpu().numpy()[None], A[t].cpu().numpy().reshape(3, -1)]) for t in targets}
         q = lib.query()
-    step = L - 1
     rng = np.random.default_rng(3)
     errs = {}
     for t in targets:
         p = info[t]
-        lo, hi = step - p["lag_hi"] - 1, step - p["lag_lo"]
-        src = w.sources[0].history(lo, hi + 1, w.dt)
-        tgt = np.zeros((16, 4, w.domains[t].N), dtype=np.float32)      # the target's own (zero) samples
         nodes = rng.integers(0, w.domains[t].N, nodes_per)
-        doms = [w.domains[t], w.domains[0]]
-        vals, _ = oracle.eval_points_windows_parallel([d.origin for d in doms], [d.n for d in doms],
-                                                      [d.h for d in doms], [tgt, src], [step - 15, lo],
-                                                      w.c, w.dt, 0, step, nodes)
-        errs[t] = rel_l2(got[t][:, nodes], vals)
+        worst = [0.0] * 4
+        for step in sorted(check):
+            lo, hi = step - p["lag_hi"] - 1, step - p["lag_lo"]
+            src = w.sources[0].history(lo, hi + 1, w.dt)
+            tgt = np.zeros((16, 4, w.domains[t].N), dtype=np.float32)      # the target's own (zero) samples
+            doms = [w.domains[t], w.domains[0]]
+            vals, _ = oracle.eval_points_windows_parallel([d.origin for d in doms], [d.n for d in doms],
+                                                          [d.h for d in doms], [tgt, src], [step - 15, lo],
+                                                          w.c, w.dt, 0, step, nodes)
+            worst = [max(a, b) for a, b in zip(worst, rel_l2(got[step][t][:, nodes], vals))]
+        errs[t] = worst
     return errs, rep, q
 
 
@@ -97,3 +106,37 @@ def test_cfg4_subset_mixed_sizes_and_spacings():
     for t, e in errs.items():
         assert max(e) <= TOL, ("cfg4x8", t, e)
 
+
+
+def test_cfg3_two_sided_far_field():
+    """cfg3 with both sides of the factors interpolated (4^3 source nodes):
+    the factors no longer grow with the 64^3 source grids."""
+    errs, _, q = far_only_errors("cfg3", [1, 4, 7], 96, source_points=4, extra_steps=(13, 40))
+    assert q["npairs_far"] == 56 and q["npairs_fft"] == 8
+    assert q["far_bytes"] < 2 ** 30, q["far_bytes"]
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg3 two-sided", t, e)
+
+
+def test_cfg5_two_sided_low_rank_under_a_gigabyte():
+    """cfg5 (32 x 48^3, 992 far pairs) on the two-sided low-rank path alone
+    (no network): far-path memory under 1 GB, far field within the bar."""
+    errs, _, q = far_only_errors("cfg5", [1, 9, 17, 31], 64, source_points=4, extra_steps=(13,))
+    assert q["npairs_far"] == 992
+    assert q["far_bytes"] < 2 ** 30, q["far_bytes"]
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg5 two-sided", t, e)
+
+
+def test_cfg4_all_64_domains_two_sided():
+    """cfg4 in full: 64 sub-domains of 24^3 to 96^3 nodes at 0.2-0.35 bohr,
+    every one of the 4032 cross pairs on the two-sided low-rank path (each
+    more than 250 bohr apart), far field of domain 0 seen from targets of
+    every size, at three steps."""
+    w = workload("cfg4")
+    sizes = sorted({d.n[0] for d in w.domains})
+    targets = [next(t for t in range(1, 64) if w.domains[t].n[0] == n) for n in sizes]
+    errs, _, q = far_only_errors("cfg4", targets, 64, source_points=4, far_distance=250.0, extra_steps=(13, 31))
+    assert q["ndomains"] == 64 and q["npairs_far"] == 4032 and q["npairs_fft"] == 64, q
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg4", t, w.domains[t].n, e)

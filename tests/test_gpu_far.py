@@ -22,12 +22,12 @@ def _setup():
     return doms, synth.seeded_sources(doms)
 
 
-def _run(doms, hists, eval_at, batch=16):
+def _run(doms, hists, eval_at, batch=16, source_points=0):
     import torch
     dev = torch.device("cuda", 0)
     out = {}
     with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_LOWRANK, far_distance=100.0,
-                               far_batch=batch) as lib:
+                               far_batch=batch, far_source_points=source_points) as lib:
         kinds = {(t, s): lib.pair_info(t, s)["kind"] for t in range(3) for s in range(3)}
         for i in range(hists[0].shape[0]):
             lib.push_all([torch.from_numpy(h[i, 0].copy()).to(dev) for h in hists],
@@ -60,13 +60,15 @@ def test_far_pairs_planned_lowrank():
         rp.rp_destroy(ctx)
 
 
-@pytest.mark.parametrize("batch", [16, 32])
-def test_far_path_total_and_far_field(batch):
+@pytest.mark.parametrize("batch,source_points", [(16, 0), (32, 0), (16, 4), (32, 4), (24, 3)])
+def test_far_path_total_and_far_field(batch, source_points):
+    """source_points = 0: the source side of the factors exact; > 0: both
+    sides interpolated (two-sided factors, the gathered GEMM)."""
     doms, srcs = _setup()
     T = 104
     hists = [s.history(0, T, 0.05) for s in srcs]
     steps = [T - 4, T - 1]
-    out, kinds, q = _run(doms, hists, steps, batch)
+    out, kinds, q = _run(doms, hists, steps, batch, source_points)
     assert q["npairs_far"] == 4
     for step in steps:
         for t, d in enumerate(doms):
@@ -75,7 +77,7 @@ def test_far_path_total_and_far_field(batch):
             assert max(errs) <= TOL, ("total", step, t, errs)
     # far field alone: only domain 2 active, seen from domains 0 and 1
     far_only = [np.zeros_like(hists[0]), np.zeros_like(hists[1]), hists[2]]
-    out, _, _ = _run(doms, far_only, steps, batch)
+    out, _, _ = _run(doms, far_only, steps, batch, source_points)
     for step in steps:
         for t in (0, 1):
             want = oracle_values(doms, far_only, 0, synth.C_AU, 0.05, t, step, np.arange(doms[t].N))
