@@ -69,10 +69,13 @@ def parse():
     p.add_argument("--learned-distance", type=float, default=2000.0)
     p.add_argument("--far-distance", type=float, default=1000.0)
     p.add_argument("--far-batch", type=int, default=32)
+    p.add_argument("--source-points", type=int, default=4,
+                   help="deep workloads: source nodes per axis of the two-sided far factors (0: source side exact)")
+    p.add_argument("--no-deep", action="store_true", help="skip the deep workloads' lines in the default run")
     return p.parse_args()
 
 
-DEEP = ("cfg3", "cfg4x8", "cfg5", "cfg5x8")
+DEEP = ("cfg3", "cfg4", "cfg4x8", "cfg5", "cfg5x8")
 
 # The direct sum's arithmetic per (target node, source node) pair: the offset
 # (3 subtractions) and R^2 (one multiply, two FMAs: 5 flops), rsqrt, tau (two
@@ -658,6 +661,21 @@ def run_ours(args, rank, world, local):
                       "streams, overlapped with the kernels of neighbouring steps)"}
     lib.close()
 
+    # ---- the deep workloads (every cross pair far, thousands-deep histories):
+    # each chosen form timed on K steps beside its plain FP32 path (extrapolated)
+    deep = None
+    if rank == 0 and not args.no_deep and args.mode == "fft":
+        deep = {}
+        for key, name, mode, plain_leg in (("cfg3", "cfg3", "lowrank", True), ("cfg4", "cfg4", "lowrank", True),
+                                           ("cfg5", "cfg5", "lowrank", True),
+                                           ("cfg5_learned", "cfg5", "learned", False)):
+            try:
+                deep[key] = deep_leg(args, name, min(K, 64), max(W, 3), local, stream, mode=mode,
+                                     source_points=args.source_points, check=not args.no_cpu, plain=plain_leg)
+            except Exception as e:   # one workload's failure must not lose the line
+                deep[key] = {"error": f"{type(e).__name__}: {e}"}
+            torch.cuda.empty_cache()
+
     if rank != 0:
         return
     q_points = w.points
@@ -693,6 +711,7 @@ def run_ours(args, rank, world, local):
         "e2e": e2e,
         "gpu_launches": launches,
         "clocks": clk,
+        "deep_configs": deep,
     }
     print(json.dumps(line), flush=True)
 
@@ -752,69 +771,175 @@ def lib_bytes_str(w, info, depth):
     return f"{alg['mac_inv_column'] / 2**20:.0f} MiB"
 
 
-def run_deep(args, rank, world, local):
-    """cfg3 / cfg5: every cross pair is far.  Inputs are made on the device
-    (histories thousands of steps deep); the accuracy check samples target
-    nodes against the FP64 oracle with a stored window per source."""
+# Far distance of the low-rank pairs per deep workload: every cross pair of
+# cfg4 is more than 250 bohr apart (cfg3 and cfg5: 500).
+DEEP_FAR_DISTANCE = {"cfg3": 500.0, "cfg4": 250.0, "cfg4x8": 500.0, "cfg5": 500.0, "cfg5x8": 500.0}
+
+
+def far_gather_work(lib, w, info, batch, source_points):
+    """Algorithmic work of one gathered-GEMM launch (two-sided factors): per
+    (target, far source, lag) block, 128 x BN x KS bf16 products three times
+    (hi*hi, hi*lo, lo*hi); bytes: the factor blocks (bf16 hi and lo), the
+    blocks' coefficient windows (128 rows x 2 KS bf16) and the partial sums
+    written (128 x BN fp32 per CTA, an upper bound of 24 blocks per CTA)."""
+    nd = len(w.domains)
+    q = source_points
+    KS = (q ** 3 + 63) // 64 * 64
+    r = max(min(4, d.n[0]) * min(4, d.n[1]) * min(4, d.n[2]) for d in w.domains)
+    BN = next(b for b in (32, 64, 128, 256) if r <= b)
+    blocks = sum(info[(t, s)]["lag_hi"] - info[(t, s)]["lag_lo"] + 1 for t in range(nd) for s in range(nd)
+                 if info[(t, s)]["kind"] == 2)
+    flops = blocks * 3 * 2 * 128 * BN * KS
+    by = blocks * (BN * 2 * KS * 2 + 128 * 2 * KS * 2) + (blocks // 24 + nd) * 128 * BN * 4
+    return flops, by, blocks
+
+
+def calibrate_fft_costs(w, local, stream, steps=24):
+    """Measured costs of the plain FFT path per size class of w: two cubic
+    n^3 domains of the class's spacing 3 box widths apart, FFT mode, every
+    launch timed.  Returns {n: (forward passes us per source, inverse plane
+    us per target, MAC us per (source, lag) entry)}."""
+    import torch
+    from paper_2311_15429_gb300 import rp
+    dev = torch.device("cuda", local)
+    out = {}
+    for n in sorted({d.n[0] for d in w.domains}):
+        h = next(d.h for d in w.domains if d.n[0] == n)
+        cw = synth.two_domain(n, h, 3.0 * n * h, "cal")
+        gen = synth.DeviceSlices(cw.sources, dev)
+        with rp.RetardedPotentials(cw.domains, cw.c, cw.dt, flags=rp.RP_FLAG_GROUND_STATE_CLAMP, device=local,
+                                   stream=stream) as lib:
+            entries = sum(lib.pair_info(t, s)["lag_hi"] - lib.pair_info(t, s)["lag_lo"] + 1
+                          for t in range(2) for s in range(2))
+            sl = [gen.step(j, cw.dt) for j in range(4)]
+            for j in range(4):
+                lib.push_all(*sl[j])
+                lib.evaluate()
+            pphi, pA = rp.pointer_array(lib.phi), rp.pointer_array(lib.A)
+            ps = [(rp.pointer_array(r), rp.pointer_array(J)) for r, J in sl]
+            ks = kernel_pass(lib, steps, lambda i: ps[i % 4], pphi, pA)
+        per = lambda k: 1e3 * ks[k]["total_ms"] / steps if k in ks else 0.0
+        out[n] = ((per("fwd_plane") + per("fwd_column")) / 2, per("inv_plane") / 2, per("mac_inv_column") / entries)
+    return out
+
+
+def calibrate_direct_rate(local, stream, steps=3):
+    """Pair-points per second of the plain direct FP32 sum (two 24^3 domains
+    of unequal spacing in RP_MODE_DIRECT)."""
+    import torch
+    from paper_2311_15429_gb300 import rp
+    dev = torch.device("cuda", local)
+    doms = [synth.cubic((0.0, 0.0, 0.0), 24, 0.25), synth.cubic((30.0, 0.0, 0.0), 24, 0.3)]
+    gen = synth.DeviceSlices(synth.seeded_sources(doms), dev)
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, mode=rp.RP_MODE_DIRECT, flags=rp.RP_FLAG_GROUND_STATE_CLAMP,
+                               device=local, stream=stream) as lib:
+        lib.push_all(*gen.step(0, 0.05))
+        lib.evaluate()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for j in range(steps):
+            lib.push_all(*gen.step(j + 1, 0.05))
+            lib.evaluate()
+        b.record(stream)
+        torch.cuda.synchronize()
+    return (2 * doms[0].N) ** 2 * steps / (a.elapsed_time(b) * 1e-3)
+
+
+def plain_path_extrapolated(w, info, costs, direct_rate):
+    """The plain FP32 path of every pair (SURVEY's per-pair unbatched FFT path:
+    self and equal-spacing cross pairs by FFT, one entry per lag; pairs of
+    unequal spacing by the direct sum), whose histories do not fit the GPU
+    for these workloads: its step time from the per-class costs measured by
+    calibrate_fft_costs and the direct sum's measured rate, scaled by the
+    workload's (pair, lag) count and pair-points."""
+    nd = len(w.domains)
+    t_us = 0.0
+    entries, direct_pp = 0, 0
+    for t in range(nd):
+        fwd, inv, _ = costs[w.domains[t].n[0]]
+        t_us += fwd + inv
+        for s in range(nd):
+            p = info[(t, s)]
+            if t == s or abs(w.domains[t].h - w.domains[s].h) <= 1e-12 * w.domains[t].h:
+                n = max(w.domains[t].n[0], w.domains[s].n[0])
+                B = p["lag_hi"] - p["lag_lo"] + 1
+                t_us += B * costs[n][2]
+                entries += B
+            else:
+                direct_pp += w.domains[t].N * w.domains[s].N
+    t_us += 1e6 * direct_pp / direct_rate
+    return {"ms_per_step": t_us / 1e3, "value": w.points / (t_us * 1e-6), "unit": UNIT, "extrapolated": True,
+            "fft_entries_per_step": entries, "direct_pair_points_per_step": direct_pp,
+            "method": "per-class forward/inverse pass and per-(source, lag) MAC costs measured on two n^3 domains in "
+                      "FFT mode, direct-sum pair-points/s measured in RP_MODE_DIRECT, scaled by this workload's "
+                      "entries and pair-points (its full-depth spectral histories do not fit the GPU)"}
+
+
+def deep_leg(args, name, K, W, local, stream, mode="lowrank", source_points=4, check=True, plain=True):
+    """One deep workload (every cross pair far) on the chosen form: the timed
+    steps (device-made inputs, no events between kernels), a kernel pass, the
+    total and far-only error at sampled nodes against the FP64 oracle with a
+    stored window per source, and the plain FP32 path extrapolated."""
     import torch
     import oracle
     from paper_2311_15429_gb300 import rp
     dev = torch.device("cuda", local)
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.current_stream(dev)
-    w = get_workload(args.workload)
-    mode = "lowrank" if args.mode == "fft" else args.mode
+    w = get_workload(name)
     flags = rp.RP_FLAG_DEFER_FAR if mode == "learned" else 0
+    fd = DEEP_FAR_DISTANCE.get(name, args.far_distance)
+    t0 = time.perf_counter()
     gen = synth.DeviceSlices(w.sources, dev)
     lib = rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, flags=flags, device=local,
-                                stream=stream, far_distance=args.far_distance, far_batch=args.far_batch)
+                                stream=stream, far_distance=fd, far_batch=args.far_batch,
+                                far_source_points=source_points)
     train = lib.train_far_model(args.learned_distance) if mode == "learned" else None
     q = lib.query()
     nd = len(w.domains)
     info = {(t, s): lib.pair_info(t, s) for t in range(nd) for s in range(nd)}
     pre = q["max_lag"] + 1
-    W, K = args.warmup, args.steps
     for j in range(pre + W):
         r, J = gen.step(j - pre, w.dt)
         lib.push_all(r, J)
         if j >= pre:
             lib.evaluate()
     lib.sync()
-    check = pre + W - 1 - pre               # time index of the last continuous step
+    setup_s = time.perf_counter() - t0
+    step_t = W - 1                       # time index of the last continuous step
     acc = None
-    if rank == 0 and not args.no_cpu:
-        tgts = [1, nd // 2]
-        errs = []
-        rng = np.random.default_rng(0)
+    if check:
+        tgts = sorted({1, nd // 2, nd - 1})
         got = {t: torch.cat([lib.phi[t][None], lib.A[t].reshape(3, -1)]).cpu().numpy() for t in tgts}
-        t0 = time.perf_counter()
+        rng = np.random.default_rng(0)
+        errs, far_errs = [], []
+        tc = time.perf_counter()
         for t in tgts:
             hists, firsts = [], []
             for s in range(nd):
                 p = info[(t, s)]
-                lo, hi = check - p["lag_hi"] - 1, check - p["lag_lo"]
+                lo, hi = step_t - p["lag_hi"] - 1, step_t - p["lag_lo"]
                 hists.append(w.sources[s].history(lo, hi + 1, w.dt))
                 firsts.append(lo)
             nodes = np.sort(rng.choice(w.domains[t].N, 48, replace=False))
-            vals, threads = oracle.eval_points_windows_parallel([d.origin for d in w.domains],
-                                                                [d.n for d in w.domains], [d.h for d in w.domains],
-                                                                hists, firsts, w.c, w.dt, t, check, nodes)
+            args_o = ([d.origin for d in w.domains], [d.n for d in w.domains], [d.h for d in w.domains])
+            vals, _ = oracle.eval_points_windows_parallel(*args_o, hists, firsts, w.c, w.dt, t, step_t, nodes)
+            own = [hh if s == t else np.zeros_like(hh) for s, hh in enumerate(hists)]
+            selfv, _ = oracle.eval_points_windows_parallel(*args_o, own, firsts, w.c, w.dt, t, step_t, nodes)
             g = got[t][:, nodes]
-            errs += [float(np.linalg.norm(g[f] - vals[:, f]) / np.linalg.norm(vals[:, f])) for f in range(4)]
-        acc = {"rel_l2_max": max(errs), "rel_l2_per_field_domain": errs,
-               "checked": f"48 seeded nodes of domains {tgts} at t={check * w.dt:.2f}, total field, vs FP64 oracle "
-                          f"({time.perf_counter() - t0:.1f} s)"}
+            for f in range(4):
+                errs.append(float(np.linalg.norm(g[f] - vals[:, f]) / np.linalg.norm(vals[:, f])))
+                far_errs.append(float(np.linalg.norm(g[f] - vals[:, f]) / np.linalg.norm(vals[:, f] - selfv[:, f])))
+        acc = {"rel_l2_max": max(errs), "far_field_rel_l2_max": max(far_errs),
+               "checked": f"48 seeded nodes of domains {tgts} at t={step_t * w.dt:.2f} against the FP64 oracle "
+                          f"({time.perf_counter() - tc:.1f} s); far field: the same error over the oracle's sum of "
+                          f"the other domains alone (all of the error charged to the far field)"}
     # timed region: cycled device inputs, no events between kernels
     ncycle = 16
-    cyc = [gen.step(pre + W + i, w.dt) for i in range(ncycle)]
+    cyc = [gen.step(W + i, w.dt) for i in range(ncycle)]
     pcyc = [(rp.pointer_array(r), rp.pointer_array(J)) for r, J in cyc]
     pphi, pA = rp.pointer_array(lib.phi), rp.pointer_array(lib.A)
     rp.rp_kernel_stats(lib.ctx, 0, reset=True)
-    clocks = ClockSampler(local)
-    barrier(world)
     torch.cuda.synchronize()
-    clocks.start()
-    time.sleep(0.15)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
     for i in range(K):
@@ -823,16 +948,11 @@ def run_deep(args, rank, world, local):
         rp.rp_evaluate(lib.ctx, pphi, pA)
     e1.record(stream)
     torch.cuda.synchronize()
-    clk = clocks.stop()
-    barrier(world)
-    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    ms = e0.elapsed_time(e1)
     launches = sum(rp.rp_kernel_count(lib.ctx, kind) for kind in range(rp.RP_K_COUNT))
-    # kernel times: a separate pass (a whole number of far batches), every launch timed
     Kp = max(args.far_batch, kernel_pass_steps(K) // args.far_batch * args.far_batch)
     kstats = kernel_pass(lib, Kp, lambda i: pcyc[(K + i) % ncycle], pphi, pA)
     alg = algorithmic_bytes(w, info)
-    if mode == "lowrank":
-        alg["far_gemm"] = far_gemm_bytes(w, info, 4, args.far_batch)
     peak, peak_kind = measured_peak()
     for k in kstats:
         if k in alg:
@@ -844,22 +964,72 @@ def run_deep(args, rank, world, local):
         roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s", "frac": ach / peak,
                 "peak_source": f"{peak_kind} hbm_gbs (copy bandwidth)", "traffic": committed_traffic(dom, w.name),
                 "algorithmic_bytes_per_launch": alg[dom],
-            "time_basis": "per step (all launches of the step)" if dom in PER_STEP_KINDS else "per launch"}
+                "time_basis": "per step (all launches of the step)" if dom in PER_STEP_KINDS else "per launch"}
+    far_roof = None
+    if source_points and "far_gemm" in kstats:
+        fl, by, blocks = far_gather_work(lib, w, info, args.far_batch, source_points)
+        us = kstats["far_gemm"]["avg_us"]
+        bf16 = bf16_peak()
+        far_roof = {"kernel": "k_far_gather (tcgen05, bf16 hi/lo, three products)", "blocks": blocks,
+                    "avg_us": us, "tflops": fl / (us * 1e-6) / 1e12, "tensor_peak": bf16[0],
+                    "tensor_frac": fl / (us * 1e-6) / 1e12 / bf16[0], "gbps": by / (us * 1e-6) / 1e9,
+                    "hbm_frac": by / (us * 1e-6) / 1e9 / peak, "flops_per_launch": fl, "bytes_per_launch": by,
+                    "peak_source": bf16[1]}
     q = lib.query()
     lib.close()
+    plain_line = None
+    if plain:
+        costs = calibrate_fft_costs(w, local, stream)
+        rate = calibrate_direct_rate(local, stream) if any(
+            abs(a.h - b.h) > 1e-12 * a.h for a in w.domains for b in w.domains) else 1.0
+        plain_line = plain_path_extrapolated(w, info, costs, rate)
+        plain_line["speedup_of_chosen"] = plain_line["ms_per_step"] / (ms / K)
+    return {"workload": name, "description": w.description, "points_per_step": w.points,
+            "value": w.points * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K, "warmup": W,
+            "path": f"FFT self terms; far pairs {mode}" + (f", two-sided factors ({source_points}^3 source nodes)"
+                                                          if source_points and mode == "lowrank" else ""),
+            "far_pairs": q["npairs_far"], "learned_pairs": q["npairs_learned"], "far_bytes": q["far_bytes"],
+            "device_bytes": q["device_bytes"], "training": train, "accuracy": acc, "roofline": roof,
+            "far_gemm_roofline": far_roof, "kernels": kstats, "gpu_launches": launches, "plain_path": plain_line,
+            "setup_s": setup_s}
+
+
+def bf16_peak():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        d = json.load(open(p))
+        return float(d["bf16_tflops"]), "measured bf16_tflops (cuBLAS burst)"
+    except Exception:
+        return 1900.0, "fallback"
+
+
+def run_deep(args, rank, world, local):
+    """cfg3 / cfg4 / cfg5 on their own line: every cross pair is far."""
+    import torch
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    mode = "lowrank" if args.mode == "fft" else args.mode
+    clocks = ClockSampler(local)
+    barrier(world)
+    clocks.start()
+    leg = deep_leg(args, args.workload, args.steps, args.warmup, local, stream, mode=mode,
+                   source_points=args.source_points, check=not args.no_cpu, plain=not args.no_plain)
+    clk = clocks.stop()
     if rank != 0:
         return
     line = {
-        "metric": METRIC, "value": world * w.points * K / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
-        "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32", "data": "synthetic",
-        "config": {"workload": w.name, "description": w.description, "points_per_step": w.points,
-                   "path": f"FFT self terms; far pairs {mode}", "far_pairs": q["npairs_far"],
-                   "learned_pairs": q["npairs_learned"], "far_bytes": q["far_bytes"],
-                   "l2": f"{ncycle} device-made input slices per domain cycled ({w.points * 16 * ncycle / 2**20:.0f} MiB)",
+        "metric": METRIC, "value": world * leg["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": leg["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": leg["workload"], "description": leg["description"],
+                   "points_per_step": leg["points_per_step"], "path": leg["path"], "far_pairs": leg["far_pairs"],
+                   "learned_pairs": leg["learned_pairs"], "far_bytes": leg["far_bytes"],
+                   "l2": "16 device-made input slices per domain cycled",
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
-        "training": train, "accuracy": acc, "roofline": roof, "kernels": kstats, "gpu_launches": launches,
-        "clocks": clk, "e2e": None, "cpu_baseline": None,
+        "training": leg["training"], "accuracy": leg["accuracy"], "roofline": leg["roofline"],
+        "far_gemm_roofline": leg["far_gemm_roofline"], "kernels": leg["kernels"], "gpu_launches": leg["gpu_launches"],
+        "plain_path": leg["plain_path"], "clocks": clk, "e2e": None, "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
 
