@@ -472,6 +472,10 @@ rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
         ctx->far2_srcs.push_back(F);
     }
     const int nsrc = (int)ctx->far2_srcs.size();
+    if (nsrc == 0) {   // every far pair is learned: only the targets' coefficient rings are needed
+        ctx->far2 = false;
+        return RP_OK;
+    }
     ctx->far2_KS = KS;
     ctx->far2_D = D;
     // coefficient rings: [source][2 D][4][2 KS], zero before the first push

@@ -140,3 +140,13 @@ def test_cfg4_all_64_domains_two_sided():
     assert q["ndomains"] == 64 and q["npairs_far"] == 4032 and q["npairs_fft"] == 64, q
     for t, e in errs.items():
         assert max(e) <= TOL, ("cfg4", t, w.domains[t].n, e)
+
+
+def test_cfg5_learned_with_two_sided_fallback():
+    """The learned far field on cfg5 with two-sided factors as its fallback:
+    pairs the gate refuses stay on the two-sided low-rank path, and when it
+    takes every pair none remain (the coefficient rings alone)."""
+    errs, rep, q = far_only_errors("cfg5", [1, 17], 64, train=True, source_points=4)
+    assert q["npairs_learned"] + q["npairs_far"] == 992 and q["npairs_learned"] == rep["learned"] > 0
+    for t, e in errs.items():
+        assert max(e) <= TOL, ("cfg5 learned, two-sided fallback", t, e)
