@@ -75,7 +75,7 @@ def parse():
     return p.parse_args()
 
 
-DEEP = ("cfg3", "cfg4", "cfg4x8", "cfg5", "cfg5x8")
+DEEP = ("cfg3", "cfg4", "cfg4x8", "cfg5", "cfg5x8", "farprobe")
 
 # The direct sum's arithmetic per (target node, source node) pair: the offset
 # (3 subtractions) and R^2 (one multiply, two FMAs: 5 flops), rsqrt, tau (two
@@ -102,6 +102,13 @@ def get_workload(name):
         w.description = ("first 8 of cfg4's 64 sub-domains: grids 24^3-96^3, spacings 0.225-0.33 bohr, "
                          "2600-16000 bohr apart")
         return w
+    if name == "farprobe":
+        # a small far-pair workload for profiling the far path: every cross
+        # pair far (at least 300 bohr apart), a few hundred pushes before the
+        # first batches of the gathered GEMM
+        return synth.scattered("farprobe", 32, 32, 0.3, 1400.0, 300.0,
+                               description="32 x 32^3, h=0.3 bohr, in a 1400 bohr cube at least 300 bohr apart "
+                                           "(far path profiling)")
     if name == "near48":
         w = synth.two_domain(48, 0.25, 200.0, "near48", steps=100, history=40)
         w.description = "2 x 48^3, h=0.25 bohr, centres 200 bohr apart on x (small ring, for profiling)"
@@ -773,7 +780,8 @@ def lib_bytes_str(w, info, depth):
 
 # Far distance of the low-rank pairs per deep workload: every cross pair of
 # cfg4 is more than 250 bohr apart (cfg3 and cfg5: 500).
-DEEP_FAR_DISTANCE = {"cfg3": 500.0, "cfg4": 250.0, "cfg4x8": 500.0, "cfg5": 500.0, "cfg5x8": 500.0}
+DEEP_FAR_DISTANCE = {"cfg3": 500.0, "cfg4": 250.0, "cfg4x8": 500.0, "cfg5": 500.0, "cfg5x8": 500.0,
+                     "farprobe": 250.0}
 
 
 def far_gather_work(lib, w, info, batch, source_points):

@@ -219,13 +219,26 @@ def seeded_sources(domains: Sequence[Domain], seed: int = SOURCE_SEED) -> List[G
             for d, s in zip(domains, ss.spawn(len(domains)))]
 
 
-def _scatter_centres(count: int, side: float, min_sep: float, rng) -> np.ndarray:
+def _scatter_centres(count: int, side: float, min_sep: float, rng, max_tries: int = 1_000_000) -> np.ndarray:
     pts: List[np.ndarray] = []
+    tries = 0
     while len(pts) < count:
+        tries += 1
+        if tries > max_tries:
+            raise ValueError(f"cannot place {count} centres {min_sep} apart in a cube of side {side}")
         p = rng.uniform(-side / 2, side / 2, 3)
         if all(np.linalg.norm(p - q) >= min_sep for q in pts):
             pts.append(p)
     return np.asarray(pts)
+
+
+def scattered(name: str, count: int, n: int, h: float, side: float, min_sep: float, seed: int = GEOMETRY_SEED,
+              description: str = "") -> Workload:
+    """``count`` cubic n^3 domains whose centres are drawn uniformly in a cube
+    of the given side with a minimum separation (seeded), with seeded sources."""
+    cs = _scatter_centres(count, side, min_sep, np.random.default_rng(seed))
+    doms = [cubic(c, n, h) for c in cs]
+    return Workload(name, doms, C_AU, 0.05, 0, 100, description, seeded_sources(doms))
 
 
 def two_domain(n: int, h: float, distance: float, name: str = "custom", steps: int = 8,
