@@ -180,7 +180,10 @@ typedef struct {
 typedef struct rp_ctx rp_ctx;
 
 /* Pair kinds reported by rp_pair_info. */
-typedef enum { RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1, RP_PAIR_LOWRANK = 2, RP_PAIR_LEARNED = 3 } rp_pair_kind;
+typedef enum {
+    RP_PAIR_FFT = 0, RP_PAIR_DIRECT = 1, RP_PAIR_LOWRANK = 2, RP_PAIR_LEARNED = 3,
+    RP_PAIR_OTHER = 4   /* not evaluated here: its source is owned by another context (rp_own_sources) */
+} rp_pair_kind;
 
 typedef struct {
     int kind;          /* rp_pair_kind */
@@ -214,6 +217,8 @@ typedef struct {
     long long host_bytes;     /* pinned host memory of the spilled history ((rho, J) slices) */
     double audit_rel_l2;      /* largest per-(domain, field) rel-L2 of the last rp_audit, -1 before the first */
     long long audit_step;     /* the step it audited, -1 before the first */
+    int owned_sources;        /* source domains this context owns (rp_own_sources; all by default) */
+    int npairs_other;         /* pairs whose source another context owns (RP_PAIR_OTHER) */
 } rp_stats;
 
 /* Kernel classes timed under RP_FLAG_PROFILE. */
@@ -230,7 +235,8 @@ typedef enum {
     RP_K_FAR_ANTERP = 9,    /* far path (two-sided factors): a pushed slice anterpolated onto its source's nodes */
     RP_K_MOMENTS = 10,      /* learned path: moments of the pushed slices */
     RP_K_LEARNED = 11,      /* learned path: network rows, network, output into the coefficients */
-    RP_K_COUNT = 12
+    RP_K_FAR_INTERP = 12,   /* far path: coefficients onto the grid of a target with no FFT pass (source partition) */
+    RP_K_COUNT = 13
 } rp_kernel_kind;
 
 /*
@@ -250,6 +256,24 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
  * finalize).  At most 256 domains.
  */
 rp_status rp_add_domain(rp_ctx *ctx, const double origin[3], const int n[3], double h, int *id);
+
+/*
+ * rp_own_sources -- source partition (Sec. IV: one process per domain, each
+ * computing its domain's contributions to every domain): this context owns
+ * the source domains ids[0 .. count-1] and no other.  It keeps only their
+ * histories and evaluates only the pairs (target, owned source), for every
+ * target: the pairs of other sources are RP_PAIR_OTHER.  rp_push / rp_push_host
+ * accept only owned domains (RP_ERR_ARG otherwise); a round is complete when
+ * every owned domain has pushed; rp_push_all reads only the owned domains'
+ * pointers (the others may be NULL).  rp_evaluate then writes, for every
+ * domain, the sum of the owned sources' contributions (every pair of an
+ * owned source is evaluated, so each target gets some): adding the outputs
+ * of contexts that own complementary
+ * sets of sources (one per GPU, summed by a reduce-scatter at each target's
+ * owner) gives the whole sum.  Before rp_finalize only; at least one id;
+ * RP_ERR_ARG for ids out of range or repeated.  Default: every domain owned.
+ */
+rp_status rp_own_sources(rp_ctx *ctx, const int *ids, int count);
 
 /*
  * rp_finalize -- plan every ordered pair (target, source), self pairs

@@ -236,6 +236,7 @@ void clear_far(rp_ctx *ctx)
     ctx->far2_BN = ctx->far2_KS = ctx->far2_D = ctx->far2_max_nz = 0; ctx->far2_fac_rows = 0;
     ctx->far_src_alone.clear(); ctx->far_src_alone_of_dom.clear();
     ctx->d_far_src_alone = nullptr;
+    ctx->far_tgt_alone.clear(); ctx->d_far_tgt_alone = nullptr; ctx->far_alone_planes = 0;
     ctx->far_max_r = ctx->npairs_far = 0;
     ctx->far_bytes = ctx->far_max_n = 0;
     ctx->far_zeroed_step = -1;
@@ -401,6 +402,9 @@ rp_status build_far_impl(rp_ctx *ctx, int max_optin)
 // target without one would have no pass that writes its output first.
 rp_status attach_far_targets(rp_ctx *ctx)
 {
+    rp_status st;
+    ctx->far_tgt_alone.clear();
+    ctx->far_alone_planes = 0;
     for (size_t k = 0; k < ctx->far_tgt.size(); ++k) {
         const FarTarget &F = ctx->far_tgt[k];
         bool done = false;
@@ -409,10 +413,17 @@ rp_status attach_far_targets(rp_ctx *ctx)
                 I.far = ctx->d_far_tgt + k;
                 done = true;
             }
-        if (!done)
-            return fail(ctx, RP_ERR_UNSUPPORTED, "far target " + std::to_string(F.dom) +
-                                                     " has no FFT self term to carry its far coefficients");
+        if (done) continue;
+        // no FFT pass (a target whose source another context owns): a separate
+        // interpolation after the direct pass, adding onto its direct pairs' output
+        FarTarget A = F;
+        A.interp_add = 0;
+        for (const DirectTarget &D : ctx->dtg)
+            if (D.dom == F.dom) A.interp_add = 1;
+        ctx->far_tgt_alone.push_back(A);
+        ctx->far_alone_planes += F.nz;
     }
+    if (!ctx->far_tgt_alone.empty() && (st = upload(ctx, &ctx->d_far_tgt_alone, ctx->far_tgt_alone))) return st;
     return RP_OK;
 }
 
@@ -784,7 +795,8 @@ const char *rp_kernel_name(int kind)
 {
     static const char *names[RP_K_COUNT] = {"ring_push", "fwd_plane", "fwd_column", "mac_inv_column",
                                             "inv_plane", "direct", "far_convert", "far_gemm",
-                                            "far_scatter", "far_anterp", "moments", "learned"};
+                                            "far_scatter", "far_anterp", "moments", "learned",
+                                            "far_interp"};
     return (kind >= 0 && kind < RP_K_COUNT) ? names[kind] : nullptr;
 }
 
@@ -850,7 +862,24 @@ rp_status rp_add_domain(rp_ctx *ctx, const double origin[3], const int n[3], dou
     d.h = h;
     d.N = (long long)n[0] * n[1] * n[2];
     ctx->doms.push_back(d);
+    if (!ctx->owned.empty()) ctx->owned.push_back(0);   // rp_own_sources named the earlier domains only
     *id = (int)ctx->doms.size() - 1;
+    return RP_OK;
+}
+
+rp_status rp_own_sources(rp_ctx *ctx, const int *ids, int count)
+{
+    if (!ctx) return RP_ERR_ARG;
+    if (ctx->finalized) return fail(ctx, RP_ERR_STATE, "rp_own_sources after rp_finalize");
+    const int nd = (int)ctx->doms.size();
+    if (!ids || count < 1 || count > nd) return fail(ctx, RP_ERR_ARG, "rp_own_sources: bad id list");
+    std::vector<char> own(nd, 0);
+    for (int i = 0; i < count; ++i) {
+        if (ids[i] < 0 || ids[i] >= nd || own[ids[i]])
+            return fail(ctx, RP_ERR_ARG, "rp_own_sources: id out of range or repeated");
+        own[ids[i]] = 1;
+    }
+    ctx->owned = own;
     return RP_OK;
 }
 
@@ -862,6 +891,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     if (nd == 0) return fail(ctx, RP_ERR_STATE, "no domains");
     const double cdt = ctx->cfg.c * ctx->cfg.dt;
     const bool fft_mode = ctx->cfg.mode == RP_MODE_FFT || ctx->cfg.mode == RP_MODE_LOWRANK;
+    if (ctx->owned.empty()) ctx->owned.assign(nd, 1);
+    ctx->n_owned = (int)std::count(ctx->owned.begin(), ctx->owned.end(), 1);
 
     // ---- pairs: lag windows and kinds
     ctx->pairs.assign((size_t)nd * nd, PairPlan{});
@@ -898,6 +929,10 @@ rp_status rp_finalize(rp_ctx *ctx)
             if (t == s && fft_mode && p.kind != RP_PAIR_FFT)
                 return fail(ctx, RP_ERR_UNSUPPORTED, "domain " + std::to_string(t) +
                                                          " exceeds 96 nodes per axis (FFT self term)");
+            if (!ctx->owned[s]) {   // another context evaluates this source's pairs
+                p.kind = RP_PAIR_OTHER;
+                continue;
+            }
             ctx->max_lag = std::max(ctx->max_lag, p.lag_hi);
         }
     // a target's FFT size: the largest over its FFT pairs
@@ -1320,10 +1355,11 @@ rp_status begin_push(rp_ctx *ctx, int id)
     if ((ctx->cfg.flags & RP_FLAG_DEFER_FAR) && !ctx->trained)
         return fail(ctx, RP_ERR_STATE, "RP_FLAG_DEFER_FAR: call rp_train_far_model before the first push");
     const int nd = (int)ctx->doms.size();
+    if (!ctx->owned[id]) return fail(ctx, RP_ERR_ARG, "domain " + std::to_string(id) + " is not owned by this context");
     if (ctx->step < 0 || ctx->npushed == nd) {
         ctx->step += 1;
-        std::fill(ctx->pushed.begin(), ctx->pushed.end(), 0);
-        ctx->npushed = 0;
+        for (int d = 0; d < nd; ++d) ctx->pushed[d] = ctx->owned[d] ? 0 : 1;   // others' sources count as pushed
+        ctx->npushed = nd - ctx->n_owned;
     }
     if (ctx->pushed[id]) return fail(ctx, RP_ERR_STATE, "domain " + std::to_string(id) + " pushed twice in one step");
     ctx->pushed[id] = 1;
@@ -1603,7 +1639,7 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     const int nd = (int)ctx->doms.size();
     if (!d_rho || !d_J) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL pointer array");
     for (int d = 0; d < nd; ++d)
-        if (!d_rho[d] || !d_J[d]) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL buffer");
+        if (ctx->owned[d] && (!d_rho[d] || !d_J[d])) return fail(ctx, RP_ERR_ARG, "rp_push_all: NULL buffer");
     if (ctx->step >= 0 && ctx->npushed != 0 && ctx->npushed != nd)
         return fail(ctx, RP_ERR_STATE, "rp_push_all inside a partially pushed step");
     if ((ctx->cfg.flags & RP_FLAG_DEFER_FAR) && !ctx->trained)
@@ -1612,7 +1648,8 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     std::fill(ctx->pushed.begin(), ctx->pushed.end(), 1);
     ctx->npushed = nd;
     IoPtrs in{};
-    for (int d = 0; d < nd; ++d) { in.rho[d] = d_rho[d]; in.J[d] = d_J[d]; }
+    for (int d = 0; d < nd; ++d)
+        if (ctx->owned[d]) { in.rho[d] = d_rho[d]; in.J[d] = d_J[d]; }
     rp_status st2;
     if ((st2 = split_inputs(ctx, 0, nd, in))) return st2;
     if ((st2 = enqueue_push(ctx, 0, nd, in))) return st2;
@@ -1688,18 +1725,19 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
     const int nd = (int)ctx->doms.size();
     if (!h_rho || !h_J) return fail(ctx, RP_ERR_ARG, "rp_push_all_host: NULL pointer array");
     for (int d = 0; d < nd; ++d)
-        if (!h_rho[d] || !h_J[d]) return fail(ctx, RP_ERR_ARG, "rp_push_all_host: NULL buffer");
+        if (ctx->owned[d] && (!h_rho[d] || !h_J[d])) return fail(ctx, RP_ERR_ARG, "rp_push_all_host: NULL buffer");
     if (ctx->step >= 0 && ctx->npushed != 0 && ctx->npushed != nd)
         return fail(ctx, RP_ERR_STATE, "rp_push_all_host inside a partially pushed step");
     if ((st = open_host_copies(ctx))) return st;
     const int b = (int)((ctx->step + 1) & 1);
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b], 0));   // the push two steps back
     for (int d = 0; d < nd; ++d)
-        if ((st = stage_host_input(ctx, d, b, h_rho[d], h_J[d]))) return st;
+        if (ctx->owned[d] && (st = stage_host_input(ctx, d, b, h_rho[d], h_J[d]))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
-    std::vector<const float *> rho(nd), J(nd);
+    std::vector<const float *> rho(nd, nullptr), J(nd, nullptr);
     for (int d = 0; d < nd; ++d) {
+        if (!ctx->owned[d]) continue;
         rho[d] = ctx->in_stage[b][d];
         J[d] = ctx->in_stage[b][d] + ctx->doms[d].N;
     }
@@ -1770,6 +1808,13 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
         if ((st = timed_launch(ctx, RP_K_DIRECT, "direct sum", [&] {
                  return launch_direct(ctx->d_dtg, (int)ctx->dtg.size(), ctx->d_dpairs, out, ctx->dir_blocks,
                                       ctx->smem_dir, kstep, clamp, inv_cdt, inv_c, ctx->stream);
+             })))
+            return st;
+    }
+    if (!ctx->far_tgt_alone.empty()) {
+        if ((st = timed_launch(ctx, RP_K_FAR_INTERP, "far interpolation", [&] {
+                 return launch_far_interp(ctx->d_far_tgt_alone, (int)ctx->far_tgt_alone.size(),
+                                          ctx->far_alone_planes, out, step, inv_c, ctx->stream);
              })))
             return st;
     }
@@ -2309,6 +2354,8 @@ rp_status rp_query(rp_ctx *ctx, rp_stats *out)
     out->host_bytes = ctx->host_bytes;
     out->audit_rel_l2 = ctx->audit_rel_l2;
     out->audit_step = ctx->audit_step;
+    out->owned_sources = ctx->n_owned;
+    for (const PairPlan &p : ctx->pairs) out->npairs_other += p.kind == RP_PAIR_OTHER;
     out->mac_warps = 0;
     for (const LaunchGroup &g : ctx->inv_groups)
         if (g.cls > 0 && ctx->tma) out->mac_warps = ctx->mac_cw[class_slot(g.cls)];

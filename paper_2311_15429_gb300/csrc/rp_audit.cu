@@ -25,7 +25,7 @@ constexpr int kAuditThreads = 256;
 struct AuditSrc {
     const float *raw;   // [depth][4][N]
     long long N;
-    int nx, ny, depth, pad_;
+    int nx, ny, depth, dom;
     double ox, oy, oz, h;
 };
 
@@ -61,7 +61,7 @@ __global__ void __launch_bounds__(kAuditThreads) k_audit(const AuditSrc *__restr
             const double vol = S.h * S.h * S.h;
             const long long N = S.N;
             for (long long q = threadIdx.x; q < N; q += blockDim.x) {
-                if (s == P.dom && q == k) {   // the node itself: cell average, lag 0
+                if (S.dom == P.dom && q == k) {   // the node itself: cell average, lag 0
                     const double w0 = self_c * S.h * S.h;
                     const float *x = S.raw + (step % S.depth) * 4 * N + q;
 #pragma unroll
@@ -136,7 +136,7 @@ rp_status audit_run(rp_ctx *ctx, const std::vector<AuditPt> &pts, const float *c
 {
     const int nd = (int)ctx->doms.size();
     for (int d = 0; d < nd; ++d)
-        if (!ctx->raw[d].ring)
+        if (ctx->owned[d] && !ctx->raw[d].ring)
             return fail(ctx, RP_ERR_STATE, "the FP64 audit needs RP_FLAG_AUDIT (every source's raw history)");
     if (ctx->step < 0 || ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "audit before every domain pushed the step");
     if (!ctx->clamp && ctx->step - ctx->max_lag < 0)
@@ -145,11 +145,14 @@ rp_status audit_run(rp_ctx *ctx, const std::vector<AuditPt> &pts, const float *c
     const int npts = (int)pts.size();
     rp_status st = audit_scratch(ctx, npts);
     if (st) return st;
-    std::vector<AuditSrc> hs(nd);
+    // the sources this context owns (all of them but under a source partition)
+    std::vector<AuditSrc> hs;
     std::vector<AuditTgt> ht(nd);
     for (int d = 0; d < nd; ++d) {
         const DomainDesc &D = ctx->doms[d];
-        hs[d] = AuditSrc{ctx->raw[d].ring, D.N, D.n[0], D.n[1], ctx->raw[d].depth, 0, D.o[0], D.o[1], D.o[2], D.h};
+        if (ctx->owned[d])
+            hs.push_back(AuditSrc{ctx->raw[d].ring, D.N, D.n[0], D.n[1], ctx->raw[d].depth, d, D.o[0], D.o[1], D.o[2],
+                                  D.h});
         ht[d] = AuditTgt{D.o[0], D.o[1], D.o[2], D.h, D.n[0], D.n[1], {0, 0}, D.N, got ? d_phi[d] : nullptr,
                          got ? d_A[d] : nullptr};
     }
@@ -159,11 +162,11 @@ rp_status audit_run(rp_ctx *ctx, const std::vector<AuditPt> &pts, const float *c
     AuditPt *d_pts = reinterpret_cast<AuditPt *>(d_tgt + nd);
     double *d_vals = reinterpret_cast<double *>(d_pts + npts);
     float *d_got = reinterpret_cast<float *>(d_vals + 4 * (size_t)npts);
-    RP_CUDA(ctx, cudaMemcpyAsync(d_src, hs.data(), nd * sizeof(AuditSrc), cudaMemcpyHostToDevice, ctx->stream));
+    RP_CUDA(ctx, cudaMemcpyAsync(d_src, hs.data(), hs.size() * sizeof(AuditSrc), cudaMemcpyHostToDevice, ctx->stream));
     RP_CUDA(ctx, cudaMemcpyAsync(d_tgt, ht.data(), nd * sizeof(AuditTgt), cudaMemcpyHostToDevice, ctx->stream));
     RP_CUDA(ctx, cudaMemcpyAsync(d_pts, pts.data(), npts * sizeof(AuditPt), cudaMemcpyHostToDevice, ctx->stream));
     const int grid = std::max(1, std::min(npts, 16 * std::max(1, ctx->sm_count)));
-    k_audit<<<grid, kAuditThreads, 0, ctx->stream>>>(d_src, nd, d_tgt, d_pts, npts, ctx->step, ctx->clamp ? 1 : 0,
+    k_audit<<<grid, kAuditThreads, 0, ctx->stream>>>(d_src, (int)hs.size(), d_tgt, d_pts, npts, ctx->step, ctx->clamp ? 1 : 0,
                                                      1.0 / (ctx->cfg.c * ctx->cfg.dt), 1.0 / ctx->cfg.c,
                                                      cube_average_constant(), d_vals, got ? d_got : nullptr);
     RP_CUDA(ctx, cudaGetLastError());

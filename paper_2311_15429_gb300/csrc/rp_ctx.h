@@ -192,8 +192,13 @@ struct rp_ctx {
     CUtensorMap far2_mapQ{}, far2_mapF{};
     int far2_BN = 0, far2_KS = 0, far2_D = 0, far2_max_nz = 0;
     long long far2_fac_rows = 0;
-    // far sources with no forward ring of their own: staged by a separate kernel
+    // far sources with no forward ring of their own: staged by a separate
+    // kernel; far targets with no FFT pass: interpolated by a separate kernel
+    // after the direct pass (only under a source partition)
     std::vector<FarSource> far_src_alone;
+    std::vector<FarTarget> far_tgt_alone;
+    FarTarget *d_far_tgt_alone = nullptr;
+    int far_alone_planes = 0;
     std::vector<int> far_src_alone_of_dom;
     FarSource *d_far_src_alone = nullptr;
     FarLink *d_far_links = nullptr;
@@ -244,10 +249,13 @@ struct rp_ctx {
     cudaEvent_t out_ready = nullptr;           // the last host evaluation's results are staged
     cudaEvent_t out_free[2] = {nullptr, nullptr};   // the copy out of out_stage[b] is done
 
-    // step state
+    // step state.  Under a source partition (rp_own_sources) the domains
+    // another context owns count as pushed from the start of every round.
     long long step = -1;
     std::vector<char> pushed;
     int npushed = 0;
+    std::vector<char> owned;          // [ndom]: this context owns the domain's source
+    int n_owned = 0;
 
     // profiling
     std::vector<ProfRec> pending;

@@ -130,7 +130,64 @@ __global__ void __launch_bounds__(kFarThreads) k_far_scatter(const FarLink *__re
     *c += acc;
 }
 
+// The far coefficients of step `step` interpolated onto the grid of a far
+// target that has no FFT pass of its own (its inverse plane pass adds them
+// otherwise): written, or added when direct pairs wrote the output first.
+// One block per z-plane.
+__global__ void __launch_bounds__(kFarThreads) k_far_interp(const FarTarget *__restrict__ tgts, int ntgt, OutPtrs out,
+                                                             long long step, float inv_c)
+{
+    __shared__ float cz[kMaxFarPts * kMaxFarPts * 4];   // coefficients contracted over z
+    int b = blockIdx.x, ti = 0;
+    for (; ti < ntgt; ++ti) {
+        if (b < tgts[ti].nz) break;
+        b -= tgts[ti].nz;
+    }
+    if (ti >= ntgt) return;
+    const FarTarget T = tgts[ti];
+    const int z = b;
+    const float *c = T.cring + (step % T.depth) * (T.r * 4);
+    for (int i = threadIdx.x; i < T.px * T.py * 4; i += blockDim.x) {
+        const int f = i % 4, ab = i / 4;
+        float s = 0.0f;
+        for (int cc = 0; cc < T.pz; ++cc) s = fmaf(T.Lz[z * T.pz + cc], c[((cc * T.py) * T.px + ab) * 4 + f], s);
+        cz[i] = s;   // index (b * px + a) * 4 + f with node a fastest
+    }
+    __syncthreads();
+    const long long N = (long long)T.nx * T.ny * T.nz;
+    for (int i = threadIdx.x; i < T.nx * T.ny; i += blockDim.x) {
+        const int x = i % T.nx, y = i / T.nx;
+        float v[4] = {0.f, 0.f, 0.f, 0.f};
+        for (int bb = 0; bb < T.py; ++bb) {
+            const float wy = T.Ly[y * T.py + bb];
+            for (int aa = 0; aa < T.px; ++aa) {
+                const float w = wy * T.Lx[x * T.px + aa];
+                const float *q = cz + (bb * T.px + aa) * 4;
+                v[0] = fmaf(w, q[0], v[0]);
+                v[1] = fmaf(w, q[1], v[1]);
+                v[2] = fmaf(w, q[2], v[2]);
+                v[3] = fmaf(w, q[3], v[3]);
+            }
+        }
+        const long long k = (long long)z * T.nx * T.ny + i;
+        float *o[4] = {out.phi[T.dom] + k, out.A[T.dom] + k, out.A[T.dom] + N + k, out.A[T.dom] + 2 * N + k};
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const float val = f == 0 ? v[f] : inv_c * v[f];
+            *o[f] = T.interp_add ? *o[f] + val : val;
+        }
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
+                              float inv_c, cudaStream_t s)
+{
+    if (ntgt <= 0 || nplanes <= 0) return cudaSuccess;
+    k_far_interp<<<nplanes, kFarThreads, 0, s>>>(d_tgts, ntgt, out, step, inv_c);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_far_build_w(const FarRow *d_rows, int nrows, const int n[3], double h, double inv_cdt, int ks,
                                __nv_bfloat16 *W, cudaStream_t s)

@@ -152,6 +152,8 @@ struct FarTarget {
     int depth;
     int lag_hi_max;          // largest lag of the target's far pairs
     int task0, task1;        // two-sided factors: this target's CTAs of the gathered GEMM
+    int interp_add;          // k_far_interp (targets without an FFT pass): add onto the output (1) or write it (0)
+    int pad_;
 };
 
 // ---- two-sided far factors (rp_far2.cu, rp_config.far_source_points > 0)
@@ -282,6 +284,8 @@ cudaError_t launch_far_build_w(const FarRow *d_rows, int nrows, const int n[3], 
 cudaError_t launch_far_convert(const FarSource *d_srcs, int nsrc, const IoPtrs &in, int slot, long long max_n,
                                cudaStream_t s);
 cudaError_t launch_far_zero(const FarTarget *d_tgts, int ntgt, long long j1, int batch, int max_r, cudaStream_t s);
+cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
+                              float inv_c, cudaStream_t s);
 cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads, const float *Z, int ldz, long long j0,
                                int batch, cudaStream_t s);
 

@@ -22,10 +22,10 @@ RP_FLAG_GROUND_STATE_SPLIT = 0x10
 RP_FLAG_HISTORY_SPILL = 0x20
 RP_FLAG_AUDIT = 0x40
 RP_FLAG_PLAIN_SUM = 0x80
-RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED = 0, 1, 2, 3
+RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED, RP_PAIR_OTHER = 0, 1, 2, 3, 4
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
  RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_ANTERP, RP_K_MOMENTS, RP_K_LEARNED,
- RP_K_COUNT) = range(13)
+ RP_K_FAR_INTERP, RP_K_COUNT) = range(14)
 MAX_DOMAINS = 256
 
 
@@ -66,7 +66,8 @@ class rp_stats(ctypes.Structure):
                 ("points", ctypes.c_longlong), ("mac_tma", ctypes.c_int), ("npairs_far", ctypes.c_int),
                 ("far_bytes", ctypes.c_longlong), ("mac_warps", ctypes.c_int), ("npairs_learned", ctypes.c_int),
                 ("spill_windows", ctypes.c_int), ("reserved", ctypes.c_int), ("host_bytes", ctypes.c_longlong),
-                ("audit_rel_l2", ctypes.c_double), ("audit_step", ctypes.c_longlong)]
+                ("audit_rel_l2", ctypes.c_double), ("audit_step", ctypes.c_longlong),
+                ("owned_sources", ctypes.c_int), ("npairs_other", ctypes.c_int)]
 
 
 class RPError(RuntimeError):
@@ -86,6 +87,7 @@ SIGNATURES = {
     "rp_add_domain": (_I, [_V, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(_I),
                            ctypes.c_double, ctypes.POINTER(_I)]),
     "rp_finalize": (_I, [_V]),
+    "rp_own_sources": (_I, [_V, ctypes.POINTER(_I), _I]),
     "rp_push": (_I, [_V, _I, _V, _V]),
     "rp_push_all": (_I, [_V, _PP, _PP]),
     "rp_push_host": (_I, [_V, _I, _V, _V]),
@@ -227,6 +229,12 @@ def rp_add_domain(ctx, origin, n, h: float) -> int:
     i = ctypes.c_int()
     _check(load().rp_add_domain(ctx, o, nn, float(h), ctypes.byref(i)), ctx)
     return i.value
+
+
+def rp_own_sources(ctx, ids: Sequence[int]):
+    """Source partition: the context owns these source domains and no other."""
+    arr = (ctypes.c_int * len(ids))(*[int(i) for i in ids])
+    _check(load().rp_own_sources(ctx, arr, len(ids)), ctx)
 
 
 def rp_finalize(ctx):
@@ -481,7 +489,7 @@ class RetardedPotentials:
                  mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
                  far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0,
                  mac_warps: int = 0, profile_every: int = 0, far_source_points: int = 0,
-                 device_budget: int = 0):
+                 device_budget: int = 0, owned_sources: Optional[Sequence[int]] = None):
         import torch
         self.domains = list(domains)
         self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
@@ -490,6 +498,8 @@ class RetardedPotentials:
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)
+            if owned_sources is not None:
+                rp_own_sources(self.ctx, owned_sources)
             rp_finalize(self.ctx)
         except Exception:
             rp_destroy(self.ctx)
