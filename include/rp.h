@@ -339,9 +339,13 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A);
  * for those calls) as a CUDA graph, without running it (the recording uses a
  * stream of its own; the replays run on the context stream).
  * The buffers are fixed: each rp_graph_step replays the step on their current
- * contents.  Call at a step boundary.  FFT and direct pairs only, without
- * RP_FLAG_PROFILE or RP_FLAG_GROUND_STATE_SPLIT (RP_ERR_UNSUPPORTED
- * otherwise): the far path's launches change from step to step.  A new
+ * contents.  Call at a step boundary.  FFT, direct and two-sided far pairs
+ * (rp_config.far_source_points > 0: their kernels read the step on the
+ * device, and the batch GEMM's launch, recorded in every step, works on a
+ * batch's last push only), without RP_FLAG_PROFILE or
+ * RP_FLAG_GROUND_STATE_SPLIT (RP_ERR_UNSUPPORTED otherwise, and for
+ * one-sided far pairs and the learned field, whose launches change from
+ * step to step).  A new
  * capture replaces the previous graph.  Not with RP_FLAG_HISTORY_SPILL (its
  * copies address the slots of the current step).  (No counterpart in the paper: a
  * property of the library.)

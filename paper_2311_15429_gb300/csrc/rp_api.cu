@@ -1467,22 +1467,25 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
             a1 = ai + 1;
         }
         if (a0 >= 0 && (st = timed_launch(ctx, RP_K_FAR_ANTERP, "far anterpolation", [&] {
-                            return launch_far_anterp(ctx->d_far2_srcs + a0, a1 - a0, ctx->far2_max_nz, in, step,
-                                                     ctx->far2_D, ctx->far2_KS, ctx->stream);
+                            return launch_far_anterp(ctx->d_far2_srcs + a0, a1 - a0, ctx->far2_max_nz, in, kstep,
+                                                     ctx->d_step, ctx->far2_D, ctx->far2_KS, ctx->stream);
                         })))
             return st;
         const int batch = ctx->cfg.far_batch;
-        if (ctx->npushed == nd && step % batch == batch - 1) {
+        // a recorded step launches both every step; they read the device step
+        // and work on a batch's last push only
+        if (ctx->capturing || (ctx->npushed == nd && step % batch == batch - 1)) {
+            const long long l0 = ctx->capturing ? -1 : step + 1;
             if ((st = timed_launch(ctx, RP_K_FAR_GEMM, "far gathered GEMM", [&] {
                      return launch_far_gather(ctx->far2_mapQ, ctx->far2_mapF, ctx->d_far2_tasks,
                                               (int)ctx->far2_tasks.size(), ctx->d_far2_kb, ctx->far2_BN, ctx->far2_KS,
-                                              ctx->far2_D, step + 1, ctx->far2_work, ctx->smem_optin, ctx->d_err,
-                                              ctx->stream);
+                                              ctx->far2_D, l0, ctx->d_step, batch, ctx->far2_work, ctx->smem_optin,
+                                              ctx->d_err, ctx->stream);
                  })))
                 return st;
             if ((st = timed_launch(ctx, RP_K_FAR_SCATTER, "far gathered sums", [&] {
                      return launch_far_reduce(ctx->d_far_tgt, (int)ctx->far_tgt.size(), ctx->far2_work, ctx->far2_BN,
-                                              step + 1, batch, ctx->far_max_r, ctx->stream);
+                                              l0, ctx->d_step, batch, ctx->far_max_r, ctx->stream);
                  })))
                 return st;
         }
@@ -1814,7 +1817,7 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     if (!ctx->far_tgt_alone.empty()) {
         if ((st = timed_launch(ctx, RP_K_FAR_INTERP, "far interpolation", [&] {
                  return launch_far_interp(ctx->d_far_tgt_alone, (int)ctx->far_tgt_alone.size(),
-                                          ctx->far_alone_planes, out, step, inv_c, ctx->stream);
+                                          ctx->far_alone_planes, out, kstep, ctx->d_step, inv_c, ctx->stream);
              })))
             return st;
     }
@@ -2235,10 +2238,13 @@ rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *
     if (!d_rho || !d_J || !d_phi || !d_A) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL pointer array");
     for (int d = 0; d < nd; ++d)
         if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
-    if (ctx->profile || ctx->split || !ctx->far_src.empty() || !ctx->far_tgt.empty() || ctx->far2 || !ctx->lpairs.empty() ||
-        (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_srcs.empty())
+    // the one-sided factors' launches and the learned field's change from step
+    // to step; the two-sided factors' kernels read the step on the device
+    if (ctx->profile || ctx->split || !ctx->far_src.empty() || (!ctx->far_tgt.empty() && !ctx->far2) ||
+        !ctx->lpairs.empty() || (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_srcs.empty())
         return fail(ctx, RP_ERR_UNSUPPORTED,
-                    "rp_graph_capture: FFT and direct pairs only, without profiling, split or history spill");
+                    "rp_graph_capture: FFT, direct and two-sided far pairs only, without profiling, split or history "
+                    "spill");
     if (ctx->step >= 0 && ctx->npushed != nd) return fail(ctx, RP_ERR_STATE, "rp_graph_capture inside a partially pushed step");
     if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
     if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }

@@ -135,8 +135,9 @@ __global__ void __launch_bounds__(kFarThreads) k_far_scatter(const FarLink *__re
 // otherwise): written, or added when direct pairs wrote the output first.
 // One block per z-plane.
 __global__ void __launch_bounds__(kFarThreads) k_far_interp(const FarTarget *__restrict__ tgts, int ntgt, OutPtrs out,
-                                                             long long step, float inv_c)
+                                                             long long step, const long long *d_step, float inv_c)
 {
+    if (step < 0) step = *d_step;   // graph replay: the step from the device counter
     __shared__ float cz[kMaxFarPts * kMaxFarPts * 4];   // coefficients contracted over z
     int b = blockIdx.x, ti = 0;
     for (; ti < ntgt; ++ti) {
@@ -182,10 +183,10 @@ __global__ void __launch_bounds__(kFarThreads) k_far_interp(const FarTarget *__r
 }  // namespace
 
 cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
-                              float inv_c, cudaStream_t s)
+                              const long long *d_step, float inv_c, cudaStream_t s)
 {
     if (ntgt <= 0 || nplanes <= 0) return cudaSuccess;
-    k_far_interp<<<nplanes, kFarThreads, 0, s>>>(d_tgts, ntgt, out, step, inv_c);
+    k_far_interp<<<nplanes, kFarThreads, 0, s>>>(d_tgts, ntgt, out, step, d_step, inv_c);
     return cudaGetLastError();
 }
 

@@ -15,7 +15,9 @@
 // at every push, k_far_anterp), and a far pair's factor is (B lags) blocks
 // of r_t x r_s: its size does not depend on the grids.
 //
-// Every `batch` pushes, one launch of k_far_gather gives every far target
+// Every `batch` pushes (in a recorded graph: every step, the kernel reading
+// the device step and doing nothing but on a batch's last push), one launch
+// of k_far_gather gives every far target
 // its node values for the next `batch` steps l0 .. l0 + batch - 1: per CTA,
 //
 //   D[(l, f)][a] = sum over its (source, lag) blocks of
@@ -57,10 +59,12 @@ __host__ __device__ __forceinline__ long long pos_mod(long long x, long long d) 
 // the z weights and writes the node coefficients of this step, bf16 hi and
 // lo, at both mirrored slots of the ring.
 __global__ void __launch_bounds__(kAnterpThreads) k_far_anterp(const FarSrc2 *__restrict__ srcs, int nsrc, IoPtrs in,
-                                                                long long step, int D, int KS)
+                                                                long long step, const long long *d_step, int D,
+                                                                int KS)
 {
     extern __shared__ float tsum[];   // [4][ny][qx]
     __shared__ int last;
+    if (step < 0) step = *d_step;   // graph replay: the step from the device counter
     const int si = blockIdx.y;
     if (si >= nsrc) return;
     const FarSrc2 S = srcs[si];
@@ -164,8 +168,13 @@ template <int BN>
 __global__ void __launch_bounds__(kGatherThreads, 1)
     k_far_gather(const __grid_constant__ CUtensorMap mapQ, const __grid_constant__ CUtensorMap mapF,
                  const FarTask *__restrict__ tasks, const FarKBlock *__restrict__ kbs, int KS, int D, long long l0,
-                 float *work, int stages, int *err)
+                 const long long *d_step, int batch, float *work, int stages, int *err)
 {
+    if (l0 < 0) {   // graph replay: every step's launch, working on the last push of a batch only
+        const long long s = *d_step;
+        if (s % batch != batch - 1) return;
+        l0 = s + 1;
+    }
     constexpr int A_BYTES = kBM * kBK * 2, B_BYTES = BN * kBK * 2;
     constexpr int B_OFF = 2 * A_BYTES;
     constexpr int STAGE = 2 * (A_BYTES + B_BYTES);
@@ -283,8 +292,13 @@ __global__ void __launch_bounds__(kGatherThreads, 1)
 // added) into its coefficient ring.  Thread (l, a, f) of target blockIdx.y.
 __global__ void __launch_bounds__(kFarThreads2) k_far_reduce(const FarTarget *__restrict__ tgts, int ntgt,
                                                               const float *__restrict__ work, int BN, long long l0,
-                                                              int batch)
+                                                              const long long *d_step, int batch)
 {
+    if (l0 < 0) {   // graph replay, as k_far_gather
+        const long long s = *d_step;
+        if (s % batch != batch - 1) return;
+        l0 = s + 1;
+    }
     const int ti = blockIdx.y;
     if (ti >= ntgt) return;
     const FarTarget T = tgts[ti];
@@ -324,13 +338,13 @@ int far_gather_bn(int r)
     return 0;
 }
 
-cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step, int D,
-                              int KS, cudaStream_t s)
+cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step,
+                              const long long *d_step, int D, int KS, cudaStream_t s)
 {
     if (nsrc <= 0) return cudaSuccess;
     // the row sums of one plane: 4 fields x ny (<= kMaxFFT) x qx (<= kMaxFarPts) floats
     const size_t smem = sizeof(float) * 4 * kMaxFFT * kMaxFarPts;
-    k_far_anterp<<<dim3(max_nz, nsrc), kAnterpThreads, smem, s>>>(d_srcs, nsrc, in, step, D, KS);
+    k_far_anterp<<<dim3(max_nz, nsrc), kAnterpThreads, smem, s>>>(d_srcs, nsrc, in, step, d_step, D, KS);
     return cudaGetLastError();
 }
 
@@ -346,8 +360,8 @@ cudaError_t launch_far_build_fac(const FarBuild *d_blocks, int nblocks, const do
 }
 
 cudaError_t launch_far_gather(const CUtensorMap &mapQ, const CUtensorMap &mapF, const FarTask *d_tasks, int ntasks,
-                              const FarKBlock *d_kb, int BN, int KS, int D, long long l0, float *work,
-                              int smem_optin, int *d_err, cudaStream_t s)
+                              const FarKBlock *d_kb, int BN, int KS, int D, long long l0, const long long *d_step,
+                              int batch, float *work, int smem_optin, int *d_err, cudaStream_t s)
 {
     if (ntasks <= 0) return cudaSuccess;
     if (KS % kBK || D < 32) return cudaErrorInvalidValue;
@@ -359,7 +373,9 @@ cudaError_t launch_far_gather(const CUtensorMap &mapQ, const CUtensorMap &mapF, 
     cudaError_t e = cudaSuccess;
     auto go = [&](auto kern) {
         e = open_smem2(kern, smem);
-        if (!e) kern<<<ntasks, kGatherThreads, smem, s>>>(mapQ, mapF, d_tasks, d_kb, KS, D, l0, work, stages, d_err);
+        if (!e)
+            kern<<<ntasks, kGatherThreads, smem, s>>>(mapQ, mapF, d_tasks, d_kb, KS, D, l0, d_step, batch, work, stages,
+                                                     d_err);
     };
     switch (BN) {
     case 32: go(k_far_gather<32>); break;
@@ -371,12 +387,12 @@ cudaError_t launch_far_gather(const CUtensorMap &mapQ, const CUtensorMap &mapF, 
     return e ? e : cudaGetLastError();
 }
 
-cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *work, int BN, long long l0, int batch,
-                              int max_r, cudaStream_t s)
+cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *work, int BN, long long l0,
+                              const long long *d_step, int batch, int max_r, cudaStream_t s)
 {
     if (ntgt <= 0) return cudaSuccess;
     const int bx = (batch * max_r * 4 + kFarThreads2 - 1) / kFarThreads2;
-    k_far_reduce<<<dim3(bx, ntgt), kFarThreads2, 0, s>>>(d_tgts, ntgt, work, BN, l0, batch);
+    k_far_reduce<<<dim3(bx, ntgt), kFarThreads2, 0, s>>>(d_tgts, ntgt, work, BN, l0, d_step, batch);
     return cudaGetLastError();
 }
 

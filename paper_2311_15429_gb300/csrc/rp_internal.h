@@ -285,21 +285,23 @@ cudaError_t launch_far_convert(const FarSource *d_srcs, int nsrc, const IoPtrs &
                                cudaStream_t s);
 cudaError_t launch_far_zero(const FarTarget *d_tgts, int ntgt, long long j1, int batch, int max_r, cudaStream_t s);
 cudaError_t launch_far_interp(const FarTarget *d_tgts, int ntgt, int nplanes, const OutPtrs &out, long long step,
-                              float inv_c, cudaStream_t s);
+                              const long long *d_step, float inv_c, cudaStream_t s);
 cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads, const float *Z, int ldz, long long j0,
                                int batch, cudaStream_t s);
 
 // two-sided far factors (rp_far2.cu)
+// step / l0 < 0: read the step from d_step (graph replay; the gather and the
+// reduction then run on a batch's last push only)
 cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step,
-                              int D, int KS, cudaStream_t s);
+                              const long long *d_step, int D, int KS, cudaStream_t s);
 cudaError_t launch_far_build_fac(const FarBuild *d_blocks, int nblocks, const double *d_tnodes,
                                  const double *d_snodes, int BN, int KS, double inv_cdt, __nv_bfloat16 *fac,
                                  cudaStream_t s);
 cudaError_t launch_far_gather(const CUtensorMap &mapQ, const CUtensorMap &mapF, const FarTask *d_tasks, int ntasks,
-                              const FarKBlock *d_kb, int BN, int KS, int D, long long l0, float *work,
-                              int smem_optin, int *d_err, cudaStream_t s);
-cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *work, int BN, long long l0, int batch,
-                              int max_r, cudaStream_t s);
+                              const FarKBlock *d_kb, int BN, int KS, int D, long long l0, const long long *d_step,
+                              int batch, float *work, int smem_optin, int *d_err, cudaStream_t s);
+cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *work, int BN, long long l0,
+                              const long long *d_step, int batch, int max_r, cudaStream_t s);
 int far_gather_bn(int r);   // gathered-GEMM column tile for r target nodes (0 if more than 256)
 
 // shared-memory sizes the kernels need for the given shapes

@@ -83,3 +83,59 @@ def test_far_path_total_and_far_field(batch, source_points):
             want = oracle_values(doms, far_only, 0, synth.C_AU, 0.05, t, step, np.arange(doms[t].N))
             errs = rel_l2(out[step][t], want)
             assert max(errs) <= TOL, ("far only", step, t, errs)
+
+
+@pytest.mark.parametrize("owned", [None, [2]])
+def test_graph_replay_two_sided_far(owned):
+    """A step with two-sided far pairs recorded as a CUDA graph: every
+    replay gives the bits of the plain calls, across three batches of the
+    gathered GEMM (whose launch is recorded in every step and works on a
+    batch's last push only), with a plain step in between; also for a
+    context that owns only the far source (its other targets written by the
+    far interpolation alone)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    doms, srcs = _setup()
+    T, start = 200, 100
+    hists = [s.history(0, T, 0.05) for s in srcs]
+    kw = dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=32, far_source_points=4)
+    if owned is not None:
+        kw["owned_sources"] = owned
+    own = owned if owned is not None else [0, 1, 2]
+    slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+
+    def push(lib, i):
+        lib.push_all([slices[i][d][0] if d in own else None for d in range(3)],
+                     [slices[i][d][1:].reshape(-1) if d in own else None for d in range(3)])
+
+    want = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, **kw) as lib:
+        for i in range(T):
+            push(lib, i)
+            if i >= start:
+                p_, a_ = lib.evaluate()
+                want[i] = [torch.cat([p_[d], a_[d]]).cpu().numpy() for d in range(3)]
+    got = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, **kw) as lib:
+        rho = [torch.zeros(d.N, device=dev) for d in doms]
+        J = [torch.zeros(3 * d.N, device=dev) for d in doms]
+        phi = [torch.empty(d.N, device=dev) for d in doms]
+        A = [torch.empty(3 * d.N, device=dev) for d in doms]
+        for i in range(start):
+            push(lib, i)
+        rp.rp_graph_capture(lib.ctx, rho, J, phi, A)
+        for i in range(start, T):
+            if i == start + 40:                       # one step by the plain calls
+                push(lib, i)
+                p_, a_ = lib.evaluate()
+                got[i] = [torch.cat([p_[d], a_[d]]).cpu().numpy() for d in range(3)]
+                continue
+            for d in own:
+                rho[d].copy_(slices[i][d][0])
+                J[d].copy_(slices[i][d][1:].reshape(-1))
+            rp.rp_graph_step(lib.ctx)
+            got[i] = [torch.cat([phi[d], A[d]]).cpu().numpy() for d in range(3)]
+        lib.sync()
+    for i in range(start, T):
+        for d in range(3):
+            np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"step {i} domain {d}")
