@@ -984,6 +984,27 @@ def deep_leg(args, name, K, W, local, stream, mode="lowrank", source_points=4, c
                     "tensor_frac": fl / (us * 1e-6) / 1e12 / bf16[0], "gbps": by / (us * 1e-6) / 1e9,
                     "hbm_frac": by / (us * 1e-6) / 1e9 / peak, "flops_per_launch": fl, "bytes_per_launch": by,
                     "peak_source": bf16[1]}
+    # the same step as one CUDA graph launch (two-sided factors): recorded on
+    # one set of the cycled inputs, replayed K times with those inputs (the
+    # work does not depend on the values; replays are checked bit for bit
+    # against the plain calls by the GPU tests)
+    graph = None
+    if source_points and mode == "lowrank":
+        r, J = cyc[0]
+        rp.rp_graph_capture(lib.ctx, r, J, lib.phi, lib.A)
+        rp.rp_graph_step(lib.ctx)
+        torch.cuda.synchronize()
+        g0, g1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        g0.record(stream)
+        for i in range(K):
+            rp.rp_graph_step(lib.ctx)
+        g1.record(stream)
+        torch.cuda.synchronize()
+        gms = g0.elapsed_time(g1) / K
+        graph = {"ms_per_step": gms, "value": w.points / (gms / 1e3), "unit": UNIT, "steps": K,
+                 "host_launches_per_step": 1,
+                 "note": "one graph launch per step: every push, FFT, MAC, far-path and interpolation kernel of the "
+                         "step; inputs fixed between replays"}
     q = lib.query()
     lib.close()
     plain_line = None
@@ -1000,7 +1021,7 @@ def deep_leg(args, name, K, W, local, stream, mode="lowrank", source_points=4, c
             "far_pairs": q["npairs_far"], "learned_pairs": q["npairs_learned"], "far_bytes": q["far_bytes"],
             "device_bytes": q["device_bytes"], "training": train, "accuracy": acc, "roofline": roof,
             "far_gemm_roofline": far_roof, "kernels": kstats, "gpu_launches": launches, "plain_path": plain_line,
-            "setup_s": setup_s}
+            "graph_replay": graph, "setup_s": setup_s}
 
 
 def far_alone_check(args, w, mode, source_points, fd, tgts, local, stream, lib):
@@ -1107,7 +1128,8 @@ def run_deep(args, rank, world, local):
                    "parallelism": f"{world} independent replicas" if world > 1 else "1 GPU"},
         "training": leg["training"], "accuracy": leg["accuracy"], "roofline": leg["roofline"],
         "far_gemm_roofline": leg["far_gemm_roofline"], "kernels": leg["kernels"], "gpu_launches": leg["gpu_launches"],
-        "plain_path": leg["plain_path"], "clocks": clk, "e2e": None, "cpu_baseline": None,
+        "plain_path": leg["plain_path"], "graph_replay": leg["graph_replay"], "clocks": clk, "e2e": None,
+        "cpu_baseline": None,
     }
     print(json.dumps(line), flush=True)
 
