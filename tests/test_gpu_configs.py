@@ -93,6 +93,10 @@ def test_cfg5_learned_far_field():
     assert rep["candidates"] == 992
     assert q["npairs_learned"] + q["npairs_far"] == 992
     assert q["npairs_learned"] == rep["learned"] and rep["learned"] > 0, rep
+    # what the network adds to the linear skip: it lowers the validation error
+    # of at least 3 % of the pairs (measured: 47 of 992); the per-pair gate
+    # keeps it only there, so no pair ends worse than with the skip alone
+    assert rep["network_pairs"] >= 0.03 * rep["candidates"], rep
     for t, e in errs.items():
         assert max(e) <= TOL, ("cfg5", t, e)
 
