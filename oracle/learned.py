@@ -157,22 +157,31 @@ def leaky_grad(z):
     return np.where(z >= 0.0, 1.0, ALPHA)
 
 
-def mlp_forward(Ws, X):
+def mlp_forward(Ws, X, act16=False):
     """Ws: [W1 (d1 x d0), ..., W4]; X [B][d0].  Returns (z list, a list)
-    with a[0] = X and a[-1] the output."""
+    with a[0] = X and a[-1] the output.  act16: each hidden activation is
+    rounded to fp16 (the representation in which a tensor-core network
+    passes it to the next layer's product), so that the slope each node
+    takes (the sign of z) is decided on the same values as there; the
+    arithmetic stays FP64."""
     a = [np.asarray(X, dtype=np.float64)]
     z = []
     for i, Wl in enumerate(Ws):
         zi = a[-1] @ np.asarray(Wl, dtype=np.float64).T
         z.append(zi)
-        a.append(leaky(zi) if i < len(Ws) - 1 else zi)
+        if i < len(Ws) - 1:
+            ai = leaky(zi)
+            a.append(ai.astype(np.float16).astype(np.float64) if act16 else ai)
+        else:
+            a.append(zi)
     return z, a
 
 
-def mlp_loss_grad(Ws, X, Y):
-    """Loss (1/2B) sum |out - Y|^2 and its gradient with respect to each W."""
+def mlp_loss_grad(Ws, X, Y, act16=False):
+    """Loss (1/2B) sum |out - Y|^2 and its gradient with respect to each W
+    (act16 as for mlp_forward)."""
     B = X.shape[0]
-    z, a = mlp_forward(Ws, X)
+    z, a = mlp_forward(Ws, X, act16)
     r = a[-1] - np.asarray(Y, dtype=np.float64)
     loss = 0.5 * np.sum(r * r) / B
     grads = [None] * len(Ws)
