@@ -72,6 +72,10 @@ def parse():
     p.add_argument("--source-points", type=int, default=4,
                    help="deep workloads: source nodes per axis of the two-sided far factors (0: source side exact)")
     p.add_argument("--no-deep", action="store_true", help="skip the deep workloads' lines in the default run")
+    p.add_argument("--partition", choices=["replicas", "sources"], default="replicas",
+                   help="N > 1: independent replicas (weak scaling), or the source partition: each rank owns some "
+                        "source domains, and one reduce-scatter per step sums every target at its owner (strong "
+                        "scaling)")
     return p.parse_args()
 
 
@@ -1134,6 +1138,82 @@ def run_deep(args, rank, world, local):
     print(json.dumps(line), flush=True)
 
 
+def run_partitioned(args, rank, world, local):
+    """The source partition across ranks (Sec. IV: one process per domain):
+    rank r owns the source domains partition.owners gives it; a step is its
+    pushes, its rp_evaluate (every target's share from its sources) and one
+    reduce-scatter of the packed shares, after which each rank holds the
+    totals of its own targets.  The work of the whole workload is fixed as
+    ranks are added (strong scaling)."""
+    import torch
+    import torch.distributed as dist
+    from paper_2311_15429_gb300 import partition, rp
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.current_stream(dev)
+    w = get_workload(args.workload)
+    lag = lag_window(w)
+    W, K = args.warmup, args.steps
+    nd = len(w.domains)
+    sizes = [d.N for d in w.domains]
+    own = partition.owners(sizes, world)
+    mine = partition.owned_by(rank, own)
+    ncycle = 16
+    pre = lag + 1
+    depth = max(w.history, lag + 1)
+    gen = synth.DeviceSlices(w.sources, dev)
+    cyc = [gen.step(j - pre, w.dt) for j in range(pre + ncycle)]
+    ptr = lambda xs: rp.pointer_array([x if d in mine else 0 for d, x in enumerate(xs)])
+    pins = [(ptr(r), ptr(J)) for r, J in cyc]
+    if not mine:   # more ranks than domains: this rank only joins the exchange
+        lib = None
+    else:
+        lib = rp.RetardedPotentials(w.domains, w.c, w.dt, history_depth=depth, device=local, stream=stream,
+                                    owned_sources=mine)
+        pphi, pA = rp.pointer_array(lib.phi), rp.pointer_array(lib.A)
+        for i in range(pre):
+            rp.rp_push_all(lib.ctx, *pins[i])
+    zeros = [torch.zeros(4 * n, device=dev) for n in sizes]
+
+    def step(i):
+        if lib is not None:
+            rp.rp_push_all(lib.ctx, *pins[pre + i % ncycle])
+            rp.rp_evaluate(lib.ctx, pphi, pA)
+            fields = [torch.cat([lib.phi[d], lib.A[d]]) for d in range(nd)]
+        else:
+            fields = zeros
+        return partition.exchange(partition.pack(fields, sizes, own, world), world)
+
+    for i in range(W):
+        step(i)
+    torch.cuda.synchronize()
+    barrier(world)
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(K):
+        step(W + i)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    barrier(world)
+    ms = max_over_ranks(e0.elapsed_time(e1), world, dev)
+    if lib is not None:
+        lib.close()
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": w.points * K / (ms / 1e3), "unit": UNIT, "n_gpus": world, "steps": K,
+            "warmup": W, "ms_per_step": ms / K, "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+            "dtype": "f32", "data": "synthetic",
+            "config": {"workload": w.name, "description": w.description, "points_per_step": w.points,
+                       "parallelism": f"source partition over {world} GPUs (owners {own}), one NCCL reduce-scatter "
+                                      f"of the packed per-target shares per step",
+                       "exchange_bytes_per_rank_per_step": 4 * world * partition.chunk_floats(sizes, own, world)},
+            "clocks": clk, "e2e": None, "cpu_baseline": None}
+    print(json.dumps(line), flush=True)
+
+
 SPLIT_SWEEP = [(8, 32, 24), (8, 32, 48), (8, 32, 96), (8, 96, 24), (8, 96, 48), (8, 96, 96),
                (16, 96, 48), (16, 96, 96)]   # (W', L', d') in nodes, h = 0.25 bohr
 
@@ -1320,6 +1400,8 @@ def main():
         run_split(args, rank, world, local)
     elif args.workload == "spill":
         run_spill(args, rank, world, local)
+    elif args.partition == "sources" and world > 1:
+        run_partitioned(args, rank, world, local)
     elif args.workload in DEEP:
         run_deep(args, rank, world, local)
     else:
