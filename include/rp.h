@@ -143,6 +143,21 @@ typedef enum {
  * whose error grows like the square root of the entry count, with the
  * autotuned 8/12/16-warp variants. */
 #define RP_FLAG_PLAIN_SUM 0x80u
+/* Overlapped pushes: a push's kernels (ring writes, forward passes, far
+ * anterpolation and batch GEMMs) run on a stream of the library's own, so
+ * that step l+1's push overlaps step l's evaluation on the context stream
+ * (the push is latency-bound, the evaluation's spectral MAC bound by HBM).
+ * The rings get one slot more than the deepest lag, so that a push never
+ * overwrites a slot the previous step's evaluation still reads, and a push
+ * waits for the evaluation two steps back.  rp_evaluate waits for the push.
+ * The inputs of a push must be complete when its kernels start: rp_push_all_event
+ * names the event after which they are; rp_push_all_host uses its own copy;
+ * rp_push and rp_push_all wait for the context stream (and so overlap
+ * nothing).  Same kernels and sums: results are bit-identical to a context
+ * without the flag.  Not with RP_FLAG_GROUND_STATE_SPLIT,
+ * RP_FLAG_HISTORY_SPILL, the learned field (RP_FLAG_DEFER_FAR) or
+ * rp_graph_capture (RP_ERR_UNSUPPORTED). */
+#define RP_FLAG_OVERLAP_PUSH 0x100u
 
 typedef struct {
     double c;            /* speed of light, > 0 (137.036 in atomic units) */
@@ -302,6 +317,17 @@ rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J);
  * of a round (no domain pushed yet in it).
  */
 rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J);
+
+/*
+ * rp_push_all_event -- rp_push_all for a context with RP_FLAG_OVERLAP_PUSH
+ * whose inputs are complete once `ready` (a cudaEvent_t the caller recorded
+ * after writing them; NULL: already complete when the call is made) has
+ * completed: the push's kernels wait for that event alone, not for the
+ * context stream, so they overlap the evaluation before them.  The buffers
+ * must stay unchanged until the next rp_evaluate has been enqueued and its
+ * stream has passed it (or rp_sync).  RP_ERR_STATE without the flag.
+ */
+rp_status rp_push_all_event(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J, void *ready);
 
 /*
  * rp_push_host -- rp_push from HOST buffers h_rho[N], h_J[3][N] (pinned

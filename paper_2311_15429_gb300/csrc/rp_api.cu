@@ -826,6 +826,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     ctx->split = (cfg->flags & RP_FLAG_GROUND_STATE_SPLIT) != 0;
     ctx->spill = (cfg->flags & RP_FLAG_HISTORY_SPILL) != 0;
     ctx->comp = (cfg->flags & RP_FLAG_PLAIN_SUM) == 0;
+    ctx->overlap = (cfg->flags & RP_FLAG_OVERLAP_PUSH) != 0;
     // the split's histories are zero before the first push: the clamped reads
     // of steps before it read the zeroed slot of step 0
     ctx->clamp = (cfg->flags & RP_FLAG_GROUND_STATE_CLAMP) != 0 || ctx->split;
@@ -979,7 +980,9 @@ rp_status rp_finalize(rp_ctx *ctx)
                 host_depth = std::max(host_depth, p.lag_hi + 1);
                 continue;
             }
-            ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1);
+            // overlapped pushes: one slot more, so that push l + 1 writes none the
+            // evaluation of step l reads
+            ring_depth[it->second] = std::max(ring_depth[it->second], p.lag_hi + 1 + (ctx->overlap ? 1 : 0));
         }
     for (size_t r = 0; r < ring_keys.size(); ++r)
         if (!src_spilled[ring_keys[r].first]) ring_depth[r] = std::max(ring_depth[r], ctx->cfg.history_depth);
@@ -1133,7 +1136,7 @@ rp_status rp_finalize(rp_ctx *ctx)
             P.lag_lo = p.lag_lo;
             P.nlag = p.lag_hi - p.lag_lo + 1;
             max_nlag = std::max(max_nlag, P.nlag);
-            rdepth[s] = std::max(rdepth[s], p.lag_hi + 1);
+            rdepth[s] = std::max(rdepth[s], p.lag_hi + 1 + (ctx->overlap ? 1 : 0));
             ctx->dpairs.push_back(P);
         }
         D.p1 = (int)ctx->dpairs.size();
@@ -1148,7 +1151,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     // FP64 audit: every source keeps its raw slices as deep as its deepest pair reads
     if (ctx->cfg.flags & RP_FLAG_AUDIT)
         for (int t = 0; t < nd; ++t)
-            for (int s = 0; s < nd; ++s) rdepth[s] = std::max(rdepth[s], ctx->pairs[(size_t)t * nd + s].lag_hi + 1);
+            for (int s = 0; s < nd; ++s)
+                rdepth[s] = std::max(rdepth[s], ctx->pairs[(size_t)t * nd + s].lag_hi + 1 + (ctx->overlap ? 1 : 0));
     ctx->smem_dir = smem_direct(max_nlag);
     ctx->raw_block0.assign(nd + 1, 0);
     for (int d = 0; d < nd; ++d) {
@@ -1186,6 +1190,15 @@ rp_status rp_finalize(rp_ctx *ctx)
     // ---- device memory
     rp_status st = use_device(ctx);
     if (st) return st;
+    if (ctx->overlap) {
+        if (ctx->split || ctx->spill || (ctx->cfg.flags & RP_FLAG_DEFER_FAR))
+            return fail(ctx, RP_ERR_UNSUPPORTED, "RP_FLAG_OVERLAP_PUSH: not with the ground-state split, the history "
+                                                 "spill or the learned field");
+        RP_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->push_stream, cudaStreamNonBlocking));
+        RP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_pushed, cudaEventDisableTiming));
+        RP_CUDA(ctx, cudaEventCreateWithFlags(&ctx->ev_stream, cudaEventDisableTiming));
+        for (cudaEvent_t &e : ctx->ev_eval) RP_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    }
     int max_optin = 0;
     RP_CUDA(ctx, cudaDeviceGetAttribute(&max_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     ctx->smem_optin = max_optin;
@@ -1563,6 +1576,29 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     return RP_OK;
 }
 
+// Overlapped pushes: the launches of a push on the push stream, after the
+// inputs' readiness (the caller's event; or, without one, everything the
+// context stream has been given) and after the evaluation two steps back
+// (whose ring slots this push's slot may otherwise reach); "pushed" is
+// recorded after them for the next evaluation.
+rp_status overlapped_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in, cudaEvent_t ready, bool have_ready)
+{
+    if (have_ready) {
+        if (ready) RP_CUDA(ctx, cudaStreamWaitEvent(ctx->push_stream, ready, 0));
+    } else {
+        RP_CUDA(ctx, cudaEventRecord(ctx->ev_stream, ctx->stream));
+        RP_CUDA(ctx, cudaStreamWaitEvent(ctx->push_stream, ctx->ev_stream, 0));
+    }
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->push_stream, ctx->ev_eval[ctx->step & 1], 0));
+    cudaStream_t user = ctx->stream;
+    ctx->stream = ctx->push_stream;
+    const rp_status st = enqueue_push(ctx, d0, d1, in);
+    ctx->stream = user;
+    if (st) return st;
+    RP_CUDA(ctx, cudaEventRecord(ctx->ev_pushed, ctx->push_stream));
+    return RP_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1629,13 +1665,30 @@ rp_status rp_push(rp_ctx *ctx, int id, const float *d_rho, const float *d_J)
     IoPtrs in{};
     in.rho[id] = d_rho;
     in.J[id] = d_J;
+    if (ctx->overlap) return overlapped_push(ctx, id, id + 1, in, nullptr, false);
     if ((st = split_inputs(ctx, id, id + 1, in))) return st;
     if ((st = enqueue_push(ctx, id, id + 1, in))) return st;
     if ((st = spill_round_done(ctx))) return st;
     return split_round_done(ctx);
 }
 
+static rp_status push_all_impl(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J, cudaEvent_t ready,
+                               bool have_ready);
+
 rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J)
+{
+    return push_all_impl(ctx, d_rho, d_J, nullptr, false);
+}
+
+rp_status rp_push_all_event(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J, void *ready)
+{
+    if (!ctx) return RP_ERR_ARG;
+    if (!ctx->overlap) return fail(ctx, RP_ERR_STATE, "rp_push_all_event needs RP_FLAG_OVERLAP_PUSH");
+    return push_all_impl(ctx, d_rho, d_J, static_cast<cudaEvent_t>(ready), true);
+}
+
+static rp_status push_all_impl(rp_ctx *ctx, const float *const *d_rho, const float *const *d_J, cudaEvent_t ready,
+                               bool have_ready)
 {
     rp_status st = check_ready(ctx);
     if (st) return st;
@@ -1653,6 +1706,7 @@ rp_status rp_push_all(rp_ctx *ctx, const float *const *d_rho, const float *const
     IoPtrs in{};
     for (int d = 0; d < nd; ++d)
         if (ctx->owned[d]) { in.rho[d] = d_rho[d]; in.J[d] = d_J[d]; }
+    if (ctx->overlap) return overlapped_push(ctx, 0, nd, in, ready, have_ready);
     rp_status st2;
     if ((st2 = split_inputs(ctx, 0, nd, in))) return st2;
     if ((st2 = enqueue_push(ctx, 0, nd, in))) return st2;
@@ -1714,8 +1768,17 @@ rp_status rp_push_host(rp_ctx *ctx, int id, const float *h_rho, const float *h_J
     RP_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_in, ctx->in_free[b], 0));
     if ((st = stage_host_input(ctx, id, b, h_rho, h_J))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
     float *dst = ctx->in_stage[b][id];
+    if (ctx->overlap) {   // the push's kernels wait for this copy alone
+        if ((st = begin_push(ctx, id))) return st;
+        IoPtrs in{};
+        in.rho[id] = dst;
+        in.J[id] = dst + ctx->doms[id].N;
+        if ((st = overlapped_push(ctx, id, id + 1, in, ctx->in_ready, true))) return st;
+        RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->push_stream));
+        return RP_OK;
+    }
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
     if ((st = rp_push(ctx, id, dst, dst + ctx->doms[id].N))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->stream));
     return RP_OK;
@@ -1737,17 +1800,25 @@ rp_status rp_push_all_host(rp_ctx *ctx, const float *const *h_rho, const float *
     for (int d = 0; d < nd; ++d)
         if (ctx->owned[d] && (st = stage_host_input(ctx, d, b, h_rho[d], h_J[d]))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_ready, ctx->copy_in));
-    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
     std::vector<const float *> rho(nd, nullptr), J(nd, nullptr);
     for (int d = 0; d < nd; ++d) {
         if (!ctx->owned[d]) continue;
         rho[d] = ctx->in_stage[b][d];
         J[d] = ctx->in_stage[b][d] + ctx->doms[d].N;
     }
+    if (ctx->overlap) {   // the push's kernels wait for these copies alone
+        if ((st = push_all_impl(ctx, rho.data(), J.data(), ctx->in_ready, true))) return st;
+        RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->push_stream));
+        return RP_OK;
+    }
+    RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->in_ready, 0));
     if ((st = rp_push_all(ctx, rho.data(), J.data()))) return st;
     RP_CUDA(ctx, cudaEventRecord(ctx->in_free[b], ctx->stream));
     return RP_OK;
 }
+
+static rp_status evaluate_launches(rp_ctx *ctx, const OutPtrs &out, long long step, long long kstep, int clamp,
+                                   float inv_c);
 
 rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
 {
@@ -1767,7 +1838,18 @@ rp_status rp_evaluate(rp_ctx *ctx, float *const *d_phi, float *const *d_A)
     const long long kstep = ctx->capturing ? -1 : step;   // graph capture: kernels read the device counter
     const int clamp = ctx->clamp ? 1 : 0;
     const float inv_c = (float)(1.0 / ctx->cfg.c);
+    if (ctx->overlap) RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_pushed, 0));   // the step's push
     if ((st = spill_fetch(ctx))) return st;
+    if ((st = evaluate_launches(ctx, out, step, kstep, clamp, inv_c))) return st;
+    // the push of step + 2 may reuse the ring slots this evaluation reads
+    if (ctx->overlap) RP_CUDA(ctx, cudaEventRecord(ctx->ev_eval[step & 1], ctx->stream));
+    return RP_OK;
+}
+
+static rp_status evaluate_launches(rp_ctx *ctx, const OutPtrs &out, long long step, long long kstep, int clamp,
+                                   float inv_c)
+{
+    rp_status st;
     for (const LaunchGroup &g : ctx->inv_groups) {
         const int ntiles = g.blk1 - g.blk0;
         if ((st = timed_launch(ctx, RP_K_MAC_INV_COLUMN, "MAC + inverse column pass", [&] {
@@ -2240,7 +2322,7 @@ rp_status rp_graph_capture(rp_ctx *ctx, const float *const *d_rho, const float *
         if (!d_rho[d] || !d_J[d] || !d_phi[d] || !d_A[d]) return fail(ctx, RP_ERR_ARG, "rp_graph_capture: NULL buffer");
     // the one-sided factors' launches and the learned field's change from step
     // to step; the two-sided factors' kernels read the step on the device
-    if (ctx->profile || ctx->split || !ctx->far_src.empty() || (!ctx->far_tgt.empty() && !ctx->far2) ||
+    if (ctx->profile || ctx->split || ctx->overlap || !ctx->far_src.empty() || (!ctx->far_tgt.empty() && !ctx->far2) ||
         !ctx->lpairs.empty() || (ctx->cfg.flags & RP_FLAG_DEFER_FAR) || !ctx->spill_srcs.empty())
         return fail(ctx, RP_ERR_UNSUPPORTED,
                     "rp_graph_capture: FFT, direct and two-sided far pairs only, without profiling, split or history "
@@ -2321,6 +2403,7 @@ rp_status rp_sync(rp_ctx *ctx)
     rp_status st = use_device(ctx);
     if (st) return st;
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->push_stream) RP_CUDA(ctx, cudaStreamSynchronize(ctx->push_stream));
     if (ctx->copy_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_in));
     if (ctx->copy_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->copy_out));
     if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
@@ -2490,6 +2573,7 @@ rp_status rp_save_state(rp_ctx *ctx, const char *path)
     if (!path) return fail(ctx, RP_ERR_ARG, "NULL path");
     if (!ctx->lpairs.empty()) return fail(ctx, RP_ERR_UNSUPPORTED, "a context with learned pairs has no saved state");
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->push_stream) RP_CUDA(ctx, cudaStreamSynchronize(ctx->push_stream));
     if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
     if (ctx->spill_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_in));
     FILE *f = std::fopen(path, "wb");
@@ -2535,6 +2619,7 @@ rp_status rp_load_state(rp_ctx *ctx, const char *path)
         return fail(ctx, RP_ERR_STATE, "state file does not match this context");
     }
     RP_CUDA(ctx, cudaStreamSynchronize(ctx->stream));
+    if (ctx->push_stream) RP_CUDA(ctx, cudaStreamSynchronize(ctx->push_stream));
     if (ctx->spill_out) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_out));
     if (ctx->spill_in) RP_CUDA(ctx, cudaStreamSynchronize(ctx->spill_in));
     std::vector<char> buf;
@@ -2562,6 +2647,12 @@ void rp_destroy(rp_ctx *ctx)
         cudaGetDevice(&cur);
         cudaSetDevice(ctx->device);
         cudaStreamSynchronize(ctx->stream);
+        if (ctx->push_stream) {
+            cudaStreamSynchronize(ctx->push_stream);
+            cudaStreamDestroy(ctx->push_stream);
+            for (cudaEvent_t e : {ctx->ev_pushed, ctx->ev_stream, ctx->ev_eval[0], ctx->ev_eval[1]})
+                if (e) cudaEventDestroy(e);
+        }
         if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
         if (ctx->graph) cudaGraphDestroy(ctx->graph);
         if (ctx->h_step_pin) cudaFreeHost(ctx->h_step_pin);

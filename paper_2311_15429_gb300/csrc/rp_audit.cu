@@ -145,6 +145,7 @@ rp_status audit_run(rp_ctx *ctx, const std::vector<AuditPt> &pts, const float *c
     const int npts = (int)pts.size();
     rp_status st = audit_scratch(ctx, npts);
     if (st) return st;
+    if (ctx->overlap) RP_CUDA(ctx, cudaStreamWaitEvent(ctx->stream, ctx->ev_pushed, 0));   // the rings' last push
     // the sources this context owns (all of them but under a source partition)
     std::vector<AuditSrc> hs;
     std::vector<AuditTgt> ht(nd);

@@ -91,6 +91,13 @@ struct rp_ctx {
     cudaStream_t stream = nullptr;
     bool plan_only = false, clamp = false, profile = false;
     bool comp = true;    // Kahan-compensated spectral sums (off under RP_FLAG_PLAIN_SUM)
+    // overlapped pushes (RP_FLAG_OVERLAP_PUSH): the push stream, "the last
+    // push round is done" on it, and "the evaluation of step s is done" on the
+    // context stream by parity of s (the push of step s + 2 waits for it)
+    bool overlap = false;
+    cudaStream_t push_stream = nullptr;
+    cudaEvent_t ev_pushed = nullptr, ev_stream = nullptr;
+    cudaEvent_t ev_eval[2] = {nullptr, nullptr};
     // ground-state split (RP_FLAG_GROUND_STATE_SPLIT): S(0), Delta S scratch
     // and the static potential P(0), [4][N] per domain
     bool split = false, static_done = false, computing_static = false;

@@ -22,6 +22,7 @@ RP_FLAG_GROUND_STATE_SPLIT = 0x10
 RP_FLAG_HISTORY_SPILL = 0x20
 RP_FLAG_AUDIT = 0x40
 RP_FLAG_PLAIN_SUM = 0x80
+RP_FLAG_OVERLAP_PUSH = 0x100
 RP_PAIR_FFT, RP_PAIR_DIRECT, RP_PAIR_LOWRANK, RP_PAIR_LEARNED, RP_PAIR_OTHER = 0, 1, 2, 3, 4
 (RP_K_RING_PUSH, RP_K_FWD_PLANE, RP_K_FWD_COLUMN, RP_K_MAC_INV_COLUMN, RP_K_INV_PLANE,
  RP_K_DIRECT, RP_K_FAR_CONVERT, RP_K_FAR_GEMM, RP_K_FAR_SCATTER, RP_K_FAR_ANTERP, RP_K_MOMENTS, RP_K_LEARNED,
@@ -92,6 +93,7 @@ SIGNATURES = {
     "rp_push_all": (_I, [_V, _PP, _PP]),
     "rp_push_host": (_I, [_V, _I, _V, _V]),
     "rp_push_all_host": (_I, [_V, _PP, _PP]),
+    "rp_push_all_event": (_I, [_V, _PP, _PP, _V]),
     "rp_evaluate": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host": (_I, [_V, _PP, _PP]),
     "rp_evaluate_host_noalloc": (_I, [_V, _PP, _PP]),
@@ -249,6 +251,16 @@ def rp_push_all(ctx, rhos: Sequence, Js: Sequence):
     pr, _a = _ptr_array(rhos)
     pj, _b = _ptr_array(Js)
     _check(load().rp_push_all(ctx, pr, pj), ctx)
+
+
+def rp_push_all_event(ctx, rhos: Sequence, Js: Sequence, ready=None):
+    """rp_push_all under RP_FLAG_OVERLAP_PUSH whose inputs are complete after
+    `ready` (a torch.cuda.Event, a raw cudaEvent_t, or None: already complete)."""
+    pr, _a = _ptr_array(rhos)
+    pj, _b = _ptr_array(Js)
+    if ready is not None and hasattr(ready, "cuda_event"):
+        ready = ready.cuda_event
+    _check(load().rp_push_all_event(ctx, pr, pj, ready or 0), ctx)
 
 
 def rp_push_host(ctx, dom: int, rho, J):

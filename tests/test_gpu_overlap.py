@@ -1,0 +1,80 @@
+"""Overlapped pushes (RP_FLAG_OVERLAP_PUSH): step l+1's push runs on the
+library's push stream while step l's evaluation runs on the context stream.
+The rings hold one slot more, so the results must be those of a context
+without the flag, bit for bit, over runs longer than the rings (every slot
+reused several times), for FFT, direct and two-sided far pairs, and through
+the host-buffer calls."""
+import numpy as np
+import pytest
+import torch
+
+from paper_2311_15429_gb300 import rp, synth
+
+pytestmark = pytest.mark.gpu
+
+
+def _run(doms, hists, flags, steps_from, event=False, host=False, **kw):
+    dev = torch.device("cuda", 0)
+    T = hists[0].shape[0]
+    out = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=flags, **kw) as lib:
+        if host:
+            hin = [torch.from_numpy(np.ascontiguousarray(h)).pin_memory() for h in hists]
+            hout = [torch.zeros(4 * d.N).pin_memory() for d in doms]
+        else:
+            slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+        for i in range(T):
+            if host:
+                rp.rp_push_all_host(lib.ctx, [x[i, 0] for x in hin], [x[i, 1:].reshape(-1) for x in hin])
+            elif event:
+                rp.rp_push_all_event(lib.ctx, [s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+            else:
+                lib.push_all([s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+            if i >= steps_from:
+                if host:
+                    rp.rp_evaluate_host(lib.ctx, [x[:d.N] for x, d in zip(hout, doms)],
+                                        [x[d.N:] for x, d in zip(hout, doms)])
+                    rp.rp_sync(lib.ctx)
+                    out[i] = [x.numpy().copy() for x in hout]
+                else:
+                    lib.evaluate()
+                    out[i] = [torch.cat([lib.phi[d], lib.A[d]]).cpu().numpy() for d in range(len(doms))]
+        lib.sync()
+        q = lib.query()
+    return out, q
+
+
+CASES = {
+    "fft": ([synth.cubic((0.0, 0.0, 0.0), 12, 0.25), synth.cubic((8.0, 0.5, -0.3), 12, 0.25)], {}, 40, 8),
+    "direct": ([synth.cubic((0.0, 0.0, 0.0), 12, 0.3), synth.cubic((9.0, 2.0, -1.0), 10, 0.25)], {}, 40, 8),
+    "far2": ([synth.cubic((0.0, 0.0, 0.0), 12, 0.25), synth.cubic((8.0, 0.5, -0.3), 12, 0.25),
+              synth.cubic((600.0, 50.0, -30.0), 12, 0.25)],
+             dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=32, far_source_points=4), 200, 100),
+}
+
+
+@pytest.mark.parametrize("case,event,host", [("fft", True, False), ("fft", False, False), ("direct", True, False),
+                                             ("far2", True, False), ("fft", False, True)])
+def test_overlapped_pushes_give_the_same_bits(case, event, host):
+    doms, kw, T, start = CASES[case]
+    hists = [s.history(0, T, 0.05) for s in synth.seeded_sources(doms)]
+    flags = rp.RP_FLAG_GROUND_STATE_CLAMP if case != "far2" else 0
+    want, q0 = _run(doms, hists, flags, start, **kw)
+    got, q1 = _run(doms, hists, flags | rp.RP_FLAG_OVERLAP_PUSH, start, event=event, host=host, **kw)
+    assert q1["spectral_depth"] == q0["spectral_depth"] + 1 or q1["raw_depth"] == q0["raw_depth"] + 1
+    for i in want:
+        for d in range(len(doms)):
+            np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"{case} step {i} domain {d}")
+
+
+def test_overlap_refusals():
+    doms = CASES["fft"][0]
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=rp.RP_FLAG_GROUND_STATE_CLAMP) as lib:
+        z = [torch.zeros(d.N, device="cuda") for d in doms], [torch.zeros(3 * d.N, device="cuda") for d in doms]
+        with pytest.raises(rp.RPError) as e:
+            rp.rp_push_all_event(lib.ctx, *z)
+        assert e.value.status == rp.RP_ERR_STATE
+    with pytest.raises(rp.RPError) as e:
+        rp.RetardedPotentials(doms, synth.C_AU, 0.05,
+                              flags=rp.RP_FLAG_OVERLAP_PUSH | rp.RP_FLAG_GROUND_STATE_SPLIT)
+    assert e.value.status == rp.RP_ERR_UNSUPPORTED
