@@ -189,7 +189,11 @@ typedef struct {
                           * an allocation that would pass it returns RP_ERR_OOM without calling the
                           * allocator (with RP_FLAG_PLAN_ONLY, rp_finalize compares the planned bytes).
                           * 0: no limit.  Not in the paper: a resource guard of the library. */
-    int reserved[4];     /* set to zero */
+    int mac_stages;      /* field-tile stages of the TMA-fed MAC's copy pipeline, 2 .. (as many as the
+                          * shared memory holds), or 0 for the most that fit; fewer stages leave
+                          * shared memory on each SM for other kernels' blocks (the overlapped push's
+                          * forward passes).  Timing only: results do not depend on it. */
+    int reserved[3];     /* set to zero */
 } rp_config;
 
 typedef struct rp_ctx rp_ctx;

@@ -157,7 +157,8 @@ rp_status plan_mac_tma(rp_ctx *ctx, int max_optin)
 {
     ctx->tma = false;
     for (int cls : {32, 48, 64, 96, 128, 192}) {
-        const int n = mac_tma_stages(cls, max_optin);
+        int n = mac_tma_stages(cls, max_optin);
+        if (ctx->cfg.mac_stages >= 2) n = std::min(n, ctx->cfg.mac_stages);
         ctx->mac_stages[class_slot(cls)] = n;
         if (n < 2) {
             for (const InvTarget &I : ctx->inv)
@@ -815,6 +816,7 @@ rp_status rp_create(const rp_config *cfg, int device, void *stream, rp_ctx **out
     if (cfg->mac_warps != 0 && cfg->mac_warps != 8 && cfg->mac_warps != 12 && cfg->mac_warps != 16) return RP_ERR_ARG;
     if (!(cfg->flags & RP_FLAG_PLAIN_SUM) && cfg->mac_warps != 0 && cfg->mac_warps != kCompWarps) return RP_ERR_ARG;
     if (cfg->profile_every < 0 || cfg->device_budget < 0) return RP_ERR_ARG;
+    if (cfg->mac_stages != 0 && cfg->mac_stages < 2) return RP_ERR_ARG;
     if (cfg->far_source_points != 0 && (cfg->far_source_points < 2 || cfg->far_source_points > kMaxFarPts))
         return RP_ERR_ARG;
     rp_ctx *ctx = new rp_ctx();

@@ -35,7 +35,7 @@ class rp_config(ctypes.Structure):
                 ("mode", ctypes.c_int), ("flags", ctypes.c_uint), ("far_points", ctypes.c_int),
                 ("far_distance", ctypes.c_double), ("far_batch", ctypes.c_int), ("mac_warps", ctypes.c_int),
                 ("profile_every", ctypes.c_int), ("far_source_points", ctypes.c_int),
-                ("device_budget", ctypes.c_longlong), ("reserved", ctypes.c_int * 4)]
+                ("device_budget", ctypes.c_longlong), ("mac_stages", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
 
 
 class rp_pair_info_t(ctypes.Structure):
@@ -206,11 +206,11 @@ def rp_last_error(ctx) -> str:
 def rp_create(c: float, dt: float, history_depth: int = 0, mode: int = RP_MODE_FFT,
               flags: int = 0, device: int = 0, stream=None, far_distance: float = 0.0,
               far_points: int = 0, far_batch: int = 0, mac_warps: int = 0, profile_every: int = 0,
-              far_source_points: int = 0, device_budget: int = 0):
+              far_source_points: int = 0, device_budget: int = 0, mac_stages: int = 0):
     """Returns the context handle.  ``stream``: a torch.cuda.Stream, a raw
     cudaStream_t int, or None for torch's current stream (NULL without torch)."""
     cfg = rp_config(c, dt, history_depth, mode, flags, far_points, far_distance, far_batch, mac_warps,
-                    profile_every, far_source_points, device_budget)
+                    profile_every, far_source_points, device_budget, mac_stages)
     if stream is None and not (flags & RP_FLAG_PLAN_ONLY):
         try:
             import torch
@@ -501,12 +501,12 @@ class RetardedPotentials:
                  mode: int = RP_MODE_FFT, flags: int = 0, device: int = 0, stream=None,
                  far_distance: float = 0.0, far_points: int = 0, far_batch: int = 0,
                  mac_warps: int = 0, profile_every: int = 0, far_source_points: int = 0,
-                 device_budget: int = 0, owned_sources: Optional[Sequence[int]] = None):
+                 device_budget: int = 0, owned_sources: Optional[Sequence[int]] = None, mac_stages: int = 0):
         import torch
         self.domains = list(domains)
         self.ctx = rp_create(c, dt, history_depth, mode, flags, device, stream, far_distance,
                              far_points, far_batch, mac_warps, profile_every, far_source_points,
-                             device_budget)
+                             device_budget, mac_stages)
         try:
             for d in self.domains:
                 rp_add_domain(self.ctx, d.origin, d.n, d.h)

@@ -191,7 +191,8 @@ def test_config_validation():
     bad = [dict(mac_warps=10), dict(mac_warps=-8), dict(mode=rp.RP_MODE_LOWRANK, far_distance=0.0),
            dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=12),
            dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_points=9), dict(profile_every=-1),
-           dict(far_source_points=1), dict(far_source_points=9), dict(device_budget=-1)]
+           dict(far_source_points=1), dict(far_source_points=9), dict(device_budget=-1),
+           dict(mac_stages=1), dict(mac_stages=-2)]
     for kw in bad:
         with pytest.raises(rp.RPError) as e:
             rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, **kw)
@@ -203,6 +204,8 @@ def test_config_validation():
     for cw in (8, 16):
         with pytest.raises(rp.RPError):
             rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_warps=cw)
+    for n in (0, 2, 3, 6):
+        rp.rp_destroy(rp.rp_create(137.0, 0.05, flags=rp.RP_FLAG_PLAN_ONLY, mac_stages=n))
 
 
 def test_ground_split_refuses_far_pairs():
