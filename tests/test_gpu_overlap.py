@@ -2,8 +2,8 @@
 library's push stream while step l's evaluation runs on the context stream.
 The rings hold one slot more, so the results must be those of a context
 without the flag, bit for bit, over runs longer than the rings (every slot
-reused several times), for FFT, direct and two-sided far pairs, and through
-the host-buffer calls."""
+reused several times), for FFT, direct and two-sided far pairs, through the
+host-buffer calls, under a source partition and across a save and load."""
 import numpy as np
 import pytest
 import torch
@@ -13,23 +13,29 @@ from paper_2311_15429_gb300 import rp, synth
 pytestmark = pytest.mark.gpu
 
 
-def _run(doms, hists, flags, steps_from, event=False, host=False, **kw):
+def _run(doms, hists, flags, steps_from, event=False, host=False, owned=None, **kw):
     dev = torch.device("cuda", 0)
     T = hists[0].shape[0]
     out = {}
+    if owned is not None:
+        kw["owned_sources"] = owned
+    own = set(range(len(doms)) if owned is None else owned)
     with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=flags, **kw) as lib:
         if host:
             hin = [torch.from_numpy(np.ascontiguousarray(h)).pin_memory() for h in hists]
             hout = [torch.zeros(4 * d.N).pin_memory() for d in doms]
         else:
-            slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+            slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) if d in own else None
+                       for d, h in enumerate(hists)] for i in range(T)]
+            pick = lambda sl, f: [None if x is None else f(x) for x in sl]
         for i in range(T):
             if host:
                 rp.rp_push_all_host(lib.ctx, [x[i, 0] for x in hin], [x[i, 1:].reshape(-1) for x in hin])
             elif event:
-                rp.rp_push_all_event(lib.ctx, [s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+                rp.rp_push_all_event(lib.ctx, pick(slices[i], lambda x: x[0]),
+                                     pick(slices[i], lambda x: x[1:].reshape(-1)))
             else:
-                lib.push_all([s[0] for s in slices[i]], [s[1:].reshape(-1) for s in slices[i]])
+                lib.push_all(pick(slices[i], lambda x: x[0]), pick(slices[i], lambda x: x[1:].reshape(-1)))
             if i >= steps_from:
                 if host:
                     rp.rp_evaluate_host(lib.ctx, [x[:d.N] for x, d in zip(hout, doms)],
@@ -65,6 +71,51 @@ def test_overlapped_pushes_give_the_same_bits(case, event, host):
     for i in want:
         for d in range(len(doms)):
             np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"{case} step {i} domain {d}")
+
+
+@pytest.mark.parametrize("owned", [[2], [0, 1]])
+def test_overlapped_pushes_under_a_source_partition(owned):
+    """A context that owns some sources (its partial fields of every target):
+    the same bits with and without the flag, two-sided far pairs included."""
+    doms, kw, T, start = CASES["far2"]
+    hists = [s.history(0, T, 0.05) for s in synth.seeded_sources(doms)]
+    want, _ = _run(doms, hists, 0, start, owned=owned, **kw)
+    got, _ = _run(doms, hists, rp.RP_FLAG_OVERLAP_PUSH, start, event=True, owned=owned, **kw)
+    for i in want:
+        for d in range(len(doms)):
+            np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"owned {owned} step {i} domain {d}")
+
+
+def test_overlapped_context_save_and_load(tmp_path):
+    """rp_save_state in the middle of overlapped steps (the push stream still
+    busy) and rp_load_state into a fresh overlapped context: the steps after
+    it give the bits of the uninterrupted sequential run."""
+    doms, kw, T, start = CASES["fft"]
+    hists = [s.history(0, T, 0.05) for s in synth.seeded_sources(doms)]
+    flags = rp.RP_FLAG_GROUND_STATE_CLAMP
+    want, _ = _run(doms, hists, flags, start, **kw)
+    dev = torch.device("cuda", 0)
+    slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+    push = lambda lib, i: rp.rp_push_all_event(lib.ctx, [x[0] for x in slices[i]],
+                                                [x[1:].reshape(-1) for x in slices[i]])
+    cut = T // 2 + 3
+    path = str(tmp_path / "state.bin")
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=flags | rp.RP_FLAG_OVERLAP_PUSH, **kw) as lib:
+        for i in range(cut):
+            push(lib, i)
+            lib.evaluate()
+        rp.rp_save_state(lib.ctx, path)
+    got = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=flags | rp.RP_FLAG_OVERLAP_PUSH, **kw) as lib:
+        rp.rp_load_state(lib.ctx, path)
+        assert lib.query()["step"] == cut - 1
+        for i in range(cut, T):
+            push(lib, i)
+            lib.evaluate()
+            got[i] = [torch.cat([lib.phi[d], lib.A[d]]).cpu().numpy() for d in range(len(doms))]
+    for i in range(cut, T):
+        for d in range(len(doms)):
+            np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"step {i} domain {d}")
 
 
 def test_overlap_refusals():
