@@ -47,18 +47,18 @@ inline cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, s
     return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
 }
 
-__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
-__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
-__device__ __forceinline__ float2 cmul(float2 a, float2 b)
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
 }
-__device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
-__device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
 
 // W_M^j (forward) or its conjugate (inverse) from a table of exp(-2 pi i j/M).
 template <bool INV>
-__device__ __forceinline__ float2 twid(const float2 *tw, int j)
+__host__ __device__ __forceinline__ float2 twid(const float2 *tw, int j)
 {
     float2 w = tw[j];
     if (INV) w.y = -w.y;
@@ -162,7 +162,7 @@ struct LaneTw {
 
 // radix 3: W = exp(-+2 pi i/3) = -1/2 -+ i sqrt3/2
 template <bool INV>
-__device__ __forceinline__ void dft3(float2 &a, float2 &b, float2 &c)
+__host__ __device__ __forceinline__ void dft3(float2 &a, float2 &b, float2 &c)
 {
     const float2 s = cadd(b, c), d = csub(b, c);
     const float2 m = make_float2(fmaf(-0.5f, s.x, a.x), fmaf(-0.5f, s.y, a.y));
@@ -174,7 +174,7 @@ __device__ __forceinline__ void dft3(float2 &a, float2 &b, float2 &c)
 }
 
 template <int R, bool INV>
-__device__ __forceinline__ void small_dft_c(float2 (&v)[R])
+__host__ __device__ __forceinline__ void small_dft_c(float2 (&v)[R])
 {
     if constexpr (R == 2) {
         const float2 a = v[0], b = v[1];
@@ -229,6 +229,196 @@ __device__ __forceinline__ void line_fft_c(float2 (&v)[LaneTw<M, INV>::R], const
             v[k] = (i == LOGL - 1) ? u : cmul(u, t.s[i]);   // last stage: w = 1
         }
     }
+}
+
+// ---------------------------------------------------------------- tile transform, M = 16 B
+//
+// The 16 columns of a shared-memory tile T[p * 16 + c] (row p < M, column
+// c < 16, one float2 each: rows of 128 bytes) transformed in place by one
+// warp.  With n = B n1 + n2 and k = k1 + 16 k2 (n1, k1 < 16; n2, k2 < B),
+//
+//   X[k1 + 16 k2] = sum_{n2} W_B^{n2 k2} [ W_M^{n2 k1} sum_{n1} x[B n1 + n2] W_16^{n1 k1} ].
+//
+// Stage 1, task (c, n2): the 16-point DFT of rows B n1 + n2 of column c, times
+// W_M^{n2 k1}, written back to the rows it read (row B k1 + n2 for k1).
+// Stage 2, task (c, k1): the B-point DFT of rows B k1 .. B k1 + B - 1, written
+// back to the same rows.  Afterwards row tile_row<B>(k) = B (k mod 16) + k / 16
+// holds X[k].  The tasks of a stage touch disjoint rows, and every warp
+// access covers whole 128-byte rows, so the tile needs neither padding nor
+// synchronisation inside a stage.  HALF: rows n >= M/2 are zero (a
+// zero-padded input), and the first radix-4 layer skips them.
+
+template <int B>
+__host__ __device__ constexpr int tile_row(int k) { return B * (k & 15) + (k >> 4); }
+
+constexpr float kCos8 = 0.923879532511286756f;   // cos(pi/8)
+constexpr float kSin8 = 0.382683432365089772f;   // sin(pi/8)
+constexpr float kRt2 = 0.707106781186547524f;    // 1/sqrt(2)
+
+// times -i (forward) or +i (inverse)
+template <bool INV>
+__host__ __device__ __forceinline__ float2 mul_mi(float2 a)
+{
+    return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+// W_16^m (forward: exp(-2 pi i m/16); inverse: its conjugate), m in {1, 2, 3, 6, 9}
+template <int m, bool INV>
+__host__ __device__ __forceinline__ float2 w16()
+{
+    const float s = INV ? -1.0f : 1.0f;
+    if constexpr (m == 1) return make_float2(kCos8, -s * kSin8);
+    else if constexpr (m == 2) return make_float2(kRt2, -s * kRt2);
+    else if constexpr (m == 3) return make_float2(kSin8, -s * kCos8);
+    else if constexpr (m == 6) return make_float2(-kRt2, -s * kRt2);
+    else return make_float2(-kCos8, s * kSin8);   // m == 9
+}
+
+// radix 4 in natural order; HALF: v2 = v3 = 0
+template <bool INV, bool HALF = false>
+__host__ __device__ __forceinline__ void r4(float2 &v0, float2 &v1, float2 &v2, float2 &v3)
+{
+    if constexpr (HALF) {
+        const float2 a = v0, jb = mul_mi<INV>(v1);
+        v2 = csub(a, v1);
+        v0 = cadd(a, v1);
+        v1 = cadd(a, jb);
+        v3 = csub(a, jb);
+    } else {
+        const float2 a0 = cadd(v0, v2), a1 = csub(v0, v2);
+        const float2 b0 = cadd(v1, v3), jb1 = mul_mi<INV>(csub(v1, v3));
+        v0 = cadd(a0, b0);
+        v2 = csub(a0, b0);
+        v1 = cadd(a1, jb1);
+        v3 = csub(a1, jb1);
+    }
+}
+
+// 16-point DFT in natural order (n = 4a + b, k = c + 4d: radix 4 over a,
+// twiddle W_16^{bc}, radix 4 over b); HALF: x[8..15] = 0.
+template <bool INV, bool HALF>
+__host__ __device__ __forceinline__ void dft16(float2 (&x)[16])
+{
+#pragma unroll
+    for (int b = 0; b < 4; ++b) r4<INV, HALF>(x[b], x[4 + b], x[8 + b], x[12 + b]);
+    // x[4c + b] = U_b[c]
+    x[5] = cmul(x[5], w16<1, INV>());
+    x[6] = cmul(x[6], w16<2, INV>());
+    x[7] = cmul(x[7], w16<3, INV>());
+    x[9] = cmul(x[9], w16<2, INV>());
+    x[10] = mul_mi<INV>(x[10]);
+    x[11] = cmul(x[11], w16<6, INV>());
+    x[13] = cmul(x[13], w16<3, INV>());
+    x[14] = cmul(x[14], w16<6, INV>());
+    x[15] = cmul(x[15], w16<9, INV>());
+#pragma unroll
+    for (int c = 0; c < 4; ++c) r4<INV>(x[4 * c], x[4 * c + 1], x[4 * c + 2], x[4 * c + 3]);
+    // x[4c + d] = Y[c + 4d]
+    float2 y[16];
+#pragma unroll
+    for (int c = 0; c < 4; ++c)
+#pragma unroll
+        for (int d = 0; d < 4; ++d) y[c + 4 * d] = x[4 * c + d];
+#pragma unroll
+    for (int k = 0; k < 16; ++k) x[k] = y[k];
+}
+
+// 8-point DFT in natural order (n = 2p + q, k = k1 + 4 k2)
+template <bool INV>
+__host__ __device__ __forceinline__ void dft8(float2 (&x)[8])
+{
+    r4<INV>(x[0], x[2], x[4], x[6]);
+    r4<INV>(x[1], x[3], x[5], x[7]);
+    // x[2 k1 + q] = U_q[k1]; times W_8^{q k1}
+    const float s = INV ? -1.0f : 1.0f;
+    x[3] = cmul(x[3], make_float2(kRt2, -s * kRt2));
+    x[5] = mul_mi<INV>(x[5]);
+    x[7] = cmul(x[7], make_float2(-kRt2, -s * kRt2));
+    float2 y[8];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) {
+        y[k1] = cadd(x[2 * k1], x[2 * k1 + 1]);
+        y[k1 + 4] = csub(x[2 * k1], x[2 * k1 + 1]);
+    }
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = y[k];
+}
+
+// 12-point DFT in natural order (n = 3p + q, k = k1 + 4 k2)
+template <bool INV>
+__host__ __device__ __forceinline__ void dft12(float2 (&x)[12])
+{
+#pragma unroll
+    for (int q = 0; q < 3; ++q) r4<INV>(x[q], x[3 + q], x[6 + q], x[9 + q]);
+    // x[3 k1 + q] = U_q[k1]; times W_12^{q k1}
+    const float s = INV ? -1.0f : 1.0f;
+    x[4] = cmul(x[4], make_float2(kSin60, -s * 0.5f));    // W^1
+    x[5] = cmul(x[5], make_float2(0.5f, -s * kSin60));    // W^2
+    x[7] = cmul(x[7], make_float2(0.5f, -s * kSin60));    // W^2
+    x[8] = cmul(x[8], make_float2(-0.5f, -s * kSin60));   // W^4
+    x[10] = mul_mi<INV>(x[10]);                           // W^3
+    x[11] = make_float2(-x[11].x, -x[11].y);              // W^6
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1) dft3<INV>(x[3 * k1], x[3 * k1 + 1], x[3 * k1 + 2]);
+    float2 y[12];
+#pragma unroll
+    for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+        for (int k2 = 0; k2 < 3; ++k2) y[k1 + 4 * k2] = x[3 * k1 + k2];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) x[k] = y[k];
+}
+
+template <int B, bool INV>
+__host__ __device__ __forceinline__ void dft_b(float2 (&v)[B])
+{
+    if constexpr (B == 4) r4<INV>(v[0], v[1], v[2], v[3]);
+    else if constexpr (B == 8) dft8<INV>(v);
+    else if constexpr (B == 12) dft12<INV>(v);
+    else small_dft_c<B, INV>(v);
+}
+
+// Stage 1, task (c, n2): rows >= nin (and, with HALF, >= M/2) read as zero.
+template <int B, bool INV, bool HALF>
+__host__ __device__ __forceinline__ void tile_stage1(float2 *T, const float2 *tw, int nin, int c, int n2)
+{
+    float2 x[16];
+#pragma unroll
+    for (int n1 = 0; n1 < 16; ++n1) {
+        const int p = B * n1 + n2;
+        x[n1] = (n1 < (HALF ? 8 : 16) && p < nin) ? T[p * 16 + c] : make_float2(0.0f, 0.0f);
+    }
+    dft16<INV, HALF>(x);
+    T[n2 * 16 + c] = x[0];
+#pragma unroll
+    for (int k1 = 1; k1 < 16; ++k1) T[(B * k1 + n2) * 16 + c] = cmul(x[k1], twid<INV>(tw, n2 * k1));
+}
+
+// Stage 2, task (c, k1).
+template <int B, bool INV>
+__host__ __device__ __forceinline__ void tile_stage2(float2 *T, int c, int k1)
+{
+    float2 v[B];
+#pragma unroll
+    for (int n2 = 0; n2 < B; ++n2) v[n2] = T[(B * k1 + n2) * 16 + c];
+    dft_b<B, INV>(v);
+#pragma unroll
+    for (int k2 = 0; k2 < B; ++k2) T[(B * k1 + k2) * 16 + c] = v[k2];
+}
+
+// The whole tile by one warp (all 32 lanes call it): stage 1 in B/2 rounds
+// of 32 tasks, stage 2 in 8.  tw: exp(-2 pi i j/M), j < M.
+template <int B, bool INV, bool HALF>
+__device__ __forceinline__ void tile_fft16(float2 *T, const float2 *tw, int nin, int lane)
+{
+    static_assert(B % 2 == 0, "tile transform: B even");
+    const int c = lane & 15, hi = lane >> 4;
+#pragma unroll 1
+    for (int r = 0; r < B / 2; ++r) tile_stage1<B, INV, HALF>(T, tw, nin, c, 2 * r + hi);
+    __syncwarp();
+#pragma unroll 1
+    for (int r = 0; r < 8; ++r) tile_stage2<B, INV>(T, c, 2 * r + hi);
+    __syncwarp();
 }
 
 // Runtime dispatch on R for a functor templated on R:  f.template run<R>().

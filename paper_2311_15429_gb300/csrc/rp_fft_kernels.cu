@@ -70,6 +70,15 @@ __device__ __forceinline__ int owner_of(const T *arr, int lo, int hi, int b, int
 
 __device__ __forceinline__ float4 ldg4(const float2 *p) { return __ldg(reinterpret_cast<const float4 *>(p)); }
 
+// 16-byte asynchronous global -> shared copy (both addresses 16-byte aligned)
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"((unsigned)__cvta_generic_to_shared(smem)),
+                 "l"(gmem)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 // ---------------------------------------------------------------- raw ring push
 
 struct PushPrefix {
@@ -360,6 +369,68 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
             dst[f * ring_field + kz * kTileY + c] = c < ncols ? V[f * fs + kz * kTileYPad + c] : make_float2(0.f, 0.f);
         }
     }
+}
+
+// The forward column pass for M = 16 B, B even (M = 64, 96, 128, 192): the
+// tile [field][z][16] dense in shared memory, one warp per field with the
+// two-stage tile transform (rows z >= nz and >= M/2 are the zero padding and
+// are neither loaded nor transformed), then each spectral row copied from
+// its tile row to the ring slot.
+constexpr int kColumn16Threads = 128;
+
+__host__ __device__ constexpr bool tile16_class(int M) { return M == 64 || M == 96 || M == 128 || M == 192; }
+
+template <int M>
+__global__ void __launch_bounds__(kColumn16Threads) k_fwd_column16(const FwdRing *__restrict__ rings, int r0, int r1,
+                                                                    int block_lo, long long step)
+{
+    constexpr int B = M / 16, kx = M / 2 + 1, ntile = M / kTileY;
+    static_assert(tile16_class(M), "k_fwd_column16: M = 16 B, B even");
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const int b = blockIdx.x + block_lo;
+    const int r = owner_of(rings, r0, r1, b, &FwdRing::tile0);
+    const FwdRing &R = rings[r];
+    const int nz = R.nz;
+    const int local = b - R.tile0;
+    const int kxi = local / ntile, kyt = local % ntile;
+    float2 *tw = sm;
+    float2 *V = tw + M;   // [field][M rows][16]
+    load_twiddles(tw, R.tw_z, M);
+    pdl_trigger();
+    pdl_wait();   // t1 is written by the plane pass
+    if (step < 0) step = *R.d_step;   // graph replay: the step from the device counter
+    const int t = threadIdx.x, p = t & 7, zr = t >> 3;   // column pair p, rows zr + 16 j
+    {
+        // rows z < nz by asynchronous 16-byte copies, all in flight at once
+        const long long t1_field = (long long)kx * nz * M;
+        const float2 *src = R.t1 + (long long)kxi * nz * M + kyt * kTileY + 2 * p;
+#pragma unroll
+        for (int f = 0; f < 4; ++f)
+#pragma unroll
+            for (int j = 0; j < B; ++j) {
+                const int z = zr + 16 * j;
+                if (z < nz) cp_async16(V + (f * M + z) * kTileY + 2 * p, src + f * t1_field + (long long)z * M);
+            }
+        cp_async_wait_all();
+    }
+    __syncthreads();
+    const int lane = t & 31, warp = t >> 5;
+    // a source as large as the target's padded half (the usual case) skips the
+    // zero half in the first layer; a larger source of a cross pair does not
+    if (nz <= M / 2) tile_fft16<B, false, true>(V + warp * M * kTileY, tw, nz, lane);
+    else tile_fft16<B, false, false>(V + warp * M * kTileY, tw, nz, lane);
+    __syncthreads();
+    float2 *dst = R.ring + (long long)((step - R.lag_off) % R.depth) * R.slot_elems +
+                  (long long)(kxi * ntile + kyt) * 4 * M * kTileY;
+#pragma unroll
+    for (int f = 0; f < 4; ++f)
+#pragma unroll
+        for (int j = 0; j < B; ++j) {
+            const int kz = zr + 16 * j;   // tile_row<B>(kz) = B zr + j
+            *reinterpret_cast<float4 *>(dst + (f * M + kz) * kTileY + 2 * p) =
+                *reinterpret_cast<const float4 *>(V + (f * M + B * zr + j) * kTileY + 2 * p);
+        }
 }
 
 // Kahan-compensated addition (the total is s - c; see k_mac_tma).
@@ -795,6 +866,8 @@ size_t smem_fwd_plane(int ny, const Axis &ax)
 
 size_t smem_fwd_column(const Axis &az) { return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad); }
 
+static size_t smem_fwd_column16(int M) { return sizeof(float2) * ((size_t)M + 4 * (size_t)M * kTileY); }
+
 size_t smem_mac_inv_column(const Axis &az)
 {
     return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad);
@@ -831,6 +904,11 @@ cudaError_t open_kernel_smem_limits(int max_optin)
         return e;
     RP_FOR_EACH_CLASS(RP_OPEN)
 #undef RP_OPEN
+#define RP_OPEN16(M)                                                                                          \
+    if ((e = cudaFuncSetAttribute(k_fwd_column16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
+        return e;
+    RP_OPEN16(64) RP_OPEN16(96) RP_OPEN16(128) RP_OPEN16(192)
+#undef RP_OPEN16
     return cudaSuccess;
 }
 
@@ -861,12 +939,28 @@ cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, 
     return cudaGetLastError();
 }
 
+template <int M>
+static cudaError_t launch_fwd_column_cls(const FwdRing *d_rings, int r0, int r1, int block_lo, int nblocks,
+                                         size_t smem, long long step, cudaStream_t s)
+{
+    if constexpr (tile16_class(M))
+        return launch_pdl(k_fwd_column16<M>, dim3(nblocks), dim3(kColumn16Threads), smem_fwd_column16(M), s, d_rings,
+                          r0, r1, block_lo, step);
+    else
+        return launch_pdl(k_fwd_column<M>, dim3(nblocks), dim3(kColumnThreads), smem, s, d_rings, r0, r1, block_lo,
+                          step);
+}
+
 cudaError_t launch_fwd_column(int cls, const FwdRing *d_rings, int r0, int r1, int block_lo, int nblocks,
                               size_t smem, long long step, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_fwd_column, kColumnThreads, d_rings, r0, r1, block_lo, step)
+#define X(M)                                                                                        \
+    case M:                                                                                         \
+        if (cudaError_t e_ = launch_fwd_column_cls<M>(d_rings, r0, r1, block_lo, nblocks, smem, step, s)) \
+            return e_;                                                                              \
+        break;
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
