@@ -1028,7 +1028,7 @@ rp_status rp_finalize(rp_ctx *ctx)
         tw[m[0]]; tw[m[1]]; tw[m[2]];
         ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
         ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
-        ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(R.ny, R.ax));
+        ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(size_class(R.ax, R.ay, R.az), R.ny, R.ax));
         ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
         const int cls = ring_class(r);
         if (ctx->fwd_groups.empty() || ctx->fwd_groups.back().cls != cls)
@@ -1093,7 +1093,7 @@ rp_status rp_finalize(rp_ctx *ctx)
         ctx->mac_blocks += I.kx * ((tm[t][1] + kTileY - 1) / kTileY);
         ctx->invp_blocks += 4 * I.nz;
         ctx->smem_mac = std::max(ctx->smem_mac, smem_mac_inv_column(I.az));
-        ctx->smem_inv = std::max(ctx->smem_inv, smem_inv_plane(I.nx, I.ny, I.ax, I.ay));
+        ctx->smem_inv = std::max(ctx->smem_inv, smem_inv_plane(size_class(I.ax, I.ay, I.az), I.nx, I.ny, I.ax, I.ay));
         const int cls = tgt_class(t);
         const int i = (int)ctx->inv.size();
         if (ctx->inv_groups.empty() || ctx->inv_groups.back().cls != cls)

@@ -378,32 +378,39 @@ __host__ __device__ __forceinline__ void dft_b(float2 (&v)[B])
     else small_dft_c<B, INV>(v);
 }
 
+// Element (row p, line c) of a tile sits at T[p * SP + c * SC]: SP = 16 (or
+// more), SC = 1 for lines down the columns (rows of 16 consecutive lines), or
+// SP = 1 and SC odd for lines along the rows.  A half warp always serves the
+// 16 lines of one row, so both forms are free of bank conflicts.
+//
 // Stage 1, task (c, n2): rows >= nin (and, with HALF, >= M/2) read as zero.
-template <int B, bool INV, bool HALF>
+template <int B, bool INV, bool HALF, int SP = 16, int SC = 1>
 __host__ __device__ __forceinline__ void tile_stage1(float2 *T, const float2 *tw, int nin, int c, int n2)
 {
+    float2 *L = T + c * SC;
     float2 x[16];
 #pragma unroll
     for (int n1 = 0; n1 < 16; ++n1) {
         const int p = B * n1 + n2;
-        x[n1] = (n1 < (HALF ? 8 : 16) && p < nin) ? T[p * 16 + c] : make_float2(0.0f, 0.0f);
+        x[n1] = (n1 < (HALF ? 8 : 16) && p < nin) ? L[p * SP] : make_float2(0.0f, 0.0f);
     }
     dft16<INV, HALF>(x);
-    T[n2 * 16 + c] = x[0];
+    L[n2 * SP] = x[0];
 #pragma unroll
-    for (int k1 = 1; k1 < 16; ++k1) T[(B * k1 + n2) * 16 + c] = cmul(x[k1], twid<INV>(tw, n2 * k1));
+    for (int k1 = 1; k1 < 16; ++k1) L[(B * k1 + n2) * SP] = cmul(x[k1], twid<INV>(tw, n2 * k1));
 }
 
 // Stage 2, task (c, k1).
-template <int B, bool INV>
+template <int B, bool INV, int SP = 16, int SC = 1>
 __host__ __device__ __forceinline__ void tile_stage2(float2 *T, int c, int k1)
 {
+    float2 *L = T + c * SC + B * k1 * SP;
     float2 v[B];
 #pragma unroll
-    for (int n2 = 0; n2 < B; ++n2) v[n2] = T[(B * k1 + n2) * 16 + c];
+    for (int n2 = 0; n2 < B; ++n2) v[n2] = L[n2 * SP];
     dft_b<B, INV>(v);
 #pragma unroll
-    for (int k2 = 0; k2 < B; ++k2) T[(B * k1 + k2) * 16 + c] = v[k2];
+    for (int k2 = 0; k2 < B; ++k2) L[k2 * SP] = v[k2];
 }
 
 // The whole tile by one warp (all 32 lanes call it): stage 1 in B/2 rounds
@@ -419,6 +426,27 @@ __device__ __forceinline__ void tile_fft16(float2 *T, const float2 *tw, int nin,
 #pragma unroll 1
     for (int r = 0; r < 8; ++r) tile_stage2<B, INV>(T, c, 2 * r + hi);
     __syncwarp();
+}
+
+// ntiles tiles (tile i at T + i * tile_stride) by the whole block, the tasks
+// of each stage spread over its threads (16 consecutive threads take the 16
+// lines of one row); ends with the block synchronised.
+template <int B, bool INV, bool HALF, int SP, int SC>
+__device__ __forceinline__ void tiles_fft_block(float2 *T, int tile_stride, int ntiles, const float2 *tw, int nin)
+{
+    const int n1 = ntiles * 16 * B;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < n1; i += blockDim.x) {
+        const int c = i & 15, rest = i >> 4;
+        const int tile = rest / B, n2 = rest - tile * B;
+        tile_stage1<B, INV, HALF, SP, SC>(T + tile * tile_stride, tw, nin, c, n2);
+    }
+    __syncthreads();
+    const int n2t = ntiles * 256;
+#pragma unroll 1
+    for (int i = threadIdx.x; i < n2t; i += blockDim.x)
+        tile_stage2<B, INV, SP, SC>(T + (i >> 8) * tile_stride, i & 15, (i >> 4) & 15);
+    __syncthreads();
 }
 
 // Runtime dispatch on R for a functor templated on R:  f.template run<R>().

@@ -841,6 +841,235 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
     }
 }
 
+// ---------------------------------------------------------------- plane passes on tiles (M = 64, 96, 128)
+//
+// The plane passes on the two-stage tile transform.  Forward: the plane's
+// rows in pairs (row 2c the real part of line c, row 2c + 1 the imaginary
+// part) transformed along x as row lines, split into the two rows' spectra
+// (Z[k] +- conj Z[M-k]), then along y as column lines over kx.  The columns
+// kx = 0 and kx = M/2 of a real plane are real, so they travel as one
+// complex column (kx = 0 in the real part, M/2 in the imaginary part) and are
+// split after the y transform: the y pass is M/32 whole tiles.  Inverse: the
+// same steps in reverse order, the rows kx = 0 and M/2 packed as S_0 + i S_M/2
+// (their transforms along y are real up to rounding), and the C2R transform
+// along x as one complex transform per pair of output rows.
+constexpr int kPlane16Threads = 256;
+
+__host__ __device__ constexpr bool plane16_class(int M) { return M == 64 || M == 96 || M == 128; }
+__host__ __device__ constexpr int plane16_xtiles(int ny) { return ((ny + 1) / 2 + 15) / 16; }
+
+// 4-byte asynchronous global -> shared copy
+__device__ __forceinline__ void cp_async4(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+// 8-byte asynchronous global -> shared copy
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"((unsigned)__cvta_generic_to_shared(smem)), "l"(gmem)
+                 : "memory");
+}
+
+template <int M>
+__global__ void __launch_bounds__(kPlane16Threads, 3) k_fwd_plane16(const FwdRing *__restrict__ rings, IoPtrs in, int r0,
+                                                                 int r1, int block_lo, int far_slot)
+{
+    constexpr int B = M / 16, H = M / 2, SX = M + 1, SQ = H + 1;
+    static_assert(plane16_class(M), "k_fwd_plane16: M = 64, 96 or 128");
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const int b = blockIdx.x + block_lo;
+    const int r = owner_of(rings, r0, r1, b, &FwdRing::plane0);
+    const FwdRing &R = rings[r];
+    const int nx = R.nx, ny = R.ny, nz = R.nz;
+    const int local = b - R.plane0;
+    const int f = local / nz, z = local % nz;
+    const long long N = (long long)nx * ny * nz;
+    const int pairs = (ny + 1) >> 1, xt = (pairs + 15) >> 4;
+    float2 *twx = sm, *twy = sm + M;
+    float2 *X = twy + M;            // x pass: line c (rows 2c, 2c + 1) at X + c * SX
+    float2 *Q = X + xt * 16 * SX;   // y pass: [M rows y][SQ]; column 0 = kx 0 and H, column k = kx k
+    load_twiddles(twx, R.tw_x, M);
+    load_twiddles(twy, R.tw_y, M);
+    pdl_trigger();
+    pdl_wait();   // the input slice may come from the previous kernel; t1 was read by it
+    const float *src = f == 0 ? in.rho[R.src] : in.J[R.src] + (long long)(f - 1) * N;
+    const float *plane = src + (long long)z * nx * ny;
+    float *Xf = reinterpret_cast<float *>(X);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int y = warp; y < ny; y += nwarps)
+        for (int x = lane; x < nx; x += 32) cp_async4(Xf + 2 * ((y >> 1) * SX + x) + (y & 1), plane + y * nx + x);
+    if (ny & 1)
+        for (int x = threadIdx.x; x < nx; x += blockDim.x) Xf[2 * ((ny >> 1) * SX + x) + 1] = 0.0f;
+    cp_async_wait_all();
+    __syncthreads();
+    if (nx <= H) tiles_fft_block<B, false, true, 1, SX>(X, 16 * SX, xt, twx, nx);
+    else tiles_fft_block<B, false, false, 1, SX>(X, 16 * SX, xt, twx, nx);
+    // two real rows from one complex transform:
+    //   A[k] = (Z[k] + conj Z[M-k]) / 2,  B[k] = (Z[k] - conj Z[M-k]) / (2i)
+    for (int i = threadIdx.x; i < pairs * H; i += blockDim.x) {
+        const int c = i / H, k = i - c * H;
+        const float2 *L = X + c * SX;
+        const int ya = 2 * c, yb = ya + 1;
+        if (k == 0) {
+            const float2 z0 = L[tile_row<B>(0)], zh = L[tile_row<B>(H)];
+            Q[ya * SQ] = make_float2(z0.x, zh.x);
+            if (yb < ny) Q[yb * SQ] = make_float2(z0.y, zh.y);
+        } else {
+            const float2 zk = L[tile_row<B>(k)], zc = cconj(L[tile_row<B>(M - k)]);
+            const float2 D = csub(zk, zc);
+            Q[ya * SQ + k] = cscale(cadd(zk, zc), 0.5f);
+            if (yb < ny) Q[yb * SQ + k] = make_float2(0.5f * D.y, -0.5f * D.x);
+        }
+    }
+    __syncthreads();
+    if (ny <= H) tiles_fft_block<B, false, true, SQ, 1>(Q, 16, H / 16, twy, ny);
+    else tiles_fft_block<B, false, false, SQ, 1>(Q, 16, H / 16, twy, ny);
+    // rows kx of T1 (ky natural), kx = 0 and H split from the packed column
+    float2 *out = R.t1 + ((long long)f * (H + 1) * nz + z) * M;
+    const long long rs = (long long)nz * M;
+    for (int kxi = warp; kxi <= H; kxi += nwarps) {
+        float2 *row = out + kxi * rs;
+        if (kxi > 0 && kxi < H) {
+            for (int ky = 2 * lane; ky < M; ky += 64) {
+                const float2 a = Q[tile_row<B>(ky) * SQ + kxi], c = Q[tile_row<B>(ky + 1) * SQ + kxi];
+                *reinterpret_cast<float4 *>(row + ky) = make_float4(a.x, a.y, c.x, c.y);
+            }
+        } else {
+            for (int ky = lane; ky < M; ky += 32) {
+                const float2 zk = Q[tile_row<B>(ky) * SQ], zc = cconj(Q[tile_row<B>(ky == 0 ? 0 : M - ky) * SQ]);
+                const float2 D = csub(zk, zc);
+                row[ky] = kxi == 0 ? cscale(cadd(zk, zc), 0.5f) : make_float2(0.5f * D.y, -0.5f * D.x);
+            }
+        }
+    }
+    if (R.far_x) {
+        // far path: this plane as bf16 hi/lo into row (slot, field) of the batch matrix
+        __nv_bfloat16 *row = R.far_x + ((long long)far_slot * 4 + f) * 2 * R.far_ks + (long long)z * nx * ny;
+        for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+            const float v = __ldg(plane + i);
+            const __nv_bfloat16 hi = __float2bfloat16(v);
+            row[i] = hi;
+            row[R.far_ks + i] = __float2bfloat16(v - __bfloat162float(hi));
+        }
+    }
+}
+
+template <int M>
+__global__ void __launch_bounds__(kPlane16Threads, 3) k_inv_plane16(const InvTarget *__restrict__ tgts, int t0, int t1,
+                                                                 int block_lo, OutPtrs out, float inv_c, long long step)
+{
+    constexpr int B = M / 16, H = M / 2, SP = M + 1, SX = 17;
+    static_assert(plane16_class(M), "k_inv_plane16: M = 64, 96 or 128");
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const int b = blockIdx.x + block_lo;
+    const int t = owner_of(tgts, t0, t1, b, &InvTarget::plane0);
+    const InvTarget &T = tgts[t];
+    const int nx = T.nx, ny = T.ny, nz = T.nz;
+    const int local = b - T.plane0;
+    const int f = local / nz, z = local % nz;
+    const int pairs = (ny + 1) >> 1, xt = (pairs + 15) >> 4;
+    float2 *twx = sm, *twy = sm + M;
+    float2 *P = twy + M;            // y pass: line kx (row lines, ky along), line 0 = kx 0 and H packed
+    float2 *X = P + H * SP;         // x pass: [xt][M rows k][SX], 16 lines (pairs of output rows) per tile
+    float *O = reinterpret_cast<float *>(P);                  // [ny][nx] output plane (P is dead by then)
+    float *fw = reinterpret_cast<float *>(X + xt * M * SX);   // far weights and scratch
+    load_twiddles(twx, T.tw_x, M);
+    load_twiddles(twy, T.tw_y, M);
+    const FarTarget *Fp = T.far;
+    int fpx = 0, fpy = 0, fpz = 0, fr = 0, fdepth = 1;
+    const float *fcring = nullptr;
+    float *cz = fw;                                         // [py][px]
+    float *ux = cz + kMaxFarPts * kMaxFarPts;               // [py][nx]
+    float *sLx = ux + kMaxFarPts * nx;                      // [nx][px]
+    float *sLy = sLx + kMaxFarPts * nx;                     // [ny][py]
+    float *sLz = sLy + kMaxFarPts * ny;                     // [pz], row z
+    float *sc = sLz + kMaxFarPts;                           // [r]: this step's coefficients of field f
+    if (Fp) {
+        fpx = Fp->px; fpy = Fp->py; fpz = Fp->pz; fr = Fp->r; fdepth = Fp->depth; fcring = Fp->cring;
+        for (int i = threadIdx.x; i < nx * fpx; i += blockDim.x) sLx[i] = __ldg(Fp->Lx + i);
+        for (int i = threadIdx.x; i < ny * fpy; i += blockDim.x) sLy[i] = __ldg(Fp->Ly + i);
+        for (int i = threadIdx.x; i < fpz; i += blockDim.x) sLz[i] = __ldg(Fp->Lz + z * fpz + i);
+    }
+    pdl_trigger();
+    pdl_wait();   // T2 is written by the MAC, the coefficient ring by the far scatter or the learned field
+    if (step < 0) step = *T.d_step;   // graph replay: the step from the device counter
+    const float2 *src = T.t2 + ((long long)f * (H + 1) * nz + z) * M;
+    const long long rs = (long long)nz * M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    for (int kxi = 1 + warp; kxi < H; kxi += nwarps)
+        for (int ky = lane; ky < M; ky += 32) cp_async8(P + kxi * SP + ky, src + kxi * rs + ky);
+    for (int ky = threadIdx.x; ky < M; ky += blockDim.x) {
+        const float2 a = src[ky], h = src[H * rs + ky];
+        P[ky] = make_float2(a.x - h.y, a.y + h.x);   // S_0 + i S_H
+    }
+    cp_async_wait_all();
+    __syncthreads();
+    tiles_fft_block<B, true, false, 1, SP>(P, 16 * SP, H / 16, twy, M);
+    // x-pass input of the pair (ya, yb): A + iB over k < M, from the rows'
+    // half spectra (kx = 0 and H real: the real and imaginary parts of line 0)
+    for (int c = warp; c < pairs; c += nwarps)
+        for (int k = lane; k < M; k += 32) {
+        const int ya = 2 * c, yb = ya + 1;
+        const bool vb = yb < ny;
+        const int kk = k <= H ? k : M - k;
+        float2 A, Bv;
+        if (kk == 0 || kk == H) {
+            const float2 pa = P[tile_row<B>(ya)], pb = vb ? P[tile_row<B>(yb)] : make_float2(0.0f, 0.0f);
+            A = make_float2(kk == 0 ? pa.x : pa.y, 0.0f);
+            Bv = make_float2(kk == 0 ? pb.x : pb.y, 0.0f);
+        } else {
+            const float2 *L = P + kk * SP;
+            A = L[tile_row<B>(ya)];
+            Bv = vb ? L[tile_row<B>(yb)] : make_float2(0.0f, 0.0f);
+            if (k > H) { A = cconj(A); Bv = cconj(Bv); }
+        }
+        X[(c >> 4) * M * SX + k * SX + (c & 15)] = make_float2(A.x - Bv.y, A.y + Bv.x);
+        }
+    __syncthreads();
+    tiles_fft_block<B, true, false, SX, 1>(X, M * SX, xt, twx, M);
+    const long long Nt = (long long)nx * ny * nz;
+    float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * Nt) + (long long)z * nx * ny;
+    const float scale = f == 0 ? 1.0f : inv_c;
+    float *O_or_dst = Fp ? O : dst;
+    for (int y = warp; y < ny; y += nwarps) {
+        const int c = y >> 1;
+        const float2 *L = X + (c >> 4) * M * SX + (c & 15);
+        for (int x = lane; x < nx; x += 32) {
+            const float2 v = L[tile_row<B>(x) * SX];
+            O_or_dst[y * nx + x] = scale * ((y & 1) ? v.y : v.x);
+        }
+    }
+    if (!Fp) return;
+    // far pairs: tensor-product Lagrange interpolation of this step's node
+    // coefficients (field f), contracted over z first
+    const float *c = fcring + (step % fdepth) * (fr * 4);
+    for (int i = threadIdx.x; i < fr; i += blockDim.x) sc[i] = c[i * 4 + f];
+    __syncthreads();
+    const int pxy = fpx * fpy;
+    for (int i = threadIdx.x; i < pxy; i += blockDim.x) {
+        float s = 0.0f;
+        for (int cc = 0; cc < fpz; ++cc) s = fmaf(sLz[cc], sc[cc * pxy + i], s);
+        cz[i] = s;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < fpy * nx; i += blockDim.x) {
+        const int bb = i / nx, x = i % nx;
+        float u = 0.0f;
+        for (int aa = 0; aa < fpx; ++aa) u = fmaf(sLx[x * fpx + aa], cz[bb * fpx + aa], u);
+        ux[i] = u;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < nx * ny; i += blockDim.x) {
+        const int x = i % nx, y = i / nx;
+        float v = 0.0f;
+        for (int bb = 0; bb < fpy; ++bb) v = fmaf(sLy[y * fpy + bb], ux[bb * nx + x], v);
+        dst[i] = fmaf(scale, v, O[i]);
+    }
+}
+
 #define RP_FOR_EACH_CLASS(X) X(0) X(32) X(48) X(64) X(96) X(128) X(192)
 
 }  // namespace
@@ -856,8 +1085,12 @@ int size_class(const Axis &ax, const Axis &ay, const Axis &az)
     }
 }
 
-size_t smem_fwd_plane(int ny, const Axis &ax)
+size_t smem_fwd_plane(int cls, int ny, const Axis &ax)
 {
+    if (plane16_class(cls)) {
+        const size_t M = cls;
+        return sizeof(float2) * (2 * M + (size_t)plane16_xtiles(ny) * 16 * (M + 1) + M * (M / 2 + 1));
+    }
     const int kx = ax.M / 2 + 1;
     const int qs = kx | 1;
     // twiddles (x and y, bounded by kMaxFFT each) + Q + per-group scratch
@@ -873,8 +1106,13 @@ size_t smem_mac_inv_column(const Axis &az)
     return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad);
 }
 
-size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay)
+size_t smem_inv_plane(int cls, int nx, int ny, const Axis &ax, const Axis &ay)
 {
+    if (plane16_class(cls)) {
+        const size_t M = cls;
+        return sizeof(float2) * (2 * M + (M / 2) * (M + 1) + (size_t)plane16_xtiles(ny) * M * 17) +
+               sizeof(float) * kMaxFarPts * (kMaxFarPts + 2 * (size_t)nx + ny + 1 + kMaxFarPts * kMaxFarPts);
+    }
     const int kx = ax.M / 2 + 1;
     const int ps = ay.M | 1;
     // + the far path: coefficients contracted over z, then over x; the
@@ -909,6 +1147,13 @@ cudaError_t open_kernel_smem_limits(int max_optin)
         return e;
     RP_OPEN16(64) RP_OPEN16(96) RP_OPEN16(128) RP_OPEN16(192)
 #undef RP_OPEN16
+#define RP_OPENP16(M)                                                                                         \
+    if ((e = cudaFuncSetAttribute(k_fwd_plane16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
+        return e;                                                                                           \
+    if ((e = cudaFuncSetAttribute(k_inv_plane16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
+        return e;
+    RP_OPENP16(64) RP_OPENP16(96) RP_OPENP16(128)
+#undef RP_OPENP16
     return cudaSuccess;
 }
 
@@ -926,12 +1171,40 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
 #define RP_CASE(M, KERNEL, THREADS, ...) \
     case M: if (cudaError_t e_ = launch_pdl(KERNEL<M>, dim3(nblocks), dim3(THREADS), smem, s, __VA_ARGS__)) return e_; break;
 
+template <int M>
+static cudaError_t launch_fwd_plane_cls(const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
+                                        int nblocks, size_t smem, int far_slot, cudaStream_t s)
+{
+    if constexpr (plane16_class(M))
+        return launch_pdl(k_fwd_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_rings, in, r0, r1,
+                          block_lo, far_slot);
+    else
+        return launch_pdl(k_fwd_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_rings, in, r0, r1, block_lo,
+                          far_slot);
+}
+
+template <int M>
+static cudaError_t launch_inv_plane_cls(const InvTarget *d_tgts, int t0, int t1, int block_lo, const OutPtrs &out,
+                                        int nblocks, size_t smem, float inv_c, long long step, cudaStream_t s)
+{
+    if constexpr (plane16_class(M))
+        return launch_pdl(k_inv_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_tgts, t0, t1, block_lo,
+                          out, inv_c, step);
+    else
+        return launch_pdl(k_inv_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_tgts, t0, t1, block_lo, out,
+                          inv_c, step);
+}
+
 cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
                              int nblocks, size_t smem, int far_slot, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_fwd_plane, kPlaneThreads, d_rings, in, r0, r1, block_lo, far_slot)
+#define X(M)                                                                                                    \
+    case M:                                                                                                     \
+        if (cudaError_t e_ = launch_fwd_plane_cls<M>(d_rings, in, r0, r1, block_lo, nblocks, smem, far_slot, s)) \
+            return e_;                                                                                          \
+        break;
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;
@@ -993,7 +1266,11 @@ cudaError_t launch_inv_plane(int cls, const InvTarget *d_tgts, int t0, int t1, i
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
-#define X(M) RP_CASE(M, k_inv_plane, kPlaneThreads, d_tgts, t0, t1, block_lo, out, inv_c, step)
+#define X(M)                                                                                                      \
+    case M:                                                                                                       \
+        if (cudaError_t e_ = launch_inv_plane_cls<M>(d_tgts, t0, t1, block_lo, out, nblocks, smem, inv_c, step, s)) \
+            return e_;                                                                                            \
+        break;
         RP_FOR_EACH_CLASS(X)
 #undef X
     default: return cudaErrorInvalidValue;

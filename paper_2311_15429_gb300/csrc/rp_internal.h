@@ -305,10 +305,10 @@ cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *wo
 int far_gather_bn(int r);   // gathered-GEMM column tile for r target nodes (0 if more than 256)
 
 // shared-memory sizes the kernels need for the given shapes
-size_t smem_fwd_plane(int ny, const Axis &ax);
+size_t smem_fwd_plane(int size_class, int ny, const Axis &ax);   // by the kernel the class runs
 size_t smem_fwd_column(const Axis &az);   // four fields per block
 size_t smem_mac_inv_column(const Axis &az);
-size_t smem_inv_plane(int nx, int ny, const Axis &ax, const Axis &ay);
+size_t smem_inv_plane(int size_class, int nx, int ny, const Axis &ax, const Axis &ay);
 cudaError_t open_kernel_smem_limits(int max_optin);
 
 // ---- host FP64 kernel spectra (rp_spectra.cpp) ----
