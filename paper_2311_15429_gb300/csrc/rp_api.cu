@@ -235,6 +235,7 @@ void clear_far(rp_ctx *ctx)
     ctx->d_far2_srcs = nullptr; ctx->d_far2_tasks = nullptr; ctx->d_far2_kb = nullptr;
     ctx->far2_qall = ctx->far2_fac = nullptr; ctx->far2_work = nullptr;
     ctx->far2_BN = ctx->far2_KS = ctx->far2_D = ctx->far2_max_nz = 0; ctx->far2_fac_rows = 0;
+    ctx->far2_max_plane = ctx->far2_max_n = 0;
     ctx->far_src_alone.clear(); ctx->far_src_alone_of_dom.clear();
     ctx->d_far_src_alone = nullptr;
     ctx->far_tgt_alone.clear(); ctx->d_far_tgt_alone = nullptr; ctx->far_alone_planes = 0;
@@ -464,10 +465,20 @@ rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
         for (int a = 0; a < 3; ++a) far_axis(S.o[a], S.h, S.n[a], Q, nodes[a], L[a]);
         F.qx = (int)nodes[0].size(); F.qy = (int)nodes[1].size(); F.qz = (int)nodes[2].size();
         F.r = F.qx * F.qy * F.qz;
+        // the weight tables padded to Q columns per axis (zero weights for the
+        // nodes a short axis lacks), so the anterpolation's sizes are fixed
+        std::vector<float> Lp[3];
+        for (int a = 0; a < 3; ++a) {
+            const int q = (int)nodes[a].size();
+            Lp[a].assign((size_t)S.n[a] * Q, 0.0f);
+            for (int i = 0; i < S.n[a]; ++i)
+                for (int b = 0; b < q; ++b) Lp[a][(size_t)i * Q + b] = L[a][(size_t)i * q + b];
+        }
         float *Lx, *Ly, *Lz;
-        if ((st = upload(ctx, &Lx, L[0])) || (st = upload(ctx, &Ly, L[1])) || (st = upload(ctx, &Lz, L[2]))) return st;
+        if ((st = upload(ctx, &Lx, Lp[0])) || (st = upload(ctx, &Ly, Lp[1])) || (st = upload(ctx, &Lz, Lp[2])))
+            return st;
         F.Lx = Lx; F.Ly = Ly; F.Lz = Lz;
-        if ((st = dev_alloc(ctx, &F.part, (size_t)S.n[2] * 4 * F.qx * F.qy))) return st;
+        if ((st = dev_alloc(ctx, &F.part, (size_t)S.n[2] * 4 * Q * Q))) return st;
         if ((st = dev_alloc(ctx, &F.count, 1))) return st;
         RP_CUDA(ctx, cudaMemset(F.count, 0, sizeof(unsigned int)));
         snode0.push_back((int)(snodes.size() / 3));
@@ -480,6 +491,8 @@ rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
                 }
         KS = std::max(KS, (F.r + 63) / 64 * 64);
         ctx->far2_max_nz = std::max(ctx->far2_max_nz, S.n[2]);
+        ctx->far2_max_plane = std::max(ctx->far2_max_plane, S.n[0] * S.n[1]);
+        ctx->far2_max_n = std::max({ctx->far2_max_n, S.n[0], S.n[1], S.n[2]});
         ctx->far2_of_dom[s] = (int)ctx->far2_srcs.size();
         ctx->far2_srcs.push_back(F);
     }
@@ -488,6 +501,8 @@ rp_status build_far2(rp_ctx *ctx, void *enc, const std::vector<int> &tidx,
         ctx->far2 = false;
         return RP_OK;
     }
+    if (smem_far_anterp(ctx->far2_max_plane, ctx->far2_max_n) > (size_t)ctx->smem_optin)
+        return fail(ctx, RP_ERR_UNSUPPORTED, "far source plane too large for the anterpolation's shared memory");
     ctx->far2_KS = KS;
     ctx->far2_D = D;
     // coefficient rings: [source][2 D][4][2 KS], zero before the first push
@@ -1482,8 +1497,10 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
             a1 = ai + 1;
         }
         if (a0 >= 0 && (st = timed_launch(ctx, RP_K_FAR_ANTERP, "far anterpolation", [&] {
-                            return launch_far_anterp(ctx->d_far2_srcs + a0, a1 - a0, ctx->far2_max_nz, in, kstep,
-                                                     ctx->d_step, ctx->far2_D, ctx->far2_KS, ctx->stream);
+                            return launch_far_anterp(ctx->d_far2_srcs + a0, a1 - a0, ctx->cfg.far_source_points,
+                                                     ctx->far2_max_nz,
+                                                     ctx->far2_max_plane, ctx->far2_max_n, in, kstep, ctx->d_step,
+                                                     ctx->far2_D, ctx->far2_KS, ctx->stream);
                         })))
             return st;
         const int batch = ctx->cfg.far_batch;

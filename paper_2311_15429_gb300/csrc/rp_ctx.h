@@ -197,7 +197,7 @@ struct rp_ctx {
     __nv_bfloat16 *far2_qall = nullptr, *far2_fac = nullptr;
     float *far2_work = nullptr;
     CUtensorMap far2_mapQ{}, far2_mapF{};
-    int far2_BN = 0, far2_KS = 0, far2_D = 0, far2_max_nz = 0;
+    int far2_BN = 0, far2_KS = 0, far2_D = 0, far2_max_nz = 0, far2_max_plane = 0, far2_max_n = 0;
     long long far2_fac_rows = 0;
     // far sources with no forward ring of their own: staged by a separate
     // kernel; far targets with no FFT pass: interpolated by a separate kernel

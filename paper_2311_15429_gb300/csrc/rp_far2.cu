@@ -53,16 +53,33 @@ constexpr int kGatherThreads = 192;
 
 __host__ __device__ __forceinline__ long long pos_mod(long long x, long long d) { return ((x % d) + d) % d; }
 
-// One block per (source plane z, far source): contract the plane over x and
-// y with the source's Lagrange weights (per field: qx * qy partial sums);
-// the last plane's block of a source adds the planes' sums in z order with
-// the z weights and writes the node coefficients of this step, bf16 hi and
-// lo, at both mirrored slots of the ring.
+// 16- and 4-byte asynchronous global -> shared copies
+__device__ __forceinline__ void an_cp16(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(su32(smem)), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void an_cp4(void *smem, const void *gmem)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(su32(smem)), "l"(gmem) : "memory");
+}
+
+// One block per (source plane z, far source): the plane's four fields
+// copied into shared memory (all copies in flight at once), contracted over
+// x (a thread per row, the rows of a warp starting at staggered columns so
+// that they read different banks) and then over y with the source's
+// Lagrange weights (per field: Q * Q partial sums); the last plane's block
+// of a source adds the planes' sums in z order with the z weights and writes
+// the node coefficients of this step, bf16 hi and lo, at both mirrored slots
+// of the ring.  Q: the context's source nodes per axis; the weight tables
+// are padded to Q columns, and a short axis's missing nodes (weight 0) are
+// dropped when the coefficients are written.
+template <int Q>
 __global__ void __launch_bounds__(kAnterpThreads) k_far_anterp(const FarSrc2 *__restrict__ srcs, int nsrc, IoPtrs in,
                                                                 long long step, const long long *d_step, int D,
                                                                 int KS)
 {
-    extern __shared__ float tsum[];   // [4][ny][qx]
+    constexpr int NQ = Q * Q, R3 = Q * Q * Q;
+    extern __shared__ float4 an_smem[];
     __shared__ int last;
     if (step < 0) step = *d_step;   // graph replay: the step from the device counter
     const int si = blockIdx.y;
@@ -71,51 +88,78 @@ __global__ void __launch_bounds__(kAnterpThreads) k_far_anterp(const FarSrc2 *__
     const int z = blockIdx.x;
     if (z >= S.nz) return;
     const float *rho = in.rho[S.dom], *J = in.J[S.dom];
-    const long long plane = (long long)S.nx * S.ny, N = plane * S.nz;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    const int qx = S.qx, qy = S.qy, nq = qx * qy;
-    // rows of the plane: sum_i Lx[i][bx] S(i, j, z)
-    for (int row = warp; row < 4 * S.ny; row += nw) {
-        const int f = row / S.ny, j = row % S.ny;
-        const float *src = (f == 0 ? rho : J + (long long)(f - 1) * N) + z * plane + (long long)j * S.nx;
-        float acc[kMaxFarPts];
+    const int nx = S.nx, ny = S.ny, nz = S.nz, nxy = nx * ny;
+    const long long N = (long long)nxy * nz;
+    float *sLx = reinterpret_cast<float *>(an_smem);    // [nx][Q] (zero-padded weights)
+    float *sLy = sLx + nx * kMaxFarPts;                  // [ny][Q]
+    float *tsum = sLy + ny * kMaxFarPts;                 // [4][ny][Q]; later the plane sums [nz][4][Q Q]
+    float *slab = tsum + 4 * ny * kMaxFarPts;            // [4][ny][nx]
+    for (int f = 0; f < 4; ++f) {
+        const float *src = (f == 0 ? rho : J + (long long)(f - 1) * N) + (long long)z * nxy;
+        float *dst = slab + f * nxy;
+        if ((((uintptr_t)src | (uintptr_t)dst) & 15) == 0 && (nxy & 3) == 0) {
+            for (int i = threadIdx.x; i < nxy / 4; i += blockDim.x) an_cp16(dst + 4 * i, src + 4 * i);
+        } else {
+            for (int i = threadIdx.x; i < nxy; i += blockDim.x) an_cp4(dst + i, src + i);
+        }
+    }
+    for (int i = threadIdx.x; i < nx * Q; i += blockDim.x) sLx[i] = __ldg(S.Lx + i);
+    for (int i = threadIdx.x; i < ny * Q; i += blockDim.x) sLy[i] = __ldg(S.Ly + i);
+    asm volatile("cp.async.wait_all;" ::: "memory");
+    __syncthreads();
+    // rows of the plane: sum_i Lx[i][bx] S(i, j, z); the rows of a warp start
+    // at different columns (banks): columns x0 .. nx - 1, then 0 .. x0 - 1
+    for (int row = threadIdx.x; row < 4 * ny; row += blockDim.x) {
+        const float *v = slab + row * nx;
+        float acc[Q];
 #pragma unroll
-        for (int b = 0; b < kMaxFarPts; ++b) acc[b] = 0.0f;
-        for (int i = lane; i < S.nx; i += 32) {
-            const float v = src[i];
+        for (int b = 0; b < Q; ++b) acc[b] = 0.0f;
+        const int x0 = row % nx;
+#pragma unroll 1
+        for (int pass = 0; pass < 2; ++pass) {
+            const int xa = pass ? 0 : x0, xb = pass ? x0 : nx;
+#pragma unroll 4
+            for (int x = xa; x < xb; ++x) {
+                const float sv = v[x];
+                const float *l = sLx + x * Q;
 #pragma unroll
-            for (int b = 0; b < kMaxFarPts; ++b)
-                if (b < qx) acc[b] = fmaf(S.Lx[i * qx + b], v, acc[b]);
+                for (int b = 0; b < Q; ++b) acc[b] = fmaf(l[b], sv, acc[b]);
+            }
         }
 #pragma unroll
-        for (int b = 0; b < kMaxFarPts; ++b)
-            for (int o = 16; o > 0; o >>= 1) acc[b] += __shfl_xor_sync(0xffffffffu, acc[b], o);
-        if (lane == 0)
-#pragma unroll
-            for (int b = 0; b < kMaxFarPts; ++b)
-                if (b < qx) tsum[(f * S.ny + j) * qx + b] = acc[b];
+        for (int b = 0; b < Q; ++b) tsum[row * Q + b] = acc[b];
     }
     __syncthreads();
     // columns: sum_j Ly[j][by] (row sums)
-    for (int o = threadIdx.x; o < 4 * nq; o += blockDim.x) {
-        const int f = o / nq, b = o % nq, by = b / qx, bx = b % qx;
+    for (int o = threadIdx.x; o < 4 * NQ; o += blockDim.x) {
+        const int f = o / NQ, b = o % NQ, by = b / Q, bx = b % Q;
+        const float *t = tsum + f * ny * Q + bx;
         float acc = 0.0f;
-        for (int j = 0; j < S.ny; ++j) acc = fmaf(S.Ly[j * qy + by], tsum[(f * S.ny + j) * qx + bx], acc);
-        S.part[((long long)z * 4 + f) * nq + b] = acc;
+        for (int j = 0; j < ny; ++j) acc = fmaf(sLy[j * Q + by], t[j * Q], acc);
+        S.part[((long long)z * 4 + f) * NQ + b] = acc;
     }
     __threadfence();
     __syncthreads();
-    if (threadIdx.x == 0) last = atomicAdd(S.count, 1u) == (unsigned)(S.nz - 1);
+    if (threadIdx.x == 0) last = atomicAdd(S.count, 1u) == (unsigned)(nz - 1);
     __syncthreads();
     if (!last) return;
     __threadfence();
-    // the source's last plane: sum_z Lz[z][bz] (plane sums), in z order
+    // the source's last plane: sum_z Lz[z][bz] (plane sums), in z order,
+    // from shared copies of every plane's sums and of the z weights (the
+    // plane sums read from L2, bypassing L1, which may hold stale lines)
+    const int np = nz * 4 * NQ;
+    float *ps = tsum, *sLz = tsum + np;   // the slab and row sums are dead
+    for (int i = threadIdx.x; i < np; i += blockDim.x) ps[i] = __ldcg(S.part + i);
+    for (int i = threadIdx.x; i < nz * Q; i += blockDim.x) sLz[i] = __ldg(S.Lz + i);
+    __syncthreads();
     const long long slot = pos_mod(step, D);
-    for (int o = threadIdx.x; o < 4 * S.r; o += blockDim.x) {
-        const int f = o / S.r, b = o % S.r, bz = b / nq, bxy = b % nq;
+    for (int o = threadIdx.x; o < 4 * R3; o += blockDim.x) {
+        const int f = o / R3, bp = o % R3, bz = bp / NQ, bxy = bp % NQ, by = bxy / Q, bx = bxy % Q;
+        if (bx >= S.qx || by >= S.qy || bz >= S.qz) continue;   // a node a short axis lacks
+        const int b = (bz * S.qy + by) * S.qx + bx;
+        const float *pp = ps + f * NQ + bxy;
         float acc = 0.0f;
-        for (int zz = 0; zz < S.nz; ++zz)
-            acc = fmaf(S.Lz[zz * S.qz + bz], __ldcg(S.part + ((long long)zz * 4 + f) * nq + bxy), acc);
+        for (int zz = 0; zz < nz; ++zz) acc = fmaf(sLz[zz * Q + bz], pp[zz * 4 * NQ], acc);
         const __nv_bfloat16 hi = __float2bfloat16(acc);
         const __nv_bfloat16 lo = __float2bfloat16(acc - __bfloat162float(hi));
 #pragma unroll
@@ -338,14 +382,37 @@ int far_gather_bn(int r)
     return 0;
 }
 
-cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step,
-                              const long long *d_step, int D, int KS, cudaStream_t s)
+size_t smem_far_anterp(int max_plane, int max_n)
+{
+    // the x and y weights, the row sums (4 x ny x qx), one plane of the four
+    // fields; the last block reuses the last two for every plane's sums
+    // (nz x 4 x qx qy) and the z weights (nz x qz)
+    const size_t main = 2 * (size_t)max_n * kMaxFarPts + 4 * (size_t)max_n * kMaxFarPts + 4 * (size_t)max_plane;
+    const size_t tail = 2 * (size_t)max_n * kMaxFarPts + (size_t)max_n * (4 * kMaxFarPts * kMaxFarPts + kMaxFarPts);
+    return sizeof(float) * std::max(main, tail);
+}
+
+cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int q, int max_nz, int max_plane, int max_n,
+                              const IoPtrs &in, long long step, const long long *d_step, int D, int KS, cudaStream_t s)
 {
     if (nsrc <= 0) return cudaSuccess;
-    // the row sums of one plane: 4 fields x ny (<= kMaxFFT) x qx (<= kMaxFarPts) floats
-    const size_t smem = sizeof(float) * 4 * kMaxFFT * kMaxFarPts;
-    k_far_anterp<<<dim3(max_nz, nsrc), kAnterpThreads, smem, s>>>(d_srcs, nsrc, in, step, d_step, D, KS);
-    return cudaGetLastError();
+    const size_t smem = smem_far_anterp(max_plane, max_n);
+    cudaError_t e = cudaErrorInvalidValue;
+    auto go = [&](auto kern) {
+        e = open_smem2(kern, smem);
+        if (!e) kern<<<dim3(max_nz, nsrc), kAnterpThreads, smem, s>>>(d_srcs, nsrc, in, step, d_step, D, KS);
+    };
+    switch (q) {
+    case 2: go(k_far_anterp<2>); break;
+    case 3: go(k_far_anterp<3>); break;
+    case 4: go(k_far_anterp<4>); break;
+    case 5: go(k_far_anterp<5>); break;
+    case 6: go(k_far_anterp<6>); break;
+    case 7: go(k_far_anterp<7>); break;
+    case 8: go(k_far_anterp<8>); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return e ? e : cudaGetLastError();
 }
 
 cudaError_t launch_far_build_fac(const FarBuild *d_blocks, int nblocks, const double *d_tnodes,

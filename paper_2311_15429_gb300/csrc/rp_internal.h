@@ -168,8 +168,8 @@ struct FarSrc2 {
     int dom;
     int nx, ny, nz;
     int qx, qy, qz, r;       // nodes per axis, r = qx*qy*qz <= KS
-    const float *Lx, *Ly, *Lz;   // [n][q] Lagrange weights per axis
-    float *part;             // [nz][4][qy*qx]: per-plane partial sums of one push
+    const float *Lx, *Ly, *Lz;   // [n][Q] Lagrange weights per axis (Q = far_source_points; zero past q)
+    float *part;             // [nz][4][Q*Q]: per-plane partial sums of one push
     unsigned int *count;     // planes done in this push (the last plane's block reduces over z)
     __nv_bfloat16 *qring;    // this source's rows of the shared ring array
     int qrow0;               // its first row there: source index * 2D * 4
@@ -292,8 +292,9 @@ cudaError_t launch_far_scatter(const FarLink *d_links, int nlinks, int nthreads,
 // two-sided far factors (rp_far2.cu)
 // step / l0 < 0: read the step from d_step (graph replay; the gather and the
 // reduction then run on a batch's last push only)
-cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int max_nz, const IoPtrs &in, long long step,
-                              const long long *d_step, int D, int KS, cudaStream_t s);
+cudaError_t launch_far_anterp(const FarSrc2 *d_srcs, int nsrc, int q, int max_nz, int max_plane, int max_n,
+                              const IoPtrs &in, long long step, const long long *d_step, int D, int KS, cudaStream_t s);
+size_t smem_far_anterp(int max_plane, int max_n);   // max_plane: nx ny, max_n: nx, ny and nz, over the far sources
 cudaError_t launch_far_build_fac(const FarBuild *d_blocks, int nblocks, const double *d_tnodes,
                                  const double *d_snodes, int BN, int KS, double inv_cdt, __nv_bfloat16 *fac,
                                  cudaStream_t s);
