@@ -400,37 +400,29 @@ __global__ void __launch_bounds__(kColumn16Threads) k_fwd_column16(const FwdRing
     pdl_trigger();
     pdl_wait();   // t1 is written by the plane pass
     if (step < 0) step = *R.d_step;   // graph replay: the step from the device counter
-    const int t = threadIdx.x, p = t & 7, zr = t >> 3;   // column pair p, rows zr + 16 j
+    __syncthreads();   // the twiddles
+    // warp f owns field f from copy-in to store: no block barrier, so the
+    // copies, transforms and stores of a block's warps interleave
+    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
+    const int p = lane & 7, zr = lane >> 3;   // column pair p, rows zr + 4 j
+    float2 *Vf = V + f * M * kTileY;
     {
-        // rows z < nz by asynchronous 16-byte copies, all in flight at once
         const long long t1_field = (long long)kx * nz * M;
-        const float2 *src = R.t1 + (long long)kxi * nz * M + kyt * kTileY + 2 * p;
-#pragma unroll
-        for (int f = 0; f < 4; ++f)
-#pragma unroll
-            for (int j = 0; j < B; ++j) {
-                const int z = zr + 16 * j;
-                if (z < nz) cp_async16(V + (f * M + z) * kTileY + 2 * p, src + f * t1_field + (long long)z * M);
-            }
+        const float2 *src = R.t1 + f * t1_field + (long long)kxi * nz * M + kyt * kTileY + 2 * p;
+        for (int z = zr; z < nz; z += 4) cp_async16(Vf + z * kTileY + 2 * p, src + (long long)z * M);
         cp_async_wait_all();
     }
-    __syncthreads();
-    const int lane = t & 31, warp = t >> 5;
+    __syncwarp();
     // a source as large as the target's padded half (the usual case) skips the
     // zero half in the first layer; a larger source of a cross pair does not
-    if (nz <= M / 2) tile_fft16<B, false, true>(V + warp * M * kTileY, tw, nz, lane);
-    else tile_fft16<B, false, false>(V + warp * M * kTileY, tw, nz, lane);
-    __syncthreads();
+    if (nz <= M / 2) tile_fft16<B, false, true>(Vf, tw, nz, lane);
+    else tile_fft16<B, false, false>(Vf, tw, nz, lane);
     float2 *dst = R.ring + (long long)((step - R.lag_off) % R.depth) * R.slot_elems +
-                  (long long)(kxi * ntile + kyt) * 4 * M * kTileY;
-#pragma unroll
-    for (int f = 0; f < 4; ++f)
-#pragma unroll
-        for (int j = 0; j < B; ++j) {
-            const int kz = zr + 16 * j;   // tile_row<B>(kz) = B zr + j
-            *reinterpret_cast<float4 *>(dst + (f * M + kz) * kTileY + 2 * p) =
-                *reinterpret_cast<const float4 *>(V + (f * M + B * zr + j) * kTileY + 2 * p);
-        }
+                  (long long)(kxi * ntile + kyt) * 4 * M * kTileY + f * M * kTileY;
+#pragma unroll 4
+    for (int kz = zr; kz < M; kz += 4)
+        *reinterpret_cast<float4 *>(dst + kz * kTileY + 2 * p) =
+            *reinterpret_cast<const float4 *>(Vf + tile_row<B>(kz) * kTileY + 2 * p);
 }
 
 // Kahan-compensated addition (the total is s - c; see k_mac_tma).
