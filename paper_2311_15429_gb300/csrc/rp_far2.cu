@@ -108,35 +108,58 @@ __global__ void __launch_bounds__(kAnterpThreads) k_far_anterp(const FarSrc2 *__
     asm volatile("cp.async.wait_all;" ::: "memory");
     __syncthreads();
     // rows of the plane: sum_i Lx[i][bx] S(i, j, z); the rows of a warp start
-    // at different columns (banks): columns x0 .. nx - 1, then 0 .. x0 - 1
+    // at different columns (banks) and wrap around
     for (int row = threadIdx.x; row < 4 * ny; row += blockDim.x) {
         const float *v = slab + row * nx;
         float acc[Q];
 #pragma unroll
         for (int b = 0; b < Q; ++b) acc[b] = 0.0f;
-        const int x0 = row % nx;
-#pragma unroll 1
-        for (int pass = 0; pass < 2; ++pass) {
-            const int xa = pass ? 0 : x0, xb = pass ? x0 : nx;
+        // every lane the same trip count (no divergence), columns wrapped
+        int x = row % nx;
 #pragma unroll 4
-            for (int x = xa; x < xb; ++x) {
-                const float sv = v[x];
+        for (int i = 0; i < nx; ++i) {
+            const float sv = v[x];
+            if constexpr (Q % 4 == 0) {   // whole 16-byte weight rows: no bank conflicts
+#pragma unroll
+                for (int b4 = 0; b4 < Q; b4 += 4) {
+                    const float4 l = *reinterpret_cast<const float4 *>(sLx + x * Q + b4);
+                    acc[b4] = fmaf(l.x, sv, acc[b4]);
+                    acc[b4 + 1] = fmaf(l.y, sv, acc[b4 + 1]);
+                    acc[b4 + 2] = fmaf(l.z, sv, acc[b4 + 2]);
+                    acc[b4 + 3] = fmaf(l.w, sv, acc[b4 + 3]);
+                }
+            } else {
                 const float *l = sLx + x * Q;
 #pragma unroll
                 for (int b = 0; b < Q; ++b) acc[b] = fmaf(l[b], sv, acc[b]);
             }
+            x = x + 1 == nx ? 0 : x + 1;
         }
+        if constexpr (Q % 4 == 0) {
 #pragma unroll
-        for (int b = 0; b < Q; ++b) tsum[row * Q + b] = acc[b];
+            for (int b4 = 0; b4 < Q; b4 += 4)
+                *reinterpret_cast<float4 *>(tsum + row * Q + b4) =
+                    make_float4(acc[b4], acc[b4 + 1], acc[b4 + 2], acc[b4 + 3]);
+        } else {
+#pragma unroll
+            for (int b = 0; b < Q; ++b) tsum[row * Q + b] = acc[b];
+        }
     }
     __syncthreads();
-    // columns: sum_j Ly[j][by] (row sums)
-    for (int o = threadIdx.x; o < 4 * NQ; o += blockDim.x) {
+    // columns: sum_j Ly[j][by] (row sums), four threads per output (rows
+    // j = part, part + 4, ...), their sums added in a fixed order
+    constexpr int n4 = 16 * NQ, n4w = (n4 + 31) / 32 * 32;   // whole warps: the shuffles take every lane
+    for (int o4 = threadIdx.x; o4 < n4w; o4 += blockDim.x) {
+        const bool act = o4 < n4;
+        const int o = act ? o4 >> 2 : 0, part = o4 & 3;
         const int f = o / NQ, b = o % NQ, by = b / Q, bx = b % Q;
         const float *t = tsum + f * ny * Q + bx;
         float acc = 0.0f;
-        for (int j = 0; j < ny; ++j) acc = fmaf(sLy[j * Q + by], t[j * Q], acc);
-        S.part[((long long)z * 4 + f) * NQ + b] = acc;
+        if (act)
+            for (int j = part; j < ny; j += 4) acc = fmaf(sLy[j * Q + by], t[j * Q], acc);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        if (act && part == 0) S.part[((long long)z * 4 + f) * NQ + b] = acc;
     }
     __threadfence();
     __syncthreads();
