@@ -389,10 +389,16 @@ __host__ __device__ __forceinline__ void tile_stage1(float2 *T, const float2 *tw
 {
     float2 *L = T + c * SC;
     float2 x[16];
+    constexpr int NR = HALF ? 8 : 16;   // rows that may be nonzero: n1 < NR
+    if (nin >= NR * B) {                // all of them present: no per-row test
 #pragma unroll
-    for (int n1 = 0; n1 < 16; ++n1) {
-        const int p = B * n1 + n2;
-        x[n1] = (n1 < (HALF ? 8 : 16) && p < nin) ? L[p * SP] : make_float2(0.0f, 0.0f);
+        for (int n1 = 0; n1 < 16; ++n1) x[n1] = n1 < NR ? L[(B * n1 + n2) * SP] : make_float2(0.0f, 0.0f);
+    } else {
+#pragma unroll
+        for (int n1 = 0; n1 < 16; ++n1) {
+            const int p = B * n1 + n2;
+            x[n1] = (n1 < NR && p < nin) ? L[p * SP] : make_float2(0.0f, 0.0f);
+        }
     }
     dft16<INV, HALF>(x);
     L[n2 * SP] = x[0];
