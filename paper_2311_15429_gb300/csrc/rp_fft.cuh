@@ -1,4 +1,5 @@
-// Device building blocks of the FFT path: complex helpers and the line FFT.
+// Device building blocks of the FFT path: complex helpers, the lane-shuffle
+// line FFT and the two-stage shared-memory tile transform (further below).
 //
 // A line of length M = R * L is transformed by L lanes of one warp (several
 // lines share a warp when L < 32).  Lane g holds x[n*L + g] for n < R in

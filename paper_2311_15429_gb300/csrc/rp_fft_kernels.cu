@@ -14,10 +14,13 @@
 // the scratch after a plane pass is [field][kx][z][ky]; every field array of
 // a domain is [z][y][x].
 //
-// Every kernel is instantiated for the cubic padded sizes M in
-// {32, 48, 64, 96, 128, 192} (shapes known at compile time, 16-byte loads
-// and stores of column pairs) and for M = 0 (any supported shape, read at run
-// time).
+// The passes come in two forms.  k_fwd_plane16, k_fwd_column16 and
+// k_inv_plane16 run the two-stage shared-memory tile transform of rp_fft.cuh
+// (M = 16 B: the plane passes for M = 64, 96, 128, the column pass also for
+// 192).  k_fwd_plane, k_fwd_column and k_inv_plane run the lane-shuffle line
+// transform for the other cubic sizes (32, 48, and 192 for the plane passes)
+// and for M = 0 (any supported shape, read at run time).  The MAC with its
+// inverse column transform is instantiated for every class.
 #include <cuda_runtime.h>
 
 #include "rp_fft.cuh"
@@ -1116,36 +1119,35 @@ size_t smem_inv_plane(int cls, int nx, int ny, const Axis &ax, const Axis &ay)
 // The dynamic shared-memory limit is an attribute of the kernel function,
 // shared by every context in the process, so each kernel is opened up to the
 // device's opt-in maximum once (contexts never lower it for one another).
+// Each size class opens the kernels it runs: the tile-transform passes where
+// the class has them, the lane-shuffle passes elsewhere.
+template <int M>
+static cudaError_t open_class_smem(int max_optin)
+{
+    cudaError_t e;
+    const auto open = [&](auto kern) { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                                    max_optin); };
+    if constexpr (plane16_class(M)) {
+        if ((e = open(k_fwd_plane16<M>)) || (e = open(k_inv_plane16<M>))) return e;
+    } else {
+        if ((e = open(k_fwd_plane<M>)) || (e = open(k_inv_plane<M>))) return e;
+    }
+    if constexpr (tile16_class(M)) {
+        if ((e = open(k_fwd_column16<M>))) return e;
+    } else {
+        if ((e = open(k_fwd_column<M>))) return e;
+    }
+    if ((e = open(k_mac_inv_column<M, false>)) || (e = open(k_mac_inv_column<M, true>))) return e;
+    return cudaSuccess;
+}
+
 cudaError_t open_kernel_smem_limits(int max_optin)
 {
     cudaError_t e;
-#define RP_OPEN(M)                                                                                          \
-    if ((e = cudaFuncSetAttribute(k_fwd_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
-        return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_fwd_column<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
-        return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,  \
-                                  max_optin)))                                                              \
-        return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_mac_inv_column<M, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,   \
-                                  max_optin)))                                                              \
-        return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_inv_plane<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
-        return e;
+#define RP_OPEN(M) \
+    if ((e = open_class_smem<M>(max_optin))) return e;
     RP_FOR_EACH_CLASS(RP_OPEN)
 #undef RP_OPEN
-#define RP_OPEN16(M)                                                                                          \
-    if ((e = cudaFuncSetAttribute(k_fwd_column16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin))) \
-        return e;
-    RP_OPEN16(64) RP_OPEN16(96) RP_OPEN16(128) RP_OPEN16(192)
-#undef RP_OPEN16
-#define RP_OPENP16(M)                                                                                         \
-    if ((e = cudaFuncSetAttribute(k_fwd_plane16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
-        return e;                                                                                           \
-    if ((e = cudaFuncSetAttribute(k_inv_plane16<M>, cudaFuncAttributeMaxDynamicSharedMemorySize, max_optin)))  \
-        return e;
-    RP_OPENP16(64) RP_OPENP16(96) RP_OPENP16(128)
-#undef RP_OPENP16
     return cudaSuccess;
 }
 
