@@ -891,7 +891,7 @@ def calibrate_direct_rate(local, stream, steps=3):
 
 
 def plain_path_extrapolated(w, info, costs, direct_rate):
-    """The plain FP32 path of every pair (SURVEY's per-pair unbatched FFT path:
+    """The plain FP32 path of every pair (the per-pair unbatched FFT path:
     self and equal-spacing cross pairs by FFT, one entry per lag; pairs of
     unequal spacing by the direct sum), whose histories do not fit the GPU
     for these workloads: its step time from the per-class costs measured by
