@@ -1043,6 +1043,34 @@ def deep_leg(args, name, K, W, local, stream, mode="lowrank", source_points=4, c
                          "step; inputs fixed between replays"}
     q = lib.query()
     lib.close()
+    # two-sided factors: the same steps with overlapped pushes (each push on the
+    # library's push stream beside the previous evaluation; the same bits as
+    # the sequential context above, which keeps the accuracy check, the kernel
+    # pass and the graph replay, which refuses overlapped contexts)
+    sequential = None
+    if source_points and mode == "lowrank":
+        sequential = {"ms_per_step": ms / K, "value": w.points * K / (ms / 1e3), "unit": UNIT,
+                      "note": "rp_push_all + rp_evaluate on a context without RP_FLAG_OVERLAP_PUSH"}
+        with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK,
+                                   flags=flags | rp.RP_FLAG_OVERLAP_PUSH, device=local, stream=stream,
+                                   far_distance=fd, far_batch=args.far_batch, far_source_points=source_points) as lo:
+            for j in range(pre + W):
+                r, J = gen.step(j - pre, w.dt)
+                lo.push_all(r, J)
+                if j >= pre:
+                    lo.evaluate()
+            lo.sync()
+            ophi, oA = rp.pointer_array(lo.phi), rp.pointer_array(lo.A)
+            torch.cuda.synchronize()
+            o0, o1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            o0.record(stream)
+            for i in range(K):
+                r, J = pcyc[i % ncycle]
+                rp.rp_push_all_event(lo.ctx, r, J)
+                rp.rp_evaluate(lo.ctx, ophi, oA)
+            o1.record(stream)
+            torch.cuda.synchronize()
+            ms = o0.elapsed_time(o1)
     plain_line = None
     if plain:
         costs = calibrate_fft_costs(w, local, stream)
@@ -1052,8 +1080,10 @@ def deep_leg(args, name, K, W, local, stream, mode="lowrank", source_points=4, c
         plain_line["speedup_of_chosen"] = plain_line["ms_per_step"] / (ms / K)
     return {"workload": name, "description": w.description, "points_per_step": w.points,
             "value": w.points * K / (ms / 1e3), "unit": UNIT, "ms_per_step": ms / K, "steps": K, "warmup": W,
-            "path": f"FFT self terms; far pairs {mode}" + (f", two-sided factors ({source_points}^3 source nodes)"
+            "path": f"FFT self terms; far pairs {mode}" + (f", two-sided factors ({source_points}^3 source nodes), "
+                                                          f"overlapped pushes"
                                                           if source_points and mode == "lowrank" else ""),
+            "sequential_push": sequential,
             "far_pairs": q["npairs_far"], "learned_pairs": q["npairs_learned"], "far_bytes": q["far_bytes"],
             "device_bytes": q["device_bytes"], "training": train, "accuracy": acc, "roofline": roof,
             "far_gemm_roofline": far_roof, "kernels": kstats, "gpu_launches": launches, "plain_path": plain_line,
