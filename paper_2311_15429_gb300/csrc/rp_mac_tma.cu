@@ -18,9 +18,10 @@
 //     mbarrier (one arrival per consumer warp);
 //   * the other CW warps (8, 12 or 16, picked per size class by timing the
 //     variants on the context's own plan) are consumers: they multiply-accumulate in registers,
-//     then write the tile to a separate shared-memory region for the column
-//     FFT (two columns per warp at a time), so the producer keeps prefetching
-//     the next tile's operands meanwhile.
+//     then write the tile to a separate shared-memory region, where the FFT
+//     warps run the inverse column transform (the two-stage tile transform of
+//     rp_fft.cuh) and store T2, so the producer keeps prefetching the next
+//     tile's operands meanwhile.
 //
 // Every wait is bounded (clock64 limit).  On a timeout the kernel sets the
 // context's error flag, stops waiting, and the producer waits (bounded) for
@@ -152,53 +153,31 @@ __device__ __forceinline__ void named_sync(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// Inverse FFT along z of the 64 columns of the FFT tile `acc` (4 fields x
-// 16 ky), shared by warps w = 0 .. nw-1 (this one is w), then rows z < nz
-// to T2; barrier `bar` (nw warps) separates the two.
+// Inverse FFT along z of the four field tiles of `acc` ([field][M][16],
+// dense) by the two-stage tile transform (rp_fft.cuh), its tasks shared by
+// warps w = 0 .. nw-1 (this one is w; barrier `bar` of nw warps between the
+// stages), then rows z < nz (row z of the transform sits at tile_row(z)) to T2.
 template <int M>
-__device__ __forceinline__ void column_fft_store(float2 *acc, const InvTarget &T, int kxi, int ky0, int w, int nw,
-                                                 int lane, const LaneTw<M, true> &lt, int bar)
+__device__ __forceinline__ void column_tile_store(float2 *acc, const float2 *tw, const InvTarget &T, int kxi, int ky0,
+                                                  int w, int nw, int lane, int bar)
 {
-    constexpr int R = LaneTw<M, true>::R, L = LaneTw<M, true>::L, LOGL = LaneTw<M, true>::LOGL;
-    constexpr int G = 32 / L;
-    constexpr int FS = M * kTileYPad;
-    const int per = 2 * nw * G;   // columns per pass, two per lane group at a time
-    const int grp = lane / L, g = lane % L;
-    const int kb = bitrev_lanes(g, LOGL) * R;
-    const int nz = T.nz;
-    for (int base = 0; base < 4 * kTileY; base += per) {
-        const int l0 = base + (w * G + grp) * 2;
-        const bool ok = l0 < 4 * kTileY;
-        float2 *c0 = acc + (ok ? (l0 / kTileY) * FS + l0 % kTileY : 0);
-        float2 *c1 = acc + (ok ? ((l0 + 1) / kTileY) * FS + (l0 + 1) % kTileY : 0);
-        float2 v0[R], v1[R];
-#pragma unroll
-        for (int n = 0; n < R; ++n) {
-            v0[n] = ok ? c0[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-            v1[n] = ok ? c1[(n * L + g) * kTileYPad] : make_float2(0.f, 0.f);
-        }
-        line_fft_c<M, true>(v0, lt);
-        line_fft_c<M, true>(v1, lt);
-        __syncwarp();
-        if (ok) {
-#pragma unroll
-            for (int k1 = 0; k1 < R; ++k1)
-                if (k1 + kb < nz) {
-                    c0[(k1 + kb) * kTileYPad] = v0[k1];
-                    c1[(k1 + kb) * kTileYPad] = v1[k1];
-                }
-        }
-        __syncwarp();
+    constexpr int B = M / 16, FS = M * kTileY;
+    const int tid = w * 32 + lane, nt = nw * 32;
+    for (int i = tid; i < 4 * 16 * B; i += nt) {
+        const int c = i & 15, rest = i >> 4, f = rest / B, n2 = rest - f * B;
+        tile_stage1<B, true, false>(acc + f * FS, tw, M, c, n2);
     }
-    named_sync(bar, nw * 32);
+    named_sync(bar, nt);
+    for (int i = tid; i < 4 * 256; i += nt) tile_stage2<B, true>(acc + (i >> 8) * FS, i & 15, (i >> 4) & 15);
+    named_sync(bar, nt);
+    const int nz = T.nz;
     const long long t2_field = (long long)(M / 2 + 1) * nz * M;
     float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
-    for (int i = w * 32 + lane; i < 4 * nz * (kTileY / 2); i += nw * 32) {
-        const int f = i / (nz * (kTileY / 2)), rem = i % (nz * (kTileY / 2));
-        const int zi = rem / (kTileY / 2), pp = rem % (kTileY / 2);
-        const float2 *sp = acc + f * FS + zi * kTileYPad + 2 * pp;
+    for (int i = tid; i < 4 * nz * (kTileY / 2); i += nt) {
+        const int f = i / (nz * (kTileY / 2)), rem = i - f * nz * (kTileY / 2);
+        const int zi = rem >> 3, pp = rem & 7;
         *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
-            make_float4(sp[0].x, sp[0].y, sp[1].x, sp[1].y);
+            *reinterpret_cast<const float4 *>(acc + f * FS + tile_row<B>(zi) * kTileY + 2 * pp);
     }
 }
 
@@ -225,7 +204,7 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
     constexpr int RSTEP = kConsumerWarps * 32 / 8;   // rows covered by one pass of the consumers
     constexpr int ROWS = (M + RSTEP - 1) / RSTEP;
     constexpr int NTY = M / kTileY;
-    constexpr int FS = M * kTileYPad;                // float2 per field of the FFT tile
+    constexpr int FS = M * kTileY;                   // float2 per field of the FFT tile (dense rows)
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sstages = smem;                                   // [ns][SSTAGE]
     unsigned char *gstages = smem + (size_t)ns * SSTAGE;             // [NG][STAGE]
@@ -338,8 +317,6 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
     if (warp >= kConsumerWarps) {
         // ------------------------------------------------------------ FFT warps
         const int fw = warp - kConsumerWarps;
-        LaneTw<M, true> lt;
-        lt.init(tw, lane & (LaneTw<M, true>::L - 1));
         uint32_t it = 0;
         for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
             const int b = tile + tile_lo;
@@ -347,13 +324,16 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
             const int local = b - T.tile0, kxi = local / NTY, ky0 = (local % NTY) * kTileY;
             if (tile + (int)gridDim.x >= ntiles) {
                 named_sync(kBarAll, (kConsumerWarps + FW) * 32);
-                column_fft_store<M>(acc, T, kxi, ky0, warp, kConsumerWarps + FW, lane, lt, kBarAll);
+                column_tile_store<M>(acc, tw, T, kxi, ky0, warp, kConsumerWarps + FW, lane, kBarAll);
                 break;
             }
             const bool have = wait_or_abort(accfull, it & 1);
             // on an abort the sums are not used: skip the transform, keep the barriers
-            if (have) column_fft_store<M>(acc, T, kxi, ky0, fw, FW, lane, lt, kBarFft);
-            else named_sync(kBarFft, FW * 32);
+            if (have) column_tile_store<M>(acc, tw, T, kxi, ky0, fw, FW, lane, kBarFft);
+            else {
+                named_sync(kBarFft, FW * 32);
+                named_sync(kBarFft, FW * 32);
+            }
             __syncwarp();
             if (lane == 0) mbar_arrive(accempty);
         }
@@ -483,19 +463,15 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
                         const float4 &c = cmp[COMP ? i : 0][f];
                         a[i][f] = make_float4(a[i][f].x - c.x, a[i][f].y - c.y, a[i][f].z - c.z, a[i][f].w - c.w);
                     }
-                    float2 *d = acc + f * FS + r * kTileYPad + 2 * p;
-                    d[0] = make_float2(a[i][f].x, a[i][f].y);
-                    d[1] = make_float2(a[i][f].z, a[i][f].w);
+                    *reinterpret_cast<float4 *>(acc + f * FS + r * kTileY + 2 * p) = a[i][f];
                 }
             }
         }
         if (tile + (int)gridDim.x >= ntiles) {
             named_sync(kBarAll, (kConsumerWarps + FW) * 32);
-            LaneTw<M, true> lt;
-            lt.init(tw, lane & (LaneTw<M, true>::L - 1));
             const int local = b - T.tile0;
-            column_fft_store<M>(acc, T, local / NTY, (local % NTY) * kTileY, warp, kConsumerWarps + FW, lane, lt,
-                                kBarAll);
+            column_tile_store<M>(acc, tw, T, local / NTY, (local % NTY) * kTileY, warp, kConsumerWarps + FW, lane,
+                                 kBarAll);
             break;
         }
         __syncwarp();
@@ -529,7 +505,7 @@ size_t mac_tma_smem(int M, int nstages)
 {
     const size_t stage = (size_t)M * 128;
     return (size_t)nstages * mac_tma_fields_per_copy(M) * stage + kKernelStages * stage +
-           sizeof(float2) * (4 * (size_t)M * kTileYPad + M) + 16 * ((size_t)nstages + kKernelStages) + 16 + 16;
+           sizeof(float2) * (4 * (size_t)M * kTileY + M) + 16 * ((size_t)nstages + kKernelStages) + 16 + 16;
 }
 
 cudaError_t open_mac_tma_smem_limit(int max_optin)

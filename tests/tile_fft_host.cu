@@ -71,5 +71,8 @@ int main()
     std::printf("cols96_sp17_inv %.6e\n", run_case<6, true, false, 17, 1>(96, 14));
     std::printf("cols96_sp49_half %.6e\n", run_case<6, false, true, 49, 1>(48, 15));
     std::printf("rows128_sc129_inv %.6e\n", run_case<8, true, false, 1, 129>(128, 16));
+    std::printf("inv32 %.6e\n", run_case<2, true, false, 16, 1>(32, 17));
+    std::printf("inv48 %.6e\n", run_case<3, true, false, 16, 1>(48, 18));
+    std::printf("fwd48_nin24 %.6e\n", run_case<3, false, false, 16, 1>(24, 19));
     return 0;
 }
