@@ -142,13 +142,6 @@ rp_status build_twiddles(rp_ctx *ctx, std::map<int, const float2 *> &tw)
 
 namespace {
 
-int class_slot(int cls)
-{
-    switch (cls) {
-    case 32: return 1; case 48: return 2; case 64: return 3; case 96: return 4; case 128: return 5; case 192: return 6;
-    default: return 0;
-    }
-}
 
 // Pipeline depth of the bulk-copy-fed MAC for every cubic class of the plan;
 // the register-blocked MAC serves the plan if some class cannot hold two
@@ -1023,6 +1016,14 @@ rp_status rp_finalize(rp_ctx *ctx)
     });
     std::vector<int> ring_pos(ring_keys.size());
     std::map<int, const float2 *> tw;
+    {   // the plane passes' form per class, from its forward plane blocks
+        int blocks[7] = {};
+        for (size_t r = 0; r < ring_keys.size(); ++r) blocks[class_slot(ring_class((int)r))] += 4 * ctx->doms[ring_keys[r].first].n[2];
+        for (size_t r = 0; r < ring_keys.size(); ++r) {
+            const int cls = ring_class((int)r);
+            ctx->fwd_tile[class_slot(cls)] = plane_tile_form(cls, blocks[class_slot(cls)]);
+        }
+    }
     for (size_t i = 0; i < ring_order.size(); ++i) {
         const int r = ring_order[i];
         ring_pos[r] = (int)i;
@@ -1043,7 +1044,12 @@ rp_status rp_finalize(rp_ctx *ctx)
         tw[m[0]]; tw[m[1]]; tw[m[2]];
         ctx->spectral_bytes += (long long)R.depth * R.slot_elems * (long long)sizeof(float2);
         ctx->spec_depth = std::max(ctx->spec_depth, R.depth);
-        ctx->smem_plane = std::max(ctx->smem_plane, smem_fwd_plane(size_class(R.ax, R.ay, R.az), R.ny, R.ax));
+        {
+            const int c = size_class(R.ax, R.ay, R.az), cs = class_slot(c);
+            const size_t need = smem_fwd_plane(c, ctx->fwd_tile[cs], R.ny, R.ax);
+            ctx->smem_plane_cls[cs] = std::max(ctx->smem_plane_cls[cs], need);
+            ctx->smem_plane = std::max(ctx->smem_plane, need);
+        }
         ctx->smem_col = std::max(ctx->smem_col, smem_fwd_column(R.az));
         const int cls = ring_class(r);
         if (ctx->fwd_groups.empty() || ctx->fwd_groups.back().cls != cls)
@@ -1068,6 +1074,11 @@ rp_status rp_finalize(rp_ctx *ctx)
     };
     std::stable_sort(tgt_order.begin(), tgt_order.end(),
                      [&](int x, int y) { return tgt_class(x) < tgt_class(y); });
+    {   // the inverse plane pass's form per class, from its blocks
+        int blocks[7] = {};
+        for (int t : tgt_order) blocks[class_slot(tgt_class(t))] += 4 * ctx->doms[t].n[2];
+        for (int t : tgt_order) ctx->inv_tile[class_slot(tgt_class(t))] = plane_tile_form(tgt_class(t), blocks[class_slot(tgt_class(t))]);
+    }
     for (int t : tgt_order) {
         const DomainDesc &T = ctx->doms[t];
         InvTarget I{};
@@ -1108,7 +1119,12 @@ rp_status rp_finalize(rp_ctx *ctx)
         ctx->mac_blocks += I.kx * ((tm[t][1] + kTileY - 1) / kTileY);
         ctx->invp_blocks += 4 * I.nz;
         ctx->smem_mac = std::max(ctx->smem_mac, smem_mac_inv_column(I.az));
-        ctx->smem_inv = std::max(ctx->smem_inv, smem_inv_plane(size_class(I.ax, I.ay, I.az), I.nx, I.ny, I.ax, I.ay));
+        {
+            const int c = size_class(I.ax, I.ay, I.az), cs = class_slot(c);
+            const size_t need = smem_inv_plane(c, ctx->inv_tile[cs], I.nx, I.ny, I.ax, I.ay);
+            ctx->smem_inv_cls[cs] = std::max(ctx->smem_inv_cls[cs], need);
+            ctx->smem_inv = std::max(ctx->smem_inv, need);
+        }
         const int cls = tgt_class(t);
         const int i = (int)ctx->inv.size();
         if (ctx->inv_groups.empty() || ctx->inv_groups.back().cls != cls)
@@ -1469,7 +1485,8 @@ rp_status enqueue_push(rp_ctx *ctx, int d0, int d1, const IoPtrs &in)
     }
     for (const LaunchGroup &g : launches) {
         if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "forward plane pass", [&] {
-                 return launch_fwd_plane(g.cls, rings, fin, g.i0, g.i1, g.blk0, g.blk1 - g.blk0, ctx->smem_plane,
+                 return launch_fwd_plane(g.cls, ctx->fwd_tile[class_slot(g.cls)], rings, fin, g.i0, g.i1, g.blk0,
+                                         g.blk1 - g.blk0, ctx->smem_plane_cls[class_slot(g.cls)],
                                          (int)(step % std::max(1, ctx->cfg.far_batch)), ctx->stream);
              })))
             return st;
@@ -1902,8 +1919,9 @@ static rp_status evaluate_launches(rp_ctx *ctx, const OutPtrs &out, long long st
     }
     for (const LaunchGroup &g : ctx->inv_groups) {
         if ((st = timed_launch(ctx, RP_K_INV_PLANE, "inverse plane pass", [&] {
-                 return launch_inv_plane(g.cls, ctx->d_inv, g.i0, g.i1, g.blk2_0, out, g.blk2_1 - g.blk2_0,
-                                         ctx->smem_inv, inv_c, kstep, ctx->stream);
+                 return launch_inv_plane(g.cls, ctx->inv_tile[class_slot(g.cls)], ctx->d_inv, g.i0, g.i1, g.blk2_0,
+                                         out, g.blk2_1 - g.blk2_0, ctx->smem_inv_cls[class_slot(g.cls)], inv_c, kstep,
+                                         ctx->stream);
              })))
             return st;
     }

@@ -43,6 +43,15 @@ struct ProfRec {
 // One launch of a kernel pair over a contiguous range [i0, i1) of rings (or
 // targets) of one size class: first kernel's blocks [blk0, blk1), second
 // kernel's blocks [blk2_0, blk2_1).
+// Index of a kernel size class (0: the run-time shape) in the per-class tables.
+inline int class_slot(int cls)
+{
+    switch (cls) {
+    case 32: return 1; case 48: return 2; case 64: return 3; case 96: return 4; case 128: return 5; case 192: return 6;
+    default: return 0;
+    }
+}
+
 struct LaunchGroup {
     int cls;
     int i0, i1;
@@ -154,6 +163,8 @@ struct rp_ctx {
     std::vector<int> raw_block0;                     // [ndom + 1], blocks of k_ring_push
     int plane_blocks = 0, col_blocks = 0, mac_blocks = 0, invp_blocks = 0, dir_blocks = 0;
     size_t smem_plane = 0, smem_col = 0, smem_mac = 0, smem_inv = 0, smem_dir = 0;
+    bool fwd_tile[7] = {}, inv_tile[7] = {};            // plane-pass form per class (index by class_slot)
+    size_t smem_plane_cls[7] = {}, smem_inv_cls[7] = {}; // their shared memory per launch
     int max_lag = 0, raw_depth = 0, spec_depth = 0;
     long long spectral_bytes = 0, kernel_bytes = 0, device_bytes = 0;
 

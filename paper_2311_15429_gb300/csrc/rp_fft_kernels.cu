@@ -1080,9 +1080,11 @@ int size_class(const Axis &ax, const Axis &ay, const Axis &az)
     }
 }
 
-size_t smem_fwd_plane(int cls, int ny, const Axis &ax)
+bool plane_tile_class(int size_class) { return plane16_class(size_class); }
+
+size_t smem_fwd_plane(int cls, bool tile, int ny, const Axis &ax)
 {
-    if (plane16_class(cls)) {
+    if (tile && plane16_class(cls)) {
         const size_t M = cls;
         return sizeof(float2) * (2 * M + (size_t)plane16_xtiles(ny) * 16 * (M + 1) + M * (M / 2 + 1));
     }
@@ -1101,9 +1103,9 @@ size_t smem_mac_inv_column(const Axis &az)
     return sizeof(float2) * ((size_t)az.M + 4 * (size_t)az.M * kTileYPad);
 }
 
-size_t smem_inv_plane(int cls, int nx, int ny, const Axis &ax, const Axis &ay)
+size_t smem_inv_plane(int cls, bool tile, int nx, int ny, const Axis &ax, const Axis &ay)
 {
-    if (plane16_class(cls)) {
+    if (tile && plane16_class(cls)) {
         const size_t M = cls;
         return sizeof(float2) * (2 * M + (M / 2) * (M + 1) + (size_t)plane16_xtiles(ny) * M * 17) +
                sizeof(float) * kMaxFarPts * (kMaxFarPts + 2 * (size_t)nx + ny + 1 + kMaxFarPts * kMaxFarPts);
@@ -1127,11 +1129,9 @@ static cudaError_t open_class_smem(int max_optin)
     cudaError_t e;
     const auto open = [&](auto kern) { return cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                                                     max_optin); };
-    if constexpr (plane16_class(M)) {
+    if constexpr (plane16_class(M))
         if ((e = open(k_fwd_plane16<M>)) || (e = open(k_inv_plane16<M>))) return e;
-    } else {
-        if ((e = open(k_fwd_plane<M>)) || (e = open(k_inv_plane<M>))) return e;
-    }
+    if ((e = open(k_fwd_plane<M>)) || (e = open(k_inv_plane<M>))) return e;
     if constexpr (tile16_class(M)) {
         if ((e = open(k_fwd_column16<M>))) return e;
     } else {
@@ -1166,37 +1166,38 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
     case M: if (cudaError_t e_ = launch_pdl(KERNEL<M>, dim3(nblocks), dim3(THREADS), smem, s, __VA_ARGS__)) return e_; break;
 
 template <int M>
-static cudaError_t launch_fwd_plane_cls(const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
-                                        int nblocks, size_t smem, int far_slot, cudaStream_t s)
+static cudaError_t launch_fwd_plane_cls(bool tile, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
+                                        int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s)
 {
     if constexpr (plane16_class(M))
-        return launch_pdl(k_fwd_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_rings, in, r0, r1,
-                          block_lo, far_slot);
-    else
-        return launch_pdl(k_fwd_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_rings, in, r0, r1, block_lo,
-                          far_slot);
+        if (tile)
+            return launch_pdl(k_fwd_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_rings, in, r0, r1,
+                              block_lo, far_slot);
+    return launch_pdl(k_fwd_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_rings, in, r0, r1, block_lo,
+                      far_slot);
 }
 
 template <int M>
-static cudaError_t launch_inv_plane_cls(const InvTarget *d_tgts, int t0, int t1, int block_lo, const OutPtrs &out,
-                                        int nblocks, size_t smem, float inv_c, long long step, cudaStream_t s)
+static cudaError_t launch_inv_plane_cls(bool tile, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+                                        const OutPtrs &out, int nblocks, size_t smem, float inv_c, long long step,
+                                        cudaStream_t s)
 {
     if constexpr (plane16_class(M))
-        return launch_pdl(k_inv_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_tgts, t0, t1, block_lo,
-                          out, inv_c, step);
-    else
-        return launch_pdl(k_inv_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_tgts, t0, t1, block_lo, out,
-                          inv_c, step);
+        if (tile)
+            return launch_pdl(k_inv_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_tgts, t0, t1,
+                              block_lo, out, inv_c, step);
+    return launch_pdl(k_inv_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_tgts, t0, t1, block_lo, out,
+                      inv_c, step);
 }
 
-cudaError_t launch_fwd_plane(int cls, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1, int block_lo,
-                             int nblocks, size_t smem, int far_slot, cudaStream_t s)
+cudaError_t launch_fwd_plane(int cls, bool tile, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
+                             int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
 #define X(M)                                                                                                    \
     case M:                                                                                                     \
-        if (cudaError_t e_ = launch_fwd_plane_cls<M>(d_rings, in, r0, r1, block_lo, nblocks, smem, far_slot, s)) \
+        if (cudaError_t e_ = launch_fwd_plane_cls<M>(tile, d_rings, in, r0, r1, block_lo, nblocks, smem, far_slot, s)) \
             return e_;                                                                                          \
         break;
         RP_FOR_EACH_CLASS(X)
@@ -1255,14 +1256,14 @@ cudaError_t launch_mac_inv_column(int cls, bool comp, const InvTarget *d_tgts, i
     return cudaGetLastError();
 }
 
-cudaError_t launch_inv_plane(int cls, const InvTarget *d_tgts, int t0, int t1, int block_lo, const OutPtrs &out,
-                             int nblocks, size_t smem, float inv_c, long long step, cudaStream_t s)
+cudaError_t launch_inv_plane(int cls, bool tile, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+                             const OutPtrs &out, int nblocks, size_t smem, float inv_c, long long step, cudaStream_t s)
 {
     if (nblocks <= 0) return cudaSuccess;
     switch (cls) {
 #define X(M)                                                                                                      \
     case M:                                                                                                       \
-        if (cudaError_t e_ = launch_inv_plane_cls<M>(d_tgts, t0, t1, block_lo, out, nblocks, smem, inv_c, step, s)) \
+        if (cudaError_t e_ = launch_inv_plane_cls<M>(tile, d_tgts, t0, t1, block_lo, out, nblocks, smem, inv_c, step, s)) \
             return e_;                                                                                            \
         break;
         RP_FOR_EACH_CLASS(X)

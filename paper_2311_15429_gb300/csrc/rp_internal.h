@@ -235,14 +235,26 @@ int size_class(const Axis &ax, const Axis &ay, const Axis &az);
 cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, int d1,
                              const int *h_block0, int nblocks, long long step,
                              cudaStream_t s);
-cudaError_t launch_fwd_plane(int size_class, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
+// The plane passes in two forms for size classes M = 64, 96, 128: tile = true
+// runs the two-stage shared-memory tile transform (fewer instructions, 3
+// blocks per SM: the better form while a class's planes fit in about one wave),
+// tile = false the lane-shuffle line (5-6 blocks per SM: the better form over
+// many waves).  The planner picks per class from its block count
+// (plane_tile_form), so a plan's bits do not depend on timing.
+constexpr int kPlaneTileMaxBlocks = 1024;
+bool plane_tile_class(int size_class);
+inline bool plane_tile_form(int size_class, int blocks)
+{
+    return plane_tile_class(size_class) && blocks <= kPlaneTileMaxBlocks;
+}
+cudaError_t launch_fwd_plane(int size_class, bool tile, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
                              int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s);
 cudaError_t launch_fwd_column(int size_class, const FwdRing *d_rings, int r0, int r1, int block_lo,
                               int nblocks, size_t smem, long long step, cudaStream_t s);
 cudaError_t launch_mac_inv_column(int size_class, bool comp, const InvTarget *d_tgts, int t0, int t1, int block_lo,
                                   const MacEntry *d_entries, int nblocks, size_t smem, long long step,
                                   int clamp, cudaStream_t s);
-cudaError_t launch_inv_plane(int size_class, const InvTarget *d_tgts, int t0, int t1, int block_lo,
+cudaError_t launch_inv_plane(int size_class, bool tile, const InvTarget *d_tgts, int t0, int t1, int block_lo,
                              const OutPtrs &out, int nblocks, size_t smem, float inv_c, long long step,
                              cudaStream_t s);
 cudaError_t launch_direct(const DirectTarget *d_tgts, int ntgt, const DirectPair *d_pairs,
@@ -306,10 +318,10 @@ cudaError_t launch_far_reduce(const FarTarget *d_tgts, int ntgt, const float *wo
 int far_gather_bn(int r);   // gathered-GEMM column tile for r target nodes (0 if more than 256)
 
 // shared-memory sizes the kernels need for the given shapes
-size_t smem_fwd_plane(int size_class, int ny, const Axis &ax);   // by the kernel the class runs
+size_t smem_fwd_plane(int size_class, bool tile, int ny, const Axis &ax);   // of the form the class runs
 size_t smem_fwd_column(const Axis &az);   // four fields per block
 size_t smem_mac_inv_column(const Axis &az);
-size_t smem_inv_plane(int size_class, int nx, int ny, const Axis &ax, const Axis &ay);
+size_t smem_inv_plane(int size_class, bool tile, int nx, int ny, const Axis &ax, const Axis &ay);
 cudaError_t open_kernel_smem_limits(int max_optin);
 
 // ---- host FP64 kernel spectra (rp_spectra.cpp) ----

@@ -155,7 +155,8 @@ static rp_status spill_transform(rp_ctx *ctx, int w0, int w1, long long j)
     const int planes = F1.plane0 + 4 * F1.nz - F0.plane0;
     const int tiles = F1.tile0 + F1.kx * ((F1.ay.M + kTileY - 1) / kTileY) - F0.tile0;
     if ((st = timed_launch(ctx, RP_K_FWD_PLANE, "window forward plane pass", [&] {
-             return launch_fwd_plane(cls, ctx->d_wfwd, in, w0, w1, F0.plane0, planes, ctx->smem_plane, 0, ctx->stream);
+             return launch_fwd_plane(cls, ctx->fwd_tile[class_slot(cls)], ctx->d_wfwd, in, w0, w1, F0.plane0, planes,
+                                     ctx->smem_plane_cls[class_slot(cls)], 0, ctx->stream);
          })))
         return st;
     return timed_launch(ctx, RP_K_FWD_COLUMN, "window forward column pass", [&] {
