@@ -109,6 +109,23 @@ def test_cubic_size_classes(n):
     _score(w.domains, hists, 0, w.c, w.dt, res, nodes=nodes)
 
 
+def test_many_planes_lane_shuffle_form():
+    """Nine 32^3 domains (padded 64^3, 1152 plane blocks per pass: above the
+    1024 up to which the planner keeps the tile-transform plane passes), so
+    the forward and inverse plane passes run the lane-shuffle form; checked
+    against the oracle on every target at its corners and seeded nodes."""
+    n, h = 32, 0.25
+    doms = [synth.cubic((12.0 * i, 12.0 * j, 0.5 * i), n, h) for i in range(3) for j in range(3)]
+    srcs = synth.seeded_sources(doms)
+    T = 12
+    hists = [s.history(0, T, 0.05) for s in srcs]
+    res = run_library(doms, synth.C_AU, 0.05, hists, 0, [T - 1])
+    rng = np.random.default_rng(9)
+    corners = [i + n * (j + n * k) for i in (0, n - 1) for j in (0, n - 1) for k in (0, n - 1)]
+    nodes = [np.array(corners + list(rng.integers(0, d.N, 24))) for d in doms]
+    _score(doms, hists, 0, synth.C_AU, 0.05, res, nodes=nodes)
+
+
 def test_ground_state_clamp():
     """Under RP_FLAG_GROUND_STATE_CLAMP, samples before the first push equal it."""
     w = synth.workload("cfg1")
