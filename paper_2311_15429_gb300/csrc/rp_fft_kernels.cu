@@ -376,9 +376,9 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
 
 // The forward column pass for M = 16 B, B even (M = 64, 96, 128, 192): the
 // tile [field][z][16] dense in shared memory, one warp per field with the
-// two-stage tile transform (rows z >= nz and >= M/2 are the zero padding and
-// are neither loaded nor transformed), then each spectral row copied from
-// its tile row to the ring slot.
+// two-stage tile transform (rows z >= nz are the zero padding: neither loaded
+// nor read; when nz <= M/2 the first layer skips the zero half), then each
+// spectral row copied from its tile row to the ring slot.
 constexpr int kColumn16Threads = 128;
 
 __host__ __device__ constexpr bool tile16_class(int M) { return M == 64 || M == 96 || M == 128 || M == 192; }
@@ -847,7 +847,10 @@ __global__ void __launch_bounds__(kPlaneThreads) k_inv_plane(const InvTarget *__
 // split after the y transform: the y pass is M/32 whole tiles.  Inverse: the
 // same steps in reverse order, the rows kx = 0 and M/2 packed as S_0 + i S_M/2
 // (their transforms along y are real up to rounding), and the C2R transform
-// along x as one complex transform per pair of output rows.
+// along x as one complex transform per pair of output rows.  A class runs
+// these while its planes fit in about one wave (plane_tile_form: 3 blocks of
+// 256 threads per SM); over many waves the lane-shuffle passes, with twice
+// the blocks per SM, finish first.
 constexpr int kPlane16Threads = 256;
 
 __host__ __device__ constexpr bool plane16_class(int M) { return M == 64 || M == 96 || M == 128; }
