@@ -435,6 +435,22 @@ __device__ __forceinline__ void tile_fft16(float2 *T, const float2 *tw, int nin,
     __syncwarp();
 }
 
+// The whole tile by a pair of warps (the 64 threads that call it with
+// half = 0 and 1; named barrier bar_id with 64 threads between the stages and
+// at the end): the rounds of each stage alternate between the two warps.
+template <int B, bool INV, bool HALF>
+__device__ __forceinline__ void tile_fft16_pair(float2 *T, const float2 *tw, int nin, int lane, int half, int bar_id)
+{
+    static_assert(B % 2 == 0, "tile transform: B even");
+    const int c = lane & 15, hi = lane >> 4;
+#pragma unroll 1
+    for (int r = half; r < B / 2; r += 2) tile_stage1<B, INV, HALF>(T, tw, nin, c, 2 * r + hi);
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+#pragma unroll 1
+    for (int r = half; r < 8; r += 2) tile_stage2<B, INV>(T, c, 2 * r + hi);
+    asm volatile("bar.sync %0, 64;" ::"r"(bar_id) : "memory");
+}
+
 // ntiles tiles (tile i at T + i * tile_stride) by the whole block, the tasks
 // of each stage spread over its threads (16 consecutive threads take the 16
 // lines of one row); ends with the block synchronised.

@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kColumnThreads) k_fwd_column(const FwdRing *__
 // two-stage tile transform (rows z >= nz are the zero padding: neither loaded
 // nor read; when nz <= M/2 the first layer skips the zero half), then each
 // spectral row copied from its tile row to the ring slot.
-constexpr int kColumn16Threads = 128;
+constexpr int kColumn16Threads = 256;   // two warps per field
 
 __host__ __device__ constexpr bool tile16_class(int M) { return M == 64 || M == 96 || M == 128 || M == 192; }
 
@@ -404,26 +404,27 @@ __global__ void __launch_bounds__(kColumn16Threads) k_fwd_column16(const FwdRing
     pdl_wait();   // t1 is written by the plane pass
     if (step < 0) step = *R.d_step;   // graph replay: the step from the device counter
     __syncthreads();   // the twiddles
-    // warp f owns field f from copy-in to store: no block barrier, so the
-    // copies, transforms and stores of a block's warps interleave
-    const int lane = threadIdx.x & 31, f = threadIdx.x >> 5;
-    const int p = lane & 7, zr = lane >> 3;   // column pair p, rows zr + 4 j
+    // the warp pair 2f, 2f + 1 owns field f from copy-in to store (named
+    // barrier 1 + f): no block barrier, so the fields' copies, transforms and
+    // stores interleave
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, f = warp >> 1, half = warp & 1;
+    const int t64 = threadIdx.x & 63, p = t64 & 7, zr = t64 >> 3;   // column pair p, rows zr + 8 j
     float2 *Vf = V + f * M * kTileY;
     {
         const long long t1_field = (long long)kx * nz * M;
         const float2 *src = R.t1 + f * t1_field + (long long)kxi * nz * M + kyt * kTileY + 2 * p;
-        for (int z = zr; z < nz; z += 4) cp_async16(Vf + z * kTileY + 2 * p, src + (long long)z * M);
+        for (int z = zr; z < nz; z += 8) cp_async16(Vf + z * kTileY + 2 * p, src + (long long)z * M);
         cp_async_wait_all();
     }
-    __syncwarp();
+    asm volatile("bar.sync %0, 64;" ::"r"(1 + f) : "memory");
     // a source as large as the target's padded half (the usual case) skips the
     // zero half in the first layer; a larger source of a cross pair does not
-    if (nz <= M / 2) tile_fft16<B, false, true>(Vf, tw, nz, lane);
-    else tile_fft16<B, false, false>(Vf, tw, nz, lane);
+    if (nz <= M / 2) tile_fft16_pair<B, false, true>(Vf, tw, nz, lane, half, 1 + f);
+    else tile_fft16_pair<B, false, false>(Vf, tw, nz, lane, half, 1 + f);
     float2 *dst = R.ring + (long long)((step - R.lag_off) % R.depth) * R.slot_elems +
                   (long long)(kxi * ntile + kyt) * 4 * M * kTileY + f * M * kTileY;
 #pragma unroll 4
-    for (int kz = zr; kz < M; kz += 4)
+    for (int kz = zr; kz < M; kz += 8)
         *reinterpret_cast<float4 *>(dst + kz * kTileY + 2 * p) =
             *reinterpret_cast<const float4 *>(Vf + tile_row<B>(kz) * kTileY + 2 * p);
 }
