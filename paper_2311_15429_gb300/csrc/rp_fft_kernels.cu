@@ -1069,6 +1069,139 @@ __global__ void __launch_bounds__(kPlane16Threads, 3) k_inv_plane16(const InvTar
     }
 }
 
+// ---------------------------------------------------------------- inverse plane pass for M = 192, in chunks
+//
+// At M = 192 a plane of spectra (97 lines of 192) takes 150 KB of shared
+// memory, so the lane-shuffle pass runs one block per SM.  This one runs the
+// tile transform through a single work tile in chunks of 16 lines: along y,
+// 16 kx lines at a time (kx = 0 and M/2 packed as one line, as in
+// k_inv_plane16), keeping only the rows y < ny of each in a compact buffer Y
+// (odd line stride: no bank conflicts); then along x, 16 pairs of output rows
+// at a time, each row written out with the far coefficients' interpolation
+// added (no output plane in shared memory).  About 109 KB per block: two
+// blocks per SM.
+constexpr int kPlaneBigThreads = 256;
+
+__host__ __device__ constexpr int plane_big_ystride(int ny) { return ny | 1; }
+
+template <int M>
+__global__ void __launch_bounds__(kPlaneBigThreads, 2) k_inv_plane_big(const InvTarget *__restrict__ tgts, int t0,
+                                                                       int t1, int block_lo, OutPtrs out, float inv_c,
+                                                                       long long step)
+{
+    constexpr int B = M / 16, H = M / 2, SW = M + 1, SX = 17;
+    static_assert(M == 192, "k_inv_plane_big: M = 192");
+    extern __shared__ float4 smem_f4[];
+    float2 *sm = reinterpret_cast<float2 *>(smem_f4);
+    const int b = blockIdx.x + block_lo;
+    const int t = owner_of(tgts, t0, t1, b, &InvTarget::plane0);
+    const InvTarget &T = tgts[t];
+    const int nx = T.nx, ny = T.ny, nz = T.nz;
+    const int local = b - T.plane0;
+    const int f = local / nz, z = local % nz;
+    const int pairs = (ny + 1) >> 1, SY = plane_big_ystride(ny);
+    float2 *twx = sm, *twy = sm + M;
+    float2 *Y = twy + M;                                  // [H lines][SY]: rows y < ny of the y transform
+    float2 *W = Y + H * SY;                               // work tile: 16 row lines of SW, or M rows of SX
+    float *ux = reinterpret_cast<float *>(W + M * SX);    // far: [py][nx]
+    float *sc = ux + kMaxFarPts * nx;                     // far: [r], this step's coefficients of field f
+    float *cz = sc + kMaxFarPts * kMaxFarPts * kMaxFarPts;   // far: [py][px]
+    load_twiddles(twx, T.tw_x, M);
+    load_twiddles(twy, T.tw_y, M);
+    pdl_trigger();
+    pdl_wait();   // T2 is written by the MAC, the coefficient ring by the far path
+    if (step < 0) step = *T.d_step;   // graph replay: the step from the device counter
+    const float2 *src = T.t2 + ((long long)f * (H + 1) * nz + z) * M;
+    const long long rs = (long long)nz * M;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    __syncthreads();
+    // along y, 16 kx lines per chunk; only the rows y < ny are kept
+    for (int ch = 0; ch < H / 16; ++ch) {
+        for (int l = warp; l < 16; l += nwarps) {
+            const int kxi = 16 * ch + l;
+            float2 *L = W + l * SW;
+            if (kxi == 0) {
+                for (int ky = lane; ky < M; ky += 32) {
+                    const float2 a = src[ky], h = src[H * rs + ky];
+                    L[ky] = make_float2(a.x - h.y, a.y + h.x);   // S_0 + i S_H
+                }
+            } else {
+                for (int ky = lane; ky < M; ky += 32) cp_async8(L + ky, src + kxi * rs + ky);
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        tiles_fft_block<B, true, false, 1, SW>(W, 16 * SW, 1, twy, M);   // ends synchronised
+        for (int i = threadIdx.x; i < 16 * ny; i += blockDim.x) {
+            const int l = i & 15, y = i >> 4;
+            Y[(16 * ch + l) * SY + y] = W[l * SW + tile_row<B>(y)];
+        }
+        __syncthreads();
+    }
+    // far pairs: this step's node coefficients of field f contracted over z,
+    // then over x (the weights read from global memory)
+    const FarTarget *Fp = T.far;
+    if (Fp) {
+        const int px = Fp->px, py = Fp->py, pz = Fp->pz, r = Fp->r, pxy = px * py;
+        const float *c = Fp->cring + (step % Fp->depth) * (r * 4);
+        for (int i = threadIdx.x; i < r; i += blockDim.x) sc[i] = c[i * 4 + f];
+        __syncthreads();
+        for (int i = threadIdx.x; i < pxy; i += blockDim.x) {
+            float s = 0.0f;
+            for (int cc = 0; cc < pz; ++cc) s = fmaf(__ldg(Fp->Lz + z * pz + cc), sc[cc * pxy + i], s);
+            cz[i] = s;
+        }
+        __syncthreads();
+        for (int i = threadIdx.x; i < py * nx; i += blockDim.x) {
+            const int bb = i / nx, x = i % nx;
+            float u = 0.0f;
+            for (int aa = 0; aa < px; ++aa) u = fmaf(__ldg(Fp->Lx + x * px + aa), cz[bb * px + aa], u);
+            ux[i] = u;
+        }
+    }
+    // along x (C2R), 16 pairs of output rows per chunk
+    const long long Nt = (long long)nx * ny * nz;
+    float *dst = (f == 0 ? out.phi[T.dom] : out.A[T.dom] + (long long)(f - 1) * Nt) + (long long)z * nx * ny;
+    const float scale = f == 0 ? 1.0f : inv_c;
+    for (int c0 = 0; c0 < pairs; c0 += 16) {
+        for (int i = threadIdx.x; i < 16 * M; i += blockDim.x) {
+            const int k = i % M, cc = i / M, c = c0 + cc;
+            float2 v = make_float2(0.0f, 0.0f);
+            if (c < pairs) {
+                const int ya = 2 * c, yb = ya + 1;
+                const bool vb = yb < ny;
+                const int kk = k <= H ? k : M - k;
+                float2 A, Bv;
+                if (kk == 0 || kk == H) {   // the real rows kx = 0 and H: parts of line 0
+                    const float2 pa = Y[ya], pb = vb ? Y[yb] : make_float2(0.0f, 0.0f);
+                    A = make_float2(kk == 0 ? pa.x : pa.y, 0.0f);
+                    Bv = make_float2(kk == 0 ? pb.x : pb.y, 0.0f);
+                } else {
+                    A = Y[kk * SY + ya];
+                    Bv = vb ? Y[kk * SY + yb] : make_float2(0.0f, 0.0f);
+                    if (k > H) { A = cconj(A); Bv = cconj(Bv); }
+                }
+                v = make_float2(A.x - Bv.y, A.y + Bv.x);   // A + iB
+            }
+            W[k * SX + cc] = v;
+        }
+        __syncthreads();
+        tiles_fft_block<B, true, false, SX, 1>(W, M * SX, 1, twx, M);   // ends synchronised
+        const int rows = min(32, ny - 2 * c0);
+        for (int i = threadIdx.x; i < rows * nx; i += blockDim.x) {
+            const int yy = i / nx, x = i - yy * nx, y = 2 * c0 + yy;
+            const float2 v = W[tile_row<B>(x) * SX + (yy >> 1)];
+            float o = scale * ((yy & 1) ? v.y : v.x);
+            if (Fp) {
+                float s = 0.0f;
+                for (int bb = 0; bb < Fp->py; ++bb) s = fmaf(__ldg(Fp->Ly + y * Fp->py + bb), ux[bb * nx + x], s);
+                o = fmaf(scale, s, o);
+            }
+            dst[y * nx + x] = o;
+        }
+        __syncthreads();
+    }
+}
 #define RP_FOR_EACH_CLASS(X) X(0) X(32) X(48) X(64) X(96) X(128) X(192)
 
 }  // namespace
@@ -1109,6 +1242,11 @@ size_t smem_mac_inv_column(const Axis &az)
 
 size_t smem_inv_plane(int cls, bool tile, int nx, int ny, const Axis &ax, const Axis &ay)
 {
+    if (cls == 192) {   // k_inv_plane_big, whatever the form flag
+        const size_t M = 192;
+        return sizeof(float2) * (2 * M + (M / 2) * (size_t)plane_big_ystride(ny) + M * 17) +
+               sizeof(float) * ((size_t)kMaxFarPts * nx + kMaxFarPts * kMaxFarPts * kMaxFarPts + kMaxFarPts * kMaxFarPts);
+    }
     if (tile && plane16_class(cls)) {
         const size_t M = cls;
         return sizeof(float2) * (2 * M + (M / 2) * (M + 1) + (size_t)plane16_xtiles(ny) * M * 17) +
@@ -1135,7 +1273,12 @@ static cudaError_t open_class_smem(int max_optin)
                                                                     max_optin); };
     if constexpr (plane16_class(M))
         if ((e = open(k_fwd_plane16<M>)) || (e = open(k_inv_plane16<M>))) return e;
-    if ((e = open(k_fwd_plane<M>)) || (e = open(k_inv_plane<M>))) return e;
+    if ((e = open(k_fwd_plane<M>))) return e;
+    if constexpr (M == 192) {
+        if ((e = open(k_inv_plane_big<M>))) return e;
+    } else {
+        if ((e = open(k_inv_plane<M>))) return e;
+    }
     if constexpr (tile16_class(M)) {
         if ((e = open(k_fwd_column16<M>))) return e;
     } else {
@@ -1190,8 +1333,12 @@ static cudaError_t launch_inv_plane_cls(bool tile, const InvTarget *d_tgts, int 
         if (tile)
             return launch_pdl(k_inv_plane16<M>, dim3(nblocks), dim3(kPlane16Threads), smem, s, d_tgts, t0, t1,
                               block_lo, out, inv_c, step);
-    return launch_pdl(k_inv_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_tgts, t0, t1, block_lo, out,
-                      inv_c, step);
+    if constexpr (M == 192)
+        return launch_pdl(k_inv_plane_big<M>, dim3(nblocks), dim3(kPlaneBigThreads), smem, s, d_tgts, t0, t1,
+                          block_lo, out, inv_c, step);
+    else
+        return launch_pdl(k_inv_plane<M>, dim3(nblocks), dim3(kPlaneThreads), smem, s, d_tgts, t0, t1, block_lo, out,
+                          inv_c, step);
 }
 
 cudaError_t launch_fwd_plane(int cls, bool tile, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,

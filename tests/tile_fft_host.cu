@@ -74,5 +74,7 @@ int main()
     std::printf("inv32 %.6e\n", run_case<2, true, false, 16, 1>(32, 17));
     std::printf("inv48 %.6e\n", run_case<3, true, false, 16, 1>(48, 18));
     std::printf("fwd48_nin24 %.6e\n", run_case<3, false, false, 16, 1>(24, 19));
+    std::printf("rows192_sc193_inv %.6e\n", run_case<12, true, false, 1, 193>(192, 20));
+    std::printf("cols192_sp17_inv %.6e\n", run_case<12, true, false, 17, 1>(192, 21));
     return 0;
 }
