@@ -118,6 +118,40 @@ def test_overlapped_context_save_and_load(tmp_path):
             np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"step {i} domain {d}")
 
 
+def test_push_event_orders_a_side_stream_producer():
+    """Each step's inputs written on another stream after a delay (a spin
+    on that stream), with the event recorded after the writes: a push that
+    did not wait for the event would read the zero buffers.  The results are
+    the bits of the sequential context."""
+    doms, kw, T, start = CASES["fft"]
+    hists = [s.history(0, T, 0.05) for s in synth.seeded_sources(doms)]
+    flags = rp.RP_FLAG_GROUND_STATE_CLAMP
+    want, _ = _run(doms, hists, flags, start, **kw)
+    dev = torch.device("cuda", 0)
+    slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+    bufs = [[torch.zeros(4 * d.N, device=dev) for d in doms] for _ in range(T)]   # one set per step
+    side = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    got = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=flags | rp.RP_FLAG_OVERLAP_PUSH, **kw) as lib:
+        for i in range(T):
+            with torch.cuda.stream(side):
+                torch.cuda._sleep(200000)            # the producer is late
+                for d in range(len(doms)):
+                    bufs[i][d].copy_(slices[i][d].reshape(-1))
+                ready = torch.cuda.Event()
+                ready.record(side)
+            rp.rp_push_all_event(lib.ctx, [x[:d.N] for x, d in zip(bufs[i], doms)],
+                                 [x[d.N:] for x, d in zip(bufs[i], doms)], ready)
+            if i >= start:
+                lib.evaluate()
+                got[i] = [torch.cat([lib.phi[d], lib.A[d]]).cpu().numpy() for d in range(len(doms))]
+        lib.sync()
+    for i in want:
+        for d in range(len(doms)):
+            np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"step {i} domain {d}")
+
+
 def test_overlap_refusals():
     doms = CASES["fft"][0]
     with rp.RetardedPotentials(doms, synth.C_AU, 0.05, flags=rp.RP_FLAG_GROUND_STATE_CLAMP) as lib:
