@@ -154,3 +154,49 @@ def test_cfg5_learned_with_two_sided_fallback():
     assert q["npairs_learned"] + q["npairs_far"] == 992 and q["npairs_learned"] == rep["learned"] > 0
     for t, e in errs.items():
         assert max(e) <= TOL, ("cfg5 learned, two-sided fallback", t, e)
+
+
+@pytest.mark.parametrize("name,far_distance", [("cfg3", 500.0), ("cfg5", 500.0), ("cfg4", 250.0)])
+def test_total_field_every_source_active(name, far_distance):
+    """The deep workloads with every source active -- cfg3 (8 x 64^3, 56
+    two-sided far pairs), cfg5 (32 x 48^3, 992; the lane-shuffle plane
+    passes), cfg4 (64 domains of 24^3 to 96^3, 4032; the chunked 192-point
+    inverse plane pass): the total potentials of three targets at two steps
+    against the FP64 oracle (each source's samples for its pair's lag window
+    stored; 48 seeded nodes per target).  Bar: 1e-6 rel-L2, the FFT path's
+    (the far field is well below 1e-3 of the total at these distances)."""
+    import torch
+    w = workload(name)
+    dev = torch.device("cuda", 0)
+    gen = synth.DeviceSlices(w.sources, dev)
+    nd = len(w.domains)
+    targets = [1, nd // 2, nd - 1]
+    got = {}
+    with rp.RetardedPotentials(w.domains, w.c, w.dt, mode=rp.RP_MODE_LOWRANK, far_distance=far_distance,
+                               far_batch=32, far_source_points=4) as lib:
+        info = {(t, s): lib.pair_info(t, s) for t in targets for s in range(nd)}
+        L = lib.query()["max_lag"] + 24
+        check = {L - 1, L - 14}
+        for j in range(L):
+            r, J = gen.step(j, w.dt)
+            lib.push_all(r, J)
+            if j in check:
+                phi, A = lib.evaluate()
+                got[j] = {t: np.concatenate([phi[t].cpu().numpy()[None], A[t].cpu().numpy().reshape(3, -1)])
+                          for t in targets}
+        lib.sync()
+    rng = np.random.default_rng(11)
+    for step in sorted(check):
+        for t in targets:
+            hists, firsts = [], []
+            for s in range(nd):
+                p = info[(t, s)]
+                lo, hi = step - p["lag_hi"] - 1, step - p["lag_lo"]
+                hists.append(w.sources[s].history(lo, hi + 1, w.dt))
+                firsts.append(lo)
+            nodes = np.sort(rng.choice(w.domains[t].N, 48, replace=False))
+            vals, _ = oracle.eval_points_windows_parallel([d.origin for d in w.domains], [d.n for d in w.domains],
+                                                          [d.h for d in w.domains], hists, firsts, w.c, w.dt, t,
+                                                          step, nodes)
+            errs = rel_l2(got[step][t][:, nodes], vals)
+            assert max(errs) <= 1e-6, (name, "total", step, t, errs)
