@@ -139,3 +139,46 @@ def test_graph_replay_two_sided_far(owned):
     for i in range(start, T):
         for d in range(3):
             np.testing.assert_array_equal(got[i][d], want[i][d], err_msg=f"step {i} domain {d}")
+
+
+@pytest.mark.parametrize("cut", [150, 160])
+def test_save_and_load_two_sided_far(tmp_path, cut):
+    """rp_save_state in the middle of a 32-step batch of the gathered GEMM
+    (cut 150) and at a batch's first push (cut 160), rp_load_state into a
+    fresh context: the steps after it give the bits of the uninterrupted run
+    (the source coefficient rings and the targets' node-value rings are part
+    of the state)."""
+    import torch
+    dev = torch.device("cuda", 0)
+    doms, srcs = _setup()
+    T, start = 200, 100
+    hists = [s.history(0, T, 0.05) for s in srcs]
+    kw = dict(mode=rp.RP_MODE_LOWRANK, far_distance=100.0, far_batch=32, far_source_points=4)
+    slices = [[torch.from_numpy(np.ascontiguousarray(h[i])).to(dev) for h in hists] for i in range(T)]
+
+    def push(lib, i):
+        lib.push_all([x[0] for x in slices[i]], [x[1:].reshape(-1) for x in slices[i]])
+
+    want = {}
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, **kw) as lib:
+        for i in range(T):
+            push(lib, i)
+            if i >= start:
+                p_, a_ = lib.evaluate()
+                want[i] = [torch.cat([p_[d], a_[d]]).cpu().numpy() for d in range(3)]
+    path = str(tmp_path / "state.bin")
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, **kw) as lib:
+        for i in range(cut):
+            push(lib, i)
+            if i >= start:
+                lib.evaluate()
+        rp.rp_save_state(lib.ctx, path)
+    with rp.RetardedPotentials(doms, synth.C_AU, 0.05, **kw) as lib:
+        rp.rp_load_state(lib.ctx, path)
+        assert lib.query()["step"] == cut - 1
+        for i in range(cut, T):
+            push(lib, i)
+            p_, a_ = lib.evaluate()
+            got = [torch.cat([p_[d], a_[d]]).cpu().numpy() for d in range(3)]
+            for d in range(3):
+                np.testing.assert_array_equal(got[d], want[i][d], err_msg=f"cut {cut} step {i} domain {d}")
