@@ -420,24 +420,10 @@ __host__ __device__ __forceinline__ void tile_stage2(float2 *T, int c, int k1)
     for (int k2 = 0; k2 < B; ++k2) L[k2 * SP] = v[k2];
 }
 
-// The whole tile by one warp (all 32 lanes call it): stage 1 in B/2 rounds
-// of 32 tasks, stage 2 in 8.  tw: exp(-2 pi i j/M), j < M.
-template <int B, bool INV, bool HALF>
-__device__ __forceinline__ void tile_fft16(float2 *T, const float2 *tw, int nin, int lane)
-{
-    static_assert(B % 2 == 0, "tile transform: B even");
-    const int c = lane & 15, hi = lane >> 4;
-#pragma unroll 1
-    for (int r = 0; r < B / 2; ++r) tile_stage1<B, INV, HALF>(T, tw, nin, c, 2 * r + hi);
-    __syncwarp();
-#pragma unroll 1
-    for (int r = 0; r < 8; ++r) tile_stage2<B, INV>(T, c, 2 * r + hi);
-    __syncwarp();
-}
-
 // The whole tile by a pair of warps (the 64 threads that call it with
 // half = 0 and 1; named barrier bar_id with 64 threads between the stages and
-// at the end): the rounds of each stage alternate between the two warps.
+// at the end): stage 1 in B/2 rounds of 32 tasks, stage 2 in 8, the rounds of
+// each stage alternating between the two warps.  tw: exp(-2 pi i j/M), j < M.
 template <int B, bool INV, bool HALF>
 __device__ __forceinline__ void tile_fft16_pair(float2 *T, const float2 *tw, int nin, int lane, int half, int bar_id)
 {
