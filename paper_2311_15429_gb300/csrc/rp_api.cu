@@ -1021,7 +1021,7 @@ rp_status rp_finalize(rp_ctx *ctx)
         for (size_t r = 0; r < ring_keys.size(); ++r) blocks[class_slot(ring_class((int)r))] += 4 * ctx->doms[ring_keys[r].first].n[2];
         for (size_t r = 0; r < ring_keys.size(); ++r) {
             const int cls = ring_class((int)r);
-            ctx->fwd_tile[class_slot(cls)] = plane_tile_form(cls, blocks[class_slot(cls)]);
+            ctx->fwd_tile[class_slot(cls)] = plane_tile_form(cls, blocks[class_slot(cls)], false);
         }
     }
     for (size_t i = 0; i < ring_order.size(); ++i) {
@@ -1077,7 +1077,8 @@ rp_status rp_finalize(rp_ctx *ctx)
     {   // the inverse plane pass's form per class, from its blocks
         int blocks[7] = {};
         for (int t : tgt_order) blocks[class_slot(tgt_class(t))] += 4 * ctx->doms[t].n[2];
-        for (int t : tgt_order) ctx->inv_tile[class_slot(tgt_class(t))] = plane_tile_form(tgt_class(t), blocks[class_slot(tgt_class(t))]);
+        for (int t : tgt_order) ctx->inv_tile[class_slot(tgt_class(t))] =
+                plane_tile_form(tgt_class(t), blocks[class_slot(tgt_class(t))], true);
     }
     for (int t : tgt_order) {
         const DomainDesc &T = ctx->doms[t];

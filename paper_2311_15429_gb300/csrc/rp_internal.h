@@ -240,12 +240,16 @@ cudaError_t launch_ring_push(const RawRing *d_rings, const IoPtrs &in, int d0, i
 // blocks per SM: the better form while a class's planes fit in about one wave),
 // tile = false the lane-shuffle line (5-6 blocks per SM: the better form over
 // many waves).  The planner picks per class from its block count
-// (plane_tile_form), so a plan's bits do not depend on timing.
+// (plane_tile_form), so a plan's bits do not depend on timing.  The inverse
+// pass at M = 128 takes the tile form at any block count: there both forms
+// hold about 100 KB of shared memory per block (two blocks per SM), so the
+// lane-shuffle form has no occupancy to trade for its extra instructions.
 constexpr int kPlaneTileMaxBlocks = 1024;
 bool plane_tile_class(int size_class);
-inline bool plane_tile_form(int size_class, int blocks)
+inline bool plane_tile_form(int size_class, int blocks, bool inverse)
 {
-    return plane_tile_class(size_class) && blocks <= kPlaneTileMaxBlocks;
+    if (!plane_tile_class(size_class)) return false;
+    return blocks <= kPlaneTileMaxBlocks || (inverse && size_class == 128);
 }
 cudaError_t launch_fwd_plane(int size_class, bool tile, const FwdRing *d_rings, const IoPtrs &in, int r0, int r1,
                              int block_lo, int nblocks, size_t smem, int far_slot, cudaStream_t s);
