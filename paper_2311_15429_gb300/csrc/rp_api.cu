@@ -150,7 +150,7 @@ rp_status plan_mac_tma(rp_ctx *ctx, int max_optin)
 {
     ctx->tma = false;
     for (int cls : {32, 48, 64, 96, 128, 192}) {
-        int n = mac_tma_stages(cls, max_optin);
+        int n = mac_tma_stages(cls, max_optin, ctx->comp);
         if (ctx->cfg.mac_stages >= 2) n = std::min(n, ctx->cfg.mac_stages);
         ctx->mac_stages[class_slot(cls)] = n;
         if (n < 2) {

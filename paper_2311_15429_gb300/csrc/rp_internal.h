@@ -275,9 +275,9 @@ cudaError_t launch_fields(int nx, int ny, int nz, double h, double c, double dt,
                           const float *A1, const float *A2, float *E, float *B, cudaStream_t s);
 
 // TMA-fed MAC (rp_mac_tma.cu): cubic classes 32..192 only.
-int mac_tma_stages(int M, int smem_optin);
+int mac_tma_stages(int M, int smem_optin, bool comp);
 cudaError_t launch_wait_selftest(long long limit_cycles, int *d_err, cudaStream_t s);
-size_t mac_tma_smem(int M, int nstages);
+size_t mac_tma_smem(int M, int nstages, bool comp);
 cudaError_t open_mac_tma_smem_limit(int max_optin);
 // comp: the Kahan-compensated variant (consumer_warps must be kCompWarps)
 constexpr int kCompWarps = 12;

@@ -153,27 +153,28 @@ __device__ __forceinline__ void named_sync(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// Inverse FFT along z of the four field tiles of `acc` ([field][M][16],
-// dense) by the two-stage tile transform (rp_fft.cuh), its tasks shared by
-// warps w = 0 .. nw-1 (this one is w; barrier `bar` of nw warps between the
-// stages), then rows z < nz (row z of the transform sits at tile_row(z)) to T2.
-template <int M>
+// Inverse FFT along z of the NF field tiles of `acc` ([field][M][16], dense;
+// fields f0 .. f0 + NF - 1) by the two-stage tile transform (rp_fft.cuh), its
+// tasks shared by warps w = 0 .. nw-1 (this one is w; barrier `bar` of nw
+// warps between the stages), then rows z < nz (row z of the transform sits at
+// tile_row(z)) to T2.
+template <int M, int NF>
 __device__ __forceinline__ void column_tile_store(float2 *acc, const float2 *tw, const InvTarget &T, int kxi, int ky0,
-                                                  int w, int nw, int lane, int bar)
+                                                  int f0, int w, int nw, int lane, int bar)
 {
     constexpr int B = M / 16, FS = M * kTileY;
     const int tid = w * 32 + lane, nt = nw * 32;
-    for (int i = tid; i < 4 * 16 * B; i += nt) {
+    for (int i = tid; i < NF * 16 * B; i += nt) {
         const int c = i & 15, rest = i >> 4, f = rest / B, n2 = rest - f * B;
         tile_stage1<B, true, false>(acc + f * FS, tw, M, c, n2);
     }
     named_sync(bar, nt);
-    for (int i = tid; i < 4 * 256; i += nt) tile_stage2<B, true>(acc + (i >> 8) * FS, i & 15, (i >> 4) & 15);
+    for (int i = tid; i < NF * 256; i += nt) tile_stage2<B, true>(acc + (i >> 8) * FS, i & 15, (i >> 4) & 15);
     named_sync(bar, nt);
     const int nz = T.nz;
     const long long t2_field = (long long)(M / 2 + 1) * nz * M;
-    float2 *dst = T.t2 + (long long)kxi * nz * M + ky0;
-    for (int i = tid; i < 4 * nz * (kTileY / 2); i += nt) {
+    float2 *dst = T.t2 + (long long)f0 * t2_field + (long long)kxi * nz * M + ky0;
+    for (int i = tid; i < NF * nz * (kTileY / 2); i += nt) {
         const int f = i / (nz * (kTileY / 2)), rem = i - f * nz * (kTileY / 2);
         const int zi = rem >> 3, pp = rem & 7;
         *reinterpret_cast<float4 *>(dst + f * t2_field + (long long)zi * M + 2 * pp) =
@@ -185,6 +186,13 @@ __device__ __forceinline__ void column_tile_store(float2 *acc, const float2 *tw,
 // MAC warps hold twice the accumulators and need the registers.
 template <bool COMP>
 __host__ __device__ constexpr int fft_warps() { return COMP ? 3 : kFftWarps; }
+
+// Field groups per tile: the compensated MAC at M = 192 would hold 128
+// accumulator and compensation floats per MAC thread for all four fields (and
+// spill them), so it sums the tile in two passes of two fields each, every
+// pass over all the tile's entries (the kernel tile read again, mostly from
+// L2), and hands each pass's two fields to the FFT warps on its own.
+__host__ __device__ constexpr int field_groups(int M, bool comp) { return comp && M == 192 ? 2 : 1; }
 
 // M: padded FFT size of the class; CW: multiply-accumulate warps (the block
 // has CW + fft_warps + 1); FPC: field tiles per ring copy (1, 2 or 4; they
@@ -205,11 +213,14 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
     constexpr int ROWS = (M + RSTEP - 1) / RSTEP;
     constexpr int NTY = M / kTileY;
     constexpr int FS = M * kTileY;                   // float2 per field of the FFT tile (dense rows)
+    constexpr int NFG = field_groups(M, COMP);      // passes per tile
+    constexpr int FH = 4 / NFG;                      // fields per pass
+    static_assert(FH % FPC == 0, "k_mac_tma: whole field copies per pass");
     extern __shared__ __align__(128) unsigned char smem[];
     unsigned char *sstages = smem;                                   // [ns][SSTAGE]
     unsigned char *gstages = smem + (size_t)ns * SSTAGE;             // [NG][STAGE]
     float2 *acc = reinterpret_cast<float2 *>(gstages + (size_t)NG * STAGE);
-    float2 *tw = acc + 4 * FS;
+    float2 *tw = acc + FH * FS;                                      // acc: [FH][M][16]
     uint64_t *sfull = reinterpret_cast<uint64_t *>(tw + M);
     uint64_t *sempty = sfull + ns;
     uint64_t *gfull = sempty + ns;
@@ -272,8 +283,9 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
             const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
             const long long tile_off = (long long)(b - T.tile0) * M * kTileY;
             const int nr = T.er - T.e0, nc = T.e1 - T.er;   // real (self) entries come first
-            for (int k = 0; k < nr + nc && ok; ++k) {
-                const MacEntry &E = entries[T.e0 + k];
+            for (int k = 0; k < NFG * (nr + nc) && ok; ++k) {   // pass h = k / (nr + nc) of the tile
+                const int h = k / (nr + nc);
+                const MacEntry &E = entries[T.e0 + k - h * (nr + nc)];
                 long long j = step - E.lag;
                 if (clamp && j < 0) j = 0;
                 const int slot = (int)(j % E.depth);
@@ -288,14 +300,14 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
                     bulk_load(gstages + (size_t)s * STAGE, src, bytes, &gfull[s], keep);
                     ++qg;
                 }
-                // the four field tiles of the source spectrum, FPC per copy
+                // the pass's field tiles of the source spectrum (fields h FH ..), FPC per copy
                 const float2 *fields = E.ring + (long long)slot * E.slot_elems + 4 * tile_off;
-                for (int o = 0; o < 4 / FPC; ++o) {
+                for (int o = 0; o < FH / FPC; ++o) {
                     if (!(ok = acquire(sempty, ns, qs))) break;
                     const int s = qs % ns;
                     mbar_expect_tx(&sfull[s], SSTAGE);
-                    bulk_load(sstages + (size_t)s * SSTAGE, fields + (long long)o * FPC * M * kTileY, SSTAGE,
-                              &sfull[s], stream);
+                    bulk_load(sstages + (size_t)s * SSTAGE, fields + (long long)(h * FH + o * FPC) * M * kTileY,
+                              SSTAGE, &sfull[s], stream);
                     ++qs;
                 }
             }
@@ -308,34 +320,37 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
         return;
     }
 
-    // Tile hand-over: the MAC warps accumulate a tile in registers, store it
-    // to the FFT tile and signal accfull; the FFT warps transform and store it
-    // while the MAC warps accumulate the next one, then signal accempty.  A
-    // block's last tile has no successor, so all its consumer warps share
+    // Hand-over, per pass of a tile (one pass of all four fields, or two of
+    // two): the MAC warps accumulate the pass in registers, store it to the
+    // FFT tile and signal accfull; the FFT warps transform and store it while
+    // the MAC warps accumulate the next pass, then signal accempty.  A
+    // block's last pass has no successor, so all its consumer warps share
     // that transform (barrier 2 in place of the two signals).
     constexpr int kBarFft = 1, kBarAll = 2;
     if (warp >= kConsumerWarps) {
         // ------------------------------------------------------------ FFT warps
         const int fw = warp - kConsumerWarps;
         uint32_t it = 0;
-        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
             const int b = tile + tile_lo;
             const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
             const int local = b - T.tile0, kxi = local / NTY, ky0 = (local % NTY) * kTileY;
-            if (tile + (int)gridDim.x >= ntiles) {
-                named_sync(kBarAll, (kConsumerWarps + FW) * 32);
-                column_tile_store<M>(acc, tw, T, kxi, ky0, warp, kConsumerWarps + FW, lane, kBarAll);
-                break;
+            for (int h = 0; h < NFG; ++h, ++it) {
+                if (tile + (int)gridDim.x >= ntiles && h == NFG - 1) {
+                    named_sync(kBarAll, (kConsumerWarps + FW) * 32);
+                    column_tile_store<M, FH>(acc, tw, T, kxi, ky0, h * FH, warp, kConsumerWarps + FW, lane, kBarAll);
+                    return;
+                }
+                const bool have = wait_or_abort(accfull, it & 1);
+                // on an abort the sums are not used: skip the transform, keep the barriers
+                if (have) column_tile_store<M, FH>(acc, tw, T, kxi, ky0, h * FH, fw, FW, lane, kBarFft);
+                else {
+                    named_sync(kBarFft, FW * 32);
+                    named_sync(kBarFft, FW * 32);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(accempty);
             }
-            const bool have = wait_or_abort(accfull, it & 1);
-            // on an abort the sums are not used: skip the transform, keep the barriers
-            if (have) column_tile_store<M>(acc, tw, T, kxi, ky0, fw, FW, lane, kBarFft);
-            else {
-                named_sync(kBarFft, FW * 32);
-                named_sync(kBarFft, FW * 32);
-            }
-            __syncwarp();
-            if (lane == 0) mbar_arrive(accempty);
         }
         return;
     }
@@ -354,128 +369,130 @@ __global__ void __launch_bounds__((CW + fft_warps<COMP>() + 1) * 32, 1)
         if (lane == 0) mbar_arrive(&empty[q % n]);
     };
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
         const int b = tile + tile_lo;
         const InvTarget &T = tgts[owner(tgts, t0, t1, b, &InvTarget::tile0)];
+        for (int h = 0; h < NFG; ++h, ++it) {   // pass h: fields h FH .. h FH + FH - 1
+            float4 a[ROWS][FH];
+            float4 cmp[COMP ? ROWS : 1][FH];   // Kahan compensation (COMP only)
+#pragma unroll
+            for (int i = 0; i < ROWS; ++i)
+#pragma unroll
+                for (int f = 0; f < FH; ++f) a[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int i = 0; i < (COMP ? ROWS : 1); ++i)
+#pragma unroll
+                for (int f = 0; f < FH; ++f) cmp[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
 
-        float4 a[ROWS][4];
-        float4 cmp[COMP ? ROWS : 1][4];   // Kahan compensation (COMP only)
+            for (int e = T.e0; e < T.er; ++e) {   // real kernels (self pair)
+                float2 g[ROWS];
+                const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
+                const float *Gt = reinterpret_cast<const float *>(st);   // [M][16]
 #pragma unroll
-        for (int i = 0; i < ROWS; ++i)
+                for (int i = 0; i < ROWS; ++i) {
+                    const int r = r0 + RSTEP * i;
+                    g[i] = (st && r < M) ? *reinterpret_cast<const float2 *>(Gt + r * 16 + 2 * p)
+                                         : make_float2(0.f, 0.f);
+                }
+                give(gempty, NG, qg++);
 #pragma unroll
-            for (int f = 0; f < 4; ++f) a[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
+                for (int o = 0; o < FH / FPC; ++o) {
+                    const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
 #pragma unroll
-        for (int i = 0; i < (COMP ? ROWS : 1); ++i)
+                    for (int ff = 0; ff < FPC; ++ff) {
+                        const int f = o * FPC + ff;
+                        const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);   // [M][8]
 #pragma unroll
-            for (int f = 0; f < 4; ++f) cmp[i][f] = make_float4(0.f, 0.f, 0.f, 0.f);
-
-        for (int e = T.e0; e < T.er; ++e) {   // real kernels (self pair)
-            float2 g[ROWS];
-            const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
-            const float *Gt = reinterpret_cast<const float *>(st);   // [M][16]
-#pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-                const int r = r0 + RSTEP * i;
-                g[i] = (st && r < M) ? *reinterpret_cast<const float2 *>(Gt + r * 16 + 2 * p) : make_float2(0.f, 0.f);
-            }
-            give(gempty, NG, qg++);
-#pragma unroll
-            for (int o = 0; o < 4 / FPC; ++o) {
-                const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
-#pragma unroll
-                for (int ff = 0; ff < FPC; ++ff) {
-                    const int f = o * FPC + ff;
-                    const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);   // [M][8]
-#pragma unroll
-                    for (int i = 0; i < ROWS; ++i) {
-                        const int r = r0 + RSTEP * i;
-                        if (sf && r < M) {
-                            const float4 s = S4[r * 8 + p];
-                            if constexpr (COMP) {
-                                float4 &c = cmp[COMP ? i : 0][f];
-                                kahan_add(a[i][f].x, c.x, g[i].x * s.x);
-                                kahan_add(a[i][f].y, c.y, g[i].x * s.y);
-                                kahan_add(a[i][f].z, c.z, g[i].y * s.z);
-                                kahan_add(a[i][f].w, c.w, g[i].y * s.w);
-                            } else {
-                                a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
-                                a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
-                                a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
-                                a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                        for (int i = 0; i < ROWS; ++i) {
+                            const int r = r0 + RSTEP * i;
+                            if (sf && r < M) {
+                                const float4 s = S4[r * 8 + p];
+                                if constexpr (COMP) {
+                                    float4 &c = cmp[COMP ? i : 0][f];
+                                    kahan_add(a[i][f].x, c.x, g[i].x * s.x);
+                                    kahan_add(a[i][f].y, c.y, g[i].x * s.y);
+                                    kahan_add(a[i][f].z, c.z, g[i].y * s.z);
+                                    kahan_add(a[i][f].w, c.w, g[i].y * s.w);
+                                } else {
+                                    a[i][f].x = fmaf(g[i].x, s.x, a[i][f].x);
+                                    a[i][f].y = fmaf(g[i].x, s.y, a[i][f].y);
+                                    a[i][f].z = fmaf(g[i].y, s.z, a[i][f].z);
+                                    a[i][f].w = fmaf(g[i].y, s.w, a[i][f].w);
+                                }
                             }
                         }
                     }
+                    give(sempty, ns, qs++);
                 }
-                give(sempty, ns, qs++);
             }
-        }
-        for (int e = T.er; e < T.e1; ++e) {   // complex kernels (other sources)
-            float4 g[ROWS];
-            const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
-            const float4 *G4 = reinterpret_cast<const float4 *>(st);
+            for (int e = T.er; e < T.e1; ++e) {   // complex kernels (other sources)
+                float4 g[ROWS];
+                const unsigned char *st = take(gstages, STAGE, gfull, NG, qg);
+                const float4 *G4 = reinterpret_cast<const float4 *>(st);
 #pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-                const int r = r0 + RSTEP * i;
-                g[i] = (st && r < M) ? G4[r * 8 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
-            }
-            give(gempty, NG, qg++);
+                for (int i = 0; i < ROWS; ++i) {
+                    const int r = r0 + RSTEP * i;
+                    g[i] = (st && r < M) ? G4[r * 8 + p] : make_float4(0.f, 0.f, 0.f, 0.f);
+                }
+                give(gempty, NG, qg++);
 #pragma unroll
-            for (int o = 0; o < 4 / FPC; ++o) {
-                const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
+                for (int o = 0; o < FH / FPC; ++o) {
+                    const unsigned char *sf = take(sstages, SSTAGE, sfull, ns, qs);
 #pragma unroll
-                for (int ff = 0; ff < FPC; ++ff) {
-                    const int f = o * FPC + ff;
-                    const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);
+                    for (int ff = 0; ff < FPC; ++ff) {
+                        const int f = o * FPC + ff;
+                        const float4 *S4 = reinterpret_cast<const float4 *>(sf + ff * STAGE);
 #pragma unroll
-                    for (int i = 0; i < ROWS; ++i) {
-                        const int r = r0 + RSTEP * i;
-                        if (sf && r < M) {
-                            const float4 s = S4[r * 8 + p];
-                            float4 &x = a[i][f];
-                            if constexpr (COMP) {
-                                float4 &c = cmp[COMP ? i : 0][f];
-                                kahan_add(x.x, c.x, fmaf(g[i].x, s.x, -g[i].y * s.y));
-                                kahan_add(x.y, c.y, fmaf(g[i].x, s.y, g[i].y * s.x));
-                                kahan_add(x.z, c.z, fmaf(g[i].z, s.z, -g[i].w * s.w));
-                                kahan_add(x.w, c.w, fmaf(g[i].z, s.w, g[i].w * s.z));
-                            } else {
-                                x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
-                                x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
-                                x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
-                                x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                        for (int i = 0; i < ROWS; ++i) {
+                            const int r = r0 + RSTEP * i;
+                            if (sf && r < M) {
+                                const float4 s = S4[r * 8 + p];
+                                float4 &x = a[i][f];
+                                if constexpr (COMP) {
+                                    float4 &c = cmp[COMP ? i : 0][f];
+                                    kahan_add(x.x, c.x, fmaf(g[i].x, s.x, -g[i].y * s.y));
+                                    kahan_add(x.y, c.y, fmaf(g[i].x, s.y, g[i].y * s.x));
+                                    kahan_add(x.z, c.z, fmaf(g[i].z, s.z, -g[i].w * s.w));
+                                    kahan_add(x.w, c.w, fmaf(g[i].z, s.w, g[i].w * s.z));
+                                } else {
+                                    x.x = fmaf(g[i].x, s.x, fmaf(-g[i].y, s.y, x.x));
+                                    x.y = fmaf(g[i].x, s.y, fmaf(g[i].y, s.x, x.y));
+                                    x.z = fmaf(g[i].z, s.z, fmaf(-g[i].w, s.w, x.z));
+                                    x.w = fmaf(g[i].z, s.w, fmaf(g[i].w, s.z, x.w));
+                                }
                             }
                         }
                     }
+                    give(sempty, ns, qs++);
                 }
-                give(sempty, ns, qs++);
             }
-        }
 
-        // hand the sums to the FFT warps once they are done with the previous tile
-        if (it == 0 || wait_or_abort(accempty, (it - 1) & 1)) {
+            // hand the sums to the FFT warps once they are done with the previous pass
+            if (it == 0 || wait_or_abort(accempty, (it - 1) & 1)) {
 #pragma unroll
-            for (int i = 0; i < ROWS; ++i) {
-                const int r = r0 + RSTEP * i;
-                if (r >= M) continue;
+                for (int i = 0; i < ROWS; ++i) {
+                    const int r = r0 + RSTEP * i;
+                    if (r >= M) continue;
 #pragma unroll
-                for (int f = 0; f < 4; ++f) {
-                    if constexpr (COMP) {   // the compensated total
-                        const float4 &c = cmp[COMP ? i : 0][f];
-                        a[i][f] = make_float4(a[i][f].x - c.x, a[i][f].y - c.y, a[i][f].z - c.z, a[i][f].w - c.w);
+                    for (int f = 0; f < FH; ++f) {
+                        if constexpr (COMP) {   // the compensated total
+                            const float4 &c = cmp[COMP ? i : 0][f];
+                            a[i][f] = make_float4(a[i][f].x - c.x, a[i][f].y - c.y, a[i][f].z - c.z, a[i][f].w - c.w);
+                        }
+                        *reinterpret_cast<float4 *>(acc + f * FS + r * kTileY + 2 * p) = a[i][f];
                     }
-                    *reinterpret_cast<float4 *>(acc + f * FS + r * kTileY + 2 * p) = a[i][f];
                 }
             }
+            if (tile + (int)gridDim.x >= ntiles && h == NFG - 1) {
+                named_sync(kBarAll, (kConsumerWarps + FW) * 32);
+                const int local = b - T.tile0;
+                column_tile_store<M, FH>(acc, tw, T, local / NTY, (local % NTY) * kTileY, h * FH, warp,
+                                         kConsumerWarps + FW, lane, kBarAll);
+                return;
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(accfull);
         }
-        if (tile + (int)gridDim.x >= ntiles) {
-            named_sync(kBarAll, (kConsumerWarps + FW) * 32);
-            const int local = b - T.tile0;
-            column_tile_store<M>(acc, tw, T, local / NTY, (local % NTY) * kTileY, warp, kConsumerWarps + FW, lane,
-                                 kBarAll);
-            break;
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(accfull);
     }
 }
 
@@ -492,20 +509,20 @@ cudaError_t launch_wait_selftest(long long limit_cycles, int *d_err, cudaStream_
 
 int mac_tma_fields_per_copy(int M) { return M <= 96 ? 4 : (M == 128 ? 2 : 1); }
 
-int mac_tma_stages(int M, int smem_optin)
+int mac_tma_stages(int M, int smem_optin, bool comp)
 {
     const long long sstage = (long long)mac_tma_fields_per_copy(M) * M * 128;
-    const long long fixed = (long long)mac_tma_smem(M, 0);   // kernel-tile ring, FFT tile, twiddles, barriers
+    const long long fixed = (long long)mac_tma_smem(M, 0, comp);   // kernel-tile ring, FFT tile, twiddles, barriers
     long long n = (smem_optin - fixed) / (sstage + 16);      // + two mbarriers per stage
     if (n > kMaxStages) n = kMaxStages;
     return (int)n;
 }
 
-size_t mac_tma_smem(int M, int nstages)
+size_t mac_tma_smem(int M, int nstages, bool comp)
 {
-    const size_t stage = (size_t)M * 128;
+    const size_t stage = (size_t)M * 128, fields = 4 / field_groups(M, comp);   // fields of the FFT tile
     return (size_t)nstages * mac_tma_fields_per_copy(M) * stage + kKernelStages * stage +
-           sizeof(float2) * (4 * (size_t)M * kTileY + M) + 16 * ((size_t)nstages + kKernelStages) + 16 + 16;
+           sizeof(float2) * (fields * (size_t)M * kTileY + M) + 16 * ((size_t)nstages + kKernelStages) + 16 + 16;
 }
 
 cudaError_t open_mac_tma_smem_limit(int max_optin)
@@ -533,7 +550,7 @@ cudaError_t launch_mac_tma(int cls, int cw, bool comp, const InvTarget *d_tgts, 
     if (ntiles <= 0) return cudaSuccess;
     if (comp ? cw != kCompWarps : (cw != 8 && cw != 12 && cw != 16)) return cudaErrorInvalidValue;
     if (nstages < 2 || nstages > kMaxStages) return cudaErrorInvalidValue;
-    const size_t smem = mac_tma_smem(cls, nstages);
+    const size_t smem = mac_tma_smem(cls, nstages, comp);
     const int threads = (cw + (comp ? fft_warps<true>() : fft_warps<false>()) + 1) * 32;
     cudaError_t e = cudaSuccess;
 #define RP_GO(M, CW, F, C)                                                                                   \
